@@ -1,0 +1,178 @@
+"""Stencil selection, FP64, plain.  Test infrastructure only (see package doc).
+
+Section 2: the operator at x_c is approximated over "a set of n neighbouring
+nodes".  Readings taken where the paper is silent:
+
+* Scattered stencil = the n nodes with the smallest key (d2, id), where
+  d2 = ((dx*dx) + (dy*dy)) + (dz*dz) in float64, evaluated exactly in that
+  order with dx = x_i - x_c, and id the node index.  The centre (d2 = 0) comes
+  first.  Ties go to the lower node id.
+* Regular (MON) stencil = {c, c-e1, c+e1, c-e2, c+e2[, c-e3, c+e3]} looked up
+  through integer lattice coordinates round(x/h).  A node is on the lattice
+  when every |x_k/h - round(x_k/h)| <= 1e-6; if two nodes share a lattice point
+  the lower id owns it.
+* A boundary node's stencil is the node itself plus its n-1 nearest interior
+  (non-boundary) nodes, by the same key.  Boundary stencils serve only the
+  normal-derivative rows of the Neumann conditions; keeping other boundary
+  nodes out of them makes each such row hold exactly after an explicit update
+  (with boundary neighbours the explicit closure couples the walls and its
+  error grows from step to step).
+* A node uses MON only when it is flagged regular, is not a boundary node and
+  all 2d lattice neighbours exist; any other regular-flagged node is demoted to
+  RBF-FD (Section 2 notes that MON is only stable on regular nodes).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+LATTICE_TOL = 1e-6
+
+
+def sq_dist(coords, c, ids=None):
+    """float64 d2 from node c to nodes ``ids`` (all nodes when None), summed in
+    coordinate order with no fused multiply-add."""
+    dim = coords.shape[0]
+    if ids is None:
+        ids = slice(None)
+    d2 = None
+    for k in range(dim):
+        dk = coords[k, ids] - coords[k, c]
+        t = dk * dk
+        d2 = t if d2 is None else d2 + t
+    return d2
+
+
+def knn_bruteforce(coords, centers, n, candidates=None):
+    """Definition: for each centre, all N distances, order by (d2, id), keep n.
+    With ``candidates`` (bool [N]) only the centre itself and candidate nodes
+    may enter the stencil."""
+    N = coords.shape[1]
+    ids = np.arange(N)
+    out = np.empty((len(centers), n), dtype=np.int64)
+    for r, c in enumerate(centers):
+        d2 = sq_dist(coords, int(c))
+        if candidates is not None:
+            allowed = candidates.copy()
+            allowed[int(c)] = True
+            d2 = np.where(allowed, d2, np.inf)
+        order = np.lexsort((ids, d2))
+        out[r] = order[:n]
+    return out
+
+
+def knn_kdtree(coords, centers, n, margin=8, candidates=None):
+    """Same result as ``knn_bruteforce`` for large N.  A k-d tree proposes the
+    nearest n+margin candidates; the candidate set is provably complete when the
+    last candidate is strictly farther than the n-th (with a relative guard
+    against the tree's own rounding), otherwise the query is widened.  The final
+    order is taken with the exact (d2, id) key."""
+    from scipy.spatial import cKDTree
+
+    centers = np.asarray(centers, dtype=np.int64)
+    if candidates is None:
+        pool = np.arange(coords.shape[1])
+    else:
+        pool = np.flatnonzero(candidates)
+    pts = coords.T
+    tree = cKDTree(pts[pool])
+    out = np.empty((len(centers), n), dtype=np.int64)
+    todo = np.arange(len(centers))
+    # the centre itself is always a member; search n nodes among the pool besides it
+    kk = n + margin
+    while len(todo):
+        kq = min(kk, len(pool))
+        dist, idx = tree.query(pts[centers[todo]], k=kq)
+        dist = np.atleast_2d(dist)
+        idx = pool[np.atleast_2d(idx)]
+        complete = (kq == len(pool)) | (dist[:, -1] > dist[:, n - 1] * (1.0 + 1e-9) + 1e-300)
+        for r in np.flatnonzero(complete):
+            c = int(centers[todo[r]])
+            cand = np.unique(np.r_[c, idx[r]])
+            d2 = sq_dist(coords, c, cand)
+            order = np.lexsort((cand, d2))
+            out[todo[r]] = cand[order[:n]]
+        todo = todo[~complete]
+        kk *= 2
+    return out
+
+
+def lattice_map(coords, h):
+    """Dict lattice ijk tuple -> lowest node id lying on that lattice point."""
+    dim, N = coords.shape
+    q = coords / h
+    r = np.rint(q)
+    on = np.all(np.abs(q - r) <= LATTICE_TOL, axis=0)
+    m = {}
+    ri = r.astype(np.int64)
+    for i in np.flatnonzero(on):
+        key = tuple(int(v) for v in ri[:, i])
+        if key not in m:
+            m[key] = int(i)
+    return m, ri, on
+
+
+def mon_stencils(coords, is_regular, is_boundary, h):
+    """Regular stencils.  Returns (nodes, idx[len(nodes), 2d+1]) for the nodes
+    that keep MON, and the array of demoted node ids."""
+    dim, N = coords.shape
+    m, ri, on = lattice_map(coords, h)
+    nodes, rows, demoted = [], [], []
+    for c in np.flatnonzero(is_regular):
+        c = int(c)
+        if is_boundary[c] or not on[c] or m.get(tuple(int(v) for v in ri[:, c])) != c:
+            demoted.append(c)
+            continue
+        row = [c]
+        ok = True
+        for k in range(dim):
+            for sgn in (-1, 1):
+                key = list(int(v) for v in ri[:, c])
+                key[k] += sgn
+                j = m.get(tuple(key))
+                if j is None:
+                    ok = False
+                    break
+                row.append(j)
+            if not ok:
+                break
+        if ok:
+            nodes.append(c)
+            rows.append(row)
+        else:
+            demoted.append(c)
+    idx = np.array(rows, dtype=np.int64).reshape(len(rows), 2 * dim + 1)
+    return np.array(nodes, dtype=np.int64), idx, np.array(demoted, dtype=np.int64)
+
+
+def build_stencils(coords, is_regular, is_boundary, h, n, centers=None, use_kdtree=None):
+    """All stencils of a node set (or of the subset ``centers``).
+
+    Returns dict with
+      mon_nodes, mon_idx   nodes that use MON and their 2d+1 stencil
+      rbf_nodes, rbf_idx   nodes that use RBF-FD (scattered + demoted) and their
+                           n-node stencil
+      demoted              regular-flagged nodes demoted to RBF-FD
+    """
+    dim, N = coords.shape
+    mon_nodes, mon_idx, demoted = mon_stencils(coords, is_regular, is_boundary, h)
+    kind = np.ones(N, dtype=np.int8)  # 1 = RBF-FD
+    kind[mon_nodes] = 0
+    if centers is not None:
+        centers = np.asarray(centers, dtype=np.int64)
+        sel = kind[centers] == 0
+        keep = np.isin(mon_nodes, centers)
+        mon_nodes, mon_idx = mon_nodes[keep], mon_idx[keep]
+        rbf_nodes = centers[~sel]
+    else:
+        rbf_nodes = np.flatnonzero(kind == 1)
+    if use_kdtree is None:
+        use_kdtree = N * len(rbf_nodes) > 2e7
+    knn = knn_kdtree if use_kdtree else knn_bruteforce
+    rbf_idx = np.zeros((len(rbf_nodes), n), dtype=np.int64)
+    on_bnd = np.asarray(is_boundary)[rbf_nodes] != 0
+    if np.any(~on_bnd):
+        rbf_idx[~on_bnd] = knn(coords, rbf_nodes[~on_bnd], n)
+    if np.any(on_bnd):
+        rbf_idx[on_bnd] = knn(coords, rbf_nodes[on_bnd], n, candidates=np.asarray(is_boundary) == 0)
+    return dict(mon_nodes=mon_nodes, mon_idx=mon_idx, rbf_nodes=rbf_nodes, rbf_idx=rbf_idx,
+                demoted=demoted)

@@ -1,0 +1,83 @@
+"""Pins for the oracle's stencil selection (Section 2: n neighbouring nodes)."""
+import json
+import os
+
+import numpy as np
+
+from oracle import stencils as ost
+from paper_2303_01760_gb300 import nodesets
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _lattice_coords(L, h=1.0):
+    j, i = np.meshgrid(np.arange(L), np.arange(L), indexing="ij")
+    return np.stack([i.ravel() * h, j.ravel() * h], 0).astype(np.float64)
+
+
+def test_knn_hand_worked_ties():
+    g = json.load(open(os.path.join(GOLD, "knn_tie_5x5.json")))
+    coords = _lattice_coords(g["lattice"])
+    got = ost.knn_bruteforce(coords, [g["center"]], g["n"])[0]
+    assert got.tolist() == g["expected"]
+    got_kd = ost.knn_kdtree(coords, [g["center"]], g["n"])[0]
+    assert got_kd.tolist() == g["expected"]
+
+
+def test_knn_kdtree_equals_bruteforce():
+    ns = nodesets.square_wall_band(n=24)
+    rng = np.random.default_rng(5)
+    centers = rng.choice(ns.N, 200, replace=False)
+    for n in (12, 30):
+        a = ost.knn_bruteforce(ns.coords, centers, n)
+        b = ost.knn_kdtree(ns.coords, centers, n)
+        assert np.array_equal(a, b)
+        assert np.all(a[:, 0] == centers)
+
+
+def test_knn_3d_kdtree_equals_bruteforce():
+    rng = np.random.default_rng(6)
+    # a lattice plus jittered points: many exact ties
+    g = np.stack(np.meshgrid(*[np.arange(6)] * 3, indexing="ij"), 0).reshape(3, -1) / 5.0
+    coords = np.concatenate([g, rng.uniform(0, 1, (3, 100))], 1)
+    centers = np.arange(0, coords.shape[1], 3)
+    for n in (20, 40):
+        assert np.array_equal(ost.knn_bruteforce(coords, centers, n), ost.knn_kdtree(coords, centers, n))
+
+
+def test_knn_is_sorted_by_distance_then_id():
+    ns = nodesets.square_wall_band(n=16)
+    idx = ost.knn_bruteforce(ns.coords, np.arange(ns.N), 12)
+    for c, row in enumerate(idx):
+        d2 = ost.sq_dist(ns.coords, c, row)
+        key = list(zip(d2.tolist(), row.tolist()))
+        assert key == sorted(key)
+        # nothing outside the stencil is strictly closer than its last member
+        all_d2 = ost.sq_dist(ns.coords, c)
+        outside = np.setdiff1d(np.arange(ns.N), row)
+        assert np.all((all_d2[outside] > d2[-1]) | ((all_d2[outside] == d2[-1]) & (outside > row[-1])))
+
+
+def test_mon_stencil_order_and_demotion():
+    ns = nodesets.square_wall_band(n=40)
+    mon_nodes, mon_idx, demoted = ost.mon_stencils(ns.coords, ns.is_regular, ns.is_boundary, ns.h)
+    h = ns.h
+    off = ns.coords[:, mon_idx] - ns.coords[:, mon_idx[:, :1]]
+    expect = np.array([[0, -h, h, 0, 0], [0, 0, 0, -h, h]])
+    assert np.allclose(off, expect[:, None, :], atol=1e-12)
+    # the 0.1-wide wall band removes lattice nodes, so the outermost regular ring is demoted
+    assert len(demoted) > 0
+    assert len(mon_nodes) + len(demoted) == int(ns.is_regular.sum())
+    for c in demoted:
+        q = np.rint(ns.coords[:, c] / h).astype(int)
+        assert np.any(q == 4) or np.any(q == 36)
+
+
+def test_paper_regular_dvd_node_count():
+    """Table 1: N = 64 005 on the regular discretisation, a 253^2 lattice
+    without its corners; the generator's lattice rule reproduces it."""
+    g = json.load(open(os.path.join(GOLD, "paper_values.json")))["dvd_regular_N"]
+    n = g["lattice_points_per_axis"] - 1
+    ns = nodesets.square_wall_band(n=n, wall_band=0.0)
+    assert ns.N == g["value"]
+    assert ns.n_scattered == int(ns.is_boundary.sum())
