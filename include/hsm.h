@@ -1,0 +1,214 @@
+/*
+ * hsm.h -- C ABI of libhsm, the GB300 (sm_103a) implementation of the hybrid
+ * scattered-regular meshless operators of Jancic, Rot and Kosec,
+ * "Spatially-varying meshless approximation method for enhanced computational
+ * efficiency" (arXiv:2303.01760).
+ *
+ * The library takes a node set with a regular/scattered flag per node
+ * (Section 2: regular nodes fill the domain, scattered nodes fill the layers
+ * near irregular boundaries), builds one stencil per node, computes the
+ * weights of Eq. 1 for the operators d/dx, d/dy, d/dz and the Laplacian --
+ * monomial-only (MON) weights on regular nodes, PHS r^3 + monomials (RBF-FD)
+ * on scattered nodes -- applies them to fields, and runs the explicit
+ * Boussinesq natural-convection step of Section 3 on top of them.
+ *
+ * Conventions for every entry point:
+ *   - Pointers marked "device" are CUDA device (or managed) memory owned by the
+ *     caller; the library never frees them.  Objects returned through handles
+ *     (hsm_plan, hsm_stepper, hsm_mlp) own their internal device memory and
+ *     release it in the matching *_destroy call.
+ *   - Coordinates and fields are structure-of-arrays: coords[k * n_nodes + i]
+ *     is coordinate k of node i.  Operator outputs are [n_ops][n_nodes] with the
+ *     operators in bit order of hsm_op (DX, DY, DZ, LAP).
+ *   - All device work is enqueued on the stream given at creation and is
+ *     asynchronous unless the comment says the call synchronises.
+ *   - Errors: the return value is an hsm_status; no exception crosses the ABI.
+ *     Argument errors are detected before any work is enqueued.  A CUDA error
+ *     is reported as HSM_ECUDA and its text is kept for hsm_last_error.
+ *   - Handles are not thread safe: use one handle per host thread.
+ */
+#ifndef HSM_H
+#define HSM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HSM_OK = 0,
+  HSM_EINVAL = 1,     /* invalid argument (null pointer, size, flag)            */
+  HSM_ENOMEM = 2,     /* device allocation failed                               */
+  HSM_ECUDA = 3,      /* a CUDA call failed; see hsm_last_error                 */
+  HSM_ESINGULAR = 4,  /* at least one node has no valid weights                 */
+  HSM_ENOTCONV = 5,   /* an iterative solve did not reach its tolerance         */
+  HSM_ETIMEOUT = 6,   /* a bounded device wait gave up                          */
+  HSM_EBOUNDS = 7,    /* a stencil index or size lies outside its range         */
+  HSM_ESTATE = 8      /* call out of order (e.g. weights before stencils)       */
+} hsm_status;
+
+/* Operators of Eq. 1 (bit flags; several may be or-ed into an op mask). */
+typedef enum { HSM_DX = 1, HSM_DY = 2, HSM_DZ = 4, HSM_LAP = 8 } hsm_op;
+
+/* How the weights of scattered (RBF-FD) nodes are obtained. */
+typedef enum {
+  HSM_PREC_FP64 = 0,         /* direct solve in FP64                               */
+  HSM_PREC_FP32_REFINE = 1,  /* FP32 LU with FP64-residual iterative refinement    */
+  HSM_PREC_LEARNED = 2       /* MLP prediction + exact FP64 consistency projection,
+                                direct FP64 solve as fallback (needs hsm_mlp_attach) */
+} hsm_prec;
+
+/* Storage type of an input field. */
+typedef enum { HSM_F32 = 0, HSM_F64 = 1 } hsm_dtype;
+
+/* Per-node status codes written by hsm_plan_compute_weights. */
+enum {
+  HSM_NODE_OK = 0,
+  HSM_NODE_DEMOTED = 1,      /* regular-flagged node that had to use RBF-FD        */
+  HSM_NODE_REFINE_FP64 = 2,  /* FP32 refinement did not converge; FP64 solve used  */
+  HSM_NODE_LEARNED_SOLVE = 3,/* learned weights rejected; FP64 solve used          */
+  HSM_NODE_SINGULAR = 255    /* no valid weights                                    */
+};
+
+typedef struct hsm_plan_s* hsm_plan;
+typedef struct hsm_stepper_s* hsm_stepper;
+typedef struct hsm_mlp_s* hsm_mlp;
+
+/* ------------------------------------------------------------------------ */
+/* Status                                                                    */
+/* ------------------------------------------------------------------------ */
+
+/* Static text for a status code (never NULL). */
+const char* hsm_status_string(hsm_status s);
+
+/* Copies the text of the last error seen by this plan (or by the library when
+ * plan is NULL) into buf (always NUL-terminated when len > 0).               */
+hsm_status hsm_last_error(hsm_plan plan, char* buf, size_t len);
+
+/* ------------------------------------------------------------------------ */
+/* Plan: node set -> stencils -> weights (Section 2, Eq. 1)                  */
+/* ------------------------------------------------------------------------ */
+
+/* Creates a plan for a node set (Section 2: nodes x_i, a regular/scattered
+ * flag per node, stencil size n, augmentation order m).
+ *   dim         2 or 3
+ *   n_nodes     N >= 1 (and < 2^31)
+ *   coords      device f64 [dim][N]; must stay valid while the plan is used
+ *   is_regular  device u8 [N]; 1 = regular lattice node (MON candidate)
+ *   is_boundary device u8 [N] or NULL; 1 = boundary node (always RBF-FD, and
+ *               its stencil is itself plus its n-1 nearest interior nodes)
+ *   h_regular   spacing of the regular lattice; lattice points are integer
+ *               multiples of h_regular along every axis
+ *   aug_m       monomial augmentation degree m of the RBF-FD basis, 1..6
+ *   stencil_n   RBF-FD stencil size; 0 selects n = 2 * C(m+d, m) (Section 1);
+ *               otherwise C(m+d, m) < stencil_n <= 128
+ *   op_mask     operators to compute weights for (or of hsm_op; DZ needs dim 3)
+ *   cuda_stream cudaStream_t the plan enqueues on (NULL = legacy default)
+ * Allocates nothing on the device until hsm_plan_build_stencils.            */
+hsm_status hsm_plan_create(hsm_plan* out, int dim, int64_t n_nodes, const double* coords,
+                           const uint8_t* is_regular, const uint8_t* is_boundary,
+                           double h_regular, int aug_m, int stencil_n, unsigned op_mask,
+                           void* cuda_stream);
+
+/* Builds every stencil (Section 2, "a set of n neighbouring nodes"):
+ *   MON nodes: {c, c-e1, c+e1, c-e2, c+e2[, c-e3, c+e3]} through the lattice;
+ *   RBF-FD nodes: the n nodes of smallest (squared distance, node id), the
+ *   squared distance summed in coordinate order in FP64 without fused
+ *   multiply-add.  A regular-flagged node that is a boundary node, is not on
+ *   the lattice, or misses a lattice neighbour is demoted to RBF-FD.
+ * Synchronises the plan's stream (the group sizes are read back).           */
+hsm_status hsm_plan_build_stencils(hsm_plan plan);
+
+/* Computes the weights of all nodes for the plan's operators (Eq. 1):
+ * MON weights solve P^T w = L p over {1, x_k, x_k^2}; RBF-FD weights solve the
+ * augmented system [A P; P^T 0][w; lambda] = [L phi; L p] with phi = r^3
+ * (Section 2.1, Section 4), by the method selected with prec.
+ *   node_status  device u8 [N] or NULL; receives one HSM_NODE_* per node
+ * Returns HSM_ESINGULAR when some node has no valid weights (its weights are
+ * then zero).  Synchronises the plan's stream (the failure count is read).  */
+hsm_status hsm_plan_compute_weights(hsm_plan plan, hsm_prec prec, uint8_t* node_status);
+
+/* Sizes after hsm_plan_build_stencils (host outputs; any may be NULL).
+ *   nnz_per_op   number of stencil entries of one operator over all nodes
+ *   n_mon        nodes using MON weights
+ *   n_demoted    regular-flagged nodes demoted to RBF-FD
+ *   n_fallback   nodes whose requested method fell back to the FP64 solve in
+ *                the last hsm_plan_compute_weights                          */
+hsm_status hsm_plan_query(hsm_plan plan, int64_t* nnz_per_op, int64_t* n_mon, int64_t* n_demoted,
+                          int64_t* n_fallback);
+
+/* Exports one operator (a single hsm_op bit present in the plan's op mask) as
+ * CSR into caller-allocated device arrays: row_ptr int64 [N+1], col int32
+ * [nnz], val f64 [nnz] (sizes from hsm_plan_query).  Column order within a row
+ * is the stencil order (centre first).                                      */
+hsm_status hsm_plan_export_csr(hsm_plan plan, unsigned op, int64_t* row_ptr, int32_t* col,
+                               double* val);
+
+/* Applies the operators of op_mask (a subset of the plan's) to one field,
+ * Eq. 1: out[o][c] = sum_i w_o[c][i] u[idx[c][i]], accumulated in FP64.
+ *   in_dtype  HSM_F64: u is f64 [N] and the FP64 weights are used;
+ *             HSM_F32: u is f32 [N] and FP32 copies of the weights are used
+ *   u         device [N]
+ *   out       device f64 [popcount(op_mask)][N]                             */
+hsm_status hsm_apply(hsm_plan plan, unsigned op_mask, hsm_dtype in_dtype, const void* u,
+                     double* out);
+
+/* Times the kernel variants of this plan (stencil-apply thread layouts and
+ * weight-solve lane counts) on its own data and keeps the fastest per group.
+ * cache_path: NULL = no cache; otherwise a text file read before and updated
+ * after tuning, keyed by device name and problem shape.  Synchronises.      */
+hsm_status hsm_plan_autotune(hsm_plan plan, const char* cache_path);
+
+/* Releases the plan and all memory it owns.  NULL is allowed.               */
+hsm_status hsm_plan_destroy(hsm_plan plan);
+
+/* ------------------------------------------------------------------------ */
+/* Explicit Boussinesq stepper (Section 3, Eqs. 2-4)                         */
+/* ------------------------------------------------------------------------ */
+
+/* Boundary kind per node for hsm_phys.bc. */
+enum { HSM_BC_INTERIOR = 0, HSM_BC_T_DIRICHLET = 1, HSM_BC_T_NEUMANN = 2 };
+
+typedef struct {
+  double Ra;             /* Rayleigh number                                        */
+  double Pr;             /* Prandtl number                                         */
+  double dt;             /* time step; Section 3 uses dt = 0.1 h^2 / 2             */
+  double T_ref;          /* reference temperature of the buoyancy term             */
+  const uint8_t* bc;     /* device u8 [N]: HSM_BC_*; every non-interior node is a
+                            no-slip wall with a zero normal pressure derivative    */
+  const double* T_bc;    /* device f64 [N]: Dirichlet temperature (read where bc=1) */
+  const double* normals; /* device f64 [dim][N]: outward unit normals (bc != 0)    */
+  double krylov_tol;     /* relative residual of the pressure solve (e.g. 1e-12)   */
+  int krylov_max_it;     /* iteration cap of the pressure solve (e.g. 2000)        */
+} hsm_phys;
+
+/* Creates a stepper on a plan whose weights exist and whose op mask holds
+ * every first derivative and the Laplacian.  Copies *phys (the device arrays
+ * it points to must stay valid).  Builds the pressure operator (Laplacian rows
+ * inside, normal-derivative rows on the boundary).                          */
+hsm_status hsm_stepper_create(hsm_stepper* out, hsm_plan plan, const hsm_phys* phys);
+
+/* Advances n_steps explicit steps in place (Section 3; Chorin projection):
+ *   1. v* = v + dt[-(v.grad)v + Pr lap v + Ra Pr (T - T_ref) e_up], v* = 0 on
+ *      walls (e_up = last axis);
+ *   2. solve [Lp 1; 1^T 0][p; c] = [div(v*) / dt (0 on walls); 0] by BiCGSTAB,
+ *      warm-started from the incoming p;
+ *   3. v = v* - dt grad p inside, 0 on walls;
+ *   4. T = T + dt[-v.grad T + lap T] inside (new v advects T);
+ *   5. Dirichlet T = T_bc; insulated nodes T_b = -sum_{i!=b} wn_i T_i / wn_b.
+ *   v  device f64 [dim][N], T device f64 [N], p device f64 [N]
+ *   krylov_iters  host int [n_steps] or NULL: pressure iterations per step
+ * Synchronises once at the end to read the solver status.  Returns
+ * HSM_ENOTCONV if a pressure solve hit krylov_max_it (the step still ran).  */
+hsm_status hsm_step(hsm_stepper st, int n_steps, double* v, double* T, double* p,
+                    int* krylov_iters);
+
+hsm_status hsm_stepper_destroy(hsm_stepper st);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HSM_H */

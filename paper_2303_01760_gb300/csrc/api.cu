@@ -1,0 +1,422 @@
+// C ABI entry points of libhsm: plan life cycle, stencils, weights, export,
+// operator application and the autotuner.  Argument checks happen here,
+// before anything is enqueued.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <fstream>
+#include <functional>
+#include <map>
+#include <mutex>
+#include <sstream>
+
+#include "common.cuh"
+
+namespace hsm {
+
+static std::mutex g_err_mu;
+static std::string g_last_error;
+
+void set_global_error(const std::string& msg) {
+  std::lock_guard<std::mutex> g(g_err_mu);
+  g_last_error = msg;
+}
+
+hsm_status set_error(hsm_plan p, hsm_status s, const std::string& msg) {
+  if (p) p->last_error = msg;
+  set_global_error(msg);
+  return s;
+}
+
+hsm_status cuda_fail(hsm_plan p, cudaError_t e, const char* what) {
+  std::string msg = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  if (e == cudaErrorMemoryAllocation) return set_error(p, HSM_ENOMEM, msg);
+  return set_error(p, HSM_ECUDA, msg);
+}
+
+static int64_t binom(int a, int b) {
+  int64_t r = 1;
+  for (int i = 1; i <= b; ++i) r = r * (a - b + i) / i;
+  return r;
+}
+
+// Graded lexicographic exponents of all monomials of total degree <= m.
+static std::vector<int8_t> monomial_exponents(int dim, int m) {
+  std::vector<int8_t> out;
+  for (int q = 0; q <= m; ++q) {
+    if (dim == 2) {
+      for (int a = q; a >= 0; --a) {
+        out.push_back((int8_t)a);
+        out.push_back((int8_t)(q - a));
+      }
+    } else {
+      for (int a = q; a >= 0; --a)
+        for (int b = q - a; b >= 0; --b) {
+          out.push_back((int8_t)a);
+          out.push_back((int8_t)b);
+          out.push_back((int8_t)(q - a - b));
+        }
+    }
+  }
+  return out;
+}
+
+}  // namespace hsm
+
+using namespace hsm;
+
+extern "C" {
+
+const char* hsm_status_string(hsm_status s) {
+  switch (s) {
+    case HSM_OK: return "ok";
+    case HSM_EINVAL: return "invalid argument";
+    case HSM_ENOMEM: return "device out of memory";
+    case HSM_ECUDA: return "CUDA error";
+    case HSM_ESINGULAR: return "singular weight system";
+    case HSM_ENOTCONV: return "iterative solve did not converge";
+    case HSM_ETIMEOUT: return "bounded device wait timed out";
+    case HSM_EBOUNDS: return "index out of bounds";
+    case HSM_ESTATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+hsm_status hsm_last_error(hsm_plan plan, char* buf, size_t len) {
+  if (!buf || len == 0) return HSM_EINVAL;
+  std::string msg;
+  if (plan) msg = plan->last_error;
+  else {
+    std::lock_guard<std::mutex> g(g_err_mu);
+    msg = g_last_error;
+  }
+  size_t n = std::min(len - 1, msg.size());
+  memcpy(buf, msg.data(), n);
+  buf[n] = 0;
+  return HSM_OK;
+}
+
+hsm_status hsm_plan_create(hsm_plan* out, int dim, int64_t n_nodes, const double* coords, const uint8_t* is_regular,
+                           const uint8_t* is_boundary, double h_regular, int aug_m, int stencil_n, unsigned op_mask,
+                           void* cuda_stream) {
+  if (!out) return set_error(nullptr, HSM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (dim != 2 && dim != 3) return set_error(nullptr, HSM_EINVAL, "dim must be 2 or 3");
+  if (n_nodes < 1 || n_nodes >= ((int64_t)1 << 31)) return set_error(nullptr, HSM_EINVAL, "n_nodes out of range");
+  if (!coords || !is_regular) return set_error(nullptr, HSM_EINVAL, "coords and is_regular are required");
+  if (!(h_regular > 0.0) || !std::isfinite(h_regular)) return set_error(nullptr, HSM_EINVAL, "h_regular must be > 0");
+  if (aug_m < 1 || aug_m > 6) return set_error(nullptr, HSM_EINVAL, "aug_m must be in 1..6");
+  if (op_mask == 0 || (op_mask & ~15u)) return set_error(nullptr, HSM_EINVAL, "op_mask must be a non-empty set of hsm_op");
+  if (dim == 2 && (op_mask & HSM_DZ)) return set_error(nullptr, HSM_EINVAL, "HSM_DZ needs dim 3");
+  const int n_mono = (int)binom(aug_m + dim, aug_m);
+  int n = stencil_n == 0 ? 2 * n_mono : stencil_n;
+  if (n <= n_mono || n > kMaxStencil)
+    return set_error(nullptr, HSM_EINVAL, "stencil_n must satisfy C(m+d,m) < n <= 128");
+  hsm_plan p = new (std::nothrow) hsm_plan_s();
+  if (!p) return set_error(nullptr, HSM_ENOMEM, "host allocation failed");
+  p->dim = dim;
+  p->N = n_nodes;
+  p->coords = coords;
+  p->is_regular = is_regular;
+  p->is_boundary = is_boundary;
+  p->h = h_regular;
+  p->m = aug_m;
+  p->n = n;
+  p->n_mono = n_mono;
+  p->op_mask = op_mask;
+  p->stream = (cudaStream_t)cuda_stream;
+  for (int b = 0; b < 4; ++b)
+    if (op_mask & (1u << b)) p->ops[p->nops++] = 1 << b;
+  *out = p;
+  return HSM_OK;
+}
+
+static void free_group(Group& g, cudaStream_t s) {
+  dev_free(&g.nodes, s);
+  dev_free(&g.idx, s);
+  dev_free(&g.w64, s);
+  dev_free(&g.w32, s);
+  g.count = 0;
+}
+
+static void free_plan_device(hsm_plan p) {
+  cudaStream_t s = p->stream;
+  free_group(p->mon, s);
+  free_group(p->rbf, s);
+  dev_free(&p->kind, s);
+  dev_free(&p->pos, s);
+  dev_free(&p->dev_flags, s);
+  dev_free(&p->dev_count, s);
+  dev_free(&p->pairs, s);
+  dev_free(&p->mono_exp, s);
+}
+
+hsm_status hsm_plan_destroy(hsm_plan p) {
+  if (!p) return HSM_OK;
+  free_plan_device(p);
+  cudaStreamSynchronize(p->stream);
+  delete p;
+  return HSM_OK;
+}
+
+hsm_status hsm_plan_build_stencils(hsm_plan p) {
+  if (!p) return set_error(nullptr, HSM_EINVAL, "plan is NULL");
+  cudaStream_t s = p->stream;
+  free_plan_device(p);
+  p->stencils_built = p->weights_built = false;
+  HSM_CUDA(p, dev_alloc(&p->kind, p->N, s));
+  HSM_CUDA(p, dev_alloc(&p->pos, p->N, s));
+  HSM_CUDA(p, dev_alloc(&p->dev_flags, 4, s));
+  HSM_CUDA(p, dev_alloc(&p->dev_count, 4, s));
+  HSM_CUDA(p, cudaMemsetAsync(p->dev_flags, 0, 4 * sizeof(unsigned), s));
+  // upper-triangle pair table and monomial exponents for the RBF-FD kernels
+  std::vector<uint16_t> pairs;
+  for (int i = 0; i < p->n; ++i)
+    for (int j = i + 1; j < p->n; ++j) pairs.push_back((uint16_t)((i << 8) | j));
+  std::vector<int8_t> ex = monomial_exponents(p->dim, p->m);
+  HSM_CUDA(p, dev_alloc(&p->pairs, pairs.size(), s));
+  HSM_CUDA(p, dev_alloc(&p->mono_exp, ex.size(), s));
+  if (!pairs.empty())
+    HSM_CUDA(p, cudaMemcpyAsync(p->pairs, pairs.data(), pairs.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, s));
+  HSM_CUDA(p, cudaMemcpyAsync(p->mono_exp, ex.data(), ex.size(), cudaMemcpyHostToDevice, s));
+  // host vectors must outlive the async copies
+  HSM_CUDA(p, cudaStreamSynchronize(s));
+  return build_stencils(p);
+}
+
+hsm_status hsm_plan_compute_weights(hsm_plan p, hsm_prec prec, uint8_t* node_status) {
+  if (!p) return set_error(nullptr, HSM_EINVAL, "plan is NULL");
+  if (!p->stencils_built) return set_error(p, HSM_ESTATE, "hsm_plan_build_stencils must come first");
+  if (prec != HSM_PREC_FP64 && prec != HSM_PREC_FP32_REFINE && prec != HSM_PREC_LEARNED)
+    return set_error(p, HSM_EINVAL, "unknown precision mode");
+  if (prec == HSM_PREC_LEARNED && !p->mlp)
+    return set_error(p, HSM_ESTATE, "HSM_PREC_LEARNED needs a predictor attached with hsm_mlp_attach");
+  cudaStream_t s = p->stream;
+  if (!p->mon.w64) HSM_CUDA(p, dev_alloc(&p->mon.w64, (size_t)p->nops * p->mon.width * p->mon.count, s));
+  if (!p->rbf.w64) HSM_CUDA(p, dev_alloc(&p->rbf.w64, (size_t)p->nops * p->rbf.width * p->rbf.count, s));
+  dev_free(&p->mon.w32, s);
+  dev_free(&p->rbf.w32, s);
+  HSM_CUDA(p, cudaMemsetAsync(p->dev_flags, 0, sizeof(unsigned), s));
+  hsm_status st = compute_mon_weights(p, node_status);
+  if (st != HSM_OK) return st;
+  p->n_fallback = 0;
+  if (prec == HSM_PREC_FP64) {
+    st = compute_rbf_weights_fp64(p, nullptr, p->rbf.count, node_status);
+    if (st != HSM_OK) return st;
+  } else {
+    int32_t* fail_list = nullptr;
+    HSM_CUDA(p, dev_alloc(&fail_list, p->rbf.count, s));
+    HSM_CUDA(p, cudaMemsetAsync(p->dev_count, 0, sizeof(int), s));
+    if (prec == HSM_PREC_FP32_REFINE)
+      st = compute_rbf_weights_fp32r(p, nullptr, p->rbf.count, node_status, fail_list, p->dev_count);
+    else
+      st = compute_rbf_weights_learned(p, node_status, fail_list, p->dev_count);
+    if (st != HSM_OK) {
+      dev_free(&fail_list, s);
+      return st;
+    }
+    int fc = 0;
+    HSM_CUDA(p, cudaMemcpyAsync(&fc, p->dev_count, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HSM_CUDA(p, cudaStreamSynchronize(s));
+    p->n_fallback = fc;
+    if (fc > 0) {
+      st = compute_rbf_weights_fp64_marked(p, fail_list, fc, node_status,
+                                           prec == HSM_PREC_FP32_REFINE ? HSM_NODE_REFINE_FP64 : HSM_NODE_LEARNED_SOLVE);
+      if (st != HSM_OK) {
+        dev_free(&fail_list, s);
+        return st;
+      }
+    }
+    dev_free(&fail_list, s);
+  }
+  unsigned flags = 0;
+  HSM_CUDA(p, cudaMemcpyAsync(&flags, p->dev_flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  HSM_CUDA(p, cudaStreamSynchronize(s));
+  p->weights_built = true;
+  if (flags & kDevSingular) return set_error(p, HSM_ESINGULAR, "some nodes have singular weight systems");
+  return HSM_OK;
+}
+
+hsm_status hsm_plan_query(hsm_plan p, int64_t* nnz_per_op, int64_t* n_mon, int64_t* n_demoted, int64_t* n_fallback) {
+  if (!p) return set_error(nullptr, HSM_EINVAL, "plan is NULL");
+  if (!p->stencils_built) return set_error(p, HSM_ESTATE, "hsm_plan_build_stencils must come first");
+  if (nnz_per_op) *nnz_per_op = p->mon.count * p->mon.width + p->rbf.count * p->rbf.width;
+  if (n_mon) *n_mon = p->mon.count;
+  if (n_demoted) *n_demoted = p->n_demoted;
+  if (n_fallback) *n_fallback = p->n_fallback;
+  return HSM_OK;
+}
+
+namespace {
+__global__ void k_row_width(const uint8_t* __restrict__ kind, int64_t N, int wm, int wr, int32_t* width) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    width[i] = kind[i] == 0 ? wm : wr;
+}
+__global__ void k_fill_csr(const uint8_t* __restrict__ kind, const int32_t* __restrict__ pos,
+                           const int32_t* __restrict__ rp32, int64_t N, Group gm, Group gr, int slot, int64_t* row_ptr,
+                           int32_t* col, double* val) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= N; i += (int64_t)gridDim.x * blockDim.x) {
+    row_ptr[i] = rp32[i];
+    if (i == N) continue;
+    const Group& g = kind[i] == 0 ? gm : gr;
+    const int64_t p = pos[i];
+    const int64_t r0 = rp32[i];
+    for (int j = 0; j < g.width; ++j) {
+      col[r0 + j] = g.idx[(int64_t)j * g.count + p];
+      val[r0 + j] = g.w64 ? g.w64[((int64_t)slot * g.width + j) * g.count + p] : 0.0;
+    }
+  }
+}
+}  // namespace
+
+hsm_status hsm_plan_export_csr(hsm_plan p, unsigned op, int64_t* row_ptr, int32_t* col, double* val) {
+  if (!p) return set_error(nullptr, HSM_EINVAL, "plan is NULL");
+  if (!p->weights_built) return set_error(p, HSM_ESTATE, "weights are not computed");
+  if (!row_ptr || !col || !val) return set_error(p, HSM_EINVAL, "output arrays are required");
+  if (__builtin_popcount(op) != 1 || !(p->op_mask & op)) return set_error(p, HSM_EINVAL, "op must be one operator of the plan");
+  int slot = 0;
+  for (int b = 0; b < 4; ++b) {
+    if ((1u << b) == op) break;
+    if (p->op_mask & (1u << b)) ++slot;
+  }
+  cudaStream_t s = p->stream;
+  int32_t *width = nullptr, *rp = nullptr;
+  HSM_CUDA(p, dev_alloc(&width, p->N, s));
+  HSM_CUDA(p, dev_alloc(&rp, p->N + 1, s));
+  const int T = 256;
+  int grid = (int)std::min<int64_t>(ceil_div(p->N + 1, T), (int64_t)num_sms() * 8);
+  k_row_width<<<grid, T, 0, s>>>(p->kind, p->N, p->mon.width, p->rbf.width, width);
+  HSM_CUDA(p, exclusive_scan_i32(width, rp, p->N, s));
+  k_fill_csr<<<grid, T, 0, s>>>(p->kind, p->pos, rp, p->N, p->mon, p->rbf, slot, row_ptr, col, val);
+  HSM_CUDA(p, cudaGetLastError());
+  dev_free(&width, s);
+  dev_free(&rp, s);
+  return HSM_OK;
+}
+
+hsm_status hsm_apply(hsm_plan p, unsigned op_mask, hsm_dtype in_dtype, const void* u, double* out) {
+  if (!p) return set_error(nullptr, HSM_EINVAL, "plan is NULL");
+  if (!p->weights_built) return set_error(p, HSM_ESTATE, "weights are not computed");
+  if (!u || !out) return set_error(p, HSM_EINVAL, "u and out are required");
+  if (op_mask == 0 || (op_mask & ~p->op_mask)) return set_error(p, HSM_EINVAL, "op_mask must be a subset of the plan's");
+  if (in_dtype != HSM_F32 && in_dtype != HSM_F64) return set_error(p, HSM_EINVAL, "unknown dtype");
+  if (in_dtype == HSM_F32 && (!p->mon.w32 || !p->rbf.w32)) {
+    HSM_CUDA(p, dev_alloc(&p->mon.w32, (size_t)p->nops * p->mon.width * p->mon.count, p->stream));
+    HSM_CUDA(p, dev_alloc(&p->rbf.w32, (size_t)p->nops * p->rbf.width * p->rbf.count, p->stream));
+    hsm_status st = weights_to_f32(p);
+    if (st != HSM_OK) return st;
+  }
+  return launch_apply(p, op_mask, in_dtype, u, out, p->stream);
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: times the apply block size and the lanes per weight system on
+// this plan's own data and keeps the fastest.  Results may be cached in a
+// text file keyed by device name and problem shape.
+// ---------------------------------------------------------------------------
+static std::string tune_key(hsm_plan p) {
+  cudaDeviceProp prop;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaGetDeviceProperties(&prop, dev);
+  std::ostringstream k;
+  k << prop.name << "|d" << p->dim << "|m" << p->m << "|n" << p->n << "|ops" << p->op_mask << "|Nm"
+    << (p->mon.count >> 12) << "|Nr" << (p->rbf.count >> 12);
+  std::string s = k.str();
+  for (auto& c : s)
+    if (c == ' ') c = '_';
+  return s;
+}
+
+static float time_ms(cudaStream_t s, const std::function<hsm_status()>& f, int reps, hsm_status* st) {
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  *st = f();  // warm-up
+  cudaEventRecord(a, s);
+  for (int i = 0; i < reps && *st == HSM_OK; ++i) *st = f();
+  cudaEventRecord(b, s);
+  cudaEventSynchronize(b);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return ms / reps;
+}
+
+hsm_status hsm_plan_autotune(hsm_plan p, const char* cache_path) {
+  if (!p) return set_error(nullptr, HSM_EINVAL, "plan is NULL");
+  if (!p->stencils_built) return set_error(p, HSM_ESTATE, "hsm_plan_build_stencils must come first");
+  const std::string key = tune_key(p);
+  std::map<std::string, std::string> cache;
+  if (cache_path) {
+    std::ifstream in(cache_path);
+    std::string k, v;
+    while (in >> k >> v) cache[k] = v;
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      int t = 0, l = 0;
+      if (sscanf(it->second.c_str(), "%d,%d", &t, &l) == 2 && t > 0 && l > 0) {
+        p->tune.apply_threads = t;
+        p->tune.rbf_lanes = l;
+        p->tune.tuned = true;
+        return HSM_OK;
+      }
+    }
+  }
+  cudaStream_t s = p->stream;
+  hsm_status st = HSM_OK;
+  // weight-solve lanes (weights must exist afterwards; the last run leaves them)
+  float best = 1e30f;
+  int best_l = p->tune.rbf_lanes;
+  if (p->rbf.count) {
+    if (!p->rbf.w64) HSM_CUDA(p, dev_alloc(&p->rbf.w64, (size_t)p->nops * p->rbf.width * p->rbf.count, s));
+    for (int l : {8, 16, 32}) {
+      p->tune.rbf_lanes = l;
+      float ms = time_ms(s, [&]() { return compute_rbf_weights_fp64(p, nullptr, p->rbf.count, nullptr); }, 2, &st);
+      if (st != HSM_OK) return st;
+      if (ms < best) {
+        best = ms;
+        best_l = l;
+      }
+    }
+  }
+  p->tune.rbf_lanes = best_l;
+  if (!p->weights_built) {
+    st = hsm_plan_compute_weights(p, HSM_PREC_FP64, nullptr);
+    if (st != HSM_OK && st != HSM_ESINGULAR) return st;
+  }
+  // apply block size
+  double* u = nullptr;
+  double* out = nullptr;
+  HSM_CUDA(p, dev_alloc(&u, p->N, s));
+  HSM_CUDA(p, dev_alloc(&out, (size_t)p->nops * p->N, s));
+  HSM_CUDA(p, cudaMemsetAsync(u, 0, p->N * sizeof(double), s));
+  best = 1e30f;
+  int best_t = p->tune.apply_threads;
+  for (int t : {128, 256, 512}) {
+    p->tune.apply_threads = t;
+    float ms = time_ms(s, [&]() { return launch_apply(p, p->op_mask, HSM_F64, u, out, s); }, 10, &st);
+    if (st != HSM_OK) break;
+    if (ms < best) {
+      best = ms;
+      best_t = t;
+    }
+  }
+  dev_free(&u, s);
+  dev_free(&out, s);
+  if (st != HSM_OK) return st;
+  p->tune.apply_threads = best_t;
+  p->tune.tuned = true;
+  if (cache_path) {
+    std::ostringstream v;
+    v << best_t << "," << best_l;
+    cache[key] = v.str();
+    std::ofstream o(cache_path, std::ios::trunc);
+    for (auto& kv : cache) o << kv.first << " " << kv.second << "\n";
+  }
+  HSM_CUDA(p, cudaStreamSynchronize(s));
+  return HSM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,145 @@
+// Internal declarations shared by the translation units of libhsm.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "hsm.h"
+
+namespace hsm {
+
+constexpr int kMaxDim = 3;
+constexpr int kMaxOps = 4;
+constexpr int kMaxStencil = 128;
+constexpr int kMaxMonomials = 84;           // C(6+3, 3): m <= 6 in 3D
+constexpr int kMaxK = kMaxStencil + kMaxMonomials;
+constexpr int32_t kEmpty = 0x7f7f7f7f;      // empty lattice-map slot (memset 0x7f)
+
+// Status bits accumulated on the device while building a plan.
+enum : unsigned {
+  kDevSingular = 1u,   // a weight system had a zero or non-finite pivot
+  kDevBounds = 2u,     // a stencil index fell outside [0, N)
+  kDevKnnShort = 4u,   // fewer than n candidate nodes were found
+};
+
+struct Group {
+  int width = 0;          // stencil width of the group
+  int64_t count = 0;      // number of nodes in the group
+  int32_t* nodes = nullptr;  // [count] node ids, ascending
+  int32_t* idx = nullptr;    // [width][count] stencil node ids (index-major)
+  double* w64 = nullptr;     // [nops][width][count]
+  float* w32 = nullptr;      // [nops][width][count]
+};
+
+struct Tuning {
+  int apply_threads = 256;  // threads per block of the apply kernel
+  int apply_split = 1;      // lanes per RBF-FD stencil in the apply kernel (1, 2, 4)
+  int rbf_lanes = 32;       // lanes per RBF-FD weight system (8, 16, 32)
+  bool tuned = false;
+};
+
+struct Mlp;  // learned predictor (mlp.cu)
+
+}  // namespace hsm
+
+struct hsm_plan_s {
+  int dim = 2;
+  int64_t N = 0;
+  const double* coords = nullptr;
+  const uint8_t* is_regular = nullptr;
+  const uint8_t* is_boundary = nullptr;
+  double h = 0.0;
+  int m = 2;
+  int n = 12;
+  int n_mono = 6;          // C(m+d, m)
+  unsigned op_mask = 0;
+  int nops = 0;
+  int ops[hsm::kMaxOps] = {0, 0, 0, 0};  // operator bits in bit order
+  cudaStream_t stream = nullptr;
+
+  hsm::Group mon, rbf;
+  uint8_t* kind = nullptr;      // [N] 0 = MON, 1 = RBF-FD
+  int32_t* pos = nullptr;       // [N] position inside its group
+  unsigned* dev_flags = nullptr;  // device status bits
+  int* dev_count = nullptr;       // device counter scratch
+  uint16_t* pairs = nullptr;      // [n(n-1)/2] (i << 8 | j) upper-triangle pairs
+  int8_t* mono_exp = nullptr;     // [n_mono][dim] monomial exponents
+  int64_t n_demoted = 0;
+  int64_t n_fallback = 0;
+  bool stencils_built = false;
+  bool weights_built = false;
+  hsm::Tuning tune;
+  hsm::Mlp* mlp = nullptr;       // attached learned predictor (not owned)
+  std::string last_error;
+};
+
+namespace hsm {
+
+// Records a CUDA error on the plan and returns HSM_ECUDA.
+hsm_status cuda_fail(hsm_plan p, cudaError_t e, const char* what);
+hsm_status set_error(hsm_plan p, hsm_status s, const std::string& msg);
+void set_global_error(const std::string& msg);
+
+#define HSM_CUDA(plan, call)                                   \
+  do {                                                         \
+    cudaError_t e_ = (call);                                   \
+    if (e_ != cudaSuccess) return ::hsm::cuda_fail((plan), e_, #call); \
+  } while (0)
+
+template <typename T>
+cudaError_t dev_alloc(T** ptr, size_t count, cudaStream_t s) {
+  *ptr = nullptr;
+  if (count == 0) count = 1;
+  return cudaMallocAsync(reinterpret_cast<void**>(ptr), count * sizeof(T), s);
+}
+
+template <typename T>
+void dev_free(T** ptr, cudaStream_t s) {
+  if (*ptr) cudaFreeAsync(*ptr, s);
+  *ptr = nullptr;
+}
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline int num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+// ---- scan.cu -------------------------------------------------------------
+// Exclusive prefix sum of in[0..n) (int32 counts) into out[0..n], out[n] = total.
+cudaError_t exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s);
+// List of indices i (ascending) with key[i] == want; count written to *count_dev.
+cudaError_t select_indices(const uint8_t* key, uint8_t want, int64_t n, int32_t* out_list,
+                           int32_t* out_pos, int* count_dev, cudaStream_t s);
+
+// ---- stencils.cu ---------------------------------------------------------
+hsm_status build_stencils(hsm_plan p);
+
+// ---- weights.cu ----------------------------------------------------------
+hsm_status compute_mon_weights(hsm_plan p, uint8_t* status);
+hsm_status compute_rbf_weights_fp64_marked(hsm_plan p, const int32_t* list, int64_t count, uint8_t* status,
+                                           uint8_t mark);
+hsm_status compute_rbf_weights_fp64(hsm_plan p, const int32_t* list, int64_t count, uint8_t* status);
+hsm_status compute_rbf_weights_fp32r(hsm_plan p, const int32_t* list, int64_t count, uint8_t* status,
+                                     int32_t* fail_list, int* fail_count);
+hsm_status weights_to_f32(hsm_plan p);
+size_t rbf_smem_per_system(int K, int ld, bool fp32);
+
+// ---- apply.cu ------------------------------------------------------------
+hsm_status launch_apply(hsm_plan p, unsigned op_mask, hsm_dtype dt, const void* u, double* out,
+                        cudaStream_t s);
+
+// ---- mlp.cu --------------------------------------------------------------
+hsm_status compute_rbf_weights_learned(hsm_plan p, uint8_t* status, int32_t* fail_list, int* fail_count);
+
+}  // namespace hsm

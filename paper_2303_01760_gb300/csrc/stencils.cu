@@ -1,0 +1,446 @@
+// Stencil selection (Section 2: "a set of n neighbouring nodes").
+//
+// Regular nodes keep the symmetric 2d+1 lattice stencil, found through a
+// dense lattice map (integer coordinates round(x/h) -> lowest node id).
+// All other nodes take the n nodes of smallest (d2, id), where
+// d2 = ((dx*dx) + (dy*dy)) + (dz*dz) is evaluated in FP64 with explicit
+// round-to-nearest intrinsics (never contracted to FMA), so the selection is
+// bit-identical to any other evaluation of the same expression.  Boundary
+// nodes search among interior nodes only (plus themselves).  The search uses
+// a uniform cell grid (cell edge = lattice spacing), one thread per query,
+// visiting square (cube) shells of cells until no unvisited cell can hold a
+// closer node.
+#include <cfloat>
+
+#include "common.cuh"
+
+namespace hsm {
+namespace {
+
+constexpr double kLatticeTol = 1e-6;
+
+__device__ __forceinline__ unsigned long long ordered_bits(double x) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double from_ordered(unsigned long long b) {
+  b = (b & 0x8000000000000000ull) ? (b & 0x7fffffffffffffffull) : ~b;
+  return __longlong_as_double((long long)b);
+}
+__host__ __device__ inline double host_from_ordered(unsigned long long b) {
+  b = (b & 0x8000000000000000ull) ? (b & 0x7fffffffffffffffull) : ~b;
+  double d;
+  memcpy(&d, &b, sizeof(d));
+  return d;
+}
+
+// Bounding box (ordered-bit atomics) and lattice extents of the node set.
+__global__ void k_bounds(const double* __restrict__ coords, int64_t N, int dim, double inv_h,
+                         unsigned long long* bbox, int* lat_lo, int* lat_hi, int32_t* ijk,
+                         uint8_t* on_lat) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    bool on = true;
+    int q[kMaxDim];
+    for (int k = 0; k < dim; ++k) {
+      double x = coords[k * N + i];
+      unsigned long long ob = ordered_bits(x);
+      atomicMin(&bbox[2 * k], ob);
+      atomicMax(&bbox[2 * k + 1], ob);
+      double t = x * inv_h;
+      double r = rint(t);
+      if (!(fabs(t - r) <= kLatticeTol) || fabs(r) > 1.0e9) on = false;
+      q[k] = on ? (int)r : 0;
+    }
+    on_lat[i] = on ? 1 : 0;
+    for (int k = 0; k < dim; ++k) {
+      ijk[k * N + i] = q[k];
+      if (on) {
+        atomicMin(&lat_lo[k], q[k]);
+        atomicMax(&lat_hi[k], q[k]);
+      }
+    }
+  }
+}
+
+struct LatticeGeom {
+  int lo[kMaxDim];
+  int ext[kMaxDim];
+  int dim;
+  __device__ __forceinline__ int64_t lin(const int* q) const {
+    int64_t l = 0;
+    for (int k = dim - 1; k >= 0; --k) {
+      int a = q[k] - lo[k];
+      if (a < 0 || a >= ext[k]) return -1;
+      l = l * ext[k] + a;
+    }
+    return l;
+  }
+};
+
+__global__ void k_lattice_insert(const int32_t* __restrict__ ijk, const uint8_t* __restrict__ on_lat,
+                                 int64_t N, LatticeGeom g, int32_t* map) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (!on_lat[i]) continue;
+    int q[kMaxDim];
+    for (int k = 0; k < g.dim; ++k) q[k] = ijk[k * N + i];
+    int64_t l = g.lin(q);
+    if (l >= 0) atomicMin(&map[l], (int32_t)i);
+  }
+}
+
+// kind = 0 (MON) when the node is regular, interior, owns its lattice point and
+// has all 2d lattice neighbours; 1 (RBF-FD) otherwise.
+__global__ void k_classify(const int32_t* __restrict__ ijk, const uint8_t* __restrict__ on_lat,
+                           const uint8_t* __restrict__ is_regular, const uint8_t* __restrict__ is_boundary,
+                           int64_t N, LatticeGeom g, const int32_t* __restrict__ map, uint8_t* kind,
+                           int* n_demoted) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    bool reg = is_regular[i] != 0;
+    bool mon = reg && on_lat[i] && !(is_boundary && is_boundary[i]);
+    if (mon) {
+      int q[kMaxDim];
+      for (int k = 0; k < g.dim; ++k) q[k] = ijk[k * N + i];
+      int64_t l = g.lin(q);
+      mon = (l >= 0) && map[l] == (int32_t)i;
+      for (int k = 0; k < g.dim && mon; ++k) {
+        for (int s = -1; s <= 1 && mon; s += 2) {
+          q[k] += s;
+          int64_t ln = g.lin(q);
+          mon = ln >= 0 && map[ln] != kEmpty;
+          q[k] -= s;
+        }
+      }
+    }
+    kind[i] = mon ? 0 : 1;
+    if (reg && !mon) atomicAdd(n_demoted, 1);
+  }
+}
+
+__global__ void k_mon_stencil(const int32_t* __restrict__ ijk, const int32_t* __restrict__ mon_nodes,
+                              int64_t count, int64_t N, LatticeGeom g, const int32_t* __restrict__ map,
+                              int32_t* idx) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < count;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    int32_t c = mon_nodes[p];
+    int q[kMaxDim];
+    for (int k = 0; k < g.dim; ++k) q[k] = ijk[k * N + c];
+    idx[p] = c;
+    int j = 1;
+    for (int k = 0; k < g.dim; ++k) {
+      for (int s = -1; s <= 1; s += 2) {
+        q[k] += s;
+        idx[(int64_t)j * count + p] = map[g.lin(q)];
+        q[k] -= s;
+        ++j;
+      }
+    }
+  }
+}
+
+// ---- uniform cell grid ----------------------------------------------------
+struct CellGrid {
+  double lo[kMaxDim];
+  double inv_cell;
+  double cell;
+  int g[kMaxDim];
+  int dim;
+  __device__ __forceinline__ int cell_of(double x, int k) const {
+    double t = floor((x - lo[k]) * inv_cell);
+    int c = (int)fmin(fmax(t, 0.0), (double)(g[k] - 1));
+    return c;
+  }
+};
+
+__global__ void k_cell_count(const double* __restrict__ coords, int64_t N, CellGrid cg, int32_t* cell_of,
+                             int32_t* counts) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t l = 0;
+    for (int k = cg.dim - 1; k >= 0; --k) l = l * cg.g[k] + cg.cell_of(coords[k * N + i], k);
+    cell_of[i] = (int32_t)l;
+    atomicAdd(&counts[l], 1);
+  }
+}
+
+__global__ void k_cell_scatter(const double* __restrict__ coords, const uint8_t* __restrict__ is_boundary,
+                               int64_t N, int dim, const int32_t* __restrict__ cell_of,
+                               const int32_t* __restrict__ start, int32_t* cursor, int32_t* sorted_id,
+                               double* sorted_xyz, uint8_t* sorted_bnd) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int32_t l = cell_of[i];
+    int32_t s = start[l] + atomicAdd(&cursor[l], 1);
+    sorted_id[s] = (int32_t)i;
+    for (int k = 0; k < dim; ++k) sorted_xyz[(int64_t)s * kMaxDim + k] = coords[k * N + i];
+    sorted_bnd[s] = is_boundary ? is_boundary[i] : 0;
+  }
+}
+
+// (d2, id) lexicographic key comparison.
+__device__ __forceinline__ bool key_less(double d2a, int32_t ia, double d2b, int32_t ib) {
+  return d2a < d2b || (d2a == d2b && ia < ib);
+}
+
+template <int DIM>
+__device__ __forceinline__ double sq_dist(const double* a, const double* b) {
+  double d = __dsub_rn(a[0], b[0]);
+  double s = __dmul_rn(d, d);
+#pragma unroll
+  for (int k = 1; k < DIM; ++k) {
+    double e = __dsub_rn(a[k], b[k]);
+    s = __dadd_rn(s, __dmul_rn(e, e));
+  }
+  return s;
+}
+
+// One thread per query; the running top-n list lives in shared memory as
+// [n][blockDim] structure-of-arrays (bank-conflict free).
+template <int DIM>
+__global__ void k_knn(const double* __restrict__ coords, int64_t N, const uint8_t* __restrict__ is_boundary,
+                      const int32_t* __restrict__ queries, int64_t nq, int n, CellGrid cg,
+                      const int32_t* __restrict__ start, const int32_t* __restrict__ sorted_id,
+                      const double* __restrict__ sorted_xyz, const uint8_t* __restrict__ sorted_bnd,
+                      int32_t* __restrict__ out_idx, unsigned* flags) {
+  extern __shared__ unsigned char smem_raw[];
+  const int B = blockDim.x;
+  double* kd = reinterpret_cast<double*>(smem_raw);
+  int32_t* ki = reinterpret_cast<int32_t*>(kd + (size_t)n * B);
+  const int t = threadIdx.x;
+  for (int64_t qi = blockIdx.x * (int64_t)B + t; qi < nq; qi += (int64_t)gridDim.x * B) {
+    const int32_t c = queries[qi];
+    double q[DIM];
+    int cq[DIM];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      q[k] = coords[k * N + c];
+      cq[k] = cg.cell_of(q[k], k);
+    }
+    const bool bnd_center = is_boundary && is_boundary[c];
+    int cnt = 0;
+    for (int r = 0;; ++r) {
+      // visit the shell of cells at Chebyshev distance r
+      int lo[DIM], hi[DIM];
+      bool any_inside = false;
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) {
+        lo[k] = cq[k] - r;
+        hi[k] = cq[k] + r;
+        if (lo[k] >= 0 || hi[k] < cg.g[k]) any_inside = true;
+      }
+      if (r > 0 && !any_inside) break;  // the whole grid has been visited
+      int cc[DIM];
+      int zlo = DIM == 3 ? max(lo[DIM - 1], 0) : 0, zhi = DIM == 3 ? min(hi[DIM - 1], cg.g[DIM - 1] - 1) : 0;
+      for (int z = zlo; z <= zhi; ++z) {
+        if (DIM == 3) cc[2] = z;
+        const bool zedge = DIM == 3 && (z == lo[2] || z == hi[2]);
+        for (int y = max(lo[1], 0); y <= min(hi[1], cg.g[1] - 1); ++y) {
+          cc[1] = y;
+          const bool full = r == 0 || zedge || y == lo[1] || y == hi[1];
+          const int xstep = full ? 1 : (hi[0] - lo[0]);
+          for (int x = lo[0]; x <= hi[0]; x += xstep) {
+            if (x < 0 || x >= cg.g[0]) continue;
+            cc[0] = x;
+            int64_t l = 0;
+#pragma unroll
+            for (int k = DIM - 1; k >= 0; --k) l = l * cg.g[k] + cc[k];
+            const int32_t s0 = start[l], s1 = start[l + 1];
+            for (int32_t s = s0; s < s1; ++s) {
+              const int32_t id = sorted_id[s];
+              if (bnd_center && id != c && sorted_bnd[s]) continue;
+              const double d2 = sq_dist<DIM>(sorted_xyz + (int64_t)s * kMaxDim, q);
+              if (cnt == n && !key_less(d2, id, kd[(n - 1) * B + t], ki[(n - 1) * B + t])) continue;
+              int j = (cnt < n) ? cnt++ : n - 1;
+              while (j > 0 && key_less(d2, id, kd[(j - 1) * B + t], ki[(j - 1) * B + t])) {
+                kd[j * B + t] = kd[(j - 1) * B + t];
+                ki[j * B + t] = ki[(j - 1) * B + t];
+                --j;
+              }
+              kd[j * B + t] = d2;
+              ki[j * B + t] = id;
+            }
+          }
+        }
+      }
+      if (cnt == n) {
+        // distance from q to the faces of the visited block that lie inside the grid
+        double bound = DBL_MAX;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+          if (lo[k] > 0) bound = fmin(bound, q[k] - (cg.lo[k] + lo[k] * cg.cell));
+          if (hi[k] < cg.g[k] - 1) bound = fmin(bound, (cg.lo[k] + (hi[k] + 1) * cg.cell) - q[k]);
+        }
+        if (bound == DBL_MAX) break;
+        bound *= (1.0 - 1e-9);
+        if (bound > 0.0 && kd[(n - 1) * B + t] < bound * bound) break;
+      }
+    }
+    if (cnt < n) atomicOr(flags, kDevKnnShort);
+    for (int j = 0; j < n; ++j) out_idx[(int64_t)j * nq + qi] = j < cnt ? ki[j * B + t] : c;
+  }
+}
+
+}  // namespace
+
+hsm_status build_stencils(hsm_plan p) {
+  cudaStream_t s = p->stream;
+  const int64_t N = p->N;
+  const int dim = p->dim;
+  const int T = 256;
+  const int grid = (int)std::min<int64_t>(ceil_div(N, T), (int64_t)num_sms() * 8);
+
+  // ---- bounds and lattice coordinates
+  unsigned long long* bbox = nullptr;
+  int* lat = nullptr;
+  int32_t* ijk = nullptr;
+  uint8_t* on_lat = nullptr;
+  HSM_CUDA(p, dev_alloc(&bbox, 2 * kMaxDim, s));
+  HSM_CUDA(p, dev_alloc(&lat, 2 * kMaxDim + 4, s));
+  HSM_CUDA(p, dev_alloc(&ijk, (size_t)dim * N, s));
+  HSM_CUDA(p, dev_alloc(&on_lat, N, s));
+  unsigned long long bb_init[2 * kMaxDim];
+  int lat_init[2 * kMaxDim + 4];
+  for (int k = 0; k < kMaxDim; ++k) {
+    bb_init[2 * k] = ~0ull;
+    bb_init[2 * k + 1] = 0ull;
+    lat_init[k] = 0x7fffffff;
+    lat_init[kMaxDim + k] = -0x7fffffff;
+  }
+  for (int k = 2 * kMaxDim; k < 2 * kMaxDim + 4; ++k) lat_init[k] = 0;
+  HSM_CUDA(p, cudaMemcpyAsync(bbox, bb_init, sizeof(bb_init), cudaMemcpyHostToDevice, s));
+  HSM_CUDA(p, cudaMemcpyAsync(lat, lat_init, sizeof(lat_init), cudaMemcpyHostToDevice, s));
+  k_bounds<<<grid, T, 0, s>>>(p->coords, N, dim, 1.0 / p->h, bbox, lat, lat + kMaxDim, ijk, on_lat);
+  HSM_CUDA(p, cudaGetLastError());
+  unsigned long long bb[2 * kMaxDim];
+  int lat_h[2 * kMaxDim + 4];
+  HSM_CUDA(p, cudaMemcpyAsync(bb, bbox, sizeof(bb), cudaMemcpyDeviceToHost, s));
+  HSM_CUDA(p, cudaMemcpyAsync(lat_h, lat, sizeof(lat_h), cudaMemcpyDeviceToHost, s));
+  HSM_CUDA(p, cudaStreamSynchronize(s));
+
+  // ---- lattice map and classification
+  LatticeGeom lg;
+  lg.dim = dim;
+  int64_t map_size = 1;
+  bool any_lat = lat_h[0] <= lat_h[kMaxDim];
+  for (int k = 0; k < kMaxDim; ++k) {
+    lg.lo[k] = any_lat && k < dim ? lat_h[k] : 0;
+    lg.ext[k] = any_lat && k < dim ? lat_h[kMaxDim + k] - lat_h[k] + 1 : 1;
+    map_size *= lg.ext[k];
+  }
+  if (map_size > (int64_t)1 << 30)
+    return set_error(p, HSM_EINVAL, "lattice extent too large for the lattice map (check h_regular)");
+  int32_t* map = nullptr;
+  HSM_CUDA(p, dev_alloc(&map, map_size, s));
+  HSM_CUDA(p, cudaMemsetAsync(map, 0x7f, map_size * sizeof(int32_t), s));
+  k_lattice_insert<<<grid, T, 0, s>>>(ijk, on_lat, N, lg, map);
+  int* d_demoted = lat + 2 * kMaxDim;
+  k_classify<<<grid, T, 0, s>>>(ijk, on_lat, p->is_regular, p->is_boundary, N, lg, map, p->kind, d_demoted);
+  HSM_CUDA(p, cudaGetLastError());
+
+  // ---- group lists (ascending node ids) and positions
+  int* counts = lat + 2 * kMaxDim + 1;
+  int32_t* list_mon = nullptr;
+  int32_t* list_rbf = nullptr;
+  HSM_CUDA(p, dev_alloc(&list_mon, N, s));
+  HSM_CUDA(p, dev_alloc(&list_rbf, N, s));
+  int cnt_h[3];
+  HSM_CUDA(p, cudaMemcpyAsync(&cnt_h[2], d_demoted, sizeof(int), cudaMemcpyDeviceToHost, s));
+  HSM_CUDA(p, select_indices(p->kind, 0, N, list_mon, p->pos, counts, s));
+  HSM_CUDA(p, select_indices(p->kind, 1, N, list_rbf, p->pos, counts + 1, s));
+  HSM_CUDA(p, cudaMemcpyAsync(cnt_h, counts, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  HSM_CUDA(p, cudaStreamSynchronize(s));
+  p->n_demoted = cnt_h[2];
+  p->mon.count = cnt_h[0];
+  p->rbf.count = cnt_h[1];
+  p->mon.width = 2 * dim + 1;
+  p->rbf.width = p->n;
+  p->mon.nodes = list_mon;
+  p->rbf.nodes = list_rbf;
+  HSM_CUDA(p, dev_alloc(&p->mon.idx, (size_t)p->mon.width * p->mon.count, s));
+  HSM_CUDA(p, dev_alloc(&p->rbf.idx, (size_t)p->rbf.width * p->rbf.count, s));
+  if (p->mon.count) {
+    int gm = (int)std::min<int64_t>(ceil_div(p->mon.count, T), (int64_t)num_sms() * 8);
+    k_mon_stencil<<<gm, T, 0, s>>>(ijk, list_mon, p->mon.count, N, lg, map, p->mon.idx);
+    HSM_CUDA(p, cudaGetLastError());
+  }
+
+  // ---- kNN for the RBF-FD group
+  if (p->rbf.count) {
+    if (N < p->n) return set_error(p, HSM_EINVAL, "fewer nodes than the stencil size");
+    CellGrid cg;
+    cg.dim = dim;
+    double ext_max = 0.0;
+    for (int k = 0; k < kMaxDim; ++k) {
+      double lo = k < dim ? host_from_ordered(bb[2 * k]) : 0.0;
+      double hi = k < dim ? host_from_ordered(bb[2 * k + 1]) : 0.0;
+      cg.lo[k] = lo;
+      ext_max = std::max(ext_max, hi - lo);
+      (void)hi;
+    }
+    double cell = p->h;
+    int64_t ncell = 0;
+    for (int tries = 0; tries < 64; ++tries) {
+      ncell = 1;
+      for (int k = 0; k < kMaxDim; ++k) {
+        double hi = k < dim ? host_from_ordered(bb[2 * k + 1]) : cg.lo[k];
+        cg.g[k] = k < dim ? (int)std::min<double>(floor((hi - cg.lo[k]) / cell) + 1.0, 1e9) : 1;
+        ncell *= cg.g[k];
+      }
+      if (ncell <= 4 * N + 1024) break;
+      cell *= 1.5;
+    }
+    cg.cell = cell;
+    cg.inv_cell = 1.0 / cell;
+    int32_t *cell_of = nullptr, *cstart = nullptr, *ccount = nullptr, *sorted_id = nullptr;
+    double* sorted_xyz = nullptr;
+    uint8_t* sorted_bnd = nullptr;
+    HSM_CUDA(p, dev_alloc(&cell_of, N, s));
+    HSM_CUDA(p, dev_alloc(&cstart, ncell + 1, s));
+    HSM_CUDA(p, dev_alloc(&ccount, ncell, s));
+    HSM_CUDA(p, dev_alloc(&sorted_id, N, s));
+    HSM_CUDA(p, dev_alloc(&sorted_xyz, (size_t)N * kMaxDim, s));
+    HSM_CUDA(p, dev_alloc(&sorted_bnd, N, s));
+    HSM_CUDA(p, cudaMemsetAsync(ccount, 0, ncell * sizeof(int32_t), s));
+    k_cell_count<<<grid, T, 0, s>>>(p->coords, N, cg, cell_of, ccount);
+    HSM_CUDA(p, cudaGetLastError());
+    HSM_CUDA(p, exclusive_scan_i32(ccount, cstart, ncell, s));
+    HSM_CUDA(p, cudaMemsetAsync(ccount, 0, ncell * sizeof(int32_t), s));
+    k_cell_scatter<<<grid, T, 0, s>>>(p->coords, p->is_boundary, N, dim, cell_of, cstart, ccount, sorted_id,
+                                      sorted_xyz, sorted_bnd);
+    HSM_CUDA(p, cudaGetLastError());
+    const int KT = 128;
+    size_t smem = (size_t)p->n * KT * (sizeof(double) + sizeof(int32_t));
+    int gk = (int)std::min<int64_t>(ceil_div(p->rbf.count, KT), (int64_t)num_sms() * 16);
+    if (dim == 2) {
+      if (smem > 48 * 1024) HSM_CUDA(p, cudaFuncSetAttribute(k_knn<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_knn<2><<<gk, KT, smem, s>>>(p->coords, N, p->is_boundary, list_rbf, p->rbf.count, p->n, cg, cstart,
+                                     sorted_id, sorted_xyz, sorted_bnd, p->rbf.idx, p->dev_flags);
+    } else {
+      if (smem > 48 * 1024) HSM_CUDA(p, cudaFuncSetAttribute(k_knn<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_knn<3><<<gk, KT, smem, s>>>(p->coords, N, p->is_boundary, list_rbf, p->rbf.count, p->n, cg, cstart,
+                                     sorted_id, sorted_xyz, sorted_bnd, p->rbf.idx, p->dev_flags);
+    }
+    HSM_CUDA(p, cudaGetLastError());
+    dev_free(&cell_of, s);
+    dev_free(&cstart, s);
+    dev_free(&ccount, s);
+    dev_free(&sorted_id, s);
+    dev_free(&sorted_xyz, s);
+    dev_free(&sorted_bnd, s);
+  }
+  dev_free(&bbox, s);
+  dev_free(&lat, s);
+  dev_free(&ijk, s);
+  dev_free(&on_lat, s);
+  dev_free(&map, s);
+  unsigned flags = 0;
+  HSM_CUDA(p, cudaMemcpyAsync(&flags, p->dev_flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  HSM_CUDA(p, cudaStreamSynchronize(s));
+  if (flags & kDevKnnShort) return set_error(p, HSM_EINVAL, "not enough candidate nodes for an RBF-FD stencil");
+  p->stencils_built = true;
+  return HSM_OK;
+}
+
+}  // namespace hsm

@@ -1,0 +1,677 @@
+// Explicit Boussinesq natural-convection step (Section 3, Eqs. 2-4) with
+// Chorin's projection, on the weights of a plan.
+//
+// Per step (rho = 1, e_up = last axis):
+//   1. v* = v + dt[-(v.grad)v + Pr lap v + Ra Pr (T - T_ref) e_up] inside,
+//      v* = 0 on walls (no-slip);
+//   2. pressure from the bordered system [Lp 1; 1' 0][p; c] = [rhs; 0] with
+//      Lp = Laplacian rows inside / normal-derivative rows on walls and
+//      rhs = div(v*)/dt inside, 0 on walls; BiCGSTAB warm-started from the
+//      previous p and c;
+//   3. v = v* - dt grad p inside, 0 on walls;
+//   4. T = T + dt[-v.grad T + lap T] inside, with the new v;
+//   5. Dirichlet walls T = T_bc; insulated walls T_b = -sum_{i>0} wn_i T_i / wn_0
+//      (a wall stencil holds only interior nodes besides its centre).
+//
+// Every kernel walks the two stencil groups of the plan (blocks of the MON
+// group first, then the RBF-FD group), one thread per node.  A BiCGSTAB
+// iteration is three kernels; each forms the vector it needs on the fly
+// inside its gathers (p = r + beta(p - omega v), s = r - alpha v), applies the
+// bordered operator, and reduces its dot products with a last-block-done
+// pattern (block partials in fixed order, no spinning), whose final block also
+// updates the scalars and the convergence flag.  Once the flag is set the
+// remaining kernels of a launched chunk return at once.
+#include <vector>
+
+#include "common.cuh"
+
+struct hsm_stepper_s {
+  hsm_plan plan = nullptr;
+  hsm_phys phys{};
+  int dim = 2;
+  int64_t N = 0;
+  int slot_d[3] = {0, 0, 0};  // weight slot of d/dx_k in the plan
+  int slot_lap = 0;
+  double* wp_rbf = nullptr;   // [n][rbf_count] pressure-row weights (lap inside, n.grad on walls)
+  double* wn_rbf = nullptr;   // [n][rbf_count] normal-derivative weights (walls only)
+  double* vstar = nullptr;    // [dim][N]
+  double* Tn = nullptr;       // [N]
+  double* vec = nullptr;      // Krylov vectors, each N+1: r, rhat, p0, p1, v0, v1, s, t, rhs
+  double* scal = nullptr;     // KrylovScalars
+  double* partial = nullptr;  // [3][blocks][4]
+  unsigned* counters = nullptr;
+  int blocks_mon = 0, blocks_rbf = 0, threads = 256;
+  double c = 0.0;             // Lagrange multiplier of the bordered system (kept on device)
+};
+
+namespace hsm {
+namespace {
+
+enum { V_R = 0, V_RHAT, V_P0, V_P1, V_V0, V_V1, V_S, V_T, V_RHS, V_COUNT };
+
+// Scalars of the Krylov solve (device memory, doubles + ints packed as doubles).
+struct KS {
+  double rho, alpha, omega, beta;
+  double bnorm2, rnorm2, tol2;
+  double xN;            // Lagrange multiplier c
+  double iter, done, breakdown, max_it, half;
+  double cur;           // which p/v buffer holds the current iterate (0 or 1)
+};
+
+struct StepArgs {
+  // plan groups
+  const int32_t* nodes[2];
+  const int32_t* idx[2];
+  const double* w[2];      // plan weights [nops][width][count]
+  const double* wp[2];     // pressure weights of the group ([width][count])
+  const double* wn[2];     // wall normal-derivative weights (rbf group only)
+  int64_t count[2];
+  int width[2];
+  int64_t bm;              // blocks of the MON group
+  int slot_d[3];
+  int slot_lap;
+  int dim;
+  int64_t N;
+  // physics
+  double Ra, Pr, dt, T_ref;
+  const uint8_t* bc;
+  const double* T_bc;
+  // fields
+  double* v;
+  double* T;
+  double* p;
+  double* vstar;
+  double* Tn;
+  double* vec;
+  KS* ks;
+  double* partial;
+  unsigned* counters;
+};
+
+__device__ __forceinline__ bool node_of(const StepArgs& a, int& g, int64_t& pos, int64_t& stride) {
+  if (blockIdx.x < a.bm) {
+    g = 0;
+    pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    stride = a.bm * blockDim.x;
+  } else {
+    g = 1;
+    pos = (blockIdx.x - a.bm) * (int64_t)blockDim.x + threadIdx.x;
+    stride = (gridDim.x - a.bm) * (int64_t)blockDim.x;
+  }
+  return true;
+}
+
+__device__ __forceinline__ const double* wslot(const StepArgs& a, int g, int slot) {
+  return a.w[g] + (int64_t)slot * a.width[g] * a.count[g];
+}
+
+// Block-reduce up to 4 partial sums; the last block to finish sums all
+// partials in block order and returns true (its thread 0 holds the totals).
+template <int Q>
+__device__ bool block_done(const StepArgs& a, int which, double (&vals)[Q], double (&tot)[Q]) {
+  __shared__ double sh[32][Q];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    double x = vals[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) sh[wid][q] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) / 32;
+    for (int q = 0; q < Q; ++q) {
+      double x = 0.0;
+      for (int i = 0; i < nw; ++i) x += sh[i][q];
+      a.partial[((int64_t)which * gridDim.x + blockIdx.x) * 4 + q] = x;
+    }
+    __threadfence();
+    unsigned t = atomicInc(&a.counters[which], gridDim.x - 1);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    for (int q = 0; q < Q; ++q) tot[q] = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b)
+      for (int q = 0; q < Q; ++q) tot[q] += __ldcg(&a.partial[((int64_t)which * gridDim.x + b) * 4 + q]);
+  }
+  return threadIdx.x == 0;
+}
+
+// ---- 1. predictor -----------------------------------------------------------
+template <int DIM>
+__global__ void k_predictor(StepArgs a) {
+  int g;
+  int64_t pos, stride;
+  node_of(a, g, pos, stride);
+  const int W = a.width[g];
+  const int64_t G = a.count[g];
+  for (; pos < G; pos += stride) {
+    const int32_t i = a.nodes[g][pos];
+    if (a.bc[i] != 0) {
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) a.vstar[k * a.N + i] = 0.0;
+      continue;
+    }
+    double grad[DIM][DIM];  // grad[k][j] = d v_k / d x_j
+    double lap[DIM];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      lap[k] = 0.0;
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) grad[k][j] = 0.0;
+    }
+    const double* wl = wslot(a, g, a.slot_lap);
+    for (int e = 0; e < W; ++e) {
+      const int32_t id = a.idx[g][(int64_t)e * G + pos];
+      const double wle = wl[(int64_t)e * G + pos];
+      double wd[DIM];
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) wd[j] = wslot(a, g, a.slot_d[j])[(int64_t)e * G + pos];
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) {
+        const double vk = a.v[k * a.N + id];
+        lap[k] = fma(wle, vk, lap[k]);
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) grad[k][j] = fma(wd[j], vk, grad[k][j]);
+      }
+    }
+    const double Ti = a.T[i];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      double adv = 0.0;
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) adv += a.v[j * a.N + i] * grad[k][j];
+      double f = -adv + a.Pr * lap[k];
+      if (k == DIM - 1) f += a.Ra * a.Pr * (Ti - a.T_ref);
+      a.vstar[k * a.N + i] = a.v[k * a.N + i] + a.dt * f;
+    }
+  }
+}
+
+// ---- 2a. rhs = div v*/dt, r = rhs - A x0, rhat = r, p = v = 0 ----------------
+template <int DIM>
+__global__ void k_krylov_init(StepArgs a) {
+  int g;
+  int64_t pos, stride;
+  node_of(a, g, pos, stride);
+  const int W = a.width[g];
+  const int64_t G = a.count[g];
+  const int64_t N1 = a.N + 1;
+  double* r = a.vec + V_R * N1;
+  double* rh = a.vec + V_RHAT * N1;
+  double* rhs = a.vec + V_RHS * N1;
+  const double xN = a.ks->xN;
+  double part[4] = {0.0, 0.0, 0.0, 0.0};  // sum x, sum rhs^2, sum r^2 (rho = rhat.r), 0
+  for (; pos < G; pos += stride) {
+    const int32_t i = a.nodes[g][pos];
+    const bool inner = a.bc[i] == 0;
+    double div = 0.0, ax = 0.0;
+    const double* wpg = a.wp[g];
+    for (int e = 0; e < W; ++e) {
+      const int32_t id = a.idx[g][(int64_t)e * G + pos];
+      if (inner) {
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) div = fma(wslot(a, g, a.slot_d[k])[(int64_t)e * G + pos], a.vstar[k * a.N + id], div);
+      }
+      ax = fma(wpg[(int64_t)e * G + pos], a.p[id], ax);
+    }
+    const double b = inner ? div / a.dt : 0.0;
+    const double ri = b - (ax + xN);
+    rhs[i] = b;
+    r[i] = ri;
+    rh[i] = ri;
+    a.vec[V_P0 * N1 + i] = 0.0;
+    a.vec[V_V0 * N1 + i] = 0.0;
+    part[0] += a.p[i];
+    part[1] += b * b;
+    part[2] += ri * ri;
+  }
+  double tot[4];
+  if (block_done<4>(a, 0, part, tot)) {
+    KS* ks = a.ks;
+    const double rN = 0.0 - tot[0];  // bordered row: 0 - sum x
+    r[a.N] = rN;
+    rh[a.N] = rN;
+    rhs[a.N] = 0.0;
+    a.vec[V_P0 * N1 + a.N] = 0.0;
+    a.vec[V_V0 * N1 + a.N] = 0.0;
+    ks->bnorm2 = tot[1];
+    ks->rnorm2 = tot[2] + rN * rN;
+    ks->rho = ks->rnorm2;  // rhat = r
+    ks->alpha = 1.0;
+    ks->omega = 1.0;
+    ks->beta = 0.0;
+    ks->cur = 0.0;
+    ks->iter = 0.0;
+    ks->half = 0.0;
+    ks->breakdown = 0.0;
+    ks->done = (ks->rnorm2 <= ks->tol2 * ks->bnorm2 || ks->bnorm2 == 0.0) ? 1.0 : 0.0;
+  }
+}
+
+// ---- 2b. one BiCGSTAB iteration in three kernels ---------------------------
+// A: p_new = r + beta (p_old - omega v_old) (on the fly), v_new = A p_new,
+//    partials: sum p_new, rhat.v_new
+template <int DIM>
+__global__ void k_bicg_a(StepArgs a) {
+  const KS* ks = a.ks;
+  if (ks->done != 0.0) return;
+  // rho_new = rhat.r is computed by kernel C of the previous iteration; on the
+  // first iteration rho_new is the initial r.r (rhat = r)
+  int g;
+  int64_t pos, stride;
+  node_of(a, g, pos, stride);
+  const int W = a.width[g];
+  const int64_t G = a.count[g];
+  const int64_t N1 = a.N + 1;
+  const int cur = (int)ks->cur;
+  const double* r = a.vec + V_R * N1;
+  const double* rh = a.vec + V_RHAT * N1;
+  const double* po = a.vec + (cur ? V_P1 : V_P0) * N1;
+  const double* vo = a.vec + (cur ? V_V1 : V_V0) * N1;
+  double* pn = a.vec + (cur ? V_P0 : V_P1) * N1;
+  double* vn = a.vec + (cur ? V_V0 : V_V1) * N1;
+  const double beta = ks->beta, omega = ks->omega;
+  const double pnN = r[a.N] + beta * (po[a.N] - omega * vo[a.N]);
+  double part[2] = {0.0, 0.0};
+  for (; pos < G; pos += stride) {
+    const int32_t i = a.nodes[g][pos];
+    double y = 0.0;
+    const double* wpg = a.wp[g];
+    for (int e = 0; e < W; ++e) {
+      const int32_t id = a.idx[g][(int64_t)e * G + pos];
+      const double pj = r[id] + beta * (po[id] - omega * vo[id]);
+      y = fma(wpg[(int64_t)e * G + pos], pj, y);
+    }
+    y += pnN;
+    const double pi = r[i] + beta * (po[i] - omega * vo[i]);
+    pn[i] = pi;
+    vn[i] = y;
+    part[0] += pi;
+    part[1] += rh[i] * y;
+  }
+  double tot[2];
+  if (block_done<2>(a, 0, part, tot)) {
+    KS* k = a.ks;
+    pn[a.N] = pnN;
+    vn[a.N] = tot[0];
+    const double rv = tot[1] + rh[a.N] * tot[0];
+    if (rv == 0.0 || !isfinite(rv)) {
+      k->breakdown = 1.0;
+      k->done = 1.0;
+      return;
+    }
+    k->alpha = k->rho / rv;
+    k->cur = 1.0 - k->cur;
+  }
+}
+
+// B: s = r - alpha v (on the fly), t = A s; partials: sum s, t.s, t.t, s.s
+template <int DIM>
+__global__ void k_bicg_b(StepArgs a) {
+  const KS* ks = a.ks;
+  if (ks->done != 0.0) return;
+  int g;
+  int64_t pos, stride;
+  node_of(a, g, pos, stride);
+  const int W = a.width[g];
+  const int64_t G = a.count[g];
+  const int64_t N1 = a.N + 1;
+  const int cur = (int)ks->cur;
+  const double* r = a.vec + V_R * N1;
+  const double* v = a.vec + (cur ? V_V1 : V_V0) * N1;
+  double* s = a.vec + V_S * N1;
+  double* t = a.vec + V_T * N1;
+  const double alpha = ks->alpha;
+  const double sN = r[a.N] - alpha * v[a.N];
+  double part[4] = {0.0, 0.0, 0.0, 0.0};
+  for (; pos < G; pos += stride) {
+    const int32_t i = a.nodes[g][pos];
+    double y = 0.0;
+    const double* wpg = a.wp[g];
+    for (int e = 0; e < W; ++e) {
+      const int32_t id = a.idx[g][(int64_t)e * G + pos];
+      y = fma(wpg[(int64_t)e * G + pos], r[id] - alpha * v[id], y);
+    }
+    y += sN;
+    const double si = r[i] - alpha * v[i];
+    s[i] = si;
+    t[i] = y;
+    part[0] += si;
+    part[1] += y * si;
+    part[2] += y * y;
+    part[3] += si * si;
+  }
+  double tot[4];
+  if (block_done<4>(a, 1, part, tot)) {
+    KS* k = a.ks;
+    s[a.N] = sN;
+    const double tN = tot[0];
+    t[a.N] = tN;
+    const double ts = tot[1] + tN * sN, tt = tot[2] + tN * tN, ss = tot[3] + sN * sN;
+    if (ss <= k->tol2 * k->bnorm2) {
+      k->half = 1.0;  // s already small: x += alpha p and stop
+      k->omega = 0.0;
+    } else if (tt == 0.0 || !isfinite(tt)) {
+      k->breakdown = 1.0;
+      k->done = 1.0;
+    } else {
+      k->omega = ts / tt;
+    }
+  }
+}
+
+// C: x += alpha p + omega s, r = s - omega t; partials: rhat.r, r.r
+template <int DIM>
+__global__ void k_bicg_c(StepArgs a) {
+  const KS* ks = a.ks;
+  if (ks->done != 0.0) return;
+  int g;
+  int64_t pos, stride;
+  node_of(a, g, pos, stride);
+  const int64_t G = a.count[g];
+  const int64_t N1 = a.N + 1;
+  const int cur = (int)ks->cur;
+  double* r = a.vec + V_R * N1;
+  const double* rh = a.vec + V_RHAT * N1;
+  const double* pc = a.vec + (cur ? V_P1 : V_P0) * N1;
+  const double* s = a.vec + V_S * N1;
+  const double* t = a.vec + V_T * N1;
+  const double alpha = ks->alpha, omega = ks->omega;
+  double part[2] = {0.0, 0.0};
+  for (; pos < G; pos += stride) {
+    const int32_t i = a.nodes[g][pos];
+    a.p[i] += alpha * pc[i] + omega * s[i];
+    const double ri = s[i] - omega * t[i];
+    r[i] = ri;
+    part[0] += rh[i] * ri;
+    part[1] += ri * ri;
+  }
+  double tot[2];
+  if (block_done<2>(a, 2, part, tot)) {
+    KS* k = a.ks;
+    k->xN += alpha * pc[a.N] + omega * s[a.N];
+    const double rN = s[a.N] - omega * t[a.N];
+    r[a.N] = rN;
+    const double rho_new = tot[0] + rh[a.N] * rN;
+    k->rnorm2 = tot[1] + rN * rN;
+    k->iter += 1.0;
+    if (k->half != 0.0 || k->rnorm2 <= k->tol2 * k->bnorm2) {
+      k->done = 1.0;
+    } else if (rho_new == 0.0 || !isfinite(rho_new) || omega == 0.0) {
+      k->breakdown = 1.0;
+      k->done = 1.0;
+    } else if (k->iter >= k->max_it) {
+      k->done = 1.0;
+    } else {
+      k->beta = (rho_new / k->rho) * (alpha / omega);
+      k->rho = rho_new;
+    }
+  }
+}
+
+// ---- 3. correction and 4. temperature ----------------------------------------
+template <int DIM>
+__global__ void k_correct_temperature(StepArgs a) {
+  int g;
+  int64_t pos, stride;
+  node_of(a, g, pos, stride);
+  const int W = a.width[g];
+  const int64_t G = a.count[g];
+  for (; pos < G; pos += stride) {
+    const int32_t i = a.nodes[g][pos];
+    const uint8_t b = a.bc[i];
+    if (b != 0) {
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) a.v[k * a.N + i] = 0.0;
+      a.Tn[i] = b == HSM_BC_T_DIRICHLET ? a.T_bc[i] : a.T[i];
+      continue;
+    }
+    double gp[DIM], gT[DIM], lT = 0.0;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) gp[k] = gT[k] = 0.0;
+    const double* wl = wslot(a, g, a.slot_lap);
+    for (int e = 0; e < W; ++e) {
+      const int32_t id = a.idx[g][(int64_t)e * G + pos];
+      const double pj = a.p[id], Tj = a.T[id];
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) {
+        const double wd = wslot(a, g, a.slot_d[k])[(int64_t)e * G + pos];
+        gp[k] = fma(wd, pj, gp[k]);
+        gT[k] = fma(wd, Tj, gT[k]);
+      }
+      lT = fma(wl[(int64_t)e * G + pos], Tj, lT);
+    }
+    double adv = 0.0;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      const double vk = a.vstar[k * a.N + i] - a.dt * gp[k];
+      a.v[k * a.N + i] = vk;
+      adv += vk * gT[k];
+    }
+    a.Tn[i] = a.T[i] + a.dt * (-adv + lT);
+  }
+}
+
+// ---- 5. temperature boundary closure and write-back -------------------------
+__global__ void k_temperature_bc(StepArgs a) {
+  int g;
+  int64_t pos, stride;
+  node_of(a, g, pos, stride);
+  const int W = a.width[g];
+  const int64_t G = a.count[g];
+  for (; pos < G; pos += stride) {
+    const int32_t i = a.nodes[g][pos];
+    double Ti = a.Tn[i];
+    if (g == 1 && a.bc[i] == HSM_BC_T_NEUMANN) {
+      const double* wn = a.wn[1];
+      double s = 0.0;
+      for (int e = 1; e < W; ++e) s = fma(wn[(int64_t)e * G + pos], a.Tn[a.idx[1][(int64_t)e * G + pos]], s);
+      Ti = -s / wn[pos];
+    }
+    a.T[i] = Ti;
+  }
+}
+
+// Pressure-row and wall normal-derivative weights of the RBF-FD group.
+template <int DIM>
+__global__ void k_wall_weights(const int32_t* __restrict__ nodes, int64_t G, int W, const double* __restrict__ w,
+                               int s0, int s1, int s2, int slap, const uint8_t* __restrict__ bc,
+                               const double* __restrict__ normals, int64_t N, double* wp, double* wn) {
+  const int slots[3] = {s0, s1, s2};
+  for (int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; pos < G; pos += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t i = nodes[pos];
+    const bool wall = bc[i] != 0;
+    for (int e = 0; e < W; ++e) {
+      double x = 0.0;
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) x = fma(normals[k * N + i], w[((int64_t)slots[k] * W + e) * G + pos], x);
+      wn[(int64_t)e * G + pos] = wall ? x : 0.0;
+      wp[(int64_t)e * G + pos] = wall ? x : w[((int64_t)slap * W + e) * G + pos];
+    }
+  }
+}
+
+StepArgs make_args(hsm_stepper st, double* v, double* T, double* p) {
+  hsm_plan pl = st->plan;
+  StepArgs a{};
+  a.nodes[0] = pl->mon.nodes;
+  a.nodes[1] = pl->rbf.nodes;
+  a.idx[0] = pl->mon.idx;
+  a.idx[1] = pl->rbf.idx;
+  a.w[0] = pl->mon.w64;
+  a.w[1] = pl->rbf.w64;
+  a.wp[0] = pl->mon.w64 + (int64_t)st->slot_lap * pl->mon.width * pl->mon.count;
+  a.wp[1] = st->wp_rbf;
+  a.wn[0] = nullptr;
+  a.wn[1] = st->wn_rbf;
+  a.count[0] = pl->mon.count;
+  a.count[1] = pl->rbf.count;
+  a.width[0] = pl->mon.width;
+  a.width[1] = pl->rbf.width;
+  a.bm = st->blocks_mon;
+  for (int k = 0; k < 3; ++k) a.slot_d[k] = st->slot_d[k];
+  a.slot_lap = st->slot_lap;
+  a.dim = st->dim;
+  a.N = st->N;
+  a.Ra = st->phys.Ra;
+  a.Pr = st->phys.Pr;
+  a.dt = st->phys.dt;
+  a.T_ref = st->phys.T_ref;
+  a.bc = st->phys.bc;
+  a.T_bc = st->phys.T_bc;
+  a.v = v;
+  a.T = T;
+  a.p = p;
+  a.vstar = st->vstar;
+  a.Tn = st->Tn;
+  a.vec = st->vec;
+  a.ks = reinterpret_cast<KS*>(st->scal);
+  a.partial = st->partial;
+  a.counters = st->counters;
+  return a;
+}
+
+template <int DIM>
+hsm_status run_steps(hsm_stepper st, int n_steps, double* v, double* T, double* p, int* iters, bool* notconv) {
+  hsm_plan pl = st->plan;
+  cudaStream_t s = pl->stream;
+  StepArgs a = make_args(st, v, T, p);
+  const dim3 grid((unsigned)(st->blocks_mon + st->blocks_rbf)), blk(st->threads);
+  const int chunk = 16;
+  KS host{};
+  for (int it = 0; it < n_steps; ++it) {
+    k_predictor<DIM><<<grid, blk, 0, s>>>(a);
+    k_krylov_init<DIM><<<grid, blk, 0, s>>>(a);
+    HSM_CUDA(pl, cudaGetLastError());
+    const int max_chunks = (int)(st->phys.krylov_max_it / chunk) + 2;
+    for (int ch = 0; ch < max_chunks; ++ch) {
+      for (int c = 0; c < chunk; ++c) {
+        k_bicg_a<DIM><<<grid, blk, 0, s>>>(a);
+        k_bicg_b<DIM><<<grid, blk, 0, s>>>(a);
+        k_bicg_c<DIM><<<grid, blk, 0, s>>>(a);
+      }
+      HSM_CUDA(pl, cudaGetLastError());
+      HSM_CUDA(pl, cudaMemcpyAsync(&host, a.ks, sizeof(KS), cudaMemcpyDeviceToHost, s));
+      HSM_CUDA(pl, cudaStreamSynchronize(s));
+      if (host.done != 0.0) break;
+    }
+    if (iters) iters[it] = (int)host.iter;
+    if (host.breakdown != 0.0 || host.rnorm2 > host.tol2 * host.bnorm2 * 1.0000001) *notconv = true;
+    k_correct_temperature<DIM><<<grid, blk, 0, s>>>(a);
+    k_temperature_bc<<<grid, blk, 0, s>>>(a);
+    HSM_CUDA(pl, cudaGetLastError());
+  }
+  HSM_CUDA(pl, cudaStreamSynchronize(s));
+  return HSM_OK;
+}
+
+}  // namespace
+}  // namespace hsm
+
+using namespace hsm;
+
+extern "C" {
+
+hsm_status hsm_stepper_create(hsm_stepper* out, hsm_plan pl, const hsm_phys* phys) {
+  if (!out || !pl || !phys) return set_error(pl, HSM_EINVAL, "out, plan and phys are required");
+  *out = nullptr;
+  if (!pl->weights_built) return set_error(pl, HSM_ESTATE, "the plan's weights are not computed");
+  const unsigned need = HSM_DX | HSM_DY | HSM_LAP | (pl->dim == 3 ? HSM_DZ : 0);
+  if ((pl->op_mask & need) != need) return set_error(pl, HSM_EINVAL, "the plan needs every first derivative and the Laplacian");
+  if (!phys->bc || !phys->T_bc || !phys->normals) return set_error(pl, HSM_EINVAL, "bc, T_bc and normals are required");
+  if (!(phys->dt > 0.0) || !(phys->krylov_tol > 0.0) || phys->krylov_max_it < 1)
+    return set_error(pl, HSM_EINVAL, "dt, krylov_tol and krylov_max_it must be positive");
+  hsm_stepper st = new (std::nothrow) hsm_stepper_s();
+  if (!st) return set_error(pl, HSM_ENOMEM, "host allocation failed");
+  st->plan = pl;
+  st->phys = *phys;
+  st->dim = pl->dim;
+  st->N = pl->N;
+  int slot = 0;
+  for (int b = 0; b < 4; ++b) {
+    if (!(pl->op_mask & (1u << b))) continue;
+    if (b < 3) st->slot_d[b] = slot;
+    else st->slot_lap = slot;
+    ++slot;
+  }
+  cudaStream_t s = pl->stream;
+  auto fail = [&](hsm_status code) {
+    hsm_stepper_destroy(st);
+    return code;
+  };
+  const int64_t N = pl->N, G = pl->rbf.count, W = pl->rbf.width;
+  if (dev_alloc(&st->wp_rbf, W * G, s) || dev_alloc(&st->wn_rbf, W * G, s) ||
+      dev_alloc(&st->vstar, (size_t)pl->dim * N, s) || dev_alloc(&st->Tn, N, s) ||
+      dev_alloc(&st->vec, (size_t)V_COUNT * (N + 1), s) || dev_alloc(&st->scal, 16, s))
+    return fail(set_error(pl, HSM_ENOMEM, "stepper allocation failed"));
+  const int T = st->threads;
+  const int64_t full = (int64_t)num_sms() * (2048 / T);
+  const int64_t tot = pl->mon.count + pl->rbf.count;
+  st->blocks_mon = pl->mon.count ? (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(pl->mon.count, T),
+                                                                                 full * pl->mon.count / tot + 1))
+                                 : 0;
+  st->blocks_rbf = pl->rbf.count ? (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(pl->rbf.count, T),
+                                                                                 full * pl->rbf.count / tot + 1))
+                                 : 0;
+  const int nb = st->blocks_mon + st->blocks_rbf;
+  if (dev_alloc(&st->partial, (size_t)3 * nb * 4, s) || dev_alloc(&st->counters, 4, s))
+    return fail(set_error(pl, HSM_ENOMEM, "stepper allocation failed"));
+  if (cudaMemsetAsync(st->counters, 0, 4 * sizeof(unsigned), s) != cudaSuccess)
+    return fail(set_error(pl, HSM_ECUDA, "memset failed"));
+  KS ks{};
+  ks.tol2 = phys->krylov_tol * phys->krylov_tol;
+  ks.max_it = phys->krylov_max_it;
+  ks.xN = 0.0;
+  ks.done = 1.0;
+  if (cudaMemcpyAsync(st->scal, &ks, sizeof(KS), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return fail(set_error(pl, HSM_ECUDA, "copy failed"));
+  if (G) {
+    int grid = (int)std::min<int64_t>(ceil_div(G, 256), (int64_t)num_sms() * 8);
+    if (pl->dim == 2)
+      k_wall_weights<2><<<grid, 256, 0, s>>>(pl->rbf.nodes, G, (int)W, pl->rbf.w64, st->slot_d[0], st->slot_d[1], 0,
+                                             st->slot_lap, phys->bc, phys->normals, N, st->wp_rbf, st->wn_rbf);
+    else
+      k_wall_weights<3><<<grid, 256, 0, s>>>(pl->rbf.nodes, G, (int)W, pl->rbf.w64, st->slot_d[0], st->slot_d[1],
+                                             st->slot_d[2], st->slot_lap, phys->bc, phys->normals, N, st->wp_rbf,
+                                             st->wn_rbf);
+  }
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(cuda_fail(pl, e, "hsm_stepper_create"));
+  *out = st;
+  return HSM_OK;
+}
+
+hsm_status hsm_step(hsm_stepper st, int n_steps, double* v, double* T, double* p, int* krylov_iters) {
+  if (!st) return set_error(nullptr, HSM_EINVAL, "stepper is NULL");
+  if (n_steps < 0 || !v || !T || !p) return set_error(st->plan, HSM_EINVAL, "invalid step arguments");
+  bool notconv = false;
+  hsm_status r = st->dim == 2 ? run_steps<2>(st, n_steps, v, T, p, krylov_iters, &notconv)
+                              : run_steps<3>(st, n_steps, v, T, p, krylov_iters, &notconv);
+  if (r != HSM_OK) return r;
+  if (notconv) return set_error(st->plan, HSM_ENOTCONV, "a pressure solve stopped before its tolerance");
+  return HSM_OK;
+}
+
+hsm_status hsm_stepper_destroy(hsm_stepper st) {
+  if (!st) return HSM_OK;
+  cudaStream_t s = st->plan ? st->plan->stream : nullptr;
+  dev_free(&st->wp_rbf, s);
+  dev_free(&st->wn_rbf, s);
+  dev_free(&st->vstar, s);
+  dev_free(&st->Tn, s);
+  dev_free(&st->vec, s);
+  dev_free(&st->scal, s);
+  dev_free(&st->partial, s);
+  dev_free(&st->counters, s);
+  cudaStreamSynchronize(s);
+  delete st;
+  return HSM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,207 @@
+"""Thin ctypes binding of libhsm (the C ABI declared in include/hsm.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+Functions keep the C names; the small ``Plan`` / ``Stepper`` classes only hold
+handles and turn status codes into exceptions.  Device buffers are passed as
+torch CUDA tensors (their ``data_ptr()``), streams as torch streams.  There is
+no CPU fallback: importing this module without the built library raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhsm.so")
+
+HSM_DX, HSM_DY, HSM_DZ, HSM_LAP = 1, 2, 4, 8
+HSM_PREC_FP64, HSM_PREC_FP32_REFINE, HSM_PREC_LEARNED = 0, 1, 2
+HSM_F32, HSM_F64 = 0, 1
+HSM_NODE_OK, HSM_NODE_DEMOTED, HSM_NODE_REFINE_FP64, HSM_NODE_LEARNED_SOLVE, HSM_NODE_SINGULAR = 0, 1, 2, 3, 255
+HSM_BC_INTERIOR, HSM_BC_T_DIRICHLET, HSM_BC_T_NEUMANN = 0, 1, 2
+STATUS = {0: "HSM_OK", 1: "HSM_EINVAL", 2: "HSM_ENOMEM", 3: "HSM_ECUDA", 4: "HSM_ESINGULAR",
+          5: "HSM_ENOTCONV", 6: "HSM_ETIMEOUT", 7: "HSM_EBOUNDS", 8: "HSM_ESTATE"}
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libhsm.so is not built ({LIB_PATH}); run paper_2303_01760_gb300/build.py "
+                      "or __graft_entry__.build()")
+
+lib = C.CDLL(LIB_PATH)
+
+_p = C.c_void_p
+_i64 = C.c_int64
+
+
+class hsm_phys(C.Structure):
+    _fields_ = [("Ra", C.c_double), ("Pr", C.c_double), ("dt", C.c_double), ("T_ref", C.c_double),
+                ("bc", _p), ("T_bc", _p), ("normals", _p), ("krylov_tol", C.c_double),
+                ("krylov_max_it", C.c_int)]
+
+
+_SIGS = {
+    "hsm_status_string": (C.c_char_p, [C.c_int]),
+    "hsm_last_error": (C.c_int, [_p, C.c_char_p, C.c_size_t]),
+    "hsm_plan_create": (C.c_int, [C.POINTER(_p), C.c_int, _i64, _p, _p, _p, C.c_double, C.c_int, C.c_int,
+                                  C.c_uint, _p]),
+    "hsm_plan_build_stencils": (C.c_int, [_p]),
+    "hsm_plan_compute_weights": (C.c_int, [_p, C.c_int, _p]),
+    "hsm_plan_query": (C.c_int, [_p, C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_i64)]),
+    "hsm_plan_export_csr": (C.c_int, [_p, C.c_uint, _p, _p, _p]),
+    "hsm_apply": (C.c_int, [_p, C.c_uint, C.c_int, _p, _p]),
+    "hsm_plan_autotune": (C.c_int, [_p, C.c_char_p]),
+    "hsm_plan_destroy": (C.c_int, [_p]),
+    "hsm_stepper_create": (C.c_int, [C.POINTER(_p), _p, C.POINTER(hsm_phys)]),
+    "hsm_step": (C.c_int, [_p, C.c_int, _p, _p, _p, C.POINTER(C.c_int)]),
+    "hsm_stepper_destroy": (C.c_int, [_p]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(lib, _name, None)
+    if _f is not None:
+        _f.restype = _res
+        _f.argtypes = _args
+        globals()[_name] = _f
+
+
+class HsmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def last_error(handle=None) -> str:
+    buf = C.create_string_buffer(1024)
+    lib.hsm_last_error(handle, buf, 1024)
+    return buf.value.decode(errors="replace")
+
+
+def check(code, handle=None):
+    if code != 0:
+        raise HsmError(code, last_error(handle))
+    return code
+
+
+def ptr(t):
+    """Device pointer of a torch tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("libhsm needs CUDA tensors")
+    if not t.is_contiguous():
+        raise ValueError("libhsm needs contiguous tensors")
+    return C.c_void_p(t.data_ptr())
+
+
+def stream_handle(stream=None):
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def op_list(mask, dim):
+    names = []
+    for b, nm in ((1, "dx"), (2, "dy"), (4, "dz"), (8, "lap")):
+        if mask & b:
+            names.append(nm)
+    return names
+
+
+class Plan:
+    """Owns an hsm_plan.  ``coords`` (f64 [dim, N]), ``is_regular`` and
+    ``is_boundary`` (u8 [N]) are CUDA tensors that must outlive the plan."""
+
+    def __init__(self, coords, is_regular, is_boundary, h, m=2, n=0, op_mask=None, stream=None):
+        dim, N = coords.shape
+        if op_mask is None:
+            op_mask = HSM_DX | HSM_DY | HSM_LAP | (HSM_DZ if dim == 3 else 0)
+        self.dim, self.N, self.op_mask = dim, N, op_mask
+        self._keep = (coords, is_regular, is_boundary)
+        h_ = C.c_void_p()
+        check(lib.hsm_plan_create(C.byref(h_), dim, N, ptr(coords), ptr(is_regular), ptr(is_boundary),
+                                  float(h), int(m), int(n), int(op_mask), stream_handle(stream)))
+        self.h = h_
+
+    def build_stencils(self):
+        check(lib.hsm_plan_build_stencils(self.h), self.h)
+        return self
+
+    def compute_weights(self, prec=HSM_PREC_FP64, node_status=None, allow_singular=False):
+        code = lib.hsm_plan_compute_weights(self.h, int(prec), ptr(node_status))
+        if code == 4 and allow_singular:
+            return code
+        check(code, self.h)
+        return code
+
+    def query(self):
+        a, b, c, d = _i64(), _i64(), _i64(), _i64()
+        check(lib.hsm_plan_query(self.h, C.byref(a), C.byref(b), C.byref(c), C.byref(d)), self.h)
+        return dict(nnz_per_op=a.value, n_mon=b.value, n_demoted=c.value, n_fallback=d.value)
+
+    def export_csr(self, op):
+        import torch
+
+        q = self.query()
+        dev = self._keep[0].device
+        rp = torch.empty(self.N + 1, dtype=torch.int64, device=dev)
+        col = torch.empty(q["nnz_per_op"], dtype=torch.int32, device=dev)
+        val = torch.empty(q["nnz_per_op"], dtype=torch.float64, device=dev)
+        check(lib.hsm_plan_export_csr(self.h, int(op), ptr(rp), ptr(col), ptr(val)), self.h)
+        return rp, col, val
+
+    def apply(self, u, op_mask=None, out=None):
+        import torch
+
+        op_mask = self.op_mask if op_mask is None else op_mask
+        k = bin(op_mask).count("1")
+        if out is None:
+            out = torch.empty((k, self.N), dtype=torch.float64, device=u.device)
+        dt = HSM_F64 if u.dtype == torch.float64 else HSM_F32
+        if u.dtype not in (torch.float64, torch.float32):
+            raise ValueError("u must be float32 or float64")
+        check(lib.hsm_apply(self.h, int(op_mask), dt, ptr(u), ptr(out)), self.h)
+        return out
+
+    def autotune(self, cache_path=None):
+        check(lib.hsm_plan_autotune(self.h, cache_path.encode() if cache_path else None), self.h)
+
+    def close(self):
+        if self.h:
+            lib.hsm_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Stepper:
+    """Owns an hsm_stepper on a plan (Section 3 explicit Boussinesq step)."""
+
+    def __init__(self, plan, Ra, Pr, dt, T_ref, bc, T_bc, normals, krylov_tol=1e-12, krylov_max_it=2000):
+        self.plan = plan
+        self._keep = (bc, T_bc, normals)
+        self.phys = hsm_phys(float(Ra), float(Pr), float(dt), float(T_ref), ptr(bc).value, ptr(T_bc).value,
+                             ptr(normals).value, float(krylov_tol), int(krylov_max_it))
+        h_ = C.c_void_p()
+        check(lib.hsm_stepper_create(C.byref(h_), plan.h, C.byref(self.phys)), plan.h)
+        self.h = h_
+
+    def step(self, v, T, p, n_steps=1, allow_notconv=False):
+        iters = (C.c_int * max(1, n_steps))()
+        code = lib.hsm_step(self.h, int(n_steps), ptr(v), ptr(T), ptr(p), iters)
+        if not (code == 5 and allow_notconv):
+            check(code, self.plan.h)
+        return list(iters)[:n_steps], code
+
+    def close(self):
+        if self.h:
+            lib.hsm_stepper_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

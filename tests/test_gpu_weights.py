@@ -1,0 +1,154 @@
+"""CUDA path vs the FP64 oracle: stencils, weights and operator application
+(Eq. 1, Section 2 and 2.1), called through the C ABI."""
+import numpy as np
+import pytest
+
+from oracle import apply as oap
+from oracle import stencils as ost
+from oracle import weights as ow
+from paper_2303_01760_gb300 import nodesets
+
+from gpu_helpers import gpu_csr, make_plan
+
+pytestmark = pytest.mark.gpu
+
+BIT = {"dx": 1, "dy": 2, "dz": 4, "lap": 8}
+TOL_FP64 = 1e-10      # relative weight error per stencil and operator, FP64 path
+TOL_FP32R = 1e-5      # FP32 factorisation + FP64 refinement
+
+
+def _rows(rp, col, val, nodes, width):
+    ix = rp[nodes][:, None] + np.arange(width)[None, :]
+    return col[ix], val[ix]
+
+
+def _rel(a, b):
+    return np.abs(a - b).max(1) / np.abs(b).max(1)
+
+
+def _check_plan(ns, m, prec=0, centers=None, tol=TOL_FP64, apply_check=True):
+    import torch
+
+    dim = ns.dim
+    n = ow.stencil_size(dim, m)
+    ops = ow.ops_for(dim)
+    plan, code, status = make_plan(ns, m=m, prec=prec, node_status=True)
+    assert code == 0
+    st = ost.build_stencils(ns.coords, ns.is_regular, ns.is_boundary, ns.h, n, centers=centers)
+    W = ow.all_weights(ns.coords, st, m)
+    q = plan.query()
+    if centers is None:
+        assert q["n_mon"] == len(st["mon_nodes"])
+        assert q["n_demoted"] == len(st["demoted"])
+    status = status.cpu().numpy()
+    if prec == 0:
+        assert np.all(status[st["mon_nodes"]] == 0)
+        assert np.all(status[st["demoted"]] == 1)
+    else:
+        assert np.all(np.isin(status[st["rbf_nodes"]], (0, 1, 2)))
+    worst = {}
+    for op in ops:
+        rp, col, val = gpu_csr(plan, BIT[op])
+        for grp, width in (("mon", 2 * dim + 1), ("rbf", n)):
+            nodes = st[grp + "_nodes"]
+            if len(nodes) == 0:
+                continue
+            c, v = _rows(rp, col, val, nodes, width)
+            assert np.array_equal(rp[nodes + 1] - rp[nodes], np.full(len(nodes), width))
+            assert np.array_equal(c, st[grp + "_idx"]), f"{grp} stencil mismatch"
+            e = _rel(v, W[grp][op])
+            worst[(grp, op)] = float(e.max())
+            assert e.max() <= tol, (grp, op, e.max(), int(np.argmax(e)))
+    if apply_check:
+        u, _ = nodesets.field_sincos(ns.coords) if dim == 2 else nodesets.field_random_smooth(ns.coords)
+        ut = torch.from_numpy(u).cuda()
+        out = plan.apply(ut).cpu().numpy()
+        out32 = plan.apply(ut.float()).cpu().numpy()
+        for k, op in enumerate(ops):
+            for grp in ("mon", "rbf"):
+                nodes = st[grp + "_nodes"]
+                if len(nodes) == 0:
+                    continue
+                ref = oap.apply_group(st[grp + "_idx"], W[grp][op], u)
+                scale = (np.abs(W[grp][op]) * np.abs(u[st[grp + "_idx"]])).sum(1)
+                assert np.all(np.abs(out[k, nodes] - ref) <= max(tol, 1e-12) * 10 * scale)
+                assert np.all(np.abs(out32[k, nodes] - ref) <= (1e-6 + tol) * scale)
+    plan.close()
+    return worst
+
+
+def test_square_wall_band_fp64_full():
+    """Unit square, lattice h=1/40 inside, Poisson-disk band along the walls,
+    m=2, n=12: every stencil and weight against the oracle."""
+    _check_plan(nodesets.square_wall_band(n=40), m=2)
+
+
+def test_square_wall_band_m4():
+    _check_plan(nodesets.square_wall_band(n=30, seed=nodesets.SEED_BASE + 11), m=4)
+
+
+def test_all_regular_and_all_scattered():
+    ns = nodesets.square_wall_band(n=32, wall_band=0.0)
+    _check_plan(ns, m=2)
+    _check_plan(ns.all_scattered(), m=2)
+
+
+def test_cube_spheres_small_m2_m3():
+    ns = nodesets.cube_spheres(n=14, n_holes=2, r_range=(0.1, 0.15), band=0.12, seed=nodesets.SEED_BASE + 21)
+    _check_plan(ns, m=2)
+    _check_plan(ns, m=3)
+
+
+def test_fp32_refinement_within_tolerance():
+    ns = nodesets.square_wall_band(n=40)
+    w = _check_plan(ns, m=2, prec=1, tol=TOL_FP32R)
+    assert max(w.values()) <= TOL_FP32R
+
+
+def test_fp32_refinement_m4_and_3d():
+    _check_plan(nodesets.square_wall_band(n=30, seed=nodesets.SEED_BASE + 11), m=4, prec=1, tol=TOL_FP32R)
+    ns = nodesets.cube_spheres(n=14, n_holes=2, r_range=(0.1, 0.15), band=0.12, seed=nodesets.SEED_BASE + 21)
+    _check_plan(ns, m=3, prec=1, tol=TOL_FP32R)
+
+
+def test_irregular_250k_sampled():
+    """The 2D irregular workload at full size (unit square minus 8 holes,
+    h=0.002): sampled nodes compared one by one with the oracle."""
+    ns = nodesets.cached(nodesets.square_holes)
+    rng = np.random.default_rng(123)
+    centers = np.unique(np.r_[rng.choice(ns.N, 3000, replace=False), np.flatnonzero(ns.is_boundary)[:500]])
+    _check_plan(ns, m=2, centers=centers)
+
+
+def test_duplicate_nodes_are_reported_singular():
+    """Two scattered nodes at the same position make their RBF-FD systems
+    singular: the call reports HSM_ESINGULAR and marks those nodes 255
+    without faulting."""
+    ns = nodesets.square_wall_band(n=20)
+    sc = np.flatnonzero((ns.is_regular == 0) & (ns.is_boundary == 0))
+    ns.coords[:, sc[1]] = ns.coords[:, sc[0]]
+    plan, code, status = make_plan(ns, m=2, node_status=True)
+    assert code == 4
+    status = status.cpu().numpy()
+    assert status[sc[0]] == 255 and status[sc[1]] == 255
+    assert np.sum(status == 255) < ns.N // 4
+    plan.close()
+
+
+def test_invalid_arguments_rejected_before_launch():
+    import torch
+    from paper_2303_01760_gb300 import hsm
+
+    ns = nodesets.square_wall_band(n=10)
+    c = torch.from_numpy(ns.coords).cuda()
+    r = torch.from_numpy(ns.is_regular).cuda()
+    with pytest.raises(hsm.HsmError) as e:
+        hsm.Plan(c, r, None, ns.h, m=2, n=3)
+    assert e.value.code == 1
+    with pytest.raises(hsm.HsmError):
+        hsm.Plan(c, r, None, ns.h, m=2, op_mask=hsm.HSM_DZ)
+    p = hsm.Plan(c, r, None, ns.h, m=2)
+    with pytest.raises(hsm.HsmError) as e:
+        p.compute_weights()
+    assert e.value.code == 8
+    p.close()
