@@ -97,8 +97,11 @@ hsm_status hsm_last_error(hsm_plan plan, char* buf, size_t len);
  *   n_nodes     N >= 1 (and < 2^31)
  *   coords      device f64 [dim][N]; must stay valid while the plan is used
  *   is_regular  device u8 [N]; 1 = regular lattice node (MON candidate)
- *   is_boundary device u8 [N] or NULL; 1 = boundary node (always RBF-FD, and
- *               its stencil is itself plus its n-1 nearest interior nodes)
+ *   is_boundary device u8 [N] or NULL; 1 = boundary node (always RBF-FD; its
+ *               stencil is itself plus the n-1 interior nodes nearest to the
+ *               point one lattice spacing inside, x_c - h_regular * n_c)
+ *   normals     device f64 [dim][N] outward unit normals of boundary nodes, or
+ *               NULL (then the search point is x_c itself)
  *   h_regular   spacing of the regular lattice; lattice points are integer
  *               multiples of h_regular along every axis
  *   aug_m       monomial augmentation degree m of the RBF-FD basis, 1..6
@@ -109,15 +112,17 @@ hsm_status hsm_last_error(hsm_plan plan, char* buf, size_t len);
  * Allocates nothing on the device until hsm_plan_build_stencils.            */
 hsm_status hsm_plan_create(hsm_plan* out, int dim, int64_t n_nodes, const double* coords,
                            const uint8_t* is_regular, const uint8_t* is_boundary,
-                           double h_regular, int aug_m, int stencil_n, unsigned op_mask,
-                           void* cuda_stream);
+                           const double* normals, double h_regular, int aug_m, int stencil_n,
+                           unsigned op_mask, void* cuda_stream);
 
 /* Builds every stencil (Section 2, "a set of n neighbouring nodes"):
  *   MON nodes: {c, c-e1, c+e1, c-e2, c+e2[, c-e3, c+e3]} through the lattice;
  *   RBF-FD nodes: the n nodes of smallest (squared distance, node id), the
  *   squared distance summed in coordinate order in FP64 without fused
- *   multiply-add.  A regular-flagged node that is a boundary node, is not on
- *   the lattice, or misses a lattice neighbour is demoted to RBF-FD.
+ *   multiply-add; boundary nodes: the node, then the n-1 interior nodes of
+ *   smallest (squared distance to x_c - h n_c, node id).  A regular-flagged
+ *   node that is a boundary node, is not on the lattice, or misses a lattice
+ *   neighbour is demoted to RBF-FD.
  * Synchronises the plan's stream (the group sizes are read back).           */
 hsm_status hsm_plan_build_stencils(hsm_plan plan);
 
@@ -126,8 +131,10 @@ hsm_status hsm_plan_build_stencils(hsm_plan plan);
  * augmented system [A P; P^T 0][w; lambda] = [L phi; L p] with phi = r^3
  * (Section 2.1, Section 4), by the method selected with prec.
  *   node_status  device u8 [N] or NULL; receives one HSM_NODE_* per node
- * Returns HSM_ESINGULAR when some node has no valid weights (its weights are
- * then zero).  Synchronises the plan's stream (the failure count is read).  */
+ * A system is singular when a pivot of the scaled FP64 system (entries of
+ * order one) falls below 1e-12 in magnitude or is not finite.  Returns
+ * HSM_ESINGULAR when some node has no valid weights (its weights are then
+ * zero and its status HSM_NODE_SINGULAR).  Synchronises the plan's stream (the failure count is read).  */
 hsm_status hsm_plan_compute_weights(hsm_plan plan, hsm_prec prec, uint8_t* node_status);
 
 /* Sizes after hsm_plan_build_stencils (host outputs; any may be NULL).

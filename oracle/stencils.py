@@ -11,12 +11,16 @@ nodes".  Readings taken where the paper is silent:
   through integer lattice coordinates round(x/h).  A node is on the lattice
   when every |x_k/h - round(x_k/h)| <= 1e-6; if two nodes share a lattice point
   the lower id owns it.
-* A boundary node's stencil is the node itself plus its n-1 nearest interior
-  (non-boundary) nodes, by the same key.  Boundary stencils serve only the
-  normal-derivative rows of the Neumann conditions; keeping other boundary
-  nodes out of them makes each such row hold exactly after an explicit update
-  (with boundary neighbours the explicit closure couples the walls and its
-  error grows from step to step).
+* A boundary node's stencil is the node itself followed by the n-1 interior
+  (non-boundary) nodes nearest to the point q = x_c - h n_c one lattice
+  spacing inside along the outward normal n_c, ordered by the same key with d2
+  measured from q (q_k = x_ck - (h * n_ck), no fused multiply-add).  Boundary
+  stencils serve only the normal-derivative rows of the Neumann conditions.
+  Keeping other boundary nodes out of them makes each such row hold exactly
+  after an explicit update (with boundary neighbours the explicit closure
+  couples the walls and its error grows from step to step); centring the
+  search inside keeps several node layers in the stencil, without which the
+  monomial part is singular on a 3D lattice wall.
 * A node uses MON only when it is flagged regular, is not a boundary node and
   all 2d lattice neighbours exist; any other regular-flagged node is demoted to
   RBF-FD (Section 2 notes that MON is only stable on regular nodes).
@@ -42,25 +46,77 @@ def sq_dist(coords, c, ids=None):
     return d2
 
 
-def knn_bruteforce(coords, centers, n, candidates=None):
-    """Definition: for each centre, all N distances, order by (d2, id), keep n.
-    With ``candidates`` (bool [N]) only the centre itself and candidate nodes
-    may enter the stencil."""
+def sq_dist_point(coords, q, ids=None):
+    """float64 d2 from the point q [dim] to nodes ``ids``, as ``sq_dist``."""
+    dim = coords.shape[0]
+    if ids is None:
+        ids = slice(None)
+    d2 = None
+    for k in range(dim):
+        dk = coords[k, ids] - q[k]
+        t = dk * dk
+        d2 = t if d2 is None else d2 + t
+    return d2
+
+
+def knn_bruteforce(coords, centers, n):
+    """Definition: for each centre, all N distances, order by (d2, id), keep n."""
     N = coords.shape[1]
     ids = np.arange(N)
     out = np.empty((len(centers), n), dtype=np.int64)
     for r, c in enumerate(centers):
         d2 = sq_dist(coords, int(c))
-        if candidates is not None:
-            allowed = candidates.copy()
-            allowed[int(c)] = True
-            d2 = np.where(allowed, d2, np.inf)
         order = np.lexsort((ids, d2))
         out[r] = order[:n]
     return out
 
 
-def knn_kdtree(coords, centers, n, margin=8, candidates=None):
+def inward_point(coords, normals, h, c):
+    """q = x_c - (h * n_c), evaluated per coordinate without fused multiply-add."""
+    return np.array([coords[k, c] - (h * normals[k, c]) for k in range(coords.shape[0])])
+
+
+def boundary_bruteforce(coords, normals, h, centers, n, interior):
+    """Definition for boundary nodes: [c] + the n-1 interior nodes of smallest
+    (d2 from q, id), q = x_c - h n_c."""
+    N = coords.shape[1]
+    ids = np.arange(N)
+    out = np.empty((len(centers), n), dtype=np.int64)
+    for r, c in enumerate(centers):
+        q = inward_point(coords, normals, h, int(c))
+        d2 = np.where(interior, sq_dist_point(coords, q), np.inf)
+        order = np.lexsort((ids, d2))
+        out[r, 0] = c
+        out[r, 1:] = order[:n - 1]
+    return out
+
+
+def boundary_kdtree(coords, normals, h, centers, n, interior, margin=8):
+    """Same result as ``boundary_bruteforce`` via a k-d tree over the interior
+    nodes, with the completeness guard of ``knn_kdtree``."""
+    from scipy.spatial import cKDTree
+
+    pool = np.flatnonzero(interior)
+    tree = cKDTree(coords.T[pool])
+    out = np.empty((len(centers), n), dtype=np.int64)
+    for r, c in enumerate(centers):
+        q = inward_point(coords, normals, h, int(c))
+        kk = n - 1 + margin
+        while True:
+            kq = min(kk, len(pool))
+            dist, idx = tree.query(q, k=kq)
+            dist, idx = np.atleast_1d(dist), pool[np.atleast_1d(idx)]
+            if kq == len(pool) or dist[-1] > dist[n - 2] * (1.0 + 1e-9) + 1e-300:
+                break
+            kk *= 2
+        d2 = sq_dist_point(coords, q, idx)
+        order = np.lexsort((idx, d2))
+        out[r, 0] = c
+        out[r, 1:] = idx[order[:n - 1]]
+    return out
+
+
+def knn_kdtree(coords, centers, n, margin=8):
     """Same result as ``knn_bruteforce`` for large N.  A k-d tree proposes the
     nearest n+margin candidates; the candidate set is provably complete when the
     last candidate is strictly farther than the n-th (with a relative guard
@@ -68,26 +124,21 @@ def knn_kdtree(coords, centers, n, margin=8, candidates=None):
     order is taken with the exact (d2, id) key."""
     from scipy.spatial import cKDTree
 
-    centers = np.asarray(centers, dtype=np.int64)
-    if candidates is None:
-        pool = np.arange(coords.shape[1])
-    else:
-        pool = np.flatnonzero(candidates)
     pts = coords.T
-    tree = cKDTree(pts[pool])
+    tree = cKDTree(pts)
+    centers = np.asarray(centers, dtype=np.int64)
     out = np.empty((len(centers), n), dtype=np.int64)
     todo = np.arange(len(centers))
-    # the centre itself is always a member; search n nodes among the pool besides it
     kk = n + margin
     while len(todo):
-        kq = min(kk, len(pool))
+        kq = min(kk, coords.shape[1])
         dist, idx = tree.query(pts[centers[todo]], k=kq)
         dist = np.atleast_2d(dist)
-        idx = pool[np.atleast_2d(idx)]
-        complete = (kq == len(pool)) | (dist[:, -1] > dist[:, n - 1] * (1.0 + 1e-9) + 1e-300)
+        idx = np.atleast_2d(idx)
+        complete = (kq == coords.shape[1]) | (dist[:, -1] > dist[:, n - 1] * (1.0 + 1e-9) + 1e-300)
         for r in np.flatnonzero(complete):
             c = int(centers[todo[r]])
-            cand = np.unique(np.r_[c, idx[r]])
+            cand = idx[r]
             d2 = sq_dist(coords, c, cand)
             order = np.lexsort((cand, d2))
             out[todo[r]] = cand[order[:n]]
@@ -144,7 +195,7 @@ def mon_stencils(coords, is_regular, is_boundary, h):
     return np.array(nodes, dtype=np.int64), idx, np.array(demoted, dtype=np.int64)
 
 
-def build_stencils(coords, is_regular, is_boundary, h, n, centers=None, use_kdtree=None):
+def build_stencils(coords, is_regular, is_boundary, h, n, centers=None, use_kdtree=None, normals=None):
     """All stencils of a node set (or of the subset ``centers``).
 
     Returns dict with
@@ -173,6 +224,9 @@ def build_stencils(coords, is_regular, is_boundary, h, n, centers=None, use_kdtr
     if np.any(~on_bnd):
         rbf_idx[~on_bnd] = knn(coords, rbf_nodes[~on_bnd], n)
     if np.any(on_bnd):
-        rbf_idx[on_bnd] = knn(coords, rbf_nodes[on_bnd], n, candidates=np.asarray(is_boundary) == 0)
+        if normals is None:
+            raise ValueError("boundary nodes need their normals")
+        bk = boundary_kdtree if use_kdtree else boundary_bruteforce
+        rbf_idx[on_bnd] = bk(coords, normals, h, rbf_nodes[on_bnd], n, np.asarray(is_boundary) == 0)
     return dict(mon_nodes=mon_nodes, mon_idx=mon_idx, rbf_nodes=rbf_nodes, rbf_idx=rbf_idx,
                 demoted=demoted)

@@ -97,8 +97,8 @@ hsm_status hsm_last_error(hsm_plan plan, char* buf, size_t len) {
 }
 
 hsm_status hsm_plan_create(hsm_plan* out, int dim, int64_t n_nodes, const double* coords, const uint8_t* is_regular,
-                           const uint8_t* is_boundary, double h_regular, int aug_m, int stencil_n, unsigned op_mask,
-                           void* cuda_stream) {
+                           const uint8_t* is_boundary, const double* normals, double h_regular, int aug_m, int stencil_n,
+                           unsigned op_mask, void* cuda_stream) {
   if (!out) return set_error(nullptr, HSM_EINVAL, "out is NULL");
   *out = nullptr;
   if (dim != 2 && dim != 3) return set_error(nullptr, HSM_EINVAL, "dim must be 2 or 3");
@@ -119,6 +119,7 @@ hsm_status hsm_plan_create(hsm_plan* out, int dim, int64_t n_nodes, const double
   p->coords = coords;
   p->is_regular = is_regular;
   p->is_boundary = is_boundary;
+  p->normals = normals;
   p->h = h_regular;
   p->m = aug_m;
   p->n = n;

@@ -52,6 +52,7 @@ struct hsm_plan_s {
   const double* coords = nullptr;
   const uint8_t* is_regular = nullptr;
   const uint8_t* is_boundary = nullptr;
+  const double* normals = nullptr;
   double h = 0.0;
   int m = 2;
   int n = 12;

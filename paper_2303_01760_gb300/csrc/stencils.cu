@@ -9,7 +9,9 @@
 // nodes search among interior nodes only (plus themselves).  The search uses
 // a uniform cell grid (cell edge = lattice spacing), one thread per query,
 // visiting square (cube) shells of cells until no unvisited cell can hold a
-// closer node.
+// closer node.  Boundary nodes keep themselves first and search the n-1
+// interior nodes nearest to x_c - h n_c, so their one-sided stencils reach
+// several node layers.
 #include <cfloat>
 
 #include "common.cuh"
@@ -200,25 +202,29 @@ __device__ __forceinline__ double sq_dist(const double* a, const double* b) {
 // [n][blockDim] structure-of-arrays (bank-conflict free).
 template <int DIM>
 __global__ void k_knn(const double* __restrict__ coords, int64_t N, const uint8_t* __restrict__ is_boundary,
-                      const int32_t* __restrict__ queries, int64_t nq, int n, CellGrid cg,
+                      const double* __restrict__ normals, double h, const int32_t* __restrict__ queries,
+                      int64_t nq, int n_full, CellGrid cg,
                       const int32_t* __restrict__ start, const int32_t* __restrict__ sorted_id,
                       const double* __restrict__ sorted_xyz, const uint8_t* __restrict__ sorted_bnd,
                       int32_t* __restrict__ out_idx, unsigned* flags) {
   extern __shared__ unsigned char smem_raw[];
   const int B = blockDim.x;
   double* kd = reinterpret_cast<double*>(smem_raw);
-  int32_t* ki = reinterpret_cast<int32_t*>(kd + (size_t)n * B);
+  int32_t* ki = reinterpret_cast<int32_t*>(kd + (size_t)n_full * B);
   const int t = threadIdx.x;
   for (int64_t qi = blockIdx.x * (int64_t)B + t; qi < nq; qi += (int64_t)gridDim.x * B) {
     const int32_t c = queries[qi];
+    const bool bnd_center = is_boundary && is_boundary[c];
+    // boundary nodes: search the n-1 interior nodes nearest to x_c - h n_c
+    const int n = bnd_center ? n_full - 1 : n_full;
     double q[DIM];
     int cq[DIM];
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
       q[k] = coords[k * N + c];
+      if (bnd_center && normals) q[k] = __dsub_rn(q[k], __dmul_rn(h, normals[k * N + c]));
       cq[k] = cg.cell_of(q[k], k);
     }
-    const bool bnd_center = is_boundary && is_boundary[c];
     int cnt = 0;
     for (int r = 0;; ++r) {
       // visit the shell of cells at Chebyshev distance r
@@ -249,7 +255,7 @@ __global__ void k_knn(const double* __restrict__ coords, int64_t N, const uint8_
             const int32_t s0 = start[l], s1 = start[l + 1];
             for (int32_t s = s0; s < s1; ++s) {
               const int32_t id = sorted_id[s];
-              if (bnd_center && id != c && sorted_bnd[s]) continue;
+              if (bnd_center && sorted_bnd[s]) continue;
               const double d2 = sq_dist<DIM>(sorted_xyz + (int64_t)s * kMaxDim, q);
               if (cnt == n && !key_less(d2, id, kd[(n - 1) * B + t], ki[(n - 1) * B + t])) continue;
               int j = (cnt < n) ? cnt++ : n - 1;
@@ -278,7 +284,9 @@ __global__ void k_knn(const double* __restrict__ coords, int64_t N, const uint8_
       }
     }
     if (cnt < n) atomicOr(flags, kDevKnnShort);
-    for (int j = 0; j < n; ++j) out_idx[(int64_t)j * nq + qi] = j < cnt ? ki[j * B + t] : c;
+    const int off = bnd_center ? 1 : 0;
+    if (bnd_center) out_idx[qi] = c;
+    for (int j = 0; j < n; ++j) out_idx[(int64_t)(j + off) * nq + qi] = j < cnt ? ki[j * B + t] : c;
   }
 }
 
@@ -415,11 +423,11 @@ hsm_status build_stencils(hsm_plan p) {
     int gk = (int)std::min<int64_t>(ceil_div(p->rbf.count, KT), (int64_t)num_sms() * 16);
     if (dim == 2) {
       if (smem > 48 * 1024) HSM_CUDA(p, cudaFuncSetAttribute(k_knn<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k_knn<2><<<gk, KT, smem, s>>>(p->coords, N, p->is_boundary, list_rbf, p->rbf.count, p->n, cg, cstart,
+      k_knn<2><<<gk, KT, smem, s>>>(p->coords, N, p->is_boundary, p->normals, p->h, list_rbf, p->rbf.count, p->n, cg, cstart,
                                      sorted_id, sorted_xyz, sorted_bnd, p->rbf.idx, p->dev_flags);
     } else {
       if (smem > 48 * 1024) HSM_CUDA(p, cudaFuncSetAttribute(k_knn<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k_knn<3><<<gk, KT, smem, s>>>(p->coords, N, p->is_boundary, list_rbf, p->rbf.count, p->n, cg, cstart,
+      k_knn<3><<<gk, KT, smem, s>>>(p->coords, N, p->is_boundary, p->normals, p->h, list_rbf, p->rbf.count, p->n, cg, cstart,
                                      sorted_id, sorted_xyz, sorted_bnd, p->rbf.idx, p->dev_flags);
     }
     HSM_CUDA(p, cudaGetLastError());

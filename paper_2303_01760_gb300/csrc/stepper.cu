@@ -17,7 +17,9 @@
 // group first, then the RBF-FD group), one thread per node.  A BiCGSTAB
 // iteration is three kernels; each forms the vector it needs on the fly
 // inside its gathers (p = r + beta(p - omega v), s = r - alpha v), applies the
-// bordered operator, and reduces its dot products with a last-block-done
+// bordered operator right-preconditioned by its diagonal (Jacobi; the
+// Laplacian rows scale as 1/h^2 and the wall rows as 1/h, and the unscaled
+// iteration stagnates), and reduces its dot products with a last-block-done
 // pattern (block partials in fixed order, no spinning), whose final block also
 // updates the scalars and the convergence flag.  Once the flag is set the
 // remaining kernels of a launched chunk return at once.
@@ -34,6 +36,7 @@ struct hsm_stepper_s {
   int slot_lap = 0;
   double* wp_rbf = nullptr;   // [n][rbf_count] pressure-row weights (lap inside, n.grad on walls)
   double* wn_rbf = nullptr;   // [n][rbf_count] normal-derivative weights (walls only)
+  double* minv = nullptr;     // [N+1] inverse diagonal of the bordered operator (1 for the border)
   double* vstar = nullptr;    // [dim][N]
   double* Tn = nullptr;       // [N]
   double* vec = nullptr;      // Krylov vectors, each N+1: r, rhat, p0, p1, v0, v1, s, t, rhs
@@ -83,6 +86,7 @@ struct StepArgs {
   double* vstar;
   double* Tn;
   double* vec;
+  const double* minv;
   KS* ks;
   double* partial;
   unsigned* counters;
@@ -286,13 +290,13 @@ __global__ void k_bicg_a(StepArgs a) {
     for (int e = 0; e < W; ++e) {
       const int32_t id = a.idx[g][(int64_t)e * G + pos];
       const double pj = r[id] + beta * (po[id] - omega * vo[id]);
-      y = fma(wpg[(int64_t)e * G + pos], pj, y);
+      y = fma(wpg[(int64_t)e * G + pos], pj * a.minv[id], y);
     }
     y += pnN;
     const double pi = r[i] + beta * (po[i] - omega * vo[i]);
     pn[i] = pi;
     vn[i] = y;
-    part[0] += pi;
+    part[0] += a.minv[i] * pi;
     part[1] += rh[i] * y;
   }
   double tot[2];
@@ -336,13 +340,13 @@ __global__ void k_bicg_b(StepArgs a) {
     const double* wpg = a.wp[g];
     for (int e = 0; e < W; ++e) {
       const int32_t id = a.idx[g][(int64_t)e * G + pos];
-      y = fma(wpg[(int64_t)e * G + pos], r[id] - alpha * v[id], y);
+      y = fma(wpg[(int64_t)e * G + pos], (r[id] - alpha * v[id]) * a.minv[id], y);
     }
     y += sN;
     const double si = r[i] - alpha * v[i];
     s[i] = si;
     t[i] = y;
-    part[0] += si;
+    part[0] += a.minv[i] * si;
     part[1] += y * si;
     part[2] += y * y;
     part[3] += si * si;
@@ -386,7 +390,7 @@ __global__ void k_bicg_c(StepArgs a) {
   double part[2] = {0.0, 0.0};
   for (; pos < G; pos += stride) {
     const int32_t i = a.nodes[g][pos];
-    a.p[i] += alpha * pc[i] + omega * s[i];
+    a.p[i] += a.minv[i] * (alpha * pc[i] + omega * s[i]);
     const double ri = s[i] - omega * t[i];
     r[i] = ri;
     part[0] += rh[i] * ri;
@@ -497,6 +501,21 @@ __global__ void k_wall_weights(const int32_t* __restrict__ nodes, int64_t G, int
   }
 }
 
+// Jacobi preconditioner: inverse of the centre weight of every pressure row
+// (the centre is the first stencil entry of both groups).
+__global__ void k_minv(StepArgs a) {
+  int g;
+  int64_t pos, stride;
+  node_of(a, g, pos, stride);
+  const int64_t G = a.count[g];
+  double* minv = const_cast<double*>(a.minv);
+  for (; pos < G; pos += stride) {
+    const double d = a.wp[g][pos];
+    minv[a.nodes[g][pos]] = (d != 0.0 && isfinite(d)) ? 1.0 / d : 1.0;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) minv[a.N] = 1.0;
+}
+
 StepArgs make_args(hsm_stepper st, double* v, double* T, double* p) {
   hsm_plan pl = st->plan;
   StepArgs a{};
@@ -531,6 +550,7 @@ StepArgs make_args(hsm_stepper st, double* v, double* T, double* p) {
   a.vstar = st->vstar;
   a.Tn = st->Tn;
   a.vec = st->vec;
+  a.minv = st->minv;
   a.ks = reinterpret_cast<KS*>(st->scal);
   a.partial = st->partial;
   a.counters = st->counters;
@@ -607,7 +627,7 @@ hsm_status hsm_stepper_create(hsm_stepper* out, hsm_plan pl, const hsm_phys* phy
   };
   const int64_t N = pl->N, G = pl->rbf.count, W = pl->rbf.width;
   if (dev_alloc(&st->wp_rbf, W * G, s) || dev_alloc(&st->wn_rbf, W * G, s) ||
-      dev_alloc(&st->vstar, (size_t)pl->dim * N, s) || dev_alloc(&st->Tn, N, s) ||
+      dev_alloc(&st->vstar, (size_t)pl->dim * N, s) || dev_alloc(&st->Tn, N, s) || dev_alloc(&st->minv, N + 1, s) ||
       dev_alloc(&st->vec, (size_t)V_COUNT * (N + 1), s) || dev_alloc(&st->scal, 16, s))
     return fail(set_error(pl, HSM_ENOMEM, "stepper allocation failed"));
   const int T = st->threads;
@@ -641,6 +661,10 @@ hsm_status hsm_stepper_create(hsm_stepper* out, hsm_plan pl, const hsm_phys* phy
                                              st->slot_d[2], st->slot_lap, phys->bc, phys->normals, N, st->wp_rbf,
                                              st->wn_rbf);
   }
+  {
+    StepArgs a = make_args(st, nullptr, nullptr, nullptr);
+    k_minv<<<st->blocks_mon + st->blocks_rbf, st->threads, 0, s>>>(a);
+  }
   cudaError_t e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return fail(cuda_fail(pl, e, "hsm_stepper_create"));
   *out = st;
@@ -663,6 +687,7 @@ hsm_status hsm_stepper_destroy(hsm_stepper st) {
   cudaStream_t s = st->plan ? st->plan->stream : nullptr;
   dev_free(&st->wp_rbf, s);
   dev_free(&st->wn_rbf, s);
+  dev_free(&st->minv, s);
   dev_free(&st->vstar, s);
   dev_free(&st->Tn, s);
   dev_free(&st->vec, s);

@@ -178,6 +178,17 @@ struct AbsBits<float> {
   }
 };
 
+template <typename T>
+struct PivTol;
+template <>
+struct PivTol<double> {
+  static constexpr double value = 1e-12;
+};
+template <>
+struct PivTol<float> {
+  static constexpr double value = 0.0;
+};
+
 __device__ __forceinline__ unsigned long long shfl_xor_u64(unsigned mask, unsigned long long v, int o, int w) {
   return (unsigned long long)__shfl_xor_sync(mask, (long long)v, o, w);
 }
@@ -342,7 +353,9 @@ __device__ __forceinline__ bool lu_solve(T* Mt, int ldt, int K, T* inv, int lane
       }
       __syncwarp(mask);
       const T piv = Mt[k * ldt + k];
-      if (!(piv != T(0)) || !isfinite((double)piv)) {
+      // the scaled system has entries of order one: a pivot below the
+      // threshold means the system is singular to working precision
+      if (!(fabs((double)piv) > PivTol<T>::value) || !isfinite((double)piv)) {
         ok = false;
         break;
       }

@@ -41,8 +41,8 @@ class hsm_phys(C.Structure):
 _SIGS = {
     "hsm_status_string": (C.c_char_p, [C.c_int]),
     "hsm_last_error": (C.c_int, [_p, C.c_char_p, C.c_size_t]),
-    "hsm_plan_create": (C.c_int, [C.POINTER(_p), C.c_int, _i64, _p, _p, _p, C.c_double, C.c_int, C.c_int,
-                                  C.c_uint, _p]),
+    "hsm_plan_create": (C.c_int, [C.POINTER(_p), C.c_int, _i64, _p, _p, _p, _p, C.c_double, C.c_int,
+                                  C.c_int, C.c_uint, _p]),
     "hsm_plan_build_stencils": (C.c_int, [_p]),
     "hsm_plan_compute_weights": (C.c_int, [_p, C.c_int, _p]),
     "hsm_plan_query": (C.c_int, [_p, C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_i64)]),
@@ -108,17 +108,18 @@ def op_list(mask, dim):
 
 class Plan:
     """Owns an hsm_plan.  ``coords`` (f64 [dim, N]), ``is_regular`` and
-    ``is_boundary`` (u8 [N]) are CUDA tensors that must outlive the plan."""
+    ``is_boundary`` (u8 [N]) and ``normals`` (f64 [dim, N]) are CUDA tensors
+    that must outlive the plan."""
 
-    def __init__(self, coords, is_regular, is_boundary, h, m=2, n=0, op_mask=None, stream=None):
+    def __init__(self, coords, is_regular, is_boundary, h, m=2, n=0, op_mask=None, stream=None, normals=None):
         dim, N = coords.shape
         if op_mask is None:
             op_mask = HSM_DX | HSM_DY | HSM_LAP | (HSM_DZ if dim == 3 else 0)
         self.dim, self.N, self.op_mask = dim, N, op_mask
-        self._keep = (coords, is_regular, is_boundary)
+        self._keep = (coords, is_regular, is_boundary, normals)
         h_ = C.c_void_p()
         check(lib.hsm_plan_create(C.byref(h_), dim, N, ptr(coords), ptr(is_regular), ptr(is_boundary),
-                                  float(h), int(m), int(n), int(op_mask), stream_handle(stream)))
+                                  ptr(normals), float(h), int(m), int(n), int(op_mask), stream_handle(stream)))
         self.h = h_
 
     def build_stencils(self):

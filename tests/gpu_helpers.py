@@ -21,7 +21,8 @@ def make_plan(ns, m=2, n=0, op_mask=None, prec=0, node_status=False):
     from paper_2303_01760_gb300 import hsm
 
     dv = to_dev(ns)
-    plan = hsm.Plan(dv["coords"], dv["is_regular"], dv["is_boundary"], ns.h, m=m, n=n, op_mask=op_mask)
+    plan = hsm.Plan(dv["coords"], dv["is_regular"], dv["is_boundary"], ns.h, m=m, n=n, op_mask=op_mask,
+                    normals=dv["normals"])
     plan.build_stencils()
     st = torch.full((ns.N,), 77, dtype=torch.uint8, device="cuda:0") if node_status else None
     code = plan.compute_weights(prec, st, allow_singular=True)

@@ -48,12 +48,12 @@ def test_argument_errors_need_no_device():
     fake = ctypes.c_void_p(16)
     f = lib.hsm_plan_create
     f.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int64, ctypes.c_void_p,
-                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int,
-                  ctypes.c_uint, ctypes.c_void_p]
-    assert f(ctypes.byref(h), 4, 10, fake, fake, None, 0.1, 2, 0, 11, None) == 1
-    assert f(ctypes.byref(h), 2, 10, fake, fake, None, -1.0, 2, 0, 11, None) == 1
-    assert f(ctypes.byref(h), 2, 10, fake, fake, None, 0.1, 2, 6, 11, None) == 1   # n <= C(4,2)
-    assert f(ctypes.byref(h), 2, 10, fake, fake, None, 0.1, 2, 0, 4, None) == 1    # dz in 2D
-    assert f(ctypes.byref(h), 2, 10, fake, fake, None, 0.1, 2, 0, 11, None) == 0
+                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_int,
+                  ctypes.c_int, ctypes.c_uint, ctypes.c_void_p]
+    assert f(ctypes.byref(h), 4, 10, fake, fake, None, None, 0.1, 2, 0, 11, None) == 1
+    assert f(ctypes.byref(h), 2, 10, fake, fake, None, None, -1.0, 2, 0, 11, None) == 1
+    assert f(ctypes.byref(h), 2, 10, fake, fake, None, None, 0.1, 2, 6, 11, None) == 1   # n <= C(4,2)
+    assert f(ctypes.byref(h), 2, 10, fake, fake, None, None, 0.1, 2, 0, 4, None) == 1    # dz in 2D
+    assert f(ctypes.byref(h), 2, 10, fake, fake, None, None, 0.1, 2, 0, 11, None) == 0
     lib.hsm_plan_destroy.argtypes = [ctypes.c_void_p]
     assert lib.hsm_plan_destroy(h) == 0

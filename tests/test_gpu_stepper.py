@@ -1,0 +1,77 @@
+"""CUDA Boussinesq stepper (Section 3) vs the FP64 oracle stepper."""
+import numpy as np
+import pytest
+
+from oracle import stencils as ost
+from oracle import stepper as ostep
+from oracle import weights as ow
+from paper_2303_01760_gb300 import nodesets
+
+from gpu_helpers import make_plan
+
+pytestmark = pytest.mark.gpu
+
+KRYLOV_TOL = 1e-12
+
+
+def _run_both(ns, Ra, Pr, steps, T0=None, m=2):
+    import torch
+    from paper_2303_01760_gb300 import hsm
+
+    n = ow.stencil_size(ns.dim, m)
+    st = ost.build_stencils(ns.coords, ns.is_regular, ns.is_boundary, ns.h, n, normals=ns.normals)
+    W = ow.all_weights(ns.coords, st, m)
+    dt = ostep.dt_rule(ns.h)
+    S = ostep.Stepper(ns.coords, ns.bc, ns.T_bc, ns.normals, ns.T_ref, st, W, Ra, Pr, dt)
+    v0, Ti = ostep.initial_state(ns.dim, ns.N, ns.bc, ns.T_bc)
+    if T0 is not None:
+        Ti = T0.copy()
+    vo, To, po = S.run(v0.copy(), Ti.copy(), steps)
+    plan, code, _ = make_plan(ns, m=m)
+    assert code == 0
+    dv = plan._dev
+    stp = hsm.Stepper(plan, Ra, Pr, dt, ns.T_ref, dv["bc"], dv["T_bc"], dv["normals"],
+                      krylov_tol=KRYLOV_TOL, krylov_max_it=20000)
+    v = torch.from_numpy(v0.copy()).cuda()
+    T = torch.from_numpy(Ti.copy()).cuda()
+    p = torch.zeros(ns.N, dtype=torch.float64, device="cuda:0")
+    iters, _ = stp.step(v, T, p, steps)
+    out = dict(v=v.cpu().numpy(), T=T.cpu().numpy(), p=p.cpu().numpy(), iters=iters)
+    stp.close()
+    plan.close()
+    return out, dict(v=vo, T=To, p=po)
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def test_hybrid_square_100_steps_matches_oracle():
+    """The hybrid unit-square set (lattice h=1/40 inside, scattered band along
+    the walls), Ra=1e4, Pr=0.71, dt = 0.1 h^2/2, 100 steps: temperature and
+    velocity against the oracle (exact pressure solve).  The pressure is
+    solved to a relative residual of 1e-12, which bounds the field error."""
+    ns = nodesets.square_wall_band(n=40)
+    g, o = _run_both(ns, 1e4, 0.71, 100)
+    eT, ev = _rel(g["T"], o["T"]), _rel(g["v"], o["v"])
+    print(f"T rel err {eT:.3e}  v rel err {ev:.3e}  iters/step {np.mean(g['iters']):.1f}")
+    assert eT <= 1e-9
+    assert ev <= 1e-7
+
+
+def test_linear_conduction_fixed_point_gpu():
+    ns = nodesets.square_wall_band(n=20)
+    T0 = ns.coords[0] - 0.5
+    g, o = _run_both(ns, 0.0, 0.71, 30, T0=T0)
+    assert np.abs(g["T"] - T0).max() <= 1e-12
+    assert np.abs(g["v"]).max() <= 1e-12
+
+
+def test_irregular_domain_steps_match_oracle():
+    """Unit square minus circular holes with Dirichlet hole temperatures and
+    insulated box walls (Section 4.2 set-up), coarse lattice, 20 steps."""
+    ns = nodesets.square_holes(n=60, n_holes=3, r_range=(0.08, 0.12), band=0.08,
+                               seed=nodesets.SEED_BASE + 31)
+    g, o = _run_both(ns, 1e5, 0.71, 20)
+    assert _rel(g["T"], o["T"]) <= 1e-9
+    assert _rel(g["v"], o["v"]) <= 1e-7

@@ -26,18 +26,38 @@ def _rel(a, b):
     return np.abs(a - b).max(1) / np.abs(b).max(1)
 
 
-def _check_plan(ns, m, prec=0, centers=None, tol=TOL_FP64, apply_check=True):
+def _oracle_cond(ns, st, m):
+    xi, _ = ow._scaled_offsets(ns.coords, st["rbf_idx"])
+    M, _ = ow.rbffd_system(xi, m, ow.ops_for(ns.dim))
+    return np.linalg.cond(M)
+
+
+def _check_plan(ns, m, prec=0, centers=None, tol=TOL_FP64, apply_check=True, singular_ok=False):
     import torch
 
     dim = ns.dim
     n = ow.stencil_size(dim, m)
     ops = ow.ops_for(dim)
     plan, code, status = make_plan(ns, m=m, prec=prec, node_status=True)
-    assert code == 0
-    st = ost.build_stencils(ns.coords, ns.is_regular, ns.is_boundary, ns.h, n, centers=centers)
+    st = ost.build_stencils(ns.coords, ns.is_regular, ns.is_boundary, ns.h, n, centers=centers,
+                            normals=ns.normals)
+    if singular_ok:
+        # nodes whose system is singular to working precision must be flagged
+        # (status 255, zero weights); well-conditioned ones must not be
+        cond = _oracle_cond(ns, st, m)
+        flagged = status.cpu().numpy()[st["rbf_nodes"]] == 255
+        assert np.all(flagged[cond > 1e14])
+        assert np.all(cond[flagged] > 1e8)
+        assert code == (4 if flagged.any() else 0)
+        keep = ~flagged
+        st = dict(st, rbf_nodes=st["rbf_nodes"][keep], rbf_idx=st["rbf_idx"][keep])
+        st["demoted"] = np.intersect1d(st["demoted"], np.r_[st["mon_nodes"], st["rbf_nodes"]])
+        centers = np.r_[st["mon_nodes"], st["rbf_nodes"]] if flagged.any() else centers
+    else:
+        assert code == 0
     W = ow.all_weights(ns.coords, st, m)
     q = plan.query()
-    if centers is None:
+    if centers is None and not singular_ok:
         assert q["n_mon"] == len(st["mon_nodes"])
         assert q["n_demoted"] == len(st["demoted"])
     status = status.cpu().numpy()
@@ -94,9 +114,13 @@ def test_all_regular_and_all_scattered():
 
 
 def test_cube_spheres_small_m2_m3():
+    """3D: unit cube minus 2 spheres, m=2 (n=20) and m=3 (n=40).  With m=3 the
+    wall nodes next to a box edge have one-sided stencils that span only three
+    lattice layers across the edge, so the cubic monomials are not unisolvent
+    there; those nodes are reported singular and excluded."""
     ns = nodesets.cube_spheres(n=14, n_holes=2, r_range=(0.1, 0.15), band=0.12, seed=nodesets.SEED_BASE + 21)
     _check_plan(ns, m=2)
-    _check_plan(ns, m=3)
+    _check_plan(ns, m=3, singular_ok=True)
 
 
 def test_fp32_refinement_within_tolerance():
@@ -108,7 +132,7 @@ def test_fp32_refinement_within_tolerance():
 def test_fp32_refinement_m4_and_3d():
     _check_plan(nodesets.square_wall_band(n=30, seed=nodesets.SEED_BASE + 11), m=4, prec=1, tol=TOL_FP32R)
     ns = nodesets.cube_spheres(n=14, n_holes=2, r_range=(0.1, 0.15), band=0.12, seed=nodesets.SEED_BASE + 21)
-    _check_plan(ns, m=3, prec=1, tol=TOL_FP32R)
+    _check_plan(ns, m=3, prec=1, tol=TOL_FP32R, singular_ok=True)
 
 
 def test_irregular_250k_sampled():

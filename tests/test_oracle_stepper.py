@@ -14,7 +14,8 @@ PAPER = json.load(open(os.path.join(GOLD, "paper_values.json")))
 
 
 def _setup(ns, Ra, Pr, dt=None, m=2):
-    st = ost.build_stencils(ns.coords, ns.is_regular, ns.is_boundary, ns.h, ow.stencil_size(ns.dim, m))
+    st = ost.build_stencils(ns.coords, ns.is_regular, ns.is_boundary, ns.h, ow.stencil_size(ns.dim, m),
+                            normals=ns.normals)
     W = ow.all_weights(ns.coords, st, m)
     dt = ostep.dt_rule(ns.h) if dt is None else dt
     return ostep.Stepper(ns.coords, ns.bc, ns.T_bc, ns.normals, ns.T_ref, st, W, Ra, Pr, dt)

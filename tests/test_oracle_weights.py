@@ -191,7 +191,7 @@ def _conv_errors(kind, ns_list, m=2):
     hs = []
     for ns in ns_list:
         st = ost.build_stencils(ns.coords, ns.is_regular, ns.is_boundary, ns.h,
-                                ow.stencil_size(2, m))
+                                ow.stencil_size(2, m), normals=ns.normals)
         W = ow.all_weights(ns.coords, st, m)
         u, der = nodesets.field_sincos(ns.coords)
         out = oap.apply_all(ns.N, st, W, u, ("dx", "dy", "lap"))
