@@ -1,0 +1,429 @@
+"""Benchmark of the hybrid scattered-regular operators on one GB300.
+
+Metric: hybrid operator nodes/s (weights + apply) on the 2D irregular
+workload (unit square minus 8 seeded circular holes, lattice h = 0.002,
+scattered nodes within 0.05 of a hole, PHS r^3 + monomials m = 2, n = 12,
+FP64 weights, operators d/dx, d/dy and the Laplacian).  One step is one pass
+of the operator path on that node set: stencil build (lattice + kNN), MON and
+RBF-FD weight solves, and one fused application of all operators to
+u = sin(pi x) cos(pi y); value = nodes / step time.  The same node set with
+every node forced to RBF-FD is timed beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the CPU oracle (test infrastructure; plain FP64
+numpy/scipy) on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "hybrid operator nodes/s (weights+apply) vs all-RBF-FD, same GPU, at L-inf tol"
+UNIT = "nodes/s"
+FP64_PEAK_DERIVED = 152 * 2 * 2 * 2070e6  # SMs x FP64 FMA/clk/SM x 2 flop x max SM clock
+L2_FLUSH_BYTES = 512 << 20
+
+
+def workload_desc(ns):
+    return {
+        "workload": "2D irregular domain: unit square minus 8 seeded circular holes (r 0.03-0.08), "
+                    "lattice h=0.002, scattered within 0.05 of a hole, PHS r^3 + monomials m=2 (n=12), "
+                    "FP64 weights, ops dx,dy,lap",
+        "nodes": int(ns.N),
+        "scattered_fraction": round(ns.n_scattered / ns.N, 4),
+        "l2": "flushed (512 MiB write) before every timed step",
+        "seed": 20230302,
+    }
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+def rbf_flops(K, nops):
+    """Algorithmic FP64 flops of one RBF-FD system: LU 2/3 K^3 plus forward and
+    back substitution 2 K^2 per right-hand side."""
+    return 2.0 / 3.0 * K ** 3 + 2.0 * nops * K ** 2
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev_index=0):
+        self.dev = dev_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        except Exception:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        import statistics
+
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        try:
+            os.remove(self.path)
+        except Exception:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def cpu_sample_run(n_sample, seed=7):
+    """The oracle (as it stands) on a bounded sample of the workload: stencils,
+    weights and one application for ``n_sample`` randomly chosen nodes.
+    Returns (seconds, nodes)."""
+    import numpy as np
+
+    from oracle import apply as oap
+    from oracle import stencils as ost
+    from oracle import weights as ow
+    from paper_2303_01760_gb300 import nodesets
+
+    ns = nodesets.cached(nodesets.square_holes)
+    rng = np.random.default_rng(seed)
+    centers = np.sort(rng.choice(ns.N, n_sample, replace=False))
+    u, _ = nodesets.field_sincos(ns.coords)
+    t0 = time.perf_counter()
+    st = ost.build_stencils(ns.coords, ns.is_regular, ns.is_boundary, ns.h, 12, centers=centers,
+                            use_kdtree=True, normals=ns.normals)
+    W = ow.all_weights(ns.coords, st, 2)
+    for op in ("dx", "dy", "lap"):
+        oap.apply_group(st["mon_idx"], W["mon"][op], u)
+        oap.apply_group(st["rbf_idx"], W["rbf"][op], u)
+    return time.perf_counter() - t0, n_sample
+
+
+def cpu_baseline(n_sample=20000):
+    """Runs the oracle sample in a fresh single-threaded process."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+            "t, n = bench.cpu_sample_run(%d); print(json.dumps([t, n]))" % (ROOT, n_sample))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": r.stderr[-500:]}
+    t, n = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": n / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} random nodes of the workload (their stencils by k-d tree, MON/RBF-FD weights by "
+                      f"numpy batched solve, one application of dx,dy,lap); {t:.1f} s single-threaded",
+            "seconds": t}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2303_01760_gb300 import hsm, nodesets
+
+    dev = torch.device("cuda", local)
+    # every rank runs its own replica of the workload (independent node sets)
+    ns = nodesets.cached(nodesets.square_holes) if rank == 0 else \
+        nodesets.cached(nodesets.square_holes, seed=nodesets.SEED_BASE + 1 + 100 * rank)
+    d = dict(coords=torch.from_numpy(ns.coords).to(dev), reg=torch.from_numpy(ns.is_regular).to(dev),
+             bnd=torch.from_numpy(ns.is_boundary).to(dev), nrm=torch.from_numpy(ns.normals).to(dev))
+    d["reg0"] = torch.zeros_like(d["reg"])
+    u_np, _ = nodesets.field_sincos(ns.coords)
+    u = torch.from_numpy(u_np).to(dev)
+    out = torch.empty((3, ns.N), dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def make(reg):
+        p = hsm.Plan(d["coords"], reg, d["bnd"], ns.h, m=2, normals=d["nrm"], stream=stream)
+        p.set_timing(True)
+        return p
+
+    def one_step(plan):
+        plan.build_stencils()
+        plan.compute_weights(hsm.HSM_PREC_FP64)
+        plan.apply(u, out=out)
+
+    def timed(plan, K, W):
+        for _ in range(W):
+            one_step(plan)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        evs = []
+        phases = []
+        launches0 = plan.profile()[1]
+        for _ in range(K):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            one_step(plan)
+            b.record(stream)
+            evs.append((a, b))
+            phases.append(plan.profile()[0])
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        ms = [a.elapsed_time(b) for a, b in evs]
+        launches = plan.profile()[1] - launches0
+        return ms, phases, launches
+
+    hyb = make(d["reg"])
+    allr = make(d["reg0"])
+    # correctness gate of this exact launch configuration: sampled nodes vs the oracle
+    hyb.build_stencils()
+    hyb.compute_weights(hsm.HSM_PREC_FP64)
+    gate = None
+    if rank == 0:
+        gate = parity_gate(ns, hyb, u, u_np)
+    with Clocks(local) as clk:
+        ms_h, ph_h, launches_h = timed(hyb, args.steps, args.warmup)
+        ms_a, ph_a, launches_a = timed(allr, args.steps, args.warmup)
+    clocks = clk.summary()
+    q_h, q_a = hyb.query(), allr.query()
+    t_h = float(np.mean(ms_h))
+    t_a = float(np.mean(ms_a))
+    if world > 1:
+        t = torch.tensor([t_h, t_a], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_h, t_a = float(t[0]), float(t[1])
+
+    # roofline of the dominant kernel: the FP64 RBF-FD weight solve
+    K = 12 + 6
+    rbf_ms = float(np.mean([p[2] for p in ph_h]))
+    rbf_ms_all = float(np.mean([p[2] for p in ph_a]))
+    n_rbf_h = ns.N - q_h["n_mon"]
+    n_rbf_a = ns.N - q_a["n_mon"]
+    ach_h = rbf_flops(K, 3) * n_rbf_h / (rbf_ms * 1e-3) / 1e9
+    ach_a = rbf_flops(K, 3) * n_rbf_a / (rbf_ms_all * 1e-3) / 1e9
+    peak = FP64_PEAK_DERIVED / 1e9
+
+    # end to end through the C ABI from pinned host buffers
+    e2e = run_e2e(ns, hsm, dev, stream, args)
+
+    res = None
+    if rank == 0:
+        value = world * ns.N / (t_h * 1e-3)
+        res = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_h, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded node sets; no paper geometry)",
+            "config": workload_desc(ns),
+            "e2e": e2e,
+            "gpu_launches": int(launches_h // max(args.steps, 1)) * args.steps,
+            "roofline": {"bound": "alu", "kernel": "k_rbf_fp64 (RBF-FD FP64 LU solve, hybrid set)",
+                         "achieved": ach_h, "peak": peak, "unit": "GFLOP/s", "frac": ach_h / peak,
+                         "traffic": None,
+                         "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz"},
+            "all_rbffd": {"value": world * ns.N / (t_a * 1e-3), "ms_per_step": t_a,
+                          "hybrid_over_all_rbffd": t_a / t_h,
+                          "roofline_frac_rbf_kernel": ach_a / peak,
+                          "rbf_kernel_gflops": ach_a},
+            "phases_ms": {"hybrid": dict(zip(["stencils", "mon_weights", "rbf_weights", "apply"],
+                                             np.mean(ph_h, 0).round(4).tolist())),
+                          "all_rbffd": dict(zip(["stencils", "mon_weights", "rbf_weights", "apply"],
+                                                np.mean(ph_a, 0).round(4).tolist()))},
+            "counts": {"mon": q_h["n_mon"], "rbf": n_rbf_h, "demoted": q_h["n_demoted"]},
+            "parity": gate,
+            "clocks": clocks,
+        }
+    hyb.close()
+    allr.close()
+    if rank == 0:
+        res["cpu_baseline"] = cpu_baseline(args.cpu_sample) if world == 1 else None
+        print(json.dumps(res))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def parity_gate(ns, plan, u, u_np, n_sample=2000):
+    """Sampled nodes of the timed plan against the oracle (weights 1e-10
+    relative per stencil, apply 1e-9 of sum |w u|)."""
+    import numpy as np
+
+    from oracle import apply as oap
+    from oracle import stencils as ost
+    from oracle import weights as ow
+
+    rng = np.random.default_rng(99)
+    centers = np.sort(rng.choice(ns.N, n_sample, replace=False))
+    st = ost.build_stencils(ns.coords, ns.is_regular, ns.is_boundary, ns.h, 12, centers=centers,
+                            use_kdtree=True, normals=ns.normals)
+    W = ow.all_weights(ns.coords, st, 2)
+    out = plan.apply(u).cpu().numpy()
+    worst_w = 0.0
+    worst_a = 0.0
+    for k, op in enumerate(("dx", "dy", "lap")):
+        rp, col, val = [t.cpu().numpy() for t in plan.export_csr(1 << (k if k < 2 else 3))]
+        for grp, width in (("mon", 5), ("rbf", 12)):
+            nodes = st[grp + "_nodes"]
+            if not len(nodes):
+                continue
+            ix = rp[nodes][:, None] + np.arange(width)[None, :]
+            if not np.array_equal(col[ix], st[grp + "_idx"]):
+                return {"ok": False, "why": f"{grp} stencils differ"}
+            e = np.abs(val[ix] - W[grp][op]).max(1) / np.abs(W[grp][op]).max(1)
+            worst_w = max(worst_w, float(e.max()))
+            ref = oap.apply_group(st[grp + "_idx"], W[grp][op], u_np)
+            sc = (np.abs(W[grp][op]) * np.abs(u_np[st[grp + "_idx"]])).sum(1)
+            worst_a = max(worst_a, float((np.abs(out[k, nodes] - ref) / sc).max()))
+    return {"ok": worst_w <= 1e-10 and worst_a <= 1e-9, "sampled_nodes": n_sample,
+            "max_rel_weight_err": worst_w, "max_rel_apply_err": worst_a}
+
+
+def run_e2e(ns, hsm, dev, stream, args):
+    """Same metric end to end: pinned host inputs copied in, stencils +
+    weights + apply, the three operator outputs copied back, every step."""
+    import numpy as np
+    import torch
+
+    h = dict(coords=torch.from_numpy(ns.coords).pin_memory(), reg=torch.from_numpy(ns.is_regular).pin_memory(),
+             bnd=torch.from_numpy(ns.is_boundary).pin_memory(), nrm=torch.from_numpy(ns.normals).pin_memory())
+    u_h = torch.from_numpy(nodesets_u(ns)).pin_memory()
+    out_h = torch.empty((3, ns.N), dtype=torch.float64).pin_memory()
+    dd = {k: torch.empty_like(v, device=dev) for k, v in h.items()}
+    u_d = torch.empty_like(u_h, device=dev)
+    out_d = torch.empty((3, ns.N), dtype=torch.float64, device=dev)
+    plan = hsm.Plan(dd["coords"], dd["reg"], dd["bnd"], ns.h, m=2, normals=dd["nrm"], stream=stream)
+    h2d = sum(v.numel() * v.element_size() for v in h.values()) + u_h.numel() * 8
+    d2h = out_h.numel() * 8
+
+    def step():
+        for k in h:
+            dd[k].copy_(h[k], non_blocking=True)
+        u_d.copy_(u_h, non_blocking=True)
+        plan.build_stencils()
+        plan.compute_weights(hsm.HSM_PREC_FP64)
+        plan.apply(u_d, out=out_d)
+        out_h.copy_(out_d, non_blocking=True)
+        torch.cuda.current_stream(dev).synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.steps):
+        step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / args.steps
+    plan.close()
+    return {"value": ns.N / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h)}
+
+
+def nodesets_u(ns):
+    from paper_2303_01760_gb300 import nodesets
+
+    return nodesets.field_sincos(ns.coords)[0]
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle on the host cores
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    # the oracle runs single-threaded (set before numpy is first imported)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    from paper_2303_01760_gb300 import nodesets
+
+    ns = nodesets.cached(nodesets.square_holes)
+    n_sample = args.ref_sample
+    cpu_sample_run(min(n_sample, 500))  # warm imports / caches
+    times = []
+    for _ in range(args.warmup):
+        cpu_sample_run(n_sample)
+    for k in range(args.steps):
+        t, n = cpu_sample_run(n_sample, seed=100 + k)
+        times.append(t)
+    t = sum(times) / len(times)
+    value = n_sample / t
+    cores = 1
+    res = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": workload_desc(ns),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"{n_sample} random nodes of the workload per step (stencils, weights, "
+                                      f"one application of dx,dy,lap)"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(res))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-sample", type=int, default=20000)
+    ap.add_argument("--ref-sample", type=int, default=5000)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

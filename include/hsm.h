@@ -168,6 +168,22 @@ hsm_status hsm_apply(hsm_plan plan, unsigned op_mask, hsm_dtype in_dtype, const 
  * after tuning, keyed by device name and problem shape.  Synchronises.      */
 hsm_status hsm_plan_autotune(hsm_plan plan, const char* cache_path);
 
+/* Phases timed by hsm_plan_profile. */
+enum { HSM_PHASE_STENCILS = 0, HSM_PHASE_MON = 1, HSM_PHASE_RBF = 2, HSM_PHASE_APPLY = 3,
+       HSM_PHASE_COUNT = 4 };
+
+/* Device time of the last run of each phase, measured with CUDA events that
+ * the library records on the plan's stream around the phase's kernels (only
+ * while timing is enabled with hsm_plan_set_timing), and the number of kernels
+ * the plan has launched since it was created.
+ *   phase_ms  host float [HSM_PHASE_COUNT] or NULL (milliseconds)
+ *   launches  host int64 or NULL
+ * Synchronises the plan's stream.                                           */
+hsm_status hsm_plan_profile(hsm_plan plan, float* phase_ms, int64_t* launches);
+
+/* Enables (1) or disables (0) the per-phase event timing of the plan.       */
+hsm_status hsm_plan_set_timing(hsm_plan plan, int enable);
+
 /* Releases the plan and all memory it owns.  NULL is allowed.               */
 hsm_status hsm_plan_destroy(hsm_plan plan);
 

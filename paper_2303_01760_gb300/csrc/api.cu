@@ -156,7 +156,28 @@ hsm_status hsm_plan_destroy(hsm_plan p) {
   if (!p) return HSM_OK;
   free_plan_device(p);
   cudaStreamSynchronize(p->stream);
+  for (auto& e : p->ev)
+    if (e) cudaEventDestroy(e);
   delete p;
+  return HSM_OK;
+}
+
+hsm_status hsm_plan_set_timing(hsm_plan p, int enable) {
+  if (!p) return set_error(nullptr, HSM_EINVAL, "plan is NULL");
+  p->timing = enable != 0;
+  return HSM_OK;
+}
+
+hsm_status hsm_plan_profile(hsm_plan p, float* phase_ms, int64_t* launches) {
+  if (!p) return set_error(nullptr, HSM_EINVAL, "plan is NULL");
+  if (launches) *launches = p->launches;
+  if (phase_ms) {
+    HSM_CUDA(p, cudaStreamSynchronize(p->stream));
+    for (int ph = 0; ph < HSM_PHASE_COUNT; ++ph) {
+      phase_ms[ph] = 0.f;
+      if (p->ev_used[ph]) HSM_CUDA(p, cudaEventElapsedTime(&phase_ms[ph], p->ev[2 * ph], p->ev[2 * ph + 1]));
+    }
+  }
   return HSM_OK;
 }
 
@@ -182,6 +203,7 @@ hsm_status hsm_plan_build_stencils(hsm_plan p) {
   HSM_CUDA(p, cudaMemcpyAsync(p->mono_exp, ex.data(), ex.size(), cudaMemcpyHostToDevice, s));
   // host vectors must outlive the async copies
   HSM_CUDA(p, cudaStreamSynchronize(s));
+  PhaseTimer tm(p, HSM_PHASE_STENCILS);
   return build_stencils(p);
 }
 
@@ -198,9 +220,14 @@ hsm_status hsm_plan_compute_weights(hsm_plan p, hsm_prec prec, uint8_t* node_sta
   dev_free(&p->mon.w32, s);
   dev_free(&p->rbf.w32, s);
   HSM_CUDA(p, cudaMemsetAsync(p->dev_flags, 0, sizeof(unsigned), s));
-  hsm_status st = compute_mon_weights(p, node_status);
+  hsm_status st;
+  {
+    PhaseTimer tm(p, HSM_PHASE_MON);
+    st = compute_mon_weights(p, node_status);
+  }
   if (st != HSM_OK) return st;
   p->n_fallback = 0;
+  PhaseTimer tm_rbf(p, HSM_PHASE_RBF);
   if (prec == HSM_PREC_FP64) {
     st = compute_rbf_weights_fp64(p, nullptr, p->rbf.count, node_status);
     if (st != HSM_OK) return st;
@@ -289,6 +316,7 @@ hsm_status hsm_plan_export_csr(hsm_plan p, unsigned op, int64_t* row_ptr, int32_
   k_row_width<<<grid, T, 0, s>>>(p->kind, p->N, p->mon.width, p->rbf.width, width);
   HSM_CUDA(p, exclusive_scan_i32(width, rp, p->N, s));
   k_fill_csr<<<grid, T, 0, s>>>(p->kind, p->pos, rp, p->N, p->mon, p->rbf, slot, row_ptr, col, val);
+  p->launches += 5;
   HSM_CUDA(p, cudaGetLastError());
   dev_free(&width, s);
   dev_free(&rp, s);
@@ -307,6 +335,7 @@ hsm_status hsm_apply(hsm_plan p, unsigned op_mask, hsm_dtype in_dtype, const voi
     hsm_status st = weights_to_f32(p);
     if (st != HSM_OK) return st;
   }
+  PhaseTimer tm(p, HSM_PHASE_APPLY);
   return launch_apply(p, op_mask, in_dtype, u, out, p->stream);
 }
 

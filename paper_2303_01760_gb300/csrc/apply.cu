@@ -148,6 +148,7 @@ hsm_status launch_apply(hsm_plan p, unsigned op_mask, hsm_dtype dt, const void* 
   // Slots<NOPS> is a prefix of Slots<4>; the kernel reads only its first NOPS ints
   void* args[] = {&gm, &gr, &bm, &sl4, &u, &out, &N};
   HSM_CUDA(p, cudaLaunchKernel(fn, dim3((unsigned)(bm + br)), dim3(T), args, 0, s));
+  p->launches += 1;
   return HSM_OK;
 }
 

@@ -76,9 +76,34 @@ struct hsm_plan_s {
   hsm::Tuning tune;
   hsm::Mlp* mlp = nullptr;       // attached learned predictor (not owned)
   std::string last_error;
+  int64_t launches = 0;          // kernels launched by this plan
+  bool timing = false;
+  cudaEvent_t ev[2 * HSM_PHASE_COUNT] = {};
+  bool ev_used[HSM_PHASE_COUNT] = {};
 };
 
 namespace hsm {
+
+// Event timing of one phase on the plan's stream (no-op unless enabled).
+struct PhaseTimer {
+  hsm_plan p;
+  int ph;
+  PhaseTimer(hsm_plan p_, int ph_) : p(p_), ph(ph_) {
+    if (p->timing) {
+      if (!p->ev[2 * ph]) {
+        cudaEventCreate(&p->ev[2 * ph]);
+        cudaEventCreate(&p->ev[2 * ph + 1]);
+      }
+      cudaEventRecord(p->ev[2 * ph], p->stream);
+    }
+  }
+  ~PhaseTimer() {
+    if (p->timing) {
+      cudaEventRecord(p->ev[2 * ph + 1], p->stream);
+      p->ev_used[ph] = true;
+    }
+  }
+};
 
 // Records a CUDA error on the plan and returns HSM_ECUDA.
 hsm_status cuda_fail(hsm_plan p, cudaError_t e, const char* what);

@@ -320,6 +320,7 @@ hsm_status build_stencils(hsm_plan p) {
   HSM_CUDA(p, cudaMemcpyAsync(bbox, bb_init, sizeof(bb_init), cudaMemcpyHostToDevice, s));
   HSM_CUDA(p, cudaMemcpyAsync(lat, lat_init, sizeof(lat_init), cudaMemcpyHostToDevice, s));
   k_bounds<<<grid, T, 0, s>>>(p->coords, N, dim, 1.0 / p->h, bbox, lat, lat + kMaxDim, ijk, on_lat);
+  p->launches += 1;
   HSM_CUDA(p, cudaGetLastError());
   unsigned long long bb[2 * kMaxDim];
   int lat_h[2 * kMaxDim + 4];
@@ -345,6 +346,7 @@ hsm_status build_stencils(hsm_plan p) {
   k_lattice_insert<<<grid, T, 0, s>>>(ijk, on_lat, N, lg, map);
   int* d_demoted = lat + 2 * kMaxDim;
   k_classify<<<grid, T, 0, s>>>(ijk, on_lat, p->is_regular, p->is_boundary, N, lg, map, p->kind, d_demoted);
+  p->launches += 2;
   HSM_CUDA(p, cudaGetLastError());
 
   // ---- group lists (ascending node ids) and positions
@@ -357,6 +359,7 @@ hsm_status build_stencils(hsm_plan p) {
   HSM_CUDA(p, cudaMemcpyAsync(&cnt_h[2], d_demoted, sizeof(int), cudaMemcpyDeviceToHost, s));
   HSM_CUDA(p, select_indices(p->kind, 0, N, list_mon, p->pos, counts, s));
   HSM_CUDA(p, select_indices(p->kind, 1, N, list_rbf, p->pos, counts + 1, s));
+  p->launches += 6;
   HSM_CUDA(p, cudaMemcpyAsync(cnt_h, counts, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
   HSM_CUDA(p, cudaStreamSynchronize(s));
   p->n_demoted = cnt_h[2];
@@ -371,6 +374,7 @@ hsm_status build_stencils(hsm_plan p) {
   if (p->mon.count) {
     int gm = (int)std::min<int64_t>(ceil_div(p->mon.count, T), (int64_t)num_sms() * 8);
     k_mon_stencil<<<gm, T, 0, s>>>(ijk, list_mon, p->mon.count, N, lg, map, p->mon.idx);
+    p->launches += 1;
     HSM_CUDA(p, cudaGetLastError());
   }
 
@@ -414,9 +418,11 @@ hsm_status build_stencils(hsm_plan p) {
     k_cell_count<<<grid, T, 0, s>>>(p->coords, N, cg, cell_of, ccount);
     HSM_CUDA(p, cudaGetLastError());
     HSM_CUDA(p, exclusive_scan_i32(ccount, cstart, ncell, s));
+    p->launches += 4;
     HSM_CUDA(p, cudaMemsetAsync(ccount, 0, ncell * sizeof(int32_t), s));
     k_cell_scatter<<<grid, T, 0, s>>>(p->coords, p->is_boundary, N, dim, cell_of, cstart, ccount, sorted_id,
                                       sorted_xyz, sorted_bnd);
+    p->launches += 2;
     HSM_CUDA(p, cudaGetLastError());
     const int KT = 128;
     size_t smem = (size_t)p->n * KT * (sizeof(double) + sizeof(int32_t));

@@ -568,6 +568,7 @@ hsm_status run_steps(hsm_stepper st, int n_steps, double* v, double* T, double* 
   for (int it = 0; it < n_steps; ++it) {
     k_predictor<DIM><<<grid, blk, 0, s>>>(a);
     k_krylov_init<DIM><<<grid, blk, 0, s>>>(a);
+    pl->launches += 2;
     HSM_CUDA(pl, cudaGetLastError());
     const int max_chunks = (int)(st->phys.krylov_max_it / chunk) + 2;
     for (int ch = 0; ch < max_chunks; ++ch) {
@@ -575,6 +576,7 @@ hsm_status run_steps(hsm_stepper st, int n_steps, double* v, double* T, double* 
         k_bicg_a<DIM><<<grid, blk, 0, s>>>(a);
         k_bicg_b<DIM><<<grid, blk, 0, s>>>(a);
         k_bicg_c<DIM><<<grid, blk, 0, s>>>(a);
+        pl->launches += 3;
       }
       HSM_CUDA(pl, cudaGetLastError());
       HSM_CUDA(pl, cudaMemcpyAsync(&host, a.ks, sizeof(KS), cudaMemcpyDeviceToHost, s));
@@ -585,6 +587,7 @@ hsm_status run_steps(hsm_stepper st, int n_steps, double* v, double* T, double* 
     if (host.breakdown != 0.0 || host.rnorm2 > host.tol2 * host.bnorm2 * 1.0000001) *notconv = true;
     k_correct_temperature<DIM><<<grid, blk, 0, s>>>(a);
     k_temperature_bc<<<grid, blk, 0, s>>>(a);
+    pl->launches += 2;
     HSM_CUDA(pl, cudaGetLastError());
   }
   HSM_CUDA(pl, cudaStreamSynchronize(s));

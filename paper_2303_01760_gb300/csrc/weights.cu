@@ -648,6 +648,7 @@ hsm_status launch_rbf(hsm_plan p, bool r32, const int32_t* list, int64_t count, 
   int grid = (int)std::min<int64_t>(want, (int64_t)num_sms() * blocks_per_sm);
   void* args[] = {&a};
   HSM_CUDA(p, cudaLaunchKernel(fn, dim3(grid), dim3(128), args, smem, p->stream));
+  p->launches += 1;
   return HSM_OK;
 }
 
@@ -680,6 +681,7 @@ hsm_status compute_mon_weights(hsm_plan p, uint8_t* status) {
   }
 #undef HSM_MON
   HSM_CUDA(p, cudaGetLastError());
+  p->launches += 1;
   return HSM_OK;
 }
 
@@ -704,6 +706,7 @@ hsm_status weights_to_f32(hsm_plan p) {
     if (!n) continue;
     int grid = (int)std::min<int64_t>(ceil_div(n, T), (int64_t)num_sms() * 8);
     k_to_f32<2, 1><<<grid, T, 0, p->stream>>>(g->w64, g->w32, n);
+    p->launches += 1;
     HSM_CUDA(p, cudaGetLastError());
   }
   return HSM_OK;

@@ -50,6 +50,8 @@ _SIGS = {
     "hsm_apply": (C.c_int, [_p, C.c_uint, C.c_int, _p, _p]),
     "hsm_plan_autotune": (C.c_int, [_p, C.c_char_p]),
     "hsm_plan_destroy": (C.c_int, [_p]),
+    "hsm_plan_profile": (C.c_int, [_p, C.POINTER(C.c_float), C.POINTER(_i64)]),
+    "hsm_plan_set_timing": (C.c_int, [_p, C.c_int]),
     "hsm_stepper_create": (C.c_int, [C.POINTER(_p), _p, C.POINTER(hsm_phys)]),
     "hsm_step": (C.c_int, [_p, C.c_int, _p, _p, _p, C.POINTER(C.c_int)]),
     "hsm_stepper_destroy": (C.c_int, [_p]),
@@ -161,6 +163,16 @@ class Plan:
             raise ValueError("u must be float32 or float64")
         check(lib.hsm_apply(self.h, int(op_mask), dt, ptr(u), ptr(out)), self.h)
         return out
+
+    def set_timing(self, enable=True):
+        check(lib.hsm_plan_set_timing(self.h, 1 if enable else 0), self.h)
+
+    def profile(self):
+        """(per-phase device ms [stencils, MON, RBF-FD, apply], kernels launched)"""
+        ms = (C.c_float * 4)()
+        n = _i64()
+        check(lib.hsm_plan_profile(self.h, ms, C.byref(n)), self.h)
+        return list(ms), n.value
 
     def autotune(self, cache_path=None):
         check(lib.hsm_plan_autotune(self.h, cache_path.encode() if cache_path else None), self.h)
