@@ -408,6 +408,36 @@ def run_reference(args):
     print(json.dumps(res))
 
 
+def run_kernels(args):
+    """Profiling driver: the timed operator path on the hybrid workload, with
+    no oracle, no parity gate and no JSON (for ncu captures)."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2303_01760_gb300 import hsm, nodesets
+
+    dev = torch.device("cuda:0")
+    ns = nodesets.cached(nodesets.square_holes)
+    c = torch.from_numpy(ns.coords).to(dev)
+    reg = torch.from_numpy(ns.is_regular).to(dev)
+    if args.all_rbffd:
+        reg = torch.zeros_like(reg)
+    bnd = torch.from_numpy(ns.is_boundary).to(dev)
+    nrm = torch.from_numpy(ns.normals).to(dev)
+    u = torch.from_numpy(nodesets.field_sincos(ns.coords)[0]).to(dev)
+    plan = hsm.Plan(c, reg, bnd, ns.h, m=2, normals=nrm)
+    prec = {"fp64": hsm.HSM_PREC_FP64, "fp32r": hsm.HSM_PREC_FP32_REFINE}[args.prec]
+    for _ in range(args.warmup + args.steps):
+        plan.build_stencils()
+        plan.compute_weights(prec)
+        plan.apply(u)
+    torch.cuda.synchronize()
+    plan.close()
+    print("kernels ok", ns.N)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -416,7 +446,13 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-sample", type=int, default=20000)
     ap.add_argument("--ref-sample", type=int, default=5000)
+    ap.add_argument("--kernels", action="store_true", help="profiling driver only (no JSON line)")
+    ap.add_argument("--all-rbffd", action="store_true", help="with --kernels: force every node to RBF-FD")
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32r"], help="with --kernels")
     args = ap.parse_args()
+    if args.kernels:
+        run_kernels(args)
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -340,7 +340,9 @@ __device__ __forceinline__ bool lu_solve(T* Mt, int ldt, int K, T* inv, int lane
         }
       }
       if (brow != k && brow < K) {
-        for (int j = k + lane; j < Ctot; j += LANES) {
+        // whole rows, multipliers included, so the stored factor stays
+        // consistent for later right-hand sides
+        for (int j = (perm ? 0 : k) + lane; j < Ctot; j += LANES) {
           T t = Mt[k * ldt + j];
           Mt[k * ldt + j] = Mt[brow * ldt + j];
           Mt[brow * ldt + j] = t;
