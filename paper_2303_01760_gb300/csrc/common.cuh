@@ -38,7 +38,7 @@ struct Group {
 struct Tuning {
   int apply_threads = 256;  // threads per block of the apply kernel
   int apply_split = 1;      // lanes per RBF-FD stencil in the apply kernel (1, 2, 4)
-  int rbf_lanes = 32;       // lanes per RBF-FD weight system (8, 16, 32)
+  int rbf_lanes = 8;        // lanes per RBF-FD weight system (8, 16, 32)
   bool tuned = false;
 };
 

@@ -36,10 +36,20 @@ __host__ __device__ inline double host_from_ordered(unsigned long long b) {
   return d;
 }
 
-// Bounding box (ordered-bit atomics) and lattice extents of the node set.
-__global__ void k_bounds(const double* __restrict__ coords, int64_t N, int dim, double inv_h,
-                         unsigned long long* bbox, int* lat_lo, int* lat_hi, int32_t* ijk,
-                         uint8_t* on_lat) {
+// Bounding box (ordered-bit keys) and lattice extents of the node set: each
+// thread keeps running extrema, the block reduces them with warp shuffles,
+// and one thread per block issues the global atomics.
+__global__ void __launch_bounds__(256) k_bounds(const double* __restrict__ coords, int64_t N, int dim, double inv_h,
+                                                unsigned long long* bbox, int* lat_lo, int* lat_hi, int32_t* ijk,
+                                                uint8_t* on_lat) {
+  unsigned long long bmin[kMaxDim], bmax[kMaxDim];
+  int lmin[kMaxDim], lmax[kMaxDim];
+  for (int k = 0; k < kMaxDim; ++k) {
+    bmin[k] = ~0ull;
+    bmax[k] = 0ull;
+    lmin[k] = 0x7fffffff;
+    lmax[k] = -0x7fffffff;
+  }
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
     bool on = true;
@@ -47,8 +57,8 @@ __global__ void k_bounds(const double* __restrict__ coords, int64_t N, int dim, 
     for (int k = 0; k < dim; ++k) {
       double x = coords[k * N + i];
       unsigned long long ob = ordered_bits(x);
-      atomicMin(&bbox[2 * k], ob);
-      atomicMax(&bbox[2 * k + 1], ob);
+      bmin[k] = ob < bmin[k] ? ob : bmin[k];
+      bmax[k] = ob > bmax[k] ? ob : bmax[k];
       double t = x * inv_h;
       double r = rint(t);
       if (!(fabs(t - r) <= kLatticeTol) || fabs(r) > 1.0e9) on = false;
@@ -58,8 +68,49 @@ __global__ void k_bounds(const double* __restrict__ coords, int64_t N, int dim, 
     for (int k = 0; k < dim; ++k) {
       ijk[k * N + i] = q[k];
       if (on) {
-        atomicMin(&lat_lo[k], q[k]);
-        atomicMax(&lat_hi[k], q[k]);
+        lmin[k] = min(lmin[k], q[k]);
+        lmax[k] = max(lmax[k], q[k]);
+      }
+    }
+  }
+  __shared__ unsigned long long sb[2][kMaxDim][8];
+  __shared__ int sl[2][kMaxDim][8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int k = 0; k < dim; ++k) {
+    for (int o = 16; o > 0; o >>= 1) {
+      unsigned long long a = __shfl_xor_sync(0xffffffffu, bmin[k], o);
+      unsigned long long b = __shfl_xor_sync(0xffffffffu, bmax[k], o);
+      int c = __shfl_xor_sync(0xffffffffu, lmin[k], o);
+      int d = __shfl_xor_sync(0xffffffffu, lmax[k], o);
+      bmin[k] = a < bmin[k] ? a : bmin[k];
+      bmax[k] = b > bmax[k] ? b : bmax[k];
+      lmin[k] = min(lmin[k], c);
+      lmax[k] = max(lmax[k], d);
+    }
+    if (lane == 0) {
+      sb[0][k][wid] = bmin[k];
+      sb[1][k][wid] = bmax[k];
+      sl[0][k][wid] = lmin[k];
+      sl[1][k][wid] = lmax[k];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) / 32;
+    for (int k = 0; k < dim; ++k) {
+      unsigned long long a = ~0ull, b = 0ull;
+      int c = 0x7fffffff, d = -0x7fffffff;
+      for (int w = 0; w < nw; ++w) {
+        a = sb[0][k][w] < a ? sb[0][k][w] : a;
+        b = sb[1][k][w] > b ? sb[1][k][w] : b;
+        c = min(c, sl[0][k][w]);
+        d = max(d, sl[1][k][w]);
+      }
+      atomicMin(&bbox[2 * k], a);
+      atomicMax(&bbox[2 * k + 1], b);
+      if (c <= d) {
+        atomicMin(&lat_lo[k], c);
+        atomicMax(&lat_hi[k], d);
       }
     }
   }
@@ -424,7 +475,8 @@ hsm_status build_stencils(hsm_plan p) {
                                       sorted_xyz, sorted_bnd);
     p->launches += 2;
     HSM_CUDA(p, cudaGetLastError());
-    const int KT = 128;
+    // one thread per query; small blocks spread the few scattered queries over every SM
+    const int KT = 32;
     size_t smem = (size_t)p->n * KT * (sizeof(double) + sizeof(int32_t));
     int gk = (int)std::min<int64_t>(ceil_div(p->rbf.count, KT), (int64_t)num_sms() * 16);
     if (dim == 2) {

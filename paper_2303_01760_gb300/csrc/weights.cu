@@ -196,23 +196,25 @@ __device__ __forceinline__ unsigned long long shfl_xor_u64(unsigned mask, unsign
 // Per-system shared memory layout (in doubles):
 //   M      K x ld        (T = double) or K x K FP64 copy + K x ld T (fp32r)
 //   xi     n x DIM
+//   rc     n          |xi_j|, the scaled distance of node j from the centre
 //   inv    K
 //   b64    K x NOPS   (fp32r only)
 //   x64    K x NOPS   (fp32r only)
 template <int DIM, int NOPS, bool R32>
 __host__ __device__ constexpr size_t sys_doubles(int K, int ld, int n) {
-  return R32 ? ((size_t)K * K + ((size_t)K * ld + 1) / 2 + (size_t)n * DIM + K + 2 * (size_t)K * NOPS + (K + 1) / 2)
-             : ((size_t)K * ld + (size_t)n * DIM + K);
+  return R32 ? ((size_t)K * K + ((size_t)K * ld + 1) / 2 + (size_t)n * (DIM + 1) + K + 2 * (size_t)K * NOPS +
+                (K + 1) / 2)
+             : ((size_t)K * ld + (size_t)n * (DIM + 1) + K);
 }
 
 // Assembles [A P | L phi; P^T 0 | L p] into Mt (row stride ld) for the scaled
 // offsets xi.  Returns via *inv_s the inverse scale.
 template <int DIM, int NOPS, int LANES, typename T>
 __device__ __forceinline__ void assemble(const RbfArgs& a, int64_t pos, int lane, unsigned mask, double* xi,
-                                         T* Mt, int ldt, double* M64, double& inv_s_out, bool& ok) {
+                                         double* rc, T* Mt, int ldt, double* M64, double& inv_s_out, bool& ok) {
   const int n = a.n, K = a.K, nm = a.n_mono;
   const int32_t c = a.nodes[pos];
-  double r2max = 0.0;
+  unsigned long long b = 0ull;
   for (int j = lane; j < n; j += LANES) {
     const int32_t id = a.idx[(int64_t)j * a.G + pos];
     double r2 = 0.0;
@@ -222,21 +224,24 @@ __device__ __forceinline__ void assemble(const RbfArgs& a, int64_t pos, int lane
       xi[j * DIM + k] = o;
       r2 += o * o;
     }
-    r2max = fmax(r2max, r2);
+    const double r = sqrt(r2);
+    rc[j] = r;
+    // non-negative doubles order like their bit patterns
+    const unsigned long long rb = (unsigned long long)__double_as_longlong(r);
+    b = rb > b ? rb : b;
   }
-  // max over the lane group: non-negative doubles order like their bit patterns
-  unsigned long long b = (unsigned long long)__double_as_longlong(r2max);
 #pragma unroll
   for (int o = LANES / 2; o > 0; o >>= 1) {
     unsigned long long t = shfl_xor_u64(mask, b, o, LANES);
     b = t > b ? t : b;
   }
-  const double s = sqrt(__longlong_as_double((long long)b));
+  const double s = __longlong_as_double((long long)b);
   const double inv_s = 1.0 / s;
   inv_s_out = inv_s;
   ok = s > 0.0 && isfinite(s);
   __syncwarp(mask);
   for (int e = lane; e < n * DIM; e += LANES) xi[e] *= inv_s;
+  for (int e = lane; e < n; e += LANES) rc[e] *= inv_s;
   __syncwarp(mask);
   // A block (zero diagonal, symmetric pairs)
   for (int e = lane; e < n; e += LANES) {
@@ -285,13 +290,10 @@ __device__ __forceinline__ void assemble(const RbfArgs& a, int64_t pos, int lane
   __syncwarp(mask);
 }
 
-// RHS value of operator o for stencil node e (e < n: PHS part) or monomial q.
+// RHS value of operator o for stencil node e (PHS part); r = |xi_e|.
 template <int DIM>
-__device__ __forceinline__ double rhs_phi(const double* xi, int e, int kind) {
-  double r2 = 0.0;
-#pragma unroll
-  for (int k = 0; k < DIM; ++k) r2 += xi[e * DIM + k] * xi[e * DIM + k];
-  const double r = sqrt(r2);
+__device__ __forceinline__ double rhs_phi(const double* xi, const double* rc, int e, int kind) {
+  const double r = rc[e];
   if (kind == 3) return 3.0 * (DIM + 1) * r;
   return -3.0 * r * xi[e * DIM + kind];
 }
@@ -419,15 +421,16 @@ __global__ void __launch_bounds__(128) k_rbf_fp64(RbfArgs a) {
   double* base = smem + (size_t)sub * sys_doubles<DIM, NOPS, false>(K, ld, n);
   double* M = base;
   double* xi = M + (size_t)K * ld;
-  double* inv = xi + n * DIM;
+  double* rc = xi + n * DIM;
+  double* inv = rc + n;
   for (int64_t t = (int64_t)blockIdx.x * SYS + sub; t < a.count; t += (int64_t)gridDim.x * SYS) {
     const int64_t pos = a.list ? a.list[t] : t;
     double inv_s;
     bool ok;
-    assemble<DIM, NOPS, LANES, double>(a, pos, lane, mask, xi, M, ld, nullptr, inv_s, ok);
+    assemble<DIM, NOPS, LANES, double>(a, pos, lane, mask, xi, rc, M, ld, nullptr, inv_s, ok);
     for (int e = lane; e < n * NOPS; e += LANES) {
       const int i = e / NOPS, o = e - (e / NOPS) * NOPS;
-      M[i * ld + K + o] = rhs_phi<DIM>(xi, i, a.ops.kind[o]);
+      M[i * ld + K + o] = rhs_phi<DIM>(xi, rc, i, a.ops.kind[o]);
     }
     for (int e = lane; e < a.n_mono * NOPS; e += LANES) {
       const int q = e / NOPS, o = e - (e / NOPS) * NOPS;
@@ -466,18 +469,19 @@ __global__ void __launch_bounds__(128) k_rbf_fp32r(RbfArgs a) {
   double* M64 = base;
   float* L32 = reinterpret_cast<float*>(M64 + (size_t)K * K);
   double* xi = M64 + (size_t)K * K + ((size_t)K * ld32 + 1) / 2;
-  float* inv = reinterpret_cast<float*>(xi + n * DIM);
-  double* b64 = xi + n * DIM + K;
+  double* rc = xi + n * DIM;
+  float* inv = reinterpret_cast<float*>(rc + n);
+  double* b64 = rc + n + K;
   double* x64 = b64 + K * NOPS;
   int* perm = reinterpret_cast<int*>(x64 + K * NOPS);
   for (int64_t t = (int64_t)blockIdx.x * SYS + sub; t < a.count; t += (int64_t)gridDim.x * SYS) {
     const int64_t pos = a.list ? a.list[t] : t;
     double inv_s;
     bool ok;
-    assemble<DIM, NOPS, LANES, float>(a, pos, lane, mask, xi, L32, ld32, M64, inv_s, ok);
+    assemble<DIM, NOPS, LANES, float>(a, pos, lane, mask, xi, rc, L32, ld32, M64, inv_s, ok);
     for (int e = lane; e < K * NOPS; e += LANES) {
       const int i = e / NOPS, o = e - (e / NOPS) * NOPS;
-      const double v = i < n ? rhs_phi<DIM>(xi, i, a.ops.kind[o]) : rhs_mono<DIM>(a.mono_exp, i - n, a.ops.kind[o]);
+      const double v = i < n ? rhs_phi<DIM>(xi, rc, i, a.ops.kind[o]) : rhs_mono<DIM>(a.mono_exp, i - n, a.ops.kind[o]);
       b64[i * NOPS + o] = v;
       L32[i * ld32 + K + o] = (float)v;
     }
@@ -601,8 +605,9 @@ void* pick(int dim, int nops, int lanes) {
 size_t smem_bytes(int dim, int nops, bool r32, int K, int ld, int n) {
   size_t d = 0;
   const int ld32 = (K + nops) | 1;
-  if (r32) d = (size_t)K * K + ((size_t)K * ld32 + 1) / 2 + (size_t)n * dim + K + 2 * (size_t)K * nops + (K + 1) / 2;
-  else d = (size_t)K * ld + (size_t)n * dim + K;
+  if (r32) d = (size_t)K * K + ((size_t)K * ld32 + 1) / 2 + (size_t)n * (dim + 1) + K + 2 * (size_t)K * nops +
+               (K + 1) / 2;
+  else d = (size_t)K * ld + (size_t)n * (dim + 1) + K;
   return d * sizeof(double);
 }
 
