@@ -424,7 +424,7 @@ hsm_status hsm_plan_autotune(hsm_plan p, const char* cache_path) {
   HSM_CUDA(p, cudaMemsetAsync(u, 0, p->N * sizeof(double), s));
   best = 1e30f;
   int best_t = p->tune.apply_threads;
-  for (int t : {128, 256, 512}) {
+  for (int t : {64, 128, 256}) {
     p->tune.apply_threads = t;
     float ms = time_ms(s, [&]() { return launch_apply(p, p->op_mask, HSM_F64, u, out, s); }, 10, &st);
     if (st != HSM_OK) break;
