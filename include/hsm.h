@@ -230,6 +230,42 @@ hsm_status hsm_step(hsm_stepper st, int n_steps, double* v, double* T, double* p
 
 hsm_status hsm_stepper_destroy(hsm_stepper st);
 
+/* ------------------------------------------------------------------------ */
+/* Allocation-free weights for caller-supplied stencils                     */
+/* ------------------------------------------------------------------------ */
+
+/* Largest batch the allocation-free entry point accepts.                    */
+#define HSM_NOALLOC_MAX_SYSTEMS (1 << 20)
+
+/* RBF-FD weights (FP32 factorisation, FP64-residual refinement, FP64 re-solve
+ * of systems whose refinement does not converge) for stencils the caller
+ * already has, allocating no device memory.  The paper has no counterpart to
+ * this entry point; it exists for callers that must not allocate device
+ * memory while they run (for example a solver embedded in an application
+ * that hands all device memory to its own pool at start-up, or a real-time
+ * loop in which an allocation could stall or fail).
+ *   dim, aug_m, stencil_n, op_mask  as for hsm_plan_create (stencil_n > 0)
+ *   coords      device f64 [dim][n_nodes]
+ *   stencils    device int32 [stencil_n][count]; row 0 holds each stencil's
+ *               centre, the other rows its neighbours (any order)
+ *   count       0 <= count <= HSM_NOALLOC_MAX_SYSTEMS, else HSM_EINVAL
+ *   weights     device f64 [popcount(op_mask)][stencil_n][count] (output)
+ *   node_status device u8 [n_nodes] or NULL: every entry is set to
+ *               HSM_NODE_OK, then centres re-solved in FP64 get
+ *               HSM_NODE_REFINE_FP64 and singular ones HSM_NODE_SINGULAR
+ * Its scratch (a fail list of HSM_NOALLOC_MAX_SYSTEMS entries, counters and
+ * small tables, about 4.3 MB) is one static device array in the library that
+ * every GPU which loads the library holds until the process exits.  All calls
+ * share it and it keeps the last call's contents; calls that overlap on the
+ * GPU (other streams, other host threads) race on it, so serialise them.  The
+ * first call on a device looks up the array's address for that device (with
+ * it current); make that first call before any stream capture.  Synchronises
+ * the stream twice.  Returns HSM_ESINGULAR when some system is singular.    */
+hsm_status hsm_rbf_weights_fp32r_noalloc(int dim, int aug_m, int stencil_n, unsigned op_mask,
+                                         const double* coords, int64_t n_nodes, const int32_t* stencils,
+                                         int64_t count, double* weights, uint8_t* node_status,
+                                         void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

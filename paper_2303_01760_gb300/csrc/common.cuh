@@ -161,6 +161,31 @@ hsm_status compute_rbf_weights_fp32r(hsm_plan p, const int32_t* list, int64_t co
 hsm_status weights_to_f32(hsm_plan p);
 size_t rbf_smem_per_system(int K, int ld, bool fp32);
 
+// Weight systems for caller-supplied stencils, described without a plan
+// (used by the allocation-free entry point in noalloc.cu).
+struct RbfExternal {
+  int dim = 2;
+  const double* coords = nullptr;  // [dim][N]
+  int64_t N = 0;
+  const int32_t* idx = nullptr;    // [n][G], row 0 = stencil centres
+  int64_t G = 0;
+  int n = 0, n_mono = 0;
+  unsigned op_mask = 0;
+  int nops = 0;
+  const int8_t* mono_exp = nullptr;
+  const uint16_t* pairs = nullptr;
+  double* w = nullptr;             // [nops][n][G]
+  unsigned* flags = nullptr;
+  int32_t* fail_list = nullptr;
+  int* fail_count = nullptr;
+  cudaStream_t stream = nullptr;
+};
+// Launches the FP32-refinement kernel (r32) or the FP64 kernel over the
+// systems in ``list`` (nullptr = 0..count-1); no allocation.  status is
+// indexed by the stencil centre; mark != 0 is written for every solved system.
+cudaError_t launch_rbf_external(const RbfExternal& x, bool r32, const int32_t* list, int64_t count, uint8_t* status,
+                                uint8_t mark, bool* too_big);
+
 // ---- apply.cu ------------------------------------------------------------
 hsm_status launch_apply(hsm_plan p, unsigned op_mask, hsm_dtype dt, const void* u, double* out,
                         cudaStream_t s);

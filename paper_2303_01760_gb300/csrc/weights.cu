@@ -663,6 +663,60 @@ hsm_status launch_rbf(hsm_plan p, bool r32, const int32_t* list, int64_t count, 
 
 size_t rbf_smem_per_system(int K, int ld, bool fp32) { return smem_bytes(3, 4, fp32, K, ld, kMaxStencil); }
 
+cudaError_t launch_rbf_external(const RbfExternal& x, bool r32, const int32_t* list, int64_t count, uint8_t* status,
+                                uint8_t mark, bool* too_big) {
+  *too_big = false;
+  if (count == 0) return cudaSuccess;
+  RbfArgs a;
+  a.coords = x.coords;
+  a.N = x.N;
+  a.list = list;
+  a.count = count;
+  a.idx = x.idx;
+  a.G = x.G;
+  a.nodes = x.idx;  // row 0 of the stencils holds the centres
+  a.n = x.n;
+  a.n_mono = x.n_mono;
+  a.K = x.n + x.n_mono;
+  a.ld = (a.K + x.nops) | 1;
+  a.mono_exp = x.mono_exp;
+  a.pairs = x.pairs;
+  OpsDesc d{};
+  int o = 0;
+  for (int b = 0; b < 4; ++b)
+    if (x.op_mask & (1u << b)) d.kind[o++] = b;
+  a.ops = d;
+  a.w = x.w;
+  a.status = status;
+  a.status_demoted_mark = mark;
+  a.is_regular = nullptr;  // never read: status is either NULL or written with mark
+  a.flags = x.flags;
+  a.fail_list = x.fail_list;
+  a.fail_count = x.fail_count;
+  int lanes = 8;
+  size_t per = smem_bytes(x.dim, x.nops, r32, a.K, a.ld, a.n);
+  size_t smem = per * (128 / lanes);
+  while (smem > 200 * 1024 && lanes < 32) {
+    lanes *= 2;
+    smem = per * (128 / lanes);
+  }
+  if (smem > 220 * 1024) {
+    *too_big = true;
+    return cudaSuccess;
+  }
+  void* fn = r32 ? pick<Fp32rKernel>(x.dim, x.nops, lanes) : pick<Fp64Kernel>(x.dim, x.nops, lanes);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int blocks_per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, fn, 128, smem);
+  if (e != cudaSuccess) return e;
+  if (blocks_per_sm < 1) blocks_per_sm = 1;
+  const int64_t want = ceil_div(count, 128 / lanes);
+  const int grid = (int)std::min<int64_t>(want, (int64_t)num_sms() * blocks_per_sm);
+  void* args[] = {&a};
+  return cudaLaunchKernel(fn, dim3(grid), dim3(128), args, smem, x.stream);
+}
+
 hsm_status compute_mon_weights(hsm_plan p, uint8_t* status) {
   const int64_t G = p->mon.count;
   if (G == 0) return HSM_OK;

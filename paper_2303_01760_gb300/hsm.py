@@ -55,7 +55,10 @@ _SIGS = {
     "hsm_stepper_create": (C.c_int, [C.POINTER(_p), _p, C.POINTER(hsm_phys)]),
     "hsm_step": (C.c_int, [_p, C.c_int, _p, _p, _p, C.POINTER(C.c_int)]),
     "hsm_stepper_destroy": (C.c_int, [_p]),
+    "hsm_rbf_weights_fp32r_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_uint, _p, _i64, _p, _i64, _p, _p,
+                                                _p]),
 }
+HSM_NOALLOC_MAX_SYSTEMS = 1 << 20
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name, None)
     if _f is not None:
@@ -218,3 +221,14 @@ class Stepper:
             self.close()
         except Exception:
             pass
+
+
+def rbf_weights_fp32r_noalloc(dim, m, n, op_mask, coords, stencils, weights, node_status=None, stream=None):
+    """Allocation-free RBF-FD weights for caller-supplied stencils
+    (``stencils`` int32 [n, count], row 0 = centres; ``weights`` f64
+    [nops, n, count] is written).  For callers that must not allocate device
+    memory while they run; the library keeps its scratch in a fixed static
+    device array.  Returns the status code."""
+    return lib.hsm_rbf_weights_fp32r_noalloc(int(dim), int(m), int(n), int(op_mask), ptr(coords),
+                                             int(coords.shape[1]), ptr(stencils), int(stencils.shape[1]),
+                                             ptr(weights), ptr(node_status), stream_handle(stream))
