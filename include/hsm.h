@@ -231,6 +231,57 @@ hsm_status hsm_step(hsm_stepper st, int n_steps, double* v, double* T, double* p
 hsm_status hsm_stepper_destroy(hsm_stepper st);
 
 /* ------------------------------------------------------------------------ */
+/* Learned RBF-FD weights (no counterpart in the paper: the specification's  */
+/* predictor).  An MLP maps the scaled offsets (x_i - x_c)/s of a stencil    */
+/* (node-major, 2n or 3n values) to its scaled weights (s w for derivatives, */
+/* s^2 w for the Laplacian, operator-major); its output is projected exactly  */
+/* onto the monomial reproduction constraints of Eq. 1 up to degree m, and a */
+/* stencil whose relative pre-projection residual exceeds 0.1 or whose       */
+/* post-projection residual exceeds 1e-10 is re-solved by the FP64 solve.    */
+/* Dense layers run on BF16 tensor cores with FP32 accumulation.             */
+/* ------------------------------------------------------------------------ */
+
+/* Creates an MLP: Linear(n_in, hidden) GELU, (Linear(hidden, hidden) GELU)
+ * x (layers-1), Linear(hidden, n_out); seeded uniform initialisation.        */
+hsm_status hsm_mlp_create(hsm_mlp* out, int n_in, int hidden, int layers, int n_out, uint64_t seed,
+                          void* cuda_stream);
+hsm_status hsm_mlp_destroy(hsm_mlp mlp);
+
+/* Number of parameters in the packed layout (per layer: W [out][in], b).    */
+hsm_status hsm_mlp_param_count(hsm_mlp mlp, int64_t* count);
+/* Host f32 copies of the parameters in the packed layout (synchronises).    */
+hsm_status hsm_mlp_get_params(hsm_mlp mlp, float* host, int64_t count);
+hsm_status hsm_mlp_set_params(hsm_mlp mlp, const float* host, int64_t count);
+
+/* Loss (mean squared error over samples and outputs) and its gradient with
+ * respect to the packed parameters, on count samples X device f32
+ * [count][n_in], Y device f32 [count][n_out].  grads_host: host f32 [param
+ * count] or NULL.  Synchronises.                                            */
+hsm_status hsm_mlp_grad(hsm_mlp mlp, const float* X, const float* Y, int64_t count, float* grads_host,
+                        float* loss);
+
+/* Adam training (lr, beta1 0.9, beta2 0.999, eps 1e-8) for `steps` steps of
+ * `batch` samples drawn with replacement from (X, Y) by a seeded counter
+ * hash.  loss_log: host f32 [steps] or NULL.  Synchronises.                  */
+hsm_status hsm_mlp_train(hsm_mlp mlp, const float* X, const float* Y, int64_t count, int steps, int batch,
+                         float lr, uint64_t seed, float* loss_log);
+
+/* Forward pass: Y device f32 [count][n_out] from X device f32 [count][n_in]. */
+hsm_status hsm_mlp_predict(hsm_mlp mlp, const float* X, int64_t count, float* Y);
+
+/* Attaches the predictor used by HSM_PREC_LEARNED (n_in = d n, n_out = nops n;
+ * not owned by the plan; NULL detaches).  The learned path is built for 2D
+ * plans with m = 2, n = 12; other plans return HSM_EINVAL from
+ * hsm_plan_compute_weights(HSM_PREC_LEARNED).                               */
+hsm_status hsm_mlp_attach(hsm_plan plan, hsm_mlp mlp);
+
+/* Training data of a plan: for every interior RBF-FD node in ascending node
+ * order, its features (X device f32 [count][d n]) and, from the plan's current
+ * weights, its labels (Y device f32 [count][nops n], may be NULL).  With X NULL
+ * only count is returned.  Synchronises.                                     */
+hsm_status hsm_plan_learned_data(hsm_plan plan, float* X, float* Y, int64_t* count);
+
+/* ------------------------------------------------------------------------ */
 /* Allocation-free weights for caller-supplied stencils                     */
 /* ------------------------------------------------------------------------ */
 

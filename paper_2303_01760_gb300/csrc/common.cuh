@@ -74,7 +74,7 @@ struct hsm_plan_s {
   bool stencils_built = false;
   bool weights_built = false;
   hsm::Tuning tune;
-  hsm::Mlp* mlp = nullptr;       // attached learned predictor (not owned)
+  hsm_mlp mlp = nullptr;         // attached learned predictor (not owned)
   std::string last_error;
   int64_t launches = 0;          // kernels launched by this plan
   bool timing = false;

@@ -1,10 +1,995 @@
-// Learned weight predictor (placeholder until the predictor kernels land).
+// Learned RBF-FD weights: an MLP from the normalised offsets of a scattered
+// stencil to its scaled operator weights, trained on this library's own FP64
+// weights, and an exact FP64 projection of its output onto the monomial
+// reproduction constraints (Eq. 1 enforced for every monomial of degree <= m),
+// with the direct FP64 solve as fallback.  The paper has no learned part; this
+// is the specification's predictor.
+//
+// Layers: Linear(2n -> H) GELU, (Linear(H -> H) GELU) x (L-1), Linear(H -> 3n),
+// GELU(x) = x Phi(x).  Every dense layer is a BF16 tensor-core GEMM with FP32
+// accumulation (mma.sync m16n8k16, operands staged in shared memory with
+// cp.async and read with ldmatrix), bias and activation fused into its
+// epilogue.  Master weights and Adam moments are FP32.  Dimensions are padded
+// so every GEMM is a whole number of 128 x 64 x 32 tiles: inputs to a multiple
+// of 64, hidden widths and outputs to multiples of 128, the batch to 128; the
+// padded inputs, outputs and weights stay zero.
+#include <cmath>
+#include <vector>
+
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace hsm {
 
-hsm_status compute_rbf_weights_learned(hsm_plan p, uint8_t*, int32_t*, int*) {
-  return set_error(p, HSM_ESTATE, "no learned predictor attached");
+struct Mlp {
+  int n_in = 24, hidden = 256, layers = 3, n_out = 36;
+  int nl = 4;                 // linear layers
+  std::vector<int> din, dout;  // padded in/out width per layer
+  std::vector<int> rin, rout;  // real widths
+  float* master = nullptr;    // fp32 [sum W + b] padded layout
+  float* adam_m = nullptr;
+  float* adam_v = nullptr;
+  float* grad = nullptr;
+  __nv_bfloat16* wbf = nullptr;  // bf16 copies of the weight matrices
+  std::vector<size_t> w_off, b_off, wbf_off;
+  size_t n_master = 0, n_wbf = 0;
+  int64_t t = 0;               // Adam step counter
+  cudaStream_t stream = nullptr;
+  // activation workspace for a batch of up to cap rows
+  int64_t cap = 0;
+  __nv_bfloat16* X = nullptr;     // [cap][din0]
+  std::vector<__nv_bfloat16*> H;  // per hidden layer [cap][dout]
+  std::vector<float*> Z;          // pre-activations [cap][dout]
+  float* Yout = nullptr;          // [cap][dout_last]
+  float* T = nullptr;             // targets [cap][dout_last]
+  __nv_bfloat16* dA = nullptr;    // [cap][max width]
+  __nv_bfloat16* dB = nullptr;
+  double* loss = nullptr;         // device loss accumulator
+  std::string last_error;
+};
+
+}  // namespace hsm
+
+struct hsm_mlp_s {
+  hsm::Mlp m;
+};
+
+namespace hsm {
+namespace {
+
+constexpr int BM = 128, BN = 64, BK = 32, PAD = 8;
+enum { EPI_BIAS_GELU = 0, EPI_BIAS = 1, EPI_DGELU = 2, EPI_F32 = 3, EPI_BF16 = 4 };
+
+struct GemmArgs {
+  const __nv_bfloat16* A;
+  const __nv_bfloat16* B;
+  int lda, ldb;
+  int M, N, K;
+  const float* bias;       // [N]
+  const float* Zin;        // pre-activation for EPI_DGELU [M][N] (ldz = N)
+  float* Cf;               // fp32 output [M][N]
+  __nv_bfloat16* Ch;       // bf16 output [M][N]
+  float* Zout;             // pre-activation output (EPI_BIAS_GELU)
+};
+
+__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad_f(float z) {
+  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+__device__ __forceinline__ void ldsm_x4(unsigned (&r)[4], const void* p) {
+  unsigned s = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(s));
+}
+__device__ __forceinline__ void ldsm_x4_t(unsigned (&r)[4], const void* p) {
+  unsigned s = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(s));
+}
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// C[M x N] = A * B with A row-major [M][K] (AT: stored [K][M]) and B given as
+// [N][K] (BT: stored [K][N]).  M % 128 == N % 64 == K % 32 == 0.
+template <bool AT, bool BT, int EPI>
+__global__ void __launch_bounds__(128) k_gemm(GemmArgs g) {
+  constexpr int A_ROWS = AT ? BK : BM, A_COLS = AT ? BM : BK;
+  constexpr int B_ROWS = BT ? BK : BN, B_COLS = BT ? BN : BK;
+  __shared__ __align__(16) __nv_bfloat16 As[2][A_ROWS][A_COLS + PAD];
+  __shared__ __align__(16) __nv_bfloat16 Bs[2][B_ROWS][B_COLS + PAD];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wm = warp >> 1, wn = warp & 1;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  float acc[4][4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc[i][j][k] = 0.f;
+
+  auto load = [&](int kt, int buf) {
+    const int k0 = kt * BK;
+    constexpr int ACH = A_ROWS * A_COLS / 8;  // 16-byte chunks
+#pragma unroll
+    for (int c = tid; c < ACH; c += 128) {
+      const int row = c / (A_COLS / 8), col = (c % (A_COLS / 8)) * 8;
+      const __nv_bfloat16* src =
+          AT ? g.A + (size_t)(k0 + row) * g.lda + m0 + col : g.A + (size_t)(m0 + row) * g.lda + k0 + col;
+      cp_async16(&As[buf][row][col], src);
+    }
+    constexpr int BCH = B_ROWS * B_COLS / 8;
+#pragma unroll
+    for (int c = tid; c < BCH; c += 128) {
+      const int row = c / (B_COLS / 8), col = (c % (B_COLS / 8)) * 8;
+      const __nv_bfloat16* src =
+          BT ? g.B + (size_t)(k0 + row) * g.ldb + n0 + col : g.B + (size_t)(n0 + row) * g.ldb + k0 + col;
+      cp_async16(&Bs[buf][row][col], src);
+    }
+  };
+
+  const int KT = g.K / BK;
+  load(0, 0);
+  cp_commit();
+  for (int kt = 0; kt < KT; ++kt) {
+    const int buf = kt & 1;
+    if (kt + 1 < KT) {
+      load(kt + 1, buf ^ 1);
+      cp_commit();
+      cp_wait<1>();
+    } else {
+      cp_wait<0>();
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK / 16; ++kk) {
+      unsigned af[4][4];
+#pragma unroll
+      for (int mi = 0; mi < 4; ++mi) {
+        const int mb = wm * 64 + mi * 16;
+        if (AT)
+          ldsm_x4_t(af[mi], &As[buf][kk * 16 + (lane & 7) + (lane >> 4) * 8][mb + ((lane >> 3) & 1) * 8]);
+        else
+          ldsm_x4(af[mi], &As[buf][mb + (lane & 7) + ((lane >> 3) & 1) * 8][kk * 16 + (lane >> 4) * 8]);
+      }
+      unsigned bf[2][4];
+#pragma unroll
+      for (int np = 0; np < 2; ++np) {
+        const int nb = wn * 32 + np * 16;
+        if (BT)
+          ldsm_x4_t(bf[np], &Bs[buf][kk * 16 + (lane & 7) + ((lane >> 3) & 1) * 8][nb + (lane >> 4) * 8]);
+        else
+          ldsm_x4(bf[np], &Bs[buf][nb + (lane & 7) + (lane >> 4) * 8][kk * 16 + ((lane >> 3) & 1) * 8]);
+      }
+#pragma unroll
+      for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni) {
+          const unsigned* b = &bf[ni >> 1][(ni & 1) * 2];
+          mma_bf16(acc[mi][ni], af[mi], b[0], b[1]);
+        }
+    }
+    __syncthreads();
+  }
+  // epilogue
+  const int gid = lane >> 2, tig = lane & 3;
+#pragma unroll
+  for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+    for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int m = m0 + wm * 64 + mi * 16 + gid + h * 8;
+        const int n = n0 + wn * 32 + ni * 8 + tig * 2;
+        float v0 = acc[mi][ni][2 * h], v1 = acc[mi][ni][2 * h + 1];
+        const size_t o = (size_t)m * g.N + n;
+        if (EPI == EPI_BIAS_GELU) {
+          v0 += g.bias[n];
+          v1 += g.bias[n + 1];
+          g.Zout[o] = v0;
+          g.Zout[o + 1] = v1;
+          *reinterpret_cast<__nv_bfloat162*>(g.Ch + o) = __floats2bfloat162_rn(gelu_f(v0), gelu_f(v1));
+        } else if (EPI == EPI_BIAS) {
+          g.Cf[o] = v0 + g.bias[n];
+          g.Cf[o + 1] = v1 + g.bias[n + 1];
+        } else if (EPI == EPI_DGELU) {
+          v0 *= gelu_grad_f(g.Zin[o]);
+          v1 *= gelu_grad_f(g.Zin[o + 1]);
+          *reinterpret_cast<__nv_bfloat162*>(g.Ch + o) = __floats2bfloat162_rn(v0, v1);
+        } else if (EPI == EPI_F32) {
+          g.Cf[o] = v0;
+          g.Cf[o + 1] = v1;
+        } else {
+          *reinterpret_cast<__nv_bfloat162*>(g.Ch + o) = __floats2bfloat162_rn(v0, v1);
+        }
+      }
+}
+
+template <bool AT, bool BT, int EPI>
+cudaError_t gemm(const GemmArgs& g, cudaStream_t s) {
+  dim3 grid(g.N / BN, g.M / BM);
+  k_gemm<AT, BT, EPI><<<grid, 128, 0, s>>>(g);
+  return cudaGetLastError();
+}
+
+// ---- small kernels ----------------------------------------------------------
+__device__ __forceinline__ uint64_t mix64(uint64_t x) {
+  // splitmix64 finaliser (Steele, Lea and Flood, 2014)
+  x += 0x9e3779b97f4a7c15ull;
+  x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+  x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+  return x ^ (x >> 31);
+}
+
+// Gathers rows of the dataset into padded bf16 inputs and fp32 targets.
+// Row r of the batch takes sample idx = mix64(seed, step, r) % count, or r
+// itself when seed == 0 (in order; rows beyond count are zero).
+__global__ void k_pack(const float* __restrict__ X, const float* __restrict__ Y, int64_t count, int n_in, int n_out,
+                       int din, int dout, int64_t rows, uint64_t seed, int64_t step, int64_t base,
+                       __nv_bfloat16* Xb, float* T) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
+    int64_t src = -1;
+    if (seed) src = (int64_t)(mix64(seed ^ mix64((uint64_t)step * 0x100000001b3ull + (uint64_t)r)) % (uint64_t)count);
+    else if (base + r < count) src = base + r;
+    for (int j = 0; j < din; ++j)
+      Xb[r * din + j] = __float2bfloat16(src >= 0 && j < n_in ? X[src * n_in + j] : 0.f);
+    if (T)
+      for (int j = 0; j < dout; ++j) T[r * dout + j] = (src >= 0 && j < n_out && Y) ? Y[src * n_out + j] : 0.f;
+  }
+}
+
+// dY = 2 (Y - T) / (rows_valid * n_out) on valid entries, 0 elsewhere; loss sum.
+__global__ void k_mse(const float* __restrict__ Yo, const float* __restrict__ T, int64_t rows, int64_t valid,
+                      int n_out, int dout, __nv_bfloat16* dY, double* loss) {
+  double part = 0.0;
+  const float scale = 2.0f / (float)((double)valid * n_out);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows * dout; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / dout;
+    const int j = (int)(i - r * dout);
+    float g = 0.f;
+    if (r < valid && j < n_out) {
+      const float d = Yo[i] - T[i];
+      g = scale * d;
+      part += (double)d * d;
+    }
+    dY[i] = __float2bfloat16(g);
+  }
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(loss, part);
+}
+
+// db[n] = sum_r dZ[r][n]
+__global__ void k_colsum(const __nv_bfloat16* __restrict__ dZ, int64_t rows, int N, float* db) {
+  const int n = blockIdx.x;
+  float s = 0.f;
+  for (int64_t r = threadIdx.x; r < rows; r += blockDim.x) s += __bfloat162float(dZ[r * N + n]);
+  __shared__ float sh[32];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) t += sh[w];
+    db[n] = t;
+  }
+}
+
+// Adam (Kingma and Ba, 2015) on every master parameter; refreshes the bf16
+// copies of the weight matrices.  Padded entries have zero gradient and stay 0.
+__global__ void k_adam(float* p, float* m, float* v, const float* g, size_t n, float lr, float b1, float b2, float eps,
+                       float c1, float c2) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+
+__global__ void k_to_bf16(const float* __restrict__ src, __nv_bfloat16* dst, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = __float2bfloat16(src[i]);
+}
+
+int rup(int a, int b) { return (a + b - 1) / b * b; }
+
+hsm_status mlp_fail(Mlp& m, hsm_status s, const std::string& msg) {
+  m.last_error = msg;
+  set_global_error(msg);
+  return s;
+}
+
+#define MLP_CUDA(call)                                                                                        \
+  do {                                                                                                        \
+    cudaError_t e_ = (call);                                                                                  \
+    if (e_ != cudaSuccess)                                                                                    \
+      return mlp_fail(m, e_ == cudaErrorMemoryAllocation ? HSM_ENOMEM : HSM_ECUDA,                             \
+                      std::string(#call) + ": " + cudaGetErrorString(e_));                                    \
+  } while (0)
+
+hsm_status ensure_cap(Mlp& m, int64_t rows) {
+  if (rows <= m.cap) return HSM_OK;
+  cudaStream_t s = m.stream;
+  dev_free(&m.X, s);
+  for (auto& h : m.H) dev_free(&h, s);
+  for (auto& z : m.Z) dev_free(&z, s);
+  dev_free(&m.Yout, s);
+  dev_free(&m.T, s);
+  dev_free(&m.dA, s);
+  dev_free(&m.dB, s);
+  int wmax = 0;
+  for (int l = 0; l < m.nl; ++l) wmax = std::max(wmax, std::max(m.din[l], m.dout[l]));
+  MLP_CUDA(dev_alloc(&m.X, (size_t)rows * m.din[0], s));
+  m.H.assign(m.nl - 1, nullptr);
+  m.Z.assign(m.nl - 1, nullptr);
+  for (int l = 0; l < m.nl - 1; ++l) {
+    MLP_CUDA(dev_alloc(&m.H[l], (size_t)rows * m.dout[l], s));
+    MLP_CUDA(dev_alloc(&m.Z[l], (size_t)rows * m.dout[l], s));
+  }
+  MLP_CUDA(dev_alloc(&m.Yout, (size_t)rows * m.dout[m.nl - 1], s));
+  MLP_CUDA(dev_alloc(&m.T, (size_t)rows * m.dout[m.nl - 1], s));
+  MLP_CUDA(dev_alloc(&m.dA, (size_t)rows * wmax, s));
+  MLP_CUDA(dev_alloc(&m.dB, (size_t)rows * wmax, s));
+  m.cap = rows;
+  return HSM_OK;
+}
+
+hsm_status refresh_bf16(Mlp& m) {
+  for (int l = 0; l < m.nl; ++l) {
+    const size_t n = (size_t)m.dout[l] * m.din[l];
+    k_to_bf16<<<(int)std::min<size_t>(ceil_div(n, 256), 4096), 256, 0, m.stream>>>(m.master + m.w_off[l],
+                                                                                    m.wbf + m.wbf_off[l], n);
+  }
+  MLP_CUDA(cudaGetLastError());
+  return HSM_OK;
+}
+
+// Forward pass of ``rows`` packed rows (m.X filled); output in m.Yout.
+hsm_status forward(Mlp& m, int64_t rows) {
+  const __nv_bfloat16* in = m.X;
+  for (int l = 0; l < m.nl; ++l) {
+    GemmArgs g{};
+    g.A = in;
+    g.lda = m.din[l];
+    g.B = m.wbf + m.wbf_off[l];
+    g.ldb = m.din[l];
+    g.M = (int)rows;
+    g.N = m.dout[l];
+    g.K = m.din[l];
+    g.bias = m.master + m.b_off[l];
+    if (l < m.nl - 1) {
+      g.Ch = m.H[l];
+      g.Zout = m.Z[l];
+      MLP_CUDA((gemm<false, false, EPI_BIAS_GELU>(g, m.stream)));
+      in = m.H[l];
+    } else {
+      g.Cf = m.Yout;
+      MLP_CUDA((gemm<false, false, EPI_BIAS>(g, m.stream)));
+    }
+  }
+  return HSM_OK;
+}
+
+// Backward pass after forward(); gradients (fp32, padded layout) into m.grad.
+hsm_status backward(Mlp& m, int64_t rows, int64_t valid) {
+  cudaStream_t s = m.stream;
+  const int L = m.nl;
+  MLP_CUDA(cudaMemsetAsync(m.loss, 0, sizeof(double), s));
+  k_mse<<<(int)std::min<int64_t>(ceil_div(rows * m.dout[L - 1], 256), 2048), 256, 0, s>>>(
+      m.Yout, m.T, rows, valid, m.n_out, m.dout[L - 1], m.dA, m.loss);
+  MLP_CUDA(cudaGetLastError());
+  __nv_bfloat16* dZ = m.dA;
+  __nv_bfloat16* dnext = m.dB;
+  for (int l = L - 1; l >= 0; --l) {
+    const __nv_bfloat16* Hprev = l == 0 ? m.X : m.H[l - 1];
+    // dW_l = dZ^T Hprev : M = dout, N = din, K = rows
+    GemmArgs gw{};
+    gw.A = dZ;
+    gw.lda = m.dout[l];
+    gw.B = Hprev;
+    gw.ldb = m.din[l];
+    gw.M = m.dout[l];
+    gw.N = m.din[l];
+    gw.K = (int)rows;
+    gw.Cf = m.grad + m.w_off[l];
+    MLP_CUDA((gemm<true, true, EPI_F32>(gw, s)));
+    k_colsum<<<m.dout[l], 256, 0, s>>>(dZ, rows, m.dout[l], m.grad + m.b_off[l]);
+    MLP_CUDA(cudaGetLastError());
+    if (l > 0) {
+      // dZ_{l-1} = (dZ_l W_l) * GELU'(Z_{l-1}) : M = rows, N = din, K = dout
+      GemmArgs gx{};
+      gx.A = dZ;
+      gx.lda = m.dout[l];
+      gx.B = m.wbf + m.wbf_off[l];
+      gx.ldb = m.din[l];
+      gx.M = (int)rows;
+      gx.N = m.din[l];
+      gx.K = m.dout[l];
+      gx.Zin = m.Z[l - 1];
+      gx.Ch = dnext;
+      MLP_CUDA((gemm<false, true, EPI_DGELU>(gx, s)));
+      std::swap(dZ, dnext);
+    }
+  }
+  return HSM_OK;
+}
+
+}  // namespace
+}  // namespace hsm
+
+using namespace hsm;
+
+extern "C" {
+
+hsm_status hsm_mlp_create(hsm_mlp* out, int n_in, int hidden, int layers, int n_out, uint64_t seed, void* stream) {
+  if (!out) return set_error(nullptr, HSM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n_in < 1 || n_in > 256 || n_out < 1 || n_out > 512 || hidden < 1 || hidden > 2048 || layers < 1 || layers > 8)
+    return set_error(nullptr, HSM_EINVAL, "MLP sizes out of range");
+  hsm_mlp h = new (std::nothrow) hsm_mlp_s();
+  if (!h) return set_error(nullptr, HSM_ENOMEM, "host allocation failed");
+  Mlp& m = h->m;
+  m.n_in = n_in;
+  m.hidden = hidden;
+  m.layers = layers;
+  m.n_out = n_out;
+  m.nl = layers + 1;
+  m.stream = (cudaStream_t)stream;
+  const int hp = rup(hidden, 128);
+  for (int l = 0; l < m.nl; ++l) {
+    m.rin.push_back(l == 0 ? n_in : hidden);
+    m.rout.push_back(l == m.nl - 1 ? n_out : hidden);
+    m.din.push_back(l == 0 ? rup(n_in, 64) : hp);
+    m.dout.push_back(l == m.nl - 1 ? rup(n_out, 128) : hp);
+  }
+  size_t off = 0, offb = 0;
+  for (int l = 0; l < m.nl; ++l) {
+    m.w_off.push_back(off);
+    off += (size_t)m.dout[l] * m.din[l];
+    m.b_off.push_back(off);
+    off += m.dout[l];
+    m.wbf_off.push_back(offb);
+    offb += (size_t)m.dout[l] * m.din[l];
+  }
+  m.n_master = off;
+  m.n_wbf = offb;
+  cudaStream_t s = m.stream;
+  auto fail = [&](const char* what) {
+    hsm_mlp_destroy(h);
+    return set_error(nullptr, HSM_ENOMEM, what);
+  };
+  if (dev_alloc(&m.master, m.n_master, s) || dev_alloc(&m.adam_m, m.n_master, s) ||
+      dev_alloc(&m.adam_v, m.n_master, s) || dev_alloc(&m.grad, m.n_master, s) || dev_alloc(&m.wbf, m.n_wbf, s) ||
+      dev_alloc(&m.loss, 1, s))
+    return fail("MLP allocation failed");
+  // initialisation: uniform +-sqrt(6/fan_in)/2 on the real entries (seeded, on the host), zero bias
+  std::vector<float> host(m.n_master, 0.f);
+  uint64_t st = seed ? seed : 0x853c49e6748fea9bull;
+  auto next = [&]() {
+    st += 0x9e3779b97f4a7c15ull;
+    uint64_t z = st;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    z ^= z >> 31;
+    return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+  };
+  for (int l = 0; l < m.nl; ++l) {
+    const double lim = std::sqrt(6.0 / m.rin[l]) * 0.5;
+    for (int o = 0; o < m.rout[l]; ++o)
+      for (int i = 0; i < m.rin[l]; ++i) host[m.w_off[l] + (size_t)o * m.din[l] + i] = (float)((2.0 * next() - 1.0) * lim);
+  }
+  if (cudaMemcpyAsync(m.master, host.data(), m.n_master * sizeof(float), cudaMemcpyHostToDevice, s) ||
+      cudaMemsetAsync(m.adam_m, 0, m.n_master * sizeof(float), s) ||
+      cudaMemsetAsync(m.adam_v, 0, m.n_master * sizeof(float), s) || cudaStreamSynchronize(s))
+    return fail("MLP initialisation failed");
+  if (refresh_bf16(m) != HSM_OK) return fail("MLP initialisation failed");
+  *out = h;
+  return HSM_OK;
+}
+
+hsm_status hsm_mlp_destroy(hsm_mlp h) {
+  if (!h) return HSM_OK;
+  Mlp& m = h->m;
+  cudaStream_t s = m.stream;
+  dev_free(&m.master, s);
+  dev_free(&m.adam_m, s);
+  dev_free(&m.adam_v, s);
+  dev_free(&m.grad, s);
+  dev_free(&m.wbf, s);
+  dev_free(&m.loss, s);
+  dev_free(&m.X, s);
+  for (auto& x : m.H) dev_free(&x, s);
+  for (auto& x : m.Z) dev_free(&x, s);
+  dev_free(&m.Yout, s);
+  dev_free(&m.T, s);
+  dev_free(&m.dA, s);
+  dev_free(&m.dB, s);
+  cudaStreamSynchronize(s);
+  delete h;
+  return HSM_OK;
+}
+
+hsm_status hsm_mlp_param_count(hsm_mlp h, int64_t* count) {
+  if (!h || !count) return set_error(nullptr, HSM_EINVAL, "mlp and count are required");
+  const Mlp& m = h->m;
+  int64_t c = 0;
+  for (int l = 0; l < m.nl; ++l) c += (int64_t)m.rout[l] * m.rin[l] + m.rout[l];
+  *count = c;
+  return HSM_OK;
+}
+
+// packed (unpadded) host layout: per layer W [out][in] then b [out]
+static hsm_status pack_io(hsm_mlp h, float* host, const float* host_in, const float* dev_src, bool to_device) {
+  Mlp& m = h->m;
+  std::vector<float> pad(m.n_master, 0.f);
+  if (!to_device) MLP_CUDA(cudaMemcpyAsync(pad.data(), dev_src, m.n_master * sizeof(float), cudaMemcpyDeviceToHost, m.stream));
+  MLP_CUDA(cudaStreamSynchronize(m.stream));
+  size_t k = 0;
+  for (int l = 0; l < m.nl; ++l) {
+    for (int o = 0; o < m.rout[l]; ++o)
+      for (int i = 0; i < m.rin[l]; ++i) {
+        float& p = pad[m.w_off[l] + (size_t)o * m.din[l] + i];
+        if (to_device) p = host_in[k++];
+        else host[k++] = p;
+      }
+    for (int o = 0; o < m.rout[l]; ++o) {
+      float& p = pad[m.b_off[l] + o];
+      if (to_device) p = host_in[k++];
+      else host[k++] = p;
+    }
+  }
+  if (to_device) {
+    MLP_CUDA(cudaMemcpyAsync(m.master, pad.data(), m.n_master * sizeof(float), cudaMemcpyHostToDevice, m.stream));
+    MLP_CUDA(cudaStreamSynchronize(m.stream));
+    return refresh_bf16(m);
+  }
+  return HSM_OK;
+}
+
+hsm_status hsm_mlp_get_params(hsm_mlp h, float* host, int64_t count) {
+  int64_t c = 0;
+  if (!h || !host) return set_error(nullptr, HSM_EINVAL, "mlp and host buffer are required");
+  hsm_mlp_param_count(h, &c);
+  if (count != c) return set_error(nullptr, HSM_EINVAL, "count must equal hsm_mlp_param_count");
+  return pack_io(h, host, nullptr, h->m.master, false);
+}
+
+hsm_status hsm_mlp_set_params(hsm_mlp h, const float* host, int64_t count) {
+  int64_t c = 0;
+  if (!h || !host) return set_error(nullptr, HSM_EINVAL, "mlp and host buffer are required");
+  hsm_mlp_param_count(h, &c);
+  if (count != c) return set_error(nullptr, HSM_EINVAL, "count must equal hsm_mlp_param_count");
+  h->m.t = 0;
+  Mlp& m = h->m;
+  MLP_CUDA(cudaMemsetAsync(m.adam_m, 0, m.n_master * sizeof(float), m.stream));
+  MLP_CUDA(cudaMemsetAsync(m.adam_v, 0, m.n_master * sizeof(float), m.stream));
+  return pack_io(h, nullptr, host, nullptr, true);
+}
+
+hsm_status hsm_mlp_grad(hsm_mlp h, const float* X, const float* Y, int64_t count, float* grads_host, float* loss) {
+  if (!h || !X || !Y || count < 1) return set_error(nullptr, HSM_EINVAL, "mlp, X, Y and count >= 1 are required");
+  Mlp& m = h->m;
+  const int64_t rows = ceil_div(count, BM) * BM;
+  hsm_status st = ensure_cap(m, rows);
+  if (st != HSM_OK) return st;
+  k_pack<<<(int)std::min<int64_t>(ceil_div(rows, 256), 4096), 256, 0, m.stream>>>(
+      X, Y, count, m.n_in, m.n_out, m.din[0], m.dout[m.nl - 1], rows, 0, 0, 0, m.X, m.T);
+  MLP_CUDA(cudaGetLastError());
+  MLP_CUDA(cudaMemsetAsync(m.grad, 0, m.n_master * sizeof(float), m.stream));
+  if ((st = forward(m, rows)) != HSM_OK) return st;
+  if ((st = backward(m, rows, count)) != HSM_OK) return st;
+  double l = 0.0;
+  MLP_CUDA(cudaMemcpyAsync(&l, m.loss, sizeof(double), cudaMemcpyDeviceToHost, m.stream));
+  if (grads_host) {
+    st = pack_io(h, grads_host, nullptr, m.grad, false);
+    if (st != HSM_OK) return st;
+  }
+  MLP_CUDA(cudaStreamSynchronize(m.stream));
+  if (loss) *loss = (float)(l / ((double)count * m.n_out));
+  return HSM_OK;
+}
+
+hsm_status hsm_mlp_train(hsm_mlp h, const float* X, const float* Y, int64_t count, int steps, int batch, float lr,
+                         uint64_t seed, float* loss_log) {
+  if (!h || !X || !Y || count < 1 || steps < 0 || batch < 1 || !(lr > 0.f))
+    return set_error(nullptr, HSM_EINVAL, "invalid training arguments");
+  Mlp& m = h->m;
+  const int64_t rows = ceil_div(batch, BM) * BM;
+  hsm_status st = ensure_cap(m, rows);
+  if (st != HSM_OK) return st;
+  double* log_dev = nullptr;
+  if (loss_log) MLP_CUDA(dev_alloc(&log_dev, std::max(steps, 1), m.stream));
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  for (int it = 0; it < steps; ++it) {
+    k_pack<<<(int)std::min<int64_t>(ceil_div(rows, 256), 4096), 256, 0, m.stream>>>(
+        X, Y, count, m.n_in, m.n_out, m.din[0], m.dout[m.nl - 1], rows, seed ? seed : 1, m.t, 0, m.X, m.T);
+    if ((st = forward(m, rows)) != HSM_OK) break;
+    if ((st = backward(m, rows, rows)) != HSM_OK) break;
+    if (log_dev) MLP_CUDA(cudaMemcpyAsync(log_dev + it, m.loss, sizeof(double), cudaMemcpyDeviceToDevice, m.stream));
+    m.t += 1;
+    const float c1 = 1.f - std::pow(b1, (float)m.t), c2 = 1.f - std::pow(b2, (float)m.t);
+    k_adam<<<(int)std::min<size_t>(ceil_div(m.n_master, 256), 4096), 256, 0, m.stream>>>(
+        m.master, m.adam_m, m.adam_v, m.grad, m.n_master, lr, b1, b2, eps, c1, c2);
+    MLP_CUDA(cudaGetLastError());
+    if ((st = refresh_bf16(m)) != HSM_OK) break;
+  }
+  if (st == HSM_OK && log_dev) {
+    std::vector<double> l(steps);
+    MLP_CUDA(cudaMemcpyAsync(l.data(), log_dev, steps * sizeof(double), cudaMemcpyDeviceToHost, m.stream));
+    MLP_CUDA(cudaStreamSynchronize(m.stream));
+    for (int i = 0; i < steps; ++i) loss_log[i] = (float)(l[i] / ((double)rows * m.n_out));
+  }
+  dev_free(&log_dev, m.stream);
+  if (st == HSM_OK) MLP_CUDA(cudaStreamSynchronize(m.stream));
+  return st;
+}
+
+hsm_status hsm_mlp_predict(hsm_mlp h, const float* X, int64_t count, float* Y) {
+  if (!h || !X || !Y || count < 0) return set_error(nullptr, HSM_EINVAL, "mlp, X and Y are required");
+  Mlp& m = h->m;
+  const int64_t chunk = 1 << 18;
+  const int64_t rows = std::min<int64_t>(ceil_div(std::max<int64_t>(count, 1), BM) * BM, chunk);
+  hsm_status st = ensure_cap(m, rows);
+  if (st != HSM_OK) return st;
+  for (int64_t b = 0; b < count; b += chunk) {
+    const int64_t cnt = std::min(chunk, count - b);
+    const int64_t r = ceil_div(cnt, BM) * BM;
+    k_pack<<<(int)std::min<int64_t>(ceil_div(r, 256), 4096), 256, 0, m.stream>>>(
+        X + b * m.n_in, nullptr, cnt, m.n_in, m.n_out, m.din[0], m.dout[m.nl - 1], r, 0, 0, 0, m.X, nullptr);
+    MLP_CUDA(cudaGetLastError());
+    if ((st = forward(m, r)) != HSM_OK) return st;
+    MLP_CUDA(cudaMemcpy2DAsync(Y + b * m.n_out, m.n_out * sizeof(float), m.Yout, m.dout[m.nl - 1] * sizeof(float),
+                               m.n_out * sizeof(float), cnt, cudaMemcpyDeviceToDevice, m.stream));
+  }
+  return HSM_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Learned weights for a plan: features -> MLP -> FP64 projection -> fallback
+// ---------------------------------------------------------------------------
+namespace hsm {
+namespace {
+
+// Features of RBF-FD stencil positions (scaled offsets, node-major) and, when
+// Ylab is given, the scaled FP64 weights as labels ([op][node]).
+template <int DIM>
+__global__ void k_features(const double* __restrict__ coords, int64_t N, const int32_t* __restrict__ idx, int64_t G,
+                           int n, const int32_t* __restrict__ list, int64_t count, const double* __restrict__ w,
+                           const int* __restrict__ op_kind, int nops, float* X, float* Ylab) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t pos = list[t];
+    const int32_t c = idx[pos];
+    double s2 = 0.0;
+    for (int j = 0; j < n; ++j) {
+      const int32_t id = idx[(int64_t)j * G + pos];
+      double r2 = 0.0;
+      for (int k = 0; k < DIM; ++k) {
+        const double o = coords[k * N + id] - coords[k * N + c];
+        r2 += o * o;
+      }
+      s2 = fmax(s2, r2);
+    }
+    const double s = sqrt(s2), inv = 1.0 / s;
+    for (int j = 0; j < n; ++j) {
+      const int32_t id = idx[(int64_t)j * G + pos];
+      for (int k = 0; k < DIM; ++k) X[t * (n * DIM) + j * DIM + k] = (float)((coords[k * N + id] - coords[k * N + c]) * inv);
+    }
+    if (Ylab)
+      for (int o = 0; o < nops; ++o) {
+        const double sc = op_kind[o] == 3 ? s * s : s;
+        for (int j = 0; j < n; ++j) Ylab[t * (n * nops) + o * n + j] = (float)(w[((int64_t)o * n + j) * G + pos] * sc);
+      }
+  }
+}
+
+// FP64 projection w = w_hat + P (P^T P)^{-1} (l_p - P^T w_hat) in the scaled
+// variable, per stencil and operator; accepts when the pre-projection
+// relative residual is <= tau and the post-projection residual <= 1e-10.
+// One thread per stencil; P^T P is factored by Cholesky.  Weights are written
+// for every stencil; rejected ones are listed for the FP64 re-solve, which
+// overwrites them.
+__device__ __forceinline__ double lp_value(const int8_t* ex, int q, int dim, int kind) {
+  int deg = 0, mx = 0, which = -1;
+  for (int k = 0; k < dim; ++k) {
+    const int e = ex[q * dim + k];
+    deg += e;
+    if (e > mx) {
+      mx = e;
+      which = k;
+    }
+  }
+  if (kind == 3) return (deg == 2 && mx == 2) ? 2.0 : 0.0;
+  return (deg == 1 && which == kind) ? 1.0 : 0.0;
+}
+
+template <int DIM, int NN, int MP>
+__global__ void __launch_bounds__(128) k_project(const double* __restrict__ coords, int64_t N,
+                                                 const int32_t* __restrict__ idx, int64_t G,
+                                                 const int8_t* __restrict__ mono_exp, const int32_t* __restrict__ list,
+                                                 int64_t count, const float* __restrict__ Yp,
+                                                 const int* __restrict__ op_kind, int nops, double tau, double* w,
+                                                 int32_t* fail_list, int* fail_count, uint8_t* status) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t pos = list[t];
+    const int32_t c = idx[pos];
+    double xi[NN][DIM];
+    double s2 = 0.0;
+#pragma unroll
+    for (int j = 0; j < NN; ++j) {
+      const int32_t id = idx[(int64_t)j * G + pos];
+      double r2 = 0.0;
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) {
+        const double o = coords[k * N + id] - coords[k * N + c];
+        xi[j][k] = o;
+        r2 += o * o;
+      }
+      s2 = fmax(s2, r2);
+    }
+    const double s = sqrt(s2), inv = 1.0 / s;
+    double Pm[NN][MP];
+#pragma unroll
+    for (int j = 0; j < NN; ++j) {
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) xi[j][k] *= inv;
+#pragma unroll
+      for (int q = 0; q < MP; ++q) {
+        double v = 1.0;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k)
+          for (int e = 0; e < mono_exp[q * DIM + k]; ++e) v *= xi[j][k];
+        Pm[j][q] = v;
+      }
+    }
+    double Lc[MP][MP];
+#pragma unroll
+    for (int a = 0; a < MP; ++a)
+#pragma unroll
+      for (int b = 0; b <= a; ++b) {
+        double v = 0.0;
+#pragma unroll
+        for (int j = 0; j < NN; ++j) v = fma(Pm[j][a], Pm[j][b], v);
+        Lc[a][b] = v;
+      }
+    bool accept = true;
+#pragma unroll
+    for (int a = 0; a < MP; ++a) {  // Cholesky, lower triangle in place
+      double d = Lc[a][a];
+#pragma unroll
+      for (int k = 0; k < a; ++k) d -= Lc[a][k] * Lc[a][k];
+      if (!(d > 0.0)) accept = false;
+      d = sqrt(fmax(d, 1e-300));
+      Lc[a][a] = d;
+#pragma unroll
+      for (int b = a + 1; b < MP; ++b) {
+        double v = Lc[b][a];
+#pragma unroll
+        for (int k = 0; k < a; ++k) v -= Lc[b][k] * Lc[a][k];
+        Lc[b][a] = v / d;
+      }
+    }
+    for (int o = 0; o < nops; ++o) {
+      const int kind = op_kind[o];
+      double wh[NN];
+#pragma unroll
+      for (int j = 0; j < NN; ++j) wh[j] = (double)Yp[t * ((int64_t)NN * nops) + o * NN + j];
+      double y[MP], lpn = 0.0, rn = 0.0;
+#pragma unroll
+      for (int q = 0; q < MP; ++q) {
+        const double lp = lp_value(mono_exp, q, DIM, kind);
+        double v = lp;
+#pragma unroll
+        for (int j = 0; j < NN; ++j) v = fma(-Pm[j][q], wh[j], v);
+        y[q] = v;
+        lpn += lp * lp;
+        rn += v * v;
+      }
+      if (!(sqrt(rn) <= tau * sqrt(lpn))) accept = false;
+#pragma unroll
+      for (int a = 0; a < MP; ++a) {
+        double v = y[a];
+#pragma unroll
+        for (int k = 0; k < a; ++k) v -= Lc[a][k] * y[k];
+        y[a] = v / Lc[a][a];
+      }
+#pragma unroll
+      for (int a = MP - 1; a >= 0; --a) {
+        double v = y[a];
+#pragma unroll
+        for (int k = a + 1; k < MP; ++k) v -= Lc[k][a] * y[k];
+        y[a] = v / Lc[a][a];
+      }
+#pragma unroll
+      for (int j = 0; j < NN; ++j) {
+        double v = wh[j];
+#pragma unroll
+        for (int q = 0; q < MP; ++q) v = fma(Pm[j][q], y[q], v);
+        wh[j] = v;
+      }
+      // post-projection residual of the constraints
+#pragma unroll
+      for (int q = 0; q < MP; ++q) {
+        double v = -lp_value(mono_exp, q, DIM, kind);
+#pragma unroll
+        for (int j = 0; j < NN; ++j) v = fma(Pm[j][q], wh[j], v);
+        if (!(fabs(v) <= 1e-10)) accept = false;
+      }
+      const double sc = kind == 3 ? inv * inv : inv;
+#pragma unroll
+      for (int j = 0; j < NN; ++j) w[((int64_t)o * NN + j) * G + pos] = wh[j] * sc;
+    }
+    if (accept) {
+      if (status) status[c] = HSM_NODE_OK;
+    } else {
+      const int slot = atomicAdd(fail_count, 1);
+      fail_list[slot] = (int32_t)pos;
+    }
+  }
+}
+
+__global__ void k_mark_zero(const int32_t* __restrict__ list, int k, uint8_t* flag) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) flag[list[i]] = 0;
+}
+
+__global__ void k_learned_split(const int32_t* __restrict__ nodes, const uint8_t* __restrict__ is_boundary,
+                                int64_t G, int32_t* learn_list, int* learn_count, int32_t* fail_list, int* fail_count) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < G; p += (int64_t)gridDim.x * blockDim.x) {
+    const bool bnd = is_boundary && is_boundary[nodes[p]];
+    if (bnd) fail_list[atomicAdd(fail_count, 1)] = (int32_t)p;
+    else learn_list[atomicAdd(learn_count, 1)] = (int32_t)p;
+  }
+}
+
+}  // namespace
+
+hsm_status compute_rbf_weights_learned(hsm_plan p, uint8_t* status, int32_t* fail_list, int* fail_count) {
+  Mlp& m = p->mlp->m;
+  const int dim = p->dim, n = p->n;
+  if (m.n_in != n * dim || m.n_out != n * p->nops)
+    return set_error(p, HSM_EINVAL, "the attached predictor's sizes do not match the plan (2n inputs, nops*n outputs)");
+  cudaStream_t s = p->stream;
+  const int64_t G = p->rbf.count;
+  if (G == 0) return HSM_OK;
+  int32_t* learn = nullptr;
+  int* lcount = nullptr;
+  float *X = nullptr, *Y = nullptr;
+  int* kinds = nullptr;
+  HSM_CUDA(p, dev_alloc(&learn, G, s));
+  HSM_CUDA(p, dev_alloc(&lcount, 1, s));
+  HSM_CUDA(p, cudaMemsetAsync(lcount, 0, sizeof(int), s));
+  const int T = 256;
+  const int grid = (int)std::min<int64_t>(ceil_div(G, T), (int64_t)num_sms() * 8);
+  k_learned_split<<<grid, T, 0, s>>>(p->rbf.nodes, p->is_boundary, G, learn, lcount, fail_list, fail_count);
+  HSM_CUDA(p, cudaGetLastError());
+  int lc = 0;
+  HSM_CUDA(p, cudaMemcpyAsync(&lc, lcount, sizeof(int), cudaMemcpyDeviceToHost, s));
+  HSM_CUDA(p, cudaStreamSynchronize(s));
+  if (lc > 0) {
+    int kh[4] = {0, 0, 0, 0};
+    int o = 0;
+    for (int b = 0; b < 4; ++b)
+      if (p->op_mask & (1u << b)) kh[o++] = b;
+    HSM_CUDA(p, dev_alloc(&kinds, 4, s));
+    HSM_CUDA(p, cudaMemcpyAsync(kinds, kh, sizeof(kh), cudaMemcpyHostToDevice, s));
+    HSM_CUDA(p, dev_alloc(&X, (size_t)lc * n * dim, s));
+    HSM_CUDA(p, dev_alloc(&Y, (size_t)lc * n * p->nops, s));
+    const int gl = (int)std::min<int64_t>(ceil_div(lc, T), (int64_t)num_sms() * 8);
+    if (dim == 2)
+      k_features<2><<<gl, T, 0, s>>>(p->coords, p->N, p->rbf.idx, G, n, learn, lc, nullptr, kinds, p->nops, X, nullptr);
+    else
+      k_features<3><<<gl, T, 0, s>>>(p->coords, p->N, p->rbf.idx, G, n, learn, lc, nullptr, kinds, p->nops, X, nullptr);
+    HSM_CUDA(p, cudaGetLastError());
+    cudaStream_t old = m.stream;
+    m.stream = s;
+    hsm_status st = hsm_mlp_predict(p->mlp, X, lc, Y);
+    m.stream = old;
+    if (st != HSM_OK) return set_error(p, st, m.last_error);
+    const int gp = (int)std::min<int64_t>(ceil_div(lc, 128), (int64_t)num_sms() * 16);
+#define HSM_PROJ(D, NN, MP)                                                                                  \
+  k_project<D, NN, MP><<<gp, 128, 0, s>>>(p->coords, p->N, p->rbf.idx, G, p->mono_exp, learn, lc, Y, kinds, \
+                                          p->nops, 1e-1, p->rbf.w64, fail_list, fail_count, status)
+    if (dim == 2 && n == 12 && p->n_mono == 6) HSM_PROJ(2, 12, 6);
+    else return set_error(p, HSM_EINVAL, "learned weights support the 2D m = 2, n = 12 stencils");
+#undef HSM_PROJ
+    HSM_CUDA(p, cudaGetLastError());
+    p->launches += 4;
+  }
+  dev_free(&learn, s);
+  dev_free(&lcount, s);
+  dev_free(&X, s);
+  dev_free(&Y, s);
+  dev_free(&kinds, s);
+  return HSM_OK;
 }
 
 }  // namespace hsm
+
+extern "C" {
+
+hsm_status hsm_mlp_attach(hsm_plan p, hsm_mlp h) {
+  if (!p) return set_error(nullptr, HSM_EINVAL, "plan is NULL");
+  p->mlp = h;
+  return HSM_OK;
+}
+
+// Features and labels of the plan's interior RBF-FD stencils (training data).
+hsm_status hsm_plan_learned_data(hsm_plan p, float* X, float* Y, int64_t* count) {
+  if (!p || !count) return set_error(p, HSM_EINVAL, "plan and count are required");
+  if (!p->stencils_built) return set_error(p, HSM_ESTATE, "hsm_plan_build_stencils must come first");
+  cudaStream_t s = p->stream;
+  const int64_t G = p->rbf.count;
+  int32_t *learn = nullptr, *skip = nullptr;
+  int* cnt = nullptr;
+  HSM_CUDA(p, dev_alloc(&learn, G, s));
+  HSM_CUDA(p, dev_alloc(&skip, G, s));
+  HSM_CUDA(p, dev_alloc(&cnt, 2, s));
+  HSM_CUDA(p, cudaMemsetAsync(cnt, 0, 2 * sizeof(int), s));
+  if (G) {
+    k_learned_split<<<(int)std::min<int64_t>(ceil_div(G, 256), (int64_t)num_sms() * 8), 256, 0, s>>>(
+        p->rbf.nodes, p->is_boundary, G, learn, cnt, skip, cnt + 1);
+    HSM_CUDA(p, cudaGetLastError());
+  }
+  int lc[2] = {0, 0};
+  HSM_CUDA(p, cudaMemcpyAsync(lc, cnt, sizeof(lc), cudaMemcpyDeviceToHost, s));
+  HSM_CUDA(p, cudaStreamSynchronize(s));
+  *count = lc[0];
+  if (X && lc[0] > 0) {
+    if (Y && !p->weights_built) return set_error(p, HSM_ESTATE, "labels need computed weights");
+    int kh[4] = {0, 0, 0, 0};
+    int o = 0;
+    for (int b = 0; b < 4; ++b)
+      if (p->op_mask & (1u << b)) kh[o++] = b;
+    int* kinds = nullptr;
+    HSM_CUDA(p, dev_alloc(&kinds, 4, s));
+    HSM_CUDA(p, cudaMemcpyAsync(kinds, kh, sizeof(kh), cudaMemcpyHostToDevice, s));
+    // ascending positions keep the data order deterministic
+    int32_t* sorted = nullptr;
+    uint8_t* flag = nullptr;
+    HSM_CUDA(p, dev_alloc(&sorted, G, s));
+    HSM_CUDA(p, dev_alloc(&flag, G, s));
+    HSM_CUDA(p, cudaMemsetAsync(flag, 1, G, s));
+    // mark boundary positions (listed in skip) with 0, then select the rest in order
+    if (lc[1] > 0) k_mark_zero<<<(int)std::min<int64_t>(ceil_div(lc[1], 256), 1024), 256, 0, s>>>(skip, lc[1], flag);
+    HSM_CUDA(p, select_indices(flag, 1, G, sorted, nullptr, cnt, s));
+    const int gl = (int)std::min<int64_t>(ceil_div(lc[0], 256), (int64_t)num_sms() * 8);
+    if (p->dim == 2)
+      k_features<2><<<gl, 256, 0, s>>>(p->coords, p->N, p->rbf.idx, G, p->n, sorted, lc[0], p->rbf.w64, kinds,
+                                         p->nops, X, Y);
+    else
+      k_features<3><<<gl, 256, 0, s>>>(p->coords, p->N, p->rbf.idx, G, p->n, sorted, lc[0], p->rbf.w64, kinds,
+                                         p->nops, X, Y);
+    HSM_CUDA(p, cudaGetLastError());
+    dev_free(&sorted, s);
+    dev_free(&flag, s);
+    dev_free(&kinds, s);
+  }
+  dev_free(&learn, s);
+  dev_free(&skip, s);
+  dev_free(&cnt, s);
+  HSM_CUDA(p, cudaStreamSynchronize(s));
+  return HSM_OK;
+}
+
+}  // extern "C"

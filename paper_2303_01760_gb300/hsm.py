@@ -57,6 +57,16 @@ _SIGS = {
     "hsm_stepper_destroy": (C.c_int, [_p]),
     "hsm_rbf_weights_fp32r_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_uint, _p, _i64, _p, _i64, _p, _p,
                                                 _p]),
+    "hsm_mlp_create": (C.c_int, [C.POINTER(_p), C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint64, _p]),
+    "hsm_mlp_destroy": (C.c_int, [_p]),
+    "hsm_mlp_param_count": (C.c_int, [_p, C.POINTER(_i64)]),
+    "hsm_mlp_get_params": (C.c_int, [_p, _p, _i64]),
+    "hsm_mlp_set_params": (C.c_int, [_p, _p, _i64]),
+    "hsm_mlp_grad": (C.c_int, [_p, _p, _p, _i64, _p, C.POINTER(C.c_float)]),
+    "hsm_mlp_train": (C.c_int, [_p, _p, _p, _i64, C.c_int, C.c_int, C.c_float, C.c_uint64, _p]),
+    "hsm_mlp_predict": (C.c_int, [_p, _p, _i64, _p]),
+    "hsm_mlp_attach": (C.c_int, [_p, _p]),
+    "hsm_plan_learned_data": (C.c_int, [_p, _p, _p, C.POINTER(_i64)]),
 }
 HSM_NOALLOC_MAX_SYSTEMS = 1 << 20
 for _name, (_res, _args) in _SIGS.items():
@@ -111,6 +121,90 @@ def op_list(mask, dim):
     return names
 
 
+def _binom(a, b):
+    from math import comb
+
+    return comb(a, b)
+
+
+class MLP:
+    """Owns an hsm_mlp (the learned weight predictor)."""
+
+    def __init__(self, n_in=24, hidden=256, layers=3, n_out=36, seed=1, stream=None):
+        h_ = C.c_void_p()
+        check(lib.hsm_mlp_create(C.byref(h_), int(n_in), int(hidden), int(layers), int(n_out), int(seed),
+                                 stream_handle(stream)))
+        self.h = h_
+        self.n_in, self.n_out = n_in, n_out
+
+    def param_count(self):
+        c = _i64()
+        check(lib.hsm_mlp_param_count(self.h, C.byref(c)))
+        return c.value
+
+    def get_params(self):
+        import numpy as np
+
+        buf = np.empty(self.param_count(), dtype=np.float32)
+        check(lib.hsm_mlp_get_params(self.h, buf.ctypes.data_as(C.c_void_p), buf.size))
+        return buf
+
+    def set_params(self, flat):
+        import numpy as np
+
+        buf = np.ascontiguousarray(flat, dtype=np.float32)
+        check(lib.hsm_mlp_set_params(self.h, buf.ctypes.data_as(C.c_void_p), buf.size))
+
+    def grad(self, X, Y):
+        import numpy as np
+
+        g = np.empty(self.param_count(), dtype=np.float32)
+        loss = C.c_float()
+        check(lib.hsm_mlp_grad(self.h, ptr(X), ptr(Y), X.shape[0], g.ctypes.data_as(C.c_void_p), C.byref(loss)))
+        return float(loss.value), g
+
+    def train(self, X, Y, steps, batch=1024, lr=1e-3, seed=7):
+        import numpy as np
+
+        log = np.empty(max(steps, 1), dtype=np.float32)
+        check(lib.hsm_mlp_train(self.h, ptr(X), ptr(Y), X.shape[0], int(steps), int(batch), float(lr), int(seed),
+                                log.ctypes.data_as(C.c_void_p)))
+        return log[:steps]
+
+    def predict(self, X):
+        import torch
+
+        Y = torch.empty((X.shape[0], self.n_out), dtype=torch.float32, device=X.device)
+        check(lib.hsm_mlp_predict(self.h, ptr(X), X.shape[0], ptr(Y)))
+        return Y
+
+    def close(self):
+        if self.h:
+            lib.hsm_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def unpack_params(flat, n_in, hidden, layers, n_out):
+    """Packed parameter vector -> [(W [out, in], b [out]), ...] (float64)."""
+    import numpy as np
+
+    dims = [n_in] + [hidden] * layers + [n_out]
+    out, k = [], 0
+    for a, b in zip(dims[:-1], dims[1:]):
+        W = np.asarray(flat[k:k + a * b], dtype=np.float64).reshape(b, a)
+        k += a * b
+        bb = np.asarray(flat[k:k + b], dtype=np.float64)
+        k += b
+        out.append((W, bb))
+    return out
+
+
 class Plan:
     """Owns an hsm_plan.  ``coords`` (f64 [dim, N]), ``is_regular`` and
     ``is_boundary`` (u8 [N]) and ``normals`` (f64 [dim, N]) are CUDA tensors
@@ -121,6 +215,7 @@ class Plan:
         if op_mask is None:
             op_mask = HSM_DX | HSM_DY | HSM_LAP | (HSM_DZ if dim == 3 else 0)
         self.dim, self.N, self.op_mask = dim, N, op_mask
+        self.n = n if n else 2 * _binom(m + dim, m)
         self._keep = (coords, is_regular, is_boundary, normals)
         h_ = C.c_void_p()
         check(lib.hsm_plan_create(C.byref(h_), dim, N, ptr(coords), ptr(is_regular), ptr(is_boundary),
@@ -176,6 +271,27 @@ class Plan:
         n = _i64()
         check(lib.hsm_plan_profile(self.h, ms, C.byref(n)), self.h)
         return list(ms), n.value
+
+    def learned_data(self, labels=True):
+        """(X [count, d*n], Y [count, nops*n] or None) of the interior RBF-FD
+        stencils, float32 CUDA tensors."""
+        import torch
+
+        cnt = _i64()
+        check(lib.hsm_plan_learned_data(self.h, None, None, C.byref(cnt)), self.h)
+        dev = self._keep[0].device
+        X = Y = None
+        if cnt.value:
+            nops = bin(self.op_mask).count("1")
+            n = self.n
+            X = torch.empty((cnt.value, self.dim * n), dtype=torch.float32, device=dev)
+            Y = torch.empty((cnt.value, nops * n), dtype=torch.float32, device=dev) if labels else None
+            check(lib.hsm_plan_learned_data(self.h, ptr(X), ptr(Y), C.byref(cnt)), self.h)
+        return X, Y
+
+    def attach(self, mlp):
+        check(lib.hsm_mlp_attach(self.h, mlp.h if mlp is not None else None), self.h)
+        self._mlp = mlp
 
     def autotune(self, cache_path=None):
         check(lib.hsm_plan_autotune(self.h, cache_path.encode() if cache_path else None), self.h)

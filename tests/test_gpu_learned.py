@@ -1,0 +1,131 @@
+"""Learned weights (the specification's predictor; no counterpart in the
+paper): tensor-core MLP gradients and forward pass against the FP64 oracle,
+the FP64 consistency projection against the oracle's, and the trained
+predictor end to end (exact monomial reproduction, fallback, accuracy)."""
+import numpy as np
+import pytest
+
+from oracle import learned as ol
+from oracle import stencils as ost
+from oracle import weights as ow
+from paper_2303_01760_gb300 import nodesets
+
+from gpu_helpers import make_plan
+
+pytestmark = pytest.mark.gpu
+
+H, L = 256, 3
+TOL_BF16_GRAD = 5e-2   # BF16 operands/activations, FP32 accumulation, 4 layers
+TOL_BF16_FWD = 2e-2
+
+
+def _dataset(seeds, n=60, jitters=(0.0, 0.1, 0.2, 0.3)):
+    """Features/labels of interior stencils of Poisson-disk sets, from the
+    library's own FP64 weights (the plain solver)."""
+    import torch
+
+    Xs, Ys = [], []
+    for sd in seeds:
+        for j in jitters:
+            ns = nodesets.square_all_scattered(n=n, seed=sd, jitter=j)
+            plan, code, _ = make_plan(ns, m=2)
+            assert code == 0
+            X, Y = plan.learned_data()
+            Xs.append(X)
+            Ys.append(Y)
+            plan.close()
+    return torch.cat(Xs), torch.cat(Ys)
+
+
+def _oracle_params(mlp):
+    from paper_2303_01760_gb300 import hsm
+
+    return hsm.unpack_params(mlp.get_params(), 24, H, L, 36)
+
+
+def test_mlp_gradients_and_forward_match_oracle():
+    from paper_2303_01760_gb300 import hsm
+
+    X, Y = _dataset([nodesets.SEED_BASE + 60], jitters=(0.2,))
+    X, Y = X[:300].contiguous(), Y[:300].contiguous()
+    mlp = hsm.MLP(24, H, L, 36, seed=3)
+    P = _oracle_params(mlp)
+    Xn, Yn = X.double().cpu().numpy(), Y.double().cpu().numpy()
+    loss_ref, g_ref = ol.loss_and_grad(P, Xn, Yn)
+    loss, g = mlp.grad(X, Y)
+    assert abs(loss - loss_ref) <= TOL_BF16_FWD * loss_ref
+    G = hsm.unpack_params(g, 24, H, L, 36)
+    for (gw, gb), (rw, rb) in zip(G, g_ref):
+        ew = np.linalg.norm(gw - rw) / np.linalg.norm(rw)
+        eb = np.linalg.norm(gb - rb) / np.linalg.norm(rb)
+        assert ew <= TOL_BF16_GRAD and eb <= TOL_BF16_GRAD, (ew, eb)
+    out_ref, _, _ = ol.forward(P, Xn)
+    out = mlp.predict(X).double().cpu().numpy()
+    assert np.abs(out - out_ref).max() <= TOL_BF16_FWD * np.abs(out_ref).max()
+    mlp.close()
+
+
+def test_learned_weights_end_to_end():
+    import torch
+    from paper_2303_01760_gb300 import hsm
+
+    Xtr, Ytr = _dataset([nodesets.SEED_BASE + 61, nodesets.SEED_BASE + 62])
+    mlp = hsm.MLP(24, H, L, 36, seed=5)
+    log = mlp.train(Xtr, Ytr, steps=1500, batch=1024, lr=1e-3, seed=11)
+    assert log[-50:].mean() < 0.05 * log[:10].mean()
+
+    ns = nodesets.square_all_scattered(n=50, seed=nodesets.SEED_BASE + 63, jitter=0.15)
+    plan, code, status = make_plan(ns, m=2, prec=0)
+    plan.attach(mlp)
+    st = torch.full((ns.N,), 77, dtype=torch.uint8, device="cuda:0")
+    code = plan.compute_weights(hsm.HSM_PREC_LEARNED, st)
+    assert code == 0
+    q = plan.query()
+    status = st.cpu().numpy()
+    # oracle: stencils, exact weights, and the projection of the GPU's own MLP output
+    stn = ost.build_stencils(ns.coords, ns.is_regular, ns.is_boundary, ns.h, 12, normals=ns.normals)
+    inner = ns.is_boundary[stn["rbf_nodes"]] == 0
+    nodes, idx = stn["rbf_nodes"][inner], stn["rbf_idx"][inner]
+    W = ow.rbffd_weights(ns.coords, idx, 2)
+    Xte, _ = plan.learned_data(labels=False)
+    Ypred = mlp.predict(Xte).double().cpu().numpy()
+    w_proj, accept = ol.learned_weights(ns.coords, idx, 2, Ypred)
+    # GPU weights
+    got = {}
+    for op, bit in (("dx", 1), ("dy", 2), ("lap", 8)):
+        rp, col, val = [t.cpu().numpy() for t in plan.export_csr(bit)]
+        ix = rp[nodes][:, None] + np.arange(12)[None, :]
+        assert np.array_equal(col[ix], idx)
+        got[op] = val[ix]
+    gpu_accept = status[nodes] == hsm.HSM_NODE_OK
+    fallback = status[nodes] == hsm.HSM_NODE_LEARNED_SOLVE
+    assert np.all(gpu_accept | fallback)
+    # the fallback decision matches the oracle's (same predictions, same rule)
+    assert np.mean(gpu_accept == accept) > 0.995
+    both = gpu_accept & accept
+    for op in ("dx", "dy", "lap"):
+        scale = np.abs(w_proj[op][both]).max(1)
+        # projection parity: FP64 on both sides from the same predictions
+        assert (np.abs(got[op][both] - w_proj[op][both]).max(1) / scale).max() <= 1e-10
+        # fallback nodes carry the direct-solve weights
+        if fallback.any():
+            e = np.abs(got[op][fallback] - W[op][fallback]).max(1) / np.abs(W[op][fallback]).max(1)
+            assert e.max() <= 1e-10
+    # every accepted stencil reproduces all monomials of degree <= 2 exactly
+    xi, s = ow._scaled_offsets(ns.coords, idx[both])
+    Pm, lp = ol.constraint_system(xi, 2, ("dx", "dy", "lap"))
+    wsc = np.stack([got["dx"][both] * s[:, None], got["dy"][both] * s[:, None], got["lap"][both] * s[:, None] ** 2], 2)
+    assert ol.post_residual(wsc, Pm, lp).max() <= 1e-9
+    assert q["n_fallback"] == int(np.sum(status == hsm.HSM_NODE_LEARNED_SOLVE))
+    # accuracy on u = sin(pi x) cos(pi y): learned + projected against the direct solve
+    u, der = nodesets.field_sincos(ns.coords)
+    err_l = np.abs((got["lap"] * u[idx]).sum(1) - der["lap"][nodes])
+    err_d = np.abs((W["lap"] * u[idx]).sum(1) - der["lap"][nodes])
+    deep = np.minimum(ns.coords[:, nodes], 1 - ns.coords[:, nodes]).min(0) > 0.15
+    rel_w = np.median(np.abs(got["lap"][both] - W["lap"][both]).max(1) / np.abs(W["lap"][both]).max(1))
+    print(f"accept {gpu_accept.mean():.3f}  median rel weight diff {rel_w:.2e}  "
+          f"lap err learned {err_l[deep].max():.3e} direct {err_d[deep].max():.3e}")
+    assert gpu_accept.mean() > 0.5
+    assert err_l[deep].max() <= 5.0 * err_d[deep].max()
+    plan.close()
+    mlp.close()
