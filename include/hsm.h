@@ -232,12 +232,13 @@ hsm_status hsm_stepper_destroy(hsm_stepper st);
 
 /* ------------------------------------------------------------------------ */
 /* Learned RBF-FD weights (no counterpart in the paper: the specification's  */
-/* predictor).  An MLP maps the scaled offsets (x_i - x_c)/s of a stencil    */
-/* (node-major, 2n or 3n values) to its scaled weights (s w for derivatives, */
-/* s^2 w for the Laplacian, operator-major); its output is projected exactly  */
-/* onto the monomial reproduction constraints of Eq. 1 up to degree m, and a */
-/* stencil whose relative pre-projection residual exceeds 0.1 or whose       */
-/* post-projection residual exceeds 1e-10 is re-solved by the FP64 solve.    */
+/* predictor).  An MLP maps the scaled offsets (x_i - x_c)/s of a stencil,  */
+/* turned into a canonical frame Q (nearest neighbour on +x, the next one in */
+/* the upper half plane; 2D), to its scaled weights (Q (s w_dx, s w_dy),     */
+/* s^2 w_lap, operator-major).  The output is turned back with Q^T and       */
+/* projected exactly onto the monomial reproduction constraints of Eq. 1 up  */
+/* to degree m; a stencil whose relative pre-projection residual exceeds 1.5 */
+/* or whose post-projection residual exceeds 1e-10 is re-solved in FP64.     */
 /* Dense layers run on BF16 tensor cores with FP32 accumulation.             */
 /* ------------------------------------------------------------------------ */
 

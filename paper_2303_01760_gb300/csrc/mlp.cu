@@ -692,15 +692,47 @@ __global__ void k_features(const double* __restrict__ coords, int64_t N, const i
       s2 = fmax(s2, r2);
     }
     const double s = sqrt(s2), inv = 1.0 / s;
+    // canonical frame (2D): entry 1 onto +x, entry 2 into the upper half plane
+    double q00 = 1.0, q01 = 0.0, q10 = 0.0, q11 = 1.0;
+    if (DIM == 2) {
+      const int32_t i1 = idx[G + pos], i2 = idx[2 * G + pos];
+      const double vx = (coords[i1] - coords[c]) * inv, vy = (coords[N + i1] - coords[N + c]) * inv;
+      const double r = sqrt(vx * vx + vy * vy);
+      q00 = vx / r;
+      q01 = vy / r;
+      q10 = -q01;
+      q11 = q00;
+      const double x2 = (coords[i2] - coords[c]) * inv, y2 = (coords[N + i2] - coords[N + c]) * inv;
+      if (q10 * x2 + q11 * y2 < 0.0) {
+        q10 = -q10;
+        q11 = -q11;
+      }
+    }
     for (int j = 0; j < n; ++j) {
       const int32_t id = idx[(int64_t)j * G + pos];
-      for (int k = 0; k < DIM; ++k) X[t * (n * DIM) + j * DIM + k] = (float)((coords[k * N + id] - coords[k * N + c]) * inv);
+      if (DIM == 2) {
+        const double a = (coords[id] - coords[c]) * inv, b = (coords[N + id] - coords[N + c]) * inv;
+        X[t * (n * DIM) + j * DIM] = (float)(q00 * a + q01 * b);
+        X[t * (n * DIM) + j * DIM + 1] = (float)(q10 * a + q11 * b);
+      } else {
+        for (int k = 0; k < DIM; ++k)
+          X[t * (n * DIM) + j * DIM + k] = (float)((coords[k * N + id] - coords[k * N + c]) * inv);
+      }
     }
-    if (Ylab)
+    if (Ylab) {
       for (int o = 0; o < nops; ++o) {
         const double sc = op_kind[o] == 3 ? s * s : s;
         for (int j = 0; j < n; ++j) Ylab[t * (n * nops) + o * n + j] = (float)(w[((int64_t)o * n + j) * G + pos] * sc);
       }
+      if (DIM == 2 && nops >= 2 && op_kind[0] == 0 && op_kind[1] == 1)
+        for (int j = 0; j < n; ++j) {
+          float* yx = &Ylab[t * (n * nops) + j];
+          float* yy = &Ylab[t * (n * nops) + n + j];
+          const double a = w[(int64_t)j * G + pos] * s, b = w[((int64_t)n + j) * G + pos] * s;
+          *yx = (float)(q00 * a + q01 * b);
+          *yy = (float)(q10 * a + q11 * b);
+        }
+    }
   }
 }
 
@@ -754,6 +786,23 @@ __global__ void __launch_bounds__(128) k_project(const double* __restrict__ coor
     for (int j = 0; j < NN; ++j) {
 #pragma unroll
       for (int k = 0; k < DIM; ++k) xi[j][k] *= inv;
+    }
+    // canonical frame of the prediction (see k_features); derivative pairs
+    // are turned back with Q^T
+    double q00 = 1.0, q01 = 0.0, q10 = 0.0, q11 = 1.0;
+    if (DIM == 2) {
+      const double r = sqrt(xi[1][0] * xi[1][0] + xi[1][1] * xi[1][1]);
+      q00 = xi[1][0] / r;
+      q01 = xi[1][1] / r;
+      q10 = -q01;
+      q11 = q00;
+      if (q10 * xi[2][0] + q11 * xi[2][1] < 0.0) {
+        q10 = -q10;
+        q11 = -q11;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < NN; ++j) {
 #pragma unroll
       for (int q = 0; q < MP; ++q) {
         double v = 1.0;
@@ -794,7 +843,13 @@ __global__ void __launch_bounds__(128) k_project(const double* __restrict__ coor
       const int kind = op_kind[o];
       double wh[NN];
 #pragma unroll
-      for (int j = 0; j < NN; ++j) wh[j] = (double)Yp[t * ((int64_t)NN * nops) + o * NN + j];
+      for (int j = 0; j < NN; ++j) {
+        const double a = (double)Yp[t * ((int64_t)NN * nops) + j];
+        const double b = (double)Yp[t * ((int64_t)NN * nops) + NN + j];
+        if (DIM == 2 && kind == 0) wh[j] = q00 * a + q10 * b;
+        else if (DIM == 2 && kind == 1) wh[j] = q01 * a + q11 * b;
+        else wh[j] = (double)Yp[t * ((int64_t)NN * nops) + o * NN + j];
+      }
       double y[MP], lpn = 0.0, rn = 0.0;
 #pragma unroll
       for (int q = 0; q < MP; ++q) {
@@ -909,9 +964,9 @@ hsm_status compute_rbf_weights_learned(hsm_plan p, uint8_t* status, int32_t* fai
     const int gp = (int)std::min<int64_t>(ceil_div(lc, 128), (int64_t)num_sms() * 16);
 #define HSM_PROJ(D, NN, MP)                                                                                  \
   k_project<D, NN, MP><<<gp, 128, 0, s>>>(p->coords, p->N, p->rbf.idx, G, p->mono_exp, learn, lc, Y, kinds, \
-                                          p->nops, 1e-1, p->rbf.w64, fail_list, fail_count, status)
-    if (dim == 2 && n == 12 && p->n_mono == 6) HSM_PROJ(2, 12, 6);
-    else return set_error(p, HSM_EINVAL, "learned weights support the 2D m = 2, n = 12 stencils");
+                                          p->nops, 1.5, p->rbf.w64, fail_list, fail_count, status)
+    if (dim == 2 && n == 12 && p->n_mono == 6 && p->op_mask == (HSM_DX | HSM_DY | HSM_LAP)) HSM_PROJ(2, 12, 6);
+    else return set_error(p, HSM_EINVAL, "learned weights support 2D m = 2, n = 12 plans with ops dx, dy, lap");
 #undef HSM_PROJ
     HSM_CUDA(p, cudaGetLastError());
     p->launches += 4;

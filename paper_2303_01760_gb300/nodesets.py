@@ -388,15 +388,22 @@ def square_all_scattered(n=400, seed=SEED_BASE + 4, jitter=0.0):
     jitter*h*U(unit disk).  Training/test stencils of the learned predictor."""
     ns = _build(f"square-scattered-n{n}", 2, n, np.zeros((0, 3)), 0.0, 1.0, seed,
                 lambda a, s: (BC_T_NEUMANN, 0.0), lambda i: 0.0, 0.0)
-    if jitter > 0.0:
-        rng = np.random.default_rng(seed + 77)
-        inner = ns.is_boundary == 0
-        m = int(inner.sum())
-        th = rng.uniform(0, 2 * math.pi, m)
-        rr = np.sqrt(rng.uniform(0, 1, m)) * jitter * ns.h
-        ns.coords[0, inner] += rr * np.cos(th)
-        ns.coords[1, inner] += rr * np.sin(th)
-    return ns
+    return jittered(ns, jitter, seed + 77) if jitter > 0.0 else ns
+
+
+def jittered(ns, jitter, seed):
+    """Copy of a 2D node set with every interior node displaced by
+    jitter*h*U(unit disk) (seeded)."""
+    rng = np.random.default_rng(seed)
+    coords = ns.coords.copy()
+    inner = ns.is_boundary == 0
+    m = int(inner.sum())
+    th = rng.uniform(0, 2 * math.pi, m)
+    rr = np.sqrt(rng.uniform(0, 1, m)) * jitter * ns.h
+    coords[0, inner] += rr * np.cos(th)
+    coords[1, inner] += rr * np.sin(th)
+    return NodeSet(f"{ns.name}-j{jitter:g}", ns.dim, ns.h, coords, ns.is_regular.copy(), ns.is_boundary.copy(),
+                   ns.normals.copy(), ns.bc.copy(), ns.T_bc.copy(), ns.T_ref, ns.holes, ns.band)
 
 
 def scatter_fraction(ns: NodeSet) -> float:

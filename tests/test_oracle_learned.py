@@ -59,7 +59,7 @@ def _stencils(n_set=30, seed=nodesets.SEED_BASE + 40):
 def test_projection_fixed_point_and_constraints():
     ns, st = _stencils()
     W = ow.rbffd_weights(ns.coords, st, 2)
-    X, Y, s = ol.features_labels(ns.coords, st, W)
+    X, Y, s, Q = ol.features_labels(ns.coords, st, W)
     w_exact, acc = ol.learned_weights(ns.coords, st, 2, Y)
     assert acc.all()
     for op in ("dx", "dy", "lap"):
@@ -69,7 +69,8 @@ def test_projection_fixed_point_and_constraints():
     rng = np.random.default_rng(3)
     xi, _ = ow._scaled_offsets(ns.coords, st)
     Pm, lp = ol.constraint_system(xi, 2, ("dx", "dy", "lap"))
-    w_hat = Y.reshape(len(st), 3, 12).transpose(0, 2, 1) + 0.05 * rng.normal(size=(len(st), 12, 3))
+    w_hat = np.stack([W["dx"] * s[:, None], W["dy"] * s[:, None], W["lap"] * s[:, None] ** 2], 2)
+    w_hat = w_hat + 0.05 * rng.normal(size=(len(st), 12, 3))
     w, pre = ol.project(w_hat, Pm, lp)
     assert ol.post_residual(w, Pm, lp).max() <= 1e-12
     assert pre.max() > 0
@@ -86,9 +87,9 @@ def test_projection_fixed_point_and_constraints():
 def test_projection_rejects_out_of_distribution_predictions():
     ns, st = _stencils()
     W = ow.rbffd_weights(ns.coords, st, 2)
-    X, Y, s = ol.features_labels(ns.coords, st, W)
+    X, Y, s, Q = ol.features_labels(ns.coords, st, W)
     bad = Y.copy()
-    bad[:10] = 0.0  # predicts nothing: the pre-projection residual is 100 %
+    bad[:10] = 50.0  # grossly wrong predictions: far outside the constraint set
     _, acc = ol.learned_weights(ns.coords, st, 2, bad)
     assert not acc[:10].any() and acc[10:].all()
 
@@ -96,7 +97,7 @@ def test_projection_rejects_out_of_distribution_predictions():
 def test_training_reduces_loss():
     ns, st = _stencils()
     W = ow.rbffd_weights(ns.coords, st, 2)
-    X, Y, _ = ol.features_labels(ns.coords, st, W)
+    X, Y, _, _ = ol.features_labels(ns.coords, st, W)
     P = ol.init_params(24, 32, 2, 36, seed=5)
     l0 = ol.loss_and_grad(P, X, Y)[0]
     state = None
@@ -104,3 +105,22 @@ def test_training_reduces_loss():
         loss, g = ol.loss_and_grad(P, X, Y)
         P, state = ol.adam_step(P, g, state, lr=3e-3, t=t)
     assert ol.loss_and_grad(P, X, Y)[0] < 0.1 * l0
+
+
+def test_canonical_frame_is_orthogonal_and_canonical():
+    ns, st = _stencils()
+    W = ow.rbffd_weights(ns.coords, st, 2)
+    X, Y, s, Q = ol.features_labels(ns.coords, st, W)
+    assert np.allclose(np.einsum("bij,bkj->bik", Q, Q), np.eye(2)[None], atol=1e-14)
+    Xr = X.reshape(len(st), 12, 2)
+    assert np.all(np.abs(Xr[:, 1, 1]) <= 1e-14) and np.all(Xr[:, 1, 0] > 0) and np.all(Xr[:, 2, 1] >= 0)
+    # the derivative weights are a vector field: the canonical labels are the
+    # weights of the rotated stencil itself
+    xi_c = Xr
+    coords_c = np.concatenate([xi_c[b].T for b in range(3)], 1)
+    st_c = np.arange(36).reshape(3, 12)
+    Wc = ow.rbffd_weights(coords_c, st_c, 2)
+    for b in range(3):
+        assert np.allclose(Wc["dx"][b], Y[b, :12], atol=1e-9 * np.abs(Y[b]).max())
+        assert np.allclose(Wc["dy"][b], Y[b, 12:24], atol=1e-9 * np.abs(Y[b]).max())
+        assert np.allclose(Wc["lap"][b], Y[b, 24:], atol=1e-9 * np.abs(Y[b]).max())
