@@ -259,6 +259,9 @@ def run_gpu(args):
 
     # end to end through the C ABI from pinned host buffers
     e2e = run_e2e(ns, hsm, dev, stream, args)
+    # large-scale apply roofline and the learned-weight comparison
+    big = run_big_apply(hsm, nodesets, dev, stream, flush, args) if (rank == 0 and not args.no_extras) else None
+    learned = run_learned(hsm, nodesets, dev, stream, flush, args) if (rank == 0 and not args.no_extras) else None
 
     res = None
     if rank == 0:
@@ -284,6 +287,8 @@ def run_gpu(args):
                                                 np.mean(ph_a, 0).round(4).tolist()))},
             "counts": {"mon": q_h["n_mon"], "rbf": n_rbf_h, "demoted": q_h["n_demoted"]},
             "parity": gate,
+            "apply_roofline": big,
+            "learned": learned,
             "clocks": clocks,
             "tuning": {"note": "lanes per RBF-FD system and apply block size picked by hsm_plan_autotune "
                                "before the timed region"},
@@ -296,6 +301,168 @@ def run_gpu(args):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def hbm_peak():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def apply_bytes(plan_q, N, n_rbf, n_mon, wm, wr, nops, f32):
+    """Algorithmic bytes of one fused application: per node its index stream,
+    its weight streams, one read of u and the operator outputs."""
+    wb = 4 if f32 else 8
+    ub = 4 if f32 else 8
+    per = lambda W: 4 * W + wb * W * nops + ub + 8 * nops
+    return n_mon * per(wm) + n_rbf * per(wr)
+
+
+def run_big_apply(hsm, nodesets, dev, stream, flush, args):
+    """The 8M-node 2D workload shape (30 % scattered, m = 2): 12 x 12 tiled
+    copies of a unit square minus 8 holes (lattice h = 1/250, scattered band
+    0.09 around the holes).  Weights (FP64) throughput and the HBM roofline of
+    the fused operator application with f64 and f32 storage."""
+    import numpy as np
+    import torch
+
+    base = nodesets.cached(nodesets.square_holes, n=250, band=0.09)
+    ns = nodesets.tiled(base, 12, 12)
+    d = dict(c=torch.from_numpy(ns.coords).to(dev), r=torch.from_numpy(ns.is_regular).to(dev),
+             b=torch.from_numpy(ns.is_boundary).to(dev), n=torch.from_numpy(ns.normals).to(dev))
+    plan = hsm.Plan(d["c"], d["r"], d["b"], ns.h, m=2, normals=d["n"], stream=stream)
+    plan.set_timing(True)
+    plan.build_stencils()
+    plan.autotune(os.path.join(ROOT, "build", "hsm_tune.txt"))
+    res = {"workload": f"2D, {ns.N} nodes ({ns.n_scattered / ns.N:.1%} scattered): 12x12 tiled copies of a unit "
+                       "square minus 8 holes, lattice h=1/250, band 0.09, m=2 n=12",
+           "nodes": int(ns.N)}
+    ws = []
+    for prec, name in ((hsm.HSM_PREC_FP64, "fp64"), (hsm.HSM_PREC_FP32_REFINE, "fp32_refine")):
+        plan.compute_weights(prec)
+        ts = []
+        for _ in range(2):
+            flush.zero_()
+            plan.compute_weights(prec)
+            ph = plan.profile()[0]
+            ts.append(ph[1] + ph[2])
+        q = plan.query()
+        ws.append((name, float(np.mean(ts)), q["n_fallback"]))
+    res["weights_ms"] = {k: round(t, 3) for k, t, _ in ws}
+    res["weights_nodes_per_s"] = {k: ns.N / (t * 1e-3) for k, t, _ in ws}
+    res["fp32_refine_fallbacks"] = ws[1][2]
+    plan.compute_weights(hsm.HSM_PREC_FP64)
+    q = plan.query()
+    n_mon = q["n_mon"]
+    n_rbf = ns.N - n_mon
+    u = torch.from_numpy(nodesets.field_sincos(ns.coords)[0]).to(dev)
+    out = torch.empty((3, ns.N), dtype=torch.float64, device=dev)
+    peak, src = hbm_peak()
+    for name, uu, f32 in (("f64", u, False), ("f32", u.float(), True)):
+        plan.apply(uu, out=out)
+        ts = []
+        for _ in range(max(args.steps, 5)):
+            flush.zero_()
+            plan.apply(uu, out=out)
+            ts.append(plan.profile()[0][3])
+        t = float(np.median(ts))
+        b = apply_bytes(q, ns.N, n_rbf, n_mon, 5, 12, 3, f32)
+        gbs = b / (t * 1e-3) / 1e9
+        res[name] = {"ms": t, "algorithmic_bytes": int(b), "bytes_per_node": b / ns.N,
+                     "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak}
+    res["bound"] = "hbm"
+    res["peak_source"] = f"{src} (MEASURED_PEAKS.json hbm_gbs: STREAM-style copy)"
+    plan.close()
+    return res
+
+
+def run_learned(hsm, nodesets, dev, stream, flush, args):
+    """Learned + projected weights against the plain FP64 solve (the
+    predictor's workload shape): trained on about 3.6M interior stencils of
+    64 jittered copies (jitter 0-30 %) of one Poisson-disk set, tested on as
+    many stencils from a second set with disjoint seeds."""
+    import numpy as np
+    import torch
+
+    from oracle import learned as ol
+    from oracle import stencils as ost
+    from oracle import weights as ow
+
+    def plan_of(ns):
+        d = dict(c=torch.from_numpy(ns.coords).to(dev), r=torch.from_numpy(ns.is_regular).to(dev),
+                 b=torch.from_numpy(ns.is_boundary).to(dev), n=torch.from_numpy(ns.normals).to(dev))
+        p = hsm.Plan(d["c"], d["r"], d["b"], ns.h, m=2, normals=d["n"], stream=stream)
+        p._d = d
+        p.set_timing(True)
+        return p
+
+    t0 = time.perf_counter()
+    base_tr = nodesets.cached(nodesets.square_all_scattered, n=300, seed=nodesets.SEED_BASE + 700)
+    base_te = nodesets.cached(nodesets.square_all_scattered, n=300, seed=nodesets.SEED_BASE + 701)
+    tr = nodesets.tiled(base_tr, 8, 8, jitter=lambda k: 0.3 * k / 63, seed=1000)
+    te = nodesets.tiled(base_te, 8, 8, jitter=lambda k: 0.3 * ((k * 37) % 64) / 63, seed=2000)
+    ptr = plan_of(tr)
+    ptr.build_stencils()
+    ptr.compute_weights(hsm.HSM_PREC_FP64)
+    X, Y = ptr.learned_data()
+    ptr.close()
+    mlp = hsm.MLP(24, 256, 3, 36, seed=5, stream=stream)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for lr, steps in ((1e-3, 6000), (3e-4, 3000), (1e-4, 3000)):
+        log = mlp.train(X, Y, steps=steps, batch=4096, lr=lr, seed=int(lr * 1e7))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    del X, Y
+    pte = plan_of(te)
+    pte.build_stencils()
+    pte.attach(mlp)
+    times = {}
+    for prec, name in ((hsm.HSM_PREC_FP64, "fp64"), (hsm.HSM_PREC_LEARNED, "learned")):
+        pte.compute_weights(prec)
+        ts = []
+        for _ in range(2):
+            flush.zero_()
+            pte.compute_weights(prec)
+            ph = pte.profile()[0]
+            ts.append(ph[2])
+        times[name] = float(np.mean(ts))
+    st = torch.zeros(te.N, dtype=torch.uint8, device=dev)
+    pte.compute_weights(hsm.HSM_PREC_LEARNED, st)
+    q = pte.query()
+    n_rbf = te.N - q["n_mon"]
+    status = st.cpu().numpy()
+    # accuracy on a sample against the oracle's direct solve
+    rng = np.random.default_rng(5)
+    inner = np.flatnonzero(te.is_boundary == 0)
+    sample = np.sort(rng.choice(inner, 3000, replace=False))
+    stn = ost.build_stencils(te.coords, te.is_regular, te.is_boundary, te.h, 12, centers=sample,
+                             use_kdtree=True, normals=te.normals)
+    Wd = ow.rbffd_weights(te.coords, stn["rbf_idx"], 2)
+    rp, col, val = [t.cpu().numpy() for t in pte.export_csr(8)]
+    nodes = stn["rbf_nodes"]
+    ix = rp[nodes][:, None] + np.arange(12)[None, :]
+    wl = val[ix]
+    acc = status[nodes] == hsm.HSM_NODE_OK
+    rel = np.abs(wl - Wd["lap"]).max(1) / np.abs(Wd["lap"]).max(1)
+    local = te.coords[:, nodes] % ((300 + 2) / 300)
+    u, der = nodesets.field_sincos(te.coords % ((300 + 2) / 300))
+    deep = np.minimum(local, 1 - local).min(0) > 0.15
+    el = np.abs((wl * u[col[ix]]).sum(1) - der["lap"][nodes])[deep & acc]
+    ed = np.abs((Wd["lap"] * u[stn["rbf_idx"]]).sum(1) - der["lap"][nodes])[deep & acc]
+    pte.close()
+    mlp.close()
+    return {"workload": f"train {tr.N} nodes, test {te.N} nodes (interior scattered stencils, n=12, m=2)",
+            "train_s": round(t_train, 2), "final_train_loss": float(np.mean(log[-50:])),
+            "weights_ms": times, "rbf_weights_per_s": {k: n_rbf / (v * 1e-3) for k, v in times.items()},
+            "learned_over_fp64": times["fp64"] / times["learned"],
+            "accepted_fraction": float(np.mean(status[inner] == hsm.HSM_NODE_OK)),
+            "fallbacks": q["n_fallback"],
+            "lap_weight_rel_diff_median": float(np.median(rel[acc])) if acc.any() else None,
+            "lap_error_on_sincos_max": {"learned": float(el.max()) if el.size else None,
+                                        "fp64": float(ed.max()) if ed.size else None},
+            "setup_s": round(time.perf_counter() - t0, 1)}
 
 
 def parity_gate(ns, plan, u, u_np, n_sample=2000):
@@ -455,6 +622,7 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=20000)
     ap.add_argument("--ref-sample", type=int, default=5000)
     ap.add_argument("--kernels", action="store_true", help="profiling driver only (no JSON line)")
+    ap.add_argument("--no-extras", action="store_true", help="skip the 7M-node apply and learned sections")
     ap.add_argument("--all-rbffd", action="store_true", help="with --kernels: force every node to RBF-FD")
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32r"], help="with --kernels")
     args = ap.parse_args()

@@ -487,3 +487,27 @@ def cached(fn, *args, cache_dir=None, **kw):
              T_ref=ns.T_ref, holes=ns.holes, band=ns.band)
     os.replace(tmp, path)
     return ns
+
+
+def tiled(ns, nx, ny, jitter=None, seed=0):
+    """nx x ny copies of a 2D node set side by side, each shifted by a whole
+    number of lattice spacings (1 + 2h) so lattice nodes stay on one global
+    lattice; ``jitter`` (a callable copy index -> jitter fraction, or None)
+    displaces the interior nodes of each copy as ``jittered`` does.  Builds
+    million-node workloads from one Poisson-disk fill."""
+    n = int(round(1.0 / ns.h))
+    step = (n + 2) * ns.h
+    parts = []
+    for iy in range(ny):
+        for ix in range(nx):
+            k = iy * nx + ix
+            c = jittered(ns, jitter(k), seed + k) if jitter is not None and jitter(k) > 0 else ns
+            coords = c.coords.copy()
+            coords[0] += ix * step
+            coords[1] += iy * step
+            parts.append((coords, c))
+    cat = lambda f: np.concatenate([f(c) for _, c in parts], -1)
+    coords = np.concatenate([p[0] for p in parts], 1)
+    return NodeSet(f"{ns.name}-tiled{nx}x{ny}", ns.dim, ns.h, coords, cat(lambda c: c.is_regular),
+                   cat(lambda c: c.is_boundary), np.concatenate([c.normals for _, c in parts], 1),
+                   cat(lambda c: c.bc), cat(lambda c: c.T_bc), ns.T_ref, ns.holes, ns.band)
