@@ -154,9 +154,10 @@ hsm_status hsm_plan_export_csr(hsm_plan plan, unsigned op, int64_t* row_ptr, int
                                double* val);
 
 /* Applies the operators of op_mask (a subset of the plan's) to one field,
- * Eq. 1: out[o][c] = sum_i w_o[c][i] u[idx[c][i]], accumulated in FP64.
- *   in_dtype  HSM_F64: u is f64 [N] and the FP64 weights are used;
- *             HSM_F32: u is f32 [N] and FP32 copies of the weights are used
+ * Eq. 1: out[o][c] = sum_i w_o[c][i] u[idx[c][i]], stored in FP64.
+ *   in_dtype  HSM_F64: u is f64 [N], FP64 weights, FP64 sums;
+ *             HSM_F32: u is f32 [N], FP32 copies of the weights, FP32 sums
+ *             (error within (n+2) 2^-24 sum |w u| of the exact sum)
  *   u         device [N]
  *   out       device f64 [popcount(op_mask)][N]                             */
 hsm_status hsm_apply(hsm_plan plan, unsigned op_mask, hsm_dtype in_dtype, const void* u,

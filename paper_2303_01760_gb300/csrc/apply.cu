@@ -4,8 +4,7 @@
 // (width 2d+1), the rest the RBF-FD group (width n), so regular and scattered
 // stencils of uneven size share one grid.  One thread owns one stencil and
 // all requested operators: the index stream is read once, every weight stream
-// once, the field gathered once per stencil entry, and the sums are kept in
-// FP64.  Index and weight arrays are index-major ([j][node] and
+// once, and the field gathered once per stencil entry.  Index and weight arrays are index-major ([j][node] and
 // [op][j][node]), so consecutive threads read consecutive addresses (fully
 // coalesced 128-byte lines); the gathered field values come from L1/L2 because
 // nodes are spatially sorted.
@@ -32,40 +31,45 @@ __device__ __forceinline__ T ldg_stream(const T* p) {
   return __ldcs(p);
 }
 
+// The stencil sum runs in the storage type (FP64 for f64 fields; FP32 for
+// f32 fields, whose n-term sums stay within (n+2) 2^-24 of the exact sum
+// relative to sum |w u|, and whose FP32 pipe is 64x wider than the FP64 one
+// on this part); every output is stored in FP64.
 template <int W, int NOPS, typename TU, typename TW>
 __device__ __forceinline__ void apply_one(const ApplyGroup& g, int width, int64_t p, Slots<NOPS> sl,
                                           const TU* __restrict__ u, double* __restrict__ out, int64_t N) {
+  typedef TW Acc;
   const int Wd = W > 0 ? W : width;
   const TW* __restrict__ w = reinterpret_cast<const TW*>(g.w);
   const int64_t G = g.count;
-  double acc[NOPS];
+  Acc acc[NOPS];
 #pragma unroll
-  for (int o = 0; o < NOPS; ++o) acc[o] = 0.0;
+  for (int o = 0; o < NOPS; ++o) acc[o] = Acc(0);
   if (W > 0) {
     int32_t id[W > 0 ? W : 1];
 #pragma unroll
     for (int j = 0; j < (W > 0 ? W : 1); ++j) id[j] = ldg_stream(g.idx + (int64_t)j * G + p);
-    double uv[W > 0 ? W : 1];
+    Acc uv[W > 0 ? W : 1];
 #pragma unroll
-    for (int j = 0; j < (W > 0 ? W : 1); ++j) uv[j] = (double)__ldg(u + id[j]);
+    for (int j = 0; j < (W > 0 ? W : 1); ++j) uv[j] = (Acc)__ldg(u + id[j]);
 #pragma unroll
     for (int o = 0; o < NOPS; ++o) {
       const TW* wo = w + (int64_t)sl.s[o] * Wd * G + p;
 #pragma unroll
-      for (int j = 0; j < (W > 0 ? W : 1); ++j) acc[o] = fma((double)ldg_stream(wo + (int64_t)j * G), uv[j], acc[o]);
+      for (int j = 0; j < (W > 0 ? W : 1); ++j) acc[o] = fma((Acc)ldg_stream(wo + (int64_t)j * G), uv[j], acc[o]);
     }
   } else {
     for (int j = 0; j < Wd; ++j) {
       const int32_t id = ldg_stream(g.idx + (int64_t)j * G + p);
-      const double uv = (double)__ldg(u + id);
+      const Acc uv = (Acc)__ldg(u + id);
 #pragma unroll
       for (int o = 0; o < NOPS; ++o)
-        acc[o] = fma((double)ldg_stream(w + ((int64_t)sl.s[o] * Wd + j) * G + p), uv, acc[o]);
+        acc[o] = fma((Acc)ldg_stream(w + ((int64_t)sl.s[o] * Wd + j) * G + p), uv, acc[o]);
     }
   }
   const int32_t node = g.nodes[p];
 #pragma unroll
-  for (int o = 0; o < NOPS; ++o) __stcs(out + (int64_t)o * N + node, acc[o]);
+  for (int o = 0; o < NOPS; ++o) __stcs(out + (int64_t)o * N + node, (double)acc[o]);
 }
 
 template <int WM, int WR, int NOPS, typename TU, typename TW>

@@ -742,87 +742,61 @@ __global__ void k_features(const double* __restrict__ coords, int64_t N, const i
 // One thread per stencil; P^T P is factored by Cholesky.  Weights are written
 // for every stencil; rejected ones are listed for the FP64 re-solve, which
 // overwrites them.
-__device__ __forceinline__ double lp_value(const int8_t* ex, int q, int dim, int kind) {
-  int deg = 0, mx = 0, which = -1;
-  for (int k = 0; k < dim; ++k) {
-    const int e = ex[q * dim + k];
-    deg += e;
-    if (e > mx) {
-      mx = e;
-      which = k;
-    }
-  }
-  if (kind == 3) return (deg == 2 && mx == 2) ? 2.0 : 0.0;
-  return (deg == 1 && which == kind) ? 1.0 : 0.0;
-}
-
-template <int DIM, int NN, int MP>
-__global__ void __launch_bounds__(128) k_project(const double* __restrict__ coords, int64_t N,
-                                                 const int32_t* __restrict__ idx, int64_t G,
-                                                 const int8_t* __restrict__ mono_exp, const int32_t* __restrict__ list,
-                                                 int64_t count, const float* __restrict__ Yp,
-                                                 const int* __restrict__ op_kind, int nops, double tau, double* w,
-                                                 int32_t* fail_list, int* fail_count, uint8_t* status) {
+// Specialised to 2D, m = 2 (basis 1, x, y, x^2, xy, y^2 in graded
+// lexicographic order) so that every loop has compile-time bounds.
+template <int NN>
+__global__ void __launch_bounds__(128) k_project2d(const double* __restrict__ coords, int64_t N,
+                                                   const int32_t* __restrict__ idx, int64_t G,
+                                                   const int32_t* __restrict__ list, int64_t count,
+                                                   const float* __restrict__ Yp, double tau, double* w,
+                                                   int32_t* fail_list, int* fail_count, uint8_t* status) {
+  constexpr int MP = 6;
+  // L p at the centre: d/dx -> (0,1,0,0,0,0), d/dy -> (0,0,1,0,0,0),
+  // Laplacian -> (0,0,0,2,0,2)
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t pos = list[t];
     const int32_t c = idx[pos];
-    double xi[NN][DIM];
+    double xs[NN], ys[NN];
     double s2 = 0.0;
+    const double cx = coords[c], cy = coords[N + c];
 #pragma unroll
     for (int j = 0; j < NN; ++j) {
       const int32_t id = idx[(int64_t)j * G + pos];
-      double r2 = 0.0;
-#pragma unroll
-      for (int k = 0; k < DIM; ++k) {
-        const double o = coords[k * N + id] - coords[k * N + c];
-        xi[j][k] = o;
-        r2 += o * o;
-      }
-      s2 = fmax(s2, r2);
+      xs[j] = coords[id] - cx;
+      ys[j] = coords[N + id] - cy;
+      s2 = fmax(s2, xs[j] * xs[j] + ys[j] * ys[j]);
     }
     const double s = sqrt(s2), inv = 1.0 / s;
-    double Pm[NN][MP];
 #pragma unroll
     for (int j = 0; j < NN; ++j) {
-#pragma unroll
-      for (int k = 0; k < DIM; ++k) xi[j][k] *= inv;
+      xs[j] *= inv;
+      ys[j] *= inv;
     }
     // canonical frame of the prediction (see k_features); derivative pairs
     // are turned back with Q^T
-    double q00 = 1.0, q01 = 0.0, q10 = 0.0, q11 = 1.0;
-    if (DIM == 2) {
-      const double r = sqrt(xi[1][0] * xi[1][0] + xi[1][1] * xi[1][1]);
-      q00 = xi[1][0] / r;
-      q01 = xi[1][1] / r;
-      q10 = -q01;
-      q11 = q00;
-      if (q10 * xi[2][0] + q11 * xi[2][1] < 0.0) {
-        q10 = -q10;
-        q11 = -q11;
-      }
+    const double r1 = sqrt(xs[1] * xs[1] + ys[1] * ys[1]);
+    const double q00 = xs[1] / r1, q01 = ys[1] / r1;
+    double q10 = -q01, q11 = q00;
+    if (q10 * xs[2] + q11 * ys[2] < 0.0) {
+      q10 = -q10;
+      q11 = -q11;
     }
-#pragma unroll
-    for (int j = 0; j < NN; ++j) {
-#pragma unroll
-      for (int q = 0; q < MP; ++q) {
-        double v = 1.0;
-#pragma unroll
-        for (int k = 0; k < DIM; ++k)
-          for (int e = 0; e < mono_exp[q * DIM + k]; ++e) v *= xi[j][k];
-        Pm[j][q] = v;
-      }
-    }
+    // G = P^T P (lower triangle), P row j = (1, x, y, x^2, xy, y^2)
     double Lc[MP][MP];
 #pragma unroll
     for (int a = 0; a < MP; ++a)
 #pragma unroll
-      for (int b = 0; b <= a; ++b) {
-        double v = 0.0;
+      for (int b = 0; b <= a; ++b) Lc[a][b] = 0.0;
 #pragma unroll
-        for (int j = 0; j < NN; ++j) v = fma(Pm[j][a], Pm[j][b], v);
-        Lc[a][b] = v;
-      }
+    for (int j = 0; j < NN; ++j) {
+      const double pj[MP] = {1.0, xs[j], ys[j], xs[j] * xs[j], xs[j] * ys[j], ys[j] * ys[j]};
+#pragma unroll
+      for (int a = 0; a < MP; ++a)
+#pragma unroll
+        for (int b = 0; b <= a; ++b) Lc[a][b] = fma(pj[a], pj[b], Lc[a][b]);
+    }
     bool accept = true;
+    double rdiag[MP];
 #pragma unroll
     for (int a = 0; a < MP; ++a) {  // Cholesky, lower triangle in place
       double d = Lc[a][a];
@@ -831,69 +805,68 @@ __global__ void __launch_bounds__(128) k_project(const double* __restrict__ coor
       if (!(d > 0.0)) accept = false;
       d = sqrt(fmax(d, 1e-300));
       Lc[a][a] = d;
+      rdiag[a] = 1.0 / d;
 #pragma unroll
       for (int b = a + 1; b < MP; ++b) {
         double v = Lc[b][a];
 #pragma unroll
         for (int k = 0; k < a; ++k) v -= Lc[b][k] * Lc[a][k];
-        Lc[b][a] = v / d;
+        Lc[b][a] = v * rdiag[a];
       }
     }
-    for (int o = 0; o < nops; ++o) {
-      const int kind = op_kind[o];
+    const float* yrow = Yp + t * ((int64_t)NN * 3);
+#pragma unroll 1
+    for (int o = 0; o < 3; ++o) {
       double wh[NN];
 #pragma unroll
       for (int j = 0; j < NN; ++j) {
-        const double a = (double)Yp[t * ((int64_t)NN * nops) + j];
-        const double b = (double)Yp[t * ((int64_t)NN * nops) + NN + j];
-        if (DIM == 2 && kind == 0) wh[j] = q00 * a + q10 * b;
-        else if (DIM == 2 && kind == 1) wh[j] = q01 * a + q11 * b;
-        else wh[j] = (double)Yp[t * ((int64_t)NN * nops) + o * NN + j];
+        const double a = (double)yrow[j], b = (double)yrow[NN + j];
+        const double c0 = o == 0 ? q00 : q01, c1 = o == 0 ? q10 : q11;
+        wh[j] = o < 2 ? c0 * a + c1 * b : (double)yrow[2 * NN + j];
       }
-      double y[MP], lpn = 0.0, rn = 0.0;
+      // r = l_p - P^T w_hat
+      double y[MP] = {0.0, o == 0 ? 1.0 : 0.0, o == 1 ? 1.0 : 0.0, o == 2 ? 2.0 : 0.0, 0.0, o == 2 ? 2.0 : 0.0};
 #pragma unroll
-      for (int q = 0; q < MP; ++q) {
-        const double lp = lp_value(mono_exp, q, DIM, kind);
-        double v = lp;
+      for (int j = 0; j < NN; ++j) {
+        const double pj[MP] = {1.0, xs[j], ys[j], xs[j] * xs[j], xs[j] * ys[j], ys[j] * ys[j]};
 #pragma unroll
-        for (int j = 0; j < NN; ++j) v = fma(-Pm[j][q], wh[j], v);
-        y[q] = v;
-        lpn += lp * lp;
-        rn += v * v;
+        for (int q = 0; q < MP; ++q) y[q] = fma(-pj[q], wh[j], y[q]);
       }
+      double rn = 0.0;
+#pragma unroll
+      for (int q = 0; q < MP; ++q) rn += y[q] * y[q];
+      const double lpn = o == 2 ? 8.0 : 1.0;
       if (!(sqrt(rn) <= tau * sqrt(lpn))) accept = false;
 #pragma unroll
-      for (int a = 0; a < MP; ++a) {
+      for (int a = 0; a < MP; ++a) {  // L z = r
         double v = y[a];
 #pragma unroll
         for (int k = 0; k < a; ++k) v -= Lc[a][k] * y[k];
-        y[a] = v / Lc[a][a];
+        y[a] = v * rdiag[a];
       }
 #pragma unroll
-      for (int a = MP - 1; a >= 0; --a) {
+      for (int a = MP - 1; a >= 0; --a) {  // L^T c = z
         double v = y[a];
 #pragma unroll
         for (int k = a + 1; k < MP; ++k) v -= Lc[k][a] * y[k];
-        y[a] = v / Lc[a][a];
+        y[a] = v * rdiag[a];
       }
+      // w = w_hat + P c, then the post-projection residual P^T w - l_p
+      double res[MP] = {0.0, o == 0 ? -1.0 : 0.0, o == 1 ? -1.0 : 0.0, o == 2 ? -2.0 : 0.0, 0.0, o == 2 ? -2.0 : 0.0};
+      const double sc = o == 2 ? inv * inv : inv;
 #pragma unroll
       for (int j = 0; j < NN; ++j) {
+        const double pj[MP] = {1.0, xs[j], ys[j], xs[j] * xs[j], xs[j] * ys[j], ys[j] * ys[j]};
         double v = wh[j];
 #pragma unroll
-        for (int q = 0; q < MP; ++q) v = fma(Pm[j][q], y[q], v);
-        wh[j] = v;
+        for (int q = 0; q < MP; ++q) v = fma(pj[q], y[q], v);
+#pragma unroll
+        for (int q = 0; q < MP; ++q) res[q] = fma(pj[q], v, res[q]);
+        w[((int64_t)o * NN + j) * G + pos] = v * sc;
       }
-      // post-projection residual of the constraints
 #pragma unroll
-      for (int q = 0; q < MP; ++q) {
-        double v = -lp_value(mono_exp, q, DIM, kind);
-#pragma unroll
-        for (int j = 0; j < NN; ++j) v = fma(Pm[j][q], wh[j], v);
-        if (!(fabs(v) <= 1e-10)) accept = false;
-      }
-      const double sc = kind == 3 ? inv * inv : inv;
-#pragma unroll
-      for (int j = 0; j < NN; ++j) w[((int64_t)o * NN + j) * G + pos] = wh[j] * sc;
+      for (int q = 0; q < MP; ++q)
+        if (!(fabs(res[q]) <= 1e-10)) accept = false;
     }
     if (accept) {
       if (status) status[c] = HSM_NODE_OK;
@@ -962,12 +935,10 @@ hsm_status compute_rbf_weights_learned(hsm_plan p, uint8_t* status, int32_t* fai
     m.stream = old;
     if (st != HSM_OK) return set_error(p, st, m.last_error);
     const int gp = (int)std::min<int64_t>(ceil_div(lc, 128), (int64_t)num_sms() * 16);
-#define HSM_PROJ(D, NN, MP)                                                                                  \
-  k_project<D, NN, MP><<<gp, 128, 0, s>>>(p->coords, p->N, p->rbf.idx, G, p->mono_exp, learn, lc, Y, kinds, \
-                                          p->nops, 1.5, p->rbf.w64, fail_list, fail_count, status)
-    if (dim == 2 && n == 12 && p->n_mono == 6 && p->op_mask == (HSM_DX | HSM_DY | HSM_LAP)) HSM_PROJ(2, 12, 6);
+    if (dim == 2 && n == 12 && p->n_mono == 6 && p->op_mask == (HSM_DX | HSM_DY | HSM_LAP))
+      k_project2d<12><<<gp, 128, 0, s>>>(p->coords, p->N, p->rbf.idx, G, learn, lc, Y, 1.5, p->rbf.w64, fail_list,
+                                         fail_count, status);
     else return set_error(p, HSM_EINVAL, "learned weights support 2D m = 2, n = 12 plans with ops dx, dy, lap");
-#undef HSM_PROJ
     HSM_CUDA(p, cudaGetLastError());
     p->launches += 4;
   }

@@ -45,6 +45,14 @@ struct hsm_stepper_s {
   unsigned* counters = nullptr;
   int blocks_mon = 0, blocks_rbf = 0, threads = 256;
   double c = 0.0;             // Lagrange multiplier of the bordered system (kept on device)
+  // CUDA graphs of the step phases, valid for the field pointers they were
+  // captured with: head = predictor + Krylov set-up + `head_chunks` chunks of
+  // Krylov iterations, chunk = one chunk, tail = correction + temperature
+  cudaGraphExec_t g_head = nullptr, g_chunk = nullptr, g_tail = nullptr;
+  cudaStream_t cap = nullptr;  // private stream the graphs are captured on
+  int head_chunks = 0;
+  const double *gv = nullptr, *gT = nullptr, *gp = nullptr;
+  int last_iters = 0;
 };
 
 namespace hsm {
@@ -557,38 +565,97 @@ StepArgs make_args(hsm_stepper st, double* v, double* T, double* p) {
   return a;
 }
 
+constexpr int kChunk = 16;  // Krylov iterations per captured chunk
+
+template <int DIM>
+void launch_chunk(const StepArgs& a, dim3 grid, dim3 blk, cudaStream_t s) {
+  for (int c = 0; c < kChunk; ++c) {
+    k_bicg_a<DIM><<<grid, blk, 0, s>>>(a);
+    k_bicg_b<DIM><<<grid, blk, 0, s>>>(a);
+    k_bicg_c<DIM><<<grid, blk, 0, s>>>(a);
+  }
+}
+
+template <typename F>
+cudaError_t capture(cudaStream_t s, cudaGraphExec_t* out, F&& body) {
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  body();
+  e = cudaStreamEndCapture(s, &g);
+  if (e != cudaSuccess) return e;
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  return e;
+}
+
+void drop_graphs(hsm_stepper st) {
+  for (cudaGraphExec_t* g : {&st->g_head, &st->g_chunk, &st->g_tail})
+    if (*g) {
+      cudaGraphExecDestroy(*g);
+      *g = nullptr;
+    }
+  st->head_chunks = 0;
+}
+
+// Each step runs as CUDA graphs: the head graph (predictor, Krylov set-up and
+// enough Krylov chunks for the previous step's iteration count plus one
+// chunk) is launched, the solver state is read once, further chunk graphs run
+// only if the solve has not converged, then the tail graph finishes the step.
+// Chunks after convergence cost only their launches: every Krylov kernel
+// returns at once when the converged flag is set.
 template <int DIM>
 hsm_status run_steps(hsm_stepper st, int n_steps, double* v, double* T, double* p, int* iters, bool* notconv) {
   hsm_plan pl = st->plan;
   cudaStream_t s = pl->stream;
   StepArgs a = make_args(st, v, T, p);
   const dim3 grid((unsigned)(st->blocks_mon + st->blocks_rbf)), blk(st->threads);
-  const int chunk = 16;
+  if (st->gv != v || st->gT != T || st->gp != p) {
+    drop_graphs(st);
+    st->gv = v;
+    st->gT = T;
+    st->gp = p;
+  }
+  // graphs are captured on a private stream (capture is not possible on the
+  // legacy default stream) and launched on the plan's stream
+  if (!st->cap) HSM_CUDA(pl, cudaStreamCreateWithFlags(&st->cap, cudaStreamNonBlocking));
+  cudaStream_t cs = st->cap;
+  if (!st->g_chunk) HSM_CUDA(pl, capture(cs, &st->g_chunk, [&] { launch_chunk<DIM>(a, grid, blk, cs); }));
+  if (!st->g_tail)
+    HSM_CUDA(pl, capture(cs, &st->g_tail, [&] {
+      k_correct_temperature<DIM><<<grid, blk, 0, cs>>>(a);
+      k_temperature_bc<<<grid, blk, 0, cs>>>(a);
+    }));
   KS host{};
+  const int max_chunks = (int)(st->phys.krylov_max_it / kChunk) + 2;
   for (int it = 0; it < n_steps; ++it) {
-    k_predictor<DIM><<<grid, blk, 0, s>>>(a);
-    k_krylov_init<DIM><<<grid, blk, 0, s>>>(a);
-    pl->launches += 2;
-    HSM_CUDA(pl, cudaGetLastError());
-    const int max_chunks = (int)(st->phys.krylov_max_it / chunk) + 2;
-    for (int ch = 0; ch < max_chunks; ++ch) {
-      for (int c = 0; c < chunk; ++c) {
-        k_bicg_a<DIM><<<grid, blk, 0, s>>>(a);
-        k_bicg_b<DIM><<<grid, blk, 0, s>>>(a);
-        k_bicg_c<DIM><<<grid, blk, 0, s>>>(a);
-        pl->launches += 3;
-      }
-      HSM_CUDA(pl, cudaGetLastError());
+    const int want = std::min(max_chunks, (st->last_iters + kChunk - 1) / kChunk + 1);
+    if (!st->g_head || st->head_chunks != want) {
+      if (st->g_head) cudaGraphExecDestroy(st->g_head);
+      st->g_head = nullptr;
+      HSM_CUDA(pl, capture(cs, &st->g_head, [&] {
+        k_predictor<DIM><<<grid, blk, 0, cs>>>(a);
+        k_krylov_init<DIM><<<grid, blk, 0, cs>>>(a);
+        for (int c = 0; c < want; ++c) launch_chunk<DIM>(a, grid, blk, cs);
+      }));
+      st->head_chunks = want;
+    }
+    HSM_CUDA(pl, cudaGraphLaunch(st->g_head, s));
+    pl->launches += 2 + 3 * kChunk * want;
+    int done_chunks = want;
+    for (;;) {
       HSM_CUDA(pl, cudaMemcpyAsync(&host, a.ks, sizeof(KS), cudaMemcpyDeviceToHost, s));
       HSM_CUDA(pl, cudaStreamSynchronize(s));
-      if (host.done != 0.0) break;
+      if (host.done != 0.0 || done_chunks >= max_chunks) break;
+      HSM_CUDA(pl, cudaGraphLaunch(st->g_chunk, s));
+      pl->launches += 3 * kChunk;
+      ++done_chunks;
     }
+    st->last_iters = (int)host.iter;
     if (iters) iters[it] = (int)host.iter;
     if (host.breakdown != 0.0 || host.rnorm2 > host.tol2 * host.bnorm2 * 1.0000001) *notconv = true;
-    k_correct_temperature<DIM><<<grid, blk, 0, s>>>(a);
-    k_temperature_bc<<<grid, blk, 0, s>>>(a);
+    HSM_CUDA(pl, cudaGraphLaunch(st->g_tail, s));
     pl->launches += 2;
-    HSM_CUDA(pl, cudaGetLastError());
   }
   HSM_CUDA(pl, cudaStreamSynchronize(s));
   return HSM_OK;
@@ -688,6 +755,8 @@ hsm_status hsm_step(hsm_stepper st, int n_steps, double* v, double* T, double* p
 hsm_status hsm_stepper_destroy(hsm_stepper st) {
   if (!st) return HSM_OK;
   cudaStream_t s = st->plan ? st->plan->stream : nullptr;
+  drop_graphs(st);
+  if (st->cap) cudaStreamDestroy(st->cap);
   dev_free(&st->wp_rbf, s);
   dev_free(&st->wn_rbf, s);
   dev_free(&st->minv, s);
