@@ -145,11 +145,30 @@ __device__ bool block_done(const StepArgs& a, int which, double (&vals)[Q], doub
   }
   __syncthreads();
   if (!last) return false;
+  // the last block sums every block's partials: thread t takes blocks
+  // t, t + blockDim, ... (a fixed order), then the block reduces
+  __threadfence();
+  double acc[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) acc[q] = 0.0;
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+#pragma unroll
+    for (int q = 0; q < Q; ++q) acc[q] += __ldcg(&a.partial[((int64_t)which * gridDim.x + b) * 4 + q]);
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    double x = acc[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) sh[wid][q] = x;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
-    for (int q = 0; q < Q; ++q) tot[q] = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b)
-      for (int q = 0; q < Q; ++q) tot[q] += __ldcg(&a.partial[((int64_t)which * gridDim.x + b) * 4 + q]);
+    const int nw = (blockDim.x + 31) / 32;
+    for (int q = 0; q < Q; ++q) {
+      double x = 0.0;
+      for (int i = 0; i < nw; ++i) x += sh[i][q];
+      tot[q] = x;
+    }
   }
   return threadIdx.x == 0;
 }
