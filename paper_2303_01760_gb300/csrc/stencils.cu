@@ -232,9 +232,12 @@ __global__ void k_cell_scatter(const double* __restrict__ coords, const uint8_t*
   }
 }
 
-// (d2, id) lexicographic key comparison.
+// (d2, id) lexicographic key comparison (integer compare of the d2 bits;
+// d2 is non-negative and finite).
 __device__ __forceinline__ bool key_less(double d2a, int32_t ia, double d2b, int32_t ib) {
-  return d2a < d2b || (d2a == d2b && ia < ib);
+  const unsigned long long a = (unsigned long long)__double_as_longlong(d2a);
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d2b);
+  return a < b || (a == b && ia < ib);
 }
 
 template <int DIM>
@@ -349,8 +352,11 @@ __global__ void k_knn(const double* __restrict__ coords, int64_t N, const uint8_
 // with the list (the 32 smallest of the 64 keys form a bitonic sequence that a
 // final bitonic merge sorts).  A round whose offers cannot enter the list is
 // skipped after a ballot.
+// Keys compare as integers: a non-negative finite double orders like its
+// bit pattern, so (bits(d2), id) is compared on the integer pipes instead of
+// the (narrow) FP64 pipe.
 struct Key {
-  double d;
+  unsigned long long d;  // bits of d2
   int32_t i;
 };
 __device__ __forceinline__ bool kless(const Key& a, const Key& b) { return a.d < b.d || (a.d == b.d && a.i < b.i); }
@@ -406,7 +412,7 @@ __global__ void __launch_bounds__(256) k_knn_warp(const double* __restrict__ coo
                                                   unsigned* flags) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  const Key INF{DBL_MAX, 0x7fffffff};
+  const Key INF{~0ull, 0x7fffffff};
   for (int64_t qi = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); qi < nq; qi += warps) {
     const int32_t c = queries[qi];
     const bool bnd_center = is_boundary && is_boundary[c];
@@ -462,7 +468,7 @@ __global__ void __launch_bounds__(256) k_knn_warp(const double* __restrict__ coo
         if (s_cur < s_end) {
           const int32_t id = sorted_id[s_cur];
           if (!(bnd_center && sorted_bnd[s_cur])) {
-            cand.d = sq_dist<DIM>(sorted_xyz + (int64_t)s_cur * kMaxDim, q);
+            cand.d = (unsigned long long)__double_as_longlong(sq_dist<DIM>(sorted_xyz + (int64_t)s_cur * kMaxDim, q));
             cand.i = id;
           }
           ++s_cur;
@@ -481,7 +487,7 @@ __global__ void __launch_bounds__(256) k_knn_warp(const double* __restrict__ coo
         if (!__any_sync(0xffffffffu, more)) break;
       }
       const Key nth = shfl_key(best, n - 1);
-      if (nth.d != DBL_MAX) {
+      if (nth.d != ~0ull) {
         double bound = DBL_MAX;
 #pragma unroll
         for (int k = 0; k < DIM; ++k) {
@@ -490,14 +496,14 @@ __global__ void __launch_bounds__(256) k_knn_warp(const double* __restrict__ coo
         }
         if (bound == DBL_MAX) break;
         bound *= (1.0 - 1e-9);
-        if (bound > 0.0 && nth.d < bound * bound) break;
+        if (bound > 0.0 && __longlong_as_double((long long)nth.d) < bound * bound) break;
       }
     }
-    const int cnt = __popc(__ballot_sync(0xffffffffu, best.d != DBL_MAX && lane < n));
+    const int cnt = __popc(__ballot_sync(0xffffffffu, best.d != ~0ull && lane < n));
     if (cnt < n && lane == 0) atomicOr(flags, kDevKnnShort);
     const int off = bnd_center ? 1 : 0;
     if (bnd_center && lane == 0) out_idx[qi] = c;
-    if (lane < n) out_idx[(int64_t)(lane + off) * nq + qi] = best.d != DBL_MAX ? best.i : c;
+    if (lane < n) out_idx[(int64_t)(lane + off) * nq + qi] = best.d != ~0ull ? best.i : c;
   }
 }
 
