@@ -344,169 +344,6 @@ __global__ void k_knn(const double* __restrict__ coords, int64_t N, const uint8_
   }
 }
 
-// ---- warp-per-query kNN (n <= 32) -----------------------------------------
-// The running top-n list is spread over the warp, lane i holding the i-th
-// smallest (d2, id) key (slots >= n hold +inf).  Each ring of cells is
-// scanned by the lanes in parallel; every round each lane offers one
-// candidate, the 32 offers are bitonic-sorted by warp shuffles and merged
-// with the list (the 32 smallest of the 64 keys form a bitonic sequence that a
-// final bitonic merge sorts).  A round whose offers cannot enter the list is
-// skipped after a ballot.
-// Keys compare as integers: a non-negative finite double orders like its
-// bit pattern, so (bits(d2), id) is compared on the integer pipes instead of
-// the (narrow) FP64 pipe.
-struct Key {
-  unsigned long long d;  // bits of d2
-  int32_t i;
-};
-__device__ __forceinline__ bool kless(const Key& a, const Key& b) { return a.d < b.d || (a.d == b.d && a.i < b.i); }
-__device__ __forceinline__ Key shfl_key(const Key& k, int src) {
-  Key o;
-  o.d = __shfl_sync(0xffffffffu, k.d, src);
-  o.i = __shfl_sync(0xffffffffu, k.i, src);
-  return o;
-}
-__device__ __forceinline__ Key shfl_key_xor(const Key& k, int m) {
-  Key o;
-  o.d = __shfl_xor_sync(0xffffffffu, k.d, m);
-  o.i = __shfl_xor_sync(0xffffffffu, k.i, m);
-  return o;
-}
-// sorts one key per lane ascending over the warp
-__device__ __forceinline__ Key warp_sort(Key k, int lane) {
-#pragma unroll
-  for (int size = 2; size <= 32; size <<= 1) {
-#pragma unroll
-    for (int j = size >> 1; j > 0; j >>= 1) {
-      const Key o = shfl_key_xor(k, j);
-      const bool up = (lane & size) == 0;
-      const bool low = (lane & j) == 0;
-      const bool take_min = (low == up);
-      const bool o_less = kless(o, k);
-      if (take_min ? o_less : !o_less) k = o;
-    }
-  }
-  return k;
-}
-// bitonic merge of a bitonic sequence held one key per lane (ascending result)
-__device__ __forceinline__ Key warp_merge(Key k, int lane) {
-#pragma unroll
-  for (int j = 16; j > 0; j >>= 1) {
-    const Key o = shfl_key_xor(k, j);
-    const bool low = (lane & j) == 0;
-    const bool o_less = kless(o, k);
-    if (low ? o_less : !o_less) k = o;
-  }
-  return k;
-}
-
-template <int DIM>
-__global__ void __launch_bounds__(256) k_knn_warp(const double* __restrict__ coords, int64_t N,
-                                                  const uint8_t* __restrict__ is_boundary,
-                                                  const double* __restrict__ normals, double h,
-                                                  const int32_t* __restrict__ queries, int64_t nq, int n_full,
-                                                  CellGrid cg, const int32_t* __restrict__ start,
-                                                  const int32_t* __restrict__ sorted_id,
-                                                  const double* __restrict__ sorted_xyz,
-                                                  const uint8_t* __restrict__ sorted_bnd, int32_t* __restrict__ out_idx,
-                                                  unsigned* flags) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  const Key INF{~0ull, 0x7fffffff};
-  for (int64_t qi = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); qi < nq; qi += warps) {
-    const int32_t c = queries[qi];
-    const bool bnd_center = is_boundary && is_boundary[c];
-    const int n = bnd_center ? n_full - 1 : n_full;
-    double q[DIM];
-    int cq[DIM];
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) {
-      q[k] = coords[k * N + c];
-      if (bnd_center && normals) q[k] = __dsub_rn(q[k], __dmul_rn(h, normals[k * N + c]));
-      cq[k] = cg.cell_of(q[k], k);
-    }
-    Key best = INF;  // lane i: i-th smallest key so far
-    for (int r = 0;; ++r) {
-      int lo[DIM], hi[DIM];
-      bool any_inside = false;
-#pragma unroll
-      for (int k = 0; k < DIM; ++k) {
-        lo[k] = cq[k] - r;
-        hi[k] = cq[k] + r;
-        if (lo[k] >= 0 || hi[k] < cg.g[k]) any_inside = true;
-      }
-      if (r > 0 && !any_inside) break;
-      // cells of the shell at Chebyshev distance r, enumerated as the
-      // (2r+1)^DIM block minus its interior; lanes take cells round-robin
-      const int side = 2 * r + 1;
-      int ncell = side;
-      for (int k = 1; k < DIM; ++k) ncell *= side;
-      int cell = lane;   // next block cell of this lane
-      int32_t s_cur = 0, s_end = 0;
-      for (;;) {
-        // advance to a cell with points left (or run out)
-        while (s_cur >= s_end && cell < ncell) {
-          int rem = cell, cc[DIM];
-          bool shell = false, inside = true;
-#pragma unroll
-          for (int k = 0; k < DIM; ++k) {
-            const int o = rem % side;
-            rem /= side;
-            cc[k] = lo[k] + o;
-            if (o == 0 || o == side - 1) shell = true;
-            if (cc[k] < 0 || cc[k] >= cg.g[k]) inside = false;
-          }
-          cell += 32;
-          if (!(shell || r == 0) || !inside) continue;
-          int64_t l = 0;
-#pragma unroll
-          for (int k = DIM - 1; k >= 0; --k) l = l * cg.g[k] + cc[k];
-          s_cur = start[l];
-          s_end = start[l + 1];
-        }
-        Key cand = INF;
-        if (s_cur < s_end) {
-          const int32_t id = sorted_id[s_cur];
-          if (!(bnd_center && sorted_bnd[s_cur])) {
-            cand.d = (unsigned long long)__double_as_longlong(sq_dist<DIM>(sorted_xyz + (int64_t)s_cur * kMaxDim, q));
-            cand.i = id;
-          }
-          ++s_cur;
-        }
-        const bool more = (s_cur < s_end) || (cell < ncell);
-        // the n-th key of the list bounds what can still enter
-        const Key worst = shfl_key(best, n - 1);
-        const bool useful = kless(cand, worst);
-        if (__any_sync(0xffffffffu, useful)) {
-          Key b = warp_sort(useful ? cand : INF, lane);
-          const Key br = shfl_key(b, 31 - lane);
-          Key m = kless(br, best) ? br : best;
-          best = warp_merge(m, lane);
-          if (lane >= n) best = INF;
-        }
-        if (!__any_sync(0xffffffffu, more)) break;
-      }
-      const Key nth = shfl_key(best, n - 1);
-      if (nth.d != ~0ull) {
-        double bound = DBL_MAX;
-#pragma unroll
-        for (int k = 0; k < DIM; ++k) {
-          if (lo[k] > 0) bound = fmin(bound, q[k] - (cg.lo[k] + lo[k] * cg.cell));
-          if (hi[k] < cg.g[k] - 1) bound = fmin(bound, (cg.lo[k] + (hi[k] + 1) * cg.cell) - q[k]);
-        }
-        if (bound == DBL_MAX) break;
-        bound *= (1.0 - 1e-9);
-        if (bound > 0.0 && __longlong_as_double((long long)nth.d) < bound * bound) break;
-      }
-    }
-    const int cnt = __popc(__ballot_sync(0xffffffffu, best.d != ~0ull && lane < n));
-    if (cnt < n && lane == 0) atomicOr(flags, kDevKnnShort);
-    const int off = bnd_center ? 1 : 0;
-    if (bnd_center && lane == 0) out_idx[qi] = c;
-    if (lane < n) out_idx[(int64_t)(lane + off) * nq + qi] = best.d != ~0ull ? best.i : c;
-  }
-}
-
 }  // namespace
 
 hsm_status build_stencils(hsm_plan p) {
@@ -645,18 +482,7 @@ hsm_status build_stencils(hsm_plan p) {
     const int KT = 32;
     size_t smem = (size_t)p->n * KT * (sizeof(double) + sizeof(int32_t));
     int gk = (int)std::min<int64_t>(ceil_div(p->rbf.count, KT), (int64_t)num_sms() * 16);
-    if (p->n <= 32) {
-      // one warp per query
-      const int gw = (int)std::min<int64_t>(ceil_div(p->rbf.count, 8), (int64_t)num_sms() * 32);
-      if (dim == 2)
-        k_knn_warp<2><<<gw, 256, 0, s>>>(p->coords, N, p->is_boundary, p->normals, p->h, list_rbf, p->rbf.count,
-                                          p->n, cg, cstart, sorted_id, sorted_xyz, sorted_bnd, p->rbf.idx,
-                                          p->dev_flags);
-      else
-        k_knn_warp<3><<<gw, 256, 0, s>>>(p->coords, N, p->is_boundary, p->normals, p->h, list_rbf, p->rbf.count,
-                                          p->n, cg, cstart, sorted_id, sorted_xyz, sorted_bnd, p->rbf.idx,
-                                          p->dev_flags);
-    } else if (dim == 2) {
+    if (dim == 2) {
       if (smem > 48 * 1024) HSM_CUDA(p, cudaFuncSetAttribute(k_knn<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       k_knn<2><<<gk, KT, smem, s>>>(p->coords, N, p->is_boundary, p->normals, p->h, list_rbf, p->rbf.count, p->n, cg, cstart,
                                      sorted_id, sorted_xyz, sorted_bnd, p->rbf.idx, p->dev_flags);
