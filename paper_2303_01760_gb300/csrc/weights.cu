@@ -1,8 +1,10 @@
 // Stencil weights of Eq. 1 (Section 2 and 2.1).
 //
 // MON (regular nodes): P^T w = L p over the 2d+1 monomials {1, x_k, x_k^2}
-// (Section 2 footnote), one thread per node, the (2d+1) x (2d+1+ops) system
-// in registers, Gaussian elimination with partial pivoting.
+// (Section 2 footnote), one thread per node: the closed-form solution of the
+// decoupled per-axis systems when the stencil is axis-aligned, otherwise the
+// (2d+1) x (2d+1+ops) system by Gaussian elimination in a fixed order that
+// needs no pivoting on lattice stencils.
 //
 // RBF-FD (scattered, boundary and demoted nodes): the augmented PHS system
 //     [A P; P^T 0][w; lambda] = [L phi; L p],  phi(r) = r^3,
@@ -42,6 +44,12 @@ __host__ OpsDesc make_ops(hsm_plan p, unsigned mask) {
 // ---------------------------------------------------------------------------
 // MON
 // ---------------------------------------------------------------------------
+// The system is ordered basis rows (1, xi_1, xi_1^2, xi_2, xi_2^2 [, xi_3,
+// xi_3^2]) against node columns (c, c-e1, c+e1, c-e2, c+e2 [, c-e3, c+e3]).
+// On (and within 1e-6 lattice units of) the lattice this order needs no
+// pivoting: every pivot stays within rounding of 1, -1 or 2, so the
+// elimination runs as straight-line code in registers.  A pivot below 1e-8
+// (impossible for a lattice stencil) marks the node singular.
 template <int DIM, int NOPS>
 __global__ void __launch_bounds__(128) k_mon(const double* __restrict__ coords, int64_t N,
                                              const int32_t* __restrict__ idx, int64_t G, OpsDesc ops,
@@ -52,6 +60,9 @@ __global__ void __launch_bounds__(128) k_mon(const double* __restrict__ coords, 
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < G; p += (int64_t)gridDim.x * blockDim.x) {
     double xi[K][DIM];
     const int32_t c = idx[p];
+    double cx[DIM];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) cx[k] = coords[k * N + c];
     double s2 = 0.0;
 #pragma unroll
     for (int j = 0; j < K; ++j) {
@@ -59,27 +70,72 @@ __global__ void __launch_bounds__(128) k_mon(const double* __restrict__ coords, 
       double r2 = 0.0;
 #pragma unroll
       for (int k = 0; k < DIM; ++k) {
-        double o = coords[k * N + id] - coords[k * N + c];
+        const double o = coords[k * N + id] - cx[k];
         xi[j][k] = o;
         r2 += o * o;
       }
       s2 = fmax(s2, r2);
     }
+    // Axis-aligned stencil (every neighbour offset is zero off its own axis,
+    // as for nodes placed exactly on the lattice): the system decouples into
+    // one 3-point Vandermonde system per axis, solved in closed form with
+    // a = |x_c - x_{c-e}|, b = |x_{c+e} - x_c|, r = 1 / (a b (a + b)):
+    //   d/dx_k : w(c-e) = -b^2 r, w(c+e) = a^2 r, w(c) = -(w(c-e) + w(c+e))
+    //   lap    : w(c-e) = 2 b r,  w(c+e) = 2 a r, summed over the axes.
+    bool aligned = true;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k)
+#pragma unroll
+      for (int e = 0; e < DIM; ++e)
+        if (e != k) aligned = aligned && xi[1 + 2 * k][e] == 0.0 && xi[2 + 2 * k][e] == 0.0;
+    if (aligned) {
+      double wm[DIM], wp[DIM], lm[DIM], lpl[DIM];
+      bool okk = true;
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) {
+        const double a = -xi[1 + 2 * k][k], b = xi[2 + 2 * k][k];
+        okk = okk && a > 0.0 && b > 0.0;
+        const double r = 1.0 / (a * b * (a + b));
+        wm[k] = -b * b * r;
+        wp[k] = a * a * r;
+        lm[k] = 2.0 * b * r;
+        lpl[k] = 2.0 * a * r;
+      }
+#pragma unroll
+      for (int o = 0; o < NOPS; ++o) {
+        const int kd = ops.kind[o];
+        double wc = 0.0;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+          double m = 0.0, pl = 0.0;
+          if (kd == 3) {
+            m = lm[k];
+            pl = lpl[k];
+          } else if (kd == k) {
+            m = wm[k];
+            pl = wp[k];
+          }
+          wc -= m + pl;
+          w[((int64_t)o * K + 1 + 2 * k) * G + p] = okk ? m : 0.0;
+          w[((int64_t)o * K + 2 + 2 * k) * G + p] = okk ? pl : 0.0;
+        }
+        w[((int64_t)o * K) * G + p] = okk ? wc : 0.0;
+      }
+      if (!okk) atomicOr(flags, kDevSingular);
+      if (status) status[nodes[p]] = okk ? HSM_NODE_OK : HSM_NODE_SINGULAR;
+      continue;
+    }
     const double s = sqrt(s2);
     const double inv_s = 1.0 / s;
-#pragma unroll
-    for (int j = 0; j < K; ++j)
-#pragma unroll
-      for (int k = 0; k < DIM; ++k) xi[j][k] *= inv_s;
-    // rows = basis functions {1, xi_k, xi_k^2}, columns = stencil nodes | rhs
     double a[K][C];
 #pragma unroll
     for (int j = 0; j < K; ++j) {
       a[0][j] = 1.0;
 #pragma unroll
       for (int k = 0; k < DIM; ++k) {
-        a[1 + k][j] = xi[j][k];
-        a[1 + DIM + k][j] = xi[j][k] * xi[j][k];
+        const double x = xi[j][k] * inv_s;
+        a[1 + 2 * k][j] = x;
+        a[2 + 2 * k][j] = x * x;
       }
     }
 #pragma unroll
@@ -87,28 +143,17 @@ __global__ void __launch_bounds__(128) k_mon(const double* __restrict__ coords, 
 #pragma unroll
       for (int o = 0; o < NOPS; ++o) {
         const int kd = ops.kind[o];
+        // row b is 1 (b == 0), xi_k (b = 1 + 2k) or xi_k^2 (b = 2 + 2k)
         double v = 0.0;
-        if (kd == 3) v = (b >= 1 + DIM) ? 2.0 : 0.0;
-        else v = (b == 1 + kd) ? 1.0 : 0.0;
+        if (kd == 3) v = (b > 0 && (b % 2) == 0) ? 2.0 : 0.0;
+        else v = (b == 1 + 2 * kd) ? 1.0 : 0.0;
         a[b][K + o] = v;
       }
     bool ok = s > 0.0;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      // partial pivoting by conditional swaps against every lower row
-#pragma unroll
-      for (int i = k + 1; i < K; ++i) {
-        if (fabs(a[i][k]) > fabs(a[k][k])) {
-#pragma unroll
-          for (int j = k; j < C; ++j) {
-            double t = a[k][j];
-            a[k][j] = a[i][j];
-            a[i][j] = t;
-          }
-        }
-      }
       const double piv = a[k][k];
-      ok = ok && piv != 0.0 && isfinite(piv);
+      ok = ok && fabs(piv) > 1e-8;
       const double inv = 1.0 / piv;
 #pragma unroll
       for (int i = k + 1; i < K; ++i) {

@@ -178,3 +178,13 @@ def test_invalid_arguments_rejected_before_launch():
         p.compute_weights()
     assert e.value.code == 8
     p.close()
+
+
+def test_mon_weights_on_slightly_perturbed_lattice():
+    """Regular nodes within the lattice tolerance but off exact alignment take
+    the general MON elimination instead of the per-axis closed form; both must
+    match the oracle's solve of the same system."""
+    ns = nodesets.square_wall_band(n=24, wall_band=0.0)
+    rng = np.random.default_rng(8)
+    ns.coords = ns.coords + rng.uniform(-1e-9, 1e-9, ns.coords.shape) * ns.h
+    _check_plan(ns, m=2)
