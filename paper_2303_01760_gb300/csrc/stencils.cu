@@ -252,21 +252,31 @@ __device__ __forceinline__ double sq_dist(const double* a, const double* b) {
   return s;
 }
 
-// One thread per query; the running top-n list lives in shared memory as
-// [n][blockDim] structure-of-arrays (bank-conflict free).
-template <int DIM>
-__global__ void k_knn(const double* __restrict__ coords, int64_t N, const uint8_t* __restrict__ is_boundary,
-                      const double* __restrict__ normals, double h, const int32_t* __restrict__ queries,
-                      int64_t nq, int n_full, CellGrid cg,
-                      const int32_t* __restrict__ start, const int32_t* __restrict__ sorted_id,
-                      const double* __restrict__ sorted_xyz, const uint8_t* __restrict__ sorted_bnd,
-                      int32_t* __restrict__ out_idx, unsigned* flags) {
+// QT threads per query (a "quad" of consecutive lanes).  The shell cells of
+// each ring are dealt round-robin to the quad's threads; every thread keeps its
+// own sorted top-n list in shared memory ([n][blockDim] structure of arrays,
+// bank-conflict free) and prunes candidates against its own n-th key and the
+// quad's merged n-th key of the previous ring.  After each ring the quad
+// leader merges the QT lists to find the quad's n-th key for the stopping
+// test; at the end it merges them into the stencil.
+template <int DIM, int QT>
+__global__ void __launch_bounds__(128) k_knn(const double* __restrict__ coords, int64_t N,
+                                             const uint8_t* __restrict__ is_boundary,
+                                             const double* __restrict__ normals, double h,
+                                             const int32_t* __restrict__ queries, int64_t nq, int n_full, CellGrid cg,
+                                             const int32_t* __restrict__ start, const int32_t* __restrict__ sorted_id,
+                                             const double* __restrict__ sorted_xyz,
+                                             const uint8_t* __restrict__ sorted_bnd, int32_t* __restrict__ out_idx,
+                                             unsigned* flags) {
   extern __shared__ unsigned char smem_raw[];
   const int B = blockDim.x;
   double* kd = reinterpret_cast<double*>(smem_raw);
   int32_t* ki = reinterpret_cast<int32_t*>(kd + (size_t)n_full * B);
-  const int t = threadIdx.x;
-  for (int64_t qi = blockIdx.x * (int64_t)B + t; qi < nq; qi += (int64_t)gridDim.x * B) {
+  const int t = threadIdx.x, sub = t % QT, lead = t - sub;
+  const int lane = t & 31;
+  const unsigned qmask = ((1u << QT) - 1u) << (lane - sub);
+  const int64_t qpb = B / QT;
+  for (int64_t qi = blockIdx.x * qpb + t / QT; qi < nq; qi += (int64_t)gridDim.x * qpb) {
     const int32_t c = queries[qi];
     const bool bnd_center = is_boundary && is_boundary[c];
     // boundary nodes: search the n-1 interior nodes nearest to x_c - h n_c
@@ -280,8 +290,9 @@ __global__ void k_knn(const double* __restrict__ coords, int64_t N, const uint8_
       cq[k] = cg.cell_of(q[k], k);
     }
     int cnt = 0;
+    double qd = DBL_MAX;  // quad's n-th key after the last ring (pruning bound)
+    int32_t qid = 0x7fffffff;
     for (int r = 0;; ++r) {
-      // visit the shell of cells at Chebyshev distance r
       int lo[DIM], hi[DIM];
       bool any_inside = false;
 #pragma unroll
@@ -290,9 +301,10 @@ __global__ void k_knn(const double* __restrict__ coords, int64_t N, const uint8_
         hi[k] = cq[k] + r;
         if (lo[k] >= 0 || hi[k] < cg.g[k]) any_inside = true;
       }
-      if (r > 0 && !any_inside) break;  // the whole grid has been visited
+      if (r > 0 && !any_inside) break;
       int cc[DIM];
-      int zlo = DIM == 3 ? max(lo[DIM - 1], 0) : 0, zhi = DIM == 3 ? min(hi[DIM - 1], cg.g[DIM - 1] - 1) : 0;
+      int turn = 0;  // shell-cell counter; this thread takes turn % QT == sub
+      const int zlo = DIM == 3 ? max(lo[DIM - 1], 0) : 0, zhi = DIM == 3 ? min(hi[DIM - 1], cg.g[DIM - 1] - 1) : 0;
       for (int z = zlo; z <= zhi; ++z) {
         if (DIM == 3) cc[2] = z;
         const bool zedge = DIM == 3 && (z == lo[2] || z == hi[2]);
@@ -302,6 +314,7 @@ __global__ void k_knn(const double* __restrict__ coords, int64_t N, const uint8_
           const int xstep = full ? 1 : (hi[0] - lo[0]);
           for (int x = lo[0]; x <= hi[0]; x += xstep) {
             if (x < 0 || x >= cg.g[0]) continue;
+            if ((turn++ % QT) != sub) continue;
             cc[0] = x;
             int64_t l = 0;
 #pragma unroll
@@ -311,6 +324,7 @@ __global__ void k_knn(const double* __restrict__ coords, int64_t N, const uint8_
               const int32_t id = sorted_id[s];
               if (bnd_center && sorted_bnd[s]) continue;
               const double d2 = sq_dist<DIM>(sorted_xyz + (int64_t)s * kMaxDim, q);
+              if (!key_less(d2, id, qd, qid)) continue;
               if (cnt == n && !key_less(d2, id, kd[(n - 1) * B + t], ki[(n - 1) * B + t])) continue;
               int j = (cnt < n) ? cnt++ : n - 1;
               while (j > 0 && key_less(d2, id, kd[(j - 1) * B + t], ki[(j - 1) * B + t])) {
@@ -324,8 +338,47 @@ __global__ void k_knn(const double* __restrict__ coords, int64_t N, const uint8_
           }
         }
       }
-      if (cnt == n) {
-        // distance from q to the faces of the visited block that lie inside the grid
+      // quad's n-th key: the leader merges the QT sorted lists
+      __syncwarp(qmask);
+      double nd = DBL_MAX;
+      int32_t nid = 0x7fffffff;
+      int total = 0;
+      // list lengths of the quad (every thread shares its cnt)
+      int lens[QT];
+#pragma unroll
+      for (int u = 0; u < QT; ++u) lens[u] = __shfl_sync(qmask, cnt, (lane - sub) + u);
+#pragma unroll
+      for (int u = 0; u < QT; ++u) total += lens[u];
+      if (sub == 0 && total >= n) {
+        int pos[QT];
+#pragma unroll
+        for (int u = 0; u < QT; ++u) pos[u] = 0;
+        for (int k = 0; k < n; ++k) {
+          int best = -1;
+          double bd = DBL_MAX;
+          int32_t bi = 0x7fffffff;
+#pragma unroll
+          for (int u = 0; u < QT; ++u) {
+            if (pos[u] < lens[u]) {
+              const double dd = kd[pos[u] * B + lead + u];
+              const int32_t ii = ki[pos[u] * B + lead + u];
+              if (best < 0 || key_less(dd, ii, bd, bi)) {
+                best = u;
+                bd = dd;
+                bi = ii;
+              }
+            }
+          }
+          ++pos[best];
+          nd = bd;
+          nid = bi;
+        }
+      }
+      nd = __shfl_sync(qmask, nd, lane - sub);
+      nid = __shfl_sync(qmask, nid, lane - sub);
+      if (total >= n) {
+        qd = nd;
+        qid = nid;
         double bound = DBL_MAX;
 #pragma unroll
         for (int k = 0; k < DIM; ++k) {
@@ -334,13 +387,48 @@ __global__ void k_knn(const double* __restrict__ coords, int64_t N, const uint8_
         }
         if (bound == DBL_MAX) break;
         bound *= (1.0 - 1e-9);
-        if (bound > 0.0 && kd[(n - 1) * B + t] < bound * bound) break;
+        if (bound > 0.0 && nd < bound * bound) break;
       }
     }
-    if (cnt < n) atomicOr(flags, kDevKnnShort);
-    const int off = bnd_center ? 1 : 0;
-    if (bnd_center) out_idx[qi] = c;
-    for (int j = 0; j < n; ++j) out_idx[(int64_t)(j + off) * nq + qi] = j < cnt ? ki[j * B + t] : c;
+    // final merge of the quad's lists by the leader
+    __syncwarp(qmask);
+    int lens[QT];
+#pragma unroll
+    for (int u = 0; u < QT; ++u) lens[u] = __shfl_sync(qmask, cnt, (lane - sub) + u);
+    if (sub == 0) {
+      int pos[QT];
+#pragma unroll
+      for (int u = 0; u < QT; ++u) pos[u] = 0;
+      const int off = bnd_center ? 1 : 0;
+      if (bnd_center) out_idx[qi] = c;
+      int got = 0;
+      for (int k = 0; k < n; ++k) {
+        int best = -1;
+        double bd = DBL_MAX;
+        int32_t bi = 0x7fffffff;
+#pragma unroll
+        for (int u = 0; u < QT; ++u) {
+          if (pos[u] < lens[u]) {
+            const double dd = kd[pos[u] * B + lead + u];
+            const int32_t ii = ki[pos[u] * B + lead + u];
+            if (best < 0 || key_less(dd, ii, bd, bi)) {
+              best = u;
+              bd = dd;
+              bi = ii;
+            }
+          }
+        }
+        int32_t v = c;
+        if (best >= 0) {
+          ++pos[best];
+          v = bi;
+          ++got;
+        }
+        out_idx[(int64_t)(k + off) * nq + qi] = v;
+      }
+      if (got < n) atomicOr(flags, kDevKnnShort);
+    }
+    __syncwarp(qmask);
   }
 }
 
@@ -478,18 +566,21 @@ hsm_status build_stencils(hsm_plan p) {
                                       sorted_xyz, sorted_bnd);
     p->launches += 2;
     HSM_CUDA(p, cudaGetLastError());
-    // one thread per query; small blocks spread the few scattered queries over every SM
-    const int KT = 32;
+    // four threads per query, 32 queries per block of 128
+    constexpr int QT = 4;
+    const int KT = 128;
     size_t smem = (size_t)p->n * KT * (sizeof(double) + sizeof(int32_t));
-    int gk = (int)std::min<int64_t>(ceil_div(p->rbf.count, KT), (int64_t)num_sms() * 16);
+    int gk = (int)std::min<int64_t>(ceil_div(p->rbf.count, KT / QT), (int64_t)num_sms() * 16);
     if (dim == 2) {
-      if (smem > 48 * 1024) HSM_CUDA(p, cudaFuncSetAttribute(k_knn<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k_knn<2><<<gk, KT, smem, s>>>(p->coords, N, p->is_boundary, p->normals, p->h, list_rbf, p->rbf.count, p->n, cg, cstart,
-                                     sorted_id, sorted_xyz, sorted_bnd, p->rbf.idx, p->dev_flags);
+      if (smem > 48 * 1024)
+        HSM_CUDA(p, cudaFuncSetAttribute(k_knn<2, QT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_knn<2, QT><<<gk, KT, smem, s>>>(p->coords, N, p->is_boundary, p->normals, p->h, list_rbf, p->rbf.count, p->n,
+                                         cg, cstart, sorted_id, sorted_xyz, sorted_bnd, p->rbf.idx, p->dev_flags);
     } else {
-      if (smem > 48 * 1024) HSM_CUDA(p, cudaFuncSetAttribute(k_knn<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k_knn<3><<<gk, KT, smem, s>>>(p->coords, N, p->is_boundary, p->normals, p->h, list_rbf, p->rbf.count, p->n, cg, cstart,
-                                     sorted_id, sorted_xyz, sorted_bnd, p->rbf.idx, p->dev_flags);
+      if (smem > 48 * 1024)
+        HSM_CUDA(p, cudaFuncSetAttribute(k_knn<3, QT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_knn<3, QT><<<gk, KT, smem, s>>>(p->coords, N, p->is_boundary, p->normals, p->h, list_rbf, p->rbf.count, p->n,
+                                         cg, cstart, sorted_id, sorted_xyz, sorted_bnd, p->rbf.idx, p->dev_flags);
     }
     HSM_CUDA(p, cudaGetLastError());
     dev_free(&cell_of, s);
