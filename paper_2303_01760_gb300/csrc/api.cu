@@ -385,10 +385,11 @@ hsm_status hsm_plan_autotune(hsm_plan p, const char* cache_path) {
     while (in >> k >> v) cache[k] = v;
     auto it = cache.find(key);
     if (it != cache.end()) {
-      int t = 0, l = 0;
-      if (sscanf(it->second.c_str(), "%d,%d", &t, &l) == 2 && t > 0 && l > 0) {
+      int t = 0, l = 0, qv = 1;
+      if (sscanf(it->second.c_str(), "%d,%d,%d", &t, &l, &qv) >= 2 && t > 0 && l > 0) {
         p->tune.apply_threads = t;
         p->tune.rbf_lanes = l;
+        p->tune.knn_qt = qv;
         p->tune.tuned = true;
         return HSM_OK;
       }
@@ -396,6 +397,23 @@ hsm_status hsm_plan_autotune(hsm_plan p, const char* cache_path) {
   }
   cudaStream_t s = p->stream;
   hsm_status st = HSM_OK;
+  // threads per kNN query: rebuild the stencils with each variant
+  {
+    float best_ms = 1e30f;
+    int best_q = p->tune.knn_qt;
+    for (int qv : {1, 2, 4}) {
+      p->tune.knn_qt = qv;
+      float ms = time_ms(s, [&]() { return hsm_plan_build_stencils(p); }, 2, &st);
+      if (st != HSM_OK) return st;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best_q = qv;
+      }
+    }
+    p->tune.knn_qt = best_q;
+    st = hsm_plan_build_stencils(p);
+    if (st != HSM_OK) return st;
+  }
   // weight-solve lanes (weights must exist afterwards; the last run leaves them)
   float best = 1e30f;
   int best_l = p->tune.rbf_lanes;
@@ -440,7 +458,7 @@ hsm_status hsm_plan_autotune(hsm_plan p, const char* cache_path) {
   p->tune.tuned = true;
   if (cache_path) {
     std::ostringstream v;
-    v << best_t << "," << best_l;
+    v << best_t << "," << best_l << "," << p->tune.knn_qt;
     cache[key] = v.str();
     std::ofstream o(cache_path, std::ios::trunc);
     for (auto& kv : cache) o << kv.first << " " << kv.second << "\n";

@@ -260,7 +260,7 @@ __device__ __forceinline__ double sq_dist(const double* a, const double* b) {
 // leader merges the QT lists to find the quad's n-th key for the stopping
 // test; at the end it merges them into the stencil.
 template <int DIM, int QT>
-__global__ void __launch_bounds__(128) k_knn(const double* __restrict__ coords, int64_t N,
+__global__ void __launch_bounds__(32 * QT) k_knn(const double* __restrict__ coords, int64_t N,
                                              const uint8_t* __restrict__ is_boundary,
                                              const double* __restrict__ normals, double h,
                                              const int32_t* __restrict__ queries, int64_t nq, int n_full, CellGrid cg,
@@ -566,21 +566,29 @@ hsm_status build_stencils(hsm_plan p) {
                                       sorted_xyz, sorted_bnd);
     p->launches += 2;
     HSM_CUDA(p, cudaGetLastError());
-    // four threads per query, 32 queries per block of 128
-    constexpr int QT = 4;
-    const int KT = 128;
+    // p->tune.knn_qt threads per query (1, 2 or 4; tuned), blocks of 32 * qt
+    const int qt = p->tune.knn_qt == 4 ? 4 : (p->tune.knn_qt == 2 ? 2 : 1);
+    const int KT = 32 * qt;
     size_t smem = (size_t)p->n * KT * (sizeof(double) + sizeof(int32_t));
-    int gk = (int)std::min<int64_t>(ceil_div(p->rbf.count, KT / QT), (int64_t)num_sms() * 16);
-    if (dim == 2) {
-      if (smem > 48 * 1024)
-        HSM_CUDA(p, cudaFuncSetAttribute(k_knn<2, QT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k_knn<2, QT><<<gk, KT, smem, s>>>(p->coords, N, p->is_boundary, p->normals, p->h, list_rbf, p->rbf.count, p->n,
-                                         cg, cstart, sorted_id, sorted_xyz, sorted_bnd, p->rbf.idx, p->dev_flags);
-    } else {
-      if (smem > 48 * 1024)
-        HSM_CUDA(p, cudaFuncSetAttribute(k_knn<3, QT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k_knn<3, QT><<<gk, KT, smem, s>>>(p->coords, N, p->is_boundary, p->normals, p->h, list_rbf, p->rbf.count, p->n,
-                                         cg, cstart, sorted_id, sorted_xyz, sorted_bnd, p->rbf.idx, p->dev_flags);
+    int gk = (int)std::min<int64_t>(ceil_div(p->rbf.count, 32), (int64_t)num_sms() * 16);
+    void* fn = nullptr;
+    if (dim == 2) fn = qt == 4 ? (void*)k_knn<2, 4> : (qt == 2 ? (void*)k_knn<2, 2> : (void*)k_knn<2, 1>);
+    else fn = qt == 4 ? (void*)k_knn<3, 4> : (qt == 2 ? (void*)k_knn<3, 2> : (void*)k_knn<3, 1>);
+    if (smem > 48 * 1024) HSM_CUDA(p, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    {
+      const double* coords = p->coords;
+      const uint8_t* isb = p->is_boundary;
+      const double* nrm = p->normals;
+      double hh = p->h;
+      const int32_t* qlist = list_rbf;
+      int64_t nq = p->rbf.count;
+      int nf = p->n;
+      int32_t* outp = p->rbf.idx;
+      unsigned* fl = p->dev_flags;
+      void* args[] = {(void*)&coords, (void*)&N, (void*)&isb, (void*)&nrm, (void*)&hh, (void*)&qlist, (void*)&nq,
+                      (void*)&nf, (void*)&cg, (void*)&cstart, (void*)&sorted_id, (void*)&sorted_xyz,
+                      (void*)&sorted_bnd, (void*)&outp, (void*)&fl};
+      HSM_CUDA(p, cudaLaunchKernel(fn, dim3(gk), dim3(KT), args, smem, s));
     }
     HSM_CUDA(p, cudaGetLastError());
     dev_free(&cell_of, s);
