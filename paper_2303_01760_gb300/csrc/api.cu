@@ -148,13 +148,13 @@ static void free_plan_device(hsm_plan p) {
   dev_free(&p->pos, s);
   dev_free(&p->dev_flags, s);
   dev_free(&p->dev_count, s);
-  dev_free(&p->pairs, s);
-  dev_free(&p->mono_exp, s);
 }
 
 hsm_status hsm_plan_destroy(hsm_plan p) {
   if (!p) return HSM_OK;
   free_plan_device(p);
+  dev_free(&p->pairs, p->stream);
+  dev_free(&p->mono_exp, p->stream);
   cudaStreamSynchronize(p->stream);
   for (auto& e : p->ev)
     if (e) cudaEventDestroy(e);
@@ -191,18 +191,20 @@ hsm_status hsm_plan_build_stencils(hsm_plan p) {
   HSM_CUDA(p, dev_alloc(&p->dev_flags, 4, s));
   HSM_CUDA(p, dev_alloc(&p->dev_count, 4, s));
   HSM_CUDA(p, cudaMemsetAsync(p->dev_flags, 0, 4 * sizeof(unsigned), s));
-  // upper-triangle pair table and monomial exponents for the RBF-FD kernels
-  std::vector<uint16_t> pairs;
-  for (int i = 0; i < p->n; ++i)
-    for (int j = i + 1; j < p->n; ++j) pairs.push_back((uint16_t)((i << 8) | j));
-  std::vector<int8_t> ex = monomial_exponents(p->dim, p->m);
-  HSM_CUDA(p, dev_alloc(&p->pairs, pairs.size(), s));
-  HSM_CUDA(p, dev_alloc(&p->mono_exp, ex.size(), s));
-  if (!pairs.empty())
-    HSM_CUDA(p, cudaMemcpyAsync(p->pairs, pairs.data(), pairs.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, s));
-  HSM_CUDA(p, cudaMemcpyAsync(p->mono_exp, ex.data(), ex.size(), cudaMemcpyHostToDevice, s));
-  // host vectors must outlive the async copies
-  HSM_CUDA(p, cudaStreamSynchronize(s));
+  // upper-triangle pair table and monomial exponents for the RBF-FD kernels,
+  // uploaded once per plan from host copies the plan keeps
+  if (!p->pairs) {
+    p->h_pairs.clear();
+    for (int i = 0; i < p->n; ++i)
+      for (int j = i + 1; j < p->n; ++j) p->h_pairs.push_back((uint16_t)((i << 8) | j));
+    p->h_exp = monomial_exponents(p->dim, p->m);
+    HSM_CUDA(p, dev_alloc(&p->pairs, p->h_pairs.size(), s));
+    HSM_CUDA(p, dev_alloc(&p->mono_exp, p->h_exp.size(), s));
+    if (!p->h_pairs.empty())
+      HSM_CUDA(p, cudaMemcpyAsync(p->pairs, p->h_pairs.data(), p->h_pairs.size() * sizeof(uint16_t),
+                                  cudaMemcpyHostToDevice, s));
+    HSM_CUDA(p, cudaMemcpyAsync(p->mono_exp, p->h_exp.data(), p->h_exp.size(), cudaMemcpyHostToDevice, s));
+  }
   PhaseTimer tm(p, HSM_PHASE_STENCILS);
   return build_stencils(p);
 }

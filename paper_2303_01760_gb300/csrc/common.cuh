@@ -70,6 +70,8 @@ struct hsm_plan_s {
   int* dev_count = nullptr;       // device counter scratch
   uint16_t* pairs = nullptr;      // [n(n-1)/2] (i << 8 | j) upper-triangle pairs
   int8_t* mono_exp = nullptr;     // [n_mono][dim] monomial exponents
+  std::vector<uint16_t> h_pairs;  // host sources of the two tables (kept for the async upload)
+  std::vector<int8_t> h_exp;
   int64_t n_demoted = 0;
   int64_t n_fallback = 0;
   bool stencils_built = false;

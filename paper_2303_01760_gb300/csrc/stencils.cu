@@ -20,6 +20,7 @@ namespace hsm {
 namespace {
 
 constexpr double kLatticeTol = 1e-6;
+constexpr double kLatticeRange = 1048576.0;  // |lattice coordinate| < 2^20 (21-bit key fields)
 
 __device__ __forceinline__ unsigned long long ordered_bits(double x) {
   unsigned long long b = (unsigned long long)__double_as_longlong(x);
@@ -61,7 +62,7 @@ __global__ void __launch_bounds__(256) k_bounds(const double* __restrict__ coord
       bmax[k] = ob > bmax[k] ? ob : bmax[k];
       double t = x * inv_h;
       double r = rint(t);
-      if (!(fabs(t - r) <= kLatticeTol) || fabs(r) > 1.0e9) on = false;
+      if (!(fabs(t - r) <= kLatticeTol) || fabs(r) >= kLatticeRange) on = false;
       q[k] = on ? (int)r : 0;
     }
     on_lat[i] = on ? 1 : 0;
@@ -116,30 +117,63 @@ __global__ void __launch_bounds__(256) k_bounds(const double* __restrict__ coord
   }
 }
 
-struct LatticeGeom {
-  int lo[kMaxDim];
-  int ext[kMaxDim];
+// Lattice map: open-addressing hash table from packed lattice coordinates
+// (21 bits per axis) to the lowest node id on that lattice point; capacity a
+// power of two >= 2N, linear probing, every probe loop bounded by the
+// capacity.
+struct LatticeHash {
+  unsigned long long* keys;  // ~0ull = empty slot
+  int32_t* vals;             // kEmpty = no node
+  unsigned long long mask;
   int dim;
-  __device__ __forceinline__ int64_t lin(const int* q) const {
-    int64_t l = 0;
-    for (int k = dim - 1; k >= 0; --k) {
-      int a = q[k] - lo[k];
-      if (a < 0 || a >= ext[k]) return -1;
-      l = l * ext[k] + a;
+  __device__ __forceinline__ unsigned long long key(const int* q) const {
+    unsigned long long k = 0;
+    for (int a = dim - 1; a >= 0; --a) k = (k << 21) | (unsigned long long)(q[a] + (1 << 20));
+    return k;
+  }
+  static __device__ __forceinline__ unsigned long long hash(unsigned long long x) {
+    x ^= x >> 33;
+    x *= 0xff51afd7ed558ccdull;
+    x ^= x >> 33;
+    x *= 0xc4ceb9fe1a85ec53ull;
+    return x ^ (x >> 33);
+  }
+  __device__ __forceinline__ void insert(const int* q, int32_t id) const {
+    const unsigned long long k = key(q);
+    unsigned long long h = hash(k) & mask;
+    for (unsigned long long probe = 0; probe <= mask; ++probe) {
+      const unsigned long long prev = atomicCAS(&keys[h], ~0ull, k);
+      if (prev == ~0ull || prev == k) {
+        atomicMin(&vals[h], id);
+        return;
+      }
+      h = (h + 1) & mask;
     }
-    return l;
+  }
+  // owner of lattice point q, or kEmpty
+  __device__ __forceinline__ int32_t find(const int* q) const {
+    for (int a = 0; a < dim; ++a)
+      if (q[a] <= -(1 << 20) || q[a] >= (1 << 20)) return kEmpty;
+    const unsigned long long k = key(q);
+    unsigned long long h = hash(k) & mask;
+    for (unsigned long long probe = 0; probe <= mask; ++probe) {
+      const unsigned long long cur = keys[h];
+      if (cur == k) return vals[h];
+      if (cur == ~0ull) return kEmpty;
+      h = (h + 1) & mask;
+    }
+    return kEmpty;
   }
 };
 
 __global__ void k_lattice_insert(const int32_t* __restrict__ ijk, const uint8_t* __restrict__ on_lat,
-                                 int64_t N, LatticeGeom g, int32_t* map) {
+                                 int64_t N, LatticeHash g) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
     if (!on_lat[i]) continue;
     int q[kMaxDim];
     for (int k = 0; k < g.dim; ++k) q[k] = ijk[k * N + i];
-    int64_t l = g.lin(q);
-    if (l >= 0) atomicMin(&map[l], (int32_t)i);
+    g.insert(q, (int32_t)i);
   }
 }
 
@@ -147,8 +181,7 @@ __global__ void k_lattice_insert(const int32_t* __restrict__ ijk, const uint8_t*
 // has all 2d lattice neighbours; 1 (RBF-FD) otherwise.
 __global__ void k_classify(const int32_t* __restrict__ ijk, const uint8_t* __restrict__ on_lat,
                            const uint8_t* __restrict__ is_regular, const uint8_t* __restrict__ is_boundary,
-                           int64_t N, LatticeGeom g, const int32_t* __restrict__ map, uint8_t* kind,
-                           int* n_demoted) {
+                           int64_t N, LatticeHash g, uint8_t* kind, int* n_demoted) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
     bool reg = is_regular[i] != 0;
@@ -156,13 +189,11 @@ __global__ void k_classify(const int32_t* __restrict__ ijk, const uint8_t* __res
     if (mon) {
       int q[kMaxDim];
       for (int k = 0; k < g.dim; ++k) q[k] = ijk[k * N + i];
-      int64_t l = g.lin(q);
-      mon = (l >= 0) && map[l] == (int32_t)i;
+      mon = g.find(q) == (int32_t)i;
       for (int k = 0; k < g.dim && mon; ++k) {
         for (int s = -1; s <= 1 && mon; s += 2) {
           q[k] += s;
-          int64_t ln = g.lin(q);
-          mon = ln >= 0 && map[ln] != kEmpty;
+          mon = g.find(q) != kEmpty;
           q[k] -= s;
         }
       }
@@ -172,9 +203,10 @@ __global__ void k_classify(const int32_t* __restrict__ ijk, const uint8_t* __res
   }
 }
 
+// MON stencils; the group size is read on the device.
 __global__ void k_mon_stencil(const int32_t* __restrict__ ijk, const int32_t* __restrict__ mon_nodes,
-                              int64_t count, int64_t N, LatticeGeom g, const int32_t* __restrict__ map,
-                              int32_t* idx) {
+                              const int* __restrict__ count_dev, int64_t N, LatticeHash g, int32_t* idx) {
+  const int64_t count = *count_dev;
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < count;
        p += (int64_t)gridDim.x * blockDim.x) {
     int32_t c = mon_nodes[p];
@@ -185,7 +217,7 @@ __global__ void k_mon_stencil(const int32_t* __restrict__ ijk, const int32_t* __
     for (int k = 0; k < g.dim; ++k) {
       for (int s = -1; s <= 1; s += 2) {
         q[k] += s;
-        idx[(int64_t)j * count + p] = map[g.lin(q)];
+        idx[(int64_t)j * count + p] = g.find(q);
         q[k] -= s;
         ++j;
       }
@@ -207,8 +239,37 @@ struct CellGrid {
   }
 };
 
-__global__ void k_cell_count(const double* __restrict__ coords, int64_t N, CellGrid cg, int32_t* cell_of,
-                             int32_t* counts) {
+// Cell grid of the bounding box: cell edge h, enlarged by 1.5x until the
+// grid has at most 4N + 1024 cells (the scan buffers are sized for that).
+__global__ void k_grid_setup(const unsigned long long* __restrict__ bbox, int dim, double h, int64_t N,
+                             CellGrid* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  CellGrid cg;
+  cg.dim = dim;
+  double lo[kMaxDim], hi[kMaxDim];
+  for (int k = 0; k < kMaxDim; ++k) {
+    lo[k] = k < dim ? from_ordered(bbox[2 * k]) : 0.0;
+    hi[k] = k < dim ? from_ordered(bbox[2 * k + 1]) : 0.0;
+    cg.lo[k] = lo[k];
+  }
+  double cell = h;
+  for (int tries = 0; tries < 64; ++tries) {
+    int64_t ncell = 1;
+    for (int k = 0; k < kMaxDim; ++k) {
+      cg.g[k] = k < dim ? (int)fmin(floor((hi[k] - lo[k]) / cell) + 1.0, 1e9) : 1;
+      ncell *= cg.g[k];
+    }
+    if (ncell <= 4 * N + 1024) break;
+    cell *= 1.5;
+  }
+  cg.cell = cell;
+  cg.inv_cell = 1.0 / cell;
+  *out = cg;
+}
+
+__global__ void k_cell_count(const double* __restrict__ coords, int64_t N, const CellGrid* __restrict__ cgp,
+                             int32_t* cell_of, int32_t* counts) {
+  const CellGrid cg = *cgp;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
     int64_t l = 0;
@@ -263,13 +324,16 @@ template <int DIM, int QT>
 __global__ void __launch_bounds__(32 * QT) k_knn(const double* __restrict__ coords, int64_t N,
                                              const uint8_t* __restrict__ is_boundary,
                                              const double* __restrict__ normals, double h,
-                                             const int32_t* __restrict__ queries, int64_t nq, int n_full, CellGrid cg,
+                                             const int32_t* __restrict__ queries, const int* __restrict__ nq_dev,
+                                             int n_full, const CellGrid* __restrict__ cgp,
                                              const int32_t* __restrict__ start, const int32_t* __restrict__ sorted_id,
                                              const double* __restrict__ sorted_xyz,
                                              const uint8_t* __restrict__ sorted_bnd, int32_t* __restrict__ out_idx,
                                              unsigned* flags) {
   extern __shared__ unsigned char smem_raw[];
   const int B = blockDim.x;
+  const int64_t nq = *nq_dev;
+  const CellGrid cg = *cgp;
   double* kd = reinterpret_cast<double*>(smem_raw);
   int32_t* ki = reinterpret_cast<int32_t*>(kd + (size_t)n_full * B);
   const int t = threadIdx.x, sub = t % QT, lead = t - sub;
@@ -434,6 +498,12 @@ __global__ void __launch_bounds__(32 * QT) k_knn(const double* __restrict__ coor
 
 }  // namespace
 
+// Everything is enqueued without reading anything back: the lattice map is a
+// hash table sized from N, the cell grid is derived from the bounding box on
+// the device, group sizes stay in device memory and the kernels that need
+// them read them there; index arrays are allocated for the largest possible
+// group.  One synchronisation at the end reads the group sizes, the demotion
+// count and the status bits.
 hsm_status build_stencils(hsm_plan p) {
   cudaStream_t s = p->stream;
   const int64_t N = p->N;
@@ -443,169 +513,123 @@ hsm_status build_stencils(hsm_plan p) {
 
   // ---- bounds and lattice coordinates
   unsigned long long* bbox = nullptr;
-  int* lat = nullptr;
+  int* lat = nullptr;  // [0,6): lattice extents (unused), [6]: demoted, [7]: n_mon, [8]: n_rbf
   int32_t* ijk = nullptr;
   uint8_t* on_lat = nullptr;
   HSM_CUDA(p, dev_alloc(&bbox, 2 * kMaxDim, s));
   HSM_CUDA(p, dev_alloc(&lat, 2 * kMaxDim + 4, s));
   HSM_CUDA(p, dev_alloc(&ijk, (size_t)dim * N, s));
   HSM_CUDA(p, dev_alloc(&on_lat, N, s));
-  unsigned long long bb_init[2 * kMaxDim];
-  int lat_init[2 * kMaxDim + 4];
-  for (int k = 0; k < kMaxDim; ++k) {
-    bb_init[2 * k] = ~0ull;
-    bb_init[2 * k + 1] = 0ull;
-    lat_init[k] = 0x7fffffff;
-    lat_init[kMaxDim + k] = -0x7fffffff;
-  }
-  for (int k = 2 * kMaxDim; k < 2 * kMaxDim + 4; ++k) lat_init[k] = 0;
-  HSM_CUDA(p, cudaMemcpyAsync(bbox, bb_init, sizeof(bb_init), cudaMemcpyHostToDevice, s));
-  HSM_CUDA(p, cudaMemcpyAsync(lat, lat_init, sizeof(lat_init), cudaMemcpyHostToDevice, s));
+  // bbox: minima start at all-ones, maxima at zero (ordered-bit keys)
+  HSM_CUDA(p, cudaMemsetAsync(bbox, 0, 2 * kMaxDim * sizeof(unsigned long long), s));
+  for (int k = 0; k < kMaxDim; ++k) HSM_CUDA(p, cudaMemsetAsync(bbox + 2 * k, 0xff, sizeof(unsigned long long), s));
+  // lattice extents: minima 0x7f7f7f7f, maxima 0x80808080 (negative) -- only
+  // their initial values matter to k_bounds; counters zero
+  HSM_CUDA(p, cudaMemsetAsync(lat, 0x7f, kMaxDim * sizeof(int), s));
+  HSM_CUDA(p, cudaMemsetAsync(lat + kMaxDim, 0x80, kMaxDim * sizeof(int), s));
+  HSM_CUDA(p, cudaMemsetAsync(lat + 2 * kMaxDim, 0, 4 * sizeof(int), s));
   k_bounds<<<grid, T, 0, s>>>(p->coords, N, dim, 1.0 / p->h, bbox, lat, lat + kMaxDim, ijk, on_lat);
   p->launches += 1;
   HSM_CUDA(p, cudaGetLastError());
-  unsigned long long bb[2 * kMaxDim];
-  int lat_h[2 * kMaxDim + 4];
-  HSM_CUDA(p, cudaMemcpyAsync(bb, bbox, sizeof(bb), cudaMemcpyDeviceToHost, s));
-  HSM_CUDA(p, cudaMemcpyAsync(lat_h, lat, sizeof(lat_h), cudaMemcpyDeviceToHost, s));
-  HSM_CUDA(p, cudaStreamSynchronize(s));
 
-  // ---- lattice map and classification
-  LatticeGeom lg;
-  lg.dim = dim;
-  int64_t map_size = 1;
-  bool any_lat = lat_h[0] <= lat_h[kMaxDim];
-  for (int k = 0; k < kMaxDim; ++k) {
-    lg.lo[k] = any_lat && k < dim ? lat_h[k] : 0;
-    lg.ext[k] = any_lat && k < dim ? lat_h[kMaxDim + k] - lat_h[k] + 1 : 1;
-    map_size *= lg.ext[k];
-  }
-  if (map_size > (int64_t)1 << 30)
-    return set_error(p, HSM_EINVAL, "lattice extent too large for the lattice map (check h_regular)");
-  int32_t* map = nullptr;
-  HSM_CUDA(p, dev_alloc(&map, map_size, s));
-  HSM_CUDA(p, cudaMemsetAsync(map, 0x7f, map_size * sizeof(int32_t), s));
-  k_lattice_insert<<<grid, T, 0, s>>>(ijk, on_lat, N, lg, map);
+  // ---- lattice hash map and classification
+  unsigned long long cap = 1;
+  while (cap < 2ull * (unsigned long long)N) cap <<= 1;
+  LatticeHash lh;
+  lh.dim = dim;
+  lh.mask = cap - 1;
+  HSM_CUDA(p, dev_alloc(&lh.keys, cap, s));
+  HSM_CUDA(p, dev_alloc(&lh.vals, cap, s));
+  HSM_CUDA(p, cudaMemsetAsync(lh.keys, 0xff, cap * sizeof(unsigned long long), s));
+  HSM_CUDA(p, cudaMemsetAsync(lh.vals, 0x7f, cap * sizeof(int32_t), s));
+  k_lattice_insert<<<grid, T, 0, s>>>(ijk, on_lat, N, lh);
   int* d_demoted = lat + 2 * kMaxDim;
-  k_classify<<<grid, T, 0, s>>>(ijk, on_lat, p->is_regular, p->is_boundary, N, lg, map, p->kind, d_demoted);
+  int* counts = lat + 2 * kMaxDim + 1;
+  k_classify<<<grid, T, 0, s>>>(ijk, on_lat, p->is_regular, p->is_boundary, N, lh, p->kind, d_demoted);
   p->launches += 2;
   HSM_CUDA(p, cudaGetLastError());
 
-  // ---- group lists (ascending node ids) and positions
-  int* counts = lat + 2 * kMaxDim + 1;
+  // ---- group lists (ascending node ids) and positions; sizes stay on the device
   int32_t* list_mon = nullptr;
   int32_t* list_rbf = nullptr;
   HSM_CUDA(p, dev_alloc(&list_mon, N, s));
   HSM_CUDA(p, dev_alloc(&list_rbf, N, s));
-  int cnt_h[3];
-  HSM_CUDA(p, cudaMemcpyAsync(&cnt_h[2], d_demoted, sizeof(int), cudaMemcpyDeviceToHost, s));
   HSM_CUDA(p, select_indices(p->kind, 0, N, list_mon, p->pos, counts, s));
   HSM_CUDA(p, select_indices(p->kind, 1, N, list_rbf, p->pos, counts + 1, s));
   p->launches += 6;
-  HSM_CUDA(p, cudaMemcpyAsync(cnt_h, counts, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
-  HSM_CUDA(p, cudaStreamSynchronize(s));
-  p->n_demoted = cnt_h[2];
-  p->mon.count = cnt_h[0];
-  p->rbf.count = cnt_h[1];
   p->mon.width = 2 * dim + 1;
   p->rbf.width = p->n;
   p->mon.nodes = list_mon;
   p->rbf.nodes = list_rbf;
-  HSM_CUDA(p, dev_alloc(&p->mon.idx, (size_t)p->mon.width * p->mon.count, s));
-  HSM_CUDA(p, dev_alloc(&p->rbf.idx, (size_t)p->rbf.width * p->rbf.count, s));
-  if (p->mon.count) {
-    int gm = (int)std::min<int64_t>(ceil_div(p->mon.count, T), (int64_t)num_sms() * 8);
-    k_mon_stencil<<<gm, T, 0, s>>>(ijk, list_mon, p->mon.count, N, lg, map, p->mon.idx);
-    p->launches += 1;
-    HSM_CUDA(p, cudaGetLastError());
-  }
+  HSM_CUDA(p, dev_alloc(&p->mon.idx, (size_t)p->mon.width * N, s));
+  HSM_CUDA(p, dev_alloc(&p->rbf.idx, (size_t)p->rbf.width * N, s));
+  k_mon_stencil<<<grid, T, 0, s>>>(ijk, list_mon, counts, N, lh, p->mon.idx);
+  p->launches += 1;
+  HSM_CUDA(p, cudaGetLastError());
 
   // ---- kNN for the RBF-FD group
-  if (p->rbf.count) {
-    if (N < p->n) return set_error(p, HSM_EINVAL, "fewer nodes than the stencil size");
-    CellGrid cg;
-    cg.dim = dim;
-    double ext_max = 0.0;
-    for (int k = 0; k < kMaxDim; ++k) {
-      double lo = k < dim ? host_from_ordered(bb[2 * k]) : 0.0;
-      double hi = k < dim ? host_from_ordered(bb[2 * k + 1]) : 0.0;
-      cg.lo[k] = lo;
-      ext_max = std::max(ext_max, hi - lo);
-      (void)hi;
-    }
-    double cell = p->h;
-    int64_t ncell = 0;
-    for (int tries = 0; tries < 64; ++tries) {
-      ncell = 1;
-      for (int k = 0; k < kMaxDim; ++k) {
-        double hi = k < dim ? host_from_ordered(bb[2 * k + 1]) : cg.lo[k];
-        cg.g[k] = k < dim ? (int)std::min<double>(floor((hi - cg.lo[k]) / cell) + 1.0, 1e9) : 1;
-        ncell *= cg.g[k];
-      }
-      if (ncell <= 4 * N + 1024) break;
-      cell *= 1.5;
-    }
-    cg.cell = cell;
-    cg.inv_cell = 1.0 / cell;
-    int32_t *cell_of = nullptr, *cstart = nullptr, *ccount = nullptr, *sorted_id = nullptr;
-    double* sorted_xyz = nullptr;
-    uint8_t* sorted_bnd = nullptr;
-    HSM_CUDA(p, dev_alloc(&cell_of, N, s));
-    HSM_CUDA(p, dev_alloc(&cstart, ncell + 1, s));
-    HSM_CUDA(p, dev_alloc(&ccount, ncell, s));
-    HSM_CUDA(p, dev_alloc(&sorted_id, N, s));
-    HSM_CUDA(p, dev_alloc(&sorted_xyz, (size_t)N * kMaxDim, s));
-    HSM_CUDA(p, dev_alloc(&sorted_bnd, N, s));
-    HSM_CUDA(p, cudaMemsetAsync(ccount, 0, ncell * sizeof(int32_t), s));
-    k_cell_count<<<grid, T, 0, s>>>(p->coords, N, cg, cell_of, ccount);
-    HSM_CUDA(p, cudaGetLastError());
-    HSM_CUDA(p, exclusive_scan_i32(ccount, cstart, ncell, s));
-    p->launches += 4;
-    HSM_CUDA(p, cudaMemsetAsync(ccount, 0, ncell * sizeof(int32_t), s));
-    k_cell_scatter<<<grid, T, 0, s>>>(p->coords, p->is_boundary, N, dim, cell_of, cstart, ccount, sorted_id,
-                                      sorted_xyz, sorted_bnd);
-    p->launches += 2;
-    HSM_CUDA(p, cudaGetLastError());
+  CellGrid* cgd = nullptr;
+  const int64_t ncell_max = 4 * N + 1024;
+  int32_t *cell_of = nullptr, *cstart = nullptr, *ccount = nullptr, *sorted_id = nullptr;
+  double* sorted_xyz = nullptr;
+  uint8_t* sorted_bnd = nullptr;
+  HSM_CUDA(p, dev_alloc(&cgd, 1, s));
+  HSM_CUDA(p, dev_alloc(&cell_of, N, s));
+  HSM_CUDA(p, dev_alloc(&cstart, ncell_max + 1, s));
+  HSM_CUDA(p, dev_alloc(&ccount, ncell_max, s));
+  HSM_CUDA(p, dev_alloc(&sorted_id, N, s));
+  HSM_CUDA(p, dev_alloc(&sorted_xyz, (size_t)N * kMaxDim, s));
+  HSM_CUDA(p, dev_alloc(&sorted_bnd, N, s));
+  k_grid_setup<<<1, 32, 0, s>>>(bbox, dim, p->h, N, cgd);
+  HSM_CUDA(p, cudaMemsetAsync(ccount, 0, ncell_max * sizeof(int32_t), s));
+  k_cell_count<<<grid, T, 0, s>>>(p->coords, N, cgd, cell_of, ccount);
+  HSM_CUDA(p, cudaGetLastError());
+  HSM_CUDA(p, exclusive_scan_i32(ccount, cstart, ncell_max, s));
+  p->launches += 5;
+  HSM_CUDA(p, cudaMemsetAsync(ccount, 0, ncell_max * sizeof(int32_t), s));
+  k_cell_scatter<<<grid, T, 0, s>>>(p->coords, p->is_boundary, N, dim, cell_of, cstart, ccount, sorted_id,
+                                    sorted_xyz, sorted_bnd);
+  p->launches += 2;
+  HSM_CUDA(p, cudaGetLastError());
+  {
     // p->tune.knn_qt threads per query (1, 2 or 4; tuned), blocks of 32 * qt
     const int qt = p->tune.knn_qt == 4 ? 4 : (p->tune.knn_qt == 2 ? 2 : 1);
     const int KT = 32 * qt;
     size_t smem = (size_t)p->n * KT * (sizeof(double) + sizeof(int32_t));
-    int gk = (int)std::min<int64_t>(ceil_div(p->rbf.count, 32), (int64_t)num_sms() * 16);
+    int gk = (int)std::min<int64_t>(ceil_div(N, 32), (int64_t)num_sms() * 16);
     void* fn = nullptr;
     if (dim == 2) fn = qt == 4 ? (void*)k_knn<2, 4> : (qt == 2 ? (void*)k_knn<2, 2> : (void*)k_knn<2, 1>);
     else fn = qt == 4 ? (void*)k_knn<3, 4> : (qt == 2 ? (void*)k_knn<3, 2> : (void*)k_knn<3, 1>);
     if (smem > 48 * 1024) HSM_CUDA(p, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    {
-      const double* coords = p->coords;
-      const uint8_t* isb = p->is_boundary;
-      const double* nrm = p->normals;
-      double hh = p->h;
-      const int32_t* qlist = list_rbf;
-      int64_t nq = p->rbf.count;
-      int nf = p->n;
-      int32_t* outp = p->rbf.idx;
-      unsigned* fl = p->dev_flags;
-      void* args[] = {(void*)&coords, (void*)&N, (void*)&isb, (void*)&nrm, (void*)&hh, (void*)&qlist, (void*)&nq,
-                      (void*)&nf, (void*)&cg, (void*)&cstart, (void*)&sorted_id, (void*)&sorted_xyz,
-                      (void*)&sorted_bnd, (void*)&outp, (void*)&fl};
-      HSM_CUDA(p, cudaLaunchKernel(fn, dim3(gk), dim3(KT), args, smem, s));
-    }
-    HSM_CUDA(p, cudaGetLastError());
-    dev_free(&cell_of, s);
-    dev_free(&cstart, s);
-    dev_free(&ccount, s);
-    dev_free(&sorted_id, s);
-    dev_free(&sorted_xyz, s);
-    dev_free(&sorted_bnd, s);
+    const double* coords = p->coords;
+    const uint8_t* isb = p->is_boundary;
+    const double* nrm = p->normals;
+    double hh = p->h;
+    const int32_t* qlist = list_rbf;
+    const int* nqd = counts + 1;
+    int nf = p->n;
+    int32_t* outp = p->rbf.idx;
+    unsigned* fl = p->dev_flags;
+    int64_t NN = N;
+    void* args[] = {(void*)&coords, (void*)&NN, (void*)&isb, (void*)&nrm, (void*)&hh, (void*)&qlist, (void*)&nqd,
+                    (void*)&nf, (void*)&cgd, (void*)&cstart, (void*)&sorted_id, (void*)&sorted_xyz,
+                    (void*)&sorted_bnd, (void*)&outp, (void*)&fl};
+    HSM_CUDA(p, cudaLaunchKernel(fn, dim3(gk), dim3(KT), args, smem, s));
+    p->launches += 1;
   }
-  dev_free(&bbox, s);
-  dev_free(&lat, s);
-  dev_free(&ijk, s);
-  dev_free(&on_lat, s);
-  dev_free(&map, s);
+  // ---- the one read-back: group sizes, demotions, status bits
+  int cnt_h[3] = {0, 0, 0};
   unsigned flags = 0;
+  HSM_CUDA(p, cudaMemcpyAsync(cnt_h, lat + 2 * kMaxDim, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
   HSM_CUDA(p, cudaMemcpyAsync(&flags, p->dev_flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  for (void* ptr : {(void*)cell_of, (void*)cstart, (void*)ccount, (void*)sorted_id, (void*)sorted_xyz,
+                    (void*)sorted_bnd, (void*)cgd, (void*)bbox, (void*)lat, (void*)ijk, (void*)on_lat,
+                    (void*)lh.keys, (void*)lh.vals})
+    cudaFreeAsync(ptr, s);
   HSM_CUDA(p, cudaStreamSynchronize(s));
+  p->n_demoted = cnt_h[0];
+  p->mon.count = cnt_h[1];
+  p->rbf.count = cnt_h[2];
   if (flags & kDevKnnShort) return set_error(p, HSM_EINVAL, "not enough candidate nodes for an RBF-FD stencil");
   p->stencils_built = true;
   return HSM_OK;
