@@ -148,6 +148,7 @@ static void free_plan_device(hsm_plan p) {
   dev_free(&p->pos, s);
   dev_free(&p->dev_flags, s);
   dev_free(&p->dev_count, s);
+  free_build_ws(p);
 }
 
 hsm_status hsm_plan_destroy(hsm_plan p) {
@@ -184,13 +185,13 @@ hsm_status hsm_plan_profile(hsm_plan p, float* phase_ms, int64_t* launches) {
 hsm_status hsm_plan_build_stencils(hsm_plan p) {
   if (!p) return set_error(nullptr, HSM_EINVAL, "plan is NULL");
   cudaStream_t s = p->stream;
-  free_plan_device(p);
+  // weights of an earlier build are stale; stencil arrays and the build
+  // workspace persist across builds
+  for (Group* g : {&p->mon, &p->rbf}) {
+    dev_free(&g->w64, s);
+    dev_free(&g->w32, s);
+  }
   p->stencils_built = p->weights_built = false;
-  HSM_CUDA(p, dev_alloc(&p->kind, p->N, s));
-  HSM_CUDA(p, dev_alloc(&p->pos, p->N, s));
-  HSM_CUDA(p, dev_alloc(&p->dev_flags, 4, s));
-  HSM_CUDA(p, dev_alloc(&p->dev_count, 4, s));
-  HSM_CUDA(p, cudaMemsetAsync(p->dev_flags, 0, 4 * sizeof(unsigned), s));
   // upper-triangle pair table and monomial exponents for the RBF-FD kernels,
   // uploaded once per plan from host copies the plan keeps
   if (!p->pairs) {

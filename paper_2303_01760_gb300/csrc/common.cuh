@@ -45,6 +45,32 @@ struct Tuning {
 
 struct Mlp;  // learned predictor (mlp.cu)
 
+// Persistent workspace of the stencil build (sizes depend only on N), so the
+// whole build can be replayed as one CUDA graph.
+struct BuildWs {
+  unsigned long long* bbox = nullptr;  // [2 * kMaxDim] ordered-bit extrema
+  int* lat = nullptr;                  // [2 * kMaxDim + 4]: lattice extents, demoted, n_mon, n_rbf
+  int32_t* ijk = nullptr;              // [dim][N]
+  uint8_t* on_lat = nullptr;           // [N]
+  unsigned long long* hkeys = nullptr; // lattice hash
+  int32_t* hvals = nullptr;
+  unsigned long long hcap = 0;
+  void* cgd = nullptr;                 // CellGrid on the device
+  int32_t* cell_of = nullptr;          // [N]
+  int32_t* cstart = nullptr;           // [4N + 1025]
+  int32_t* ccount = nullptr;           // [4N + 1024]
+  int32_t* sorted_id = nullptr;        // [N]
+  double* sorted_xyz = nullptr;        // [N][kMaxDim]
+  uint8_t* sorted_bnd = nullptr;       // [N]
+  int32_t* scan_ws = nullptr;          // scan block sums
+  int* readback = nullptr;             // pinned host: demoted, n_mon, n_rbf, flags
+  cudaGraphExec_t graph = nullptr;
+  int graph_qt = 0;                    // kNN variant the graph was captured with
+  int graph_kernels = 0;               // kernels per replay
+  cudaStream_t cap = nullptr;
+  bool ready = false;
+};
+
 }  // namespace hsm
 
 struct hsm_plan_s {
@@ -79,6 +105,7 @@ struct hsm_plan_s {
   hsm::Tuning tune;
   hsm_mlp mlp = nullptr;         // attached learned predictor (not owned)
   std::string last_error;
+  hsm::BuildWs ws;               // stencil-build workspace and graph
   int64_t launches = 0;          // kernels launched by this plan
   bool timing = false;
   cudaEvent_t ev[2 * HSM_PHASE_COUNT] = {};
@@ -146,13 +173,17 @@ inline int num_sms() {
 
 // ---- scan.cu -------------------------------------------------------------
 // Exclusive prefix sum of in[0..n) (int32 counts) into out[0..n], out[n] = total.
-cudaError_t exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s);
+// ws: scratch of scan_scratch(n) ints, or nullptr to allocate one.
+cudaError_t exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s, int32_t* ws = nullptr);
 // List of indices i (ascending) with key[i] == want; count written to *count_dev.
 cudaError_t select_indices(const uint8_t* key, uint8_t want, int64_t n, int32_t* out_list,
-                           int32_t* out_pos, int* count_dev, cudaStream_t s);
+                           int32_t* out_pos, int* count_dev, cudaStream_t s, int32_t* ws = nullptr);
+int64_t scan_scratch(int64_t n);
 
 // ---- stencils.cu ---------------------------------------------------------
 hsm_status build_stencils(hsm_plan p);
+hsm_status alloc_build_ws(hsm_plan p);
+void free_build_ws(hsm_plan p);
 
 // ---- weights.cu ----------------------------------------------------------
 hsm_status compute_mon_weights(hsm_plan p, uint8_t* status);

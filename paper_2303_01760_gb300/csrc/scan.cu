@@ -109,28 +109,33 @@ struct WriteSelect {
 };
 
 template <typename F, typename W>
-cudaError_t run_scan(F f, W w, int64_t n, int32_t* grand, cudaStream_t s) {
+cudaError_t run_scan(F f, W w, int64_t n, int32_t* grand, cudaStream_t s, int32_t* ws) {
   int nb = (int)ceil_div(n > 0 ? n : 1, kScanTile);
-  int32_t* sums = nullptr;
-  cudaError_t e = dev_alloc(&sums, nb, s);
-  if (e != cudaSuccess) return e;
+  int32_t* sums = ws;
+  cudaError_t e = cudaSuccess;
+  if (!sums) {
+    e = dev_alloc(&sums, nb, s);
+    if (e != cudaSuccess) return e;
+  }
   k_block_sums<<<nb, kScanThreads, 0, s>>>(f, n, sums);
   k_scan_sums<<<1, kScanThreads, 0, s>>>(sums, nb, grand);
   k_block_write<<<nb, kScanThreads, 0, s>>>(f, n, sums, w);
   e = cudaGetLastError();
-  dev_free(&sums, s);
+  if (!ws) dev_free(&sums, s);
   return e;
 }
 
 }  // namespace
 
-cudaError_t exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s) {
-  return run_scan(CountsIn{in}, WriteExcl{out}, n, out + n, s);
+cudaError_t exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s, int32_t* ws) {
+  return run_scan(CountsIn{in}, WriteExcl{out}, n, out + n, s, ws);
 }
 
 cudaError_t select_indices(const uint8_t* key, uint8_t want, int64_t n, int32_t* out_list,
-                           int32_t* out_pos, int* count_dev, cudaStream_t s) {
-  return run_scan(KeyEq{key, want}, WriteSelect{out_list, out_pos}, n, count_dev, s);
+                           int32_t* out_pos, int* count_dev, cudaStream_t s, int32_t* ws) {
+  return run_scan(KeyEq{key, want}, WriteSelect{out_list, out_pos}, n, count_dev, s, ws);
 }
+
+int64_t scan_scratch(int64_t n) { return ceil_div(n > 0 ? n : 1, kScanTile); }
 
 }  // namespace hsm

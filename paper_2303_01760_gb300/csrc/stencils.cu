@@ -498,139 +498,224 @@ __global__ void __launch_bounds__(32 * QT) k_knn(const double* __restrict__ coor
 
 }  // namespace
 
-// Everything is enqueued without reading anything back: the lattice map is a
-// hash table sized from N, the cell grid is derived from the bounding box on
-// the device, group sizes stay in device memory and the kernels that need
-// them read them there; index arrays are allocated for the largest possible
-// group.  One synchronisation at the end reads the group sizes, the demotion
-// count and the status bits.
-hsm_status build_stencils(hsm_plan p) {
+// The workspace of the build depends only on N, dim and n, so it is
+// allocated once per plan; the group node lists and index arrays are sized for
+// the largest possible group.
+hsm_status alloc_build_ws(hsm_plan p) {
+  BuildWs& w = p->ws;
+  if (w.ready) return HSM_OK;
   cudaStream_t s = p->stream;
+  const int64_t N = p->N;
+  const int64_t ncell_max = 4 * N + 1024;
+  unsigned long long cap = 1;
+  while (cap < 2ull * (unsigned long long)N) cap <<= 1;
+  w.hcap = cap;
+  CellGrid* cg = nullptr;
+  HSM_CUDA(p, dev_alloc(&w.bbox, 2 * kMaxDim, s));
+  HSM_CUDA(p, dev_alloc(&w.lat, 2 * kMaxDim + 4, s));
+  HSM_CUDA(p, dev_alloc(&w.ijk, (size_t)p->dim * N, s));
+  HSM_CUDA(p, dev_alloc(&w.on_lat, N, s));
+  HSM_CUDA(p, dev_alloc(&w.hkeys, cap, s));
+  HSM_CUDA(p, dev_alloc(&w.hvals, cap, s));
+  HSM_CUDA(p, dev_alloc(&cg, 1, s));
+  w.cgd = cg;
+  HSM_CUDA(p, dev_alloc(&w.cell_of, N, s));
+  HSM_CUDA(p, dev_alloc(&w.cstart, ncell_max + 1, s));
+  HSM_CUDA(p, dev_alloc(&w.ccount, ncell_max, s));
+  HSM_CUDA(p, dev_alloc(&w.sorted_id, N, s));
+  HSM_CUDA(p, dev_alloc(&w.sorted_xyz, (size_t)N * kMaxDim, s));
+  HSM_CUDA(p, dev_alloc(&w.sorted_bnd, N, s));
+  HSM_CUDA(p, dev_alloc(&w.scan_ws, scan_scratch(ncell_max), s));
+  HSM_CUDA(p, dev_alloc(&p->kind, N, s));
+  HSM_CUDA(p, dev_alloc(&p->pos, N, s));
+  HSM_CUDA(p, dev_alloc(&p->dev_flags, 4, s));
+  HSM_CUDA(p, dev_alloc(&p->dev_count, 4, s));
+  p->mon.width = 2 * p->dim + 1;
+  p->rbf.width = p->n;
+  HSM_CUDA(p, dev_alloc(&p->mon.nodes, N, s));
+  HSM_CUDA(p, dev_alloc(&p->rbf.nodes, N, s));
+  HSM_CUDA(p, dev_alloc(&p->mon.idx, (size_t)p->mon.width * N, s));
+  HSM_CUDA(p, dev_alloc(&p->rbf.idx, (size_t)p->rbf.width * N, s));
+  HSM_CUDA(p, cudaMallocHost((void**)&w.readback, 4 * sizeof(int)));
+  HSM_CUDA(p, cudaStreamCreateWithFlags(&w.cap, cudaStreamNonBlocking));
+  w.ready = true;
+  return HSM_OK;
+}
+
+void free_build_ws(hsm_plan p) {
+  BuildWs& w = p->ws;
+  cudaStream_t s = p->stream;
+  if (w.graph) cudaGraphExecDestroy(w.graph);
+  w.graph = nullptr;
+  for (void** ptr : {(void**)&w.bbox, (void**)&w.lat, (void**)&w.ijk, (void**)&w.on_lat, (void**)&w.hkeys,
+                     (void**)&w.hvals, (void**)&w.cgd, (void**)&w.cell_of, (void**)&w.cstart, (void**)&w.ccount,
+                     (void**)&w.sorted_id, (void**)&w.sorted_xyz, (void**)&w.sorted_bnd, (void**)&w.scan_ws})
+    dev_free(ptr, s);
+  if (w.readback) cudaFreeHost(w.readback);
+  w.readback = nullptr;
+  if (w.cap) cudaStreamDestroy(w.cap);
+  w.cap = nullptr;
+  w.ready = false;
+}
+
+namespace {
+
+#define HSM_TRY(x)                       \
+  do {                                   \
+    cudaError_t e_ = (x);                \
+    if (e_ != cudaSuccess) return e_;    \
+  } while (0)
+
+// Enqueues the whole build on stream s without reading anything back: the
+// lattice map is a hash table sized from N, the cell grid is derived from the
+// bounding box on the device, group sizes stay in device memory and the
+// kernels that need them read them there.  The last node copies the group
+// sizes, the demotion count and the status bits to pinned host memory.
+// Returns the number of kernels enqueued in *nk.
+cudaError_t enqueue_build(hsm_plan p, cudaStream_t s, int qt, int* nk) {
+  BuildWs& w = p->ws;
   const int64_t N = p->N;
   const int dim = p->dim;
   const int T = 256;
   const int grid = (int)std::min<int64_t>(ceil_div(N, T), (int64_t)num_sms() * 8);
+  int k = 0;
 
   // ---- bounds and lattice coordinates
-  unsigned long long* bbox = nullptr;
-  int* lat = nullptr;  // [0,6): lattice extents (unused), [6]: demoted, [7]: n_mon, [8]: n_rbf
-  int32_t* ijk = nullptr;
-  uint8_t* on_lat = nullptr;
-  HSM_CUDA(p, dev_alloc(&bbox, 2 * kMaxDim, s));
-  HSM_CUDA(p, dev_alloc(&lat, 2 * kMaxDim + 4, s));
-  HSM_CUDA(p, dev_alloc(&ijk, (size_t)dim * N, s));
-  HSM_CUDA(p, dev_alloc(&on_lat, N, s));
-  // bbox: minima start at all-ones, maxima at zero (ordered-bit keys)
-  HSM_CUDA(p, cudaMemsetAsync(bbox, 0, 2 * kMaxDim * sizeof(unsigned long long), s));
-  for (int k = 0; k < kMaxDim; ++k) HSM_CUDA(p, cudaMemsetAsync(bbox + 2 * k, 0xff, sizeof(unsigned long long), s));
+  int* lat = w.lat;  // [0,6): lattice extents (unused), [6]: demoted, [7]: n_mon, [8]: n_rbf, [9]: flags
+  HSM_TRY(cudaMemsetAsync(p->dev_flags, 0, 4 * sizeof(unsigned), s));
+  // bbox: minima start at all-ones, maxima at zero (ordered-bit keys), stored
+  // interleaved [min_k, max_k]
+  HSM_TRY(cudaMemsetAsync(w.bbox, 0, 2 * kMaxDim * sizeof(unsigned long long), s));
+  for (int d = 0; d < kMaxDim; ++d) HSM_TRY(cudaMemsetAsync(w.bbox + 2 * d, 0xff, sizeof(unsigned long long), s));
   // lattice extents: minima 0x7f7f7f7f, maxima 0x80808080 (negative) -- only
   // their initial values matter to k_bounds; counters zero
-  HSM_CUDA(p, cudaMemsetAsync(lat, 0x7f, kMaxDim * sizeof(int), s));
-  HSM_CUDA(p, cudaMemsetAsync(lat + kMaxDim, 0x80, kMaxDim * sizeof(int), s));
-  HSM_CUDA(p, cudaMemsetAsync(lat + 2 * kMaxDim, 0, 4 * sizeof(int), s));
-  k_bounds<<<grid, T, 0, s>>>(p->coords, N, dim, 1.0 / p->h, bbox, lat, lat + kMaxDim, ijk, on_lat);
-  p->launches += 1;
-  HSM_CUDA(p, cudaGetLastError());
+  HSM_TRY(cudaMemsetAsync(lat, 0x7f, kMaxDim * sizeof(int), s));
+  HSM_TRY(cudaMemsetAsync(lat + kMaxDim, 0x80, kMaxDim * sizeof(int), s));
+  HSM_TRY(cudaMemsetAsync(lat + 2 * kMaxDim, 0, 4 * sizeof(int), s));
+  k_bounds<<<grid, T, 0, s>>>(p->coords, N, dim, 1.0 / p->h, w.bbox, lat, lat + kMaxDim, w.ijk, w.on_lat);
+  ++k;
+  HSM_TRY(cudaGetLastError());
 
   // ---- lattice hash map and classification
-  unsigned long long cap = 1;
-  while (cap < 2ull * (unsigned long long)N) cap <<= 1;
   LatticeHash lh;
   lh.dim = dim;
-  lh.mask = cap - 1;
-  HSM_CUDA(p, dev_alloc(&lh.keys, cap, s));
-  HSM_CUDA(p, dev_alloc(&lh.vals, cap, s));
-  HSM_CUDA(p, cudaMemsetAsync(lh.keys, 0xff, cap * sizeof(unsigned long long), s));
-  HSM_CUDA(p, cudaMemsetAsync(lh.vals, 0x7f, cap * sizeof(int32_t), s));
-  k_lattice_insert<<<grid, T, 0, s>>>(ijk, on_lat, N, lh);
+  lh.mask = w.hcap - 1;
+  lh.keys = w.hkeys;
+  lh.vals = w.hvals;
+  HSM_TRY(cudaMemsetAsync(lh.keys, 0xff, w.hcap * sizeof(unsigned long long), s));
+  HSM_TRY(cudaMemsetAsync(lh.vals, 0x7f, w.hcap * sizeof(int32_t), s));
+  k_lattice_insert<<<grid, T, 0, s>>>(w.ijk, w.on_lat, N, lh);
   int* d_demoted = lat + 2 * kMaxDim;
   int* counts = lat + 2 * kMaxDim + 1;
-  k_classify<<<grid, T, 0, s>>>(ijk, on_lat, p->is_regular, p->is_boundary, N, lh, p->kind, d_demoted);
-  p->launches += 2;
-  HSM_CUDA(p, cudaGetLastError());
+  k_classify<<<grid, T, 0, s>>>(w.ijk, w.on_lat, p->is_regular, p->is_boundary, N, lh, p->kind, d_demoted);
+  k += 2;
+  HSM_TRY(cudaGetLastError());
 
-  // ---- group lists (ascending node ids) and positions; sizes stay on the device
-  int32_t* list_mon = nullptr;
-  int32_t* list_rbf = nullptr;
-  HSM_CUDA(p, dev_alloc(&list_mon, N, s));
-  HSM_CUDA(p, dev_alloc(&list_rbf, N, s));
-  HSM_CUDA(p, select_indices(p->kind, 0, N, list_mon, p->pos, counts, s));
-  HSM_CUDA(p, select_indices(p->kind, 1, N, list_rbf, p->pos, counts + 1, s));
-  p->launches += 6;
-  p->mon.width = 2 * dim + 1;
-  p->rbf.width = p->n;
-  p->mon.nodes = list_mon;
-  p->rbf.nodes = list_rbf;
-  HSM_CUDA(p, dev_alloc(&p->mon.idx, (size_t)p->mon.width * N, s));
-  HSM_CUDA(p, dev_alloc(&p->rbf.idx, (size_t)p->rbf.width * N, s));
-  k_mon_stencil<<<grid, T, 0, s>>>(ijk, list_mon, counts, N, lh, p->mon.idx);
-  p->launches += 1;
-  HSM_CUDA(p, cudaGetLastError());
+  // ---- group lists (ascending node ids) and positions
+  HSM_TRY(select_indices(p->kind, 0, N, p->mon.nodes, p->pos, counts, s, w.scan_ws));
+  HSM_TRY(select_indices(p->kind, 1, N, p->rbf.nodes, p->pos, counts + 1, s, w.scan_ws));
+  k += 6;
+  k_mon_stencil<<<grid, T, 0, s>>>(w.ijk, p->mon.nodes, counts, N, lh, p->mon.idx);
+  ++k;
+  HSM_TRY(cudaGetLastError());
 
   // ---- kNN for the RBF-FD group
-  CellGrid* cgd = nullptr;
   const int64_t ncell_max = 4 * N + 1024;
-  int32_t *cell_of = nullptr, *cstart = nullptr, *ccount = nullptr, *sorted_id = nullptr;
-  double* sorted_xyz = nullptr;
-  uint8_t* sorted_bnd = nullptr;
-  HSM_CUDA(p, dev_alloc(&cgd, 1, s));
-  HSM_CUDA(p, dev_alloc(&cell_of, N, s));
-  HSM_CUDA(p, dev_alloc(&cstart, ncell_max + 1, s));
-  HSM_CUDA(p, dev_alloc(&ccount, ncell_max, s));
-  HSM_CUDA(p, dev_alloc(&sorted_id, N, s));
-  HSM_CUDA(p, dev_alloc(&sorted_xyz, (size_t)N * kMaxDim, s));
-  HSM_CUDA(p, dev_alloc(&sorted_bnd, N, s));
-  k_grid_setup<<<1, 32, 0, s>>>(bbox, dim, p->h, N, cgd);
-  HSM_CUDA(p, cudaMemsetAsync(ccount, 0, ncell_max * sizeof(int32_t), s));
-  k_cell_count<<<grid, T, 0, s>>>(p->coords, N, cgd, cell_of, ccount);
-  HSM_CUDA(p, cudaGetLastError());
-  HSM_CUDA(p, exclusive_scan_i32(ccount, cstart, ncell_max, s));
-  p->launches += 5;
-  HSM_CUDA(p, cudaMemsetAsync(ccount, 0, ncell_max * sizeof(int32_t), s));
-  k_cell_scatter<<<grid, T, 0, s>>>(p->coords, p->is_boundary, N, dim, cell_of, cstart, ccount, sorted_id,
-                                    sorted_xyz, sorted_bnd);
-  p->launches += 2;
-  HSM_CUDA(p, cudaGetLastError());
+  CellGrid* cgd = static_cast<CellGrid*>(w.cgd);
+  k_grid_setup<<<1, 32, 0, s>>>(w.bbox, dim, p->h, N, cgd);
+  HSM_TRY(cudaMemsetAsync(w.ccount, 0, ncell_max * sizeof(int32_t), s));
+  k_cell_count<<<grid, T, 0, s>>>(p->coords, N, cgd, w.cell_of, w.ccount);
+  HSM_TRY(cudaGetLastError());
+  HSM_TRY(exclusive_scan_i32(w.ccount, w.cstart, ncell_max, s, w.scan_ws));
+  k += 5;
+  HSM_TRY(cudaMemsetAsync(w.ccount, 0, ncell_max * sizeof(int32_t), s));
+  k_cell_scatter<<<grid, T, 0, s>>>(p->coords, p->is_boundary, N, dim, w.cell_of, w.cstart, w.ccount, w.sorted_id,
+                                    w.sorted_xyz, w.sorted_bnd);
+  ++k;
+  HSM_TRY(cudaGetLastError());
   {
-    // p->tune.knn_qt threads per query (1, 2 or 4; tuned), blocks of 32 * qt
-    const int qt = p->tune.knn_qt == 4 ? 4 : (p->tune.knn_qt == 2 ? 2 : 1);
+    // qt threads per query (1, 2 or 4), blocks of 32 * qt
     const int KT = 32 * qt;
     size_t smem = (size_t)p->n * KT * (sizeof(double) + sizeof(int32_t));
     int gk = (int)std::min<int64_t>(ceil_div(N, 32), (int64_t)num_sms() * 16);
     void* fn = nullptr;
     if (dim == 2) fn = qt == 4 ? (void*)k_knn<2, 4> : (qt == 2 ? (void*)k_knn<2, 2> : (void*)k_knn<2, 1>);
     else fn = qt == 4 ? (void*)k_knn<3, 4> : (qt == 2 ? (void*)k_knn<3, 2> : (void*)k_knn<3, 1>);
-    if (smem > 48 * 1024) HSM_CUDA(p, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const double* coords = p->coords;
     const uint8_t* isb = p->is_boundary;
     const double* nrm = p->normals;
     double hh = p->h;
-    const int32_t* qlist = list_rbf;
+    const int32_t* qlist = p->rbf.nodes;
     const int* nqd = counts + 1;
     int nf = p->n;
     int32_t* outp = p->rbf.idx;
     unsigned* fl = p->dev_flags;
     int64_t NN = N;
+    int32_t* cs = w.cstart;
+    int32_t* sid = w.sorted_id;
+    double* sxyz = w.sorted_xyz;
+    uint8_t* sb = w.sorted_bnd;
     void* args[] = {(void*)&coords, (void*)&NN, (void*)&isb, (void*)&nrm, (void*)&hh, (void*)&qlist, (void*)&nqd,
-                    (void*)&nf, (void*)&cgd, (void*)&cstart, (void*)&sorted_id, (void*)&sorted_xyz,
-                    (void*)&sorted_bnd, (void*)&outp, (void*)&fl};
-    HSM_CUDA(p, cudaLaunchKernel(fn, dim3(gk), dim3(KT), args, smem, s));
-    p->launches += 1;
+                    (void*)&nf, (void*)&cgd, (void*)&cs, (void*)&sid, (void*)&sxyz,
+                    (void*)&sb, (void*)&outp, (void*)&fl};
+    HSM_TRY(cudaLaunchKernel(fn, dim3(gk), dim3(KT), args, smem, s));
+    ++k;
   }
-  // ---- the one read-back: group sizes, demotions, status bits
-  int cnt_h[3] = {0, 0, 0};
-  unsigned flags = 0;
-  HSM_CUDA(p, cudaMemcpyAsync(cnt_h, lat + 2 * kMaxDim, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
-  HSM_CUDA(p, cudaMemcpyAsync(&flags, p->dev_flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
-  for (void* ptr : {(void*)cell_of, (void*)cstart, (void*)ccount, (void*)sorted_id, (void*)sorted_xyz,
-                    (void*)sorted_bnd, (void*)cgd, (void*)bbox, (void*)lat, (void*)ijk, (void*)on_lat,
-                    (void*)lh.keys, (void*)lh.vals})
-    cudaFreeAsync(ptr, s);
+  // ---- status bits next to the counters, then the one read-back
+  HSM_TRY(cudaMemcpyAsync(lat + 2 * kMaxDim + 3, p->dev_flags, sizeof(unsigned), cudaMemcpyDeviceToDevice, s));
+  HSM_TRY(cudaMemcpyAsync(w.readback, lat + 2 * kMaxDim, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  *nk = k;
+  return cudaSuccess;
+}
+
+#undef HSM_TRY
+
+}  // namespace
+
+// The build is captured once per plan (and kNN variant) as a CUDA graph on a
+// private stream and replayed on the plan's stream: one graph launch and one
+// synchronisation per build instead of some fifty API calls.
+hsm_status build_stencils(hsm_plan p) {
+  hsm_status st = alloc_build_ws(p);
+  if (st != HSM_OK) return st;
+  BuildWs& w = p->ws;
+  cudaStream_t s = p->stream;
+  const int qt = p->tune.knn_qt == 4 ? 4 : (p->tune.knn_qt == 2 ? 2 : 1);
+  if (!w.graph || w.graph_qt != qt) {
+    if (w.graph) cudaGraphExecDestroy(w.graph);
+    w.graph = nullptr;
+    // kernel attributes are set outside the capture
+    const size_t smem = (size_t)p->n * 32 * qt * (sizeof(double) + sizeof(int32_t));
+    void* fn = nullptr;
+    if (p->dim == 2) fn = qt == 4 ? (void*)k_knn<2, 4> : (qt == 2 ? (void*)k_knn<2, 2> : (void*)k_knn<2, 1>);
+    else fn = qt == 4 ? (void*)k_knn<3, 4> : (qt == 2 ? (void*)k_knn<3, 2> : (void*)k_knn<3, 1>);
+    if (smem > 48 * 1024) HSM_CUDA(p, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // the workspace allocations must be complete before the captured work runs
+    HSM_CUDA(p, cudaStreamSynchronize(s));
+    HSM_CUDA(p, cudaStreamBeginCapture(w.cap, cudaStreamCaptureModeThreadLocal));
+    int nk = 0;
+    cudaError_t e = enqueue_build(p, w.cap, qt, &nk);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(w.cap, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&w.graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      w.graph = nullptr;
+      HSM_CUDA(p, e);
+    }
+    w.graph_qt = qt;
+    w.graph_kernels = nk;
+  }
+  HSM_CUDA(p, cudaGraphLaunch(w.graph, s));
+  p->launches += w.graph_kernels;
   HSM_CUDA(p, cudaStreamSynchronize(s));
-  p->n_demoted = cnt_h[0];
-  p->mon.count = cnt_h[1];
-  p->rbf.count = cnt_h[2];
-  if (flags & kDevKnnShort) return set_error(p, HSM_EINVAL, "not enough candidate nodes for an RBF-FD stencil");
+  const int* rb = w.readback;
+  p->n_demoted = rb[0];
+  p->mon.count = rb[1];
+  p->rbf.count = rb[2];
+  if ((unsigned)rb[3] & kDevKnnShort)
+    return set_error(p, HSM_EINVAL, "not enough candidate nodes for an RBF-FD stencil");
   p->stencils_built = true;
   return HSM_OK;
 }
