@@ -388,11 +388,12 @@ hsm_status hsm_plan_autotune(hsm_plan p, const char* cache_path) {
     while (in >> k >> v) cache[k] = v;
     auto it = cache.find(key);
     if (it != cache.end()) {
-      int t = 0, l = 0, qv = 1;
-      if (sscanf(it->second.c_str(), "%d,%d,%d", &t, &l, &qv) >= 2 && t > 0 && l > 0) {
+      int t = 0, l = 0, qv = 1, l32 = 8;
+      if (sscanf(it->second.c_str(), "%d,%d,%d,%d", &t, &l, &qv, &l32) >= 2 && t > 0 && l > 0) {
         p->tune.apply_threads = t;
         p->tune.rbf_lanes = l;
         p->tune.knn_qt = qv;
+        p->tune.rbf_lanes32 = l32;
         p->tune.tuned = true;
         return HSM_OK;
       }
@@ -419,10 +420,10 @@ hsm_status hsm_plan_autotune(hsm_plan p, const char* cache_path) {
   }
   // weight-solve lanes (weights must exist afterwards; the last run leaves them)
   float best = 1e30f;
-  int best_l = p->tune.rbf_lanes;
+  int best_l = p->tune.rbf_lanes, best_l32 = p->tune.rbf_lanes32;
   if (p->rbf.count) {
     if (!p->rbf.w64) HSM_CUDA(p, dev_alloc(&p->rbf.w64, (size_t)p->nops * p->rbf.width * p->rbf.count, s));
-    for (int l : {8, 16, 32}) {
+    for (int l : {4, 8, 16, 32}) {
       p->tune.rbf_lanes = l;
       float ms = time_ms(s, [&]() { return compute_rbf_weights_fp64(p, nullptr, p->rbf.count, nullptr); }, 2, &st);
       if (st != HSM_OK) return st;
@@ -431,8 +432,27 @@ hsm_status hsm_plan_autotune(hsm_plan p, const char* cache_path) {
         best_l = l;
       }
     }
+    // the FP32 + refinement kernel has its own lane count
+    int32_t* fail_list = nullptr;
+    HSM_CUDA(p, dev_alloc(&fail_list, p->rbf.count, s));
+    float best32 = 1e30f;
+    for (int l : {4, 8, 16, 32}) {
+      p->tune.rbf_lanes32 = l;
+      float ms = time_ms(s, [&]() {
+        HSM_CUDA(p, cudaMemsetAsync(p->dev_count, 0, sizeof(int), s));
+        return compute_rbf_weights_fp32r(p, nullptr, p->rbf.count, nullptr, fail_list, p->dev_count);
+      }, 2, &st);
+      if (st != HSM_OK) break;
+      if (ms < best32) {
+        best32 = ms;
+        best_l32 = l;
+      }
+    }
+    dev_free(&fail_list, s);
+    if (st != HSM_OK) return st;
   }
   p->tune.rbf_lanes = best_l;
+  p->tune.rbf_lanes32 = best_l32;
   if (!p->weights_built) {
     st = hsm_plan_compute_weights(p, HSM_PREC_FP64, nullptr);
     if (st != HSM_OK && st != HSM_ESINGULAR) return st;
@@ -461,7 +481,7 @@ hsm_status hsm_plan_autotune(hsm_plan p, const char* cache_path) {
   p->tune.tuned = true;
   if (cache_path) {
     std::ostringstream v;
-    v << best_t << "," << best_l << "," << p->tune.knn_qt;
+    v << best_t << "," << best_l << "," << p->tune.knn_qt << "," << best_l32;
     cache[key] = v.str();
     std::ofstream o(cache_path, std::ios::trunc);
     for (auto& kv : cache) o << kv.first << " " << kv.second << "\n";

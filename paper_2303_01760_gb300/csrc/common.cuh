@@ -38,7 +38,8 @@ struct Group {
 struct Tuning {
   int apply_threads = 256;  // threads per block of the apply kernel
   int apply_split = 1;      // lanes per RBF-FD stencil in the apply kernel (1, 2, 4)
-  int rbf_lanes = 8;        // lanes per RBF-FD weight system (8, 16, 32)
+  int rbf_lanes = 8;        // lanes per FP64 RBF-FD weight system (4, 8, 16, 32)
+  int rbf_lanes32 = 8;      // lanes per FP32 + refinement weight system (4, 8, 16, 32)
   int knn_qt = 1;           // threads per kNN query (1, 2, 4)
   bool tuned = false;
 };

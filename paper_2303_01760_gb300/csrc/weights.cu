@@ -23,23 +23,18 @@
 // iterate is then accurate to about 1e-7) or three corrections were taken;
 // systems that do not converge are re-solved by the FP64 kernel.
 #include <cfloat>
+#include <vector>
 
 #include "common.cuh"
+#include "rbf_kernels.cuh"
 
 namespace hsm {
+
+// Kernels with compile-time system sizes (rbf_fixed.cu); nullptr when the
+// size or lane count has none.
+void* pick_fp32r_fixed(int dim, int nops, int K, int lanes);
+
 namespace {
-
-struct OpsDesc {
-  int kind[kMaxOps];  // 0,1,2 = d/dx_k ; 3 = Laplacian
-};
-
-__host__ OpsDesc make_ops(hsm_plan p, unsigned mask) {
-  OpsDesc d{};
-  int o = 0;
-  for (int b = 0; b < 4; ++b)
-    if (mask & (1u << b)) d.kind[o++] = b;
-  return d;
-}
 
 // ---------------------------------------------------------------------------
 // MON
@@ -184,429 +179,6 @@ __global__ void __launch_bounds__(128) k_mon(const double* __restrict__ coords, 
   }
 }
 
-// ---------------------------------------------------------------------------
-// RBF-FD: lane-group-per-system LU in shared memory
-// ---------------------------------------------------------------------------
-struct RbfArgs {
-  const double* coords;
-  int64_t N;
-  const int32_t* list;     // positions to solve (nullptr = 0..count-1)
-  int64_t count;
-  const int32_t* idx;      // [n][G]
-  int64_t G;
-  const int32_t* nodes;    // [G] node ids of the group
-  int n, n_mono, K, ld;
-  const int8_t* mono_exp;  // [n_mono][dim]
-  const uint16_t* pairs;   // [n(n-1)/2]
-  OpsDesc ops;
-  double* w;               // [nops][n][G]
-  uint8_t* status;         // [N] or nullptr
-  uint8_t status_demoted_mark;
-  const uint8_t* is_regular;
-  unsigned* flags;
-  int32_t* fail_list;      // fp32r: positions that did not converge
-  int* fail_count;
-};
-
-template <typename T>
-struct AbsBits;
-template <>
-struct AbsBits<double> {
-  static __device__ __forceinline__ unsigned long long get(double x) {
-    return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
-  }
-};
-template <>
-struct AbsBits<float> {
-  static __device__ __forceinline__ unsigned long long get(float x) {
-    return (unsigned long long)(__float_as_uint(x) & 0x7fffffffu);
-  }
-};
-
-template <typename T>
-struct PivTol;
-template <>
-struct PivTol<double> {
-  static constexpr double value = 1e-12;
-};
-template <>
-struct PivTol<float> {
-  static constexpr double value = 0.0;
-};
-
-__device__ __forceinline__ unsigned long long shfl_xor_u64(unsigned mask, unsigned long long v, int o, int w) {
-  return (unsigned long long)__shfl_xor_sync(mask, (long long)v, o, w);
-}
-
-// Per-system shared memory layout (in doubles):
-//   M      K x ld        (T = double) or K x K FP64 copy + K x ld T (fp32r)
-//   xi     n x DIM
-//   rc     n          |xi_j|, the scaled distance of node j from the centre
-//   inv    K
-//   b64    K x NOPS   (fp32r only)
-//   x64    K x NOPS   (fp32r only)
-template <int DIM, int NOPS, bool R32>
-__host__ __device__ constexpr size_t sys_doubles(int K, int ld, int n) {
-  return R32 ? ((size_t)K * K + ((size_t)K * ld + 1) / 2 + (size_t)n * (DIM + 1) + K + 2 * (size_t)K * NOPS +
-                (K + 1) / 2)
-             : ((size_t)K * ld + (size_t)n * (DIM + 1) + K);
-}
-
-// Assembles [A P | L phi; P^T 0 | L p] into Mt (row stride ld) for the scaled
-// offsets xi.  Returns via *inv_s the inverse scale.
-template <int DIM, int NOPS, int LANES, typename T>
-__device__ __forceinline__ void assemble(const RbfArgs& a, int64_t pos, int lane, unsigned mask, double* xi,
-                                         double* rc, T* Mt, int ldt, double* M64, double& inv_s_out, bool& ok) {
-  const int n = a.n, K = a.K, nm = a.n_mono;
-  const int32_t c = a.nodes[pos];
-  unsigned long long b = 0ull;
-  for (int j = lane; j < n; j += LANES) {
-    const int32_t id = a.idx[(int64_t)j * a.G + pos];
-    double r2 = 0.0;
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) {
-      double o = a.coords[k * a.N + id] - a.coords[k * a.N + c];
-      xi[j * DIM + k] = o;
-      r2 += o * o;
-    }
-    const double r = sqrt(r2);
-    rc[j] = r;
-    // non-negative doubles order like their bit patterns
-    const unsigned long long rb = (unsigned long long)__double_as_longlong(r);
-    b = rb > b ? rb : b;
-  }
-#pragma unroll
-  for (int o = LANES / 2; o > 0; o >>= 1) {
-    unsigned long long t = shfl_xor_u64(mask, b, o, LANES);
-    b = t > b ? t : b;
-  }
-  const double s = __longlong_as_double((long long)b);
-  const double inv_s = 1.0 / s;
-  inv_s_out = inv_s;
-  ok = s > 0.0 && isfinite(s);
-  __syncwarp(mask);
-  for (int e = lane; e < n * DIM; e += LANES) xi[e] *= inv_s;
-  for (int e = lane; e < n; e += LANES) rc[e] *= inv_s;
-  __syncwarp(mask);
-  // A block (zero diagonal, symmetric pairs)
-  for (int e = lane; e < n; e += LANES) {
-    Mt[e * ldt + e] = T(0);
-    if (M64) M64[e * K + e] = 0.0;
-  }
-  const int npairs = n * (n - 1) / 2;
-  for (int e = lane; e < npairs; e += LANES) {
-    const uint16_t pr = a.pairs[e];
-    const int i = pr >> 8, j = pr & 0xff;
-    double d2 = 0.0;
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) {
-      double d = xi[i * DIM + k] - xi[j * DIM + k];
-      d2 += d * d;
-    }
-    const double v = d2 * sqrt(d2);
-    Mt[i * ldt + j] = T(v);
-    Mt[j * ldt + i] = T(v);
-    if (M64) {
-      M64[i * K + j] = v;
-      M64[j * K + i] = v;
-    }
-  }
-  // P and P^T blocks
-  for (int e = lane; e < n * nm; e += LANES) {
-    const int i = e / nm, q = e - (e / nm) * nm;
-    double v = 1.0;
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) {
-      const int ex = a.mono_exp[q * DIM + k];
-      for (int t = 0; t < ex; ++t) v *= xi[i * DIM + k];
-    }
-    Mt[i * ldt + n + q] = T(v);
-    Mt[(n + q) * ldt + i] = T(v);
-    if (M64) {
-      M64[i * K + n + q] = v;
-      M64[(n + q) * K + i] = v;
-    }
-  }
-  for (int e = lane; e < nm * nm; e += LANES) {
-    const int i = e / nm, q = e - (e / nm) * nm;
-    Mt[(n + i) * ldt + n + q] = T(0);
-    if (M64) M64[(n + i) * K + n + q] = 0.0;
-  }
-  __syncwarp(mask);
-}
-
-// RHS value of operator o for stencil node e (PHS part); r = |xi_e|.
-template <int DIM>
-__device__ __forceinline__ double rhs_phi(const double* xi, const double* rc, int e, int kind) {
-  const double r = rc[e];
-  if (kind == 3) return 3.0 * (DIM + 1) * r;
-  return -3.0 * r * xi[e * DIM + kind];
-}
-template <int DIM>
-__device__ __forceinline__ double rhs_mono(const int8_t* ex, int q, int kind) {
-  int deg = 0, mx = 0, which = -1;
-#pragma unroll
-  for (int k = 0; k < DIM; ++k) {
-    int e = ex[q * DIM + k];
-    deg += e;
-    if (e > mx) {
-      mx = e;
-      which = k;
-    }
-  }
-  if (kind == 3) return (deg == 2 && mx == 2) ? 2.0 : 0.0;
-  return (deg == 1 && which == kind) ? 1.0 : 0.0;
-}
-
-// LU with partial pivoting of the K x (K+NOPS) matrix Mt (row stride ldt),
-// in place, followed by back substitution; the solutions overwrite the
-// right-hand-side columns.  inv[k] receives the inverse pivots.
-template <int NOPS, int LANES, typename T>
-__device__ __forceinline__ bool lu_solve(T* Mt, int ldt, int K, T* inv, int lane, unsigned mask, bool factor,
-                                         int* perm = nullptr) {
-  const int Ctot = K + NOPS;
-  bool ok = true;
-  if (factor) {
-    for (int k = 0; k < K; ++k) {
-      unsigned long long best = 0ull;
-      int brow = K;
-      for (int i = k + lane; i < K; i += LANES) {
-        unsigned long long v = AbsBits<T>::get(Mt[i * ldt + k]);
-        if (v > best || (v == best && i < brow)) {
-          best = v;
-          brow = i;
-        }
-      }
-#pragma unroll
-      for (int o = LANES / 2; o > 0; o >>= 1) {
-        unsigned long long ob = shfl_xor_u64(mask, best, o, LANES);
-        int orow = __shfl_xor_sync(mask, brow, o, LANES);
-        if (ob > best || (ob == best && orow < brow)) {
-          best = ob;
-          brow = orow;
-        }
-      }
-      if (brow != k && brow < K) {
-        // whole rows, multipliers included, so the stored factor stays
-        // consistent for later right-hand sides
-        for (int j = (perm ? 0 : k) + lane; j < Ctot; j += LANES) {
-          T t = Mt[k * ldt + j];
-          Mt[k * ldt + j] = Mt[brow * ldt + j];
-          Mt[brow * ldt + j] = t;
-        }
-        if (perm && lane == 0) {
-          int t = perm[k];
-          perm[k] = perm[brow];
-          perm[brow] = t;
-        }
-      }
-      __syncwarp(mask);
-      const T piv = Mt[k * ldt + k];
-      // the scaled system has entries of order one: a pivot below the
-      // threshold means the system is singular to working precision
-      if (!(fabs((double)piv) > PivTol<T>::value) || !isfinite((double)piv)) {
-        ok = false;
-        break;
-      }
-      const T ip = T(1) / piv;
-      if (lane == 0) inv[k] = ip;
-      for (int i = k + 1 + lane; i < K; i += LANES) Mt[i * ldt + k] *= ip;
-      __syncwarp(mask);
-      const int R = K - k - 1, C = Ctot - k - 1;
-      const int total = R * C;
-      if (total > 0) {
-        int i = lane / C, j = lane - (lane / C) * C;
-        const int dq = LANES / C, dr = LANES - (LANES / C) * C;
-        const T* prow = Mt + k * ldt + k + 1;
-        T* base = Mt + (k + 1) * ldt + k + 1;
-        for (int e = lane; e < total; e += LANES) {
-          T* row = base + i * ldt;
-          row[j] = fma(-row[-1], prow[j], row[j]);
-          j += dr;
-          i += dq;
-          if (j >= C) {
-            j -= C;
-            ++i;
-          }
-        }
-      }
-      __syncwarp(mask);
-    }
-  } else {
-    // forward elimination of the right-hand sides only, with the stored
-    // multipliers and the row order already applied to the factor
-    for (int k = 0; k < K - 1; ++k) {
-      for (int e = lane; e < (K - k - 1) * NOPS; e += LANES) {
-        const int i = k + 1 + e / NOPS, o = e - (e / NOPS) * NOPS;
-        Mt[i * ldt + K + o] = fma(-Mt[i * ldt + k], Mt[k * ldt + K + o], Mt[i * ldt + K + o]);
-      }
-      __syncwarp(mask);
-    }
-  }
-  if (!ok) return false;
-  for (int k = K - 1; k >= 0; --k) {
-    for (int o = lane; o < NOPS; o += LANES) Mt[k * ldt + K + o] *= inv[k];
-    __syncwarp(mask);
-    for (int e = lane; e < k * NOPS; e += LANES) {
-      const int i = e / NOPS, o = e - (e / NOPS) * NOPS;
-      Mt[i * ldt + K + o] = fma(-Mt[i * ldt + k], Mt[k * ldt + K + o], Mt[i * ldt + K + o]);
-    }
-    __syncwarp(mask);
-  }
-  return true;
-}
-
-template <int DIM, int NOPS, int LANES>
-__global__ void __launch_bounds__(128) k_rbf_fp64(RbfArgs a) {
-  extern __shared__ double smem[];
-  constexpr int SYS = 128 / LANES;
-  const int sub = threadIdx.x / LANES, lane = threadIdx.x % LANES;
-  const unsigned mask = LANES == 32 ? 0xffffffffu : (((1u << LANES) - 1u) << ((threadIdx.x & 31) / LANES * LANES));
-  const int K = a.K, ld = a.ld, n = a.n;
-  double* base = smem + (size_t)sub * sys_doubles<DIM, NOPS, false>(K, ld, n);
-  double* M = base;
-  double* xi = M + (size_t)K * ld;
-  double* rc = xi + n * DIM;
-  double* inv = rc + n;
-  for (int64_t t = (int64_t)blockIdx.x * SYS + sub; t < a.count; t += (int64_t)gridDim.x * SYS) {
-    const int64_t pos = a.list ? a.list[t] : t;
-    double inv_s;
-    bool ok;
-    assemble<DIM, NOPS, LANES, double>(a, pos, lane, mask, xi, rc, M, ld, nullptr, inv_s, ok);
-    for (int e = lane; e < n * NOPS; e += LANES) {
-      const int i = e / NOPS, o = e - (e / NOPS) * NOPS;
-      M[i * ld + K + o] = rhs_phi<DIM>(xi, rc, i, a.ops.kind[o]);
-    }
-    for (int e = lane; e < a.n_mono * NOPS; e += LANES) {
-      const int q = e / NOPS, o = e - (e / NOPS) * NOPS;
-      M[(n + q) * ld + K + o] = rhs_mono<DIM>(a.mono_exp, q, a.ops.kind[o]);
-    }
-    __syncwarp(mask);
-    ok = lu_solve<NOPS, LANES, double>(M, ld, K, inv, lane, mask, true) && ok;
-    for (int e = lane; e < n * NOPS; e += LANES) {
-      const int j = e / NOPS, o = e - (e / NOPS) * NOPS;
-      const double sc = a.ops.kind[o] == 3 ? inv_s * inv_s : inv_s;
-      const double v = M[j * ld + K + o] * sc;
-      a.w[((int64_t)o * n + j) * a.G + pos] = ok && isfinite(v) ? v : 0.0;
-    }
-    if (lane == 0) {
-      const int32_t node = a.nodes[pos];
-      if (!ok) atomicOr(a.flags, kDevSingular);
-      if (a.status)
-        a.status[node] = !ok ? HSM_NODE_SINGULAR
-                             : (a.status_demoted_mark ? a.status_demoted_mark
-                                                      : (a.is_regular[node] ? HSM_NODE_DEMOTED : HSM_NODE_OK));
-    }
-    __syncwarp(mask);
-  }
-}
-
-template <int DIM, int NOPS, int LANES>
-__global__ void __launch_bounds__(128) k_rbf_fp32r(RbfArgs a) {
-  extern __shared__ double smem[];
-  constexpr int SYS = 128 / LANES;
-  constexpr int kMaxIt = 3;
-  const int sub = threadIdx.x / LANES, lane = threadIdx.x % LANES;
-  const unsigned mask = LANES == 32 ? 0xffffffffu : (((1u << LANES) - 1u) << ((threadIdx.x & 31) / LANES * LANES));
-  const int K = a.K, n = a.n;
-  const int ld32 = (K + NOPS) | 1;
-  double* base = smem + (size_t)sub * sys_doubles<DIM, NOPS, true>(K, ld32, n);
-  double* M64 = base;
-  float* L32 = reinterpret_cast<float*>(M64 + (size_t)K * K);
-  double* xi = M64 + (size_t)K * K + ((size_t)K * ld32 + 1) / 2;
-  double* rc = xi + n * DIM;
-  float* inv = reinterpret_cast<float*>(rc + n);
-  double* b64 = rc + n + K;
-  double* x64 = b64 + K * NOPS;
-  int* perm = reinterpret_cast<int*>(x64 + K * NOPS);
-  for (int64_t t = (int64_t)blockIdx.x * SYS + sub; t < a.count; t += (int64_t)gridDim.x * SYS) {
-    const int64_t pos = a.list ? a.list[t] : t;
-    double inv_s;
-    bool ok;
-    assemble<DIM, NOPS, LANES, float>(a, pos, lane, mask, xi, rc, L32, ld32, M64, inv_s, ok);
-    for (int e = lane; e < K * NOPS; e += LANES) {
-      const int i = e / NOPS, o = e - (e / NOPS) * NOPS;
-      const double v = i < n ? rhs_phi<DIM>(xi, rc, i, a.ops.kind[o]) : rhs_mono<DIM>(a.mono_exp, i - n, a.ops.kind[o]);
-      b64[i * NOPS + o] = v;
-      L32[i * ld32 + K + o] = (float)v;
-    }
-    for (int i = lane; i < K; i += LANES) perm[i] = i;
-    __syncwarp(mask);
-    ok = lu_solve<NOPS, LANES, float>(L32, ld32, K, inv, lane, mask, true, perm) && ok;
-    bool conv = false;
-    if (ok) {
-      for (int e = lane; e < K * NOPS; e += LANES) {
-        const int i = e / NOPS, o = e - (e / NOPS) * NOPS;
-        x64[i * NOPS + o] = (double)L32[i * ld32 + K + o];
-      }
-      __syncwarp(mask);
-      for (int it = 0; it < kMaxIt && !conv; ++it) {
-        // r = b - M x in FP64 (original equation order), rounded into the
-        // FP32 right-hand-side columns in the factor's row order
-        for (int e = lane; e < K * NOPS; e += LANES) {
-          const int kf = e / NOPS, o = e - (e / NOPS) * NOPS;
-          const int i = perm[kf];
-          double r = b64[i * NOPS + o];
-          const double* row = M64 + (size_t)i * K;
-          for (int j = 0; j < K; ++j) r = fma(-row[j], x64[j * NOPS + o], r);
-          L32[kf * ld32 + K + o] = (float)r;
-        }
-        __syncwarp(mask);
-        lu_solve<NOPS, LANES, float>(L32, ld32, K, inv, lane, mask, false);
-        // x += d ; converged when max|d| <= 3e-4 max|x| for every operator
-        unsigned long long dmax[NOPS], xmax[NOPS];
-#pragma unroll
-        for (int o = 0; o < NOPS; ++o) dmax[o] = xmax[o] = 0ull;
-        for (int e = lane; e < K * NOPS; e += LANES) {
-          const int i = e / NOPS, o = e - (e / NOPS) * NOPS;
-          const double d = (double)L32[i * ld32 + K + o];
-          const double x = x64[i * NOPS + o] + d;
-          x64[i * NOPS + o] = x;
-#pragma unroll
-          for (int q = 0; q < NOPS; ++q)
-            if (q == o) {
-              unsigned long long bd = AbsBits<double>::get(d), bx = AbsBits<double>::get(x);
-              dmax[q] = bd > dmax[q] ? bd : dmax[q];
-              xmax[q] = bx > xmax[q] ? bx : xmax[q];
-            }
-        }
-        bool c = true;
-#pragma unroll
-        for (int o = 0; o < NOPS; ++o) {
-#pragma unroll
-          for (int s = LANES / 2; s > 0; s >>= 1) {
-            unsigned long long t1 = shfl_xor_u64(mask, dmax[o], s, LANES);
-            unsigned long long t2 = shfl_xor_u64(mask, xmax[o], s, LANES);
-            dmax[o] = t1 > dmax[o] ? t1 : dmax[o];
-            xmax[o] = t2 > xmax[o] ? t2 : xmax[o];
-          }
-          const double dm = __longlong_as_double((long long)dmax[o]);
-          const double xm = __longlong_as_double((long long)xmax[o]);
-          c = c && isfinite(xm) && dm <= 3e-4 * xm;
-        }
-        conv = c;
-        __syncwarp(mask);
-      }
-    }
-    const bool good = ok && conv;
-    for (int e = lane; e < n * NOPS; e += LANES) {
-      const int j = e / NOPS, o = e - (e / NOPS) * NOPS;
-      const double sc = a.ops.kind[o] == 3 ? inv_s * inv_s : inv_s;
-      a.w[((int64_t)o * n + j) * a.G + pos] = good ? x64[j * NOPS + o] * sc : 0.0;
-    }
-    if (lane == 0) {
-      const int32_t node = a.nodes[pos];
-      if (!good) {
-        int slot = atomicAdd(a.fail_count, 1);
-        a.fail_list[slot] = (int32_t)pos;
-      } else if (a.status) {
-        a.status[node] = a.is_regular[node] ? HSM_NODE_DEMOTED : HSM_NODE_OK;
-      }
-    }
-    __syncwarp(mask);
-  }
-}
-
 template <int DIM, int NOPS>
 __global__ void k_to_f32(const double* __restrict__ w, float* __restrict__ w32, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -622,12 +194,13 @@ struct Fp64Kernel {
 };
 template <int DIM, int NOPS, int LANES>
 struct Fp32rKernel {
-  static void* ptr() { return (void*)k_rbf_fp32r<DIM, NOPS, LANES>; }
+  static void* ptr() { return (void*)k_rbf_fp32r<DIM, NOPS, LANES, 0>; }
 };
 
 template <template <int, int, int> class KT, int DIM, int NOPS>
 void* pick_lanes(int lanes) {
   switch (lanes) {
+    case 4: return KT<DIM, NOPS, 4>::ptr();
     case 8: return KT<DIM, NOPS, 8>::ptr();
     case 16: return KT<DIM, NOPS, 16>::ptr();
     default: return KT<DIM, NOPS, 32>::ptr();
@@ -648,12 +221,66 @@ void* pick(int dim, int nops, int lanes) {
 }
 
 size_t smem_bytes(int dim, int nops, bool r32, int K, int ld, int n) {
-  size_t d = 0;
-  const int ld32 = (K + nops) | 1;
-  if (r32) d = (size_t)K * K + ((size_t)K * ld32 + 1) / 2 + (size_t)n * (dim + 1) + K + 2 * (size_t)K * nops +
-               (K + 1) / 2;
-  else d = (size_t)K * ld + (size_t)n * (dim + 1) + K;
+  const size_t d = r32 ? r32_doubles(dim, nops, K, n) : (size_t)K * ld + (size_t)n * (dim + 1) + K;
   return d * sizeof(double);
+}
+
+// Launch shape of an RBF-FD kernel: the lane count (the requested one,
+// doubled while a system does not fit) and the block size that keeps the most
+// systems resident per SM.  Shapes are cached per kernel and system size.
+struct RbfShape {
+  void* fn = nullptr;
+  int lanes = 0, threads = 0, blocks_per_sm = 0;
+  size_t smem = 0;
+};
+
+cudaError_t rbf_shape(bool r32, int dim, int nops, int K, int ld, int n, int lanes, RbfShape* out) {
+  struct Entry {
+    void* fn;
+    size_t per;
+    RbfShape shape;
+  };
+  thread_local std::vector<Entry> cache;
+  const size_t per = smem_bytes(dim, nops, r32, K, ld, n);
+  for (; lanes <= 32; lanes *= 2) {
+    void* fn = r32 ? pick_fp32r_fixed(dim, nops, K, lanes) : nullptr;
+    if (!fn) fn = r32 ? pick<Fp32rKernel>(dim, nops, lanes) : pick<Fp64Kernel>(dim, nops, lanes);
+    for (const Entry& e : cache)
+      if (e.fn == fn && e.per == per) {
+        *out = e.shape;
+        return cudaSuccess;
+      }
+    RbfShape best;
+    int best_sys = 0;
+    for (int threads : {64, 96, 128, 160, 192, 256}) {
+      if (threads < lanes) continue;
+      const size_t smem = per * (size_t)(threads / lanes);
+      if (smem > 220 * 1024) continue;
+      cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      int bps = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, threads, smem);
+      if (e != cudaSuccess) return e;
+      const int sys = bps * (threads / lanes);
+      if (sys > best_sys) {
+        best_sys = sys;
+        best.fn = fn;
+        best.lanes = lanes;
+        best.threads = threads;
+        best.blocks_per_sm = bps;
+        best.smem = smem;
+      }
+    }
+    if (best_sys > 0) {
+      cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)best.smem);
+      if (e != cudaSuccess) return e;
+      cache.push_back({fn, per, best});
+      *out = best;
+      return cudaSuccess;
+    }
+  }
+  *out = RbfShape{};
+  return cudaSuccess;
 }
 
 hsm_status launch_rbf(hsm_plan p, bool r32, const int32_t* list, int64_t count, uint8_t* status,
@@ -681,25 +308,13 @@ hsm_status launch_rbf(hsm_plan p, bool r32, const int32_t* list, int64_t count, 
   a.flags = p->dev_flags;
   a.fail_list = fail_list;
   a.fail_count = fail_count;
-  int lanes = p->tune.rbf_lanes;
-  const int sys_per_block = 128 / lanes;
-  size_t per = smem_bytes(p->dim, p->nops, r32, a.K, a.ld, a.n);
-  size_t smem = per * sys_per_block;
-  while (smem > 200 * 1024 && lanes < 32) {
-    lanes *= 2;
-    smem = per * (128 / lanes);
-  }
-  if (smem > 220 * 1024) return set_error(p, HSM_EINVAL, "RBF-FD system too large for shared memory");
-  void* fn = r32 ? pick<Fp32rKernel>(p->dim, p->nops, lanes) : pick<Fp64Kernel>(p->dim, p->nops, lanes);
-  HSM_CUDA(p, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int blocks_per_sm = 0;
-  HSM_CUDA(p, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, fn, 128, smem));
-  if (blocks_per_sm < 1) blocks_per_sm = 1;
-  const int spb = 128 / lanes;
-  int64_t want = ceil_div(count, spb);
-  int grid = (int)std::min<int64_t>(want, (int64_t)num_sms() * blocks_per_sm);
+  RbfShape sh;
+  HSM_CUDA(p, rbf_shape(r32, p->dim, p->nops, a.K, a.ld, a.n, r32 ? p->tune.rbf_lanes32 : p->tune.rbf_lanes, &sh));
+  if (!sh.fn) return set_error(p, HSM_EINVAL, "RBF-FD system too large for shared memory");
+  const int spb = sh.threads / sh.lanes;
+  const int grid = (int)std::min<int64_t>(ceil_div(count, spb), (int64_t)num_sms() * sh.blocks_per_sm);
   void* args[] = {&a};
-  HSM_CUDA(p, cudaLaunchKernel(fn, dim3(grid), dim3(128), args, smem, p->stream));
+  HSM_CUDA(p, cudaLaunchKernel(sh.fn, dim3(grid), dim3(sh.threads), args, sh.smem, p->stream));
   p->launches += 1;
   return HSM_OK;
 }
@@ -738,28 +353,17 @@ cudaError_t launch_rbf_external(const RbfExternal& x, bool r32, const int32_t* l
   a.flags = x.flags;
   a.fail_list = x.fail_list;
   a.fail_count = x.fail_count;
-  int lanes = 8;
-  size_t per = smem_bytes(x.dim, x.nops, r32, a.K, a.ld, a.n);
-  size_t smem = per * (128 / lanes);
-  while (smem > 200 * 1024 && lanes < 32) {
-    lanes *= 2;
-    smem = per * (128 / lanes);
-  }
-  if (smem > 220 * 1024) {
+  RbfShape sh;
+  cudaError_t e = rbf_shape(r32, x.dim, x.nops, a.K, a.ld, a.n, 8, &sh);
+  if (e != cudaSuccess) return e;
+  if (!sh.fn) {
     *too_big = true;
     return cudaSuccess;
   }
-  void* fn = r32 ? pick<Fp32rKernel>(x.dim, x.nops, lanes) : pick<Fp64Kernel>(x.dim, x.nops, lanes);
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  int blocks_per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, fn, 128, smem);
-  if (e != cudaSuccess) return e;
-  if (blocks_per_sm < 1) blocks_per_sm = 1;
-  const int64_t want = ceil_div(count, 128 / lanes);
-  const int grid = (int)std::min<int64_t>(want, (int64_t)num_sms() * blocks_per_sm);
+  const int spb = sh.threads / sh.lanes;
+  const int grid = (int)std::min<int64_t>(ceil_div(count, spb), (int64_t)num_sms() * sh.blocks_per_sm);
   void* args[] = {&a};
-  return cudaLaunchKernel(fn, dim3(grid), dim3(128), args, smem, x.stream);
+  return cudaLaunchKernel(sh.fn, dim3(grid), dim3(sh.threads), args, sh.smem, x.stream);
 }
 
 hsm_status compute_mon_weights(hsm_plan p, uint8_t* status) {
