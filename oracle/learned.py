@@ -32,10 +32,11 @@ Definitions used by both the oracle and the tests:
   |P^T w_hat - l_p| / |l_p| exceeds tau_ood = 1.5 (a prediction that far from
   consistent is treated as out of distribution).
 
-Parity of the MLP itself is unpinned beyond the finite-difference gradient
-check and the closed-form GELU values; the projection is pinned by its
-defining properties (constraints met, correction in range(P), minimum norm,
-exact weights are a fixed point).
+Pins: GELU by closed-form values of the normal CDF; the forward pass by a
+hand-computed 2-2-1 network; the gradients by finite differences of the loss;
+Adam by its bias-corrected first step; the projection by its defining
+properties (constraints met, correction in range(P), minimum norm, exact
+weights are a fixed point).
 """
 from __future__ import annotations
 

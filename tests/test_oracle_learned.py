@@ -124,3 +124,15 @@ def test_canonical_frame_is_orthogonal_and_canonical():
         assert np.allclose(Wc["dx"][b], Y[b, :12], atol=1e-9 * np.abs(Y[b]).max())
         assert np.allclose(Wc["dy"][b], Y[b, 12:24], atol=1e-9 * np.abs(Y[b]).max())
         assert np.allclose(Wc["lap"][b], Y[b, 24:], atol=1e-9 * np.abs(Y[b]).max())
+
+
+def test_mlp_forward_hand_computed():
+    """A 2-2-1 network with hand-chosen weights: the output is fixed by the
+    standard normal CDF values Phi(1) and Phi(2) alone."""
+    P = [(np.eye(2), np.zeros(2)), (np.array([[1.0, -3.0]]), np.array([0.5]))]
+    out, pre, _ = ol.forward(P, np.array([[1.0, 2.0], [-1.0, 0.0]]))
+    phi1, phi2 = 0.8413447460685429, 0.9772498680518208
+    assert abs(out[0, 0] - (phi1 - 3.0 * 2.0 * phi2 + 0.5)) < 1e-14
+    # gelu(-1) = -(1 - Phi(1)), gelu(0) = 0
+    assert abs(out[1, 0] - (-(1.0 - phi1) + 0.5)) < 1e-14
+    assert np.array_equal(pre[0], np.array([[1.0, 2.0], [-1.0, 0.0]]))
