@@ -330,7 +330,8 @@ def run_stepper(hsm, ns, plan, d, dev, stream, args, steps=30):
     ms = a.elapsed_time(b)
     st.close()
     return {"workload": "2D irregular domain (the timed node set), Ra=1e6, Pr=0.71, dt=0.1h^2/2, "
-                        "bordered pressure by Jacobi-BiCGSTAB to 1e-10",
+                        "bordered pressure by BiCGSTAB to 1e-10, right-preconditioned by an aggregation-multigrid "
+                        "V(2,2)-cycle",
             "steps": steps, "ms_per_step": ms / steps, "node_steps_per_s": ns.N * steps / (ms * 1e-3),
             "krylov_iters_per_step": float(np.mean(its)), "first_steps_iters": it0,
             "converged": code == 0, "T_finite": bool(torch.isfinite(T).all())}

@@ -206,7 +206,15 @@ typedef struct {
   const double* normals; /* device f64 [dim][N]: outward unit normals (bc != 0)    */
   double krylov_tol;     /* relative residual of the pressure solve (e.g. 1e-12)   */
   int krylov_max_it;     /* iteration cap of the pressure solve (e.g. 2000)        */
+  int precond;           /* HSM_PRECOND_AMG (0, default) or HSM_PRECOND_JACOBI     */
 } hsm_phys;
+
+/* Right preconditioner of the pressure BiCGSTAB.  AMG: an aggregation
+ * multigrid V(2,2)-cycle of the pressure operator (geometric aggregates of
+ * 2^d nodes per level, Galerkin coarse operators, damped Jacobi smoothing,
+ * dense solve of the coarsest bordered system), built once by
+ * hsm_stepper_create.  JACOBI: the inverse diagonal.                       */
+enum { HSM_PRECOND_AMG = 0, HSM_PRECOND_JACOBI = 1 };
 
 /* Creates a stepper on a plan whose weights exist and whose op mask holds
  * every first derivative and the Laplacian.  Copies *phys (the device arrays

@@ -1,0 +1,617 @@
+// Aggregation multigrid for the pressure operator of the Boussinesq step
+// (Section 3: the Poisson problem of Chorin's projection), the right
+// preconditioner of its BiCGSTAB solve.
+//
+// Aggregates are geometric: level l+1 groups the rows of level l whose nodes
+// fall into one cell of edge 2^(l+1) h.  Cell indices of every level are the
+// finest cell indices shifted right by l, so the cells nest exactly, and each
+// aggregate is numbered by the rank of its lowest node id, which makes the
+// hierarchy independent of thread timing.  Prolongation is piecewise
+// constant; the coarse operators are the Galerkin products A_c = P^T A P,
+// assembled one coarse row per thread from its member rows in ascending
+// order.  Coarsening stops at kMgCoarsest rows, whose bordered system
+// [A_c 1; 1^T 0] (the Neumann operator's constant null space, as in the fine
+// bordered system) is inverted densely once.
+//
+// The cycle is V(2,2) with damped Jacobi (omega = 2/3); the coarse correction
+// is scaled by alpha, the over-correction plain aggregation needs (1.8 in 2D,
+// 1.5 in 3D, set on the seeded node sets).  Everything is FP64: rounding of an
+// FP32 cycle makes the preconditioner slightly nonlinear, and BiCGSTAB then
+// needed 1.6x the iterations.
+#include <algorithm>
+#include <vector>
+
+#include "amg.cuh"
+
+namespace hsm {
+namespace {
+
+constexpr unsigned long long kEmptyKey = ~0ull;
+constexpr int kMaxProbe = 256;
+
+// Grid-stride over the rows of a level: blocks [0, bm) take group 0, the rest group 1.
+__device__ __forceinline__ void mg_rows(const MgLevel& L, int& g, int64_t& p, int64_t& stride) {
+  if ((int)blockIdx.x < L.bm) {
+    g = 0;
+    p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    stride = (int64_t)L.bm * blockDim.x;
+  } else {
+    g = 1;
+    p = (blockIdx.x - L.bm) * (int64_t)blockDim.x + threadIdx.x;
+    stride = (int64_t)(gridDim.x - L.bm) * blockDim.x;
+  }
+}
+__device__ __forceinline__ int64_t mg_row_id(const MgLevel& L, int g, int64_t p) {
+  return L.nodes[g] ? (int64_t)L.nodes[g][p] : p;
+}
+__device__ __forceinline__ void mg_locate(const MgLevel& L, int64_t r, int& g, int64_t& p) {
+  if (L.kind) {
+    g = L.kind[r];
+    p = L.pos[r];
+  } else {
+    g = 0;
+    p = r;
+  }
+}
+__device__ __forceinline__ double row_dot(const MgLevel& L, int g, int64_t p, const double* __restrict__ x) {
+  const int W = L.width[g];
+  const int64_t G = L.count[g];
+  double s = 0.0;
+  for (int e = 0; e < W; ++e) s = fma(L.val[g][(int64_t)e * G + p], x[L.idx[g][(int64_t)e * G + p]], s);
+  return s;
+}
+
+// ---- cycle -------------------------------------------------------------------
+// x = w f + w (f - A w f), w = omega D^-1: two Jacobi sweeps from zero.
+__global__ void __launch_bounds__(kMgThreads) k_mg_pre(MgLevel L, const double* __restrict__ f, const double* done) {
+  if (*done != 0.0) return;
+  int g;
+  int64_t p, stride;
+  mg_rows(L, g, p, stride);
+  const int W = L.width[g];
+  const int64_t G = L.count[g];
+  for (; p < G; p += stride) {
+    const int64_t i = mg_row_id(L, g, p);
+    double acc = 0.0;
+    for (int e = 0; e < W; ++e) {
+      const int32_t j = L.idx[g][(int64_t)e * G + p];
+      acc = fma(L.val[g][(int64_t)e * G + p], L.odinv[j] * f[j], acc);
+    }
+    const double fi = f[i], di = L.odinv[i];
+    L.x[i] = di * fi + di * (fi - acc);
+  }
+}
+
+// fc[I] = sum over the rows r of aggregate I of (f - A x)_r (fixed order).
+__global__ void __launch_bounds__(kMgThreads) k_mg_restrict(MgLevel L, const double* __restrict__ f,
+                                                            double* __restrict__ fc, int64_t nc, const double* done) {
+  if (*done != 0.0) return;
+  for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < nc; I += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int32_t m = L.mstart[I]; m < L.mstart[I + 1]; ++m) {
+      const int32_t r = L.mlist[m];
+      int g;
+      int64_t p;
+      mg_locate(L, r, g, p);
+      s += f[r] - row_dot(L, g, p, L.x);
+    }
+    fc[I] = s;
+  }
+}
+
+// y = x' + w (f - A x'), x' = x + alpha P xc (prolongation on the fly).
+__global__ void __launch_bounds__(kMgThreads) k_mg_post1(MgLevel L, const double* __restrict__ f,
+                                                         const double* __restrict__ xc, double alpha,
+                                                         const double* done) {
+  if (*done != 0.0) return;
+  int g;
+  int64_t p, stride;
+  mg_rows(L, g, p, stride);
+  const int W = L.width[g];
+  const int64_t G = L.count[g];
+  for (; p < G; p += stride) {
+    const int64_t i = mg_row_id(L, g, p);
+    double acc = 0.0;
+    for (int e = 0; e < W; ++e) {
+      const int32_t j = L.idx[g][(int64_t)e * G + p];
+      acc = fma(L.val[g][(int64_t)e * G + p], fma(alpha, xc[L.agg[j]], L.x[j]), acc);
+    }
+    const double xi = fma(alpha, xc[L.agg[i]], L.x[i]);
+    L.y[i] = fma(L.odinv[i], f[i] - acc, xi);
+  }
+}
+
+// out = y + w (f - A y); on level 0 the border entry passes through.
+__global__ void __launch_bounds__(kMgThreads) k_mg_post2(MgLevel L, const double* __restrict__ f,
+                                                         double* __restrict__ out, int border,
+                                                         const double* done) {
+  if (*done != 0.0) return;
+  int g;
+  int64_t p, stride;
+  mg_rows(L, g, p, stride);
+  for (; p < L.count[g]; p += stride) {
+    const int64_t i = mg_row_id(L, g, p);
+    out[i] = fma(L.odinv[i], f[i] - row_dot(L, g, p, L.y), L.y[i]);
+  }
+  if (border && blockIdx.x == 0 && threadIdx.x == 0) out[L.n] = f[L.n];
+}
+
+// x = Binv f, one warp per row; border >= 0 copies f[border] to x[border].
+__global__ void __launch_bounds__(kMgThreads) k_mg_coarse(const double* __restrict__ binv, int m,
+                                                          const double* __restrict__ f, double* __restrict__ x,
+                                                          int64_t border, const double* done) {
+  if (*done != 0.0) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); r < m; r += warps) {
+    double s = 0.0;
+    for (int c = lane; c < m; c += 32) s = fma(binv[r * m + c], f[c], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) x[r] = s;
+  }
+  if (border >= 0 && blockIdx.x == 0 && threadIdx.x == 0) x[border] = f[border];
+}
+
+// ---- set-up ------------------------------------------------------------------
+__global__ void k_mg_odinv0(MgLevel L, double omega) {
+  int g;
+  int64_t p, stride;
+  mg_rows(L, g, p, stride);
+  for (; p < L.count[g]; p += stride) {
+    const double d = L.val[g][p];  // the centre is the first stencil entry
+    L.odinv[mg_row_id(L, g, p)] = (d != 0.0 && isfinite(d)) ? omega / d : 0.0;
+  }
+}
+
+__device__ __forceinline__ unsigned long long ordered_bits(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
+}
+
+__global__ void k_mg_min_coords(const double* __restrict__ coords, int64_t N, int dim, unsigned long long* lo) {
+  unsigned long long m[3] = {~0ull, ~0ull, ~0ull};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    for (int k = 0; k < dim; ++k) m[k] = min(m[k], ordered_bits(coords[k * N + i]));
+  for (int k = 0; k < dim; ++k) {
+    unsigned long long v = m[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = min(v, (unsigned long long)__shfl_xor_sync(0xffffffffu, (long long)v, o));
+    if ((threadIdx.x & 31) == 0) atomicMin(&lo[k], v);
+  }
+}
+
+__global__ void k_mg_cells(const double* __restrict__ coords, int64_t N, int dim, double lo0, double lo1, double lo2,
+                           double inv_c, int32_t* cell) {
+  const double lo[3] = {lo0, lo1, lo2};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    for (int k = 0; k < dim; ++k) cell[k * N + i] = (int32_t)floor((coords[k * N + i] - lo[k]) * inv_c);
+}
+
+__device__ __forceinline__ unsigned long long cell_key(const int32_t* cell, int64_t N, int dim, int64_t i, int l) {
+  unsigned long long key = 0ull;
+  for (int k = 0; k < dim; ++k) key = (key << 21) | (unsigned long long)((cell[k * N + i] >> l) & 0x1fffff);
+  return key;
+}
+__device__ __forceinline__ unsigned long long mix(unsigned long long k) {
+  k ^= k >> 33;
+  k *= 0xff51afd7ed558ccdull;
+  k ^= k >> 33;
+  return k;
+}
+
+// Inserts every node's level-l cell; the slot keeps the lowest node id.
+__global__ void k_mg_insert(const int32_t* __restrict__ cell, int64_t N, int dim, int l, unsigned long long* keys,
+                            int32_t* owner, int32_t* slot, unsigned long long mask, unsigned* overflow) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long key = cell_key(cell, N, dim, i, l);
+    unsigned long long h = mix(key) & mask;
+    int probe = 0;
+    for (; probe < kMaxProbe; ++probe) {
+      const unsigned long long prev = atomicCAS(&keys[h], kEmptyKey, key);
+      if (prev == kEmptyKey || prev == key) break;
+      h = (h + 1) & mask;
+    }
+    if (probe == kMaxProbe) {
+      atomicOr(overflow, 1u);
+      slot[i] = -1;
+      continue;
+    }
+    atomicMin(&owner[h], (int32_t)i);
+    slot[i] = (int32_t)h;
+  }
+}
+
+__global__ void k_mg_leader(const int32_t* __restrict__ slot, const int32_t* __restrict__ owner, int64_t N,
+                            uint8_t* lead) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    lead[i] = (slot[i] >= 0 && owner[slot[i]] == (int32_t)i) ? 1 : 0;
+}
+
+// cid[i] = coarse index of node i's cell; agg of the finer level's rows.
+__global__ void k_mg_cid(const int32_t* __restrict__ slot, const int32_t* __restrict__ owner,
+                         const int32_t* __restrict__ rank, const int32_t* __restrict__ cid_prev, int64_t N,
+                         int32_t* cid, int32_t* agg) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t c = rank[owner[slot[i]]];
+    cid[i] = c;
+    // every node of a finer row lies in the same coarse cell: equal writes
+    agg[cid_prev ? cid_prev[i] : i] = c;
+  }
+}
+
+__global__ void k_mg_count(const int32_t* __restrict__ agg, int64_t n, int32_t* cnt) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&cnt[agg[r]], 1);
+}
+__global__ void k_mg_fill(const int32_t* __restrict__ agg, int64_t n, const int32_t* __restrict__ start,
+                          int32_t* cursor, int32_t* list) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t I = agg[r];
+    list[start[I] + atomicAdd(&cursor[I], 1)] = (int32_t)r;
+  }
+}
+// members of each aggregate in ascending order (fixed summation order)
+__global__ void k_mg_sort(const int32_t* __restrict__ start, int64_t nc, int32_t* list) {
+  for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < nc; I += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t a = start[I], b = start[I + 1];
+    for (int32_t k = a + 1; k < b; ++k) {
+      const int32_t v = list[k];
+      int32_t j = k - 1;
+      while (j >= a && list[j] > v) {
+        list[j + 1] = list[j];
+        --j;
+      }
+      list[j + 1] = v;
+    }
+  }
+}
+
+// Galerkin coarse row I = sum of its member rows with columns mapped by agg.
+// Pass 1 counts distinct columns (max into *maxw); pass 2 writes the ELL row
+// sorted by column, padded with (I, 0), and omega / diagonal.
+template <bool FILL>
+__global__ void k_mg_assemble(MgLevel L, int64_t nc, int Wc, int32_t* cidx, double* cval, double* codinv,
+                              double omega, int* maxw, unsigned* overflow) {
+  for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < nc; I += (int64_t)gridDim.x * blockDim.x) {
+    int32_t cols[kMgMaxRow];
+    double vals[kMgMaxRow];
+    int cnt = 0;
+    bool over = false;
+    for (int32_t m = L.mstart[I]; m < L.mstart[I + 1]; ++m) {
+      int g;
+      int64_t p;
+      mg_locate(L, L.mlist[m], g, p);
+      const int W = L.width[g];
+      const int64_t G = L.count[g];
+      for (int e = 0; e < W; ++e) {
+        const int32_t J = L.agg[L.idx[g][(int64_t)e * G + p]];
+        const double a = L.val[g][(int64_t)e * G + p];
+        int k = 0;
+        while (k < cnt && cols[k] != J) ++k;
+        if (k < cnt) {
+          vals[k] += a;
+        } else if (cnt < kMgMaxRow) {
+          cols[cnt] = J;
+          vals[cnt] = a;
+          ++cnt;
+        } else {
+          over = true;
+        }
+      }
+    }
+    if (over) atomicOr(overflow, 2u);
+    if (!FILL) {
+      atomicMax(maxw, cnt);
+      continue;
+    }
+    for (int k = 1; k < cnt; ++k) {
+      const int32_t c = cols[k];
+      const double v = vals[k];
+      int j = k - 1;
+      while (j >= 0 && cols[j] > c) {
+        cols[j + 1] = cols[j];
+        vals[j + 1] = vals[j];
+        --j;
+      }
+      cols[j + 1] = c;
+      vals[j + 1] = v;
+    }
+    double diag = 0.0;
+    for (int k = 0; k < Wc; ++k) {
+      const bool have = k < cnt;
+      cidx[(int64_t)k * nc + I] = have ? cols[k] : (int32_t)I;
+      cval[(int64_t)k * nc + I] = have ? vals[k] : 0.0;
+      if (have && cols[k] == (int32_t)I) diag = vals[k];
+    }
+    codinv[I] = (diag != 0.0 && isfinite(diag)) ? omega / diag : 0.0;
+  }
+}
+
+// Dense bordered matrix [A 1; 1^T 0] of the coarsest level, row-major (m+1)^2.
+__global__ void k_mg_dense(MgLevel L, int m, double* B) {
+  const int n1 = m + 1;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < m; r += (int64_t)gridDim.x * blockDim.x) {
+    int g;
+    int64_t p;
+    mg_locate(L, r, g, p);
+    const int W = L.width[g];
+    const int64_t G = L.count[g];
+    for (int e = 0; e < W; ++e) B[r * n1 + L.idx[g][(int64_t)e * G + p]] += L.val[g][(int64_t)e * G + p];
+    B[r * n1 + m] = 1.0;
+    B[(int64_t)m * n1 + r] = 1.0;
+  }
+}
+
+// Gauss-Jordan inversion with partial pivoting of the n1 x n1 matrix B into
+// the right half of the n1 x 2n1 workspace M, one block; writes the leading
+// m x m block of the inverse to binv.  *singular is set when a pivot vanishes.
+__global__ void __launch_bounds__(1024) k_mg_invert(const double* B, int n1, double* M, double* binv,
+                                                    unsigned* singular) {
+  __shared__ double sv[1024];
+  __shared__ int si[1024];
+  __shared__ double fac[1024];
+  const int t = threadIdx.x, T = blockDim.x, w = 2 * n1;
+  for (int64_t e = t; e < (int64_t)n1 * w; e += T) {
+    const int r = (int)(e / w), c = (int)(e % w);
+    M[e] = c < n1 ? B[(int64_t)r * n1 + c] : (c - n1 == r ? 1.0 : 0.0);
+  }
+  __syncthreads();
+  for (int k = 0; k < n1; ++k) {
+    double best = -1.0;
+    int brow = k;
+    for (int r = k + t; r < n1; r += T) {
+      const double v = fabs(M[(int64_t)r * w + k]);
+      if (v > best) {
+        best = v;
+        brow = r;
+      }
+    }
+    sv[t] = best;
+    si[t] = brow;
+    __syncthreads();
+    for (int s = T / 2; s > 0; s >>= 1) {
+      if (t < s && (sv[t + s] > sv[t] || (sv[t + s] == sv[t] && si[t + s] < si[t]))) {
+        sv[t] = sv[t + s];
+        si[t] = si[t + s];
+      }
+      __syncthreads();
+    }
+    const int pr = si[0];
+    const double pv = sv[0];
+    __syncthreads();
+    if (!(pv > 0.0) || !isfinite(pv)) {
+      if (t == 0) *singular = 1u;
+      return;
+    }
+    if (pr != k)
+      for (int c = t; c < w; c += T) {
+        const double a = M[(int64_t)k * w + c];
+        M[(int64_t)k * w + c] = M[(int64_t)pr * w + c];
+        M[(int64_t)pr * w + c] = a;
+      }
+    __syncthreads();
+    const double ip = 1.0 / M[(int64_t)k * w + k];
+    __syncthreads();
+    for (int c = t; c < w; c += T) M[(int64_t)k * w + c] *= ip;
+    for (int r = t; r < n1; r += T) fac[r] = r == k ? 0.0 : M[(int64_t)r * w + k];
+    __syncthreads();
+    for (int64_t e = t; e < (int64_t)n1 * w; e += T) {
+      const int r = (int)(e / w), c = (int)(e % w);
+      if (r != k) M[e] = fma(-fac[r], M[(int64_t)k * w + c], M[e]);
+    }
+    __syncthreads();
+  }
+  const int m = n1 - 1;
+  for (int64_t e = t; e < (int64_t)m * m; e += T) {
+    const int r = (int)(e / m), c = (int)(e % m);
+    binv[e] = M[(int64_t)r * w + n1 + c];
+  }
+}
+
+int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, kMgThreads), (int64_t)num_sms() * 8)); }
+
+}  // namespace
+
+hsm_status amg_setup(hsm_plan pl, const double* wp_mon, const double* wp_rbf, double alpha, Amg* amg) {
+  cudaStream_t s = pl->stream;
+  const int64_t N = pl->N;
+  const int dim = pl->dim;
+  amg->alpha = alpha;
+  const double omega = amg->omega;
+  MgLevel& L0 = amg->lev[0];
+  L0.n = N;
+  L0.nodes[0] = pl->mon.nodes;
+  L0.nodes[1] = pl->rbf.nodes;
+  L0.idx[0] = pl->mon.idx;
+  L0.idx[1] = pl->rbf.idx;
+  L0.val[0] = wp_mon;
+  L0.val[1] = wp_rbf;
+  L0.count[0] = pl->mon.count;
+  L0.count[1] = pl->rbf.count;
+  L0.width[0] = pl->mon.width;
+  L0.width[1] = pl->rbf.width;
+  L0.bm = pl->mon.count ? grid_for(pl->mon.count) : 0;
+  L0.blocks = L0.bm + (pl->rbf.count ? grid_for(pl->rbf.count) : 0);
+  L0.kind = pl->kind;
+  L0.pos = pl->pos;
+  HSM_CUDA(pl, dev_alloc(&L0.odinv, N, s));
+  HSM_CUDA(pl, dev_alloc(&L0.x, N, s));
+  HSM_CUDA(pl, dev_alloc(&L0.y, N, s));
+  k_mg_odinv0<<<L0.blocks, kMgThreads, 0, s>>>(L0, omega);
+  pl->launches += 1;
+
+  // finest cells: edge 2h from the lower corner of the node set
+  unsigned long long* lo_d = nullptr;
+  HSM_CUDA(pl, dev_alloc(&lo_d, 3, s));
+  HSM_CUDA(pl, cudaMemsetAsync(lo_d, 0xff, 3 * sizeof(unsigned long long), s));
+  k_mg_min_coords<<<grid_for(N), kMgThreads, 0, s>>>(pl->coords, N, dim, lo_d);
+  unsigned long long lo_h[3] = {0, 0, 0};
+  HSM_CUDA(pl, cudaMemcpyAsync(lo_h, lo_d, sizeof(lo_h), cudaMemcpyDeviceToHost, s));
+  HSM_CUDA(pl, cudaStreamSynchronize(s));
+  double lo[3] = {0.0, 0.0, 0.0};
+  for (int k = 0; k < dim; ++k) {
+    unsigned long long b = lo_h[k];
+    b = (b & 0x8000000000000000ull) ? (b & 0x7fffffffffffffffull) : ~b;
+    memcpy(&lo[k], &b, sizeof(double));
+  }
+  unsigned long long cap = 1;
+  while (cap < 2ull * (unsigned long long)N) cap <<= 1;
+  int32_t *cell = nullptr, *owner = nullptr, *slot = nullptr, *rank = nullptr, *list = nullptr, *cid = nullptr,
+          *cid_prev = nullptr, *cnt = nullptr, *scan_ws = nullptr;
+  unsigned long long* keys = nullptr;
+  uint8_t* lead = nullptr;
+  unsigned* flags = nullptr;
+  int* maxw = nullptr;
+  auto release = [&]() {
+    for (void** ptr : {(void**)&cell, (void**)&owner, (void**)&slot, (void**)&rank, (void**)&list, (void**)&cid,
+                       (void**)&cid_prev, (void**)&cnt, (void**)&scan_ws, (void**)&keys, (void**)&lead,
+                       (void**)&flags, (void**)&maxw, (void**)&lo_d})
+      dev_free(ptr, s);
+  };
+  cudaError_t ce = cudaSuccess;
+  for (auto e : {dev_alloc(&cell, (size_t)dim * N, s), dev_alloc(&owner, cap, s), dev_alloc(&slot, N, s),
+                 dev_alloc(&rank, N, s), dev_alloc(&list, N, s), dev_alloc(&cid, N, s), dev_alloc(&cid_prev, N, s),
+                 dev_alloc(&cnt, N + 1, s), dev_alloc(&scan_ws, scan_scratch(N + 1), s), dev_alloc(&keys, cap, s),
+                 dev_alloc(&lead, N, s), dev_alloc(&flags, 2, s), dev_alloc(&maxw, 1, s)})
+    if (e != cudaSuccess) ce = e;
+  if (ce != cudaSuccess) {
+    release();
+    return cuda_fail(pl, ce, "multigrid set-up allocation");
+  }
+  k_mg_cells<<<grid_for(N), kMgThreads, 0, s>>>(pl->coords, N, dim, lo[0], lo[1], lo[2], 0.5 / pl->h, cell);
+  HSM_CUDA(pl, cudaMemsetAsync(flags, 0, 2 * sizeof(unsigned), s));
+  int l = 0;
+  bool first = true;
+  for (; l + 1 < kMgMaxLevels && amg->lev[l].n > kMgCoarsest; ++l) {
+    MgLevel& F = amg->lev[l];
+    // aggregates: the level-(l+1) cells of the nodes, numbered by lowest node id
+    HSM_CUDA(pl, cudaMemsetAsync(keys, 0xff, cap * sizeof(unsigned long long), s));
+    HSM_CUDA(pl, cudaMemsetAsync(owner, 0x7f, cap * sizeof(int32_t), s));
+    k_mg_insert<<<grid_for(N), kMgThreads, 0, s>>>(cell, N, dim, l, keys, owner, slot, cap - 1, flags);
+    k_mg_leader<<<grid_for(N), kMgThreads, 0, s>>>(slot, owner, N, lead);
+    HSM_CUDA(pl, select_indices(lead, 1, N, list, rank, cnt, s, scan_ws));
+    int nc_h = 0;
+    unsigned fl = 0;
+    HSM_CUDA(pl, cudaMemcpyAsync(&nc_h, cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HSM_CUDA(pl, cudaMemcpyAsync(&fl, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    HSM_CUDA(pl, cudaStreamSynchronize(s));
+    if (fl) {
+      release();
+      return set_error(pl, HSM_ECUDA, "multigrid aggregation hash overflowed");
+    }
+    if (nc_h >= F.n || nc_h < 1) break;  // no coarsening: this level is the coarsest
+    const int64_t nc = nc_h;
+    HSM_CUDA(pl, dev_alloc(&F.agg, F.n, s));
+    k_mg_cid<<<grid_for(N), kMgThreads, 0, s>>>(slot, owner, rank, first ? nullptr : cid_prev, N, cid, F.agg);
+    first = false;
+    std::swap(cid, cid_prev);
+    // rows of each aggregate, ascending
+    HSM_CUDA(pl, dev_alloc(&F.mstart, nc + 1, s));
+    HSM_CUDA(pl, dev_alloc(&F.mlist, F.n, s));
+    HSM_CUDA(pl, cudaMemsetAsync(cnt, 0, (nc + 1) * sizeof(int32_t), s));
+    k_mg_count<<<grid_for(F.n), kMgThreads, 0, s>>>(F.agg, F.n, cnt);
+    HSM_CUDA(pl, exclusive_scan_i32(cnt, F.mstart, nc, s, scan_ws));
+    HSM_CUDA(pl, cudaMemsetAsync(cnt, 0, (nc + 1) * sizeof(int32_t), s));
+    k_mg_fill<<<grid_for(F.n), kMgThreads, 0, s>>>(F.agg, F.n, F.mstart, cnt, F.mlist);
+    k_mg_sort<<<grid_for(nc), kMgThreads, 0, s>>>(F.mstart, nc, F.mlist);
+    F.cblocks = grid_for(nc);
+    // Galerkin coarse operator
+    HSM_CUDA(pl, cudaMemsetAsync(maxw, 0, sizeof(int), s));
+    k_mg_assemble<false><<<grid_for(nc), kMgThreads, 0, s>>>(F, nc, 0, nullptr, nullptr, nullptr, omega, maxw, flags);
+    int wc = 0;
+    HSM_CUDA(pl, cudaMemcpyAsync(&wc, maxw, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HSM_CUDA(pl, cudaMemcpyAsync(&fl, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    HSM_CUDA(pl, cudaStreamSynchronize(s));
+    if (fl) {
+      release();
+      return set_error(pl, HSM_ECUDA, "a coarse multigrid row has more than 64 columns");
+    }
+    MgLevel& C = amg->lev[l + 1];
+    C.n = nc;
+    C.count[0] = nc;
+    C.width[0] = std::max(wc, 1);
+    C.bm = C.blocks = grid_for(nc);
+    HSM_CUDA(pl, dev_alloc(&C.own_idx, (size_t)C.width[0] * nc, s));
+    HSM_CUDA(pl, dev_alloc(&C.own_val, (size_t)C.width[0] * nc, s));
+    HSM_CUDA(pl, dev_alloc(&C.odinv, nc, s));
+    HSM_CUDA(pl, dev_alloc(&C.f, nc, s));
+    HSM_CUDA(pl, dev_alloc(&C.x, nc, s));
+    HSM_CUDA(pl, dev_alloc(&C.y, nc, s));
+    C.idx[0] = C.own_idx;
+    C.val[0] = C.own_val;
+    k_mg_assemble<true><<<grid_for(nc), kMgThreads, 0, s>>>(F, nc, C.width[0], C.own_idx, C.own_val, C.odinv, omega,
+                                                            maxw, flags);
+    pl->launches += 8;
+  }
+  amg->L = l + 1;
+  // coarsest level: dense inverse of its bordered system
+  const MgLevel& Cs = amg->lev[l];
+  if (Cs.n + 1 > 1024) {  // the dense inversion runs in one block of 1024 threads
+    release();
+    return set_error(pl, HSM_EINVAL, "multigrid coarsening stalled above 1023 rows");
+  }
+  const int m = (int)Cs.n, n1 = m + 1;
+  amg->m = m;
+  double *B = nullptr, *M = nullptr;
+  HSM_CUDA(pl, dev_alloc(&B, (size_t)n1 * n1, s));
+  HSM_CUDA(pl, dev_alloc(&M, (size_t)n1 * 2 * n1, s));
+  HSM_CUDA(pl, dev_alloc(&amg->binv, (size_t)m * m, s));
+  HSM_CUDA(pl, cudaMemsetAsync(B, 0, (size_t)n1 * n1 * sizeof(double), s));
+  HSM_CUDA(pl, cudaMemsetAsync(flags, 0, 2 * sizeof(unsigned), s));
+  k_mg_dense<<<grid_for(m), kMgThreads, 0, s>>>(Cs, m, B);
+  k_mg_invert<<<1, 1024, 0, s>>>(B, n1, M, amg->binv, flags);
+  pl->launches += 2;
+  unsigned sing = 0;
+  HSM_CUDA(pl, cudaMemcpyAsync(&sing, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  HSM_CUDA(pl, cudaStreamSynchronize(s));
+  dev_free(&B, s);
+  dev_free(&M, s);
+  release();
+  if (sing) return set_error(pl, HSM_ESINGULAR, "the coarsest multigrid system is singular");
+  return HSM_OK;
+}
+
+void amg_vcycle(const Amg& A, const double* in, double* out, const double* done, cudaStream_t s) {
+  const int cg = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div((int64_t)A.m, kMgThreads / 32), 1024));
+  if (A.L == 1) {
+    k_mg_coarse<<<cg, kMgThreads, 0, s>>>(A.binv, A.m, in, out, A.lev[0].n, done);
+    return;
+  }
+  const double* f = in;
+  for (int l = 0; l + 1 < A.L; ++l) {
+    const MgLevel& F = A.lev[l];
+    k_mg_pre<<<F.blocks, kMgThreads, 0, s>>>(F, f, done);
+    k_mg_restrict<<<F.cblocks, kMgThreads, 0, s>>>(F, f, A.lev[l + 1].f, A.lev[l + 1].n, done);
+    f = A.lev[l + 1].f;
+  }
+  const MgLevel& Cs = A.lev[A.L - 1];
+  k_mg_coarse<<<cg, kMgThreads, 0, s>>>(A.binv, A.m, Cs.f, Cs.x, -1, done);
+  for (int l = A.L - 2; l >= 0; --l) {
+    const MgLevel& F = A.lev[l];
+    const double* fl = l == 0 ? in : F.f;
+    k_mg_post1<<<F.blocks, kMgThreads, 0, s>>>(F, fl, A.lev[l + 1].x, A.alpha, done);
+    k_mg_post2<<<F.blocks, kMgThreads, 0, s>>>(F, fl, l == 0 ? out : F.x, l == 0 ? 1 : 0, done);
+  }
+}
+
+int amg_kernels_per_cycle(const Amg& A) { return A.L == 1 ? 1 : 4 * (A.L - 1) + 1; }
+
+void amg_free(Amg* A, cudaStream_t s) {
+  for (int l = 0; l < kMgMaxLevels; ++l) {
+    MgLevel& L = A->lev[l];
+    dev_free(&L.odinv, s);
+    dev_free(&L.agg, s);
+    dev_free(&L.mstart, s);
+    dev_free(&L.mlist, s);
+    dev_free(&L.f, s);
+    dev_free(&L.x, s);
+    dev_free(&L.y, s);
+    dev_free(&L.own_idx, s);
+    dev_free(&L.own_val, s);
+  }
+  dev_free(&A->binv, s);
+  A->L = 0;
+}
+
+}  // namespace hsm

@@ -23,8 +23,14 @@
 // pattern (block partials in fixed order, no spinning), whose final block also
 // updates the scalars and the convergence flag.  Once the flag is set the
 // remaining kernels of a launched chunk return at once.
+//
+// With the multigrid preconditioner (the default) an iteration forms p, runs
+// a V-cycle p -> p^ = M^-1 p, applies the bordered operator v = A p^, forms
+// s, runs s -> s^ = M^-1 s, applies t = A s^, and updates x and r: five
+// vector/operator kernels around two V-cycles (amg.cu).
 #include <vector>
 
+#include "amg.cuh"
 #include "common.cuh"
 
 struct hsm_stepper_s {
@@ -53,12 +59,13 @@ struct hsm_stepper_s {
   int head_chunks = 0;
   const double *gv = nullptr, *gT = nullptr, *gp = nullptr;
   int last_iters = 0;
+  hsm::Amg* amg = nullptr;    // multigrid preconditioner (nullptr: Jacobi)
 };
 
 namespace hsm {
 namespace {
 
-enum { V_R = 0, V_RHAT, V_P0, V_P1, V_V0, V_V1, V_S, V_T, V_RHS, V_COUNT };
+enum { V_R = 0, V_RHAT, V_P0, V_P1, V_V0, V_V1, V_S, V_T, V_RHS, V_PH, V_SH, V_COUNT };
 
 // Scalars of the Krylov solve (device memory, doubles + ints packed as doubles).
 struct KS {
@@ -446,6 +453,170 @@ __global__ void k_bicg_c(StepArgs a) {
   }
 }
 
+// ---- 2c. BiCGSTAB right-preconditioned by a multigrid cycle -----------------
+// The iterate of the bordered system is (p, c): the pressure field and KS::xN.
+// p = r + beta (p - omega v) over all N+1 entries.
+__global__ void k_pc_p(StepArgs a) {
+  const KS* ks = a.ks;
+  if (ks->done != 0.0) return;
+  const int64_t N1 = a.N + 1;
+  const double* r = a.vec + V_R * N1;
+  const double* v = a.vec + V_V0 * N1;
+  double* pv = a.vec + V_P0 * N1;
+  const double beta = ks->beta, omega = ks->omega;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N1; i += (int64_t)gridDim.x * blockDim.x)
+    pv[i] = r[i] + beta * (pv[i] - omega * v[i]);
+}
+
+// v = A p^ (bordered); alpha = rho / rhat.v
+template <int DIM>
+__global__ void k_pc_v(StepArgs a) {
+  const KS* ks = a.ks;
+  if (ks->done != 0.0) return;
+  int g;
+  int64_t pos, stride;
+  node_of(a, g, pos, stride);
+  const int W = a.width[g];
+  const int64_t G = a.count[g];
+  const int64_t N1 = a.N + 1;
+  const double* ph = a.vec + V_PH * N1;
+  const double* rh = a.vec + V_RHAT * N1;
+  double* v = a.vec + V_V0 * N1;
+  const double phN = ph[a.N];
+  double part[2] = {0.0, 0.0};
+  for (; pos < G; pos += stride) {
+    const int32_t i = a.nodes[g][pos];
+    const double* wpg = a.wp[g];
+    double y = phN;
+    for (int e = 0; e < W; ++e) y = fma(wpg[(int64_t)e * G + pos], ph[a.idx[g][(int64_t)e * G + pos]], y);
+    v[i] = y;
+    part[0] += ph[i];
+    part[1] += rh[i] * y;
+  }
+  double tot[2];
+  if (block_done<2>(a, 0, part, tot)) {
+    KS* k = a.ks;
+    v[a.N] = tot[0];
+    const double rv = tot[1] + rh[a.N] * tot[0];
+    if (rv == 0.0 || !isfinite(rv)) {
+      k->breakdown = 1.0;
+      k->done = 1.0;
+      return;
+    }
+    k->alpha = k->rho / rv;
+  }
+}
+
+// s = r - alpha v; a small s ends the iteration after x += alpha p^
+__global__ void k_pc_s(StepArgs a) {
+  const KS* ks = a.ks;
+  if (ks->done != 0.0) return;
+  const int64_t N1 = a.N + 1;
+  const double* r = a.vec + V_R * N1;
+  const double* v = a.vec + V_V0 * N1;
+  double* sv = a.vec + V_S * N1;
+  const double alpha = ks->alpha;
+  double part[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N1; i += (int64_t)gridDim.x * blockDim.x) {
+    const double si = r[i] - alpha * v[i];
+    sv[i] = si;
+    part[0] += si * si;
+  }
+  double tot[1];
+  if (block_done<1>(a, 1, part, tot)) {
+    KS* k = a.ks;
+    k->half = tot[0] <= k->tol2 * k->bnorm2 ? 1.0 : 0.0;
+  }
+}
+
+// t = A s^ (bordered); omega = t.s / t.t
+template <int DIM>
+__global__ void k_pc_t(StepArgs a) {
+  const KS* ks = a.ks;
+  if (ks->done != 0.0) return;
+  if (ks->half != 0.0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.ks->omega = 0.0;
+    return;
+  }
+  int g;
+  int64_t pos, stride;
+  node_of(a, g, pos, stride);
+  const int W = a.width[g];
+  const int64_t G = a.count[g];
+  const int64_t N1 = a.N + 1;
+  const double* sh = a.vec + V_SH * N1;
+  const double* sv = a.vec + V_S * N1;
+  double* t = a.vec + V_T * N1;
+  const double shN = sh[a.N];
+  double part[3] = {0.0, 0.0, 0.0};
+  for (; pos < G; pos += stride) {
+    const int32_t i = a.nodes[g][pos];
+    const double* wpg = a.wp[g];
+    double y = shN;
+    for (int e = 0; e < W; ++e) y = fma(wpg[(int64_t)e * G + pos], sh[a.idx[g][(int64_t)e * G + pos]], y);
+    t[i] = y;
+    part[0] += sh[i];
+    part[1] += y * sv[i];
+    part[2] += y * y;
+  }
+  double tot[3];
+  if (block_done<3>(a, 1, part, tot)) {
+    KS* k = a.ks;
+    const double tN = tot[0];
+    t[a.N] = tN;
+    const double ts = tot[1] + tN * sv[a.N], tt = tot[2] + tN * tN;
+    if (tt == 0.0 || !isfinite(tt)) {
+      k->breakdown = 1.0;
+      k->done = 1.0;
+    } else {
+      k->omega = ts / tt;
+    }
+  }
+}
+
+// x += alpha p^ + omega s^, r = s - omega t; rho_new = rhat.r, |r|^2
+__global__ void k_pc_x(StepArgs a) {
+  const KS* ks = a.ks;
+  if (ks->done != 0.0) return;
+  const int64_t N1 = a.N + 1;
+  double* r = a.vec + V_R * N1;
+  const double* rh = a.vec + V_RHAT * N1;
+  const double* ph = a.vec + V_PH * N1;
+  const double* sh = a.vec + V_SH * N1;
+  const double* sv = a.vec + V_S * N1;
+  const double* t = a.vec + V_T * N1;
+  const double alpha = ks->alpha, omega = ks->omega;
+  double part[2] = {0.0, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.N; i += (int64_t)gridDim.x * blockDim.x) {
+    a.p[i] += alpha * ph[i] + omega * sh[i];
+    const double ri = sv[i] - omega * t[i];
+    r[i] = ri;
+    part[0] += rh[i] * ri;
+    part[1] += ri * ri;
+  }
+  double tot[2];
+  if (block_done<2>(a, 2, part, tot)) {
+    KS* k = a.ks;
+    k->xN += alpha * ph[a.N] + omega * sh[a.N];
+    const double rN = sv[a.N] - omega * t[a.N];
+    r[a.N] = rN;
+    const double rho_new = tot[0] + rh[a.N] * rN;
+    k->rnorm2 = tot[1] + rN * rN;
+    k->iter += 1.0;
+    if (k->half != 0.0 || k->rnorm2 <= k->tol2 * k->bnorm2) {
+      k->done = 1.0;
+    } else if (rho_new == 0.0 || !isfinite(rho_new) || omega == 0.0) {
+      k->breakdown = 1.0;
+      k->done = 1.0;
+    } else if (k->iter >= k->max_it) {
+      k->done = 1.0;
+    } else {
+      k->beta = (rho_new / k->rho) * (alpha / omega);
+      k->rho = rho_new;
+    }
+  }
+}
+
 // ---- 3. correction and 4. temperature ----------------------------------------
 template <int DIM>
 __global__ void k_correct_temperature(StepArgs a) {
@@ -584,14 +755,31 @@ StepArgs make_args(hsm_stepper st, double* v, double* T, double* p) {
   return a;
 }
 
-constexpr int kChunk = 16;  // Krylov iterations per captured chunk
+// Krylov iterations per captured chunk: Jacobi needs thousands of iterations
+// per solve, the multigrid preconditioner tens, each of ~50 kernels.
+int chunk_iters(hsm_stepper st) { return st->amg ? 2 : 16; }
+int chunk_kernels(hsm_stepper st) {
+  return st->amg ? chunk_iters(st) * (5 + 2 * amg_kernels_per_cycle(*st->amg)) : chunk_iters(st) * 3;
+}
 
 template <int DIM>
-void launch_chunk(const StepArgs& a, dim3 grid, dim3 blk, cudaStream_t s) {
-  for (int c = 0; c < kChunk; ++c) {
-    k_bicg_a<DIM><<<grid, blk, 0, s>>>(a);
-    k_bicg_b<DIM><<<grid, blk, 0, s>>>(a);
-    k_bicg_c<DIM><<<grid, blk, 0, s>>>(a);
+void launch_chunk(hsm_stepper st, const StepArgs& a, dim3 grid, dim3 blk, cudaStream_t s) {
+  const int64_t N1 = a.N + 1;
+  for (int c = 0; c < chunk_iters(st); ++c) {
+    if (st->amg) {
+      const double* done = &a.ks->done;
+      k_pc_p<<<grid, blk, 0, s>>>(a);
+      amg_vcycle(*st->amg, a.vec + V_P0 * N1, a.vec + V_PH * N1, done, s);
+      k_pc_v<DIM><<<grid, blk, 0, s>>>(a);
+      k_pc_s<<<grid, blk, 0, s>>>(a);
+      amg_vcycle(*st->amg, a.vec + V_S * N1, a.vec + V_SH * N1, done, s);
+      k_pc_t<DIM><<<grid, blk, 0, s>>>(a);
+      k_pc_x<<<grid, blk, 0, s>>>(a);
+    } else {
+      k_bicg_a<DIM><<<grid, blk, 0, s>>>(a);
+      k_bicg_b<DIM><<<grid, blk, 0, s>>>(a);
+      k_bicg_c<DIM><<<grid, blk, 0, s>>>(a);
+    }
   }
 }
 
@@ -639,13 +827,14 @@ hsm_status run_steps(hsm_stepper st, int n_steps, double* v, double* T, double* 
   // legacy default stream) and launched on the plan's stream
   if (!st->cap) HSM_CUDA(pl, cudaStreamCreateWithFlags(&st->cap, cudaStreamNonBlocking));
   cudaStream_t cs = st->cap;
-  if (!st->g_chunk) HSM_CUDA(pl, capture(cs, &st->g_chunk, [&] { launch_chunk<DIM>(a, grid, blk, cs); }));
+  if (!st->g_chunk) HSM_CUDA(pl, capture(cs, &st->g_chunk, [&] { launch_chunk<DIM>(st, a, grid, blk, cs); }));
   if (!st->g_tail)
     HSM_CUDA(pl, capture(cs, &st->g_tail, [&] {
       k_correct_temperature<DIM><<<grid, blk, 0, cs>>>(a);
       k_temperature_bc<<<grid, blk, 0, cs>>>(a);
     }));
   KS host{};
+  const int kChunk = chunk_iters(st);
   const int max_chunks = (int)(st->phys.krylov_max_it / kChunk) + 2;
   for (int it = 0; it < n_steps; ++it) {
     const int want = std::min(max_chunks, (st->last_iters + kChunk - 1) / kChunk + 1);
@@ -655,19 +844,19 @@ hsm_status run_steps(hsm_stepper st, int n_steps, double* v, double* T, double* 
       HSM_CUDA(pl, capture(cs, &st->g_head, [&] {
         k_predictor<DIM><<<grid, blk, 0, cs>>>(a);
         k_krylov_init<DIM><<<grid, blk, 0, cs>>>(a);
-        for (int c = 0; c < want; ++c) launch_chunk<DIM>(a, grid, blk, cs);
+        for (int c = 0; c < want; ++c) launch_chunk<DIM>(st, a, grid, blk, cs);
       }));
       st->head_chunks = want;
     }
     HSM_CUDA(pl, cudaGraphLaunch(st->g_head, s));
-    pl->launches += 2 + 3 * kChunk * want;
+    pl->launches += 2 + chunk_kernels(st) * want;
     int done_chunks = want;
     for (;;) {
       HSM_CUDA(pl, cudaMemcpyAsync(&host, a.ks, sizeof(KS), cudaMemcpyDeviceToHost, s));
       HSM_CUDA(pl, cudaStreamSynchronize(s));
       if (host.done != 0.0 || done_chunks >= max_chunks) break;
       HSM_CUDA(pl, cudaGraphLaunch(st->g_chunk, s));
-      pl->launches += 3 * kChunk;
+      pl->launches += chunk_kernels(st);
       ++done_chunks;
     }
     st->last_iters = (int)host.iter;
@@ -696,6 +885,8 @@ hsm_status hsm_stepper_create(hsm_stepper* out, hsm_plan pl, const hsm_phys* phy
   if (!phys->bc || !phys->T_bc || !phys->normals) return set_error(pl, HSM_EINVAL, "bc, T_bc and normals are required");
   if (!(phys->dt > 0.0) || !(phys->krylov_tol > 0.0) || phys->krylov_max_it < 1)
     return set_error(pl, HSM_EINVAL, "dt, krylov_tol and krylov_max_it must be positive");
+  if (phys->precond != HSM_PRECOND_AMG && phys->precond != HSM_PRECOND_JACOBI)
+    return set_error(pl, HSM_EINVAL, "unknown preconditioner");
   hsm_stepper st = new (std::nothrow) hsm_stepper_s();
   if (!st) return set_error(pl, HSM_ENOMEM, "host allocation failed");
   st->plan = pl;
@@ -753,6 +944,13 @@ hsm_status hsm_stepper_create(hsm_stepper* out, hsm_plan pl, const hsm_phys* phy
   {
     StepArgs a = make_args(st, nullptr, nullptr, nullptr);
     k_minv<<<st->blocks_mon + st->blocks_rbf, st->threads, 0, s>>>(a);
+    if (phys->precond == HSM_PRECOND_AMG) {
+      st->amg = new (std::nothrow) Amg();
+      if (!st->amg) return fail(set_error(pl, HSM_ENOMEM, "host allocation failed"));
+      // over-correction of the coarse-grid step (2^d nodes per aggregate)
+      const hsm_status as = amg_setup(pl, a.wp[0], a.wp[1], pl->dim == 2 ? 1.8 : 1.5, st->amg);
+      if (as != HSM_OK) return fail(as);
+    }
   }
   cudaError_t e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return fail(cuda_fail(pl, e, "hsm_stepper_create"));
@@ -776,6 +974,11 @@ hsm_status hsm_stepper_destroy(hsm_stepper st) {
   cudaStream_t s = st->plan ? st->plan->stream : nullptr;
   drop_graphs(st);
   if (st->cap) cudaStreamDestroy(st->cap);
+  if (st->amg) {
+    amg_free(st->amg, s);
+    delete st->amg;
+    st->amg = nullptr;
+  }
   dev_free(&st->wp_rbf, s);
   dev_free(&st->wn_rbf, s);
   dev_free(&st->minv, s);

@@ -35,7 +35,11 @@ _i64 = C.c_int64
 class hsm_phys(C.Structure):
     _fields_ = [("Ra", C.c_double), ("Pr", C.c_double), ("dt", C.c_double), ("T_ref", C.c_double),
                 ("bc", _p), ("T_bc", _p), ("normals", _p), ("krylov_tol", C.c_double),
-                ("krylov_max_it", C.c_int)]
+                ("krylov_max_it", C.c_int), ("precond", C.c_int)]
+
+
+HSM_PRECOND_AMG = 0
+HSM_PRECOND_JACOBI = 1
 
 
 _SIGS = {
@@ -311,11 +315,12 @@ class Plan:
 class Stepper:
     """Owns an hsm_stepper on a plan (Section 3 explicit Boussinesq step)."""
 
-    def __init__(self, plan, Ra, Pr, dt, T_ref, bc, T_bc, normals, krylov_tol=1e-12, krylov_max_it=2000):
+    def __init__(self, plan, Ra, Pr, dt, T_ref, bc, T_bc, normals, krylov_tol=1e-12, krylov_max_it=2000,
+                 precond=HSM_PRECOND_AMG):
         self.plan = plan
         self._keep = (bc, T_bc, normals)
         self.phys = hsm_phys(float(Ra), float(Pr), float(dt), float(T_ref), ptr(bc).value, ptr(T_bc).value,
-                             ptr(normals).value, float(krylov_tol), int(krylov_max_it))
+                             ptr(normals).value, float(krylov_tol), int(krylov_max_it), int(precond))
         h_ = C.c_void_p()
         check(lib.hsm_stepper_create(C.byref(h_), plan.h, C.byref(self.phys)), plan.h)
         self.h = h_
