@@ -638,6 +638,53 @@ def run_kernels(args):
     u = torch.from_numpy(nodesets.field_sincos(ns.coords)[0]).to(dev)
     plan = hsm.Plan(c, reg, bnd, ns.h, m=2, normals=nrm)
     prec = {"fp64": hsm.HSM_PREC_FP64, "fp32r": hsm.HSM_PREC_FP32_REFINE}[args.prec]
+    if args.learned:
+        # learned weights on the predictor's workload shape: a short training on
+        # one tiled Poisson-disk set, then learned weights of a second set
+        def plan_of(nsx):
+            dd = [torch.from_numpy(a).to(dev) for a in (nsx.coords, nsx.is_regular, nsx.is_boundary, nsx.normals)]
+            px = hsm.Plan(dd[0], dd[1], dd[2], nsx.h, m=2, normals=dd[3])
+            px._d = dd
+            return px
+
+        base_tr = nodesets.cached(nodesets.square_all_scattered, n=300, seed=nodesets.SEED_BASE + 700)
+        base_te = nodesets.cached(nodesets.square_all_scattered, n=300, seed=nodesets.SEED_BASE + 701)
+        tr = nodesets.tiled(base_tr, 8, 8, jitter=lambda k: 0.3 * k / 63, seed=1000)
+        te = nodesets.tiled(base_te, 8, 8, jitter=lambda k: 0.3 * ((k * 37) % 64) / 63, seed=2000)
+        ptr_ = plan_of(tr)
+        ptr_.build_stencils()
+        ptr_.compute_weights(hsm.HSM_PREC_FP64)
+        X, Y = ptr_.learned_data()
+        ptr_.close()
+        mlp = hsm.MLP(24, 256, 3, 36, seed=5)
+        mlp.train(X, Y, steps=args.train_steps, batch=4096, lr=1e-3, seed=3)
+        pte = plan_of(te)
+        pte.build_stencils()
+        pte.attach(mlp)
+        for _ in range(args.warmup + args.steps):
+            pte.compute_weights(hsm.HSM_PREC_LEARNED)
+        torch.cuda.synchronize()
+        print("learned ok", te.N, pte.query()["n_fallback"])
+        pte.close()
+        mlp.close()
+        return
+    if args.stepper:
+        # explicit Boussinesq steps on the hybrid plan (Ra = 1e6, as in the bench's stepper section)
+        plan.build_stencils()
+        plan.compute_weights(hsm.HSM_PREC_FP64)
+        bc = torch.from_numpy(ns.bc).to(dev)
+        Tbc = torch.from_numpy(ns.T_bc).to(dev)
+        st = hsm.Stepper(plan, 1e6, 0.71, 0.1 * ns.h * ns.h / 2.0, ns.T_ref, bc, Tbc, nrm, krylov_tol=1e-10,
+                         krylov_max_it=4000)
+        v = torch.zeros((2, ns.N), dtype=torch.float64, device=dev)
+        T = torch.where(bc == 1, Tbc, torch.zeros_like(Tbc)).contiguous()
+        p = torch.zeros(ns.N, dtype=torch.float64, device=dev)
+        its, _ = st.step(v, T, p, args.steps, allow_notconv=True)
+        torch.cuda.synchronize()
+        st.close()
+        plan.close()
+        print("stepper ok", ns.N, its)
+        return
     for _ in range(args.warmup + args.steps):
         plan.build_stencils()
         plan.compute_weights(prec)
@@ -659,6 +706,9 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the 7M-node apply and learned sections")
     ap.add_argument("--all-rbffd", action="store_true", help="with --kernels: force every node to RBF-FD")
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32r"], help="with --kernels")
+    ap.add_argument("--stepper", action="store_true", help="with --kernels: run --steps Boussinesq steps instead")
+    ap.add_argument("--learned", action="store_true", help="with --kernels: learned weights instead")
+    ap.add_argument("--train-steps", type=int, default=3000, help="with --kernels --learned")
     args = ap.parse_args()
     if args.kernels:
         run_kernels(args)

@@ -18,38 +18,7 @@
 
 #include <cuda_bf16.h>
 
-#include "common.cuh"
-
-namespace hsm {
-
-struct Mlp {
-  int n_in = 24, hidden = 256, layers = 3, n_out = 36;
-  int nl = 4;                 // linear layers
-  std::vector<int> din, dout;  // padded in/out width per layer
-  std::vector<int> rin, rout;  // real widths
-  float* master = nullptr;    // fp32 [sum W + b] padded layout
-  float* adam_m = nullptr;
-  float* adam_v = nullptr;
-  float* grad = nullptr;
-  __nv_bfloat16* wbf = nullptr;  // bf16 copies of the weight matrices
-  std::vector<size_t> w_off, b_off, wbf_off;
-  size_t n_master = 0, n_wbf = 0;
-  int64_t t = 0;               // Adam step counter
-  cudaStream_t stream = nullptr;
-  // activation workspace for a batch of up to cap rows
-  int64_t cap = 0;
-  __nv_bfloat16* X = nullptr;     // [cap][din0]
-  std::vector<__nv_bfloat16*> H;  // per hidden layer [cap][dout]
-  std::vector<float*> Z;          // pre-activations [cap][dout]
-  float* Yout = nullptr;          // [cap][dout_last]
-  float* T = nullptr;             // targets [cap][dout_last]
-  __nv_bfloat16* dA = nullptr;    // [cap][max width]
-  __nv_bfloat16* dB = nullptr;
-  double* loss = nullptr;         // device loss accumulator
-  std::string last_error;
-};
-
-}  // namespace hsm
+#include "mlp.cuh"
 
 struct hsm_mlp_s {
   hsm::Mlp m;
@@ -524,6 +493,8 @@ hsm_status hsm_mlp_destroy(hsm_mlp h) {
   dev_free(&m.T, s);
   dev_free(&m.dA, s);
   dev_free(&m.dB, s);
+  dev_free(&m.Xf, s);
+  dev_free(&m.tc_err, s);
   cudaStreamSynchronize(s);
   delete h;
   return HSM_OK;
@@ -647,6 +618,30 @@ hsm_status hsm_mlp_train(hsm_mlp h, const float* X, const float* Y, int64_t coun
 hsm_status hsm_mlp_predict(hsm_mlp h, const float* X, int64_t count, float* Y) {
   if (!h || !X || !Y || count < 0) return set_error(nullptr, HSM_EINVAL, "mlp, X and Y are required");
   Mlp& m = h->m;
+  if (mlp_forward_tc_supported(m)) {
+    // fused tcgen05 forward pass: only the packed inputs live in global memory
+    const int64_t chunk = 1 << 20;
+    const int64_t rows = std::min<int64_t>(ceil_div(std::max<int64_t>(count, 1), BM) * BM, chunk);
+    if (rows > m.capf) {
+      dev_free(&m.Xf, m.stream);
+      MLP_CUDA(dev_alloc(&m.Xf, (size_t)rows * m.din[0], m.stream));
+      m.capf = rows;
+    }
+    for (int64_t b = 0; b < count; b += chunk) {
+      const int64_t cnt = std::min(chunk, count - b);
+      const int64_t r = ceil_div(cnt, BM) * BM;
+      k_pack<<<(int)std::min<int64_t>(ceil_div(r, 256), 4096), 256, 0, m.stream>>>(
+          X + b * m.n_in, nullptr, cnt, m.n_in, m.n_out, m.din[0], m.dout[m.nl - 1], r, 0, 0, 0, m.Xf, nullptr);
+      MLP_CUDA(cudaGetLastError());
+      const hsm_status st = mlp_forward_tc(m, m.Xf, cnt, Y + b * m.n_out, m.n_out);
+      if (st != HSM_OK) return mlp_fail(m, st, "fused tensor-core forward pass failed to launch");
+    }
+    unsigned err = 0;
+    MLP_CUDA(cudaMemcpyAsync(&err, m.tc_err, sizeof(unsigned), cudaMemcpyDeviceToHost, m.stream));
+    MLP_CUDA(cudaStreamSynchronize(m.stream));
+    if (err) return mlp_fail(m, HSM_ETIMEOUT, "fused tensor-core forward pass timed out");
+    return HSM_OK;
+  }
   const int64_t chunk = 1 << 18;
   const int64_t rows = std::min<int64_t>(ceil_div(std::max<int64_t>(count, 1), BM) * BM, chunk);
   hsm_status st = ensure_cap(m, rows);
@@ -672,6 +667,40 @@ hsm_status hsm_mlp_predict(hsm_mlp h, const float* X, int64_t count, float* Y) {
 namespace hsm {
 namespace {
 
+// Features of one 2D stencil: the scale s = max |x_i - x_c| and the canonical
+// frame Q (entry 1 onto +x, reflection putting entry 2 in the upper half
+// plane) in FP64, then the rotated scaled offsets in FP32 -- they feed a bf16
+// network.  Training data and inference use this one routine, so a stencil
+// gets bit-identical features on both paths.  Returns inv = 1/s, the frame
+// as (q00, q01, reflection sign).
+template <int NN>
+__device__ __forceinline__ void features2d(const double* __restrict__ coords, int64_t N,
+                                           const int32_t* __restrict__ idx, int64_t G, int64_t pos, float* x,
+                                           double& inv, double& q00, double& q01, double& sg) {
+  const int32_t c = idx[pos];
+  const double cx = coords[c], cy = coords[N + c];
+  double ox[NN], oy[NN], s2 = 0.0;
+#pragma unroll
+  for (int j = 0; j < NN; ++j) {
+    const int32_t id = idx[(int64_t)j * G + pos];
+    ox[j] = coords[id] - cx;
+    oy[j] = coords[N + id] - cy;
+    s2 = fmax(s2, ox[j] * ox[j] + oy[j] * oy[j]);
+  }
+  inv = 1.0 / sqrt(s2);
+  const double r1 = sqrt(ox[1] * ox[1] + oy[1] * oy[1]);
+  q00 = ox[1] / r1;
+  q01 = oy[1] / r1;
+  sg = (q00 * oy[2] - q01 * ox[2]) < 0.0 ? -1.0 : 1.0;  // second row of Q is sg * (-q01, q00)
+  const float f00 = (float)q00, f01 = (float)q01, fs = (float)sg, fi = (float)inv;
+#pragma unroll
+  for (int j = 0; j < NN; ++j) {
+    const float a = (float)ox[j] * fi, b = (float)oy[j] * fi;
+    x[2 * j] = fmaf(f00, a, f01 * b);
+    x[2 * j + 1] = fs * fmaf(f00, b, -f01 * a);
+  }
+}
+
 // Features of RBF-FD stencil positions (scaled offsets, node-major) and, when
 // Ylab is given, the scaled FP64 weights as labels ([op][node]).
 template <int DIM>
@@ -691,30 +720,18 @@ __global__ void k_features(const double* __restrict__ coords, int64_t N, const i
       }
       s2 = fmax(s2, r2);
     }
-    const double s = sqrt(s2), inv = 1.0 / s;
+    const double s = sqrt(s2);
+    double inv = 1.0 / s;
     // canonical frame (2D): entry 1 onto +x, entry 2 into the upper half plane
     double q00 = 1.0, q01 = 0.0, q10 = 0.0, q11 = 1.0;
-    if (DIM == 2) {
-      const int32_t i1 = idx[G + pos], i2 = idx[2 * G + pos];
-      const double vx = (coords[i1] - coords[c]) * inv, vy = (coords[N + i1] - coords[N + c]) * inv;
-      const double r = sqrt(vx * vx + vy * vy);
-      q00 = vx / r;
-      q01 = vy / r;
-      q10 = -q01;
-      q11 = q00;
-      const double x2 = (coords[i2] - coords[c]) * inv, y2 = (coords[N + i2] - coords[N + c]) * inv;
-      if (q10 * x2 + q11 * y2 < 0.0) {
-        q10 = -q10;
-        q11 = -q11;
-      }
-    }
-    for (int j = 0; j < n; ++j) {
-      const int32_t id = idx[(int64_t)j * G + pos];
-      if (DIM == 2) {
-        const double a = (coords[id] - coords[c]) * inv, b = (coords[N + id] - coords[N + c]) * inv;
-        X[t * (n * DIM) + j * DIM] = (float)(q00 * a + q01 * b);
-        X[t * (n * DIM) + j * DIM + 1] = (float)(q10 * a + q11 * b);
-      } else {
+    if (DIM == 2 && n == 12) {
+      double sg;
+      features2d<12>(coords, N, idx, G, pos, X + t * (n * DIM), inv, q00, q01, sg);
+      q10 = -sg * q01;
+      q11 = sg * q00;
+    } else {
+      for (int j = 0; j < n; ++j) {
+        const int32_t id = idx[(int64_t)j * G + pos];
         for (int k = 0; k < DIM; ++k)
           X[t * (n * DIM) + j * DIM + k] = (float)((coords[k * N + id] - coords[k * N + c]) * inv);
       }
@@ -736,6 +753,17 @@ __global__ void k_features(const double* __restrict__ coords, int64_t N, const i
   }
 }
 
+template <int NN>
+__global__ void k_features_infer2d(const double* __restrict__ coords, int64_t N, const int32_t* __restrict__ idx,
+                                   int64_t G, const int32_t* __restrict__ list, int64_t count, float* X,
+                                   double4* frame) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x) {
+    double inv, q00, q01, sg;
+    features2d<NN>(coords, N, idx, G, list[t], X + t * (2 * NN), inv, q00, q01, sg);
+    frame[t] = make_double4(inv, q00, q01, sg);
+  }
+}
+
 // FP64 projection w = w_hat + P (P^T P)^{-1} (l_p - P^T w_hat) in the scaled
 // variable, per stencil and operator; accepts when the pre-projection
 // relative residual is <= tau and the post-projection residual <= 1e-10.
@@ -748,52 +776,46 @@ template <int NN>
 __global__ void __launch_bounds__(128) k_project2d(const double* __restrict__ coords, int64_t N,
                                                    const int32_t* __restrict__ idx, int64_t G,
                                                    const int32_t* __restrict__ list, int64_t count,
-                                                   const float* __restrict__ Yp, double tau, double* w,
-                                                   int32_t* fail_list, int* fail_count, uint8_t* status) {
+                                                   const float* __restrict__ Yp, const double4* __restrict__ frame,
+                                                   double tau, double* w, int32_t* fail_list, int* fail_count,
+                                                   uint8_t* status) {
   constexpr int MP = 6;
   // L p at the centre: d/dx -> (0,1,0,0,0,0), d/dy -> (0,0,1,0,0,0),
   // Laplacian -> (0,0,0,2,0,2)
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t pos = list[t];
     const int32_t c = idx[pos];
-    double xs[NN], ys[NN];
-    double s2 = 0.0;
+    // scale and frame of the features the prediction was made from
+    const double4 fr = frame[t];
+    const double inv = fr.x, q00 = fr.y, q01 = fr.z, q10 = -fr.w * fr.z, q11 = fr.w * fr.y;
+    double pj[NN][MP - 1];  // x, y, x^2, xy, y^2 of every node
     const double cx = coords[c], cy = coords[N + c];
 #pragma unroll
     for (int j = 0; j < NN; ++j) {
       const int32_t id = idx[(int64_t)j * G + pos];
-      xs[j] = coords[id] - cx;
-      ys[j] = coords[N + id] - cy;
-      s2 = fmax(s2, xs[j] * xs[j] + ys[j] * ys[j]);
-    }
-    const double s = sqrt(s2), inv = 1.0 / s;
-#pragma unroll
-    for (int j = 0; j < NN; ++j) {
-      xs[j] *= inv;
-      ys[j] *= inv;
-    }
-    // canonical frame of the prediction (see k_features); derivative pairs
-    // are turned back with Q^T
-    const double r1 = sqrt(xs[1] * xs[1] + ys[1] * ys[1]);
-    const double q00 = xs[1] / r1, q01 = ys[1] / r1;
-    double q10 = -q01, q11 = q00;
-    if (q10 * xs[2] + q11 * ys[2] < 0.0) {
-      q10 = -q10;
-      q11 = -q11;
+      const double x = (coords[id] - cx) * inv, y = (coords[N + id] - cy) * inv;
+      pj[j][0] = x;
+      pj[j][1] = y;
+      pj[j][2] = x * x;
+      pj[j][3] = x * y;
+      pj[j][4] = y * y;
     }
     // G = P^T P (lower triangle), P row j = (1, x, y, x^2, xy, y^2)
     double Lc[MP][MP];
+    Lc[0][0] = (double)NN;
 #pragma unroll
-    for (int a = 0; a < MP; ++a)
+    for (int a = 1; a < MP; ++a) {
+      double sa = 0.0;
 #pragma unroll
-      for (int b = 0; b <= a; ++b) Lc[a][b] = 0.0;
+      for (int j = 0; j < NN; ++j) sa += pj[j][a - 1];
+      Lc[a][0] = sa;
 #pragma unroll
-    for (int j = 0; j < NN; ++j) {
-      const double pj[MP] = {1.0, xs[j], ys[j], xs[j] * xs[j], xs[j] * ys[j], ys[j] * ys[j]};
+      for (int b = 1; b <= a; ++b) {
+        double v = 0.0;
 #pragma unroll
-      for (int a = 0; a < MP; ++a)
-#pragma unroll
-        for (int b = 0; b <= a; ++b) Lc[a][b] = fma(pj[a], pj[b], Lc[a][b]);
+        for (int j = 0; j < NN; ++j) v = fma(pj[j][a - 1], pj[j][b - 1], v);
+        Lc[a][b] = v;
+      }
     }
     bool accept = true;
     double rdiag[MP];
@@ -820,23 +842,27 @@ __global__ void __launch_bounds__(128) k_project2d(const double* __restrict__ co
       double wh[NN];
 #pragma unroll
       for (int j = 0; j < NN; ++j) {
-        const double a = (double)yrow[j], b = (double)yrow[NN + j];
-        const double c0 = o == 0 ? q00 : q01, c1 = o == 0 ? q10 : q11;
-        wh[j] = o < 2 ? c0 * a + c1 * b : (double)yrow[2 * NN + j];
+        if (o < 2) {
+          // Q^T per node: (a, b) canonical -> physical component o
+          const double a = (double)yrow[j], b = (double)yrow[NN + j];
+          wh[j] = o == 0 ? fma(q00, a, q10 * b) : fma(q01, a, q11 * b);
+        } else {
+          wh[j] = (double)yrow[2 * NN + j];
+        }
       }
       // r = l_p - P^T w_hat
       double y[MP] = {0.0, o == 0 ? 1.0 : 0.0, o == 1 ? 1.0 : 0.0, o == 2 ? 2.0 : 0.0, 0.0, o == 2 ? 2.0 : 0.0};
 #pragma unroll
       for (int j = 0; j < NN; ++j) {
-        const double pj[MP] = {1.0, xs[j], ys[j], xs[j] * xs[j], xs[j] * ys[j], ys[j] * ys[j]};
+        y[0] -= wh[j];
 #pragma unroll
-        for (int q = 0; q < MP; ++q) y[q] = fma(-pj[q], wh[j], y[q]);
+        for (int q = 1; q < MP; ++q) y[q] = fma(-pj[j][q - 1], wh[j], y[q]);
       }
       double rn = 0.0;
 #pragma unroll
-      for (int q = 0; q < MP; ++q) rn += y[q] * y[q];
-      const double lpn = o == 2 ? 8.0 : 1.0;
-      if (!(sqrt(rn) <= tau * sqrt(lpn))) accept = false;
+      for (int q = 0; q < MP; ++q) rn = fma(y[q], y[q], rn);
+      const double lpn = o == 2 ? 8.0 : 1.0;  // |l_p|^2
+      if (!(rn <= tau * tau * lpn)) accept = false;
 #pragma unroll
       for (int a = 0; a < MP; ++a) {  // L z = r
         double v = y[a];
@@ -856,12 +882,12 @@ __global__ void __launch_bounds__(128) k_project2d(const double* __restrict__ co
       const double sc = o == 2 ? inv * inv : inv;
 #pragma unroll
       for (int j = 0; j < NN; ++j) {
-        const double pj[MP] = {1.0, xs[j], ys[j], xs[j] * xs[j], xs[j] * ys[j], ys[j] * ys[j]};
-        double v = wh[j];
+        double v = wh[j] + y[0];
 #pragma unroll
-        for (int q = 0; q < MP; ++q) v = fma(pj[q], y[q], v);
+        for (int q = 1; q < MP; ++q) v = fma(pj[j][q - 1], y[q], v);
+        res[0] += v;
 #pragma unroll
-        for (int q = 0; q < MP; ++q) res[q] = fma(pj[q], v, res[q]);
+        for (int q = 1; q < MP; ++q) res[q] = fma(pj[j][q - 1], v, res[q]);
         w[((int64_t)o * NN + j) * G + pos] = v * sc;
       }
 #pragma unroll
@@ -903,6 +929,7 @@ hsm_status compute_rbf_weights_learned(hsm_plan p, uint8_t* status, int32_t* fai
   int32_t* learn = nullptr;
   int* lcount = nullptr;
   float *X = nullptr, *Y = nullptr;
+  double4* frame = nullptr;
   int* kinds = nullptr;
   HSM_CUDA(p, dev_alloc(&learn, G, s));
   HSM_CUDA(p, dev_alloc(&lcount, 1, s));
@@ -921,13 +948,13 @@ hsm_status compute_rbf_weights_learned(hsm_plan p, uint8_t* status, int32_t* fai
       if (p->op_mask & (1u << b)) kh[o++] = b;
     HSM_CUDA(p, dev_alloc(&kinds, 4, s));
     HSM_CUDA(p, cudaMemcpyAsync(kinds, kh, sizeof(kh), cudaMemcpyHostToDevice, s));
+    if (!(dim == 2 && n == 12 && p->n_mono == 6 && p->op_mask == (HSM_DX | HSM_DY | HSM_LAP)))
+      return set_error(p, HSM_EINVAL, "learned weights support 2D m = 2, n = 12 plans with ops dx, dy, lap");
     HSM_CUDA(p, dev_alloc(&X, (size_t)lc * n * dim, s));
     HSM_CUDA(p, dev_alloc(&Y, (size_t)lc * n * p->nops, s));
+    HSM_CUDA(p, dev_alloc(&frame, lc, s));
     const int gl = (int)std::min<int64_t>(ceil_div(lc, T), (int64_t)num_sms() * 8);
-    if (dim == 2)
-      k_features<2><<<gl, T, 0, s>>>(p->coords, p->N, p->rbf.idx, G, n, learn, lc, nullptr, kinds, p->nops, X, nullptr);
-    else
-      k_features<3><<<gl, T, 0, s>>>(p->coords, p->N, p->rbf.idx, G, n, learn, lc, nullptr, kinds, p->nops, X, nullptr);
+    k_features_infer2d<12><<<gl, T, 0, s>>>(p->coords, p->N, p->rbf.idx, G, learn, lc, X, frame);
     HSM_CUDA(p, cudaGetLastError());
     cudaStream_t old = m.stream;
     m.stream = s;
@@ -935,10 +962,8 @@ hsm_status compute_rbf_weights_learned(hsm_plan p, uint8_t* status, int32_t* fai
     m.stream = old;
     if (st != HSM_OK) return set_error(p, st, m.last_error);
     const int gp = (int)std::min<int64_t>(ceil_div(lc, 128), (int64_t)num_sms() * 16);
-    if (dim == 2 && n == 12 && p->n_mono == 6 && p->op_mask == (HSM_DX | HSM_DY | HSM_LAP))
-      k_project2d<12><<<gp, 128, 0, s>>>(p->coords, p->N, p->rbf.idx, G, learn, lc, Y, 1.5, p->rbf.w64, fail_list,
-                                         fail_count, status);
-    else return set_error(p, HSM_EINVAL, "learned weights support 2D m = 2, n = 12 plans with ops dx, dy, lap");
+    k_project2d<12><<<gp, 128, 0, s>>>(p->coords, p->N, p->rbf.idx, G, learn, lc, Y, frame, 1.5, p->rbf.w64,
+                                       fail_list, fail_count, status);
     HSM_CUDA(p, cudaGetLastError());
     p->launches += 4;
   }
@@ -946,6 +971,7 @@ hsm_status compute_rbf_weights_learned(hsm_plan p, uint8_t* status, int32_t* fai
   dev_free(&lcount, s);
   dev_free(&X, s);
   dev_free(&Y, s);
+  dev_free(&frame, s);
   dev_free(&kinds, s);
   return HSM_OK;
 }

@@ -129,3 +129,22 @@ def test_learned_weights_end_to_end():
     assert err_l[deep].max() <= 5.0 * err_d[deep].max()
     plan.close()
     mlp.close()
+
+
+def test_fused_forward_spans_many_tiles():
+    """The fused tcgen05 forward pass over 1,000 128-row tiles plus a ragged
+    tail (rows % 128 = 37), against the FP64 oracle forward pass."""
+    import torch
+    from paper_2303_01760_gb300 import hsm
+
+    rng = np.random.default_rng(11)
+    rows = 128 * 1000 + 37
+    Xn = rng.uniform(-1.0, 1.0, size=(rows, 24))
+    mlp = hsm.MLP(24, H, L, 36, seed=9)
+    P = _oracle_params(mlp)
+    out = mlp.predict(torch.from_numpy(Xn.astype(np.float32)).cuda()).double().cpu().numpy()
+    sample = np.r_[np.arange(0, 300), rng.choice(rows, 3000, replace=False), np.arange(rows - 200, rows)]
+    out_ref, _, _ = ol.forward(P, Xn[sample].astype(np.float32).astype(np.float64))
+    scale = np.abs(out_ref).max()
+    assert np.abs(out[sample] - out_ref).max() <= TOL_BF16_FWD * scale
+    mlp.close()
