@@ -262,6 +262,7 @@ def run_gpu(args):
     # large-scale apply roofline and the learned-weight comparison
     big = run_big_apply(hsm, nodesets, dev, stream, flush, args) if (rank == 0 and not args.no_extras) else None
     learned = run_learned(hsm, nodesets, dev, stream, flush, args) if (rank == 0 and not args.no_extras) else None
+    three_d = run_3d(hsm, nodesets, dev, stream, flush, args) if (rank == 0 and not args.no_extras) else None
 
     res = None
     if rank == 0:
@@ -288,6 +289,7 @@ def run_gpu(args):
             "counts": {"mon": q_h["n_mon"], "rbf": n_rbf_h, "demoted": q_h["n_demoted"]},
             "parity": gate,
             "apply_roofline": big,
+            "three_d": three_d,
             "learned": learned,
             "clocks": clocks,
             "tuning": {"note": "lanes per RBF-FD system and apply block size picked by hsm_plan_autotune "
@@ -408,6 +410,86 @@ def run_big_apply(hsm, nodesets, dev, stream, flush, args):
     res["bound"] = "hbm"
     res["peak_source"] = f"{src} (MEASURED_PEAKS.json hbm_gbs: STREAM-style copy)"
     plan.close()
+    return res
+
+
+def run_3d(hsm, nodesets, dev, stream, flush, args):
+    """The 3D configuration's shape at 213k nodes: unit cube minus 20 seeded
+    spheres, lattice h = 1/60, scattered within 0.05 of a sphere.  For m = 2
+    (n = 20) and m = 3 (n = 40): FP64 and FP32 + FP64-refinement weights
+    (times, fallbacks, sampled parity against the oracle) and the fused
+    application of grad and Laplacian with f64 and f32 storage."""
+    import numpy as np
+    import torch
+
+    from oracle import stencils as ost
+    from oracle import weights as ow
+
+    ns = nodesets.cached(nodesets.cube_spheres, n=60)
+    d = [torch.from_numpy(a).to(dev) for a in (ns.coords, ns.is_regular, ns.is_boundary, ns.normals)]
+    u = torch.from_numpy(nodesets.field_random_smooth(ns.coords)[0]).to(dev)
+    rng = np.random.default_rng(17)
+    sample = np.sort(rng.choice(ns.N, 300, replace=False))
+    res = {"workload": f"3D, {ns.N} nodes ({ns.n_scattered / ns.N:.1%} scattered): unit cube minus 20 spheres, "
+                       "lattice h=1/60, band 0.05; ops dx,dy,dz,lap", "nodes": int(ns.N)}
+    peak, _ = hbm_peak()
+    for m in (2, 3):
+        n = ow.stencil_size(3, m)
+        plan = hsm.Plan(d[0], d[1], d[2], ns.h, m=m, normals=d[3], stream=stream)
+        plan.set_timing(True)
+        plan.build_stencils()
+        plan.autotune(os.path.join(ROOT, "build", "hsm_tune.txt"))
+        st = ost.build_stencils(ns.coords, ns.is_regular, ns.is_boundary, ns.h, n, centers=sample,
+                                use_kdtree=True, normals=ns.normals)
+        out = {"n": n}
+        status = torch.zeros(ns.N, dtype=torch.uint8, device=dev)
+        # systems singular to working precision (flagged 255) have no weights
+        # on either side: leave them out of the sampled comparison
+        plan.compute_weights(hsm.HSM_PREC_FP64, status, allow_singular=True)
+        sing = status.cpu().numpy()[st["rbf_nodes"]] == 255
+        st = dict(st, rbf_nodes=st["rbf_nodes"][~sing], rbf_idx=st["rbf_idx"][~sing])
+        W = ow.all_weights(ns.coords, st, m)
+        for prec, name in ((hsm.HSM_PREC_FP64, "fp64"), (hsm.HSM_PREC_FP32_REFINE, "fp32_refine")):
+            plan.compute_weights(prec, status, allow_singular=True)
+            ts = []
+            for _ in range(2):
+                flush.zero_()
+                plan.compute_weights(prec, status, allow_singular=True)
+                ph = plan.profile()[0]
+                ts.append(ph[1] + ph[2])
+            q = plan.query()
+            stat = status.cpu().numpy()
+            singular = stat == 255
+            worst = 0.0
+            for k, op in enumerate(("dx", "dy", "dz", "lap")):
+                rp, col, val = [t.cpu().numpy() for t in plan.export_csr(1 << k)]
+                nodes, idx = st["rbf_nodes"], st["rbf_idx"]
+                keep = ~singular[nodes]
+                ix = rp[nodes[keep]][:, None] + np.arange(n)[None, :]
+                if not np.array_equal(col[ix], idx[keep]):
+                    worst = float("inf")
+                    break
+                Wo = W["rbf"][op][keep]
+                e = np.abs(val[ix] - Wo).max(1) / np.abs(Wo).max(1)
+                worst = max(worst, float(e.max()) if e.size else 0.0)
+            out[name] = {"weights_ms": float(np.mean(ts)), "nodes_per_s": ns.N / (np.mean(ts) * 1e-3),
+                         "fallbacks": q["n_fallback"], "singular_nodes": int(singular.sum()),
+                         "sampled_rbf_nodes": int(len(st["rbf_nodes"])), "max_rel_weight_err": worst}
+        plan.compute_weights(hsm.HSM_PREC_FP64, allow_singular=True)
+        q = plan.query()
+        o = torch.empty((4, ns.N), dtype=torch.float64, device=dev)
+        for name, uu, f32 in (("apply_f64", u, False), ("apply_f32", u.float(), True)):
+            plan.apply(uu, out=o)
+            ts = []
+            for _ in range(max(args.steps, 5)):
+                flush.zero_()
+                plan.apply(uu, out=o)
+                ts.append(plan.profile()[0][3])
+            t = float(np.median(ts))
+            b = apply_bytes(q, ns.N, ns.N - q["n_mon"], q["n_mon"], 7, n, 4, f32)
+            out[name] = {"ms": t, "achieved_GBs": b / (t * 1e-3) / 1e9, "frac": b / (t * 1e-3) / 1e9 / peak}
+        res[f"m{m}"] = out
+        plan.close()
     return res
 
 
