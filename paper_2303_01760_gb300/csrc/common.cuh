@@ -69,6 +69,8 @@ struct BuildWs {
   int graph_qt = 0;                    // kNN variant the graph was captured with
   int graph_kernels = 0;               // kernels per replay
   cudaStream_t cap = nullptr;
+  cudaStream_t side = nullptr;         // capture branch of the MON stencils
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool ready = false;
 };
 

@@ -37,86 +37,6 @@ __host__ __device__ inline double host_from_ordered(unsigned long long b) {
   return d;
 }
 
-// Bounding box (ordered-bit keys) and lattice extents of the node set: each
-// thread keeps running extrema, the block reduces them with warp shuffles,
-// and one thread per block issues the global atomics.
-__global__ void __launch_bounds__(256) k_bounds(const double* __restrict__ coords, int64_t N, int dim, double inv_h,
-                                                unsigned long long* bbox, int* lat_lo, int* lat_hi, int32_t* ijk,
-                                                uint8_t* on_lat) {
-  unsigned long long bmin[kMaxDim], bmax[kMaxDim];
-  int lmin[kMaxDim], lmax[kMaxDim];
-  for (int k = 0; k < kMaxDim; ++k) {
-    bmin[k] = ~0ull;
-    bmax[k] = 0ull;
-    lmin[k] = 0x7fffffff;
-    lmax[k] = -0x7fffffff;
-  }
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    bool on = true;
-    int q[kMaxDim];
-    for (int k = 0; k < dim; ++k) {
-      double x = coords[k * N + i];
-      unsigned long long ob = ordered_bits(x);
-      bmin[k] = ob < bmin[k] ? ob : bmin[k];
-      bmax[k] = ob > bmax[k] ? ob : bmax[k];
-      double t = x * inv_h;
-      double r = rint(t);
-      if (!(fabs(t - r) <= kLatticeTol) || fabs(r) >= kLatticeRange) on = false;
-      q[k] = on ? (int)r : 0;
-    }
-    on_lat[i] = on ? 1 : 0;
-    for (int k = 0; k < dim; ++k) {
-      ijk[k * N + i] = q[k];
-      if (on) {
-        lmin[k] = min(lmin[k], q[k]);
-        lmax[k] = max(lmax[k], q[k]);
-      }
-    }
-  }
-  __shared__ unsigned long long sb[2][kMaxDim][8];
-  __shared__ int sl[2][kMaxDim][8];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int k = 0; k < dim; ++k) {
-    for (int o = 16; o > 0; o >>= 1) {
-      unsigned long long a = __shfl_xor_sync(0xffffffffu, bmin[k], o);
-      unsigned long long b = __shfl_xor_sync(0xffffffffu, bmax[k], o);
-      int c = __shfl_xor_sync(0xffffffffu, lmin[k], o);
-      int d = __shfl_xor_sync(0xffffffffu, lmax[k], o);
-      bmin[k] = a < bmin[k] ? a : bmin[k];
-      bmax[k] = b > bmax[k] ? b : bmax[k];
-      lmin[k] = min(lmin[k], c);
-      lmax[k] = max(lmax[k], d);
-    }
-    if (lane == 0) {
-      sb[0][k][wid] = bmin[k];
-      sb[1][k][wid] = bmax[k];
-      sl[0][k][wid] = lmin[k];
-      sl[1][k][wid] = lmax[k];
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const int nw = (blockDim.x + 31) / 32;
-    for (int k = 0; k < dim; ++k) {
-      unsigned long long a = ~0ull, b = 0ull;
-      int c = 0x7fffffff, d = -0x7fffffff;
-      for (int w = 0; w < nw; ++w) {
-        a = sb[0][k][w] < a ? sb[0][k][w] : a;
-        b = sb[1][k][w] > b ? sb[1][k][w] : b;
-        c = min(c, sl[0][k][w]);
-        d = max(d, sl[1][k][w]);
-      }
-      atomicMin(&bbox[2 * k], a);
-      atomicMax(&bbox[2 * k + 1], b);
-      if (c <= d) {
-        atomicMin(&lat_lo[k], c);
-        atomicMax(&lat_hi[k], d);
-      }
-    }
-  }
-}
-
 // Lattice map: open-addressing hash table from packed lattice coordinates
 // (21 bits per axis) to the lowest node id on that lattice point; capacity a
 // power of two >= 2N, linear probing, every probe loop bounded by the
@@ -166,16 +86,88 @@ struct LatticeHash {
   }
 };
 
-__global__ void k_lattice_insert(const int32_t* __restrict__ ijk, const uint8_t* __restrict__ on_lat,
-                                 int64_t N, LatticeHash g) {
+// Bounding box (ordered-bit keys) and lattice extents of the node set, and
+// the lattice map: each thread keeps running extrema and inserts its node's
+// lattice point, the block reduces the extrema with warp shuffles, and one
+// thread per block issues the global atomics.
+__global__ void __launch_bounds__(256) k_bounds(const double* __restrict__ coords, int64_t N, int dim, double inv_h,
+                                                unsigned long long* bbox, int* lat_lo, int* lat_hi, int32_t* ijk,
+                                                uint8_t* on_lat, LatticeHash lh) {
+  unsigned long long bmin[kMaxDim], bmax[kMaxDim];
+  int lmin[kMaxDim], lmax[kMaxDim];
+  for (int k = 0; k < kMaxDim; ++k) {
+    bmin[k] = ~0ull;
+    bmax[k] = 0ull;
+    lmin[k] = 0x7fffffff;
+    lmax[k] = -0x7fffffff;
+  }
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
-    if (!on_lat[i]) continue;
+    bool on = true;
     int q[kMaxDim];
-    for (int k = 0; k < g.dim; ++k) q[k] = ijk[k * N + i];
-    g.insert(q, (int32_t)i);
+    for (int k = 0; k < dim; ++k) {
+      double x = coords[k * N + i];
+      unsigned long long ob = ordered_bits(x);
+      bmin[k] = ob < bmin[k] ? ob : bmin[k];
+      bmax[k] = ob > bmax[k] ? ob : bmax[k];
+      double t = x * inv_h;
+      double r = rint(t);
+      if (!(fabs(t - r) <= kLatticeTol) || fabs(r) >= kLatticeRange) on = false;
+      q[k] = on ? (int)r : 0;
+    }
+    on_lat[i] = on ? 1 : 0;
+    for (int k = 0; k < dim; ++k) {
+      ijk[k * N + i] = q[k];
+      if (on) {
+        lmin[k] = min(lmin[k], q[k]);
+        lmax[k] = max(lmax[k], q[k]);
+      }
+    }
+    if (on) lh.insert(q, (int32_t)i);
+  }
+  __shared__ unsigned long long sb[2][kMaxDim][8];
+  __shared__ int sl[2][kMaxDim][8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int k = 0; k < dim; ++k) {
+    for (int o = 16; o > 0; o >>= 1) {
+      unsigned long long a = __shfl_xor_sync(0xffffffffu, bmin[k], o);
+      unsigned long long b = __shfl_xor_sync(0xffffffffu, bmax[k], o);
+      int c = __shfl_xor_sync(0xffffffffu, lmin[k], o);
+      int d = __shfl_xor_sync(0xffffffffu, lmax[k], o);
+      bmin[k] = a < bmin[k] ? a : bmin[k];
+      bmax[k] = b > bmax[k] ? b : bmax[k];
+      lmin[k] = min(lmin[k], c);
+      lmax[k] = max(lmax[k], d);
+    }
+    if (lane == 0) {
+      sb[0][k][wid] = bmin[k];
+      sb[1][k][wid] = bmax[k];
+      sl[0][k][wid] = lmin[k];
+      sl[1][k][wid] = lmax[k];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) / 32;
+    for (int k = 0; k < dim; ++k) {
+      unsigned long long a = ~0ull, b = 0ull;
+      int c = 0x7fffffff, d = -0x7fffffff;
+      for (int w = 0; w < nw; ++w) {
+        a = sb[0][k][w] < a ? sb[0][k][w] : a;
+        b = sb[1][k][w] > b ? sb[1][k][w] : b;
+        c = min(c, sl[0][k][w]);
+        d = max(d, sl[1][k][w]);
+      }
+      atomicMin(&bbox[2 * k], a);
+      atomicMax(&bbox[2 * k + 1], b);
+      if (c <= d) {
+        atomicMin(&lat_lo[k], c);
+        atomicMax(&lat_hi[k], d);
+      }
+    }
   }
 }
+
 
 // kind = 0 (MON) when the node is regular, interior, owns its lattice point and
 // has all 2d lattice neighbours; 1 (RBF-FD) otherwise.
@@ -538,6 +530,8 @@ hsm_status alloc_build_ws(hsm_plan p) {
   HSM_CUDA(p, dev_alloc(&p->rbf.idx, (size_t)p->rbf.width * N, s));
   HSM_CUDA(p, cudaMallocHost((void**)&w.readback, 4 * sizeof(int)));
   HSM_CUDA(p, cudaStreamCreateWithFlags(&w.cap, cudaStreamNonBlocking));
+  HSM_CUDA(p, cudaStreamCreateWithFlags(&w.side, cudaStreamNonBlocking));
+  for (cudaEvent_t* e : {&w.ev_fork, &w.ev_join}) HSM_CUDA(p, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
   w.ready = true;
   return HSM_OK;
 }
@@ -554,7 +548,12 @@ void free_build_ws(hsm_plan p) {
   if (w.readback) cudaFreeHost(w.readback);
   w.readback = nullptr;
   if (w.cap) cudaStreamDestroy(w.cap);
-  w.cap = nullptr;
+  if (w.side) cudaStreamDestroy(w.side);
+  for (cudaEvent_t* e : {&w.ev_fork, &w.ev_join}) {
+    if (*e) cudaEventDestroy(*e);
+    *e = nullptr;
+  }
+  w.cap = w.side = nullptr;
   w.ready = false;
 }
 
@@ -592,11 +591,7 @@ cudaError_t enqueue_build(hsm_plan p, cudaStream_t s, int qt, int* nk) {
   HSM_TRY(cudaMemsetAsync(lat, 0x7f, kMaxDim * sizeof(int), s));
   HSM_TRY(cudaMemsetAsync(lat + kMaxDim, 0x80, kMaxDim * sizeof(int), s));
   HSM_TRY(cudaMemsetAsync(lat + 2 * kMaxDim, 0, 4 * sizeof(int), s));
-  k_bounds<<<grid, T, 0, s>>>(p->coords, N, dim, 1.0 / p->h, w.bbox, lat, lat + kMaxDim, w.ijk, w.on_lat);
-  ++k;
-  HSM_TRY(cudaGetLastError());
-
-  // ---- lattice hash map and classification
+  // lattice hash map, filled by k_bounds
   LatticeHash lh;
   lh.dim = dim;
   lh.mask = w.hcap - 1;
@@ -604,20 +599,28 @@ cudaError_t enqueue_build(hsm_plan p, cudaStream_t s, int qt, int* nk) {
   lh.vals = w.hvals;
   HSM_TRY(cudaMemsetAsync(lh.keys, 0xff, w.hcap * sizeof(unsigned long long), s));
   HSM_TRY(cudaMemsetAsync(lh.vals, 0x7f, w.hcap * sizeof(int32_t), s));
-  k_lattice_insert<<<grid, T, 0, s>>>(w.ijk, w.on_lat, N, lh);
+  k_bounds<<<grid, T, 0, s>>>(p->coords, N, dim, 1.0 / p->h, w.bbox, lat, lat + kMaxDim, w.ijk, w.on_lat, lh);
+  ++k;
+  HSM_TRY(cudaGetLastError());
+
+  // ---- classification
   int* d_demoted = lat + 2 * kMaxDim;
   int* counts = lat + 2 * kMaxDim + 1;
   k_classify<<<grid, T, 0, s>>>(w.ijk, w.on_lat, p->is_regular, p->is_boundary, N, lh, p->kind, d_demoted);
-  k += 2;
+  ++k;
   HSM_TRY(cudaGetLastError());
 
   // ---- group lists (ascending node ids) and positions
   HSM_TRY(select_indices(p->kind, 0, N, p->mon.nodes, p->pos, counts, s, w.scan_ws));
   HSM_TRY(select_indices(p->kind, 1, N, p->rbf.nodes, p->pos, counts + 1, s, w.scan_ws));
   k += 6;
-  k_mon_stencil<<<grid, T, 0, s>>>(w.ijk, p->mon.nodes, counts, N, lh, p->mon.idx);
+  // MON stencils on a side branch of the graph, joined before the read-back
+  HSM_TRY(cudaEventRecord(w.ev_fork, s));
+  HSM_TRY(cudaStreamWaitEvent(w.side, w.ev_fork, 0));
+  k_mon_stencil<<<grid, T, 0, w.side>>>(w.ijk, p->mon.nodes, counts, N, lh, p->mon.idx);
   ++k;
   HSM_TRY(cudaGetLastError());
+  HSM_TRY(cudaEventRecord(w.ev_join, w.side));
 
   // ---- kNN for the RBF-FD group
   const int64_t ncell_max = 4 * N + 1024;
@@ -662,6 +665,7 @@ cudaError_t enqueue_build(hsm_plan p, cudaStream_t s, int qt, int* nk) {
     ++k;
   }
   // ---- status bits next to the counters, then the one read-back
+  HSM_TRY(cudaStreamWaitEvent(s, w.ev_join, 0));
   HSM_TRY(cudaMemcpyAsync(lat + 2 * kMaxDim + 3, p->dev_flags, sizeof(unsigned), cudaMemcpyDeviceToDevice, s));
   HSM_TRY(cudaMemcpyAsync(w.readback, lat + 2 * kMaxDim, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
   *nk = k;

@@ -53,28 +53,18 @@ __global__ void __launch_bounds__(128) k_mon(const double* __restrict__ coords, 
   constexpr int K = 2 * DIM + 1;
   constexpr int C = K + NOPS;
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < G; p += (int64_t)gridDim.x * blockDim.x) {
-    double xi[K][DIM];
-    const int32_t c = idx[p];
+    int32_t id[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) id[j] = idx[(int64_t)j * G + p];
+    const int32_t c = id[0];
     double cx[DIM];
 #pragma unroll
     for (int k = 0; k < DIM; ++k) cx[k] = coords[k * N + c];
-    double s2 = 0.0;
-#pragma unroll
-    for (int j = 0; j < K; ++j) {
-      const int32_t id = idx[(int64_t)j * G + p];
-      double r2 = 0.0;
-#pragma unroll
-      for (int k = 0; k < DIM; ++k) {
-        const double o = coords[k * N + id] - cx[k];
-        xi[j][k] = o;
-        r2 += o * o;
-      }
-      s2 = fmax(s2, r2);
-    }
-    // Axis-aligned stencil (every neighbour offset is zero off its own axis,
-    // as for nodes placed exactly on the lattice): the system decouples into
-    // one 3-point Vandermonde system per axis, solved in closed form with
-    // a = |x_c - x_{c-e}|, b = |x_{c+e} - x_c|, r = 1 / (a b (a + b)):
+    // Axis-aligned stencil (each neighbour c -+ e_k shares every other
+    // coordinate with c, as for nodes placed exactly on the lattice), tested
+    // on the coordinates' bits: the system decouples into one 3-point
+    // Vandermonde system per axis, solved in closed form with
+    // a = x_c - x_{c-e}, b = x_{c+e} - x_c, r = 1 / (a b (a + b)):
     //   d/dx_k : w(c-e) = -b^2 r, w(c+e) = a^2 r, w(c) = -(w(c-e) + w(c+e))
     //   lap    : w(c-e) = 2 b r,  w(c+e) = 2 a r, summed over the axes.
     bool aligned = true;
@@ -82,19 +72,27 @@ __global__ void __launch_bounds__(128) k_mon(const double* __restrict__ coords, 
     for (int k = 0; k < DIM; ++k)
 #pragma unroll
       for (int e = 0; e < DIM; ++e)
-        if (e != k) aligned = aligned && xi[1 + 2 * k][e] == 0.0 && xi[2 + 2 * k][e] == 0.0;
+        if (e != k) {
+          const long long ce = __double_as_longlong(cx[e]);
+          aligned = aligned && __double_as_longlong(coords[e * N + id[1 + 2 * k]]) == ce &&
+                    __double_as_longlong(coords[e * N + id[2 + 2 * k]]) == ce;
+        }
     if (aligned) {
       double wm[DIM], wp[DIM], lm[DIM], lpl[DIM];
       bool okk = true;
 #pragma unroll
       for (int k = 0; k < DIM; ++k) {
-        const double a = -xi[1 + 2 * k][k], b = xi[2 + 2 * k][k];
-        okk = okk && a > 0.0 && b > 0.0;
-        const double r = 1.0 / (a * b * (a + b));
-        wm[k] = -b * b * r;
-        wp[k] = a * a * r;
-        lm[k] = 2.0 * b * r;
-        lpl[k] = 2.0 * a * r;
+        const double a = cx[k] - coords[k * N + id[1 + 2 * k]], b = coords[k * N + id[2 + 2 * k]] - cx[k];
+        // a, b > 0 and finite, on the bits
+        const unsigned long long ab = (unsigned long long)__double_as_longlong(a),
+                                 bb = (unsigned long long)__double_as_longlong(b);
+        okk = okk && ab - 1ull < 0x7fefffffffffffffull && bb - 1ull < 0x7fefffffffffffffull;
+        const double r = recip(a * b * (a + b));
+        const double br = b * r, ar = a * r;
+        wm[k] = -b * br;
+        wp[k] = a * ar;
+        lm[k] = br + br;
+        lpl[k] = ar + ar;
       }
 #pragma unroll
       for (int o = 0; o < NOPS; ++o) {
@@ -110,7 +108,7 @@ __global__ void __launch_bounds__(128) k_mon(const double* __restrict__ coords, 
             m = wm[k];
             pl = wp[k];
           }
-          wc -= m + pl;
+          if (kd == 3 || kd == k) wc -= m + pl;
           w[((int64_t)o * K + 1 + 2 * k) * G + p] = okk ? m : 0.0;
           w[((int64_t)o * K + 2 + 2 * k) * G + p] = okk ? pl : 0.0;
         }
@@ -119,6 +117,19 @@ __global__ void __launch_bounds__(128) k_mon(const double* __restrict__ coords, 
       if (!okk) atomicOr(flags, kDevSingular);
       if (status) status[nodes[p]] = okk ? HSM_NODE_OK : HSM_NODE_SINGULAR;
       continue;
+    }
+    double xi[K][DIM];
+    double s2 = 0.0;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      double r2 = 0.0;
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) {
+        const double o = coords[k * N + id[j]] - cx[k];
+        xi[j][k] = o;
+        r2 += o * o;
+      }
+      s2 = fmax(s2, r2);
     }
     const double s = sqrt(s2);
     const double inv_s = 1.0 / s;
