@@ -587,8 +587,15 @@ __global__ void __launch_bounds__(256) k_rbf_fp32r(RbfArgs a) {
         const float df = xf[i * DIM + k] - xf[j * DIM + k];
         f2 = fmaf(df, df, f2);
       }
-      A64[e] = d2 * sqrt(d2);
-      const float vf = f2 * sqrtf(f2);
+      // r = sqrt(d2) by one step of the coupled (Goldschmidt) Newton-Raphson
+      // iteration g <- g + h (d2 - g^2), h ~ 1/(2g), from the single-precision
+      // root of the FP32 distance: relative error ~1e-12, which moves the
+      // refinement's fixed point by about cond * 1e-12
+      const float gf = sqrtf(f2);
+      double g = (double)gf;
+      g = fma((double)(0.5f / gf), fma(-g, g, d2), g);
+      A64[e] = d2 * g;
+      const float vf = f2 * gf;
       L32[i * ld32 + j] = vf;
       L32[j * ld32 + i] = vf;
     }
