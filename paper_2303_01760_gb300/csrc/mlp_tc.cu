@@ -8,8 +8,8 @@
 //   * warp 1 owns a 128 x 256 FP32 accumulator in tensor memory and issues
 //     tcgen05.mma (M = 128, N = layer width, K = 16 per instruction) with both
 //     operands K-major in shared memory, committing to mbarriers;
-//   * warps 4..11 drain the accumulator with tcgen05.ld (each warp its lane
-//     quarter, half of the columns), add the bias, apply GELU and write the
+//   * warps 4..19 drain the accumulator with tcgen05.ld (each warp its lane
+//     quarter, a quarter of the columns), add the bias, apply GELU and write the
 //     bf16 activations straight back into shared memory in the swizzled
 //     K-major layout the next layer's MMA reads; the last layer adds its bias
 //     and writes FP32 outputs to global memory.
@@ -24,8 +24,9 @@
 namespace hsm {
 namespace {
 
-constexpr int kThreads = 384;
+constexpr int kThreads = 640;
 constexpr int kTileRows = 128;
+constexpr int kEpiWarps = 16;  // warps 4..19: four per TMEM lane quarter
 constexpr int kStages = 3;
 constexpr int kMaxLayers = 4;
 constexpr int kActBytes = 4 * 16384;     // 128 rows x 256 bf16, four 64-column K slices
@@ -129,18 +130,23 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 }
 
 // GELU(z) = z Phi(z) = (z + |z| erf(|z| / sqrt 2)) / 2, with erf from
-// Abramowitz and Stegun 7.1.26: erf(x) = 1 - t (a1 + t (a2 + ... + t a5)) e^(-x^2),
-// t = 1 / (1 + p x), x >= 0, |error| <= 1.5e-7 -- far below the bf16 rounding
-// of the activations it feeds.
+// Abramowitz and Stegun 7.1.28: erf(x) = 1 - (1 + a1 x + ... + a6 x^6)^-16,
+// x >= 0, |error| <= 3e-7 -- far below the bf16 rounding of the activations
+// it feeds, and one reciprocal per element as the only special function.
 __device__ __forceinline__ float gelu(float z) {
   const float x = fabsf(z) * 0.70710678118654752f;
-  const float t = __fdividef(1.0f, fmaf(0.3275911f, x, 1.0f));
-  float poly = fmaf(t, 1.061405429f, -1.453152027f);
-  poly = fmaf(t, poly, 1.421413741f);
-  poly = fmaf(t, poly, -0.284496736f);
-  poly = fmaf(t, poly, 0.254829592f);
-  poly *= t;
-  const float e = fmaf(-poly, __expf(-x * x), 1.0f);
+  float p = fmaf(x, 0.0000430638f, 0.0002765672f);
+  p = fmaf(x, p, 0.0001520143f);
+  p = fmaf(x, p, 0.0092705272f);
+  p = fmaf(x, p, 0.0422820123f);
+  p = fmaf(x, p, 0.0705230784f);
+  p = fmaf(x, p, 1.0f);
+  float t = __fdividef(1.0f, p);  // (1 + ...)^-1, then ^16 by squaring
+  t *= t;
+  t *= t;
+  t *= t;
+  t *= t;
+  const float e = 1.0f - t;
   return 0.5f * fmaf(fabsf(z), e, z);
 }
 
@@ -173,7 +179,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_init(xfull, 1);
     mbar_init(xempty, 1);
     mbar_init(accfull, 1);
-    mbar_init(accempty, 8);
+    mbar_init(accempty, kEpiWarps);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -243,7 +249,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp >= 4) {
     // ---- epilogue: TMEM -> bias (+ GELU) -> shared activations or global outputs
-    const int q = warp & 3, half = (warp - 4) >> 2;
+    const int q = warp & 3, part = (warp - 4) >> 2;  // lane quarter, column quarter
     const int r = 32 * q + lane;
     const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16);
     uint32_t nfull = 0;
@@ -255,10 +261,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld needs the whole warp
         if (!ok) break;
         tc_fence_after();
-        const int N = a.dout[l], c0 = half * (N / 2);
+        const int N = a.dout[l], c0 = part * (N / 4);
         const float* bias = sbias + l * 256;
         const bool last = l == a.nl - 1;
-        for (int cc = c0; cc < c0 + N / 2; cc += 32) {
+        for (int cc = c0; cc < c0 + N / 4; cc += 32) {
           float v[32];
           tmem_ld32(trow + (uint32_t)cc, v);
           if (!last) {
