@@ -1,22 +1,26 @@
 // Fused forward pass of the learned-weight MLP on the 5th-generation tensor
-// cores.  One CTA per SM walks 128-row tiles; a tile goes through every layer
-// without leaving the SM:
+// cores.  One CTA per SM walks its 128-row tiles two at a time (two slots,
+// each with its own activation buffer and tensor-memory accumulator), and a
+// tile goes through every layer without leaving the SM:
 //
-//   * warp 0 streams the padded bf16 inputs of the tile and the weight
-//     matrices (64-column K slices, three stages) into shared memory with TMA
-//     (cp.async.bulk.tensor, 128-byte swizzle);
-//   * warp 1 owns a 128 x 256 FP32 accumulator in tensor memory and issues
-//     tcgen05.mma (M = 128, N = layer width, K = 16 per instruction) with both
-//     operands K-major in shared memory, committing to mbarriers;
-//   * warps 4..19 drain the accumulator with tcgen05.ld (each warp its lane
-//     quarter, a quarter of the columns), add the bias, apply GELU and write the
-//     bf16 activations straight back into shared memory in the swizzled
-//     K-major layout the next layer's MMA reads; the last layer adds its bias
-//     and writes FP32 outputs to global memory.
+//   * warp 0 streams each tile's padded bf16 inputs into its slot's
+//     activation buffer and the weight matrices (64-column K slices, two
+//     stages) into shared memory with TMA (cp.async.bulk.tensor, 128-byte
+//     swizzle);
+//   * warp 1 owns two 128 x 256 FP32 accumulators in tensor memory (512
+//     columns) and issues tcgen05.mma (M = 128, N = layer width, K = 16 per
+//     instruction) with both operands K-major in shared memory, alternating
+//     the slots layer by layer and committing to mbarriers;
+//   * warps 4..19 drain an accumulator with tcgen05.ld (each warp its lane
+//     quarter, a quarter of the columns), add the bias, apply GELU and write
+//     the bf16 activations straight back into the slot's buffer in the
+//     swizzled K-major layout the next layer's MMA reads; the last layer adds
+//     its bias and writes FP32 outputs to global memory.
 //
-// Only the inputs and outputs touch HBM.  Every wait on an mbarrier is
-// bounded: on expiry the kernel records an error flag, every role leaves its
-// loop and the tensor memory is released.
+// While the epilogue drains one slot the tensor cores run the other slot's
+// layer.  Only the inputs and outputs touch HBM.  Every wait on an mbarrier
+// is bounded: on expiry the kernel records an error flag, every role leaves
+// its loop and the tensor memory is released.
 #include <cuda.h>
 
 #include "mlp.cuh"
@@ -27,14 +31,14 @@ namespace {
 constexpr int kThreads = 640;
 constexpr int kTileRows = 128;
 constexpr int kEpiWarps = 16;  // warps 4..19: four per TMEM lane quarter
-constexpr int kStages = 3;
+constexpr int kStages = 2;
+constexpr int kSlots = 2;
 constexpr int kMaxLayers = 4;
-constexpr int kActBytes = 4 * 16384;     // 128 rows x 256 bf16, four 64-column K slices
-constexpr int kXBytes = 16384;           // 128 rows x 64 bf16
+constexpr int kActBytes = 4 * 16384;     // 128 rows x 256 bf16, four 64-column K slices; inputs land in slice 0
 constexpr int kWStageBytes = 256 * 128;  // up to 256 rows x 64 bf16
 constexpr int kBiasBytes = kMaxLayers * 256 * 4;
-constexpr int kSmemBytes = kActBytes + kXBytes + kStages * kWStageBytes + kBiasBytes + 256 + 1024;
-constexpr uint32_t kTmemCols = 256;
+constexpr int kSmemBytes = kSlots * kActBytes + kStages * kWStageBytes + kBiasBytes + 256 + 1024;
+constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kMaxSpins = 1u << 20;
 
 struct TcArgs {
@@ -156,18 +160,17 @@ __global__ void __launch_bounds__(kThreads, 1)
              const __grid_constant__ CUtensorMap tw3) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  uint8_t* act = base;
-  uint8_t* xb = act + kActBytes;
-  uint8_t* wb = xb + kXBytes;
+  uint8_t* act = base;                      // [slot][4 slices][128 rows][128 B]
+  uint8_t* wb = act + kSlots * kActBytes;   // [stage][<=256 rows][128 B]
   float* sbias = reinterpret_cast<float*>(wb + kStages * kWStageBytes);  // [layer][256]
   uint64_t* bars = reinterpret_cast<uint64_t*>(sbias + kMaxLayers * 256);
-  uint64_t* wfull = bars;
-  uint64_t* wempty = bars + kStages;
-  uint64_t* xfull = bars + 2 * kStages;
-  uint64_t* xempty = xfull + 1;
-  uint64_t* accfull = xfull + 2;
-  uint64_t* accempty = xfull + 3;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(xfull + 4);
+  uint64_t* wfull = bars;                   // [stage]
+  uint64_t* wempty = wfull + kStages;       // [stage]
+  uint64_t* xfull = wempty + kStages;       // [slot] inputs landed
+  uint64_t* actfree = xfull + kSlots;       // [slot] last layer's MMAs done: buffer free for new inputs
+  uint64_t* accfull = actfree + kSlots;     // [slot] a layer's MMAs done
+  uint64_t* accempty = accfull + kSlots;    // [slot] a layer's epilogue done
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accempty + kSlots);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -176,10 +179,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&wfull[s], 1);
       mbar_init(&wempty[s], 1);
     }
-    mbar_init(xfull, 1);
-    mbar_init(xempty, 1);
-    mbar_init(accfull, 1);
-    mbar_init(accempty, kEpiWarps);
+    for (int s = 0; s < kSlots; ++s) {
+      mbar_init(&xfull[s], 1);
+      mbar_init(&actfree[s], 1);
+      mbar_init(&accfull[s], 1);
+      mbar_init(&accempty[s], kEpiWarps);
+    }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -198,109 +203,133 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const int64_t ntiles = (a.rows + kTileRows - 1) / kTileRows;
+  const int64_t mine = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;  // tiles of this CTA
+  const int64_t npairs = (mine + 1) / 2;
   const CUtensorMap* tw[kMaxLayers] = {&tw0, &tw1, &tw2, &tw3};
+  // tile of slot s in pair p, or -1
+  auto tile_of = [&](int64_t p, int s) -> int64_t {
+    const int64_t j = 2 * p + s;
+    return j < mine ? blockIdx.x + j * (int64_t)gridDim.x : -1;
+  };
 
   if (warp == 0 && lane == 0) {
-    // ---- producer: inputs and weight slices
-    uint32_t seq = 0, xt = 0;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++xt) {
-      if (!mbar_wait(xempty, (xt & 1) ^ 1, abort_flag, a.err)) break;
-      mbar_expect_tx(xfull, kXBytes);
-      tma_load_2d(xb, &tx, 0, (int)(tile * kTileRows), xfull);
-      bool ok = true;
-      for (int l = 0; l < a.nl && ok; ++l)
-        for (int c = 0; c < a.din[l] / 64 && ok; ++c, ++seq) {
-          const uint32_t s = seq % kStages, u = seq / kStages;
-          ok = mbar_wait(&wempty[s], (u & 1) ^ 1, abort_flag, a.err);
-          if (!ok) break;
-          mbar_expect_tx(&wfull[s], (uint32_t)a.dout[l] * 128u);
-          tma_load_2d(wb + s * kWStageBytes, tw[l], c * 64, 0, &wfull[s]);
-        }
-      if (!ok) break;
-    }
-  } else if (warp == 1 && lane == 0) {
-    // ---- MMA issuer
-    uint32_t seq = 0, xt = 0, nacc = 0;
+    // ---- producer: each slot's inputs, then the weight slices in MMA order
+    uint32_t seq = 0, nx[kSlots] = {0, 0};
     bool ok = true;
-    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++xt) {
-      for (int l = 0; l < a.nl && ok; ++l) {
-        ok = mbar_wait(accempty, (nacc & 1) ^ 1, abort_flag, a.err);
-        ++nacc;
-        if (ok && l == 0) ok = mbar_wait(xfull, xt & 1, abort_flag, a.err);
+    for (int64_t p = 0; p < npairs && ok; ++p) {
+      for (int s = 0; s < kSlots && ok; ++s) {
+        const int64_t tile = tile_of(p, s);
+        if (tile < 0) continue;
+        ok = mbar_wait(&actfree[s], (nx[s] & 1) ^ 1, abort_flag, a.err);
         if (!ok) break;
-        tc_fence_after();
-        const uint32_t idesc = idesc_bf16(kTileRows, a.dout[l]);
-        for (int c = 0; c < a.din[l] / 64; ++c, ++seq) {
-          const uint32_t s = seq % kStages, u = seq / kStages;
-          ok = mbar_wait(&wfull[s], u & 1, abort_flag, a.err);
-          if (!ok) break;
-          tc_fence_after();
-          const uint64_t ad = sw128_desc(saddr(l == 0 ? xb : act + c * 16384));
-          const uint64_t bd = sw128_desc(saddr(wb + s * kWStageBytes));
-#pragma unroll
-          for (int kk = 0; kk < 4; ++kk)  // K = 16 per MMA: 32 bytes along the swizzled row
-            umma(tmem, ad + 2 * kk, bd + 2 * kk, idesc, (c | kk) != 0 ? 1u : 0u);
-          umma_commit(&wempty[s]);
-        }
-        if (!ok) break;
-        umma_commit(accfull);
-        if (l == 0) umma_commit(xempty);
+        ++nx[s];
+        mbar_expect_tx(&xfull[s], 16384u);
+        tma_load_2d(act + s * kActBytes, &tx, 0, (int)(tile * kTileRows), &xfull[s]);
       }
-    }
-  } else if (warp >= 4) {
-    // ---- epilogue: TMEM -> bias (+ GELU) -> shared activations or global outputs
-    const int q = warp & 3, part = (warp - 4) >> 2;  // lane quarter, column quarter
-    const int r = 32 * q + lane;
-    const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16);
-    uint32_t nfull = 0;
-    bool ok = true;
-    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-      for (int l = 0; l < a.nl; ++l) {
-        ok = mbar_wait(accfull, nfull & 1, abort_flag, a.err);
-        ++nfull;
-        ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld needs the whole warp
-        if (!ok) break;
-        tc_fence_after();
-        const int N = a.dout[l], c0 = part * (N / 4);
-        const float* bias = sbias + l * 256;
-        const bool last = l == a.nl - 1;
-        for (int cc = c0; cc < c0 + N / 4; cc += 32) {
-          float v[32];
-          tmem_ld32(trow + (uint32_t)cc, v);
-          if (!last) {
-#pragma unroll
-            for (int j = 0; j < 32; j += 8) {
-              uint32_t pk[4];
-#pragma unroll
-              for (int t = 0; t < 4; ++t) {
-                const float g0 = gelu(v[j + 2 * t] + bias[cc + j + 2 * t]);
-                const float g1 = gelu(v[j + 2 * t + 1] + bias[cc + j + 2 * t + 1]);
-                const __nv_bfloat162 h2 = __floats2bfloat162_rn(g0, g1);
-                pk[t] = *reinterpret_cast<const uint32_t*>(&h2);
-              }
-              const int k = cc + j;  // the next layer's K index
-              const uint32_t dst = saddr(act + (k >> 6) * 16384 + r * 128 + ((((k & 63) >> 3) ^ (r & 7)) << 4));
-              asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(pk[0]), "r"(pk[1]), "r"(pk[2]),
-                           "r"(pk[3])
-                           : "memory");
-            }
-          } else {
-            const int64_t row = tile * kTileRows + r;
-            if (row < a.rows) {
-              float* y = a.Y + row * (int64_t)a.ldy;
-#pragma unroll
-              for (int j = 0; j < 32; ++j)
-                if (cc + j < a.ncols) y[cc + j] = v[j] + bias[cc + j];
-            }
+      for (int l = 0; l < a.nl && ok; ++l)
+        for (int s = 0; s < kSlots && ok; ++s) {
+          if (tile_of(p, s) < 0) continue;
+          for (int c = 0; c < a.din[l] / 64 && ok; ++c, ++seq) {
+            const uint32_t st = seq % kStages, u = seq / kStages;
+            ok = mbar_wait(&wempty[st], (u & 1) ^ 1, abort_flag, a.err);
+            if (!ok) break;
+            mbar_expect_tx(&wfull[st], (uint32_t)a.dout[l] * 128u);
+            tma_load_2d(wb + st * kWStageBytes, tw[l], c * 64, 0, &wfull[st]);
           }
         }
-        tc_fence_before();
-        // the activations written here are read next by the tensor cores (async proxy)
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncwarp();
-        if (lane == 0) mbar_arrive(accempty);
-      }
     }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer: layer by layer, alternating the slots
+    uint32_t seq = 0, nx[kSlots] = {0, 0}, njob[kSlots] = {0, 0};
+    bool ok = true;
+    for (int64_t p = 0; p < npairs && ok; ++p)
+      for (int l = 0; l < a.nl && ok; ++l)
+        for (int s = 0; s < kSlots && ok; ++s) {
+          if (tile_of(p, s) < 0) continue;
+          ok = mbar_wait(&accempty[s], (njob[s] & 1) ^ 1, abort_flag, a.err);
+          ++njob[s];
+          if (ok && l == 0) {
+            ok = mbar_wait(&xfull[s], nx[s] & 1, abort_flag, a.err);
+            ++nx[s];
+          }
+          if (!ok) break;
+          tc_fence_after();
+          const uint32_t idesc = idesc_bf16(kTileRows, a.dout[l]);
+          const uint32_t d = tmem + (uint32_t)(s * 256);
+          for (int c = 0; c < a.din[l] / 64; ++c, ++seq) {
+            const uint32_t st = seq % kStages, u = seq / kStages;
+            ok = mbar_wait(&wfull[st], u & 1, abort_flag, a.err);
+            if (!ok) break;
+            tc_fence_after();
+            const uint64_t ad = sw128_desc(saddr(act + s * kActBytes + c * 16384));
+            const uint64_t bd = sw128_desc(saddr(wb + st * kWStageBytes));
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)  // K = 16 per MMA: 32 bytes along the swizzled row
+              umma(d, ad + 2 * kk, bd + 2 * kk, idesc, (c | kk) != 0 ? 1u : 0u);
+            umma_commit(&wempty[st]);
+          }
+          if (!ok) break;
+          umma_commit(&accfull[s]);
+          if (l == a.nl - 1) umma_commit(&actfree[s]);
+        }
+  } else if (warp >= 4) {
+    // ---- epilogue: TMEM -> bias (+ GELU) -> the slot's activations or global outputs
+    const int q = warp & 3, part = (warp - 4) >> 2;  // lane quarter, column quarter
+    const int r = 32 * q + lane;
+    uint32_t njob[kSlots] = {0, 0};
+    bool ok = true;
+    for (int64_t p = 0; p < npairs && ok; ++p)
+      for (int l = 0; l < a.nl && ok; ++l)
+        for (int s = 0; s < kSlots && ok; ++s) {
+          const int64_t tile = tile_of(p, s);
+          if (tile < 0) continue;
+          ok = mbar_wait(&accfull[s], njob[s] & 1, abort_flag, a.err);
+          ++njob[s];
+          ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld needs the whole warp
+          if (!ok) break;
+          tc_fence_after();
+          const uint32_t trow = tmem + (uint32_t)(s * 256) + ((uint32_t)(32 * q) << 16);
+          uint8_t* sact = act + s * kActBytes;
+          const int N = a.dout[l], c0 = part * (N / 4);
+          const float* bias = sbias + l * 256;
+          const bool last = l == a.nl - 1;
+          for (int cc = c0; cc < c0 + N / 4; cc += 32) {
+            float v[32];
+            tmem_ld32(trow + (uint32_t)cc, v);
+            if (!last) {
+#pragma unroll
+              for (int j = 0; j < 32; j += 8) {
+                uint32_t pk[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                  const float g0 = gelu(v[j + 2 * t] + bias[cc + j + 2 * t]);
+                  const float g1 = gelu(v[j + 2 * t + 1] + bias[cc + j + 2 * t + 1]);
+                  const __nv_bfloat162 h2 = __floats2bfloat162_rn(g0, g1);
+                  pk[t] = *reinterpret_cast<const uint32_t*>(&h2);
+                }
+                const int k = cc + j;  // the next layer's K index
+                const uint32_t dst =
+                    saddr(sact + (k >> 6) * 16384 + r * 128 + ((((k & 63) >> 3) ^ (r & 7)) << 4));
+                asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(pk[0]), "r"(pk[1]),
+                             "r"(pk[2]), "r"(pk[3])
+                             : "memory");
+              }
+            } else {
+              const int64_t row = tile * kTileRows + r;
+              if (row < a.rows) {
+                float* y = a.Y + row * (int64_t)a.ldy;
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                  if (cc + j < a.ncols) y[cc + j] = v[j] + bias[cc + j];
+              }
+            }
+          }
+          tc_fence_before();
+          // the activations written here are read next by the tensor cores (async proxy)
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&accempty[s]);
+        }
   }
   tc_fence_before();
   __syncthreads();
