@@ -152,6 +152,26 @@ def cpu_baseline(n_sample=20000):
 
 # ---------------------------------------------------------------------------
 # GPU arm
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# k_rbf_fp64<2, 3, 8> on the hybrid workload, from an ncu capture of the
+# kernel as it stands; the 8.7 MB of weights it writes stay in L2 during the
+# launch.  Set to None whenever that kernel changes until it is re-captured.
+RBF64_TRAFFIC_BYTES = 2461696 + 256
+
+
+def aggregate_ranks(times, n_nodes, dist, device):
+    """Replicas on several ranks: the step times are the maximum over ranks
+    (the job is as slow as its slowest replica) and the nodes processed per
+    step are summed over ranks (each rank runs its own seeded node set)."""
+    import torch
+
+    t = torch.tensor([float(x) for x in times], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    n = torch.tensor([float(n_nodes)], dtype=torch.float64, device=device)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return [float(x) for x in t], float(n[0])
+
+
 # ---------------------------------------------------------------------------
 def run_gpu(args):
     import numpy as np
@@ -242,10 +262,9 @@ def run_gpu(args):
     q_h, q_a = hyb.query(), allr.query()
     t_h = float(np.mean(ms_h))
     t_a = float(np.mean(ms_a))
+    n_total = float(ns.N)
     if world > 1:
-        t = torch.tensor([t_h, t_a], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_h, t_a = float(t[0]), float(t[1])
+        (t_h, t_a), n_total = aggregate_ranks([t_h, t_a], ns.N, dist, dev)
 
     # roofline of the dominant kernel: the FP64 RBF-FD weight solve
     K = 12 + 6
@@ -266,7 +285,7 @@ def run_gpu(args):
 
     res = None
     if rank == 0:
-        value = world * ns.N / (t_h * 1e-3)
+        value = n_total / (t_h * 1e-3)
         res = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_h, "higher_is_better": True, "scaling": "weak",
@@ -276,9 +295,9 @@ def run_gpu(args):
             "gpu_launches": int(launches_h // max(args.steps, 1)) * args.steps,
             "roofline": {"bound": "alu", "kernel": "k_rbf_fp64 (RBF-FD FP64 LU solve, hybrid set)",
                          "achieved": ach_h, "peak": peak, "unit": "GFLOP/s", "frac": ach_h / peak,
-                         "traffic": None,
+                         "traffic": RBF64_TRAFFIC_BYTES,
                          "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz"},
-            "all_rbffd": {"value": world * ns.N / (t_a * 1e-3), "ms_per_step": t_a,
+            "all_rbffd": {"value": n_total / (t_a * 1e-3), "ms_per_step": t_a,
                           "hybrid_over_all_rbffd": t_a / t_h,
                           "roofline_frac_rbf_kernel": ach_a / peak,
                           "rbf_kernel_gflops": ach_a},
