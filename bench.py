@@ -47,10 +47,20 @@ def workload_desc(ns):
 # ---------------------------------------------------------------------------
 # helpers
 # ---------------------------------------------------------------------------
-def rbf_flops(K, nops):
-    """Algorithmic FP64 flops of one RBF-FD system: LU 2/3 K^3 plus forward and
-    back substitution 2 K^2 per right-hand side."""
-    return 2.0 / 3.0 * K ** 3 + 2.0 * nops * K ** 2
+def rbf_flops(n, m, nops):
+    """Algorithmic FP64 flops of one RBF-FD system (n nodes, m monomials, nops
+    right-hand sides) solved by the null-space method of the FP64 kernel, r = n - m:
+    LU of P with row pivoting, U^T and L1^T triangular solves, [A Z | b],
+    [Z^T A Z | Z^T b], the r x r LU with its substitutions, and w = w_t - X y.
+    Assembly (pair roots, monomials) is not counted."""
+    r = n - m
+    lu_p = sum((n - k - 1) * (1 + 2 * (m - k - 1)) for k in range(m))
+    tri = nops * m * m + (r + nops) * m * (m - 1)
+    bz = 2 * m * n * (r + nops)
+    sz = 2 * m * r * (r + nops)
+    lu_s = 2.0 / 3.0 * r ** 3 + 2.0 * nops * r ** 2
+    out = 2 * m * r * nops
+    return lu_p + tri + bz + sz + lu_s + out
 
 
 class Clocks:
@@ -154,9 +164,9 @@ def cpu_baseline(n_sample=20000):
 # GPU arm
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # k_rbf_fp64<2, 3, 8> on the hybrid workload, from an ncu capture of the
-# kernel as it stands; the 8.7 MB of weights it writes stay in L2 during the
-# launch.  Set to None whenever that kernel changes until it is re-captured.
-RBF64_TRAFFIC_BYTES = 2461696 + 256
+# kernel as it stands.  Set to None whenever that kernel changes until it is
+# re-captured.
+RBF64_TRAFFIC_BYTES = None
 
 
 def aggregate_ranks(times, n_nodes, dist, device):
@@ -267,13 +277,12 @@ def run_gpu(args):
         (t_h, t_a), n_total = aggregate_ranks([t_h, t_a], ns.N, dist, dev)
 
     # roofline of the dominant kernel: the FP64 RBF-FD weight solve
-    K = 12 + 6
     rbf_ms = float(np.mean([p[2] for p in ph_h]))
     rbf_ms_all = float(np.mean([p[2] for p in ph_a]))
     n_rbf_h = ns.N - q_h["n_mon"]
     n_rbf_a = ns.N - q_a["n_mon"]
-    ach_h = rbf_flops(K, 3) * n_rbf_h / (rbf_ms * 1e-3) / 1e9
-    ach_a = rbf_flops(K, 3) * n_rbf_a / (rbf_ms_all * 1e-3) / 1e9
+    ach_h = rbf_flops(12, 6, 3) * n_rbf_h / (rbf_ms * 1e-3) / 1e9
+    ach_a = rbf_flops(12, 6, 3) * n_rbf_a / (rbf_ms_all * 1e-3) / 1e9
     peak = FP64_PEAK_DERIVED / 1e9
 
     # end to end through the C ABI from pinned host buffers
@@ -293,7 +302,7 @@ def run_gpu(args):
             "config": workload_desc(ns),
             "e2e": e2e,
             "gpu_launches": int(launches_h // max(args.steps, 1)) * args.steps,
-            "roofline": {"bound": "alu", "kernel": "k_rbf_fp64 (RBF-FD FP64 LU solve, hybrid set)",
+            "roofline": {"bound": "alu", "kernel": "k_rbf_fp64 (RBF-FD FP64 null-space solve, hybrid set)",
                          "achieved": ach_h, "peak": peak, "unit": "GFLOP/s", "frac": ach_h / peak,
                          "traffic": RBF64_TRAFFIC_BYTES,
                          "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz"},

@@ -65,14 +65,23 @@ __device__ __forceinline__ unsigned long long shfl_xor_u64(unsigned mask, unsign
   return (unsigned long long)__shfl_xor_sync(mask, (long long)v, o, w);
 }
 
-// Per-system shared memory of the FP64 kernel (in doubles):
-//   M      K x ld     matrix, LU factor and right-hand sides
-//   xi     n x DIM    scaled offsets
-//   rc     n          |xi_j|, the scaled distance of node j from the centre
-//   inv    K          reciprocal pivots
-template <int DIM, int NOPS, bool R32>
-__host__ __device__ constexpr size_t sys_doubles(int K, int ld, int n) {
-  return (size_t)K * ld + (size_t)n * (DIM + 1) + K;
+// Per-system shared memory of the FP64 kernel (in doubles), m monomials,
+// r = n - m, ldA = n | 1, ldB = (r + NOPS) | 1:
+//   xi    n x DIM          scaled offsets
+//   rc    n                |xi_j|
+//   Ap    max(n ldA, r ldB) A in pivot order; later [S | Z^T b], then y
+//   Pw    (n + NOPS) x m   LU of P; rows m..n-1 become X, rows n.. the
+//                          monomial right-hand sides, then w_t
+//   Bm    n x ldB          [A Z | f - A w_t]
+//   inv   n                reciprocal pivots of P (m), then of S (r)
+//   perm  n ints           stencil position of each pivot-order row
+__host__ __device__ constexpr size_t ns_apsize(int nops, int n, int m) {
+  return (size_t)n * (n | 1) > (size_t)(n - m) * ((n - m + nops) | 1) ? (size_t)n * (n | 1)
+                                                                       : (size_t)(n - m) * ((n - m + nops) | 1);
+}
+__host__ __device__ constexpr size_t sys_doubles(int dim, int nops, int n, int m) {
+  return (size_t)n * (dim + 1) + ns_apsize(nops, n, m) + (size_t)(n + nops) * m + (size_t)n * ((n - m + nops) | 1) +
+         n + (n + 1) / 2;
 }
 
 // Per-system shared memory of the FP32 + FP64-refinement kernel: the FP64
@@ -101,14 +110,39 @@ __device__ __forceinline__ double pow2_inv_scale(unsigned long long d2bits) {
   return __longlong_as_double((long long)(1023 - t) << 52);
 }
 
+// Seeds for the FP64 iterations below are formed in single precision; the
+// conversions between the formats are done on the integer pipes, which keeps
+// them off the FP64 pipe, the bound of the weight kernels.
+// f32_trunc: x truncated to single precision (relative error < 2^-23), for x
+// whose binary exponent lies in single precision's normal range.
+__device__ __forceinline__ float f32_trunc(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x);
+  const unsigned lo = (unsigned)__double2loint(x);
+  const unsigned mag = (((hi & 0x7fffffffu) - (896u << 20)) << 3) | (lo >> 29);
+  return __uint_as_float(mag | (hi & 0x80000000u));
+}
+// f64_of: exact widening of a normal single-precision value.
+__device__ __forceinline__ double f64_of(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned hi = (((b & 0x7fffffffu) >> 3) + (896u << 20)) | (b & 0x80000000u);
+  return __hiloint2double((int)hi, (int)(b << 29));
+}
+// Biased binary exponent of x.
+__device__ __forceinline__ unsigned f64_exp(double x) { return ((unsigned)__double2hiint(x) >> 20) & 0x7ffu; }
+// x > 0 with its binary exponent within 120 of zero (the sign bit makes the
+// shifted high word exceed the range), tested on the bits.
+__device__ __forceinline__ bool f64_pos_in_f32(double x) {
+  return ((unsigned)__double2hiint(x) >> 20) - (1023u - 120u) <= 240u;
+}
+
 // Reciprocal by the Newton-Raphson iteration y <- y + y (1 - x y), started
-// from the correctly rounded single-precision reciprocal: two steps take the
-// seed's 2^-24 relative error below double rounding.  Arguments whose
-// exponent lies outside single range take the division.
+// from the single-precision reciprocal of x truncated to single precision:
+// two steps take the seed's 2^-22 relative error below double rounding.
+// Arguments whose exponent lies outside single range take the division.
 __device__ __forceinline__ double recip(double x) {
-  const unsigned ex = (unsigned)((unsigned long long)__double_as_longlong(x) >> 52) & 0x7ffu;
+  const unsigned ex = f64_exp(x);
   if (ex < 1023u - 120u || ex > 1023u + 120u) return 1.0 / x;
-  double y = (double)__frcp_rn((float)x);
+  double y = f64_of(__frcp_rn(f32_trunc(x)));
   double e = fma(-x, y, 1.0);
   y = fma(y, e, y);
   e = fma(-x, y, 1.0);
@@ -130,85 +164,73 @@ __device__ __forceinline__ bool pivot_ok<float>(float piv) {
   return b > 0u && b < 0x7f800000u;
 }
 
-// Assembles [A P | L phi; P^T 0 | L p] into Mt (row stride ld) for the scaled
-// offsets xi = (x - x_c) * inv_s, inv_s a power of two (pow2_inv_scale).
-template <int DIM, int NOPS, int LANES, typename T>
-__device__ __forceinline__ void assemble(const RbfArgs& a, int64_t pos, int lane, unsigned mask, double* xi,
-                                         double* rc, T* Mt, int ldt, double* M64, double& inv_s_out, bool& ok) {
-  const int n = a.n, K = a.K, nm = a.n_mono;
-  const int32_t c = a.nodes[pos];
-  unsigned long long b = 0ull;
-  for (int j = lane; j < n; j += LANES) {
-    const int32_t id = a.idx[(int64_t)j * a.G + pos];
-    double r2 = 0.0;
+// sqrt(x) for x > 0 by two steps of Goldschmidt's coupled iteration
+//   r = 1/2 - g h,  g <- g + g r  (-> sqrt x),  h <- h + h r  (-> 1/(2 sqrt x)),
+// started from the single-precision reciprocal square root (g = x y, h = y/2).
+// Each step squares the relative error: ~2^-22 -> ~2^-43 -> below double
+// rounding.  Zero, and arguments outside single precision's normal range,
+// take the library square root.
+__device__ __forceinline__ double sqrt_gs(double x) {
+  if (!f64_pos_in_f32(x)) return sqrt(x);
+  const double y = f64_of(rsqrtf(f32_trunc(x)));
+  double g = x * y, h = 0.5 * y;
+  double r = fma(-g, h, 0.5);
+  g = fma(g, r, g);
+  h = fma(h, r, h);
+  r = fma(-g, h, 0.5);
+  return fma(g, r, g);
+}
+
+// sqrt(x) by one Newton-Raphson step g + (x - g^2) / (2g) from the
+// single-precision root g of x truncated to single precision.  The relative
+// error is the seed's (below 2^-23) squared over two plus the seed's times
+// that of the single-precision 1/(2g) (2^-24): below 1.5e-14.  Zero, and
+// arguments outside single precision's normal range, take the library root.
+__device__ __forceinline__ double sqrt_nr1(double x) {
+  if (!f64_pos_in_f32(x)) return sqrt(x);
+  const float gf = sqrtf(f32_trunc(x));
+  const double g = f64_of(gf);
+  return fma(f64_of(0.5f * __frcp_rn(gf)), fma(-g, g, x), g);
+}
+
+// Monomial q of the basis is monomial par[q] times coordinate cor[q] (the
+// exponent vector minus one unit in its first non-zero coordinate), so each
+// monomial costs one product.  par[q] = -1 for the constant and -2 where the
+// basis lacks that lower monomial (such entries take the exponent loop).
+// Filled by the block's first n_mono threads; the caller synchronises.
+__device__ __forceinline__ void mono_parents(const int8_t* ex, int nm, int dim, int8_t* par, int8_t* cor) {
+  const int q = threadIdx.x;
+  if (q >= nm) return;
+  int k0 = -1;
+  for (int k = 0; k < dim; ++k)
+    if (k0 < 0 && ex[q * dim + k] > 0) k0 = k;
+  int pq = -1;
+  if (k0 >= 0) {
+    pq = -2;
+    for (int p = 0; p < nm && pq == -2; ++p) {
+      bool eq = true;
+      for (int k = 0; k < dim; ++k) eq = eq && ex[p * dim + k] == ex[q * dim + k] - (k == k0 ? 1 : 0);
+      if (eq) pq = p;
+    }
+  }
+  par[q] = (int8_t)pq;
+  cor[q] = (int8_t)(k0 < 0 ? 0 : k0);
+}
+
+// Monomials of node j into row[0..nm) (row[q] = p_q(xi_j)), by the parent
+// table: linear terms are copies, every higher one is one multiplication.
+template <int DIM, typename T>
+__device__ __forceinline__ T mono_value(const T* row, const T* x, int q, const int8_t* par, const int8_t* cor,
+                                        const int8_t* ex) {
+  const int pq = par[q];
+  if (pq == -1) return T(1);
+  if (pq == 0) return x[cor[q]];
+  if (pq > 0) return row[pq] * x[cor[q]];
+  T v = T(1);
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) {
-      const double o = a.coords[k * a.N + id] - a.coords[k * a.N + c];
-      xi[j * DIM + k] = o;
-      r2 = fma(o, o, r2);
-    }
-    rc[j] = r2;
-    // non-negative doubles order like their bit patterns
-    const unsigned long long rb = (unsigned long long)__double_as_longlong(r2);
-    b = rb > b ? rb : b;
-  }
-#pragma unroll
-  for (int o = LANES / 2; o > 0; o >>= 1) {
-    unsigned long long t = shfl_xor_u64(mask, b, o, LANES);
-    b = t > b ? t : b;
-  }
-  const double inv_s = pow2_inv_scale(b);
-  inv_s_out = inv_s;
-  ok = b != 0ull && b < 0x7ff0000000000000ull;
-  __syncwarp(mask);
-  for (int e = lane; e < n * DIM; e += LANES) xi[e] *= inv_s;
-  for (int e = lane; e < n; e += LANES) rc[e] = sqrt(rc[e] * (inv_s * inv_s));
-  __syncwarp(mask);
-  // A block (zero diagonal, symmetric pairs)
-  for (int e = lane; e < n; e += LANES) {
-    Mt[e * ldt + e] = T(0);
-    if (M64) M64[e * K + e] = 0.0;
-  }
-  const int npairs = n * (n - 1) / 2;
-  for (int e = lane; e < npairs; e += LANES) {
-    const uint16_t pr = a.pairs[e];
-    const int i = pr >> 8, j = pr & 0xff;
-    double d2 = 0.0;
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) {
-      double d = xi[i * DIM + k] - xi[j * DIM + k];
-      d2 += d * d;
-    }
-    const double v = d2 * sqrt(d2);
-    Mt[i * ldt + j] = T(v);
-    Mt[j * ldt + i] = T(v);
-    if (M64) {
-      M64[i * K + j] = v;
-      M64[j * K + i] = v;
-    }
-  }
-  // P and P^T blocks
-  for (int e = lane; e < n * nm; e += LANES) {
-    const int i = e / nm, q = e - (e / nm) * nm;
-    double v = 1.0;
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) {
-      const int ex = a.mono_exp[q * DIM + k];
-      for (int t = 0; t < ex; ++t) v *= xi[i * DIM + k];
-    }
-    Mt[i * ldt + n + q] = T(v);
-    Mt[(n + q) * ldt + i] = T(v);
-    if (M64) {
-      M64[i * K + n + q] = v;
-      M64[(n + q) * K + i] = v;
-    }
-  }
-  for (int e = lane; e < nm * nm; e += LANES) {
-    const int i = e / nm, q = e - (e / nm) * nm;
-    Mt[(n + i) * ldt + n + q] = T(0);
-    if (M64) M64[(n + i) * K + n + q] = 0.0;
-  }
-  __syncwarp(mask);
+  for (int k = 0; k < DIM; ++k)
+    for (int t = 0; t < ex[q * DIM + k]; ++t) v *= x[k];
+  return v;
 }
 
 // RHS value of operator o for stencil node e (PHS part); r = |xi_e|.
@@ -468,42 +490,229 @@ struct FixedLU {
   }
 };
 
+// Calls f(i, j) for every (i, j) of [0, R) x [0, C), dealt to the lanes in
+// row-major order so that every lane of each instruction has work.
+template <int LANES, typename F>
+__device__ __forceinline__ void flat2(int R, int C, int lane, F&& f) {
+  const int total = R * C;
+  if (total <= 0) return;
+  int i = lane / C, j = lane - (lane / C) * C;
+  const int dq = LANES / C, dr = LANES - (LANES / C) * C;
+  for (int e = lane; e < total; e += LANES) {
+    f(i, j);
+    j += dr;
+    i += dq;
+    if (j >= C) {
+      j -= C;
+      ++i;
+    }
+  }
+}
+
+// FP64 RBF-FD weights of Eq. 1 by the null-space method for the saddle-point
+// system [A P; P^T 0] [w; lambda] = [f; g] (Section 2.1).  Only w is needed:
+//   1. P = Pi^T [L1; L2] U by Gaussian elimination with row pivoting (Pi the
+//      row order, L1 unit lower m x m, L2 r x m, U upper);
+//   2. every w with P^T w = g is w = Pi^T ([w_t; 0] + Z y), where
+//      Z = [-X; I], X = L1^-T L2^T spans the null space of P^T and
+//      w_t = L1^-T U^-T g;
+//   3. (Z^T A Z) y = Z^T (f - A w_t): an r x r system, r = n - m.  r^3 is
+//      conditionally positive definite of order 2 and the monomials include
+//      all linear ones, so Z^T A Z is positive definite.
+// In exact arithmetic this is the solution of the augmented system; it takes
+// about half the FP64 operations of an LU of the (n + m) x (n + m) matrix.
 template <int DIM, int NOPS, int LANES>
 __global__ void __launch_bounds__(256) k_rbf_fp64(RbfArgs a) {
   extern __shared__ double smem[];
   const int SYS = blockDim.x / LANES;
   const int sub = threadIdx.x / LANES, lane = threadIdx.x % LANES;
   const unsigned mask = LANES == 32 ? 0xffffffffu : (((1u << LANES) - 1u) << ((threadIdx.x & 31) / LANES * LANES));
-  const int K = a.K, ld = a.ld, n = a.n;
-  double* base = smem + (size_t)sub * sys_doubles<DIM, NOPS, false>(K, ld, n);
-  double* M = base;
-  double* xi = M + (size_t)K * ld;
+  const int n = a.n, m = a.n_mono, r = n - m, rc_ = r + NOPS;
+  const int ldA = n | 1, ldB = rc_ | 1;
+  double* xi = smem + (size_t)sub * sys_doubles(DIM, NOPS, n, m);
   double* rc = xi + n * DIM;
-  double* inv = rc + n;
+  double* Ap = rc + n;
+  double* Sm = Ap;  // Ap is dead once Bm is formed
+  double* Pw = Ap + ns_apsize(NOPS, n, m);
+  double* Bm = Pw + (n + NOPS) * m;
+  double* inv = Bm + n * ldB;
+  int* perm = reinterpret_cast<int*>(inv + n);
+  __shared__ int8_t par[kMaxMonomials], cor[kMaxMonomials];
+  mono_parents(a.mono_exp, m, DIM, par, cor);
+  __syncthreads();
   for (int64_t t = (int64_t)blockIdx.x * SYS + sub; t < a.count; t += (int64_t)gridDim.x * SYS) {
     const int64_t pos = a.list ? a.list[t] : t;
-    double inv_s;
-    bool ok;
-    assemble<DIM, NOPS, LANES, double>(a, pos, lane, mask, xi, rc, M, ld, nullptr, inv_s, ok);
-    for (int e = lane; e < n * NOPS; e += LANES) {
-      const int i = e / NOPS, o = e - (e / NOPS) * NOPS;
-      M[i * ld + K + o] = rhs_phi<DIM>(xi, rc, i, a.ops.kind[o]);
+    const int32_t c = a.nodes[pos];
+    // ---- offsets, the power-of-two scale, |xi| and the monomial rows of P
+    unsigned long long bmax = 0ull;
+    for (int j = lane; j < n; j += LANES) {
+      const int32_t id = a.idx[(int64_t)j * a.G + pos];
+      double r2 = 0.0;
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) {
+        const double o = a.coords[k * a.N + id] - a.coords[k * a.N + c];
+        xi[j * DIM + k] = o;
+        r2 = fma(o, o, r2);
+      }
+      rc[j] = r2;
+      // non-negative doubles order like their bit patterns
+      const unsigned long long rb = (unsigned long long)__double_as_longlong(r2);
+      bmax = rb > bmax ? rb : bmax;
     }
-    for (int e = lane; e < a.n_mono * NOPS; e += LANES) {
-      const int q = e / NOPS, o = e - (e / NOPS) * NOPS;
-      M[(n + q) * ld + K + o] = rhs_mono<DIM>(a.mono_exp, q, a.ops.kind[o]);
+#pragma unroll
+    for (int o = LANES / 2; o > 0; o >>= 1) {
+      const unsigned long long u = shfl_xor_u64(mask, bmax, o, LANES);
+      bmax = u > bmax ? u : bmax;
+    }
+    const double inv_s = pow2_inv_scale(bmax);
+    bool ok = bmax != 0ull && bmax < 0x7ff0000000000000ull;
+    __syncwarp(mask);
+    for (int j = lane; j < n; j += LANES) {
+      double* x = xi + j * DIM;
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) x[k] *= inv_s;
+      rc[j] = sqrt_gs(rc[j] * (inv_s * inv_s));
+      double* row = Pw + j * m;
+      for (int q = 0; q < m; ++q) row[q] = mono_value<DIM, double>(row, x, q, par, cor, a.mono_exp);
+      perm[j] = j;
     }
     __syncwarp(mask);
-    // the flat (row, column) update of lu_solve fills every lane of each FP64
-    // instruction, which matters more here than its index arithmetic
-    ok = lu_solve<NOPS, LANES, double>(M, ld, K, inv, lane, mask, true) && ok;
-    for (int e = lane; e < n * NOPS; e += LANES) {
-      const int j = e / NOPS, o = e - (e / NOPS) * NOPS;
-      const double sc = a.ops.kind[o] == 3 ? inv_s * inv_s : inv_s;
-      const double v = M[j * ld + K + o] * sc;
-      const bool fin = ((unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull) < 0x7ff0000000000000ull;
-      a.w[((int64_t)o * n + j) * a.G + pos] = ok && fin ? v : 0.0;
+    // ---- 1. P = Pi^T [L1; L2] U, whole rows swapped, multipliers in place
+    for (int k = 0; k < m && ok; ++k) {
+      unsigned long long best = 0ull;
+      int brow = n;
+      for (int i = k + lane; i < n; i += LANES) {
+        const unsigned long long v = AbsBits<double>::get(Pw[i * m + k]);
+        if (v > best || (v == best && i < brow)) {
+          best = v;
+          brow = i;
+        }
+      }
+#pragma unroll
+      for (int o = LANES / 2; o > 0; o >>= 1) {
+        const unsigned long long ob = shfl_xor_u64(mask, best, o, LANES);
+        const int orow = __shfl_xor_sync(mask, brow, o, LANES);
+        if (ob > best || (ob == best && orow < brow)) {
+          best = ob;
+          brow = orow;
+        }
+      }
+      if (brow != k && brow < n) {
+        for (int j = lane; j < m; j += LANES) {
+          const double tmp = Pw[k * m + j];
+          Pw[k * m + j] = Pw[brow * m + j];
+          Pw[brow * m + j] = tmp;
+        }
+        if (lane == 0) {
+          const int tp = perm[k];
+          perm[k] = perm[brow];
+          perm[brow] = tp;
+        }
+      }
+      __syncwarp(mask);
+      const double piv = Pw[k * m + k];
+      // a pivot below the threshold: the stencil is not unisolvent for the
+      // monomials to working precision
+      if (!pivot_ok<double>(piv)) {
+        ok = false;
+        break;
+      }
+      const double ip = recip(piv);
+      if (lane == 0) inv[k] = ip;
+      for (int i = k + 1 + lane; i < n; i += LANES) Pw[i * m + k] *= ip;
+      __syncwarp(mask);
+      const double* urow = Pw + k * m + k + 1;
+      double* base = Pw + (k + 1) * m + k + 1;
+      flat2<LANES>(n - k - 1, m - k - 1, lane, [&](int i, int j) {
+        double* row = base + i * m;
+        row[j] = fma(-row[-1], urow[j], row[j]);
+      });
+      __syncwarp(mask);
     }
+    if (ok) {
+      // ---- 2a. U^T z = g, column by column; z_i is finished (scaled by
+      // 1/u_ii) by the step that removes its last term
+      flat2<LANES>(NOPS, m, lane, [&](int o, int q) {
+        const double g = rhs_mono<DIM>(a.mono_exp, q, a.ops.kind[o]);
+        Pw[(n + o) * m + q] = q == 0 ? g * inv[0] : g;
+      });
+      __syncwarp(mask);
+      for (int i = 0; i + 1 < m; ++i) {
+        flat2<LANES>(NOPS, m - i - 1, lane, [&](int o, int tt) {
+          const int q = i + 1 + tt;
+          double* z = Pw + (n + o) * m;
+          const double v = fma(-Pw[i * m + q], z[i], z[q]);
+          z[q] = tt == 0 ? v * inv[q] : v;
+        });
+        __syncwarp(mask);
+      }
+      // ---- 2b. L1^T [X | w_t] = [L2^T | z]: rows m .. n + NOPS - 1 of Pw
+      for (int i = m - 1; i > 0; --i) {
+        flat2<LANES>(rc_, i, lane, [&](int cc, int q) {
+          double* col = Pw + (m + cc) * m;
+          col[q] = fma(-Pw[i * m + q], col[i], col[q]);
+        });
+        __syncwarp(mask);
+      }
+      // ---- A and f in pivot order
+      const int npairs = n * (n - 1) / 2;
+      for (int e = lane; e < npairs; e += LANES) {
+        const uint16_t pr = a.pairs[e];
+        const int i = pr >> 8, j = pr & 0xff;
+        const double* xa = xi + perm[i] * DIM;
+        const double* xb = xi + perm[j] * DIM;
+        double d2 = 0.0;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+          const double d = xa[k] - xb[k];
+          d2 = fma(d, d, d2);
+        }
+        // one Newton step: the pair values' relative error (< 1e-14) moves
+        // the weights by about 1e-12 on the worst-conditioned test sets
+        const double v = d2 * sqrt_nr1(d2);
+        Ap[i * ldA + j] = v;
+        Ap[j * ldA + i] = v;
+      }
+      for (int i = lane; i < n; i += LANES) Ap[i * ldA + i] = 0.0;
+      flat2<LANES>(n, NOPS, lane, [&](int i, int o) { Bm[i * ldB + r + o] = rhs_phi<DIM>(xi, rc, perm[i], a.ops.kind[o]); });
+      __syncwarp(mask);
+      // ---- [A Z | f - A w_t]: column cc < r is A_{:,m+cc} - A_{:,0..m} X_{:,cc}
+      flat2<LANES>(n, rc_, lane, [&](int i, int cc) {
+        const double* arow = Ap + i * ldA;
+        const double* xc = Pw + (m + cc) * m;
+        double v = cc < r ? arow[m + cc] : Bm[i * ldB + cc];
+        for (int q = 0; q < m; ++q) v = fma(-arow[q], xc[q], v);
+        Bm[i * ldB + cc] = v;
+      });
+      __syncwarp(mask);
+      // ---- [Z^T A Z | Z^T b] over Ap's storage
+      flat2<LANES>(r, rc_, lane, [&](int j, int cc) {
+        const double* xj = Pw + (m + j) * m;
+        double v = Bm[(m + j) * ldB + cc];
+        for (int q = 0; q < m; ++q) v = fma(-xj[q], Bm[q * ldB + cc], v);
+        Sm[j * ldB + cc] = v;
+      });
+      __syncwarp(mask);
+      // ---- 3. the r x r positive definite system: y in columns r ..
+      ok = lu_solve<NOPS, LANES, double>(Sm, ldB, r, inv + m, lane, mask, true);
+    }
+    // ---- w = Pi^T ([w_t - X y; y]), unscaled, in stencil order
+    flat2<LANES>(n, NOPS, lane, [&](int i, int o) {
+      double v = 0.0;
+      if (ok) {
+        if (i < m) {
+          v = Pw[(n + o) * m + i];
+          for (int j = 0; j < r; ++j) v = fma(-Pw[(m + j) * m + i], Sm[j * ldB + r + o], v);
+        } else {
+          v = Sm[(i - m) * ldB + r + o];
+        }
+        v *= a.ops.kind[o] == 3 ? inv_s * inv_s : inv_s;
+        const bool fin = ((unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull) < 0x7ff0000000000000ull;
+        v = fin ? v : 0.0;
+      }
+      const int node = ok ? perm[i] : i;
+      a.w[((int64_t)o * n + node) * a.G + pos] = v;
+    });
     if (lane == 0) {
       const int32_t node = a.nodes[pos];
       if (!ok) atomicOr(a.flags, kDevSingular);
@@ -541,6 +750,9 @@ __global__ void __launch_bounds__(256) k_rbf_fp32r(RbfArgs a) {
   float* piv = L32 + K * ld32;
   int* perm = reinterpret_cast<int*>(piv + K);
   int* iperm = perm + K;
+  __shared__ int8_t par[kMaxMonomials], cor[kMaxMonomials];
+  mono_parents(a.mono_exp, a.n_mono, DIM, par, cor);
+  __syncthreads();
   for (int64_t t = (int64_t)blockIdx.x * SYS + sub; t < a.count; t += (int64_t)gridDim.x * SYS) {
     const int64_t pos = a.list ? a.list[t] : t;
     const int32_t c = a.nodes[pos];
@@ -572,7 +784,7 @@ __global__ void __launch_bounds__(256) k_rbf_fp32r(RbfArgs a) {
       xi[e] = v;
       xf[e] = (float)v;
     }
-    for (int j = lane; j < n; j += LANES) rc[j] = sqrt(rc[j] * (inv_s * inv_s));
+    for (int j = lane; j < n; j += LANES) rc[j] = sqrt_gs(rc[j] * (inv_s * inv_s));
     __syncwarp(mask);
     // ---- pair values: r^3 in FP64 (kept) and in FP32 (into the matrix)
     for (int e = lane; e < npairs; e += LANES) {
@@ -601,21 +813,15 @@ __global__ void __launch_bounds__(256) k_rbf_fp32r(RbfArgs a) {
     }
     for (int i = lane; i < n; i += LANES) L32[i * ld32 + i] = 0.f;
     // ---- monomial block (FP64 kept, FP32 into the matrix) and its zero block
-    for (int e = lane; e < n * M; e += LANES) {
-      const int i = e / M, q = e - (e / M) * M;
-      double v = 1.0;
-      float vf = 1.f;
-#pragma unroll
-      for (int k = 0; k < DIM; ++k) {
-        const int ex = a.mono_exp[q * DIM + k];
-        for (int u = 0; u < ex; ++u) {
-          v *= xi[i * DIM + k];
-          vf *= xf[i * DIM + k];
-        }
+    for (int i = lane; i < n; i += LANES) {
+      double* prow = P64 + i * M;
+      float* frow = L32 + i * ld32 + n;
+      for (int q = 0; q < M; ++q) {
+        prow[q] = mono_value<DIM, double>(prow, xi + i * DIM, q, par, cor, a.mono_exp);
+        const float vf = mono_value<DIM, float>(frow, xf + i * DIM, q, par, cor, a.mono_exp);
+        frow[q] = vf;
+        L32[(n + q) * ld32 + i] = vf;
       }
-      P64[e] = v;
-      L32[i * ld32 + n + q] = vf;
-      L32[(n + q) * ld32 + i] = vf;
     }
     for (int e = lane; e < M * M; e += LANES) {
       const int i = e / M, q = e - (e / M) * M;

@@ -232,7 +232,7 @@ void* pick(int dim, int nops, int lanes) {
 }
 
 size_t smem_bytes(int dim, int nops, bool r32, int K, int ld, int n) {
-  const size_t d = r32 ? r32_doubles(dim, nops, K, n) : (size_t)K * ld + (size_t)n * (dim + 1) + K;
+  const size_t d = r32 ? r32_doubles(dim, nops, K, n) : sys_doubles(dim, nops, n, K - n);
   return d * sizeof(double);
 }
 
