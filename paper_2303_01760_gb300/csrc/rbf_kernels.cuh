@@ -138,15 +138,30 @@ __device__ __forceinline__ bool f64_pos_in_f32(double x) {
 // Reciprocal by the Newton-Raphson iteration y <- y + y (1 - x y), started
 // from the single-precision reciprocal of x truncated to single precision:
 // two steps take the seed's 2^-22 relative error below double rounding.
-// Arguments whose exponent lies outside single range take the division.
-__device__ __forceinline__ double recip(double x) {
-  const unsigned ex = f64_exp(x);
-  if (ex < 1023u - 120u || ex > 1023u + 120u) return 1.0 / x;
+__device__ __forceinline__ double recip_core(double x) {
   double y = f64_of(__frcp_rn(f32_trunc(x)));
   double e = fma(-x, y, 1.0);
   y = fma(y, e, y);
   e = fma(-x, y, 1.0);
   return fma(y, e, y);
+}
+// 2^k for -1022 <= k <= 1023, from the bits.
+__device__ __forceinline__ double pow2i(int k) { return __longlong_as_double((long long)(1023 + k) << 52); }
+// Arguments outside single range are scaled by powers of two into it and
+// back (exact); zeros, infinities and NaNs are answered from the bits.  No
+// library division, whose out-of-line slow path would cost the kernels
+// their registers.
+__device__ __forceinline__ double recip(double x) {
+  const unsigned ex = f64_exp(x);
+  if (ex >= 1023u - 120u && ex <= 1023u + 120u) return recip_core(x);
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned long long sign = b & 0x8000000000000000ull;
+  if (ex == 0x7ffu) return (b & 0x000fffffffffffffull) ? x : __longlong_as_double((long long)sign);
+  if ((b << 1) == 0ull) return __longlong_as_double((long long)(sign | 0x7ff0000000000000ull));
+  const double pre = ex == 0u ? 0x1p+64 : 1.0;  // subnormal: 1/x = 2^64 / (2^64 x)
+  const double xs = x * pre;
+  const int t = (int)f64_exp(xs) - 1023, t1 = t / 2, t2 = t - t1;
+  return recip_core(xs * pow2i(-t1) * pow2i(-t2)) * pow2i(-t1) * pow2i(-t2) * pre;
 }
 __device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
 
@@ -164,14 +179,29 @@ __device__ __forceinline__ bool pivot_ok<float>(float piv) {
   return b > 0u && b < 0x7f800000u;
 }
 
+// Square-root arguments outside single range: x = x1 4^k with x1 in range,
+// sqrt x = 2^k sqrt x1 (exact scalings); zero, infinity and NaN return
+// themselves, negative arguments NaN.
+template <typename F>
+__device__ __forceinline__ double sqrt_wide(double x, F&& core) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned ex = f64_exp(x);
+  if ((b << 1) == 0ull || (ex == 0x7ffu && !(b >> 63))) return x;
+  if (b >> 63) return __longlong_as_double(0x7ff8000000000000ll);
+  const bool sub = ex == 0u;
+  const double xs = sub ? x * 0x1p+64 : x;
+  const int t = ((int)f64_exp(xs) - 1023) & ~1, t1 = t / 2, t2 = t - t1;
+  const double r = core(xs * pow2i(-t1) * pow2i(-t2));
+  return r * pow2i(t / 2) * (sub ? 0x1p-32 : 1.0);
+}
+
 // sqrt(x) for x > 0 by two steps of Goldschmidt's coupled iteration
 //   r = 1/2 - g h,  g <- g + g r  (-> sqrt x),  h <- h + h r  (-> 1/(2 sqrt x)),
 // started from the single-precision reciprocal square root (g = x y, h = y/2).
 // Each step squares the relative error: ~2^-22 -> ~2^-43 -> below double
-// rounding.  Zero, and arguments outside single precision's normal range,
-// take the library square root.
-__device__ __forceinline__ double sqrt_gs(double x) {
-  if (!f64_pos_in_f32(x)) return sqrt(x);
+// rounding.  Arguments outside single precision's normal range go through
+// sqrt_wide.
+__device__ __forceinline__ double sqrt_gs_core(double x) {
   const double y = f64_of(rsqrtf(f32_trunc(x)));
   double g = x * y, h = 0.5 * y;
   double r = fma(-g, h, 0.5);
@@ -180,17 +210,24 @@ __device__ __forceinline__ double sqrt_gs(double x) {
   r = fma(-g, h, 0.5);
   return fma(g, r, g);
 }
+__device__ __forceinline__ double sqrt_gs(double x) {
+  if (!f64_pos_in_f32(x)) return sqrt_wide(x, [](double v) { return sqrt_gs_core(v); });
+  return sqrt_gs_core(x);
+}
 
 // sqrt(x) by one Newton-Raphson step g + (x - g^2) / (2g) from the
 // single-precision root g of x truncated to single precision.  The relative
 // error is the seed's (below 2^-23) squared over two plus the seed's times
-// that of the single-precision 1/(2g) (2^-24): below 1.5e-14.  Zero, and
-// arguments outside single precision's normal range, take the library root.
-__device__ __forceinline__ double sqrt_nr1(double x) {
-  if (!f64_pos_in_f32(x)) return sqrt(x);
+// that of the single-precision 1/(2g) (2^-24): below 1.5e-14.  Arguments
+// outside single precision's normal range go through sqrt_wide.
+__device__ __forceinline__ double sqrt_nr1_core(double x) {
   const float gf = sqrtf(f32_trunc(x));
   const double g = f64_of(gf);
   return fma(f64_of(0.5f * __frcp_rn(gf)), fma(-g, g, x), g);
+}
+__device__ __forceinline__ double sqrt_nr1(double x) {
+  if (!f64_pos_in_f32(x)) return sqrt_wide(x, [](double v) { return sqrt_nr1_core(v); });
+  return sqrt_nr1_core(x);
 }
 
 // Monomial q of the basis is monomial par[q] times coordinate cor[q] (the
@@ -571,11 +608,12 @@ __global__ void __launch_bounds__(256) k_rbf_fp64(RbfArgs a) {
       double* x = xi + j * DIM;
 #pragma unroll
       for (int k = 0; k < DIM; ++k) x[k] *= inv_s;
-      rc[j] = sqrt_gs(rc[j] * (inv_s * inv_s));
       double* row = Pw + j * m;
       for (int q = 0; q < m; ++q) row[q] = mono_value<DIM, double>(row, x, q, par, cor, a.mono_exp);
       perm[j] = j;
     }
+    // |xi_j| comes with the pair values (the centre, node 0, sits at xi = 0)
+    if (lane == 0) rc[0] = 0.0;
     __syncwarp(mask);
     // ---- 1. P = Pi^T [L1; L2] U, whole rows swapped, multipliers in place
     for (int k = 0; k < m && ok; ++k) {
@@ -659,8 +697,9 @@ __global__ void __launch_bounds__(256) k_rbf_fp64(RbfArgs a) {
       for (int e = lane; e < npairs; e += LANES) {
         const uint16_t pr = a.pairs[e];
         const int i = pr >> 8, j = pr & 0xff;
-        const double* xa = xi + perm[i] * DIM;
-        const double* xb = xi + perm[j] * DIM;
+        const int ni = perm[i], nj = perm[j];
+        const double* xa = xi + ni * DIM;
+        const double* xb = xi + nj * DIM;
         double d2 = 0.0;
 #pragma unroll
         for (int k = 0; k < DIM; ++k) {
@@ -669,11 +708,15 @@ __global__ void __launch_bounds__(256) k_rbf_fp64(RbfArgs a) {
         }
         // one Newton step: the pair values' relative error (< 1e-14) moves
         // the weights by about 1e-12 on the worst-conditioned test sets
-        const double v = d2 * sqrt_nr1(d2);
+        const double g = sqrt_nr1(d2);
+        const double v = d2 * g;
         Ap[i * ldA + j] = v;
         Ap[j * ldA + i] = v;
+        if (ni == 0) rc[nj] = g;
+        if (nj == 0) rc[ni] = g;
       }
       for (int i = lane; i < n; i += LANES) Ap[i * ldA + i] = 0.0;
+      __syncwarp(mask);
       flat2<LANES>(n, NOPS, lane, [&](int i, int o) { Bm[i * ldB + r + o] = rhs_phi<DIM>(xi, rc, perm[i], a.ops.kind[o]); });
       __syncwarp(mask);
       // ---- [A Z | f - A w_t]: column cc < r is A_{:,m+cc} - A_{:,0..m} X_{:,cc}
@@ -697,22 +740,22 @@ __global__ void __launch_bounds__(256) k_rbf_fp64(RbfArgs a) {
       ok = lu_solve<NOPS, LANES, double>(Sm, ldB, r, inv + m, lane, mask, true);
     }
     // ---- w = Pi^T ([w_t - X y; y]), unscaled, in stencil order
-    flat2<LANES>(n, NOPS, lane, [&](int i, int o) {
-      double v = 0.0;
-      if (ok) {
-        if (i < m) {
-          v = Pw[(n + o) * m + i];
-          for (int j = 0; j < r; ++j) v = fma(-Pw[(m + j) * m + i], Sm[j * ldB + r + o], v);
-        } else {
-          v = Sm[(i - m) * ldB + r + o];
-        }
-        v *= a.ops.kind[o] == 3 ? inv_s * inv_s : inv_s;
+    if (ok) {
+      const double inv_s2 = inv_s * inv_s;
+      auto put = [&](int i, int o, double v) {
+        v *= a.ops.kind[o] == 3 ? inv_s2 : inv_s;
         const bool fin = ((unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull) < 0x7ff0000000000000ull;
-        v = fin ? v : 0.0;
-      }
-      const int node = ok ? perm[i] : i;
-      a.w[((int64_t)o * n + node) * a.G + pos] = v;
-    });
+        a.w[((int64_t)o * n + perm[i]) * a.G + pos] = fin ? v : 0.0;
+      };
+      flat2<LANES>(m, NOPS, lane, [&](int i, int o) {
+        double v = Pw[(n + o) * m + i];
+        for (int j = 0; j < r; ++j) v = fma(-Pw[(m + j) * m + i], Sm[j * ldB + r + o], v);
+        put(i, o, v);
+      });
+      flat2<LANES>(r, NOPS, lane, [&](int j, int o) { put(m + j, o, Sm[j * ldB + r + o]); });
+    } else {
+      flat2<LANES>(n, NOPS, lane, [&](int i, int o) { a.w[((int64_t)o * n + i) * a.G + pos] = 0.0; });
+    }
     if (lane == 0) {
       const int32_t node = a.nodes[pos];
       if (!ok) atomicOr(a.flags, kDevSingular);
