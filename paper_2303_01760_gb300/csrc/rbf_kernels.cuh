@@ -66,18 +66,22 @@ __device__ __forceinline__ unsigned long long shfl_xor_u64(unsigned mask, unsign
 }
 
 // Per-system shared memory of the FP64 kernel (in doubles), m monomials,
-// r = n - m, ldA = n | 1, ldB = (r + NOPS) | 1:
+// r = n - m, ldB = (r + NOPS) | 1:
 //   xi    n x DIM          scaled offsets
 //   rc    n                |xi_j|
-//   Ap    max(n ldA, r ldB) A in pivot order; later [S | Z^T b], then y
+//   Ap    max(n(n-1)/2 + 1, r ldB) A in pivot order, strict upper triangle
+//                          packed by rows, then one zero for the diagonal (A
+//                          is symmetric with a zero diagonal); later
+//                          [S | Z^T b], then y
 //   Pw    (n + NOPS) x m   LU of P; rows m..n-1 become X, rows n.. the
 //                          monomial right-hand sides, then w_t
 //   Bm    n x ldB          [A Z | f - A w_t]
 //   inv   n                reciprocal pivots of P (m), then of S (r)
 //   perm  n ints           stencil position of each pivot-order row
 __host__ __device__ constexpr size_t ns_apsize(int nops, int n, int m) {
-  return (size_t)n * (n | 1) > (size_t)(n - m) * ((n - m + nops) | 1) ? (size_t)n * (n | 1)
-                                                                       : (size_t)(n - m) * ((n - m + nops) | 1);
+  return (size_t)n * (n - 1) / 2 + 1 > (size_t)(n - m) * ((n - m + nops) | 1)
+             ? (size_t)n * (n - 1) / 2 + 1
+             : (size_t)(n - m) * ((n - m + nops) | 1);
 }
 __host__ __device__ constexpr size_t sys_doubles(int dim, int nops, int n, int m) {
   return (size_t)n * (dim + 1) + ns_apsize(nops, n, m) + (size_t)(n + nops) * m + (size_t)n * ((n - m + nops) | 1) +
@@ -527,6 +531,10 @@ struct FixedLU {
   }
 };
 
+// Position of A[i][j], i < j, in the strict upper triangle of an n x n
+// matrix packed by rows (the pair table's order).
+__device__ __forceinline__ int tri_index(int n, int i, int j) { return ((i * (2 * n - i - 1)) >> 1) + (j - i - 1); }
+
 // Calls f(i, j) for every (i, j) of [0, R) x [0, C), dealt to the lanes in
 // row-major order so that every lane of each instruction has work.
 template <int LANES, typename F>
@@ -565,7 +573,8 @@ __global__ void __launch_bounds__(256) k_rbf_fp64(RbfArgs a) {
   const int sub = threadIdx.x / LANES, lane = threadIdx.x % LANES;
   const unsigned mask = LANES == 32 ? 0xffffffffu : (((1u << LANES) - 1u) << ((threadIdx.x & 31) / LANES * LANES));
   const int n = a.n, m = a.n_mono, r = n - m, rc_ = r + NOPS;
-  const int ldA = n | 1, ldB = rc_ | 1;
+  const int ldB = rc_ | 1;
+
   double* xi = smem + (size_t)sub * sys_doubles(DIM, NOPS, n, m);
   double* rc = xi + n * DIM;
   double* Ap = rc + n;
@@ -709,24 +718,41 @@ __global__ void __launch_bounds__(256) k_rbf_fp64(RbfArgs a) {
         // one Newton step: the pair values' relative error (< 1e-14) moves
         // the weights by about 1e-12 on the worst-conditioned test sets
         const double g = sqrt_nr1(d2);
-        const double v = d2 * g;
-        Ap[i * ldA + j] = v;
-        Ap[j * ldA + i] = v;
+        Ap[e] = d2 * g;
         if (ni == 0) rc[nj] = g;
         if (nj == 0) rc[ni] = g;
       }
-      for (int i = lane; i < n; i += LANES) Ap[i * ldA + i] = 0.0;
+      if (lane == 0) Ap[npairs] = 0.0;
       __syncwarp(mask);
       flat2<LANES>(n, NOPS, lane, [&](int i, int o) { Bm[i * ldB + r + o] = rhs_phi<DIM>(xi, rc, perm[i], a.ops.kind[o]); });
       __syncwarp(mask);
       // ---- [A Z | f - A w_t]: column cc < r is A_{:,m+cc} - A_{:,0..m} X_{:,cc}
-      flat2<LANES>(n, rc_, lane, [&](int i, int cc) {
-        const double* arow = Ap + i * ldA;
-        const double* xc = Pw + (m + cc) * m;
-        double v = cc < r ? arow[m + cc] : Bm[i * ldB + cc];
-        for (int q = 0; q < m; ++q) v = fma(-arow[q], xc[q], v);
-        Bm[i * ldB + cc] = v;
-      });
+      {
+        // (the flat loop written out: as a lambda it was not inlined)
+        const int C = rc_;
+        int i = lane / C, cc = lane - (lane / C) * C;
+        const int dq = LANES / C, dr = LANES - (LANES / C) * C;
+        for (int e = lane; e < n * C; e += LANES) {
+          const double* xc = Pw + (m + cc) * m;
+          double v;
+          if (cc < r) {
+            const int jc = m + cc;
+            v = Ap[jc == i ? npairs : tri_index(n, min(i, jc), max(i, jc))];
+          } else {
+            v = Bm[i * ldB + cc];
+          }
+          // every lane runs the same m products; the diagonal A[i][i] = 0
+          // is read from the zero kept after the triangle
+          for (int q = 0; q < m; ++q) v = fma(-Ap[q == i ? npairs : tri_index(n, min(i, q), max(i, q))], xc[q], v);
+          Bm[i * ldB + cc] = v;
+          cc += dr;
+          i += dq;
+          if (cc >= C) {
+            cc -= C;
+            ++i;
+          }
+        }
+      }
       __syncwarp(mask);
       // ---- [Z^T A Z | Z^T b] over Ap's storage
       flat2<LANES>(r, rc_, lane, [&](int j, int cc) {
