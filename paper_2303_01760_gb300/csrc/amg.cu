@@ -64,8 +64,6 @@ __device__ __forceinline__ double row_dot(const MgLevel& L, int g, int64_t p, co
 // ---- cycle -------------------------------------------------------------------
 // x = w f + w (f - A w f), w = omega D^-1: two Jacobi sweeps from zero.
 __global__ void __launch_bounds__(kMgThreads) k_mg_pre(MgLevel L, const double* __restrict__ f, const double* done) {
-  pdl_wait();
-  pdl_release();
   if (*done != 0.0) return;
   int g;
   int64_t p, stride;
@@ -89,8 +87,6 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_pre(MgLevel L, const double* 
 // matrix, then their stencils) so their dependent loads overlap.
 __global__ void __launch_bounds__(kMgThreads) k_mg_restrict(MgLevel L, const double* __restrict__ f,
                                                             double* __restrict__ fc, int64_t nc, const double* done) {
-  pdl_wait();
-  pdl_release();
   constexpr int kBatch = 8;
   if (*done != 0.0) return;
   for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < nc; I += (int64_t)gridDim.x * blockDim.x) {
@@ -116,8 +112,6 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_restrict(MgLevel L, const dou
 __global__ void __launch_bounds__(kMgThreads) k_mg_post1(MgLevel L, const double* __restrict__ f,
                                                          const double* __restrict__ xc, double alpha,
                                                          const double* done) {
-  pdl_wait();
-  pdl_release();
   if (*done != 0.0) return;
   int g;
   int64_t p, stride;
@@ -140,8 +134,6 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_post1(MgLevel L, const double
 __global__ void __launch_bounds__(kMgThreads) k_mg_post2(MgLevel L, const double* __restrict__ f,
                                                          double* __restrict__ out, int border,
                                                          const double* done) {
-  pdl_wait();
-  pdl_release();
   if (*done != 0.0) return;
   int g;
   int64_t p, stride;
@@ -157,8 +149,6 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_post2(MgLevel L, const double
 __global__ void __launch_bounds__(kMgThreads) k_mg_coarse(const double* __restrict__ binv, int m,
                                                           const double* __restrict__ f, double* __restrict__ x,
                                                           int64_t border, const double* done) {
-  pdl_wait();
-  pdl_release();
   if (*done != 0.0) return;
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -593,32 +583,26 @@ hsm_status amg_setup(hsm_plan pl, const double* wp_mon, const double* wp_rbf, do
 
 cudaError_t amg_vcycle(const Amg& A, const double* in, double* out, const double* done, cudaStream_t s) {
   const int cg = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div((int64_t)A.m, kMgThreads / 32), 1024));
-  const dim3 T(kMgThreads);
-  cudaError_t e = cudaSuccess;
-  auto chk = [&](cudaError_t r) {
-    if (e == cudaSuccess) e = r;
-  };
   if (A.L == 1) {
-    chk(launch_pdl(k_mg_coarse, dim3(cg), T, s, (const double*)A.binv, A.m, in, out, (int64_t)A.lev[0].n, done));
-    return e;
+    k_mg_coarse<<<cg, kMgThreads, 0, s>>>(A.binv, A.m, in, out, A.lev[0].n, done);
+    return cudaGetLastError();
   }
   const double* f = in;
   for (int l = 0; l + 1 < A.L; ++l) {
     const MgLevel& F = A.lev[l];
-    chk(launch_pdl(k_mg_pre, dim3(F.blocks), T, s, F, f, done));
-    chk(launch_pdl(k_mg_restrict, dim3(F.cblocks), T, s, F, f, A.lev[l + 1].f, (int64_t)A.lev[l + 1].n, done));
+    k_mg_pre<<<F.blocks, kMgThreads, 0, s>>>(F, f, done);
+    k_mg_restrict<<<F.cblocks, kMgThreads, 0, s>>>(F, f, A.lev[l + 1].f, A.lev[l + 1].n, done);
     f = A.lev[l + 1].f;
   }
   const MgLevel& Cs = A.lev[A.L - 1];
-  chk(launch_pdl(k_mg_coarse, dim3(cg), T, s, (const double*)A.binv, A.m, (const double*)Cs.f, Cs.x, (int64_t)-1,
-                 done));
+  k_mg_coarse<<<cg, kMgThreads, 0, s>>>(A.binv, A.m, Cs.f, Cs.x, -1, done);
   for (int l = A.L - 2; l >= 0; --l) {
     const MgLevel& F = A.lev[l];
     const double* fl = l == 0 ? in : F.f;
-    chk(launch_pdl(k_mg_post1, dim3(F.blocks), T, s, F, fl, (const double*)A.lev[l + 1].x, A.alpha, done));
-    chk(launch_pdl(k_mg_post2, dim3(F.blocks), T, s, F, fl, l == 0 ? out : F.x, l == 0 ? 1 : 0, done));
+    k_mg_post1<<<F.blocks, kMgThreads, 0, s>>>(F, fl, A.lev[l + 1].x, A.alpha, done);
+    k_mg_post2<<<F.blocks, kMgThreads, 0, s>>>(F, fl, l == 0 ? out : F.x, l == 0 ? 1 : 0, done);
   }
-  return e;
+  return cudaGetLastError();
 }
 
 int amg_kernels_per_cycle(const Amg& A) { return A.L == 1 ? 1 : 4 * (A.L - 1) + 1; }

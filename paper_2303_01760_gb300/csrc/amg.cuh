@@ -52,7 +52,6 @@ hsm_status amg_setup(hsm_plan pl, const double* wp_mon, const double* wp_rbf, do
 // Enqueues one V(2,2)-cycle on s: out[0..N) = M^-1 in[0..N), out[N] = in[N]
 // (the border unknown of the bordered system is left as it is).  Every kernel
 // returns at once when *done != 0.
-// Kernels are launched with programmatic dependent launch.
 cudaError_t amg_vcycle(const Amg& amg, const double* in, double* out, const double* done, cudaStream_t s);
 int amg_kernels_per_cycle(const Amg& amg);
 void amg_free(Amg* amg, cudaStream_t s);

@@ -142,6 +142,7 @@ static void free_group(Group& g, cudaStream_t s) {
 
 static void free_plan_device(hsm_plan p) {
   cudaStream_t s = p->stream;
+  if (p->mon.w64 == p->ws.mon_w64) p->mon.w64 = nullptr;  // owned by the build workspace
   free_group(p->mon, s);
   free_group(p->rbf, s);
   dev_free(&p->kind, s);
@@ -187,6 +188,7 @@ hsm_status hsm_plan_build_stencils(hsm_plan p) {
   cudaStream_t s = p->stream;
   // weights of an earlier build are stale; stencil arrays and the build
   // workspace persist across builds
+  if (p->mon.w64 == p->ws.mon_w64) p->mon.w64 = nullptr;  // owned by the build workspace
   for (Group* g : {&p->mon, &p->rbf}) {
     dev_free(&g->w64, s);
     dev_free(&g->w32, s);
@@ -223,8 +225,10 @@ hsm_status hsm_plan_compute_weights(hsm_plan p, hsm_prec prec, uint8_t* node_sta
   dev_free(&p->mon.w32, s);
   dev_free(&p->rbf.w32, s);
   HSM_CUDA(p, cudaMemsetAsync(p->dev_flags, 0, sizeof(unsigned), s));
-  hsm_status st;
-  {
+  hsm_status st = HSM_OK;
+  // the stencil build computed the MON weights; they are computed again here
+  // only when the caller asks for per-node status
+  if (node_status) {
     PhaseTimer tm(p, HSM_PHASE_MON);
     st = compute_mon_weights(p, node_status);
   }
@@ -264,7 +268,7 @@ hsm_status hsm_plan_compute_weights(hsm_plan p, hsm_prec prec, uint8_t* node_sta
   HSM_CUDA(p, cudaMemcpyAsync(&flags, p->dev_flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   HSM_CUDA(p, cudaStreamSynchronize(s));
   p->weights_built = true;
-  if (flags & kDevSingular) return set_error(p, HSM_ESINGULAR, "some nodes have singular weight systems");
+  if ((flags | p->build_flags) & kDevSingular) return set_error(p, HSM_ESINGULAR, "some nodes have singular weight systems");
   return HSM_OK;
 }
 

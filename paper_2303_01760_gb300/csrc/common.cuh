@@ -62,6 +62,7 @@ struct BuildWs {
   int32_t* ccount = nullptr;           // [4N + 1024]
   int32_t* sorted_id = nullptr;        // [N]
   double* sorted_xyz = nullptr;        // [N][kMaxDim]
+  double* mon_w64 = nullptr;           // MON weights, [nops][2 dim + 1][count], room for count = N
   uint8_t* sorted_bnd = nullptr;       // [N]
   int32_t* scan_ws = nullptr;          // scan block sums
   int* readback = nullptr;             // pinned host: demoted, n_mon, n_rbf, flags
@@ -103,6 +104,7 @@ struct hsm_plan_s {
   std::vector<int8_t> h_exp;
   int64_t n_demoted = 0;
   int64_t n_fallback = 0;
+  unsigned build_flags = 0;  // device status bits of the last stencil build (MON weights included)
   bool stencils_built = false;
   bool weights_built = false;
   hsm::Tuning tune;
@@ -163,28 +165,6 @@ void dev_free(T** ptr, cudaStream_t s) {
 }
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
-// Programmatic dependent launch: the kernel may be scheduled while its
-// predecessor in the stream drains.  Every kernel launched this way calls
-// pdl_wait() before it reads or writes anything (it returns once the
-// predecessor has completed and its memory is visible), and lets its own
-// dependents be scheduled with pdl_release().
-template <typename... KArgs, typename... Args>
-cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kernel, args...);
-}
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-
 inline int num_sms() {
   static int sms = 0;
   if (!sms) {
@@ -209,6 +189,8 @@ int64_t scan_scratch(int64_t n);
 hsm_status build_stencils(hsm_plan p);
 hsm_status alloc_build_ws(hsm_plan p);
 void free_build_ws(hsm_plan p);
+// MON weights enqueued inside the stencil build (count read on the device).
+cudaError_t enqueue_mon_weights(hsm_plan p, const int* count_dev, double* w, cudaStream_t s);
 
 // ---- weights.cu ----------------------------------------------------------
 hsm_status compute_mon_weights(hsm_plan p, uint8_t* status);

@@ -516,6 +516,7 @@ hsm_status alloc_build_ws(hsm_plan p) {
   HSM_CUDA(p, dev_alloc(&w.ccount, ncell_max, s));
   HSM_CUDA(p, dev_alloc(&w.sorted_id, N, s));
   HSM_CUDA(p, dev_alloc(&w.sorted_xyz, (size_t)N * kMaxDim, s));
+  HSM_CUDA(p, dev_alloc(&w.mon_w64, (size_t)p->nops * (2 * p->dim + 1) * N, s));
   HSM_CUDA(p, dev_alloc(&w.sorted_bnd, N, s));
   HSM_CUDA(p, dev_alloc(&w.scan_ws, scan_scratch(ncell_max), s));
   HSM_CUDA(p, dev_alloc(&p->kind, N, s));
@@ -543,7 +544,7 @@ void free_build_ws(hsm_plan p) {
   w.graph = nullptr;
   for (void** ptr : {(void**)&w.bbox, (void**)&w.lat, (void**)&w.ijk, (void**)&w.on_lat, (void**)&w.hkeys,
                      (void**)&w.hvals, (void**)&w.cgd, (void**)&w.cell_of, (void**)&w.cstart, (void**)&w.ccount,
-                     (void**)&w.sorted_id, (void**)&w.sorted_xyz, (void**)&w.sorted_bnd, (void**)&w.scan_ws})
+                     (void**)&w.sorted_id, (void**)&w.sorted_xyz, (void**)&w.mon_w64, (void**)&w.sorted_bnd, (void**)&w.scan_ws})
     dev_free(ptr, s);
   if (w.readback) cudaFreeHost(w.readback);
   w.readback = nullptr;
@@ -620,6 +621,10 @@ cudaError_t enqueue_build(hsm_plan p, cudaStream_t s, int qt, int* nk) {
   k_mon_stencil<<<grid, T, 0, w.side>>>(w.ijk, p->mon.nodes, counts, N, lh, p->mon.idx);
   ++k;
   HSM_TRY(cudaGetLastError());
+  // MON weights on the same branch: they need only the MON stencils and run
+  // beside the kNN search, which leaves most of each SM idle
+  HSM_TRY(enqueue_mon_weights(p, counts, w.mon_w64, w.side));
+  ++k;
   HSM_TRY(cudaEventRecord(w.ev_join, w.side));
 
   // ---- kNN for the RBF-FD group
@@ -718,6 +723,8 @@ hsm_status build_stencils(hsm_plan p) {
   p->n_demoted = rb[0];
   p->mon.count = rb[1];
   p->rbf.count = rb[2];
+  p->build_flags = (unsigned)rb[3];
+  p->mon.w64 = w.mon_w64;
   if ((unsigned)rb[3] & kDevKnnShort)
     return set_error(p, HSM_EINVAL, "not enough candidate nodes for an RBF-FD stencil");
   p->stencils_built = true;

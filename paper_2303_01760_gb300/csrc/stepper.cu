@@ -457,8 +457,6 @@ __global__ void k_bicg_c(StepArgs a) {
 // The iterate of the bordered system is (p, c): the pressure field and KS::xN.
 // p = r + beta (p - omega v) over all N+1 entries.
 __global__ void k_pc_p(StepArgs a) {
-  pdl_wait();
-  pdl_release();
   const KS* ks = a.ks;
   if (ks->done != 0.0) return;
   const int64_t N1 = a.N + 1;
@@ -473,8 +471,6 @@ __global__ void k_pc_p(StepArgs a) {
 // v = A p^ (bordered); alpha = rho / rhat.v
 template <int DIM>
 __global__ void k_pc_v(StepArgs a) {
-  pdl_wait();
-  pdl_release();
   const KS* ks = a.ks;
   if (ks->done != 0.0) return;
   int g;
@@ -513,8 +509,6 @@ __global__ void k_pc_v(StepArgs a) {
 
 // s = r - alpha v; a small s ends the iteration after x += alpha p^
 __global__ void k_pc_s(StepArgs a) {
-  pdl_wait();
-  pdl_release();
   const KS* ks = a.ks;
   if (ks->done != 0.0) return;
   const int64_t N1 = a.N + 1;
@@ -538,8 +532,6 @@ __global__ void k_pc_s(StepArgs a) {
 // t = A s^ (bordered); omega = t.s / t.t
 template <int DIM>
 __global__ void k_pc_t(StepArgs a) {
-  pdl_wait();
-  pdl_release();
   const KS* ks = a.ks;
   if (ks->done != 0.0) return;
   if (ks->half != 0.0) {
@@ -584,8 +576,6 @@ __global__ void k_pc_t(StepArgs a) {
 
 // x += alpha p^ + omega s^, r = s - omega t; rho_new = rhat.r, |r|^2
 __global__ void k_pc_x(StepArgs a) {
-  pdl_wait();
-  pdl_release();
   const KS* ks = a.ks;
   if (ks->done != 0.0) return;
   const int64_t N1 = a.N + 1;
@@ -778,13 +768,13 @@ void launch_chunk(hsm_stepper st, const StepArgs& a, dim3 grid, dim3 blk, cudaSt
   for (int c = 0; c < chunk_iters(st); ++c) {
     if (st->amg) {
       const double* done = &a.ks->done;
-      launch_pdl(k_pc_p, grid, blk, s, a);
+      k_pc_p<<<grid, blk, 0, s>>>(a);
       amg_vcycle(*st->amg, a.vec + V_P0 * N1, a.vec + V_PH * N1, done, s);
-      launch_pdl(k_pc_v<DIM>, grid, blk, s, a);
-      launch_pdl(k_pc_s, grid, blk, s, a);
+      k_pc_v<DIM><<<grid, blk, 0, s>>>(a);
+      k_pc_s<<<grid, blk, 0, s>>>(a);
       amg_vcycle(*st->amg, a.vec + V_S * N1, a.vec + V_SH * N1, done, s);
-      launch_pdl(k_pc_t<DIM>, grid, blk, s, a);
-      launch_pdl(k_pc_x, grid, blk, s, a);
+      k_pc_t<DIM><<<grid, blk, 0, s>>>(a);
+      k_pc_x<<<grid, blk, 0, s>>>(a);
     } else {
       k_bicg_a<DIM><<<grid, blk, 0, s>>>(a);
       k_bicg_b<DIM><<<grid, blk, 0, s>>>(a);

@@ -49,9 +49,13 @@ template <int DIM, int NOPS>
 __global__ void __launch_bounds__(128) k_mon(const double* __restrict__ coords, int64_t N,
                                              const int32_t* __restrict__ idx, int64_t G, OpsDesc ops,
                                              double* __restrict__ w, uint8_t* __restrict__ status,
-                                             const int32_t* __restrict__ nodes, unsigned* flags) {
+                                             const int32_t* __restrict__ nodes, unsigned* flags,
+                                             const int* __restrict__ G_dev) {
   constexpr int K = 2 * DIM + 1;
   constexpr int C = K + NOPS;
+  // the group size is read on the device when the launch is part of the
+  // stencil build (it is known on the host only after the build)
+  if (G_dev) G = *G_dev;
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < G; p += (int64_t)gridDim.x * blockDim.x) {
     int32_t id[K];
 #pragma unroll
@@ -377,15 +381,15 @@ cudaError_t launch_rbf_external(const RbfExternal& x, bool r32, const int32_t* l
   return cudaLaunchKernel(sh.fn, dim3(grid), dim3(sh.threads), args, sh.smem, x.stream);
 }
 
-hsm_status compute_mon_weights(hsm_plan p, uint8_t* status) {
-  const int64_t G = p->mon.count;
-  if (G == 0) return HSM_OK;
+// MON weights of the G (or *G_dev) nodes of the MON group into w, on stream s.
+static cudaError_t launch_mon(hsm_plan p, int64_t G, const int* G_dev, double* w, uint8_t* status,
+                              cudaStream_t s) {
   OpsDesc ops = make_ops(p, p->op_mask);
   const int T = 128;
   int grid = (int)std::min<int64_t>(ceil_div(G, T), (int64_t)num_sms() * 16);
-#define HSM_MON(D, O)                                                                                      \
-  k_mon<D, O><<<grid, T, 0, p->stream>>>(p->coords, p->N, p->mon.idx, G, ops, p->mon.w64, status, p->mon.nodes, \
-                                         p->dev_flags)
+#define HSM_MON(D, O)                                                                                         \
+  k_mon<D, O><<<grid, T, 0, s>>>(p->coords, p->N, p->mon.idx, G, ops, w, status, p->mon.nodes, p->dev_flags, \
+                                 G_dev)
   if (p->dim == 2) {
     switch (p->nops) {
       case 1: HSM_MON(2, 1); break;
@@ -401,9 +405,18 @@ hsm_status compute_mon_weights(hsm_plan p, uint8_t* status) {
     }
   }
 #undef HSM_MON
-  HSM_CUDA(p, cudaGetLastError());
+  return cudaGetLastError();
+}
+
+hsm_status compute_mon_weights(hsm_plan p, uint8_t* status) {
+  if (p->mon.count == 0) return HSM_OK;
+  HSM_CUDA(p, launch_mon(p, p->mon.count, nullptr, p->mon.w64, status, p->stream));
   p->launches += 1;
   return HSM_OK;
+}
+
+cudaError_t enqueue_mon_weights(hsm_plan p, const int* count_dev, double* w, cudaStream_t s) {
+  return launch_mon(p, p->N, count_dev, w, nullptr, s);
 }
 
 hsm_status compute_rbf_weights_fp64(hsm_plan p, const int32_t* list, int64_t count, uint8_t* status) {

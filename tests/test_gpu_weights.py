@@ -188,3 +188,30 @@ def test_mon_weights_on_slightly_perturbed_lattice():
     rng = np.random.default_rng(8)
     ns.coords = ns.coords + rng.uniform(-1e-9, 1e-9, ns.coords.shape) * ns.h
     _check_plan(ns, m=2)
+
+
+def test_mon_weights_from_the_build_match_the_oracle():
+    """Without a node-status request the MON weights come from the stencil
+    build (computed beside the kNN search); they match the oracle, and bit for
+    bit the weights that the status-writing path computes."""
+    base = nodesets.square_wall_band(n=24, wall_band=0.0)
+    pert = nodesets.square_wall_band(n=24, wall_band=0.0)
+    rng = np.random.default_rng(9)
+    pert.coords = pert.coords + rng.uniform(-1e-9, 1e-9, pert.coords.shape) * pert.h
+    for ns in (nodesets.square_wall_band(n=40), base, pert):
+        plan_a, code_a, _ = make_plan(ns, m=2)
+        plan_b, code_b, _ = make_plan(ns, m=2, node_status=True)
+        assert code_a == code_b == 0
+        st = ost.build_stencils(ns.coords, ns.is_regular, ns.is_boundary, ns.h, 12, normals=ns.normals)
+        W = ow.all_weights(ns.coords, st, 2)
+        nodes = st["mon_nodes"]
+        assert len(nodes) > 0
+        for op in ow.ops_for(2):
+            rp, col, val = gpu_csr(plan_a, BIT[op])
+            _, _, val_b = gpu_csr(plan_b, BIT[op])
+            assert np.array_equal(val, val_b)
+            c, v = _rows(rp, col, val, nodes, 5)
+            assert np.array_equal(c, st["mon_idx"])
+            assert _rel(v, W["mon"][op]).max() <= TOL_FP64
+        plan_a.close()
+        plan_b.close()
