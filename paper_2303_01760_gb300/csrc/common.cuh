@@ -56,6 +56,8 @@ struct BuildWs {
   unsigned long long* hkeys = nullptr; // lattice hash
   int32_t* hvals = nullptr;
   unsigned long long hcap = 0;
+  int32_t* dmap = nullptr;             // dense lattice map, 4N + 1024 entries
+  void* ldesc = nullptr;               // its extents (device)
   void* cgd = nullptr;                 // CellGrid on the device
   int32_t* cell_of = nullptr;          // [N]
   int32_t* cstart = nullptr;           // [4N + 1025]

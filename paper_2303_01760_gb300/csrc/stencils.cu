@@ -1,7 +1,9 @@
 // Stencil selection (Section 2: "a set of n neighbouring nodes").
 //
 // Regular nodes keep the symmetric 2d+1 lattice stencil, found through a
-// dense lattice map (integer coordinates round(x/h) -> lowest node id).
+// lattice map (integer coordinates round(x/h) -> lowest node id): a dense
+// array over the lattice's extents when it has at most 4N + 1024 points, an
+// open-addressing hash otherwise.
 // All other nodes take the n nodes of smallest (d2, id), where
 // d2 = ((dx*dx) + (dy*dy)) + (dz*dz) is evaluated in FP64 with explicit
 // round-to-nearest intrinsics (never contracted to FMA), so the selection is
@@ -46,9 +48,11 @@ struct LatticeHash {
   int32_t* vals;             // kEmpty = no node
   unsigned long long mask;
   int dim;
+  template <int DIM>
   __device__ __forceinline__ unsigned long long key(const int* q) const {
     unsigned long long k = 0;
-    for (int a = dim - 1; a >= 0; --a) k = (k << 21) | (unsigned long long)(q[a] + (1 << 20));
+#pragma unroll
+    for (int a = DIM - 1; a >= 0; --a) k = (k << 21) | (unsigned long long)(q[a] + (1 << 20));
     return k;
   }
   static __device__ __forceinline__ unsigned long long hash(unsigned long long x) {
@@ -58,8 +62,9 @@ struct LatticeHash {
     x *= 0xc4ceb9fe1a85ec53ull;
     return x ^ (x >> 33);
   }
+  template <int DIM>
   __device__ __forceinline__ void insert(const int* q, int32_t id) const {
-    const unsigned long long k = key(q);
+    const unsigned long long k = key<DIM>(q);
     unsigned long long h = hash(k) & mask;
     for (unsigned long long probe = 0; probe <= mask; ++probe) {
       const unsigned long long prev = atomicCAS(&keys[h], ~0ull, k);
@@ -71,10 +76,12 @@ struct LatticeHash {
     }
   }
   // owner of lattice point q, or kEmpty
+  template <int DIM>
   __device__ __forceinline__ int32_t find(const int* q) const {
-    for (int a = 0; a < dim; ++a)
+#pragma unroll
+    for (int a = 0; a < DIM; ++a)
       if (q[a] <= -(1 << 20) || q[a] >= (1 << 20)) return kEmpty;
-    const unsigned long long k = key(q);
+    const unsigned long long k = key<DIM>(q);
     unsigned long long h = hash(k) & mask;
     for (unsigned long long probe = 0; probe <= mask; ++probe) {
       const unsigned long long cur = keys[h];
@@ -86,13 +93,67 @@ struct LatticeHash {
   }
 };
 
-// Bounding box (ordered-bit keys) and lattice extents of the node set, and
-// the lattice map: each thread keeps running extrema and inserts its node's
-// lattice point, the block reduces the extrema with warp shuffles, and one
-// thread per block issues the global atomics.
+// Extents of the dense lattice map, written on the device once the lattice
+// extents are known.
+struct LatticeDense {
+  int lo[kMaxDim];
+  int ext[kMaxDim];
+  long long size;  // product of the extents
+  int dense;       // 1: the dense array holds the map; 0: the hash does
+};
+
+// The lattice map used by the kernels: the dense array when the lattice is
+// compact, the hash otherwise.  load() reads the device-side extents; the
+// choice is the same for every thread of a launch.
+struct LatticeMap {
+  LatticeHash hash;
+  int32_t* dmap;  // [size] owner ids, kEmpty = no node
+  const LatticeDense* desc;
+  int lo[kMaxDim], ext[kMaxDim];
+  int dense;
+  __device__ __forceinline__ void load() {
+    const LatticeDense d = *desc;
+    dense = d.dense;
+#pragma unroll
+    for (int k = 0; k < kMaxDim; ++k) {
+      lo[k] = d.lo[k];
+      ext[k] = d.ext[k];
+    }
+  }
+  template <int DIM>
+  __device__ __forceinline__ long long slot(const int* q) const {
+    long long l = 0;
+#pragma unroll
+    for (int k = DIM - 1; k >= 0; --k) {
+      const int t = q[k] - lo[k];
+      if (t < 0 || t >= ext[k]) return -1;
+      l = l * ext[k] + t;
+    }
+    return l;
+  }
+  template <int DIM>
+  __device__ __forceinline__ int32_t find(const int* q) const {
+    if (!dense) return hash.find<DIM>(q);
+    const long long l = slot<DIM>(q);
+    return l < 0 ? kEmpty : dmap[l];
+  }
+  template <int DIM>
+  __device__ __forceinline__ void insert(const int* q, int32_t id) const {
+    if (!dense) {
+      hash.insert<DIM>(q, id);
+      return;
+    }
+    const long long l = slot<DIM>(q);
+    if (l >= 0) atomicMin(&dmap[l], id);
+  }
+};
+
+// Bounding box (ordered-bit keys) and lattice extents of the node set: each
+// thread keeps running extrema, the block reduces them with warp shuffles,
+// and one thread per block issues the global atomics.
 __global__ void __launch_bounds__(256) k_bounds(const double* __restrict__ coords, int64_t N, int dim, double inv_h,
                                                 unsigned long long* bbox, int* lat_lo, int* lat_hi, int32_t* ijk,
-                                                uint8_t* on_lat, LatticeHash lh) {
+                                                uint8_t* on_lat) {
   unsigned long long bmin[kMaxDim], bmax[kMaxDim];
   int lmin[kMaxDim], lmax[kMaxDim];
   for (int k = 0; k < kMaxDim; ++k) {
@@ -123,7 +184,6 @@ __global__ void __launch_bounds__(256) k_bounds(const double* __restrict__ coord
         lmax[k] = max(lmax[k], q[k]);
       }
     }
-    if (on) lh.insert(q, (int32_t)i);
   }
   __shared__ unsigned long long sb[2][kMaxDim][8];
   __shared__ int sl[2][kMaxDim][8];
@@ -169,23 +229,80 @@ __global__ void __launch_bounds__(256) k_bounds(const double* __restrict__ coord
 }
 
 
+// Dense map extents from the lattice extents; the dense array is used when
+// the lattice has at most dense_cap points.
+__global__ void k_lattice_setup(const int* __restrict__ lat_lo, const int* __restrict__ lat_hi, int dim,
+                                long long dense_cap, LatticeDense* desc) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  LatticeDense d;
+  long long size = 1;
+  bool fits = true;
+  for (int k = 0; k < kMaxDim; ++k) {
+    d.lo[k] = k < dim ? lat_lo[k] : 0;
+    const long long e = k < dim ? (long long)lat_hi[k] - lat_lo[k] + 1 : 1;
+    d.ext[k] = e > 0 && e < (1ll << 30) ? (int)e : 0;
+    if (e <= 0) size = 0;  // no node on the lattice
+    if (e >= (1ll << 30)) fits = false;
+    if (fits && size > 0) {
+      size *= e;
+      if (size > dense_cap) fits = false;
+    }
+  }
+  d.size = fits ? size : 0;
+  d.dense = fits ? 1 : 0;
+  *desc = d;
+}
+
+// Empties the map in use: the dense array's first size entries, or the hash.
+__global__ void k_lattice_clear(LatticeMap g, unsigned long long hcap) {
+  g.load();
+  const long long n = g.dense ? g.desc->size : (long long)hcap;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    if (g.dense) {
+      g.dmap[i] = kEmpty;
+    } else {
+      g.hash.keys[i] = ~0ull;
+      g.hash.vals[i] = kEmpty;
+    }
+  }
+}
+
+// Lattice point of every on-lattice node into the map (owner = lowest id).
+template <int DIM>
+__global__ void k_lattice_insert(const int32_t* __restrict__ ijk, const uint8_t* __restrict__ on_lat, int64_t N,
+                                 LatticeMap g) {
+  g.load();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    if (!on_lat[i]) continue;
+    int q[DIM];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) q[k] = ijk[k * N + i];
+    g.insert<DIM>(q, (int32_t)i);
+  }
+}
+
 // kind = 0 (MON) when the node is regular, interior, owns its lattice point and
 // has all 2d lattice neighbours; 1 (RBF-FD) otherwise.
+template <int DIM>
 __global__ void k_classify(const int32_t* __restrict__ ijk, const uint8_t* __restrict__ on_lat,
                            const uint8_t* __restrict__ is_regular, const uint8_t* __restrict__ is_boundary,
-                           int64_t N, LatticeHash g, uint8_t* kind, int* n_demoted) {
+                           int64_t N, LatticeMap g, uint8_t* kind, int* n_demoted) {
+  g.load();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
     bool reg = is_regular[i] != 0;
     bool mon = reg && on_lat[i] && !(is_boundary && is_boundary[i]);
     if (mon) {
-      int q[kMaxDim];
-      for (int k = 0; k < g.dim; ++k) q[k] = ijk[k * N + i];
-      mon = g.find(q) == (int32_t)i;
-      for (int k = 0; k < g.dim && mon; ++k) {
-        for (int s = -1; s <= 1 && mon; s += 2) {
+      int q[DIM];
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) q[k] = ijk[k * N + i];
+      mon = g.find<DIM>(q) == (int32_t)i;
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) {
+#pragma unroll
+        for (int s = -1; s <= 1; s += 2) {
           q[k] += s;
-          mon = g.find(q) != kEmpty;
+          mon = mon && g.find<DIM>(q) != kEmpty;
           q[k] -= s;
         }
       }
@@ -196,22 +313,25 @@ __global__ void k_classify(const int32_t* __restrict__ ijk, const uint8_t* __res
 }
 
 // MON stencils; the group size is read on the device.
+template <int DIM>
 __global__ void k_mon_stencil(const int32_t* __restrict__ ijk, const int32_t* __restrict__ mon_nodes,
-                              const int* __restrict__ count_dev, int64_t N, LatticeHash g, int32_t* idx) {
+                              const int* __restrict__ count_dev, int64_t N, LatticeMap g, int32_t* idx) {
+  g.load();
   const int64_t count = *count_dev;
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < count;
        p += (int64_t)gridDim.x * blockDim.x) {
     int32_t c = mon_nodes[p];
-    int q[kMaxDim];
-    for (int k = 0; k < g.dim; ++k) q[k] = ijk[k * N + c];
+    int q[DIM];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) q[k] = ijk[k * N + c];
     idx[p] = c;
-    int j = 1;
-    for (int k = 0; k < g.dim; ++k) {
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+#pragma unroll
       for (int s = -1; s <= 1; s += 2) {
         q[k] += s;
-        idx[(int64_t)j * count + p] = g.find(q);
+        idx[(int64_t)(1 + 2 * k + (s + 1) / 2) * count + p] = g.find<DIM>(q);
         q[k] -= s;
-        ++j;
       }
     }
   }
@@ -509,6 +629,12 @@ hsm_status alloc_build_ws(hsm_plan p) {
   HSM_CUDA(p, dev_alloc(&w.on_lat, N, s));
   HSM_CUDA(p, dev_alloc(&w.hkeys, cap, s));
   HSM_CUDA(p, dev_alloc(&w.hvals, cap, s));
+  HSM_CUDA(p, dev_alloc(&w.dmap, 4 * N + 1024, s));
+  {
+    LatticeDense* ld = nullptr;
+    HSM_CUDA(p, dev_alloc(&ld, 1, s));
+    w.ldesc = ld;
+  }
   HSM_CUDA(p, dev_alloc(&cg, 1, s));
   w.cgd = cg;
   HSM_CUDA(p, dev_alloc(&w.cell_of, N, s));
@@ -543,7 +669,7 @@ void free_build_ws(hsm_plan p) {
   if (w.graph) cudaGraphExecDestroy(w.graph);
   w.graph = nullptr;
   for (void** ptr : {(void**)&w.bbox, (void**)&w.lat, (void**)&w.ijk, (void**)&w.on_lat, (void**)&w.hkeys,
-                     (void**)&w.hvals, (void**)&w.cgd, (void**)&w.cell_of, (void**)&w.cstart, (void**)&w.ccount,
+                     (void**)&w.hvals, (void**)&w.dmap, (void**)&w.ldesc, (void**)&w.cgd, (void**)&w.cell_of, (void**)&w.cstart, (void**)&w.ccount,
                      (void**)&w.sorted_id, (void**)&w.sorted_xyz, (void**)&w.mon_w64, (void**)&w.sorted_bnd, (void**)&w.scan_ws})
     dev_free(ptr, s);
   if (w.readback) cudaFreeHost(w.readback);
@@ -581,7 +707,7 @@ cudaError_t enqueue_build(hsm_plan p, cudaStream_t s, int qt, int* nk) {
   int k = 0;
 
   // ---- bounds and lattice coordinates
-  int* lat = w.lat;  // [0,6): lattice extents (unused), [6]: demoted, [7]: n_mon, [8]: n_rbf, [9]: flags
+  int* lat = w.lat;  // [0,6): lattice extents, [6]: demoted, [7]: n_mon, [8]: n_rbf, [9]: flags
   HSM_TRY(cudaMemsetAsync(p->dev_flags, 0, 4 * sizeof(unsigned), s));
   // bbox: minima start at all-ones, maxima at zero (ordered-bit keys), stored
   // interleaved [min_k, max_k]
@@ -592,22 +718,30 @@ cudaError_t enqueue_build(hsm_plan p, cudaStream_t s, int qt, int* nk) {
   HSM_TRY(cudaMemsetAsync(lat, 0x7f, kMaxDim * sizeof(int), s));
   HSM_TRY(cudaMemsetAsync(lat + kMaxDim, 0x80, kMaxDim * sizeof(int), s));
   HSM_TRY(cudaMemsetAsync(lat + 2 * kMaxDim, 0, 4 * sizeof(int), s));
-  // lattice hash map, filled by k_bounds
-  LatticeHash lh;
-  lh.dim = dim;
-  lh.mask = w.hcap - 1;
-  lh.keys = w.hkeys;
-  lh.vals = w.hvals;
-  HSM_TRY(cudaMemsetAsync(lh.keys, 0xff, w.hcap * sizeof(unsigned long long), s));
-  HSM_TRY(cudaMemsetAsync(lh.vals, 0x7f, w.hcap * sizeof(int32_t), s));
-  k_bounds<<<grid, T, 0, s>>>(p->coords, N, dim, 1.0 / p->h, w.bbox, lat, lat + kMaxDim, w.ijk, w.on_lat, lh);
+  k_bounds<<<grid, T, 0, s>>>(p->coords, N, dim, 1.0 / p->h, w.bbox, lat, lat + kMaxDim, w.ijk, w.on_lat);
   ++k;
+  HSM_TRY(cudaGetLastError());
+  // lattice map: dense over the lattice's extents when they hold at most
+  // 4N + 1024 points, else the hash
+  LatticeMap lh;
+  lh.hash.dim = dim;
+  lh.hash.mask = w.hcap - 1;
+  lh.hash.keys = w.hkeys;
+  lh.hash.vals = w.hvals;
+  lh.dmap = w.dmap;
+  lh.desc = static_cast<const LatticeDense*>(w.ldesc);
+  k_lattice_setup<<<1, 32, 0, s>>>(lat, lat + kMaxDim, dim, (long long)(4 * N + 1024), static_cast<LatticeDense*>(w.ldesc));
+  k_lattice_clear<<<grid, T, 0, s>>>(lh, w.hcap);
+  if (dim == 2) k_lattice_insert<2><<<grid, T, 0, s>>>(w.ijk, w.on_lat, N, lh);
+  else k_lattice_insert<3><<<grid, T, 0, s>>>(w.ijk, w.on_lat, N, lh);
+  k += 3;
   HSM_TRY(cudaGetLastError());
 
   // ---- classification
   int* d_demoted = lat + 2 * kMaxDim;
   int* counts = lat + 2 * kMaxDim + 1;
-  k_classify<<<grid, T, 0, s>>>(w.ijk, w.on_lat, p->is_regular, p->is_boundary, N, lh, p->kind, d_demoted);
+  if (dim == 2) k_classify<2><<<grid, T, 0, s>>>(w.ijk, w.on_lat, p->is_regular, p->is_boundary, N, lh, p->kind, d_demoted);
+  else k_classify<3><<<grid, T, 0, s>>>(w.ijk, w.on_lat, p->is_regular, p->is_boundary, N, lh, p->kind, d_demoted);
   ++k;
   HSM_TRY(cudaGetLastError());
 
@@ -618,7 +752,8 @@ cudaError_t enqueue_build(hsm_plan p, cudaStream_t s, int qt, int* nk) {
   // MON stencils on a side branch of the graph, joined before the read-back
   HSM_TRY(cudaEventRecord(w.ev_fork, s));
   HSM_TRY(cudaStreamWaitEvent(w.side, w.ev_fork, 0));
-  k_mon_stencil<<<grid, T, 0, w.side>>>(w.ijk, p->mon.nodes, counts, N, lh, p->mon.idx);
+  if (dim == 2) k_mon_stencil<2><<<grid, T, 0, w.side>>>(w.ijk, p->mon.nodes, counts, N, lh, p->mon.idx);
+  else k_mon_stencil<3><<<grid, T, 0, w.side>>>(w.ijk, p->mon.nodes, counts, N, lh, p->mon.idx);
   ++k;
   HSM_TRY(cudaGetLastError());
   // MON weights on the same branch: they need only the MON stencils and run
