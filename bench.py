@@ -809,6 +809,68 @@ def run_kernels(args):
     print("kernels ok", ns.N)
 
 
+PAPER_NU_DVD = {"hybrid": 8.870, "scattered": 8.867, "regular": 8.852}  # Section 4.1, Table 1
+
+
+def run_dvd(args):
+    """De Vahl Davis natural convection (Section 4.1): Ra = 1e6, Pr = 0.71, from
+    rest to t = args.t_end on the quarter layouts, dt = 0.1 h^2 / 2, with the
+    average Nusselt number on the cold wall sampled along the way.  Prints one
+    JSON line (a validation run, not the benchmark metric)."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2303_01760_gb300 import hsm, nodesets
+
+    dev = torch.device("cuda:0")
+    ns = nodesets.square_quarters(n=args.dvd, layout=args.layout)
+    d = {k: torch.from_numpy(np.ascontiguousarray(getattr(ns, k))).to(dev)
+         for k in ("coords", "is_regular", "is_boundary", "normals", "bc", "T_bc")}
+    t0 = time.time()
+    plan = hsm.Plan(d["coords"], d["is_regular"], d["is_boundary"], ns.h, m=2, normals=d["normals"])
+    plan.build_stencils()
+    plan.compute_weights(hsm.HSM_PREC_FP64)
+    q = plan.query()
+    dt = 0.1 * ns.h * ns.h / 2.0
+    st = hsm.Stepper(plan, 1e6, 0.71, dt, ns.T_ref, d["bc"], d["T_bc"], d["normals"], krylov_tol=1e-10,
+                     krylov_max_it=4000)
+    v = torch.zeros((2, ns.N), dtype=torch.float64, device=dev)
+    T = torch.where(d["bc"] == 1, d["T_bc"], torch.zeros_like(d["T_bc"])).contiguous()
+    p = torch.zeros(ns.N, dtype=torch.float64, device=dev)
+    cold = np.flatnonzero((ns.is_boundary == 1) & (ns.coords[0] == 0.0)).astype(np.int32)
+    cold_d = torch.from_numpy(cold).to(dev)
+    n_steps = int(round(args.t_end / dt))
+    chunk = max(1, n_steps // 150)
+    series, iters, done, worst = [], 0, 0, 0
+    torch.cuda.synchronize()
+    t_run = time.time()
+    while done < n_steps:
+        k = min(chunk, n_steps - done)
+        its, code = st.step(v, T, p, k, allow_notconv=True)
+        iters += sum(its)
+        worst = max(worst, max(its))
+        done += k
+        nu = float(plan.wall_flux_mean(T, cold_d, d["normals"], scale=1.0).item())
+        series.append([round(done * dt, 6), nu])
+    torch.cuda.synchronize()
+    wall = time.time() - t_run
+    vmax = float(v.abs().max().item())
+    ref = PAPER_NU_DVD[args.layout]
+    out = {"dvd": {"layout": args.layout, "n": args.dvd, "h": ns.h, "N": int(ns.N), "n_mon": int(q["n_mon"]),
+                   "n_scattered": int(ns.n_scattered), "Ra": 1e6, "Pr": 0.71, "dt": dt, "t_end": args.t_end,
+                   "steps": n_steps, "krylov_iters_per_step": iters / n_steps, "krylov_iters_max": worst},
+           "nu_final": series[-1][1], "nu_paper": ref, "nu_rel_diff": series[-1][1] / ref - 1.0,
+           "nu_last_tenth_spread": float(np.ptp([x[1] for x in series[-max(2, len(series) // 10):]])),
+           "max_speed": vmax, "finite": bool(torch.isfinite(T).all() and torch.isfinite(v).all()),
+           "run_s": wall, "ms_per_step": 1e3 * wall / n_steps, "setup_s": t_run - t0, "nu_series": series}
+    st.close()
+    plan.close()
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -824,7 +886,13 @@ def main():
     ap.add_argument("--stepper", action="store_true", help="with --kernels: run --steps Boussinesq steps instead")
     ap.add_argument("--learned", action="store_true", help="with --kernels: learned weights instead")
     ap.add_argument("--train-steps", type=int, default=3000, help="with --kernels --learned")
+    ap.add_argument("--dvd", type=int, default=0, help="de Vahl Davis validation run on a 1/n lattice (no benchmark)")
+    ap.add_argument("--layout", default="hybrid", choices=["hybrid", "scattered", "regular"], help="with --dvd")
+    ap.add_argument("--t-end", type=float, default=0.15, help="with --dvd")
     args = ap.parse_args()
+    if args.dvd:
+        run_dvd(args)
+        return
     if args.kernels:
         run_kernels(args)
         return

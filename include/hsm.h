@@ -153,6 +153,20 @@ hsm_status hsm_plan_query(hsm_plan plan, int64_t* nnz_per_op, int64_t* n_mon, in
 hsm_status hsm_plan_export_csr(hsm_plan plan, unsigned op, int64_t* row_ptr, int32_t* col,
                                double* val);
 
+/* Mean normal flux of a field over a set of nodes, the average Nusselt number
+ * of Section 4.1: out[0] = scale * (1/count) * sum_i |n_i . grad T(x_i)|, the
+ * gradient taken with the plan's first-derivative weights (Eq. 1).  The
+ * plan's op mask must hold d/dx_k for every axis of its dimension.
+ *   T        device f64 [N]
+ *   nodes    device int32 [count] node ids, count >= 1
+ *   normals  device f64 [dim][N] unit normals (only the listed nodes are read)
+ *   scale    L / (T_H - T_C) for the Nusselt number
+ *   out      device f64 [1]
+ * Enqueued on the plan's stream without synchronisation.  The sum runs in a
+ * fixed order, so repeated calls give the same bits.                          */
+hsm_status hsm_wall_flux_mean(hsm_plan plan, const double* T, const int32_t* nodes, int64_t count,
+                              const double* normals, double scale, double* out);
+
 /* Applies the operators of op_mask (a subset of the plan's) to one field,
  * Eq. 1: out[o][c] = sum_i w_o[c][i] u[idx[c][i]], stored in FP64.
  *   in_dtype  HSM_F64: u is f64 [N], FP64 weights, FP64 sums;

@@ -35,3 +35,13 @@ def to_csr(N, st, W, op):
     cols = np.concatenate([st["mon_idx"].ravel(), st["rbf_idx"].ravel()])
     vals = np.concatenate([W["mon"][op].ravel(), W["rbf"][op].ravel()])
     return sp.csr_matrix((vals, (rows, cols)), shape=(N, N))
+
+
+def wall_flux_mean(N, st, W, T, nodes, normals, scale=1.0):
+    """Average Nusselt number of Section 4.1 over the given wall nodes:
+    scale * mean_i |n_i . grad T(x_i)|, grad T from the first-derivative
+    weights (Eq. 1), scale = L / (T_H - T_C).  normals [dim, N]."""
+    dim = normals.shape[0]
+    grads = apply_all(N, st, W, T, ("dx", "dy", "dz")[:dim])
+    g = np.stack([grads[op][nodes] for op in ("dx", "dy", "dz")[:dim]])   # [dim, count]
+    return scale * float(np.mean(np.abs((normals[:, nodes] * g).sum(0))))

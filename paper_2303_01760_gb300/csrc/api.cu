@@ -346,6 +346,15 @@ hsm_status hsm_apply(hsm_plan p, unsigned op_mask, hsm_dtype in_dtype, const voi
   return launch_apply(p, op_mask, in_dtype, u, out, p->stream);
 }
 
+hsm_status hsm_wall_flux_mean(hsm_plan p, const double* T, const int32_t* nodes, int64_t count,
+                              const double* normals, double scale, double* out) {
+  if (!p) return set_error(nullptr, HSM_EINVAL, "plan is NULL");
+  if (!p->weights_built) return set_error(p, HSM_ESTATE, "weights are not computed");
+  if (!T || !nodes || !normals || !out) return set_error(p, HSM_EINVAL, "T, nodes, normals and out are required");
+  if (count < 1) return set_error(p, HSM_EINVAL, "count must be at least 1");
+  return launch_wall_flux(p, T, nodes, count, normals, scale, out);
+}
+
 // ---------------------------------------------------------------------------
 // Autotuner: times the apply block size and the lanes per weight system on
 // this plan's own data and keeps the fastest.  Results may be cached in a

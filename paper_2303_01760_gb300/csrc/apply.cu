@@ -109,6 +109,47 @@ void* pick_nops(int nops, int wm, int wr) {
   }
 }
 
+// Average Nusselt number of Section 4.1: scale * mean_i |n_i . grad T(x_i)|
+// over the listed nodes, one block; each thread sums its nodes in order and
+// the block adds the partial sums in a fixed tree, so the result does not
+// depend on timing.
+constexpr int kFluxThreads = 256;
+
+template <int DIM>
+__global__ void __launch_bounds__(kFluxThreads) k_wall_flux(
+    const double* __restrict__ T, const int32_t* __restrict__ nodes, int64_t count,
+    const double* __restrict__ normals, int64_t N, const uint8_t* __restrict__ kind, const int32_t* __restrict__ pos,
+    const int32_t* __restrict__ idx_m, const double* __restrict__ w_m, int64_t cnt_m, int width_m,
+    const int32_t* __restrict__ idx_r, const double* __restrict__ w_r, int64_t cnt_r, int width_r, Slots<3> slot,
+    double scale, double* out) {
+  __shared__ double part[kFluxThreads];
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < count; i += kFluxThreads) {
+    const int32_t c = nodes[i];
+    const bool mon = kind[c] == 0;
+    const int32_t* idx = mon ? idx_m : idx_r;
+    const double* w = mon ? w_m : w_r;
+    const int64_t G = mon ? cnt_m : cnt_r;
+    const int W = mon ? width_m : width_r;
+    const int64_t p = pos[c];
+    double flux = 0.0;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      double g = 0.0;
+      for (int j = 0; j < W; ++j) g = fma(w[((int64_t)slot.s[k] * W + j) * G + p], T[idx[(int64_t)j * G + p]], g);
+      flux = fma(normals[k * N + c], g, flux);
+    }
+    acc += fabs(flux);
+  }
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  for (int h = kFluxThreads / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) part[threadIdx.x] += part[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = scale * part[0] / (double)count;
+}
+
 }  // namespace
 
 hsm_status launch_apply(hsm_plan p, unsigned op_mask, hsm_dtype dt, const void* u, double* out, cudaStream_t s) {
@@ -152,6 +193,28 @@ hsm_status launch_apply(hsm_plan p, unsigned op_mask, hsm_dtype dt, const void* 
   // Slots<NOPS> is a prefix of Slots<4>; the kernel reads only its first NOPS ints
   void* args[] = {&gm, &gr, &bm, &sl4, &u, &out, &N};
   HSM_CUDA(p, cudaLaunchKernel(fn, dim3((unsigned)(bm + br)), dim3(T), args, 0, s));
+  p->launches += 1;
+  return HSM_OK;
+}
+
+hsm_status launch_wall_flux(hsm_plan p, const double* T, const int32_t* nodes, int64_t count, const double* normals,
+                            double scale, double* out) {
+  Slots<3> sl{};
+  for (int k = 0; k < p->dim; ++k) {
+    sl.s[k] = -1;
+    for (int o = 0; o < p->nops; ++o)
+      if (p->ops[o] == (1 << k)) sl.s[k] = o;
+    if (sl.s[k] < 0) return set_error(p, HSM_EINVAL, "the plan's op mask lacks a first derivative");
+  }
+  if (p->dim == 2)
+    k_wall_flux<2><<<1, kFluxThreads, 0, p->stream>>>(T, nodes, count, normals, p->N, p->kind, p->pos, p->mon.idx,
+                                                      p->mon.w64, p->mon.count, p->mon.width, p->rbf.idx, p->rbf.w64,
+                                                      p->rbf.count, p->rbf.width, sl, scale, out);
+  else
+    k_wall_flux<3><<<1, kFluxThreads, 0, p->stream>>>(T, nodes, count, normals, p->N, p->kind, p->pos, p->mon.idx,
+                                                      p->mon.w64, p->mon.count, p->mon.width, p->rbf.idx, p->rbf.w64,
+                                                      p->rbf.count, p->rbf.width, sl, scale, out);
+  HSM_CUDA(p, cudaGetLastError());
   p->launches += 1;
   return HSM_OK;
 }

@@ -232,6 +232,8 @@ cudaError_t launch_rbf_external(const RbfExternal& x, bool r32, const int32_t* l
 // ---- apply.cu ------------------------------------------------------------
 hsm_status launch_apply(hsm_plan p, unsigned op_mask, hsm_dtype dt, const void* u, double* out,
                         cudaStream_t s);
+hsm_status launch_wall_flux(hsm_plan p, const double* T, const int32_t* nodes, int64_t count, const double* normals,
+                            double scale, double* out);
 
 // ---- mlp.cu --------------------------------------------------------------
 hsm_status compute_rbf_weights_learned(hsm_plan p, uint8_t* status, int32_t* fail_list, int* fail_count);

@@ -52,6 +52,7 @@ _SIGS = {
     "hsm_plan_query": (C.c_int, [_p, C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_i64)]),
     "hsm_plan_export_csr": (C.c_int, [_p, C.c_uint, _p, _p, _p]),
     "hsm_apply": (C.c_int, [_p, C.c_uint, C.c_int, _p, _p]),
+    "hsm_wall_flux_mean": (C.c_int, [_p, _p, _p, _i64, _p, C.c_double, _p]),
     "hsm_plan_autotune": (C.c_int, [_p, C.c_char_p]),
     "hsm_plan_destroy": (C.c_int, [_p]),
     "hsm_plan_profile": (C.c_int, [_p, C.POINTER(C.c_float), C.POINTER(_i64)]),
@@ -264,6 +265,19 @@ class Plan:
         if u.dtype not in (torch.float64, torch.float32):
             raise ValueError("u must be float32 or float64")
         check(lib.hsm_apply(self.h, int(op_mask), dt, ptr(u), ptr(out)), self.h)
+        return out
+
+    def wall_flux_mean(self, T, nodes, normals, scale=1.0, out=None):
+        """scale * mean over ``nodes`` of |n . grad T| (the average Nusselt
+        number of Section 4.1); a one-element f64 CUDA tensor, not synchronised."""
+        import torch
+
+        if out is None:
+            out = torch.empty(1, dtype=torch.float64, device=T.device)
+        nodes = nodes.to(torch.int32).contiguous()
+        check(lib.hsm_wall_flux_mean(self.h, ptr(T), ptr(nodes), int(nodes.numel()), ptr(normals), float(scale),
+                                     ptr(out)), self.h)
+        self._flux_keep = nodes
         return out
 
     def set_timing(self, enable=True):

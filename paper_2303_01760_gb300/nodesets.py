@@ -254,8 +254,10 @@ def _min_hole_gap(x, holes, dim):
     return d.min(1)
 
 
-def _build(name, dim, n, holes, band, wall_band, seed, bc_walls, hole_T, T_ref, k=None):
-    """Common hybrid construction (Section 2): lattice, removal, Poisson refill."""
+def _build(name, dim, n, holes, band, wall_band, seed, bc_walls, hole_T, T_ref, k=None, region=None):
+    """Common hybrid construction (Section 2): lattice, removal, Poisson refill.
+    ``region(p)`` (optional) marks further points whose neighbourhood is
+    discretised with scattered nodes."""
     rng = np.random.default_rng(seed)
     h = 1.0 / n
     ijk = _lattice(dim, n)
@@ -267,6 +269,8 @@ def _build(name, dim, n, holes, band, wall_band, seed, bc_walls, hole_T, T_ref, 
     wall_dist = np.minimum(x, 1.0 - x).min(1)
     eps = 1e-9 * h
     in_band_lat = (gap < band - eps) | (wall_dist < wall_band - eps)
+    if region is not None:
+        in_band_lat |= region(x)
     interior_lat = keep & (n_wall == 0) & ~in_band_lat & (gap > 0)
     wall_lat = keep & (n_wall == 1) & (gap > 0.5 * h)
     lat_pts = x[interior_lat | wall_lat]
@@ -286,13 +290,25 @@ def _build(name, dim, n, holes, band, wall_band, seed, bc_walls, hole_T, T_ref, 
     def accept(p):
         g = _min_hole_gap(p, holes, dim) if len(holes) else np.full(len(p), np.inf)
         wd = np.minimum(p, 1.0 - p).min(1)
-        return (g > 0) & ((g < band - eps) | (wd < wall_band - eps))
+        inside = (g < band - eps) | (wd < wall_band - eps)
+        if region is not None:
+            inside = inside | region(p)
+        return (g > 0) & inside
 
     fixed = np.concatenate([lat_pts, hole_pts], 0)
     grow = 2.0 * h
     fixed_gap = _min_hole_gap(fixed, holes, dim)
     fixed_wd = np.minimum(fixed, 1.0 - fixed).min(1)
-    seeds = fixed[(fixed_gap < band + grow) | (fixed_wd < wall_band + grow)]
+    near = (fixed_gap < band + grow) | (fixed_wd < wall_band + grow)
+    if region is not None:
+        # fixed points within 2h of the region seed its fill
+        near |= region(fixed)
+        for a in range(dim):
+            for sgn in (-1.0, 1.0):
+                q = fixed.copy()
+                q[:, a] += sgn * grow
+                near |= region(q)
+    seeds = fixed[near]
     if k is None:
         k = 16 if dim == 2 else 10
     scat = _poisson_fill(fixed, seeds, accept, h, np.zeros(dim), np.ones(dim), rng, k)
@@ -345,6 +361,35 @@ def square_wall_band(n=40, wall_band=0.1, seed=SEED_BASE + 0):
 
     return _build(f"square-wallband-n{n}", 2, n, np.zeros((0, 3)), 0.0, wall_band, seed,
                   bc_walls, lambda i: 0.0, 0.0)
+
+
+def square_quarters(n=100, layout="hybrid", seed=SEED_BASE + 5):
+    """The de Vahl Davis square split into quarters, each discretised with
+    either scattered or regular nodes (Section 4.1).  ``layout``: "hybrid"
+    (bottom-left and top-right quarters scattered, the other two regular),
+    "scattered" (all four) or "regular" (none).  Walls as in
+    ``square_wall_band``: T_C = -0.5 at x = 0, T_H = +0.5 at x = 1, insulated
+    top and bottom."""
+
+    def bc_walls(axis, side):
+        if axis == 0:
+            return BC_T_DIRICHLET, (0.5 if side else -0.5)
+        return BC_T_NEUMANN, 0.0
+
+    if layout == "hybrid":
+        def region(p):
+            lo = (p[:, 0] < 0.5) & (p[:, 1] < 0.5)
+            hi = (p[:, 0] >= 0.5) & (p[:, 1] >= 0.5)
+            return lo | hi
+        return _build(f"square-quarters-n{n}", 2, n, np.zeros((0, 3)), 0.0, 0.0, seed, bc_walls,
+                      lambda i: 0.0, 0.0, region=region)
+    if layout == "scattered":
+        return _build(f"square-scattered-dvd-n{n}", 2, n, np.zeros((0, 3)), 0.0, 1.0, seed, bc_walls,
+                      lambda i: 0.0, 0.0)
+    if layout == "regular":
+        return _build(f"square-regular-n{n}", 2, n, np.zeros((0, 3)), 0.0, 0.0, seed, bc_walls,
+                      lambda i: 0.0, 0.0)
+    raise ValueError(layout)
 
 
 def square_holes(n=500, n_holes=8, r_range=(0.03, 0.08), band=0.05, seed=SEED_BASE + 1,

@@ -215,3 +215,24 @@ def test_mon_weights_from_the_build_match_the_oracle():
             assert _rel(v, W["mon"][op]).max() <= TOL_FP64
         plan_a.close()
         plan_b.close()
+
+
+def test_sparse_lattice_takes_the_hashed_map():
+    """Two copies of a wall-band set 400 lattice spacings apart: the lattice's
+    extents hold far more than 4N + 1024 points, so the build keeps its map
+    in the hash instead of the dense array.  Stencils and weights must still
+    match the oracle."""
+    import dataclasses
+
+    a = nodesets.square_wall_band(n=40)
+    shift = 400 * a.h
+    ns = dataclasses.replace(
+        a, name="two copies",
+        coords=np.concatenate([a.coords, a.coords + shift], axis=1),
+        is_regular=np.concatenate([a.is_regular, a.is_regular]),
+        is_boundary=np.concatenate([a.is_boundary, a.is_boundary]),
+        normals=np.concatenate([a.normals, a.normals], axis=1),
+        bc=np.concatenate([a.bc, a.bc]), T_bc=np.concatenate([a.T_bc, a.T_bc]))
+    lattice_points = (401 + 40) ** 2
+    assert lattice_points > 4 * ns.N + 1024
+    _check_plan(ns, m=2)
