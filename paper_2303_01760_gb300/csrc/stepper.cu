@@ -56,10 +56,19 @@ struct hsm_stepper_s {
   // Krylov iterations, chunk = one chunk, tail = correction + temperature
   cudaGraphExec_t g_head = nullptr, g_chunk = nullptr, g_tail = nullptr;
   cudaStream_t cap = nullptr;  // private stream the graphs are captured on
+  cudaStream_t body = nullptr; // second capture stream (the conditional loop's body)
   int head_chunks = 0;
   const double *gv = nullptr, *gT = nullptr, *gp = nullptr;
   int last_iters = 0;
   hsm::Amg* amg = nullptr;    // multigrid preconditioner (nullptr: Jacobi)
+  // one graph per step with the Krylov iterations in a conditional WHILE
+  // node: the loop ends on the device, without a host round trip
+  cudaGraphExec_t g_step = nullptr;
+  bool g_step_failed = false;  // conditional nodes unavailable: host-driven loop
+  unsigned* ctl = nullptr;     // [0] iterations of the current loop, [1] steps recorded, [2] loop cap reached
+  int* step_iters = nullptr;   // per step of the current hsm_step call
+  int* step_bad = nullptr;     // 1 where a step's solve stopped short of its tolerance
+  int step_cap = 0;
 };
 
 namespace hsm {
@@ -755,6 +764,27 @@ StepArgs make_args(hsm_stepper st, double* v, double* T, double* p) {
   return a;
 }
 
+// Device side of the conditional Krylov loop.  Every pass of the loop body
+// ends with k_loop_cond, which keeps the loop going while the solve has not
+// converged; a pass counter caps the loop at cap passes, so it always ends.
+__global__ void k_loop_begin(unsigned* ctl) { ctl[0] = 0u; }
+
+__global__ void k_loop_cond(const KS* ks, unsigned* ctl, unsigned cap, cudaGraphConditionalHandle h) {
+  const unsigned c = ++ctl[0];
+  const bool open = ks->done == 0.0;
+  if (open && c >= cap) ctl[2] = 1u;
+  cudaGraphSetConditional(h, open && c < cap ? 1u : 0u);
+}
+
+// Iterations and convergence of the step that just finished.
+__global__ void k_step_record(const KS* ks, unsigned* ctl, int* iters, int* bad, int cap) {
+  const unsigned k = ctl[1]++;
+  if ((int)k < cap) {
+    iters[k] = (int)ks->iter;
+    bad[k] = (ks->breakdown != 0.0 || ks->rnorm2 > ks->tol2 * ks->bnorm2 * 1.0000001) ? 1 : 0;
+  }
+}
+
 // Krylov iterations per captured chunk: Jacobi needs thousands of iterations
 // per solve, the multigrid preconditioner tens, each of ~50 kernels.
 int chunk_iters(hsm_stepper st) { return st->amg ? 2 : 16; }
@@ -763,9 +793,9 @@ int chunk_kernels(hsm_stepper st) {
 }
 
 template <int DIM>
-void launch_chunk(hsm_stepper st, const StepArgs& a, dim3 grid, dim3 blk, cudaStream_t s) {
+void launch_iters(hsm_stepper st, const StepArgs& a, dim3 grid, dim3 blk, cudaStream_t s, int n_iters) {
   const int64_t N1 = a.N + 1;
-  for (int c = 0; c < chunk_iters(st); ++c) {
+  for (int c = 0; c < n_iters; ++c) {
     if (st->amg) {
       const double* done = &a.ks->done;
       k_pc_p<<<grid, blk, 0, s>>>(a);
@@ -783,6 +813,11 @@ void launch_chunk(hsm_stepper st, const StepArgs& a, dim3 grid, dim3 blk, cudaSt
   }
 }
 
+template <int DIM>
+void launch_chunk(hsm_stepper st, const StepArgs& a, dim3 grid, dim3 blk, cudaStream_t s) {
+  launch_iters<DIM>(st, a, grid, blk, s, chunk_iters(st));
+}
+
 template <typename F>
 cudaError_t capture(cudaStream_t s, cudaGraphExec_t* out, F&& body) {
   cudaGraph_t g = nullptr;
@@ -797,12 +832,64 @@ cudaError_t capture(cudaStream_t s, cudaGraphExec_t* out, F&& body) {
 }
 
 void drop_graphs(hsm_stepper st) {
-  for (cudaGraphExec_t* g : {&st->g_head, &st->g_chunk, &st->g_tail})
+  for (cudaGraphExec_t* g : {&st->g_head, &st->g_chunk, &st->g_tail, &st->g_step})
     if (*g) {
       cudaGraphExecDestroy(*g);
       *g = nullptr;
     }
   st->head_chunks = 0;
+}
+
+// One step as one graph: predictor, Krylov set-up, the Krylov iterations in
+// a conditional WHILE node (body: one iteration and k_loop_cond), correction,
+// temperature and the record of the step's iteration count.
+template <int DIM>
+cudaError_t capture_step(hsm_stepper st, const StepArgs& a, dim3 grid, dim3 blk, cudaStream_t cs, cudaStream_t bs,
+                         cudaGraphExec_t* out) {
+  const unsigned cap = (unsigned)st->phys.krylov_max_it + 2u;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  k_predictor<DIM><<<grid, blk, 0, cs>>>(a);
+  k_krylov_init<DIM><<<grid, blk, 0, cs>>>(a);
+  k_loop_begin<<<1, 1, 0, cs>>>(st->ctl);
+  cudaStreamCaptureStatus status;
+  cudaGraph_t cg = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  cudaGraphConditionalHandle h{};
+  cudaGraphNode_t cnode = nullptr;
+  cudaGraphNodeParams np = {};
+  e = cudaStreamGetCaptureInfo(cs, &status, nullptr, &cg, &deps, nullptr, &ndeps);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, cg, 1u, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) {
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    e = cudaGraphAddNode(&cnode, cg, deps, nullptr, ndeps, &np);
+  }
+  if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+  if (e == cudaSuccess) {
+    // the loop body, captured on a second stream into the node's graph
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      launch_iters<DIM>(st, a, grid, blk, bs, 1);
+      k_loop_cond<<<1, 1, 0, bs>>>(a.ks, st->ctl, cap, h);
+      e = cudaStreamEndCapture(bs, &body);
+    }
+  }
+  if (e == cudaSuccess) {
+    k_correct_temperature<DIM><<<grid, blk, 0, cs>>>(a);
+    k_temperature_bc<<<grid, blk, 0, cs>>>(a);
+    k_step_record<<<1, 1, 0, cs>>>(a.ks, st->ctl, st->step_iters, st->step_bad, st->step_cap);
+  }
+  cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+  if (g) cudaGraphDestroy(g);
+  return e;
 }
 
 // Each step runs as CUDA graphs: the head graph (predictor, Krylov set-up and
@@ -833,6 +920,52 @@ hsm_status run_steps(hsm_stepper st, int n_steps, double* v, double* T, double* 
       k_correct_temperature<DIM><<<grid, blk, 0, cs>>>(a);
       k_temperature_bc<<<grid, blk, 0, cs>>>(a);
     }));
+  // device-side loop: one graph launch per step, one synchronisation per call
+  if (!st->g_step_failed) {
+    if (n_steps > st->step_cap) {
+      dev_free(&st->step_iters, s);
+      dev_free(&st->step_bad, s);
+      drop_graphs(st);
+      const int cap = std::max(n_steps, 64);
+      HSM_CUDA(pl, dev_alloc(&st->step_iters, cap, s));
+      HSM_CUDA(pl, dev_alloc(&st->step_bad, cap, s));
+      st->step_cap = cap;
+    }
+    if (!st->ctl) HSM_CUDA(pl, dev_alloc(&st->ctl, 4, s));
+    if (!st->g_step) {
+      if (!st->body) HSM_CUDA(pl, cudaStreamCreateWithFlags(&st->body, cudaStreamNonBlocking));
+      if (capture_step<DIM>(st, a, grid, blk, cs, st->body, &st->g_step) != cudaSuccess) {
+        // conditional graph nodes are not available here: clear the error and
+        // fall back to the host-driven loop below
+        cudaGetLastError();
+        st->g_step = nullptr;
+        st->g_step_failed = true;
+      }
+    }
+  }
+  if (st->g_step) {
+    HSM_CUDA(pl, cudaMemsetAsync(st->ctl, 0, 4 * sizeof(unsigned), s));
+    for (int it = 0; it < n_steps; ++it) {
+      HSM_CUDA(pl, cudaGraphLaunch(st->g_step, s));
+      pl->launches += 6;
+    }
+    std::vector<int> it_h(n_steps > 0 ? n_steps : 1), bad_h(n_steps > 0 ? n_steps : 1);
+    unsigned ctl_h[4] = {0, 0, 0, 0};
+    if (n_steps > 0) {
+      HSM_CUDA(pl, cudaMemcpyAsync(it_h.data(), st->step_iters, n_steps * sizeof(int), cudaMemcpyDeviceToHost, s));
+      HSM_CUDA(pl, cudaMemcpyAsync(bad_h.data(), st->step_bad, n_steps * sizeof(int), cudaMemcpyDeviceToHost, s));
+    }
+    HSM_CUDA(pl, cudaMemcpyAsync(ctl_h, st->ctl, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    HSM_CUDA(pl, cudaStreamSynchronize(s));
+    for (int it = 0; it < n_steps; ++it) {
+      if (iters) iters[it] = it_h[it];
+      if (bad_h[it]) *notconv = true;
+      pl->launches += (int64_t)it_h[it] * (chunk_kernels(st) / chunk_iters(st) + 1);
+    }
+    if (ctl_h[2]) *notconv = true;
+    if (n_steps > 0) st->last_iters = it_h[n_steps - 1];
+    return HSM_OK;
+  }
   KS host{};
   const int kChunk = chunk_iters(st);
   const int max_chunks = (int)(st->phys.krylov_max_it / kChunk) + 2;
@@ -974,6 +1107,10 @@ hsm_status hsm_stepper_destroy(hsm_stepper st) {
   cudaStream_t s = st->plan ? st->plan->stream : nullptr;
   drop_graphs(st);
   if (st->cap) cudaStreamDestroy(st->cap);
+  if (st->body) cudaStreamDestroy(st->body);
+  dev_free(&st->ctl, s);
+  dev_free(&st->step_iters, s);
+  dev_free(&st->step_bad, s);
   if (st->amg) {
     amg_free(st->amg, s);
     delete st->amg;
