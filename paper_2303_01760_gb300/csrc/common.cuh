@@ -185,6 +185,11 @@ cudaError_t exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, cudaS
 // List of indices i (ascending) with key[i] == want; count written to *count_dev.
 cudaError_t select_indices(const uint8_t* key, uint8_t want, int64_t n, int32_t* out_list,
                            int32_t* out_pos, int* count_dev, cudaStream_t s, int32_t* ws = nullptr);
+// Both lists of a 0/1 split in one scan: items with key == want go to
+// first (in order), the others to second; pos[i] = place of i in its list;
+// the list sizes go to count_first / count_second (device).
+cudaError_t partition_indices(const uint8_t* key, uint8_t want, int64_t n, int32_t* first, int32_t* second,
+                              int32_t* pos, int* count_first, int* count_second, cudaStream_t s, int32_t* ws);
 int64_t scan_scratch(int64_t n);
 
 // ---- stencils.cu ---------------------------------------------------------

@@ -60,7 +60,7 @@ __global__ void k_block_sums(F f, int64_t n, int32_t* sums) {
   if (threadIdx.x == 0) sums[blockIdx.x] = total;
 }
 
-__global__ void k_scan_sums(int32_t* sums, int nb, int32_t* grand) {
+__global__ void k_scan_sums(int32_t* sums, int nb, int32_t* grand, int64_t n, int32_t* rest) {
   __shared__ int total;
   int carry = 0;
   for (int s = 0; s < nb; s += kScanThreads) {
@@ -72,6 +72,7 @@ __global__ void k_scan_sums(int32_t* sums, int nb, int32_t* grand) {
     __syncthreads();
   }
   if (threadIdx.x == 0 && grand) *grand = carry;
+  if (threadIdx.x == 0 && rest) *rest = (int32_t)(n - carry);
 }
 
 template <typename F, typename W>
@@ -97,6 +98,18 @@ struct WriteExcl {
   int32_t* out;
   __device__ void operator()(int64_t i, int e, int) const { out[i] = e; }
 };
+// Stable partition by a 0/1 key: e counts the selected items before i, so an
+// unselected item goes to place i - e of the second list.
+struct WritePartition {
+  int32_t* first;
+  int32_t* second;
+  int32_t* pos;
+  __device__ void operator()(int64_t i, int e, int v) const {
+    const int32_t q = v ? e : (int32_t)(i - e);
+    (v ? first : second)[q] = (int32_t)i;
+    pos[i] = q;
+  }
+};
 struct WriteSelect {
   int32_t* list;
   int32_t* pos;
@@ -109,7 +122,7 @@ struct WriteSelect {
 };
 
 template <typename F, typename W>
-cudaError_t run_scan(F f, W w, int64_t n, int32_t* grand, cudaStream_t s, int32_t* ws) {
+cudaError_t run_scan(F f, W w, int64_t n, int32_t* grand, cudaStream_t s, int32_t* ws, int32_t* rest = nullptr) {
   int nb = (int)ceil_div(n > 0 ? n : 1, kScanTile);
   int32_t* sums = ws;
   cudaError_t e = cudaSuccess;
@@ -118,7 +131,7 @@ cudaError_t run_scan(F f, W w, int64_t n, int32_t* grand, cudaStream_t s, int32_
     if (e != cudaSuccess) return e;
   }
   k_block_sums<<<nb, kScanThreads, 0, s>>>(f, n, sums);
-  k_scan_sums<<<1, kScanThreads, 0, s>>>(sums, nb, grand);
+  k_scan_sums<<<1, kScanThreads, 0, s>>>(sums, nb, grand, n, rest);
   k_block_write<<<nb, kScanThreads, 0, s>>>(f, n, sums, w);
   e = cudaGetLastError();
   if (!ws) dev_free(&sums, s);
@@ -134,6 +147,11 @@ cudaError_t exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, cudaS
 cudaError_t select_indices(const uint8_t* key, uint8_t want, int64_t n, int32_t* out_list,
                            int32_t* out_pos, int* count_dev, cudaStream_t s, int32_t* ws) {
   return run_scan(KeyEq{key, want}, WriteSelect{out_list, out_pos}, n, count_dev, s, ws);
+}
+
+cudaError_t partition_indices(const uint8_t* key, uint8_t want, int64_t n, int32_t* first, int32_t* second,
+                              int32_t* pos, int* count_first, int* count_second, cudaStream_t s, int32_t* ws) {
+  return run_scan(KeyEq{key, want}, WritePartition{first, second, pos}, n, count_first, s, ws, count_second);
 }
 
 int64_t scan_scratch(int64_t n) { return ceil_div(n > 0 ? n : 1, kScanTile); }

@@ -746,9 +746,8 @@ cudaError_t enqueue_build(hsm_plan p, cudaStream_t s, int qt, int* nk) {
   HSM_TRY(cudaGetLastError());
 
   // ---- group lists (ascending node ids) and positions
-  HSM_TRY(select_indices(p->kind, 0, N, p->mon.nodes, p->pos, counts, s, w.scan_ws));
-  HSM_TRY(select_indices(p->kind, 1, N, p->rbf.nodes, p->pos, counts + 1, s, w.scan_ws));
-  k += 6;
+  HSM_TRY(partition_indices(p->kind, 0, N, p->mon.nodes, p->rbf.nodes, p->pos, counts, counts + 1, s, w.scan_ws));
+  k += 3;
   // MON stencils on a side branch of the graph, joined before the read-back
   HSM_TRY(cudaEventRecord(w.ev_fork, s));
   HSM_TRY(cudaStreamWaitEvent(w.side, w.ev_fork, 0));
