@@ -47,12 +47,22 @@ def workload_desc(ns):
 # ---------------------------------------------------------------------------
 # helpers
 # ---------------------------------------------------------------------------
-def rbf_flops(n, m, nops):
+def rbf_flops(n, m, nops, dim=2):
     """Algorithmic FP64 flops of one RBF-FD system (n nodes, m monomials, nops
-    right-hand sides) solved by the null-space method of the FP64 kernel, r = n - m:
-    LU of P with row pivoting, U^T and L1^T triangular solves, [A Z | b],
-    [Z^T A Z | Z^T b], the r x r LU with its substitutions, and w = w_t - X y.
-    Assembly (pair roots, monomials) is not counted."""
+    right-hand sides; dim + 1 operators: the first derivatives and the
+    Laplacian), assembly included.
+    Assembly: offsets and their scaling (2 n dim), pair values r^3 (dim
+    subtractions, dim products, dim - 1 sums, a root and a product per pair),
+    monomials of degree >= 2 (one product each per node), the RHS (2 products
+    per node for each first derivative, 1 for the Laplacian) and the unscaling
+    of the weights (n nops).
+    Solve, by the null-space method of the FP64 kernel, r = n - m: LU of P with
+    row pivoting, U^T and L1^T triangular solves, [A Z | b], [Z^T A Z | Z^T b],
+    the r x r LU with its substitutions, and w = w_t - X y."""
+
+    higher = m - 1 - dim  # monomials of degree >= 2
+    asm = (2 * n * dim + n * (n - 1) // 2 * (3 * dim + 1) + n * max(higher, 0)
+           + n * (2 * (nops - 1) + 1) + n * nops)
     r = n - m
     lu_p = sum((n - k - 1) * (1 + 2 * (m - k - 1)) for k in range(m))
     tri = nops * m * m + (r + nops) * m * (m - 1)
@@ -60,7 +70,7 @@ def rbf_flops(n, m, nops):
     sz = 2 * m * r * (r + nops)
     lu_s = 2.0 / 3.0 * r ** 3 + 2.0 * nops * r ** 2
     out = 2 * m * r * nops
-    return lu_p + tri + bz + sz + lu_s + out
+    return asm + lu_p + tri + bz + sz + lu_s + out
 
 
 class Clocks:
