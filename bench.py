@@ -334,8 +334,10 @@ def run_gpu(args):
                                "before the timed region"},
         }
     stepper = run_stepper(hsm, ns, hyb, d, dev, stream, args) if (rank == 0 and not args.no_extras) else None
+    cond = run_condition(hsm, ns, hyb, dev) if (rank == 0 and not args.no_extras) else None
     if res is not None:
         res["stepper"] = stepper
+        res["condition"] = cond
     hyb.close()
     allr.close()
     if rank == 0:
@@ -344,6 +346,39 @@ def run_gpu(args):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def run_condition(hsm, ns, plan, dev):
+    """Condition numbers kappa_2 of every node's weight system on the timed
+    hybrid set (Section 2.2): MON nodes, RBF-FD nodes, and the demoted
+    regular nodes, which sit where the lattice meets the scattered band."""
+    import numpy as np
+    import torch
+
+    plan.build_stencils()
+    plan.compute_weights(hsm.HSM_PREC_FP64)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    kap = plan.condition()
+    b.record()
+    torch.cuda.synchronize()
+    k = kap.cpu().numpy()
+    # MON nodes are the rows of width 2d+1
+    rp = plan.export_csr(hsm.HSM_LAP)[0]
+    mon = ((rp[1:] - rp[:-1]).cpu().numpy() == 2 * ns.dim + 1)
+    assert int(mon.sum()) == plan.query()["n_mon"]
+    demoted = (ns.is_regular == 1) & ~mon
+
+    def stats(v):
+        v = v[np.isfinite(v)]
+        return {"count": int(v.size), "median": float(np.median(v)) if v.size else None,
+                "p99": float(np.quantile(v, 0.99)) if v.size else None, "max": float(v.max()) if v.size else None}
+
+    return {"workload": "the timed 2D irregular node set; kappa_2 of the scaled weight systems",
+            "ms": a.elapsed_time(b), "mon": stats(k[mon]), "rbf": stats(k[~mon]),
+            "rbf_demoted_regular": stats(k[demoted]), "rbf_scattered": stats(k[~mon & ~demoted]),
+            "singular": int((~np.isfinite(k)).sum())}
 
 
 def run_stepper(hsm, ns, plan, d, dev, stream, args, steps=30):

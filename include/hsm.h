@@ -153,6 +153,16 @@ hsm_status hsm_plan_query(hsm_plan plan, int64_t* nnz_per_op, int64_t* n_mon, in
 hsm_status hsm_plan_export_csr(hsm_plan plan, unsigned op, int64_t* row_ptr, int32_t* col,
                                double* val);
 
+/* Condition number kappa_2(M) = ||M||_2 ||M^-1||_2 of every node's weight
+ * system (Section 2.2, "Computational stability"): the MON matrix P^T of a
+ * regular node, the augmented RBF-FD matrix [A P; P^T 0] of a scattered one,
+ * both in the offsets xi = (x - x_c) / s, s = max |x_i - x_c|.  Eigenvalues
+ * by the cyclic Jacobi method (at most 40 sweeps), one thread per system; a
+ * diagnostic, not on the weight path.  Needs hsm_plan_build_stencils.
+ *   kappa  device f64 [N]; +inf where a system is singular
+ * Enqueued on the plan's stream without synchronisation.                     */
+hsm_status hsm_plan_condition(hsm_plan plan, double* kappa);
+
 /* Mean normal flux of a field over a set of nodes, the average Nusselt number
  * of Section 4.1: out[0] = scale * (1/count) * sum_i |n_i . grad T(x_i)|, the
  * gradient taken with the plan's first-derivative weights (Eq. 1).  The

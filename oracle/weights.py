@@ -189,3 +189,27 @@ def stencil_size(dim, m):
     from math import comb
 
     return 2 * comb(m + dim, m)
+
+
+def condition_numbers(coords, st, m):
+    """2-norm condition numbers kappa(M) = ||M|| ||M^-1|| of every stencil's
+    weight system (Section 2.2, "Computational stability"): the scaled MON
+    matrix P^T of a regular node, the scaled augmented RBF-FD matrix of a
+    scattered one.  Scaling by s = max |x_i - x_c| as for the weights.
+    Returns {"mon": [N_mon], "rbf": [N_rbf]}."""
+    dim = coords.shape[0]
+    ops = ops_for(dim)
+    out = {}
+    if len(st["mon_idx"]):
+        xi, _ = _scaled_offsets(coords, np.asarray(st["mon_idx"]))
+        Mt, _ = mon_system(xi, ops)
+        out["mon"] = np.linalg.cond(Mt, 2)
+    else:
+        out["mon"] = np.zeros(0)
+    if len(st["rbf_idx"]):
+        xi, _ = _scaled_offsets(coords, np.asarray(st["rbf_idx"]))
+        M, _ = rbffd_system(xi, m, ops)
+        out["rbf"] = np.linalg.cond(M, 2)
+    else:
+        out["rbf"] = np.zeros(0)
+    return out

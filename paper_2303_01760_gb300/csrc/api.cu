@@ -346,6 +346,13 @@ hsm_status hsm_apply(hsm_plan p, unsigned op_mask, hsm_dtype in_dtype, const voi
   return launch_apply(p, op_mask, in_dtype, u, out, p->stream);
 }
 
+hsm_status hsm_plan_condition(hsm_plan p, double* kappa) {
+  if (!p) return set_error(nullptr, HSM_EINVAL, "plan is NULL");
+  if (!p->stencils_built) return set_error(p, HSM_ESTATE, "hsm_plan_build_stencils must come first");
+  if (!kappa) return set_error(p, HSM_EINVAL, "kappa is required");
+  return launch_condition(p, kappa);
+}
+
 hsm_status hsm_wall_flux_mean(hsm_plan p, const double* T, const int32_t* nodes, int64_t count,
                               const double* normals, double scale, double* out) {
   if (!p) return set_error(nullptr, HSM_EINVAL, "plan is NULL");

@@ -237,6 +237,7 @@ cudaError_t launch_rbf_external(const RbfExternal& x, bool r32, const int32_t* l
 // ---- apply.cu ------------------------------------------------------------
 hsm_status launch_apply(hsm_plan p, unsigned op_mask, hsm_dtype dt, const void* u, double* out,
                         cudaStream_t s);
+hsm_status launch_condition(hsm_plan p, double* kappa);
 hsm_status launch_wall_flux(hsm_plan p, const double* T, const int32_t* nodes, int64_t count, const double* normals,
                             double scale, double* out);
 

@@ -53,6 +53,7 @@ _SIGS = {
     "hsm_plan_export_csr": (C.c_int, [_p, C.c_uint, _p, _p, _p]),
     "hsm_apply": (C.c_int, [_p, C.c_uint, C.c_int, _p, _p]),
     "hsm_wall_flux_mean": (C.c_int, [_p, _p, _p, _i64, _p, C.c_double, _p]),
+    "hsm_plan_condition": (C.c_int, [_p, _p]),
     "hsm_plan_autotune": (C.c_int, [_p, C.c_char_p]),
     "hsm_plan_destroy": (C.c_int, [_p]),
     "hsm_plan_profile": (C.c_int, [_p, C.POINTER(C.c_float), C.POINTER(_i64)]),
@@ -265,6 +266,15 @@ class Plan:
         if u.dtype not in (torch.float64, torch.float32):
             raise ValueError("u must be float32 or float64")
         check(lib.hsm_apply(self.h, int(op_mask), dt, ptr(u), ptr(out)), self.h)
+        return out
+
+    def condition(self, out=None):
+        """kappa_2 of every node's weight system (Section 2.2), f64 CUDA [N]."""
+        import torch
+
+        if out is None:
+            out = torch.empty(self.N, dtype=torch.float64, device=self._keep[0].device)
+        check(lib.hsm_plan_condition(self.h, ptr(out)), self.h)
         return out
 
     def wall_flux_mean(self, T, nodes, normals, scale=1.0, out=None):
