@@ -207,7 +207,6 @@ hsm_status compute_rbf_weights_fp64(hsm_plan p, const int32_t* list, int64_t cou
 hsm_status compute_rbf_weights_fp32r(hsm_plan p, const int32_t* list, int64_t count, uint8_t* status,
                                      int32_t* fail_list, int* fail_count);
 hsm_status weights_to_f32(hsm_plan p);
-size_t rbf_smem_per_system(int K, int ld, bool fp32);
 
 // Weight systems for caller-supplied stencils, described without a plan
 // (used by the allocation-free entry point in noalloc.cu).

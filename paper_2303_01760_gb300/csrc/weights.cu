@@ -336,8 +336,6 @@ hsm_status launch_rbf(hsm_plan p, bool r32, const int32_t* list, int64_t count, 
 
 }  // namespace
 
-size_t rbf_smem_per_system(int K, int ld, bool fp32) { return smem_bytes(3, 4, fp32, K, ld, kMaxStencil); }
-
 cudaError_t launch_rbf_external(const RbfExternal& x, bool r32, const int32_t* list, int64_t count, uint8_t* status,
                                 uint8_t mark, bool* too_big) {
   *too_big = false;
