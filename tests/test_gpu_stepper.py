@@ -102,3 +102,16 @@ def test_multigrid_pressure_solve_on_the_holes_set():
     assert _rel(g["T"], o["T"]) <= 1e-9
     assert _rel(g["v"], o["v"]) <= 1e-7
     assert max(g["iters"]) < 200
+
+
+def test_3d_steps_match_oracle():
+    """Unit cube minus two spheres (Section 4.3 set-up: Dirichlet spheres,
+    insulated box), m = 2 (n = 20), Ra = 1e4, 10 steps with the multigrid-
+    preconditioned pressure solve: temperature and velocity against the
+    oracle."""
+    ns = nodesets.cube_spheres(n=14, n_holes=2, r_range=(0.1, 0.15), band=0.12, seed=nodesets.SEED_BASE + 21)
+    g, o = _run_both(ns, 1e4, 0.71, 10)
+    eT, ev = _rel(g["T"], o["T"]), _rel(g["v"], o["v"])
+    print(f"3D: T rel err {eT:.3e}  v rel err {ev:.3e}  iters/step {np.mean(g['iters']):.1f}")
+    assert eT <= 1e-9
+    assert ev <= 1e-7
