@@ -309,6 +309,20 @@ hsm_status hsm_mlp_predict(hsm_mlp mlp, const float* X, int64_t count, float* Y)
  * hsm_plan_compute_weights(HSM_PREC_LEARNED).                               */
 hsm_status hsm_mlp_attach(hsm_plan plan, hsm_mlp mlp);
 
+/* Batch validation of HSM_PREC_LEARNED (no paper passage; the learned path's
+ * third fallback rule): `samples` stencils spread evenly over the batch are
+ * solved directly (they keep those weights and status HSM_NODE_LEARNED_SOLVE);
+ * when the mean over the accepted ones of max|w_learned - w_direct| /
+ * max|w_direct| exceeds tol, every stencil of the batch takes the direct
+ * solve.  Defaults: tol 1e-3, samples 512; samples = 0 turns it off.       */
+hsm_status hsm_plan_set_learned_gate(hsm_plan plan, double tol, int64_t samples);
+
+/* Result of the last learned batch's validation (host outputs, any may be
+ * NULL): error (-1 when none was measured), failed (1 when the batch took the
+ * direct solve) and accepted (validated samples that the per-stencil checks
+ * had accepted, the ones the error averages).                               */
+hsm_status hsm_plan_learned_gate(hsm_plan plan, double* error, int* failed, int64_t* accepted);
+
 /* Training data of a plan: for every interior RBF-FD node in ascending node
  * order, its features (X device f32 [count][d n]) and, from the plan's current
  * weights, its labels (Y device f32 [count][nops n], may be NULL).  With X NULL

@@ -242,10 +242,11 @@ hsm_status hsm_plan_compute_weights(hsm_plan p, hsm_prec prec, uint8_t* node_sta
     int32_t* fail_list = nullptr;
     HSM_CUDA(p, dev_alloc(&fail_list, p->rbf.count, s));
     HSM_CUDA(p, cudaMemsetAsync(p->dev_count, 0, sizeof(int), s));
+    int64_t gate_extra = 0;
     if (prec == HSM_PREC_FP32_REFINE)
       st = compute_rbf_weights_fp32r(p, nullptr, p->rbf.count, node_status, fail_list, p->dev_count);
     else
-      st = compute_rbf_weights_learned(p, node_status, fail_list, p->dev_count);
+      st = compute_rbf_weights_learned(p, node_status, fail_list, p->dev_count, &gate_extra);
     if (st != HSM_OK) {
       dev_free(&fail_list, s);
       return st;
@@ -253,7 +254,16 @@ hsm_status hsm_plan_compute_weights(hsm_plan p, hsm_prec prec, uint8_t* node_sta
     int fc = 0;
     HSM_CUDA(p, cudaMemcpyAsync(&fc, p->dev_count, sizeof(int), cudaMemcpyDeviceToHost, s));
     HSM_CUDA(p, cudaStreamSynchronize(s));
-    p->n_fallback = fc;
+    p->n_fallback = fc + gate_extra;
+    if (prec == HSM_PREC_LEARNED && p->gate_failed) {
+      // the batch failed its validation: every stencil takes the direct solve
+      dev_free(&fail_list, s);
+      p->n_fallback = p->rbf.count;
+      st = compute_rbf_weights_fp64_marked(p, nullptr, p->rbf.count, node_status, HSM_NODE_LEARNED_SOLVE);
+      if (st != HSM_OK) return st;
+      fc = 0;
+      fail_list = nullptr;
+    }
     if (fc > 0) {
       st = compute_rbf_weights_fp64_marked(p, fail_list, fc, node_status,
                                            prec == HSM_PREC_FP32_REFINE ? HSM_NODE_REFINE_FP64 : HSM_NODE_LEARNED_SOLVE);
@@ -344,6 +354,22 @@ hsm_status hsm_apply(hsm_plan p, unsigned op_mask, hsm_dtype in_dtype, const voi
   }
   PhaseTimer tm(p, HSM_PHASE_APPLY);
   return launch_apply(p, op_mask, in_dtype, u, out, p->stream);
+}
+
+hsm_status hsm_plan_set_learned_gate(hsm_plan p, double tol, int64_t samples) {
+  if (!p) return set_error(nullptr, HSM_EINVAL, "plan is NULL");
+  if (!(tol >= 0.0) || samples < 0) return set_error(p, HSM_EINVAL, "tol must be >= 0 and samples >= 0");
+  p->gate_tol = tol;
+  p->gate_samples = samples;
+  return HSM_OK;
+}
+
+hsm_status hsm_plan_learned_gate(hsm_plan p, double* error, int* failed, int64_t* accepted) {
+  if (!p) return set_error(nullptr, HSM_EINVAL, "plan is NULL");
+  if (error) *error = p->gate_error;
+  if (failed) *failed = p->gate_failed;
+  if (accepted) *accepted = p->gate_accepted;
+  return HSM_OK;
 }
 
 hsm_status hsm_plan_condition(hsm_plan p, double* kappa) {

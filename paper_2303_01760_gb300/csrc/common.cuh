@@ -111,6 +111,14 @@ struct hsm_plan_s {
   bool weights_built = false;
   hsm::Tuning tune;
   hsm_mlp mlp = nullptr;         // attached learned predictor (not owned)
+  // batch validation of the learned weights: `gate_samples` stencils of the
+  // batch are solved directly; when the mean relative weight error of the
+  // accepted ones exceeds gate_tol, the whole batch takes the direct solve
+  double gate_tol = 1e-3;
+  int64_t gate_samples = 512;    // 0: no batch validation
+  double gate_error = 0.0;       // of the last learned batch (-1: not measured)
+  int gate_failed = 0;
+  int64_t gate_accepted = 0;     // validated samples the per-stencil checks accepted
   std::string last_error;
   hsm::BuildWs ws;               // stencil-build workspace and graph
   int64_t launches = 0;          // kernels launched by this plan
@@ -241,6 +249,9 @@ hsm_status launch_wall_flux(hsm_plan p, const double* T, const int32_t* nodes, i
                             double scale, double* out);
 
 // ---- mlp.cu --------------------------------------------------------------
-hsm_status compute_rbf_weights_learned(hsm_plan p, uint8_t* status, int32_t* fail_list, int* fail_count);
+// Learned weights; *gate_extra receives the number of accepted stencils the
+// batch validation solved directly (they carry direct-solve weights).
+hsm_status compute_rbf_weights_learned(hsm_plan p, uint8_t* status, int32_t* fail_list, int* fail_count,
+                                       int64_t* gate_extra);
 
 }  // namespace hsm

@@ -753,14 +753,20 @@ __global__ void k_features(const double* __restrict__ coords, int64_t N, const i
   }
 }
 
+// Scale and canonical frame of one stencil's features: x = 1/s, (y, z) the
+// first row of the rotation, w the reflection sign.
+struct StencilFrame {
+  double x, y, z, w;
+};
+
 template <int NN>
 __global__ void k_features_infer2d(const double* __restrict__ coords, int64_t N, const int32_t* __restrict__ idx,
                                    int64_t G, const int32_t* __restrict__ list, int64_t count, float* X,
-                                   double4* frame) {
+                                   StencilFrame* frame) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x) {
     double inv, q00, q01, sg;
     features2d<NN>(coords, N, idx, G, list[t], X + t * (2 * NN), inv, q00, q01, sg);
-    frame[t] = make_double4(inv, q00, q01, sg);
+    frame[t] = StencilFrame{inv, q00, q01, sg};
   }
 }
 
@@ -776,9 +782,9 @@ template <int NN>
 __global__ void __launch_bounds__(128) k_project2d(const double* __restrict__ coords, int64_t N,
                                                    const int32_t* __restrict__ idx, int64_t G,
                                                    const int32_t* __restrict__ list, int64_t count,
-                                                   const float* __restrict__ Yp, const double4* __restrict__ frame,
+                                                   const float* __restrict__ Yp, const StencilFrame* __restrict__ frame,
                                                    double tau, double* w, int32_t* fail_list, int* fail_count,
-                                                   uint8_t* status) {
+                                                   uint8_t* status, uint8_t* acc) {
   constexpr int MP = 6;
   // L p at the centre: d/dx -> (0,1,0,0,0,0), d/dy -> (0,0,1,0,0,0),
   // Laplacian -> (0,0,0,2,0,2)
@@ -786,7 +792,7 @@ __global__ void __launch_bounds__(128) k_project2d(const double* __restrict__ co
     const int64_t pos = list[t];
     const int32_t c = idx[pos];
     // scale and frame of the features the prediction was made from
-    const double4 fr = frame[t];
+    const StencilFrame fr = frame[t];
     const double inv = fr.x, q00 = fr.y, q01 = fr.z, q10 = -fr.w * fr.z, q11 = fr.w * fr.y;
     double pj[NN][MP - 1];  // x, y, x^2, xy, y^2 of every node
     const double cx = coords[c], cy = coords[N + c];
@@ -900,6 +906,67 @@ __global__ void __launch_bounds__(128) k_project2d(const double* __restrict__ co
       const int slot = atomicAdd(fail_count, 1);
       fail_list[slot] = (int32_t)pos;
     }
+    if (acc) acc[t] = accept ? 1 : 0;
+  }
+}
+
+// Batch validation (a check the paper does not have): S stencils spread evenly
+// over the learned list; their learned weights are saved, then solved
+// directly in place, then compared.
+__global__ void k_gate_sample(const int32_t* __restrict__ learn, int64_t lc, int S, const uint8_t* __restrict__ acc,
+                              int32_t* sample_pos, uint8_t* sample_acc) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S; i += gridDim.x * blockDim.x) {
+    const int64_t t = (int64_t)i * lc / S;
+    sample_pos[i] = learn[t];
+    sample_acc[i] = acc[t];
+  }
+}
+
+__global__ void k_gate_gather(const double* __restrict__ w, int64_t G, int width, int nops,
+                              const int32_t* __restrict__ sample_pos, int S, double* saved) {
+  const int64_t total = (int64_t)S * width * nops;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / ((int64_t)width * nops));
+    const int64_t r = e - (int64_t)i * width * nops;  // o * width + j
+    saved[e] = w[r * G + sample_pos[i]];
+  }
+}
+
+// Mean over the accepted samples of max|w_learned - w_direct| / max|w_direct|
+// (over all operators and stencil nodes), summed in a fixed order.
+constexpr int kGateThreads = 256;
+__global__ void __launch_bounds__(kGateThreads) k_gate_error(const double* __restrict__ w, int64_t G, int width,
+                                                             int nops, const int32_t* __restrict__ sample_pos,
+                                                             const uint8_t* __restrict__ sample_acc, int S,
+                                                             const double* __restrict__ saved, double* out) {
+  __shared__ double se[kGateThreads];
+  __shared__ int sn[kGateThreads];
+  double acc_e = 0.0;
+  int acc_n = 0;
+  for (int i = threadIdx.x; i < S; i += kGateThreads) {
+    if (!sample_acc[i]) continue;
+    double dmax = 0.0, wmax = 0.0;
+    for (int r = 0; r < width * nops; ++r) {
+      const double wd = w[(int64_t)r * G + sample_pos[i]];
+      dmax = fmax(dmax, fabs(saved[(int64_t)i * width * nops + r] - wd));
+      wmax = fmax(wmax, fabs(wd));
+    }
+    acc_e += wmax > 0.0 ? dmax / wmax : 0.0;
+    ++acc_n;
+  }
+  se[threadIdx.x] = acc_e;
+  sn[threadIdx.x] = acc_n;
+  __syncthreads();
+  for (int h = kGateThreads / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+      se[threadIdx.x] += se[threadIdx.x + h];
+      sn[threadIdx.x] += sn[threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = sn[0] > 0 ? se[0] / sn[0] : 0.0;
+    out[1] = (double)sn[0];
   }
 }
 
@@ -907,18 +974,41 @@ __global__ void k_mark_zero(const int32_t* __restrict__ list, int k, uint8_t* fl
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) flag[list[i]] = 0;
 }
 
-__global__ void k_learned_split(const int32_t* __restrict__ nodes, const uint8_t* __restrict__ is_boundary,
-                                int64_t G, int32_t* learn_list, int* learn_count, int32_t* fail_list, int* fail_count) {
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < G; p += (int64_t)gridDim.x * blockDim.x) {
-    const bool bnd = is_boundary && is_boundary[nodes[p]];
-    if (bnd) fail_list[atomicAdd(fail_count, 1)] = (int32_t)p;
-    else learn_list[atomicAdd(learn_count, 1)] = (int32_t)p;
+__global__ void k_boundary_key(const int32_t* __restrict__ nodes, const uint8_t* __restrict__ is_boundary, int64_t G,
+                               uint8_t* key) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < G; p += (int64_t)gridDim.x * blockDim.x)
+    key[p] = is_boundary && is_boundary[nodes[p]] ? 1 : 0;
+}
+
+// Positions of the RBF-FD group split into interior stencils (learned) and
+// boundary ones (direct solve), both in ascending order, with their counts
+// on the device.
+cudaError_t learned_split(hsm_plan p, int32_t* learn_list, int* learn_count, int32_t* other_list, int* other_count,
+                          cudaStream_t s) {
+  const int64_t G = p->rbf.count;
+  uint8_t* key = nullptr;
+  int32_t* pos = nullptr;
+  cudaError_t e = dev_alloc(&key, G, s);
+  if (e == cudaSuccess) e = dev_alloc(&pos, G, s);
+  if (e == cudaSuccess) {
+    k_boundary_key<<<(int)std::min<int64_t>(ceil_div(G, 256), (int64_t)num_sms() * 8), 256, 0, s>>>(
+        p->rbf.nodes, p->is_boundary, G, key);
+    e = cudaGetLastError();
   }
+  if (e == cudaSuccess) e = partition_indices(key, 0, G, learn_list, other_list, pos, learn_count, other_count, s, nullptr);
+  dev_free(&key, s);
+  dev_free(&pos, s);
+  return e;
 }
 
 }  // namespace
 
-hsm_status compute_rbf_weights_learned(hsm_plan p, uint8_t* status, int32_t* fail_list, int* fail_count) {
+hsm_status compute_rbf_weights_learned(hsm_plan p, uint8_t* status, int32_t* fail_list, int* fail_count,
+                                       int64_t* gate_extra) {
+  *gate_extra = 0;
+  p->gate_error = -1.0;
+  p->gate_failed = 0;
+  p->gate_accepted = 0;
   Mlp& m = p->mlp->m;
   const int dim = p->dim, n = p->n;
   if (m.n_in != n * dim || m.n_out != n * p->nops)
@@ -929,15 +1019,15 @@ hsm_status compute_rbf_weights_learned(hsm_plan p, uint8_t* status, int32_t* fai
   int32_t* learn = nullptr;
   int* lcount = nullptr;
   float *X = nullptr, *Y = nullptr;
-  double4* frame = nullptr;
+  StencilFrame* frame = nullptr;
   int* kinds = nullptr;
+  uint8_t* acc = nullptr;
   HSM_CUDA(p, dev_alloc(&learn, G, s));
   HSM_CUDA(p, dev_alloc(&lcount, 1, s));
   HSM_CUDA(p, cudaMemsetAsync(lcount, 0, sizeof(int), s));
   const int T = 256;
   const int grid = (int)std::min<int64_t>(ceil_div(G, T), (int64_t)num_sms() * 8);
-  k_learned_split<<<grid, T, 0, s>>>(p->rbf.nodes, p->is_boundary, G, learn, lcount, fail_list, fail_count);
-  HSM_CUDA(p, cudaGetLastError());
+  HSM_CUDA(p, learned_split(p, learn, lcount, fail_list, fail_count, s));
   int lc = 0;
   HSM_CUDA(p, cudaMemcpyAsync(&lc, lcount, sizeof(int), cudaMemcpyDeviceToHost, s));
   HSM_CUDA(p, cudaStreamSynchronize(s));
@@ -953,6 +1043,7 @@ hsm_status compute_rbf_weights_learned(hsm_plan p, uint8_t* status, int32_t* fai
     HSM_CUDA(p, dev_alloc(&X, (size_t)lc * n * dim, s));
     HSM_CUDA(p, dev_alloc(&Y, (size_t)lc * n * p->nops, s));
     HSM_CUDA(p, dev_alloc(&frame, lc, s));
+    HSM_CUDA(p, dev_alloc(&acc, lc, s));
     const int gl = (int)std::min<int64_t>(ceil_div(lc, T), (int64_t)num_sms() * 8);
     k_features_infer2d<12><<<gl, T, 0, s>>>(p->coords, p->N, p->rbf.idx, G, learn, lc, X, frame);
     HSM_CUDA(p, cudaGetLastError());
@@ -963,9 +1054,41 @@ hsm_status compute_rbf_weights_learned(hsm_plan p, uint8_t* status, int32_t* fai
     if (st != HSM_OK) return set_error(p, st, m.last_error);
     const int gp = (int)std::min<int64_t>(ceil_div(lc, 128), (int64_t)num_sms() * 16);
     k_project2d<12><<<gp, 128, 0, s>>>(p->coords, p->N, p->rbf.idx, G, learn, lc, Y, frame, 1.5, p->rbf.w64,
-                                       fail_list, fail_count, status);
+                                       fail_list, fail_count, status, acc);
     HSM_CUDA(p, cudaGetLastError());
     p->launches += 4;
+    if (p->gate_samples > 0) {
+      const int S = (int)std::min<int64_t>(lc, p->gate_samples);
+      const int width = n, nops = p->nops;
+      int32_t* spos = nullptr;
+      uint8_t* sacc = nullptr;
+      double *saved = nullptr, *gerr = nullptr;
+      HSM_CUDA(p, dev_alloc(&spos, S, s));
+      HSM_CUDA(p, dev_alloc(&sacc, S, s));
+      HSM_CUDA(p, dev_alloc(&saved, (size_t)S * width * nops, s));
+      HSM_CUDA(p, dev_alloc(&gerr, 2, s));
+      k_gate_sample<<<(S + 255) / 256, 256, 0, s>>>(learn, lc, S, acc, spos, sacc);
+      k_gate_gather<<<(int)std::min<int64_t>(ceil_div((int64_t)S * width * nops, 256), 1024), 256, 0, s>>>(
+          p->rbf.w64, G, width, nops, spos, S, saved);
+      HSM_CUDA(p, cudaGetLastError());
+      // the samples' direct solve, in place (their status: learned -> solve)
+      hsm_status gs = compute_rbf_weights_fp64_marked(p, spos, S, status, HSM_NODE_LEARNED_SOLVE);
+      if (gs != HSM_OK) return gs;
+      k_gate_error<<<1, kGateThreads, 0, s>>>(p->rbf.w64, G, width, nops, spos, sacc, S, saved, gerr);
+      HSM_CUDA(p, cudaGetLastError());
+      double gh[2] = {0.0, 0.0};
+      HSM_CUDA(p, cudaMemcpyAsync(gh, gerr, sizeof(gh), cudaMemcpyDeviceToHost, s));
+      HSM_CUDA(p, cudaStreamSynchronize(s));
+      p->gate_error = gh[0];
+      p->gate_failed = gh[0] > p->gate_tol ? 1 : 0;
+      *gate_extra = (int64_t)gh[1];
+      p->gate_accepted = (int64_t)gh[1];
+      p->launches += 4;
+      dev_free(&spos, s);
+      dev_free(&sacc, s);
+      dev_free(&saved, s);
+      dev_free(&gerr, s);
+    }
   }
   dev_free(&learn, s);
   dev_free(&lcount, s);
@@ -973,6 +1096,7 @@ hsm_status compute_rbf_weights_learned(hsm_plan p, uint8_t* status, int32_t* fai
   dev_free(&Y, s);
   dev_free(&frame, s);
   dev_free(&kinds, s);
+  dev_free(&acc, s);
   return HSM_OK;
 }
 
@@ -999,9 +1123,7 @@ hsm_status hsm_plan_learned_data(hsm_plan p, float* X, float* Y, int64_t* count)
   HSM_CUDA(p, dev_alloc(&cnt, 2, s));
   HSM_CUDA(p, cudaMemsetAsync(cnt, 0, 2 * sizeof(int), s));
   if (G) {
-    k_learned_split<<<(int)std::min<int64_t>(ceil_div(G, 256), (int64_t)num_sms() * 8), 256, 0, s>>>(
-        p->rbf.nodes, p->is_boundary, G, learn, cnt, skip, cnt + 1);
-    HSM_CUDA(p, cudaGetLastError());
+    HSM_CUDA(p, learned_split(p, learn, cnt, skip, cnt + 1, s));
   }
   int lc[2] = {0, 0};
   HSM_CUDA(p, cudaMemcpyAsync(lc, cnt, sizeof(lc), cudaMemcpyDeviceToHost, s));

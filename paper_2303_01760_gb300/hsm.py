@@ -54,6 +54,8 @@ _SIGS = {
     "hsm_apply": (C.c_int, [_p, C.c_uint, C.c_int, _p, _p]),
     "hsm_wall_flux_mean": (C.c_int, [_p, _p, _p, _i64, _p, C.c_double, _p]),
     "hsm_plan_condition": (C.c_int, [_p, _p]),
+    "hsm_plan_set_learned_gate": (C.c_int, [_p, C.c_double, _i64]),
+    "hsm_plan_learned_gate": (C.c_int, [_p, C.POINTER(C.c_double), C.POINTER(C.c_int), C.POINTER(_i64)]),
     "hsm_plan_autotune": (C.c_int, [_p, C.c_char_p]),
     "hsm_plan_destroy": (C.c_int, [_p]),
     "hsm_plan_profile": (C.c_int, [_p, C.POINTER(C.c_float), C.POINTER(_i64)]),
@@ -316,6 +318,17 @@ class Plan:
             Y = torch.empty((cnt.value, nops * n), dtype=torch.float32, device=dev) if labels else None
             check(lib.hsm_plan_learned_data(self.h, ptr(X), ptr(Y), C.byref(cnt)), self.h)
         return X, Y
+
+    def set_learned_gate(self, tol=1e-3, samples=512):
+        """Batch validation of the learned weights (samples = 0 turns it off)."""
+        check(lib.hsm_plan_set_learned_gate(self.h, float(tol), int(samples)), self.h)
+
+    def learned_gate(self):
+        """(mean relative error of the validated samples, batch fell back,
+        accepted samples the error averages)."""
+        e, f, a = C.c_double(), C.c_int(), _i64()
+        check(lib.hsm_plan_learned_gate(self.h, C.byref(e), C.byref(f), C.byref(a)), self.h)
+        return e.value, bool(f.value), a.value
 
     def attach(self, mlp):
         check(lib.hsm_mlp_attach(self.h, mlp.h if mlp is not None else None), self.h)

@@ -77,9 +77,12 @@ def test_learned_weights_end_to_end():
     ns = nodesets.square_all_scattered(n=50, seed=nodesets.SEED_BASE + 63, jitter=0.15)
     plan, code, status = make_plan(ns, m=2, prec=0)
     plan.attach(mlp)
+    # the projection path itself: no batch validation here
+    plan.set_learned_gate(samples=0)
     st = torch.full((ns.N,), 77, dtype=torch.uint8, device="cuda:0")
     code = plan.compute_weights(hsm.HSM_PREC_LEARNED, st)
     assert code == 0
+    assert plan.learned_gate()[:2] == (-1.0, False)
     q = plan.query()
     status = st.cpu().numpy()
     # oracle: stencils, exact weights, and the projection of the GPU's own MLP output
@@ -127,6 +130,74 @@ def test_learned_weights_end_to_end():
           f"lap err learned {err_l[deep].max():.3e} direct {err_d[deep].max():.3e}")
     assert gpu_accept.mean() > 0.5
     assert err_l[deep].max() <= 5.0 * err_d[deep].max()
+    plan.close()
+    mlp.close()
+
+
+def test_learned_batch_gate():
+    """Batch validation of the learned weights: S stencils spread evenly over
+    the interior (learned) positions are solved directly; the mean over the
+    accepted ones of max|w_learned - w_direct| / max|w_direct| is the batch
+    error.  It matches the oracle's value for the same samples and
+    predictions; above the tolerance the whole batch takes the direct solve."""
+    import torch
+    from paper_2303_01760_gb300 import hsm
+
+    Xtr, Ytr = _dataset([nodesets.SEED_BASE + 61])
+    mlp = hsm.MLP(24, H, L, 36, seed=5)
+    mlp.train(Xtr, Ytr, steps=300, batch=1024, lr=1e-3, seed=11)
+    ns = nodesets.square_all_scattered(n=50, seed=nodesets.SEED_BASE + 63, jitter=0.15)
+    stn = ost.build_stencils(ns.coords, ns.is_regular, ns.is_boundary, ns.h, 12, normals=ns.normals)
+    inner = ns.is_boundary[stn["rbf_nodes"]] == 0
+    learn_pos = np.flatnonzero(inner)          # interior positions of the RBF-FD group, ascending
+    W_all = ow.rbffd_weights(ns.coords, stn["rbf_idx"], 2)
+    S = 64
+    samp = learn_pos[(np.arange(S) * len(learn_pos)) // S]
+
+    # a loose tolerance: the batch passes; the samples carry the direct weights
+    plan, _, _ = make_plan(ns, m=2, prec=0)
+    plan.attach(mlp)
+    plan.set_learned_gate(tol=10.0, samples=S)
+    st = torch.full((ns.N,), 77, dtype=torch.uint8, device="cuda:0")
+    assert plan.compute_weights(hsm.HSM_PREC_LEARNED, st) == 0
+    err, failed, n_acc = plan.learned_gate()
+    assert not failed
+    Xte, _ = plan.learned_data(labels=False)
+    Ypred = mlp.predict(Xte).double().cpu().numpy()
+    w_proj, accept = ol.learned_weights(ns.coords, stn["rbf_idx"][inner], 2, Ypred)
+    k = np.searchsorted(learn_pos, samp)       # the samples' rows among the learned stencils
+    ok = accept[k]
+    rel = np.stack([np.abs(w_proj[op][k] - W_all[op][samp]).max(1) for op in ("dx", "dy", "lap")]).max(0)
+    den = np.stack([np.abs(W_all[op][samp]).max(1) for op in ("dx", "dy", "lap")]).max(0)
+    ref_err = float(np.mean((rel / den)[ok]))
+    if n_acc == int(ok.sum()):
+        # the same samples on both sides (the acceptance rule agrees)
+        assert abs(err - ref_err) <= 1e-7 * ref_err
+    else:
+        assert abs(n_acc - int(ok.sum())) <= 2 and abs(err / ref_err - 1.0) <= 0.2
+    status = st.cpu().numpy()
+    nodes = stn["rbf_nodes"]
+    assert np.all(status[nodes[samp[ok]]] == hsm.HSM_NODE_LEARNED_SOLVE)
+    assert plan.query()["n_fallback"] == int(np.sum(status == hsm.HSM_NODE_LEARNED_SOLVE))
+    plan.close()
+
+    # the default tolerance (1e-3): this briefly trained predictor fails it,
+    # and every RBF-FD stencil carries the direct-solve weights
+    plan, _, _ = make_plan(ns, m=2, prec=0)
+    plan.attach(mlp)
+    plan.set_learned_gate(samples=S)
+    st = torch.full((ns.N,), 77, dtype=torch.uint8, device="cuda:0")
+    assert plan.compute_weights(hsm.HSM_PREC_LEARNED, st) == 0
+    err2, failed2, _ = plan.learned_gate()
+    assert failed2 and err2 == err and err2 > 1e-3
+    status = st.cpu().numpy()
+    assert np.all(status[nodes] == hsm.HSM_NODE_LEARNED_SOLVE)
+    assert plan.query()["n_fallback"] == len(nodes)
+    for op, bit in (("dx", 1), ("dy", 2), ("lap", 8)):
+        rp, col, val = [t.cpu().numpy() for t in plan.export_csr(bit)]
+        ix = rp[nodes][:, None] + np.arange(12)[None, :]
+        e = np.abs(val[ix] - W_all[op]).max(1) / np.abs(W_all[op]).max(1)
+        assert e.max() <= 1e-10
     plan.close()
     mlp.close()
 
