@@ -936,17 +936,64 @@ def run_dvd(args):
     print(json.dumps(out))
 
 
-PAPER_3D = {"Nu": 6.91, "hours": 20.54, "N": 74137}  # Section 4.3, Table 3 (hybrid)
+PAPER_2D_REFINED = {"hybrid": {"Nu": 12.36, "minutes": 29.11, "N": 11535},
+                    "scattered": {"Nu": 12.32, "minutes": 46.31, "N": 10534}}  # Section 4.2, Table 2
+PAPER_3D = {"hybrid": {"Nu": 6.91, "hours": 20.54, "N": 74137},
+            "scattered": {"Nu": 7.36, "hours": 48.12, "N": 65526}}  # Section 4.3, Table 3
+REFINED_2D = dict(n=100, n_holes=4, r_range=(0.06, 0.12), ratio=3.0, seed=20230351)
+REFINED_3D = dict(dim=3, n=40, n_holes=4, r_range=(0.08, 0.16), delta_h=4.0, ratio=2.0, seed=20230341)
 
 
-def run_spheres3d(args):
-    """Natural convection in the unit cube minus 4 seeded spheres (the shape of
-    Section 4.3: two spheres at T_C = 0, two at T_H = 1, insulated box),
-    Ra = 1e4, Pr = 0.71, lattice h = 1/n, dt = 0.1 (h/2)^2 / 2 (the paper's time
-    step, set by its spacing h/2 at the spheres), from rest to t = args.t_end,
-    with the average Nusselt number on the cold spheres.  The paper's spheres
-    are random and unpublished and its node spacing is refined towards them,
-    so its Nu is context only.  Prints one JSON line (a validation run)."""
+def _refined_dev(ns, dev, reg=None):
+    import numpy as np
+    import torch
+
+    d = {k: torch.from_numpy(np.ascontiguousarray(getattr(ns, k))).to(dev)
+         for k in ("coords", "is_regular", "is_boundary", "normals", "bc", "T_bc", "spacing")}
+    if reg is not None:
+        d["is_regular"] = reg
+    return d
+
+
+def _time_steps(hsm, plan, ns, d, dev, n_steps, Ra, dt, cold=None):
+    """n_steps explicit Boussinesq steps from rest; returns ms/step (CUDA
+    events), Krylov iterations per step and, with ``cold``, the final mean
+    |dT/dn| on those nodes."""
+    import numpy as np
+    import torch
+
+    st = hsm.Stepper(plan, Ra, 0.71, dt, ns.T_ref, d["bc"], d["T_bc"], d["normals"], krylov_tol=1e-10,
+                     krylov_max_it=4000)
+    v = torch.zeros((ns.dim, ns.N), dtype=torch.float64, device=dev)
+    T = torch.where(d["bc"] == 1, d["T_bc"], torch.zeros_like(d["T_bc"])).contiguous()
+    p = torch.zeros(ns.N, dtype=torch.float64, device=dev)
+    st.step(v, T, p, 3, allow_notconv=True)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    its, _ = st.step(v, T, p, n_steps, allow_notconv=True)
+    ev[1].record()
+    torch.cuda.synchronize()
+    out = {"ms_per_step": ev[0].elapsed_time(ev[1]) / n_steps, "krylov_iters_per_step": float(np.mean(its)),
+           "max_speed": float(v.abs().max().item()),
+           "finite": bool(torch.isfinite(T).all() and torch.isfinite(v).all())}
+    if cold is not None:
+        cd = torch.from_numpy(cold).to(dev)
+        out["nu_cold"] = float(plan.wall_flux_mean(T, cd, d["normals"]).item())
+    st.close()
+    return out
+
+
+def run_refined(args):
+    """h-refinement and the width of the scattered layer (Section 4.2 and its
+    delta_h study): unit square minus 4 seeded circular holes (standing in for
+    the ducks), h_r = 0.01, spacing falling linearly to h_s = h_r/3 at the
+    holes over h_r * delta_h, which is also the layer width; delta_h swept over
+    2..32, plus the fully scattered set with the same refinement.  Per set:
+    node counts, the operator pass (stencils + FP64 weights + one apply of
+    dx, dy, Laplacian) of the set and of the same nodes all RBF-FD, the
+    operator error on u = sin(pi x) cos(pi y), and the explicit step
+    (Ra = 1e6, dt = 0.1 h_s^2 / 2).  Prints one JSON line."""
     import numpy as np
     import torch
 
@@ -956,49 +1003,185 @@ def run_spheres3d(args):
     from paper_2303_01760_gb300 import hsm, nodesets
 
     dev = torch.device("cuda:0")
-    ns = nodesets.cube_spheres(n=args.spheres3d, n_holes=4, r_range=(0.08, 0.16), band=0.05,
-                               seed=nodesets.SEED_BASE + 40)
-    d = {k: torch.from_numpy(np.ascontiguousarray(getattr(ns, k))).to(dev)
-         for k in ("coords", "is_regular", "is_boundary", "normals", "bc", "T_bc")}
-    t0 = time.time()
-    plan = hsm.Plan(d["coords"], d["is_regular"], d["is_boundary"], ns.h, m=2, normals=d["normals"])
-    plan.build_stencils()
-    plan.compute_weights(hsm.HSM_PREC_FP64)
-    q = plan.query()
-    dt = 0.1 * (ns.h / 2) ** 2 / 2.0
-    st = hsm.Stepper(plan, 1e4, 0.71, dt, ns.T_ref, d["bc"], d["T_bc"], d["normals"], krylov_tol=1e-10,
-                     krylov_max_it=4000)
-    v = torch.zeros((3, ns.N), dtype=torch.float64, device=dev)
-    T = torch.where(d["bc"] == 1, d["T_bc"], torch.zeros_like(d["T_bc"])).contiguous()
-    p = torch.zeros(ns.N, dtype=torch.float64, device=dev)
-    on_sphere = (ns.is_boundary == 1) & (ns.bc == 1)
-    cold = np.flatnonzero(on_sphere & (ns.T_bc == 0.0)).astype(np.int32)
-    cold_d = torch.from_numpy(cold).to(dev)
-    n_steps = int(round(args.t_end / dt))
-    chunk = max(1, n_steps // 100)
-    series, iters, done, worst = [], 0, 0, 0
-    torch.cuda.synchronize()
-    t_run = time.time()
-    while done < n_steps:
-        k = min(chunk, n_steps - done)
-        its, code = st.step(v, T, p, k, allow_notconv=True)
-        iters += sum(its)
-        worst = max(worst, max(its))
-        done += k
-        series.append([round(done * dt, 6), float(plan.wall_flux_mean(T, cold_d, d["normals"]).item())])
-    torch.cuda.synchronize()
-    wall = time.time() - t_run
-    out = {"spheres3d": {"n": args.spheres3d, "h": ns.h, "N": int(ns.N), "n_mon": int(q["n_mon"]),
-                         "n_scattered": int(ns.n_scattered), "spheres": np.round(ns.holes, 4).tolist(),
-                         "Ra": 1e4, "Pr": 0.71, "dt": dt, "t_end": args.t_end, "steps": n_steps,
-                         "krylov_iters_per_step": iters / n_steps, "krylov_iters_max": worst},
-           "nu_cold_final": series[-1][1], "nu_last_tenth_spread": float(np.ptp([x[1] for x in series[-10:]])),
-           "max_speed": float(v.abs().max().item()), "finite": bool(torch.isfinite(T).all() and torch.isfinite(v).all()),
-           "run_s": wall, "ms_per_step": 1e3 * wall / n_steps, "setup_s": t_run - t0, "paper": PAPER_3D,
-           "nu_series": series}
-    st.close()
-    plan.close()
+    rows = []
+    for dh, full in [(2.0, False), (4.0, False), (8.0, False), (16.0, False), (32.0, False), (4.0, True)]:
+        ns = nodesets.cached(nodesets.holes_refined, delta_h=dh, all_scattered=full, **REFINED_2D)
+        d = _refined_dev(ns, dev)
+        u, ex = nodesets.field_sincos(ns.coords)
+        ut = torch.from_numpy(u).to(dev)
+        inner = ns.is_boundary == 0
+        row = {"delta_h": dh, "layout": "scattered" if full else "hybrid", "N": int(ns.N),
+               "n_scattered": int(ns.n_scattered), "n_regular": int(ns.N - ns.n_scattered)}
+        for name, reg in (("set", None), ("all_rbffd", torch.zeros_like(d["is_regular"]))):
+            if full and name == "all_rbffd":
+                continue
+            dd = dict(d, is_regular=d["is_regular"] if reg is None else reg)
+            plan = hsm.Plan(dd["coords"], dd["is_regular"], dd["is_boundary"], ns.h, m=2, normals=dd["normals"],
+                            spacing=dd["spacing"])
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            times = []
+            for it in range(args.warmup + args.steps):
+                torch.cuda.synchronize()
+                ev[0].record()
+                plan.build_stencils()
+                plan.compute_weights(hsm.HSM_PREC_FP64)
+                out = plan.apply(ut)
+                ev[1].record()
+                torch.cuda.synchronize()
+                if it >= args.warmup:
+                    times.append(ev[0].elapsed_time(ev[1]))
+            q = plan.query()
+            o = out.cpu().numpy()
+            err = {op: float(np.abs(o[k, inner] - ex[op][inner]).max() / np.abs(ex[op][inner]).max())
+                   for k, op in enumerate(("dx", "dy", "lap"))}
+            row[name] = {"ms": float(np.median(times)), "n_mon": int(q["n_mon"]), "rel_err": err}
+            if name == "set":
+                cold = np.flatnonzero((ns.is_boundary == 1) & (ns.bc == nodesets.BC_T_DIRICHLET)
+                                      & (ns.T_bc == 0.0)).astype(np.int32)
+                dt = 0.1 * float(ns.spacing.min()) ** 2 / 2.0
+                row["step"] = _time_steps(hsm, plan, ns, dd, dev, args.refined_steps, 1e6, dt, cold)
+                row["step"]["dt"] = dt
+            plan.close()
+        if "all_rbffd" in row:
+            row["operator_speedup_vs_all_rbffd"] = row["all_rbffd"]["ms"] / row["set"]["ms"]
+        rows.append(row)
+        print(json.dumps(row), file=sys.stderr)
+    h4 = next(r for r in rows if r["delta_h"] == 4.0 and r["layout"] == "hybrid")
+    s4 = next(r for r in rows if r["layout"] == "scattered")
+    out = {"refined": {"domain": "unit square minus 4 circular holes (r 0.06-0.12), h_r = 0.01, h_s = h_r/3",
+                       "Ra": 1e6, "Pr": 0.71, "steps_timed": args.refined_steps, "sets": rows},
+           "delta_h_4": {"N_hybrid": h4["N"], "N_scattered": s4["N"],
+                         "step_ms_hybrid": h4["step"]["ms_per_step"], "step_ms_scattered": s4["step"]["ms_per_step"],
+                         "step_time_ratio_hybrid_over_scattered":
+                             h4["step"]["ms_per_step"] / s4["step"]["ms_per_step"],
+                         "paper": PAPER_2D_REFINED,
+                         "paper_time_ratio": PAPER_2D_REFINED["hybrid"]["minutes"]
+                         / PAPER_2D_REFINED["scattered"]["minutes"]}}
     print(json.dumps(out))
+
+
+def run_spheres3d(args):
+    """Natural convection in the unit cube minus 4 seeded spheres (Section 4.3:
+    two spheres at T_C = 0, two at T_H = 1, insulated box, Ra = 1e4,
+    Pr = 0.71), h_r = 1/n, spacing falling linearly to h_s = h_r/2 at the
+    spheres over 4 h_r (delta_h = 4), dt = 0.1 h_s^2 / 2 (7.8125e-6 at
+    n = 40, the paper's step).  Hybrid and fully scattered sets, each run from
+    rest for ``--t-end`` time units (or ``--spheres3d-steps`` steps), with the
+    average Nusselt number on the cold spheres.  The paper's spheres are random
+    and unpublished, so its Nu and hours are context.  Prints one JSON line."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2303_01760_gb300 import hsm, nodesets
+
+    dev = torch.device("cuda:0")
+    cfg = dict(REFINED_3D, n=args.spheres3d)
+    out = {"spheres3d": {"n": args.spheres3d, "h_r": 1.0 / args.spheres3d, "Ra": 1e4, "Pr": 0.71},
+           "paper": PAPER_3D}
+    for layout in ("hybrid", "scattered"):
+        ns = nodesets.cached(nodesets.holes_refined, all_scattered=layout == "scattered", **cfg)
+        d = _refined_dev(ns, dev)
+        t0 = time.time()
+        plan = hsm.Plan(d["coords"], d["is_regular"], d["is_boundary"], ns.h, m=2, normals=d["normals"],
+                        spacing=d["spacing"])
+        plan.build_stencils()
+        plan.compute_weights(hsm.HSM_PREC_FP64)
+        q = plan.query()
+        dt = 0.1 * float(ns.spacing.min()) ** 2 / 2.0
+        n_steps = args.spheres3d_steps if args.t_end is None else int(round(args.t_end / dt))
+        cold = np.flatnonzero((ns.is_boundary == 1) & (ns.bc == nodesets.BC_T_DIRICHLET)
+                              & (ns.T_bc == 0.0)).astype(np.int32)
+        setup = time.time() - t0
+        r = _time_steps(hsm, plan, ns, d, dev, n_steps, 1e4, dt, cold)
+        plan.close()
+        r.update({"N": int(ns.N), "n_mon": int(q["n_mon"]), "n_scattered": int(ns.n_scattered), "dt": dt,
+                  "steps": n_steps, "t_reached": n_steps * dt, "setup_s": setup,
+                  "hours_per_time_unit": r["ms_per_step"] * (1.0 / dt) / 3.6e6})
+        out[layout] = r
+    out["time_ratio_hybrid_over_scattered"] = out["hybrid"]["ms_per_step"] / out["scattered"]["ms_per_step"]
+    out["paper_time_ratio"] = PAPER_3D["hybrid"]["hours"] / PAPER_3D["scattered"]["hours"]
+    print(json.dumps(out))
+
+
+# band widths of square_holes (h = 0.002, 8 holes) whose scattered fraction is
+# within 1 % of 5 / 20 / 50 %, found by bisecting the band on the host
+SWEEP_BANDS = {0.05: 0.02344, 0.20: 0.07031, 0.50: 0.12891}
+
+
+def run_sweep(args):
+    """The 2D irregular configuration with the scattered fraction swept over
+    about 5 / 13 (the nominal 0.05 band) / 20 / 50 / 100 %, for m = 2 (n = 12)
+    and m = 4 (n = 30), FP64 weights.  Per set: the operator pass (stencils +
+    weights + one apply of dx, dy, Laplacian; L2 flushed before each rep) and
+    the apply alone, nodes/s, the same nodes all RBF-FD, the combined rate
+    N S / (T_w + S T_a) for S = 2000 steps, and for m = 2 the explicit step
+    (Ra = 1e6).  Prints one JSON line."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2303_01760_gb300 import hsm, nodesets
+
+    dev = torch.device("cuda:0")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    S = 2000
+    sets = [("5%", SWEEP_BANDS[0.05]), ("nominal", 0.05), ("20%", SWEEP_BANDS[0.20]), ("50%", SWEEP_BANDS[0.50]),
+            ("100%", None)]
+    rows = []
+    for label, band in sets:
+        ns = nodesets.cached(nodesets.square_holes) if label in ("nominal", "100%") else \
+            nodesets.cached(nodesets.square_holes, band=band)
+        d = {k: torch.from_numpy(np.ascontiguousarray(getattr(ns, k))).to(dev)
+             for k in ("coords", "is_regular", "is_boundary", "normals", "bc", "T_bc")}
+        if label == "100%":
+            d["is_regular"] = torch.zeros_like(d["is_regular"])
+        u = torch.from_numpy(nodesets.field_sincos(ns.coords)[0]).to(dev)
+        out = torch.empty((3, ns.N), dtype=torch.float64, device=dev)
+        row = {"set": label, "band": band, "N": int(ns.N),
+               "scattered_fraction": 1.0 if label == "100%" else round(ns.n_scattered / ns.N, 4)}
+        for m in (2, 4):
+            plan = hsm.Plan(d["coords"], d["is_regular"], d["is_boundary"], ns.h, m=m, normals=d["normals"])
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            tw, ta = [], []
+            for it in range(args.warmup + args.steps):
+                flush.fill_(it)
+                ev[0].record()
+                plan.build_stencils()
+                plan.compute_weights(hsm.HSM_PREC_FP64)
+                ev[1].record()
+                flush.fill_(it + 1)
+                ev[2].record()
+                plan.apply(u, out=out)
+                ev[3].record()
+                torch.cuda.synchronize()
+                if it >= args.warmup:
+                    tw.append(ev[0].elapsed_time(ev[1]))
+                    ta.append(ev[2].elapsed_time(ev[3]))
+            Tw, Ta = float(np.median(tw)), float(np.median(ta))
+            q = plan.query()
+            r = {"n": plan.n, "n_mon": int(q["n_mon"]), "weights_ms": Tw, "apply_ms": Ta,
+                 "nodes_per_s_weights": ns.N / (Tw * 1e-3), "nodes_per_s_apply": ns.N / (Ta * 1e-3),
+                 "nodes_per_s_combined": ns.N * S / ((Tw + S * Ta) * 1e-3)}
+            if m == 2:
+                dt = 0.1 * ns.h * ns.h / 2.0
+                r["step"] = _time_steps(hsm, plan, ns, d, dev, args.sweep_steps, 1e6, dt)
+            plan.close()
+            row[f"m{m}"] = r
+        rows.append(row)
+        print(json.dumps(row), file=sys.stderr)
+    full = rows[-1]
+    for row in rows:
+        for m in (2, 4):
+            # throughput (nodes/s) relative to the all-RBF-FD set
+            row[f"m{m}"]["combined_vs_all_rbffd"] = (row[f"m{m}"]["nodes_per_s_combined"]
+                                                     / full[f"m{m}"]["nodes_per_s_combined"])
+    print(json.dumps({"sweep": {"workload": "unit square minus 8 holes, lattice h = 0.002, scattered band swept",
+                                "S": S, "sets": rows}}))
 
 
 def main():
@@ -1020,14 +1203,24 @@ def main():
     ap.add_argument("--layout", default="hybrid", choices=["hybrid", "scattered", "regular"], help="with --dvd")
     ap.add_argument("--t-end", type=float, default=None, help="with --dvd (default 0.15) or --spheres3d (default 1)")
     ap.add_argument("--spheres3d", type=int, default=0, help="3D natural-convection validation run on a 1/n lattice")
+    ap.add_argument("--spheres3d-steps", type=int, default=2000, help="with --spheres3d when --t-end is not given")
+    ap.add_argument("--refined", action="store_true", help="h-refinement / scattered-layer width sweep (2D)")
+    ap.add_argument("--refined-steps", type=int, default=500, help="with --refined")
+    ap.add_argument("--sweep", action="store_true", help="scattered-fraction sweep (5..100 %%), m = 2 and 4")
+    ap.add_argument("--sweep-steps", type=int, default=100, help="with --sweep: explicit steps timed per set")
     args = ap.parse_args()
     if args.dvd:
         args.t_end = 0.15 if args.t_end is None else args.t_end
         run_dvd(args)
         return
     if args.spheres3d:
-        args.t_end = 1.0 if args.t_end is None else args.t_end
         run_spheres3d(args)
+        return
+    if args.refined:
+        run_refined(args)
+        return
+    if args.sweep:
+        run_sweep(args)
         return
     if args.kernels:
         run_kernels(args)

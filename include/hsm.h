@@ -115,12 +115,26 @@ hsm_status hsm_plan_create(hsm_plan* out, int dim, int64_t n_nodes, const double
                            const double* normals, double h_regular, int aug_m, int stencil_n,
                            unsigned op_mask, void* cuda_stream);
 
+/* Sets the local internodal distance h(x_i) of an h-refined node set (Section
+ * 4.2: the spacing decreases linearly from h_r on the regular nodes to h_s at
+ * the irregular boundary; Section 4.3 likewise in 3D).  It only moves the
+ * search point of boundary stencils, which becomes x_c - h(x_c) * n_c: one
+ * LOCAL spacing inside, so that a boundary node in a refined layer keeps the
+ * nodes around it in its stencil.
+ *   spacing  device f64 [N], every entry > 0, or NULL to restore h_regular;
+ *            caller-owned, must stay valid while the plan is used
+ * Takes effect at the next hsm_plan_build_stencils; stencils and weights
+ * built before must be rebuilt.  Nothing is checked on the device; returns
+ * HSM_EINVAL only for a NULL plan.                                           */
+hsm_status hsm_plan_set_spacing(hsm_plan plan, const double* spacing);
+
 /* Builds every stencil (Section 2, "a set of n neighbouring nodes"):
  *   MON nodes: {c, c-e1, c+e1, c-e2, c+e2[, c-e3, c+e3]} through the lattice;
  *   RBF-FD nodes: the n nodes of smallest (squared distance, node id), the
  *   squared distance summed in coordinate order in FP64 without fused
  *   multiply-add; boundary nodes: the node, then the n-1 interior nodes of
- *   smallest (squared distance to x_c - h n_c, node id).  A regular-flagged
+ *   smallest (squared distance to x_c - h n_c, node id), h = h_regular or the
+ *   node's entry of hsm_plan_set_spacing.  A regular-flagged
  *   node that is a boundary node, is not on the lattice, or misses a lattice
  *   neighbour is demoted to RBF-FD.
  * Synchronises the plan's stream (the group sizes are read back).           */

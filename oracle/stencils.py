@@ -14,7 +14,10 @@ nodes".  Readings taken where the paper is silent:
 * A boundary node's stencil is the node itself followed by the n-1 interior
   (non-boundary) nodes nearest to the point q = x_c - h n_c one lattice
   spacing inside along the outward normal n_c, ordered by the same key with d2
-  measured from q (q_k = x_ck - (h * n_ck), no fused multiply-add).  Boundary
+  measured from q (q_k = x_ck - (h * n_ck), no fused multiply-add).  On an
+  h-refined node set (Sections 4.2 and 4.3: the internodal distance h(x)
+  falls towards the irregular boundary) h is the local spacing h(x_c), so the
+  search point stays one local spacing inside.  Boundary
   stencils serve only the normal-derivative rows of the Neumann conditions.
   Keeping other boundary nodes out of them makes each such row hold exactly
   after an explicit update (with boundary neighbours the explicit closure
@@ -72,8 +75,10 @@ def knn_bruteforce(coords, centers, n):
 
 
 def inward_point(coords, normals, h, c):
-    """q = x_c - (h * n_c), evaluated per coordinate without fused multiply-add."""
-    return np.array([coords[k, c] - (h * normals[k, c]) for k in range(coords.shape[0])])
+    """q = x_c - (h * n_c), evaluated per coordinate without fused multiply-add;
+    ``h`` is a scalar or a per-node spacing array (then h = h[c])."""
+    hc = float(h[c]) if np.ndim(h) else h
+    return np.array([coords[k, c] - (hc * normals[k, c]) for k in range(coords.shape[0])])
 
 
 def boundary_bruteforce(coords, normals, h, centers, n, interior):
@@ -195,8 +200,11 @@ def mon_stencils(coords, is_regular, is_boundary, h):
     return np.array(nodes, dtype=np.int64), idx, np.array(demoted, dtype=np.int64)
 
 
-def build_stencils(coords, is_regular, is_boundary, h, n, centers=None, use_kdtree=None, normals=None):
-    """All stencils of a node set (or of the subset ``centers``).
+def build_stencils(coords, is_regular, is_boundary, h, n, centers=None, use_kdtree=None, normals=None,
+                   spacing=None):
+    """All stencils of a node set (or of the subset ``centers``).  ``spacing``
+    (optional, [N]) is the local internodal distance of an h-refined set; it
+    replaces h in the search point of boundary stencils.
 
     Returns dict with
       mon_nodes, mon_idx   nodes that use MON and their 2d+1 stencil
@@ -227,6 +235,7 @@ def build_stencils(coords, is_regular, is_boundary, h, n, centers=None, use_kdtr
         if normals is None:
             raise ValueError("boundary nodes need their normals")
         bk = boundary_kdtree if use_kdtree else boundary_bruteforce
-        rbf_idx[on_bnd] = bk(coords, normals, h, rbf_nodes[on_bnd], n, np.asarray(is_boundary) == 0)
+        hb = h if spacing is None else np.asarray(spacing, dtype=np.float64)
+        rbf_idx[on_bnd] = bk(coords, normals, hb, rbf_nodes[on_bnd], n, np.asarray(is_boundary) == 0)
     return dict(mon_nodes=mon_nodes, mon_idx=mon_idx, rbf_nodes=rbf_nodes, rbf_idx=rbf_idx,
                 demoted=demoted)

@@ -164,6 +164,14 @@ hsm_status hsm_plan_destroy(hsm_plan p) {
   return HSM_OK;
 }
 
+hsm_status hsm_plan_set_spacing(hsm_plan p, const double* spacing) {
+  if (!p) return set_error(nullptr, HSM_EINVAL, "plan is NULL");
+  p->spacing = spacing;
+  p->stencils_built = false;
+  p->weights_built = false;
+  return HSM_OK;
+}
+
 hsm_status hsm_plan_set_timing(hsm_plan p, int enable) {
   if (!p) return set_error(nullptr, HSM_EINVAL, "plan is NULL");
   p->timing = enable != 0;

@@ -70,6 +70,7 @@ struct BuildWs {
   int* readback = nullptr;             // pinned host: demoted, n_mon, n_rbf, flags
   cudaGraphExec_t graph = nullptr;
   int graph_qt = 0;                    // kNN variant the graph was captured with
+  const double* graph_spacing = nullptr;  // spacing array the graph was captured with
   int graph_kernels = 0;               // kernels per replay
   cudaStream_t cap = nullptr;
   cudaStream_t side = nullptr;         // capture branch of the MON stencils
@@ -86,6 +87,7 @@ struct hsm_plan_s {
   const uint8_t* is_regular = nullptr;
   const uint8_t* is_boundary = nullptr;
   const double* normals = nullptr;
+  const double* spacing = nullptr;  // local internodal distance [N] (NULL: h everywhere)
   double h = 0.0;
   int m = 2;
   int n = 12;

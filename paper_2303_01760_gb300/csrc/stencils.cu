@@ -436,6 +436,7 @@ template <int DIM, int QT>
 __global__ void __launch_bounds__(32 * QT) k_knn(const double* __restrict__ coords, int64_t N,
                                              const uint8_t* __restrict__ is_boundary,
                                              const double* __restrict__ normals, double h,
+                                             const double* __restrict__ spacing,
                                              const int32_t* __restrict__ queries, const int* __restrict__ nq_dev,
                                              int n_full, const CellGrid* __restrict__ cgp,
                                              const int32_t* __restrict__ start, const int32_t* __restrict__ sorted_id,
@@ -459,10 +460,12 @@ __global__ void __launch_bounds__(32 * QT) k_knn(const double* __restrict__ coor
     const int n = bnd_center ? n_full - 1 : n_full;
     double q[DIM];
     int cq[DIM];
+    // one local spacing inside: h(x_c) of a refined node set, else h
+    const double hc = (bnd_center && spacing) ? spacing[c] : h;
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
       q[k] = coords[k * N + c];
-      if (bnd_center && normals) q[k] = __dsub_rn(q[k], __dmul_rn(h, normals[k * N + c]));
+      if (bnd_center && normals) q[k] = __dsub_rn(q[k], __dmul_rn(hc, normals[k * N + c]));
       cq[k] = cg.cell_of(q[k], k);
     }
     int cnt = 0;
@@ -787,6 +790,7 @@ cudaError_t enqueue_build(hsm_plan p, cudaStream_t s, int qt, int* nk) {
     const uint8_t* isb = p->is_boundary;
     const double* nrm = p->normals;
     double hh = p->h;
+    const double* spc = p->spacing;
     const int32_t* qlist = p->rbf.nodes;
     const int* nqd = counts + 1;
     int nf = p->n;
@@ -797,8 +801,8 @@ cudaError_t enqueue_build(hsm_plan p, cudaStream_t s, int qt, int* nk) {
     int32_t* sid = w.sorted_id;
     double* sxyz = w.sorted_xyz;
     uint8_t* sb = w.sorted_bnd;
-    void* args[] = {(void*)&coords, (void*)&NN, (void*)&isb, (void*)&nrm, (void*)&hh, (void*)&qlist, (void*)&nqd,
-                    (void*)&nf, (void*)&cgd, (void*)&cs, (void*)&sid, (void*)&sxyz,
+    void* args[] = {(void*)&coords, (void*)&NN, (void*)&isb, (void*)&nrm, (void*)&hh, (void*)&spc, (void*)&qlist,
+                    (void*)&nqd, (void*)&nf, (void*)&cgd, (void*)&cs, (void*)&sid, (void*)&sxyz,
                     (void*)&sb, (void*)&outp, (void*)&fl};
     HSM_TRY(cudaLaunchKernel(fn, dim3(gk), dim3(KT), args, smem, s));
     ++k;
@@ -824,7 +828,7 @@ hsm_status build_stencils(hsm_plan p) {
   BuildWs& w = p->ws;
   cudaStream_t s = p->stream;
   const int qt = p->tune.knn_qt == 4 ? 4 : (p->tune.knn_qt == 2 ? 2 : 1);
-  if (!w.graph || w.graph_qt != qt) {
+  if (!w.graph || w.graph_qt != qt || w.graph_spacing != p->spacing) {
     if (w.graph) cudaGraphExecDestroy(w.graph);
     w.graph = nullptr;
     // kernel attributes are set outside the capture
@@ -848,6 +852,7 @@ hsm_status build_stencils(hsm_plan p) {
       HSM_CUDA(p, e);
     }
     w.graph_qt = qt;
+    w.graph_spacing = p->spacing;
     w.graph_kernels = nk;
   }
   HSM_CUDA(p, cudaGraphLaunch(w.graph, s));

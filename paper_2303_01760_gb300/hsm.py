@@ -60,6 +60,7 @@ _SIGS = {
     "hsm_plan_destroy": (C.c_int, [_p]),
     "hsm_plan_profile": (C.c_int, [_p, C.POINTER(C.c_float), C.POINTER(_i64)]),
     "hsm_plan_set_timing": (C.c_int, [_p, C.c_int]),
+    "hsm_plan_set_spacing": (C.c_int, [_p, _p]),
     "hsm_stepper_create": (C.c_int, [C.POINTER(_p), _p, C.POINTER(hsm_phys)]),
     "hsm_step": (C.c_int, [_p, C.c_int, _p, _p, _p, C.POINTER(C.c_int)]),
     "hsm_stepper_destroy": (C.c_int, [_p]),
@@ -218,20 +219,30 @@ class Plan:
     ``is_boundary`` (u8 [N]) and ``normals`` (f64 [dim, N]) are CUDA tensors
     that must outlive the plan."""
 
-    def __init__(self, coords, is_regular, is_boundary, h, m=2, n=0, op_mask=None, stream=None, normals=None):
+    def __init__(self, coords, is_regular, is_boundary, h, m=2, n=0, op_mask=None, stream=None, normals=None,
+                 spacing=None):
         dim, N = coords.shape
         if op_mask is None:
             op_mask = HSM_DX | HSM_DY | HSM_LAP | (HSM_DZ if dim == 3 else 0)
         self.dim, self.N, self.op_mask = dim, N, op_mask
         self.n = n if n else 2 * _binom(m + dim, m)
-        self._keep = (coords, is_regular, is_boundary, normals)
+        self._keep = (coords, is_regular, is_boundary, normals, spacing)
         h_ = C.c_void_p()
         check(lib.hsm_plan_create(C.byref(h_), dim, N, ptr(coords), ptr(is_regular), ptr(is_boundary),
                                   ptr(normals), float(h), int(m), int(n), int(op_mask), stream_handle(stream)))
         self.h = h_
+        if spacing is not None:
+            check(lib.hsm_plan_set_spacing(self.h, ptr(spacing)), self.h)
 
     def build_stencils(self):
         check(lib.hsm_plan_build_stencils(self.h), self.h)
+        return self
+
+    def set_spacing(self, spacing):
+        """Local internodal distance h(x_i) (f64 CUDA [N], or None for h_regular)
+        of an h-refined set; takes effect at the next build_stencils."""
+        check(lib.hsm_plan_set_spacing(self.h, ptr(spacing)), self.h)
+        self._keep = self._keep[:4] + (spacing,)
         return self
 
     def compute_weights(self, prec=HSM_PREC_FP64, node_status=None, allow_singular=False):

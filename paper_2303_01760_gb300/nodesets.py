@@ -49,6 +49,8 @@ class NodeSet:
     bc          uint8   [N]        BC_INTERIOR / BC_T_DIRICHLET / BC_T_NEUMANN
     T_bc        float64 [N]        Dirichlet temperature (0 where not Dirichlet)
     T_ref       float               reference temperature of the Boussinesq term
+    spacing     float64 [N] or None local internodal distance h(x_i) of an
+                                    h-refined set (None: h everywhere)
     """
 
     name: str
@@ -63,6 +65,7 @@ class NodeSet:
     T_ref: float
     holes: np.ndarray = field(default_factory=lambda: np.zeros((0, 3)))
     band: float = 0.0
+    spacing: np.ndarray | None = None
 
     @property
     def N(self) -> int:
@@ -77,7 +80,7 @@ class NodeSet:
         return NodeSet(self.name + "-allrbf", self.dim, self.h, self.coords,
                        np.zeros_like(self.is_regular), self.is_boundary,
                        self.normals, self.bc, self.T_bc, self.T_ref,
-                       self.holes, self.band)
+                       self.holes, self.band, self.spacing)
 
 
 # --------------------------------------------------------------------------
@@ -89,7 +92,11 @@ _SLOTS = 4
 
 
 class _Grid:
-    def __init__(self, dim, h, lo, hi):
+    """``h`` is the smallest spacing (it sets the cell size); ``reach`` the
+    largest distance a proximity query asks about (default h)."""
+
+    def __init__(self, dim, h, lo, hi, reach=None):
+        reach = h if reach is None else reach
         self.dim = dim
         self.h = h
         self.cell = h / math.sqrt(dim)
@@ -98,13 +105,14 @@ class _Grid:
         self.ncell = int(np.prod(self.shape))
         self.slots = np.full((self.ncell, _SLOTS), -1, dtype=np.int64)
         self.fill = np.zeros(self.ncell, dtype=np.int64)
-        r = int(math.ceil(h / self.cell))
+        r = int(math.ceil(reach / self.cell))
         rng = np.arange(-r, r + 1)
         offs = np.stack(np.meshgrid(*([rng] * dim), indexing="ij"), -1).reshape(-1, dim)
-        # skip neighbour cells whose closest point is already >= h away
+        # skip neighbour cells whose closest point is already >= reach away
         gap = np.maximum(np.abs(offs) - 1, 0) * self.cell
-        self.offs = offs[np.sqrt((gap ** 2).sum(1)) < h]
+        self.offs = offs[np.sqrt((gap ** 2).sum(1)) < reach]
         self.pts = np.zeros((0, dim))
+        self.rad = np.zeros(0)  # per-point exclusion radius (variable-density fills)
 
     def cell_of(self, p):
         c = np.floor((p - self.lo) / self.cell).astype(np.int64)
@@ -116,9 +124,10 @@ class _Grid:
             idx = idx * self.shape[k] + c[..., k]
         return idx
 
-    def insert(self, p):
+    def insert(self, p, rad=None):
         base = len(self.pts)
         self.pts = np.concatenate([self.pts, p], 0)
+        self.rad = np.concatenate([self.rad, np.zeros(len(p)) if rad is None else rad])
         cid = self.lin(self.cell_of(p))
         order = np.argsort(cid, kind="stable")
         cs = cid[order]
@@ -130,8 +139,13 @@ class _Grid:
         self.slots[cs, slot] = base + order
         np.add.at(self.fill, cs, 1)
 
-    def too_close(self, p, chunk=1 << 16):
+    def too_close(self, p, chunk=1 << 16, radius=None):
+        """Whether a stored point lies closer than h to each p[i]; with
+        ``radius`` (per query point, up to ``reach``) closer than the larger of
+        radius[i] and the stored point's own radius."""
         out = np.zeros(len(p), dtype=bool)
+        if radius is not None:
+            chunk = max(256, (1 << 22) // (len(self.offs) * _SLOTS))
         for s in range(0, len(p), chunk):
             q = p[s:s + chunk]
             c = self.cell_of(q)
@@ -143,7 +157,11 @@ class _Grid:
             valid = ids >= 0
             pp = self.pts[np.where(valid, ids, 0)]     # [m, k, dim]
             d2 = ((pp - q[:, None, :]) ** 2).sum(-1)
-            out[s:s + chunk] = np.any(valid & (d2 < self.h * self.h), axis=1)
+            if radius is None:
+                lim = self.h * self.h
+            else:
+                lim = np.maximum(radius[s:s + chunk][:, None], self.rad[np.where(valid, ids, 0)]) ** 2
+            out[s:s + chunk] = np.any(valid & (d2 < lim), axis=1)
         return out
 
 
@@ -185,6 +203,61 @@ def _poisson_fill(fixed, seeds, accept, h, lo, hi, rng, k):
                 lose[j[~first_loses]] = True
             new = cands[~lose]
             g.insert(new)
+        else:
+            new = np.zeros((0, dim))
+        active = np.concatenate([active[alive], new], 0)
+    return g.pts[n_fixed:]
+
+
+def _poisson_fill_var(fixed, fixed_rad, seeds, accept, hfun, h_min, h_max, lo, hi, rng, k):
+    """Variable-density dart throwing (the h-refined fills of Sections 4.2 and
+    4.3): darts from an active point a land at distances h(a)..2h(a).  Every
+    point keeps its own exclusion disk (radius h(q) for a dart, ``fixed_rad``
+    for the fixed nodes): a dart q is kept when no point p lies closer than
+    max(h(q), r_p), so darts cannot squeeze between fixed nodes spaced wider
+    than the local h, and keeps h(q)/2 from the box faces; of two kept darts
+    closer than the larger of their spacings, the one of lower random
+    priority goes."""
+    from scipy.spatial import cKDTree
+
+    dim = fixed.shape[1]
+    g = _Grid(dim, h_min, lo, hi, reach=h_max)
+    g.insert(fixed, fixed_rad)
+    n_fixed = len(fixed)
+    active = np.asarray(seeds, dtype=np.float64)
+    while len(active):
+        m = len(active)
+        if dim == 2:
+            th = rng.uniform(0.0, 2.0 * math.pi, (m, k))
+            dirs = np.stack([np.cos(th), np.sin(th)], -1)
+        else:
+            dirs = rng.normal(size=(m, k, dim))
+            dirs /= np.linalg.norm(dirs, axis=-1, keepdims=True)
+        rad = hfun(active)[:, None, None] * rng.uniform(1.0, 2.0, (m, k, 1))
+        cand = (active[:, None, :] + rad * dirs).reshape(-1, dim)
+        # half a local spacing clear of the box faces: keeps darts out of the
+        # empty channels along box edges (edge lattice nodes are dropped)
+        inside = np.min(np.minimum(cand - lo, hi - cand), axis=1) >= 0.5 * hfun(cand)
+        ok = inside.copy()
+        ok[inside] = accept(cand[inside])
+        ok[ok] = ~g.too_close(cand[ok], radius=hfun(cand[ok]))
+        alive = ok.reshape(m, k).any(1)
+        cands = cand[np.flatnonzero(ok)]
+        if len(cands):
+            pri = rng.random(len(cands))
+            hc = hfun(cands)
+            pairs = cKDTree(cands).query_pairs(h_max, output_type="ndarray")
+            lose = np.zeros(len(cands), dtype=bool)
+            if len(pairs):
+                i, j = pairs[:, 0], pairs[:, 1]
+                dd = np.sqrt(((cands[i] - cands[j]) ** 2).sum(1))
+                clash = dd < np.maximum(hc[i], hc[j]) * (1.0 - 1e-12)
+                i, j = i[clash], j[clash]
+                first_loses = pri[i] > pri[j]
+                lose[i[first_loses]] = True
+                lose[j[~first_loses]] = True
+            new = cands[~lose]
+            g.insert(new, hc[~lose])
         else:
             new = np.zeros((0, dim))
         active = np.concatenate([active[alive], new], 0)
@@ -254,10 +327,13 @@ def _min_hole_gap(x, holes, dim):
     return d.min(1)
 
 
-def _build(name, dim, n, holes, band, wall_band, seed, bc_walls, hole_T, T_ref, k=None, region=None):
+def _build(name, dim, n, holes, band, wall_band, seed, bc_walls, hole_T, T_ref, k=None, region=None,
+           hfun=None, h_min=None):
     """Common hybrid construction (Section 2): lattice, removal, Poisson refill.
     ``region(p)`` (optional) marks further points whose neighbourhood is
-    discretised with scattered nodes."""
+    discretised with scattered nodes.  ``hfun(p)`` (optional) is a spacing
+    function for an h-refined fill, between ``h_min`` (on the hole surfaces)
+    and the lattice spacing."""
     rng = np.random.default_rng(seed)
     h = 1.0 / n
     ijk = _lattice(dim, n)
@@ -279,7 +355,7 @@ def _build(name, dim, n, holes, band, wall_band, seed, bc_walls, hole_T, T_ref, 
 
     hole_pts, hole_nrm, hole_id = [], [], []
     for hid, hc in enumerate(holes):
-        p, nr = _hole_surface(dim, hc[:dim], hc[dim], h, rng)
+        p, nr = _hole_surface(dim, hc[:dim], hc[dim], h if hfun is None else h_min, rng)
         hole_pts.append(p.T)
         hole_nrm.append(nr.T)
         hole_id.append(np.full(p.shape[1], hid))
@@ -311,7 +387,13 @@ def _build(name, dim, n, holes, band, wall_band, seed, bc_walls, hole_T, T_ref, 
     seeds = fixed[near]
     if k is None:
         k = 16 if dim == 2 else 10
-    scat = _poisson_fill(fixed, seeds, accept, h, np.zeros(dim), np.ones(dim), rng, k)
+    if hfun is None:
+        scat = _poisson_fill(fixed, seeds, accept, h, np.zeros(dim), np.ones(dim), rng, k)
+    else:
+        # lattice and wall nodes keep the lattice spacing, hole nodes h_min
+        fixed_rad = np.r_[np.full(len(lat_pts), h), np.full(len(hole_pts), h_min)]
+        scat = _poisson_fill_var(fixed, fixed_rad, seeds, accept, hfun, h_min, h, np.zeros(dim), np.ones(dim), rng,
+                                 k)
 
     N = len(fixed) + len(scat)
     coords = np.concatenate([fixed, scat], 0).T.copy()
@@ -341,9 +423,11 @@ def _build(name, dim, n, holes, band, wall_band, seed, bc_walls, hole_T, T_ref, 
     T_bc[sl] = np.array([hole_T(int(i)) for i in hole_id]) if n_hole else 0.0
 
     order = _morton_order(coords, h)
+    # each node's spacing: its exclusion radius in the fill
+    spacing = None if hfun is None else np.r_[fixed_rad, hfun(scat)][order].copy()
     return NodeSet(name, dim, h, coords[:, order].copy(), is_regular[order].copy(),
                    is_boundary[order].copy(), normals[:, order].copy(), bc[order].copy(),
-                   T_bc[order].copy(), T_ref, np.asarray(holes, dtype=np.float64), band)
+                   T_bc[order].copy(), T_ref, np.asarray(holes, dtype=np.float64), band, spacing)
 
 
 # --------------------------------------------------------------------------
@@ -427,6 +511,34 @@ def cube_spheres(n=125, n_holes=20, r_range=(0.03, 0.08), band=0.05, seed=SEED_B
                   bc_walls, lambda i: float(i % 2), 0.5)
 
 
+def holes_refined(dim=2, n=100, n_holes=4, r_range=(0.06, 0.12), delta_h=4.0, ratio=3.0,
+                  all_scattered=False, seed=SEED_BASE + 50, hole_gap=0.1):
+    """h-refined irregular domain (Section 4.2 in 2D, Section 4.3 in 3D): the
+    unit square (cube) minus ``n_holes`` seeded circular (spherical) holes.
+    The internodal distance falls linearly from h_r = 1/n (the regular
+    lattice) to h_s = h_r/ratio on the hole surfaces over a distance
+    h_r*delta_h; the scattered layer has the same width, or covers the whole
+    domain when ``all_scattered`` (then the refinement still spans h_r*delta_h).
+    Box insulated; holes alternate T_C = 0 / T_H = 1.  ``spacing`` holds h(x_i)."""
+    rng = np.random.default_rng(seed)
+    h = 1.0 / n
+    holes = _place_holes(dim, n_holes, r_range, hole_gap, 2 * h, rng)
+    h_s = h / ratio
+    dist = h * delta_h
+
+    def hfun(p):
+        g = _min_hole_gap(p, holes, dim)
+        return h_s + (h - h_s) * np.clip(g / dist, 0.0, 1.0)
+
+    def bc_walls(axis, side):
+        return BC_T_NEUMANN, 0.0
+
+    band = 4.0 if all_scattered else dist
+    kind = "allscat" if all_scattered else "hybrid"
+    return _build(f"{'square' if dim == 2 else 'cube'}-refined-n{n}-d{delta_h:g}-r{ratio:g}-{kind}", dim, n,
+                  holes, band, 0.0, seed + 1000, bc_walls, lambda i: float(i % 2), 0.5, hfun=hfun, h_min=h_s)
+
+
 def square_all_scattered(n=400, seed=SEED_BASE + 4, jitter=0.0):
     """Unit square filled only with Poisson-disk scattered nodes of spacing 1/n
     (plus the lattice wall nodes); each interior node is then displaced by
@@ -448,7 +560,7 @@ def jittered(ns, jitter, seed):
     coords[0, inner] += rr * np.cos(th)
     coords[1, inner] += rr * np.sin(th)
     return NodeSet(f"{ns.name}-j{jitter:g}", ns.dim, ns.h, coords, ns.is_regular.copy(), ns.is_boundary.copy(),
-                   ns.normals.copy(), ns.bc.copy(), ns.T_bc.copy(), ns.T_ref, ns.holes, ns.band)
+                   ns.normals.copy(), ns.bc.copy(), ns.T_bc.copy(), ns.T_ref, ns.holes, ns.band, ns.spacing)
 
 
 def scatter_fraction(ns: NodeSet) -> float:
@@ -521,15 +633,17 @@ def cached(fn, *args, cache_dir=None, **kw):
     path = os.path.join(cache_dir, f"{fn.__name__}-{key}.npz")
     if os.path.exists(path):
         z = np.load(path, allow_pickle=False)
+        spacing = z["spacing"] if "spacing" in z.files and z["spacing"].size else None
         return NodeSet(str(z["name"]), int(z["dim"]), float(z["h"]), z["coords"], z["is_regular"],
                        z["is_boundary"], z["normals"], z["bc"], z["T_bc"], float(z["T_ref"]),
-                       z["holes"], float(z["band"]))
+                       z["holes"], float(z["band"]), spacing)
     ns = fn(*args, **kw)
     os.makedirs(cache_dir, exist_ok=True)
     tmp = path + f".{os.getpid()}.tmp.npz"
     np.savez(tmp, name=ns.name, dim=ns.dim, h=ns.h, coords=ns.coords, is_regular=ns.is_regular,
              is_boundary=ns.is_boundary, normals=ns.normals, bc=ns.bc, T_bc=ns.T_bc,
-             T_ref=ns.T_ref, holes=ns.holes, band=ns.band)
+             T_ref=ns.T_ref, holes=ns.holes, band=ns.band,
+             spacing=np.zeros(0) if ns.spacing is None else ns.spacing)
     os.replace(tmp, path)
     return ns
 
@@ -555,4 +669,5 @@ def tiled(ns, nx, ny, jitter=None, seed=0):
     coords = np.concatenate([p[0] for p in parts], 1)
     return NodeSet(f"{ns.name}-tiled{nx}x{ny}", ns.dim, ns.h, coords, cat(lambda c: c.is_regular),
                    cat(lambda c: c.is_boundary), np.concatenate([c.normals for _, c in parts], 1),
-                   cat(lambda c: c.bc), cat(lambda c: c.T_bc), ns.T_ref, ns.holes, ns.band)
+                   cat(lambda c: c.bc), cat(lambda c: c.T_bc), ns.T_ref, ns.holes, ns.band,
+                   None if ns.spacing is None else cat(lambda c: c.spacing))

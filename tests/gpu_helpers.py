@@ -7,6 +7,7 @@ def to_dev(ns):
 
     d = torch.device("cuda:0")
     return dict(
+        spacing=None if ns.spacing is None else torch.from_numpy(np.ascontiguousarray(ns.spacing)).to(d),
         coords=torch.from_numpy(np.ascontiguousarray(ns.coords)).to(d),
         is_regular=torch.from_numpy(np.ascontiguousarray(ns.is_regular)).to(d),
         is_boundary=torch.from_numpy(np.ascontiguousarray(ns.is_boundary)).to(d),
@@ -22,7 +23,7 @@ def make_plan(ns, m=2, n=0, op_mask=None, prec=0, node_status=False):
 
     dv = to_dev(ns)
     plan = hsm.Plan(dv["coords"], dv["is_regular"], dv["is_boundary"], ns.h, m=m, n=n, op_mask=op_mask,
-                    normals=dv["normals"])
+                    normals=dv["normals"], spacing=dv["spacing"])
     plan.build_stencils()
     st = torch.full((ns.N,), 77, dtype=torch.uint8, device="cuda:0") if node_status else None
     code = plan.compute_weights(prec, st, allow_singular=True)

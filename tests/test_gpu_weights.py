@@ -40,7 +40,7 @@ def _check_plan(ns, m, prec=0, centers=None, tol=TOL_FP64, apply_check=True, sin
     ops = ow.ops_for(dim)
     plan, code, status = make_plan(ns, m=m, prec=prec, node_status=True)
     st = ost.build_stencils(ns.coords, ns.is_regular, ns.is_boundary, ns.h, n, centers=centers,
-                            normals=ns.normals)
+                            normals=ns.normals, spacing=ns.spacing)
     if singular_ok:
         # nodes whose system is singular to working precision must be flagged
         # (status 255, zero weights); well-conditioned ones must not be
@@ -236,3 +236,49 @@ def test_sparse_lattice_takes_the_hashed_map():
     lattice_points = (401 + 40) ** 2
     assert lattice_points > 4 * ns.N + 1024
     _check_plan(ns, m=2)
+
+
+REFINED_2D = dict(n=40, n_holes=2, r_range=(0.1, 0.15), delta_h=4.0, seed=nodesets.SEED_BASE + 60)
+REFINED_3D = dict(dim=3, n=12, n_holes=1, r_range=(0.15, 0.2), delta_h=3.0, ratio=2.0, seed=nodesets.SEED_BASE + 61)
+
+
+def test_refined_sets_2d_and_3d():
+    """h-refined sets (Sections 4.2 and 4.3: spacing h_r/3 in 2D and h_r/2 in
+    3D at the holes), boundary stencils searched one local spacing inside:
+    every stencil and weight against the oracle, in FP64 and FP32 + refinement.
+    On the coarse 3D set one wall node next to a box edge has a one-sided
+    stencil whose system is singular to working precision (kappa ~ 3e18, with
+    either search point); it must be flagged, the rest must match."""
+    ns2 = nodesets.holes_refined(**REFINED_2D)
+    _check_plan(ns2, m=2)
+    _check_plan(ns2, m=2, prec=1, tol=TOL_FP32R)
+    _check_plan(ns2.all_scattered(), m=2)
+    _check_plan(nodesets.holes_refined(**REFINED_3D), m=2, singular_ok=True)
+
+
+def test_setting_the_spacing_rebuilds_the_boundary_stencils():
+    """A plan built with h_regular, then given the local spacing: the next
+    build (a fresh capture of the build graph) takes the new search points,
+    and clearing the spacing brings the old stencils back."""
+    import torch
+    from paper_2303_01760_gb300 import hsm
+
+    ns = nodesets.holes_refined(**REFINED_2D)
+    d = {k: torch.from_numpy(np.ascontiguousarray(getattr(ns, k))).cuda()
+         for k in ("coords", "is_regular", "is_boundary", "normals", "spacing")}
+    plan = hsm.Plan(d["coords"], d["is_regular"], d["is_boundary"], ns.h, m=2, normals=d["normals"])
+    bnd = np.flatnonzero(ns.is_boundary)
+    want = {}
+    for key, sp in (("lattice", None), ("local", ns.spacing)):
+        st = ost.build_stencils(ns.coords, ns.is_regular, ns.is_boundary, ns.h, 12, centers=bnd,
+                                normals=ns.normals, spacing=sp)
+        want[key] = st["rbf_idx"]
+    assert not np.array_equal(want["lattice"], want["local"])
+    for key, sp in (("lattice", None), ("local", d["spacing"]), ("lattice", None)):
+        plan.set_spacing(sp)
+        plan.build_stencils()
+        plan.compute_weights(hsm.HSM_PREC_FP64)
+        rp, col, val = gpu_csr(plan, BIT["dx"])
+        c, _ = _rows(rp, col, val, bnd, 12)
+        assert np.array_equal(c, want[key]), key
+    plan.close()

@@ -81,3 +81,53 @@ def test_paper_regular_dvd_node_count():
     ns = nodesets.square_wall_band(n=n, wall_band=0.0)
     assert ns.N == g["value"]
     assert ns.n_scattered == int(ns.is_boundary.sum())
+
+
+def test_boundary_search_point_moves_by_the_local_spacing():
+    """Hand-worked: a wall node at (0, 0.5) with outward normal (-1, 0) and
+    interior nodes on a 0.1 grid.  With spacing 0.1 the search point is
+    (0.1, 0.5) and the nearest interior node is the one there; with a local
+    spacing of 0.3 (an h-refined set) the search point is (0.3, 0.5)."""
+    xs = np.arange(1, 6) * 0.1
+    ys = np.arange(3, 8) * 0.1
+    gx, gy = np.meshgrid(xs, ys, indexing="xy")
+    coords = np.concatenate([[[0.0], [0.5]], np.stack([gx.ravel(), gy.ravel()])], 1)
+    normals = np.zeros_like(coords)
+    normals[0, 0] = -1.0
+    is_bnd = np.zeros(coords.shape[1], dtype=np.uint8)
+    is_bnd[0] = 1
+    interior = is_bnd == 0
+    at = lambda x, y: int(np.flatnonzero(np.isclose(coords[0], x) & np.isclose(coords[1], y))[0])
+    got = ost.boundary_bruteforce(coords, normals, 0.1, [0], 2, interior)[0]
+    assert got.tolist() == [0, at(0.1, 0.5)]
+    spacing = np.full(coords.shape[1], 0.1)
+    assert ost.boundary_bruteforce(coords, normals, spacing, [0], 2, interior)[0].tolist() == got.tolist()
+    spacing[0] = 0.3
+    assert ost.boundary_bruteforce(coords, normals, spacing, [0], 2, interior)[0].tolist() == [0, at(0.3, 0.5)]
+    assert ost.boundary_kdtree(coords, normals, spacing, [0], 2, interior)[0].tolist() == [0, at(0.3, 0.5)]
+    # the whole-set builder takes the spacing array the same way
+    st = ost.build_stencils(coords, np.zeros(coords.shape[1], np.uint8), is_bnd, 0.1, 2, normals=normals,
+                            spacing=spacing)
+    r = int(np.flatnonzero(st["rbf_nodes"] == 0)[0])
+    assert st["rbf_idx"][r].tolist() == [0, at(0.3, 0.5)]
+
+
+def test_refined_boundary_stencils_are_more_local():
+    """On an h-refined set (spacing h_r/3 at the holes) hole-node stencils
+    searched one LOCAL spacing inside keep each node's nearest interior
+    neighbour and reach less far than those searched a whole lattice spacing
+    inside."""
+    ns = nodesets.holes_refined(n=30, n_holes=2, r_range=(0.1, 0.15), delta_h=4.0, seed=nodesets.SEED_BASE + 60)
+    hole = np.flatnonzero((ns.is_boundary == 1) & (ns.bc == nodesets.BC_T_DIRICHLET))
+    interior = ns.is_boundary == 0
+    reach = {}
+    for name, hh in (("local", ns.spacing), ("lattice", ns.h)):
+        st = ost.boundary_bruteforce(ns.coords, ns.normals, hh, hole, 12, interior)
+        far = []
+        for r, c in enumerate(hole):
+            far.append(np.sqrt(ost.sq_dist(ns.coords, int(c), st[r, 1:])).max() / ns.spacing[c])
+            if name == "local":
+                nearest = int(np.argmin(np.where(interior, ost.sq_dist(ns.coords, int(c)), np.inf)))
+                assert nearest in st[r]
+        reach[name] = np.median(far)
+    assert reach["local"] < 0.9 * reach["lattice"]
