@@ -314,8 +314,21 @@ hsm_status hsm_mlp_grad(hsm_mlp mlp, const float* X, const float* Y, int64_t cou
 hsm_status hsm_mlp_train(hsm_mlp mlp, const float* X, const float* Y, int64_t count, int steps, int batch,
                          float lr, uint64_t seed, float* loss_log);
 
-/* Forward pass: Y device f32 [count][n_out] from X device f32 [count][n_in]. */
+/* Forward pass: Y device f32 [count][n_out] from X device f32 [count][n_in].
+ * The fused tensor-core pass bounds every wait on its pipeline barriers; if
+ * one expires, every role leaves its loop, the tensor memory is released and
+ * the call returns HSM_ETIMEOUT (Y is then undefined; the handle stays
+ * usable).  Synchronises the MLP's stream.                                   */
 hsm_status hsm_mlp_predict(hsm_mlp mlp, const float* X, int64_t count, float* Y);
+
+/* Failure-path test hook (no paper counterpart).  HSM_FAULT_HOLD_MLP_LOADS
+ * makes the next fused forward pass issue no loads at all, so that nothing
+ * is ever in flight and the waits of its tensor-core and epilogue roles run
+ * out: that hsm_mlp_predict returns HSM_ETIMEOUT, and later calls work as
+ * before.  The hook applies to one pass; HSM_FAULT_NONE clears it.
+ * HSM_EINVAL for a NULL handle or an unknown fault.                          */
+enum { HSM_FAULT_NONE = 0, HSM_FAULT_HOLD_MLP_LOADS = 1 };
+hsm_status hsm_mlp_inject_fault(hsm_mlp mlp, int fault);
 
 /* Attaches the predictor used by HSM_PREC_LEARNED (n_in = d n, n_out = nops n;
  * not owned by the plan; NULL detaches).  The learned path is built for 2D

@@ -615,6 +615,14 @@ hsm_status hsm_mlp_train(hsm_mlp h, const float* X, const float* Y, int64_t coun
   return st;
 }
 
+hsm_status hsm_mlp_inject_fault(hsm_mlp h, int fault) {
+  if (!h) return set_error(nullptr, HSM_EINVAL, "mlp is NULL");
+  if (fault != HSM_FAULT_NONE && fault != HSM_FAULT_HOLD_MLP_LOADS)
+    return set_error(nullptr, HSM_EINVAL, "unknown fault");
+  h->m.fault_hold_loads = fault == HSM_FAULT_HOLD_MLP_LOADS;
+  return HSM_OK;
+}
+
 hsm_status hsm_mlp_predict(hsm_mlp h, const float* X, int64_t count, float* Y) {
   if (!h || !X || !Y || count < 0) return set_error(nullptr, HSM_EINVAL, "mlp, X and Y are required");
   Mlp& m = h->m;
@@ -627,6 +635,9 @@ hsm_status hsm_mlp_predict(hsm_mlp h, const float* X, int64_t count, float* Y) {
       MLP_CUDA(dev_alloc(&m.Xf, (size_t)rows * m.din[0], m.stream));
       m.capf = rows;
     }
+    // the timeout flag of the fused pass: cleared per call, so an expired
+    // wait in one call does not fail the next
+    if (m.tc_err) MLP_CUDA(cudaMemsetAsync(m.tc_err, 0, sizeof(unsigned), m.stream));
     for (int64_t b = 0; b < count; b += chunk) {
       const int64_t cnt = std::min(chunk, count - b);
       const int64_t r = ceil_div(cnt, BM) * BM;

@@ -23,6 +23,7 @@ struct Mlp {
   std::vector<size_t> w_off, b_off, wbf_off;
   size_t n_master = 0, n_wbf = 0;
   int64_t t = 0;               // Adam step counter
+  int fault_hold_loads = 0;    // test hook: the next fused forward pass issues no loads
   cudaStream_t stream = nullptr;
   // activation workspace for a batch of up to cap rows
   int64_t cap = 0;

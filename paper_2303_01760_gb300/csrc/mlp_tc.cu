@@ -49,6 +49,7 @@ struct TcArgs {
   float* Y;
   int ldy, ncols;
   unsigned* err;
+  int hold_loads;  // test hook: the producer issues nothing, so the consumers' bounded waits expire
 };
 
 __device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -212,7 +213,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     return j < mine ? blockIdx.x + j * (int64_t)gridDim.x : -1;
   };
 
-  if (warp == 0 && lane == 0) {
+  if (warp == 0 && lane == 0 && !a.hold_loads) {
     // ---- producer: each slot's inputs, then the weight slices in MMA order
     uint32_t seq = 0, nx[kSlots] = {0, 0};
     bool ok = true;
@@ -409,6 +410,8 @@ hsm_status mlp_forward_tc(Mlp& m, const __nv_bfloat16* X, int64_t rows, float* Y
   a.ldy = ldy;
   a.ncols = m.n_out;
   a.err = m.tc_err;
+  a.hold_loads = m.fault_hold_loads;
+  m.fault_hold_loads = 0;
   static bool attr = false;
   if (!attr) {
     if (cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess)

@@ -38,6 +38,8 @@ class hsm_phys(C.Structure):
                 ("krylov_max_it", C.c_int), ("precond", C.c_int)]
 
 
+HSM_FAULT_NONE, HSM_FAULT_HOLD_MLP_LOADS = 0, 1
+
 HSM_PRECOND_AMG = 0
 HSM_PRECOND_JACOBI = 1
 
@@ -74,6 +76,7 @@ _SIGS = {
     "hsm_mlp_grad": (C.c_int, [_p, _p, _p, _i64, _p, C.POINTER(C.c_float)]),
     "hsm_mlp_train": (C.c_int, [_p, _p, _p, _i64, C.c_int, C.c_int, C.c_float, C.c_uint64, _p]),
     "hsm_mlp_predict": (C.c_int, [_p, _p, _i64, _p]),
+    "hsm_mlp_inject_fault": (C.c_int, [_p, C.c_int]),
     "hsm_mlp_attach": (C.c_int, [_p, _p]),
     "hsm_plan_learned_data": (C.c_int, [_p, _p, _p, C.POINTER(_i64)]),
 }
@@ -179,6 +182,11 @@ class MLP:
         check(lib.hsm_mlp_train(self.h, ptr(X), ptr(Y), X.shape[0], int(steps), int(batch), float(lr), int(seed),
                                 log.ctypes.data_as(C.c_void_p)))
         return log[:steps]
+
+    def inject_fault(self, fault=HSM_FAULT_HOLD_MLP_LOADS):
+        """Failure-path test hook: the next fused forward pass issues no loads,
+        so its bounded waits expire and predict raises HSM_ETIMEOUT."""
+        check(lib.hsm_mlp_inject_fault(self.h, int(fault)))
 
     def predict(self, X):
         import torch
