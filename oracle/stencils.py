@@ -167,13 +167,15 @@ def lattice_map(coords, h):
     return m, ri, on
 
 
-def mon_stencils(coords, is_regular, is_boundary, h):
+def mon_stencils(coords, is_regular, is_boundary, h, only=None):
     """Regular stencils.  Returns (nodes, idx[len(nodes), 2d+1]) for the nodes
-    that keep MON, and the array of demoted node ids."""
+    that keep MON, and the array of demoted node ids; with ``only`` (node ids)
+    just for those of them that are flagged regular."""
     dim, N = coords.shape
     m, ri, on = lattice_map(coords, h)
     nodes, rows, demoted = [], [], []
-    for c in np.flatnonzero(is_regular):
+    cand = np.flatnonzero(is_regular) if only is None else np.asarray(only)[np.asarray(is_regular)[only] != 0]
+    for c in cand:
         c = int(c)
         if is_boundary[c] or not on[c] or m.get(tuple(int(v) for v in ri[:, c])) != c:
             demoted.append(c)
@@ -213,7 +215,8 @@ def build_stencils(coords, is_regular, is_boundary, h, n, centers=None, use_kdtr
       demoted              regular-flagged nodes demoted to RBF-FD
     """
     dim, N = coords.shape
-    mon_nodes, mon_idx, demoted = mon_stencils(coords, is_regular, is_boundary, h)
+    mon_nodes, mon_idx, demoted = mon_stencils(coords, is_regular, is_boundary, h,
+                                               only=None if centers is None else np.asarray(centers, dtype=np.int64))
     kind = np.ones(N, dtype=np.int8)  # 1 = RBF-FD
     kind[mon_nodes] = 0
     if centers is not None:

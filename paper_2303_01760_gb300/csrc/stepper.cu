@@ -914,6 +914,12 @@ hsm_status run_steps(hsm_stepper st, int n_steps, double* v, double* T, double* 
   // legacy default stream) and launched on the plan's stream
   if (!st->cap) HSM_CUDA(pl, cudaStreamCreateWithFlags(&st->cap, cudaStreamNonBlocking));
   cudaStream_t cs = st->cap;
+  // The caller owns p, the stepper only the bordering constant c: a c left by
+  // an earlier call need not match the p passed now (a reset or restarted
+  // run), and with a near-zero right-hand side (a first step from rest) the
+  // solve could not then reach its relative tolerance.  Each call starts c
+  // at zero; within a call every solve is warm-started from the last.
+  HSM_CUDA(pl, cudaMemsetAsync(reinterpret_cast<char*>(st->scal) + offsetof(KS, xN), 0, sizeof(double), s));
   if (!st->g_chunk) HSM_CUDA(pl, capture(cs, &st->g_chunk, [&] { launch_chunk<DIM>(st, a, grid, blk, cs); }));
   if (!st->g_tail)
     HSM_CUDA(pl, capture(cs, &st->g_tail, [&] {

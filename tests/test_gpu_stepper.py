@@ -128,3 +128,80 @@ def test_3d_steps_match_oracle():
     print(f"3D: T rel err {eT:.3e}  v rel err {ev:.3e}  iters/step {np.mean(g['iters']):.1f}")
     assert eT <= 1e-9
     assert ev <= 1e-7
+
+
+def _stepper_on(ns, Ra, dt, tol=1e-12):
+    import torch
+    from paper_2303_01760_gb300 import hsm
+
+    plan, code, _ = make_plan(ns, m=2)
+    assert code == 0
+    dv = plan._dev
+    st = hsm.Stepper(plan, Ra, 0.71, dt, ns.T_ref, dv["bc"], dv["T_bc"], dv["normals"], krylov_tol=tol,
+                     krylov_max_it=4000)
+    return plan, st, dv
+
+
+def test_restart_from_saved_fields_matches_a_continuous_run():
+    """Checkpoint and resume through the public API.  The caller owns v, T
+    and p, so 10 steps, a copy of the fields to the host, a fresh plan and
+    stepper, and 10 more steps reach the fields of 20 uninterrupted steps, to
+    the pressure solve's tolerance (only the bordering constant of the first
+    resumed solve starts from zero)."""
+    import torch
+
+    ns = nodesets.square_wall_band(n=40)
+    dt = ostep.dt_rule(ns.h)
+
+    def fresh(dv):
+        v = torch.zeros((2, ns.N), dtype=torch.float64, device="cuda:0")
+        T = torch.where(dv["bc"] == 1, dv["T_bc"], torch.zeros_like(dv["T_bc"])).contiguous()
+        return v, T, torch.zeros(ns.N, dtype=torch.float64, device="cuda:0")
+
+    plan, st, dv = _stepper_on(ns, 1e5, dt)
+    v, T, p = fresh(dv)
+    st.step(v, T, p, 20)
+    ref = [x.cpu().numpy() for x in (v, T, p)]
+    v, T, p = fresh(dv)
+    st.step(v, T, p, 10)
+    saved = [x.cpu().numpy() for x in (v, T, p)]
+    st.close()
+    plan.close()
+    plan, st, dv = _stepper_on(ns, 1e5, dt)
+    v, T, p = (torch.from_numpy(x.copy()).cuda() for x in saved)
+    st.step(v, T, p, 10)
+    got = [x.cpu().numpy() for x in (v, T, p)]
+    st.close()
+    plan.close()
+    assert _rel(got[1], ref[1]) <= 1e-10
+    assert _rel(got[0], ref[0]) <= 1e-8
+
+
+def test_too_thin_refined_layer_diverges_and_is_reported():
+    """Section 4.2 finds delta_h = 4 the smallest stable width of the scattered
+    layer.  With h-refinement to h_r/3 over 2 h_r the explicit step at Ra = 1e6
+    blows up within a few hundred steps, and hsm_step says so (the pressure
+    solve meets non-finite values and stops: HSM_ENOTCONV) instead of
+    returning normally; over 4 h_r the same run stays finite and converged."""
+    import torch
+
+    codes = {}
+    for dh in (2.0, 4.0):
+        ns = nodesets.holes_refined(n=100, n_holes=4, r_range=(0.06, 0.12), delta_h=dh, ratio=3.0,
+                                    seed=nodesets.SEED_BASE + 50)
+        plan, st, dv = _stepper_on(ns, 1e6, ostep.dt_rule(float(ns.spacing.min())), tol=1e-10)
+        v = torch.zeros((2, ns.N), dtype=torch.float64, device="cuda:0")
+        T = torch.where(dv["bc"] == 1, dv["T_bc"], torch.zeros_like(dv["T_bc"])).contiguous()
+        p = torch.zeros(ns.N, dtype=torch.float64, device="cuda:0")
+        seen = []
+        for _ in range(10):
+            _, code = st.step(v, T, p, 30, allow_notconv=True)
+            seen.append(code)
+            if code != 0:
+                break
+        codes[dh] = (seen, bool(torch.isfinite(v).all() and torch.isfinite(T).all()))
+        st.close()
+        plan.close()
+    print(codes)
+    assert codes[2.0][0][-1] == 5
+    assert all(c == 0 for c in codes[4.0][0]) and codes[4.0][1]

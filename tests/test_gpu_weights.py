@@ -146,6 +146,34 @@ def test_irregular_250k_sampled():
     _check_plan(ns, m=2, centers=centers)
 
 
+@pytest.mark.parametrize("m,all_rbffd", [(4, False), (2, True)])
+def test_irregular_250k_sampled_m4_and_all_rbffd(m, all_rbffd):
+    """The same full-size set with m = 4 (n = 30), and with every node forced
+    to RBF-FD (the 100 % end of the scattered-fraction sweep): sampled nodes
+    against the oracle."""
+    ns = nodesets.cached(nodesets.square_holes)
+    if all_rbffd:
+        ns = ns.all_scattered()
+    rng = np.random.default_rng(124)
+    centers = np.unique(np.r_[rng.choice(ns.N, 2000, replace=False), np.flatnonzero(ns.is_boundary)[:300]])
+    _check_plan(ns, m=m, centers=centers)
+
+
+def test_tiled_7m_sampled():
+    """The 8M-node 2D shape, 30 % scattered: 12 x 12 tiled copies of a unit
+    square minus 8 holes (lattice h = 1/250, band 0.09), 7,339,248 nodes, the
+    plan the benchmark times for its apply roofline.  Sampled nodes against
+    the oracle, FP64 and FP32 + refinement weights and the f64/f32 apply."""
+    base = nodesets.cached(nodesets.square_holes, n=250, band=0.09)
+    ns = nodesets.tiled(base, 12, 12)
+    assert ns.N == 7339248
+    rng = np.random.default_rng(125)
+    bnd = np.flatnonzero(ns.is_boundary)
+    centers = np.unique(np.r_[rng.choice(ns.N, 2500, replace=False), rng.choice(bnd, 500, replace=False)])
+    _check_plan(ns, m=2, centers=centers)
+    _check_plan(ns, m=2, prec=1, tol=TOL_FP32R, centers=centers, apply_check=False)
+
+
 def test_duplicate_nodes_are_reported_singular():
     """Two scattered nodes at the same position make their RBF-FD systems
     singular: the call reports HSM_ESINGULAR and marks those nodes 255
