@@ -140,8 +140,12 @@ CPU_SAMPLE_SEED = 7
 
 
 def cpu_sample_nodes(N, n_sample, seed=CPU_SAMPLE_SEED):
+    """``n_sample`` random nodes in ascending order; every node when
+    n_sample <= 0 or >= N."""
     import numpy as np
 
+    if n_sample <= 0 or n_sample >= N:
+        return np.arange(N)
     return np.sort(np.random.default_rng(seed).choice(N, n_sample, replace=False))
 
 
@@ -161,6 +165,7 @@ def cpu_sample_run(n_sample, gpu_npz=None, seed=CPU_SAMPLE_SEED):
 
     ns = nodesets.cached(nodesets.square_holes)
     centers = cpu_sample_nodes(ns.N, n_sample, seed)
+    n_sample = len(centers)
     u, _ = nodesets.field_sincos(ns.coords)
     t0 = time.perf_counter()
     st = ost.build_stencils(ns.coords, ns.is_regular, ns.is_boundary, ns.h, 12, centers=centers,
@@ -195,7 +200,7 @@ def cpu_sample_run(n_sample, gpu_npz=None, seed=CPU_SAMPLE_SEED):
     return t, n_sample, parity
 
 
-def cpu_baseline(n_sample=20000, gpu_npz=None):
+def cpu_baseline(n_sample=0, gpu_npz=None):
     """Runs the oracle sample in a fresh single-threaded process (and, after
     its timing, the parity check of the GPU's outputs for the same nodes).
     Returns (cpu_baseline, parity)."""
@@ -207,8 +212,9 @@ def cpu_baseline(n_sample=20000, gpu_npz=None):
         return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": r.stderr[-500:]}, None
     t, n, par = json.loads(r.stdout.strip().splitlines()[-1])
     return {"value": n / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n} random nodes of the workload (their stencils by k-d tree, MON/RBF-FD weights by "
-                      f"numpy batched solve, one application of dx,dy,lap); {t:.1f} s single-threaded",
+            "sample": f"{n} nodes of the workload{' (all of it)' if n_sample <= 0 else ' at random'}: their "
+                      f"stencils by k-d tree, MON/RBF-FD weights by numpy batched solve, one application of "
+                      f"dx,dy,lap; {t:.1f} s single-threaded",
             "seconds": t}, par
 
 
@@ -776,8 +782,12 @@ def run_reference(args):
     from paper_2303_01760_gb300 import nodesets
 
     ns = nodesets.cached(nodesets.square_holes)
-    n_sample = args.ref_sample
-    cpu_sample_run(min(n_sample, 500))  # warm imports / caches
+    # each step processes the whole workload, unless K + W steps of it would
+    # take more than a few minutes; then each step takes an equal share
+    n_sample = args.ref_sample if args.ref_sample > 0 else \
+        (ns.N if args.steps + args.warmup <= 40 else max(5000, ns.N * 40 // (args.steps + args.warmup)))
+    n_sample = min(n_sample, ns.N)
+    cpu_sample_run(500)  # warm imports / caches
     times = []
     for _ in range(args.warmup):
         cpu_sample_run(n_sample)
@@ -792,8 +802,8 @@ def run_reference(args):
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": workload_desc(ns),
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                            "sample": f"{n_sample} random nodes of the workload per step (stencils, weights, "
-                                      f"one application of dx,dy,lap)"},
+                            "sample": f"{n_sample} of the workload's {ns.N} nodes per step (stencils, weights, "
+                                      f"one application of dx,dy,lap), single-threaded"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(res))
 
@@ -1196,8 +1206,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--cpu-sample", type=int, default=20000)
-    ap.add_argument("--ref-sample", type=int, default=5000)
+    ap.add_argument("--cpu-sample", type=int, default=0, help="oracle nodes in cpu_baseline (0: all)")
+    ap.add_argument("--ref-sample", type=int, default=0, help="oracle nodes per --impl reference step (0: all, "
+                    "or an equal share of a few minutes when --steps + --warmup > 40)")
     ap.add_argument("--kernels", action="store_true", help="profiling driver only (no JSON line)")
     ap.add_argument("--no-extras", action="store_true", help="skip the 7M-node apply and learned sections")
     ap.add_argument("--all-rbffd", action="store_true", help="with --kernels: force every node to RBF-FD")

@@ -131,3 +131,20 @@ def test_refined_boundary_stencils_are_more_local():
                 assert nearest in st[r]
         reach[name] = np.median(far)
     assert reach["local"] < 0.9 * reach["lattice"]
+
+
+def test_subset_build_equals_full_build_on_those_nodes():
+    """Stencils built for a subset of centres (as the full-size sampled parity
+    tests do) are the full build's stencils of those nodes."""
+    ns = nodesets.square_holes(n=60, n_holes=3, r_range=(0.08, 0.12), band=0.08, seed=nodesets.SEED_BASE + 31)
+    full = ost.build_stencils(ns.coords, ns.is_regular, ns.is_boundary, ns.h, 12, normals=ns.normals)
+    rng = np.random.default_rng(3)
+    centers = np.unique(rng.choice(ns.N, 400, replace=False))
+    sub = ost.build_stencils(ns.coords, ns.is_regular, ns.is_boundary, ns.h, 12, centers=centers,
+                             normals=ns.normals)
+    for grp in ("mon", "rbf"):
+        rows = {int(c): r.tolist() for c, r in zip(full[grp + "_nodes"], full[grp + "_idx"])}
+        assert set(sub[grp + "_nodes"].tolist()) == set(rows) & set(centers.tolist())
+        for c, r in zip(sub[grp + "_nodes"], sub[grp + "_idx"]):
+            assert r.tolist() == rows[int(c)]
+    assert set(sub["demoted"].tolist()) == set(full["demoted"].tolist()) & set(centers.tolist())
