@@ -57,3 +57,24 @@ def test_argument_errors_need_no_device():
     assert f(ctypes.byref(h), 2, 10, fake, fake, None, None, 0.1, 2, 0, 11, None) == 0
     lib.hsm_plan_destroy.argtypes = [ctypes.c_void_p]
     assert lib.hsm_plan_destroy(h) == 0
+
+
+def test_spacing_and_fault_hooks_validate_on_the_host():
+    """hsm_plan_set_spacing and hsm_mlp_inject_fault only record their
+    argument on the host: NULL handles and unknown faults give HSM_EINVAL."""
+    lib = _lib()
+    lib.hsm_plan_set_spacing.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    lib.hsm_mlp_inject_fault.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    assert lib.hsm_plan_set_spacing(None, None) == 1
+    assert lib.hsm_mlp_inject_fault(None, 1) == 1
+    h = ctypes.c_void_p()
+    fake = ctypes.c_void_p(16)
+    f = lib.hsm_plan_create
+    f.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int64, ctypes.c_void_p,
+                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_int,
+                  ctypes.c_int, ctypes.c_uint, ctypes.c_void_p]
+    assert f(ctypes.byref(h), 2, 10, fake, fake, None, None, 0.1, 2, 0, 11, None) == 0
+    assert lib.hsm_plan_set_spacing(h, fake) == 0
+    assert lib.hsm_plan_set_spacing(h, None) == 0
+    lib.hsm_plan_destroy.argtypes = [ctypes.c_void_p]
+    assert lib.hsm_plan_destroy(h) == 0
