@@ -1,0 +1,21 @@
+"""The algorithmic work per unit that the benchmark's roofline figures divide
+by: FP64 flops of one RBF-FD system and bytes of one fused application."""
+import bench
+
+
+def test_rbf_flops_per_system():
+    # 2D, m = 2 (6 monomials), n = 12, dx/dy/lap: assembly 642 + null-space solve 3,239
+    assert round(bench.rbf_flops(12, 6, 3)) == 3881
+    # the assembly part alone: offsets 48, pairs 66 x 7, higher monomials 36, RHS 60, unscaling 36
+    assert 2 * 12 * 2 + 66 * 7 + 12 * 3 + 12 * 5 + 12 * 3 == 642
+
+
+def test_apply_bytes_per_node():
+    """Per node: int32 indices, FP64 weights of 3 operators, one read of u and
+    three FP64 outputs: 172 B (MON, 5 nodes), 368 B (RBF-FD, n = 12) and
+    872 B (n = 30); FP32 storage halves the weights and u (outputs stay FP64)."""
+    per = lambda w, f32=False: bench.apply_bytes(None, 1, 1, 0, 5, w, 3, f32)
+    assert bench.apply_bytes(None, 1, 0, 1, 5, 12, 3, False) == 172
+    assert per(12) == 368
+    assert per(30) == 872
+    assert per(12, True) == 48 + 144 + 4 + 24
