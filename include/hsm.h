@@ -257,21 +257,26 @@ enum { HSM_PRECOND_AMG = 0, HSM_PRECOND_JACOBI = 1 };
 /* Creates a stepper on a plan whose weights exist and whose op mask holds
  * every first derivative and the Laplacian.  Copies *phys (the device arrays
  * it points to must stay valid).  Builds the pressure operator (Laplacian rows
- * inside, normal-derivative rows on the boundary).                          */
+ * inside, normal-derivative rows on the boundary) once, from the plan's
+ * weights; the steps read the plan's weights in place.  Weights recomputed
+ * afterwards (or a new hsm_plan_set_spacing and rebuild) need a new stepper. */
 hsm_status hsm_stepper_create(hsm_stepper* out, hsm_plan plan, const hsm_phys* phys);
 
 /* Advances n_steps explicit steps in place (Section 3; Chorin projection):
  *   1. v* = v + dt[-(v.grad)v + Pr lap v + Ra Pr (T - T_ref) e_up], v* = 0 on
  *      walls (e_up = last axis);
  *   2. solve [Lp 1; 1^T 0][p; c] = [div(v*) / dt (0 on walls); 0] by BiCGSTAB,
- *      warm-started from the incoming p;
+ *      warm-started from the incoming p and, within one call, from the last
+ *      step's c (each call starts c at 0: the caller owns p, so v, T and p
+ *      are the whole state to save and restore between calls);
  *   3. v = v* - dt grad p inside, 0 on walls;
  *   4. T = T + dt[-v.grad T + lap T] inside (new v advects T);
  *   5. Dirichlet T = T_bc; insulated nodes T_b = -sum_{i!=b} wn_i T_i / wn_b.
  *   v  device f64 [dim][N], T device f64 [N], p device f64 [N]
  *   krylov_iters  host int [n_steps] or NULL: pressure iterations per step
  * Synchronises once at the end to read the solver status.  Returns
- * HSM_ENOTCONV if a pressure solve hit krylov_max_it (the step still ran).  */
+ * HSM_ENOTCONV if a pressure solve hit krylov_max_it or broke down on
+ * non-finite values (the steps still ran).                                  */
 hsm_status hsm_step(hsm_stepper st, int n_steps, double* v, double* T, double* p,
                     int* krylov_iters);
 
