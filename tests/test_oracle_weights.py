@@ -229,3 +229,28 @@ def test_convergence_rbffd_scattered():
     sl = {op: np.polyfit(np.log(hs), np.log(e[op]), 1)[0] for op in e}
     assert sl["dx"] > 1.5 and sl["dy"] > 1.5, sl
     assert sl["lap"] > 0.7, sl
+
+
+def test_convergence_on_h_refined_sets():
+    """h-refined sets (Section 4.2: spacing h_r/3 at the holes, delta_h = 4)
+    with boundary stencils searched one local spacing inside: the maximum
+    error of the hybrid operators on u = sin(pi x) cos(pi y) over interior
+    nodes falls with h_r at about the method's order (m = 2: 2 for the first
+    derivatives, 1 for the Laplacian).  Measured least-squares slopes over
+    h_r = 1/50, 1/100, 1/200: 2.0 (dx), 1.8 (dy), 1.1 (Laplacian); the bounds
+    leave room for the randomness of the node sets."""
+    hs, errs = [], {op: [] for op in ("dx", "dy", "lap")}
+    for n in (50, 100, 200):
+        ns = nodesets.holes_refined(n=n, n_holes=2, r_range=(0.15, 0.2), delta_h=4.0, seed=nodesets.SEED_BASE + 62)
+        st = ost.build_stencils(ns.coords, ns.is_regular, ns.is_boundary, ns.h, 12, normals=ns.normals,
+                                spacing=ns.spacing)
+        W = ow.all_weights(ns.coords, st, 2)
+        u, ex = nodesets.field_sincos(ns.coords)
+        out = oap.apply_all(ns.N, st, W, u, ("dx", "dy", "lap"))
+        inner = ns.is_boundary == 0
+        hs.append(ns.h)
+        for op in errs:
+            errs[op].append(np.abs(out[op][inner] - ex[op][inner]).max())
+    slope = {op: np.polyfit(np.log(hs), np.log(errs[op]), 1)[0] for op in errs}
+    assert slope["dx"] >= 1.5 and slope["dy"] >= 1.5, slope
+    assert slope["lap"] >= 0.8, slope
