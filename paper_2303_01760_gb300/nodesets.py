@@ -12,6 +12,11 @@ spacing.  The paper's own positioning algorithm (a cited advancing-front fill)
 and its duck-shaped obstacles are not available; circular / spherical holes and
 a Bridson-style dart-throwing fill, both seeded, stand in for them.
 
+The h-refined sets of Sections 4.2 and 4.3 (``holes_refined``) refill the
+layer with a variable-density dart throwing instead: the spacing falls
+linearly from the lattice spacing to a fraction of it at the obstacles, and
+each node's spacing is kept in ``NodeSet.spacing``.
+
 Node order: all nodes are sorted by the Morton code of their position at
 resolution h (ties keep lattice-first construction order), which keeps stencil
 neighbours close in memory.  Node ids are positions in that order.
