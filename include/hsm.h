@@ -168,7 +168,7 @@ hsm_status hsm_plan_export_csr(hsm_plan plan, unsigned op, int64_t* row_ptr, int
                                double* val);
 
 /* Condition number kappa_2(M) = ||M||_2 ||M^-1||_2 of every node's weight
- * system (Section 2.2, "Computational stability"): the MON matrix P^T of a
+ * system (Section 2.1, "Computational stability"): the MON matrix P^T of a
  * regular node, the augmented RBF-FD matrix [A P; P^T 0] of a scattered one,
  * both in the offsets xi = (x - x_c) / s, s = max |x_i - x_c|.  Eigenvalues
  * by the cyclic Jacobi method (at most 40 sweeps), one thread per system; a
@@ -375,27 +375,61 @@ hsm_status hsm_plan_learned_data(hsm_plan plan, float* X, float* Y, int64_t* cou
  * memory while they run (for example a solver embedded in an application
  * that hands all device memory to its own pool at start-up, or a real-time
  * loop in which an allocation could stall or fail).
- *   dim, aug_m, stencil_n, op_mask  as for hsm_plan_create (stencil_n > 0)
+ *   dim, aug_m, stencil_n, op_mask  as for hsm_plan_create (stencil_n > 0);
+ *               sizes for which either the FP32 kernel or the FP64 re-solve
+ *               kernel has no shared-memory shape (for example 2D, m = 1,
+ *               n >= 83) are rejected with HSM_EINVAL before any work
  *   coords      device f64 [dim][n_nodes]
  *   stencils    device int32 [stencil_n][count]; row 0 holds each stencil's
- *               centre, the other rows its neighbours (any order)
+ *               centre, the other rows its neighbours (any order).  Every
+ *               entry must lie in [0, n_nodes): a first pass checks them all
+ *               and returns HSM_EBOUNDS, with weights and node_status left
+ *               untouched, if one does not
  *   count       0 <= count <= HSM_NOALLOC_MAX_SYSTEMS, else HSM_EINVAL
  *   weights     device f64 [popcount(op_mask)][stencil_n][count] (output)
  *   node_status device u8 [n_nodes] or NULL: every entry is set to
  *               HSM_NODE_OK, then centres re-solved in FP64 get
  *               HSM_NODE_REFINE_FP64 and singular ones HSM_NODE_SINGULAR
  * Its scratch (a fail list of HSM_NOALLOC_MAX_SYSTEMS entries, counters and
- * small tables, about 4.3 MB) is one static device array in the library that
+ * small tables, 4,211,200 bytes) is one static device array in the library that
  * every GPU which loads the library holds until the process exits.  All calls
  * share it and it keeps the last call's contents; calls that overlap on the
  * GPU (other streams, other host threads) race on it, so serialise them.  The
  * first call on a device looks up the array's address for that device (with
  * it current); make that first call before any stream capture.  Synchronises
- * the stream twice.  Returns HSM_ESINGULAR when some system is singular.    */
+ * the stream three times.  Returns HSM_ESINGULAR when some system is
+ * singular.                                                                */
 hsm_status hsm_rbf_weights_fp32r_noalloc(int dim, int aug_m, int stencil_n, unsigned op_mask,
                                          const double* coords, int64_t n_nodes, const int32_t* stencils,
                                          int64_t count, double* weights, uint8_t* node_status,
                                          void* cuda_stream);
+
+/* ------------------------------------------------------------------------ */
+/* Measurement and self-check (no paper passage)                             */
+/* ------------------------------------------------------------------------ */
+
+/* FP64 fused multiply-add throughput of the current device, the bound of the
+ * RBF-FD weight solves: 8 independent FMA chains per thread, 8 blocks of 256
+ * threads per SM, 4096 iterations; the best of 5 timed launches (CUDA events
+ * on cuda_stream) after one warm-up.
+ *   gflops  host f64: 2 flop per FMA / best time, in GFLOP/s (required)
+ *   ms      host f32 or NULL: that launch's time
+ * Synchronises the stream.                                                   */
+hsm_status hsm_probe_fp64_peak(double* gflops, float* ms, void* cuda_stream);
+
+/* Hand-written device math helpers of the weight kernels and the fused MLP
+ * pass, evaluated elementwise so that tests can hold them to their error
+ * bounds against IEEE results:
+ *   RECIP     1/x: Newton-Raphson from the single-precision reciprocal;
+ *   SQRT_NR1  sqrt x: one Newton-Raphson step from the single-precision root;
+ *   SQRT_GS   sqrt x: two steps of Goldschmidt's coupled iteration;
+ *   ERF_AS    erf(x) of Abramowitz and Stegun 7.1.28 in FP32 (x >= 0);
+ *   GELU      z Phi(z) in FP32 through ERF_AS.
+ * The FP32 helpers take x rounded to FP32 and return their FP32 result
+ * widened.  x, y device f64 [n]; enqueued on cuda_stream.                    */
+enum { HSM_HELPER_RECIP = 0, HSM_HELPER_SQRT_NR1 = 1, HSM_HELPER_SQRT_GS = 2, HSM_HELPER_ERF_AS = 3,
+       HSM_HELPER_GELU = 4 };
+hsm_status hsm_eval_helper(int fn, const double* x, double* y, int64_t n, void* cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -193,7 +193,7 @@ def stencil_size(dim, m):
 
 def condition_numbers(coords, st, m):
     """2-norm condition numbers kappa(M) = ||M|| ||M^-1|| of every stencil's
-    weight system (Section 2.2, "Computational stability"): the scaled MON
+    weight system (Section 2.1, "Computational stability"): the scaled MON
     matrix P^T of a regular node, the scaled augmented RBF-FD matrix of a
     scattered one.  Scaling by s = max |x_i - x_c| as for the weights.
     Returns {"mon": [N_mon], "rbf": [N_rbf]}."""

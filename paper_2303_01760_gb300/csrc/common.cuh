@@ -242,6 +242,9 @@ struct RbfExternal {
 // indexed by the stencil centre; mark != 0 is written for every solved system.
 cudaError_t launch_rbf_external(const RbfExternal& x, bool r32, const int32_t* list, int64_t count, uint8_t* status,
                                 uint8_t mark, bool* too_big);
+// Whether the FP32-refinement kernel (r32) or the FP64 kernel has a launch
+// shape (shared memory per system within the block limit) for x's sizes.
+cudaError_t rbf_external_fits(const RbfExternal& x, bool r32, bool* fits);
 
 // ---- apply.cu ------------------------------------------------------------
 hsm_status launch_apply(hsm_plan p, unsigned op_mask, hsm_dtype dt, const void* u, double* out,

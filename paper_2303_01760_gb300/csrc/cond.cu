@@ -1,5 +1,5 @@
 // Per-stencil condition numbers kappa_2(M) = ||M|| ||M^-1|| of the weight
-// systems (Section 2.2, "Computational stability"): the scaled MON matrix P^T
+// systems (Section 2.1, "Computational stability"): the scaled MON matrix P^T
 // of a regular node and the scaled augmented RBF-FD matrix [A P; P^T 0] of a
 // scattered one, both in xi = (x - x_c) / s with s = max |x_i - x_c|.
 //

@@ -23,6 +23,7 @@
 // its loop and the tensor memory is released.
 #include <cuda.h>
 
+#include "gelu.cuh"
 #include "mlp.cuh"
 
 namespace hsm {
@@ -132,27 +133,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// GELU(z) = z Phi(z) = (z + |z| erf(|z| / sqrt 2)) / 2, with erf from
-// Abramowitz and Stegun 7.1.28: erf(x) = 1 - (1 + a1 x + ... + a6 x^6)^-16,
-// x >= 0, |error| <= 3e-7 -- far below the bf16 rounding of the activations
-// it feeds, and one reciprocal per element as the only special function.
-__device__ __forceinline__ float gelu(float z) {
-  const float x = fabsf(z) * 0.70710678118654752f;
-  float p = fmaf(x, 0.0000430638f, 0.0002765672f);
-  p = fmaf(x, p, 0.0001520143f);
-  p = fmaf(x, p, 0.0092705272f);
-  p = fmaf(x, p, 0.0422820123f);
-  p = fmaf(x, p, 0.0705230784f);
-  p = fmaf(x, p, 1.0f);
-  float t = __fdividef(1.0f, p);  // (1 + ...)^-1, then ^16 by squaring
-  t *= t;
-  t *= t;
-  t *= t;
-  t *= t;
-  const float e = 1.0f - t;
-  return 0.5f * fmaf(fabsf(z), e, z);
 }
 
 __global__ void __launch_bounds__(kThreads, 1)

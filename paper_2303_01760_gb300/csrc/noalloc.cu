@@ -8,6 +8,7 @@
 // that need the FP64 re-solve, its counter, a status word and the monomial and
 // pair tables) live in one file-scope device array of fixed size below, so
 // nothing is allocated.  The paper has no counterpart to this entry point.
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -63,6 +64,16 @@ int64_t binom(int a, int b) {
   return r;
 }
 
+// Sets kDevBounds in *flags when any of the `total` stencil entries lies
+// outside [0, N).  Runs before the weight kernels, which gather coordinates
+// and write node_status through these ids without checking them.
+__global__ void k_check_ids(const int32_t* __restrict__ ids, int64_t total, int64_t N, unsigned* flags) {
+  bool bad = false;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
+    bad |= (uint64_t)(int64_t)__ldg(ids + i) >= (uint64_t)N;
+  if (bad) atomicOr(flags, hsm::kDevBounds);
+}
+
 }  // namespace
 
 extern "C" hsm_status hsm_rbf_weights_fp32r_noalloc(int dim, int aug_m, int stencil_n, unsigned op_mask,
@@ -83,10 +94,30 @@ extern "C" hsm_status hsm_rbf_weights_fp32r_noalloc(int dim, int aug_m, int sten
   if (!coords || !stencils || !weights) return fail(HSM_EINVAL, "coords, stencils and weights are required");
   if (count == 0) return HSM_OK;
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  int nops = 0;
+  for (int b = 0; b < 4; ++b) nops += (op_mask >> b) & 1;
 
   unsigned char* base = nullptr;
   cudaError_t e = scratch_address(&base);
   if (e != cudaSuccess) return fail_cuda(e, "cudaGetSymbolAddress");
+
+  // both kernels must have a launch shape for these sizes: a system that the
+  // FP32 pass cannot refine is re-solved by the FP64 kernel, whose shared
+  // memory per system is larger for some (dim, m, n)
+  {
+    hsm::RbfExternal probe;
+    probe.dim = dim;
+    probe.n = stencil_n;
+    probe.n_mono = n_mono;
+    probe.nops = nops;
+    for (bool r32 : {true, false}) {
+      bool fits = false;
+      if ((e = hsm::rbf_external_fits(probe, r32, &fits)) != cudaSuccess) return fail_cuda(e, "kernel shape");
+      if (!fits)
+        return fail(HSM_EINVAL, r32 ? "RBF-FD system too large for shared memory (FP32 refinement kernel)"
+                                    : "RBF-FD system too large for shared memory (FP64 re-solve kernel)");
+    }
+  }
   int* fail_count = reinterpret_cast<int*>(base);
   unsigned* flags = reinterpret_cast<unsigned*>(base + 4);
   int32_t* fail_list = reinterpret_cast<int32_t*>(base + kCtlBytes);
@@ -120,6 +151,21 @@ extern "C" hsm_status hsm_rbf_weights_fp32r_noalloc(int dim, int aug_m, int sten
     return fail_cuda(e, "cudaMemcpyAsync(exponents)");
   // the scratch keeps the previous call's contents: clear what must start at zero
   if ((e = cudaMemsetAsync(base, 0, 8, s)) != cudaSuccess) return fail_cuda(e, "cudaMemsetAsync(scratch)");
+
+  // every stencil id (centres included) must lie in [0, n_nodes) before any
+  // kernel gathers through it; nothing is written to the outputs otherwise
+  {
+    const int64_t total = (int64_t)stencil_n * count;
+    const int T = 256;
+    const int grid = (int)std::min<int64_t>(hsm::ceil_div(total, T), (int64_t)hsm::num_sms() * 8);
+    k_check_ids<<<grid, T, 0, s>>>(stencils, total, n_nodes, flags);
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail_cuda(e, "stencil id check launch");
+    unsigned fl0 = 0;
+    if ((e = cudaMemcpyAsync(&fl0, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+      return fail_cuda(e, "cudaMemcpyAsync(flags)");
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail_cuda(e, "cudaStreamSynchronize");
+    if (fl0 & hsm::kDevBounds) return fail(HSM_EBOUNDS, "a stencil id lies outside [0, n_nodes)");
+  }
   if (node_status && (e = cudaMemsetAsync(node_status, HSM_NODE_OK, (size_t)n_nodes, s)) != cudaSuccess)
     return fail_cuda(e, "cudaMemsetAsync(node_status)");
 
@@ -132,7 +178,7 @@ extern "C" hsm_status hsm_rbf_weights_fp32r_noalloc(int dim, int aug_m, int sten
   x.n = stencil_n;
   x.n_mono = n_mono;
   x.op_mask = op_mask;
-  for (int b = 0; b < 4; ++b) x.nops += (op_mask >> b) & 1;
+  x.nops = nops;
   x.mono_exp = exps;
   x.pairs = pairs;
   x.w = weights;
@@ -142,8 +188,8 @@ extern "C" hsm_status hsm_rbf_weights_fp32r_noalloc(int dim, int aug_m, int sten
   x.stream = s;
   bool too_big = false;
   e = hsm::launch_rbf_external(x, true, nullptr, count, nullptr, 0, &too_big);
-  if (too_big) return fail(HSM_EINVAL, "RBF-FD system too large for shared memory");
   if (e != cudaSuccess) return fail_cuda(e, "FP32 refinement launch");
+  if (too_big) return fail(HSM_EINVAL, "RBF-FD system too large for shared memory");
   int fc = 0;
   if ((e = cudaMemcpyAsync(&fc, fail_count, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
     return fail_cuda(e, "cudaMemcpyAsync(fail count)");
@@ -151,6 +197,9 @@ extern "C" hsm_status hsm_rbf_weights_fp32r_noalloc(int dim, int aug_m, int sten
   if (fc > 0) {
     e = hsm::launch_rbf_external(x, false, fail_list, fc, node_status, HSM_NODE_REFINE_FP64, &too_big);
     if (e != cudaSuccess) return fail_cuda(e, "FP64 re-solve launch");
+    // cannot happen after the shape check above; never return weights the
+    // re-solve did not write as if they were valid
+    if (too_big) return fail(HSM_EINVAL, "FP64 RBF-FD system too large for shared memory");
   }
   unsigned fl = 0;
   if ((e = cudaMemcpyAsync(&fl, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s)) != cudaSuccess)

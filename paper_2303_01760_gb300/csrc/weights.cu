@@ -379,6 +379,16 @@ cudaError_t launch_rbf_external(const RbfExternal& x, bool r32, const int32_t* l
   return cudaLaunchKernel(sh.fn, dim3(grid), dim3(sh.threads), args, sh.smem, x.stream);
 }
 
+cudaError_t rbf_external_fits(const RbfExternal& x, bool r32, bool* fits) {
+  *fits = false;
+  const int K = x.n + x.n_mono;
+  RbfShape sh;
+  cudaError_t e = rbf_shape(r32, x.dim, x.nops, K, (K + x.nops) | 1, x.n, 8, &sh);
+  if (e != cudaSuccess) return e;
+  *fits = sh.fn != nullptr;
+  return cudaSuccess;
+}
+
 // MON weights of the G (or *G_dev) nodes of the MON group into w, on stream s.
 static cudaError_t launch_mon(hsm_plan p, int64_t G, const int* G_dev, double* w, uint8_t* status,
                               cudaStream_t s) {

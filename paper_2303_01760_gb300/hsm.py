@@ -38,6 +38,8 @@ class hsm_phys(C.Structure):
                 ("krylov_max_it", C.c_int), ("precond", C.c_int)]
 
 
+(HSM_OK, HSM_EINVAL, HSM_ENOMEM, HSM_ECUDA, HSM_ESINGULAR, HSM_ENOTCONV, HSM_ETIMEOUT, HSM_EBOUNDS,
+ HSM_ESTATE) = range(9)
 HSM_FAULT_NONE, HSM_FAULT_HOLD_MLP_LOADS = 0, 1
 
 HSM_PRECOND_AMG = 0
@@ -79,7 +81,10 @@ _SIGS = {
     "hsm_mlp_inject_fault": (C.c_int, [_p, C.c_int]),
     "hsm_mlp_attach": (C.c_int, [_p, _p]),
     "hsm_plan_learned_data": (C.c_int, [_p, _p, _p, C.POINTER(_i64)]),
+    "hsm_probe_fp64_peak": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_float), _p]),
+    "hsm_eval_helper": (C.c_int, [C.c_int, _p, _p, _i64, _p]),
 }
+HSM_HELPER_RECIP, HSM_HELPER_SQRT_NR1, HSM_HELPER_SQRT_GS, HSM_HELPER_ERF_AS, HSM_HELPER_GELU = range(5)
 HSM_NOALLOC_MAX_SYSTEMS = 1 << 20
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name, None)
@@ -290,7 +295,7 @@ class Plan:
         return out
 
     def condition(self, out=None):
-        """kappa_2 of every node's weight system (Section 2.2), f64 CUDA [N]."""
+        """kappa_2 of every node's weight system (Section 2.1), f64 CUDA [N]."""
         import torch
 
         if out is None:
@@ -409,3 +414,20 @@ def rbf_weights_fp32r_noalloc(dim, m, n, op_mask, coords, stencils, weights, nod
     return lib.hsm_rbf_weights_fp32r_noalloc(int(dim), int(m), int(n), int(op_mask), ptr(coords),
                                              int(coords.shape[1]), ptr(stencils), int(stencils.shape[1]),
                                              ptr(weights), ptr(node_status), stream_handle(stream))
+
+
+def probe_fp64_peak(stream=None):
+    """Measured FP64 FMA throughput of the current device: (GFLOP/s, ms)."""
+    g, ms = C.c_double(), C.c_float()
+    check(lib.hsm_probe_fp64_peak(C.byref(g), C.byref(ms), stream_handle(stream)))
+    return g.value, ms.value
+
+
+def eval_helper(fn, x, stream=None):
+    """One of the HSM_HELPER_* device math helpers applied elementwise to the
+    f64 CUDA tensor ``x``; returns a new f64 tensor."""
+    import torch
+
+    y = torch.empty_like(x)
+    check(lib.hsm_eval_helper(int(fn), ptr(x), ptr(y), int(x.numel()), stream_handle(stream)))
+    return y

@@ -1,0 +1,74 @@
+"""Autotuned launch configurations against the FP64 oracle.
+
+hsm_plan_autotune picks, per plan, the threads per kNN query, the lanes per
+RBF-FD system (FP64 and FP32 + refinement) and the apply block size.  Every
+configuration it can pick must give the oracle's stencils (bit-exact), weights
+(1e-10 FP64, 1e-5 FP32 + refinement) and operator values.  The tuner's own
+choice is checked, then every variant is forced through its cache file."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import apply as oap
+from oracle import stencils as ost
+from oracle import weights as ow
+from paper_2303_01760_gb300 import nodesets
+
+from gpu_helpers import gpu_csr, to_dev
+
+pytestmark = pytest.mark.gpu
+
+BIT = {"dx": 1, "dy": 2, "dz": 4, "lap": 8}
+
+
+def _check(plan, ns, st, W, prec, tol):
+    import torch
+
+    plan.build_stencils()
+    assert plan.compute_weights(prec) == 0
+    u, _ = nodesets.field_sincos(ns.coords)
+    out = plan.apply(torch.from_numpy(u).cuda()).cpu().numpy()
+    for k, op in enumerate(("dx", "dy", "lap")):
+        rp, col, val = gpu_csr(plan, BIT[op])
+        for grp, width in (("mon", 5), ("rbf", 12)):
+            nodes = st[grp + "_nodes"]
+            ix = rp[nodes][:, None] + np.arange(width)[None, :]
+            assert np.array_equal(col[ix], st[grp + "_idx"])
+            e = np.abs(val[ix] - W[grp][op]).max(1) / np.abs(W[grp][op]).max(1)
+            assert e.max() <= tol, (grp, op, prec, e.max())
+            ref = oap.apply_group(st[grp + "_idx"], W[grp][op], u)
+            scale = (np.abs(W[grp][op]) * np.abs(u[st[grp + "_idx"]])).sum(1)
+            assert np.all(np.abs(out[k, nodes] - ref) <= max(tol, 1e-12) * 10 * scale)
+
+
+def test_autotuned_plan_and_every_variant_match_the_oracle(tmp_path):
+    from paper_2303_01760_gb300 import hsm
+
+    ns = nodesets.square_wall_band(n=60, seed=nodesets.SEED_BASE + 5)
+    st = ost.build_stencils(ns.coords, ns.is_regular, ns.is_boundary, ns.h, 12, normals=ns.normals)
+    W = ow.all_weights(ns.coords, st, 2)
+    dv = to_dev(ns)
+
+    def plan_with(cache):
+        p = hsm.Plan(dv["coords"], dv["is_regular"], dv["is_boundary"], ns.h, m=2, normals=dv["normals"])
+        p.build_stencils()
+        p.autotune(cache)
+        return p
+
+    cache = str(tmp_path / "tune.txt")
+    p = plan_with(cache)                      # times the variants, writes the cache
+    _check(p, ns, st, W, hsm.HSM_PREC_FP64, 1e-10)
+    _check(p, ns, st, W, hsm.HSM_PREC_FP32_REFINE, 1e-5)
+    p.close()
+    key, chosen = open(cache).read().split()
+    assert len(chosen.split(",")) == 4
+    # apply threads, FP64 lanes, kNN threads per query, FP32 lanes
+    for t, l64, q, l32 in ((64, 4, 2, 16), (128, 16, 4, 32), (256, 32, 1, 4)):
+        with open(cache, "w") as f:
+            f.write(f"{key} {t},{l64},{q},{l32}\n")
+        p = plan_with(cache)                  # loads the forced variant
+        _check(p, ns, st, W, hsm.HSM_PREC_FP64, 1e-10)
+        _check(p, ns, st, W, hsm.HSM_PREC_FP32_REFINE, 1e-5)
+        p.close()
+    assert os.path.exists(cache)

@@ -1,4 +1,4 @@
-"""Per-stencil condition numbers (Section 2.2) through the C ABI against the
+"""Per-stencil condition numbers (Section 2.1) through the C ABI against the
 oracle."""
 import numpy as np
 import pytest
@@ -33,7 +33,7 @@ def _check(ns, m):
 
 def test_condition_2d_and_3d():
     kap, st = _check(nodesets.square_wall_band(n=30), 2)
-    # RBF-FD systems are worse conditioned than MON ones (Section 2.2)
+    # RBF-FD systems are worse conditioned than MON ones (Section 2.1)
     assert np.median(kap[st["rbf_nodes"]]) > 10 * np.median(kap[st["mon_nodes"]])
     _check(nodesets.cube_spheres(n=14, n_holes=2, r_range=(0.1, 0.15), band=0.12, seed=nodesets.SEED_BASE + 21), 2)
     # a coarser 3D set with one system singular to working precision

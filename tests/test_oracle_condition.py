@@ -1,4 +1,4 @@
-"""Pins of the oracle's per-stencil condition numbers (Section 2.2)."""
+"""Pins of the oracle's per-stencil condition numbers (Section 2.1)."""
 import numpy as np
 
 from oracle import stencils as ost
@@ -25,6 +25,6 @@ def test_rbf_condition_from_the_spectrum():
     M, _ = ow.rbffd_system(xi, 2, ow.ops_for(2))
     lam = np.abs(np.linalg.eigvalsh(M))
     assert np.allclose(k["rbf"], lam.max(1) / lam.min(1), rtol=1e-9)
-    # the qualitative claim of Section 2.2: RBF-FD systems are worse conditioned
+    # the qualitative claim of Section 2.1: RBF-FD systems are worse conditioned
     assert np.median(k["rbf"]) > 10 * np.median(k["mon"])
     assert np.all(k["mon"] >= 1.0)
