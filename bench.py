@@ -894,7 +894,7 @@ def run_kernels(args):
         bc = torch.from_numpy(ns.bc).to(dev)
         Tbc = torch.from_numpy(ns.T_bc).to(dev)
         st = hsm.Stepper(plan, 1e6, 0.71, 0.1 * ns.h * ns.h / 2.0, ns.T_ref, bc, Tbc, nrm, krylov_tol=1e-10,
-                         krylov_max_it=4000)
+                         krylov_max_it=4000, guess_order=args.guess_order)
         v = torch.zeros((2, ns.N), dtype=torch.float64, device=dev)
         T = torch.where(bc == 1, Tbc, torch.zeros_like(Tbc)).contiguous()
         p = torch.zeros(ns.N, dtype=torch.float64, device=dev)
@@ -905,9 +905,9 @@ def run_kernels(args):
         its, _ = st.step(v, T, p, args.steps, allow_notconv=True)
         ev[1].record()
         torch.cuda.synchronize()
+        print("stepper ok", ns.N, its, "ms/step %.3f" % (ev[0].elapsed_time(ev[1]) / args.steps), st.info())
         st.close()
         plan.close()
-        print("stepper ok", ns.N, its, "ms/step %.3f" % (ev[0].elapsed_time(ev[1]) / args.steps))
         return
     for _ in range(args.warmup + args.steps):
         plan.build_stencils()
@@ -1228,6 +1228,88 @@ def run_sweep(args):
                                 "S": S, "sets": rows}}))
 
 
+def oracle_steps(n_steps, out_npz, seed_set="square_holes"):
+    """The oracle's stepper on the 2D irregular workload from rest, Ra = 1e6,
+    Pr = 0.71, dt = 0.1 h^2/2 (exact pressure solve by sparse LU): the fields
+    after ``n_steps`` steps go to ``out_npz``, with the host seconds it took."""
+    import numpy as np
+
+    from oracle import stencils as ost
+    from oracle import stepper as ostep
+    from oracle import weights as ow
+    from paper_2303_01760_gb300 import nodesets
+
+    ns = nodesets.cached(getattr(nodesets, seed_set))
+    t0 = time.perf_counter()
+    st = ost.build_stencils(ns.coords, ns.is_regular, ns.is_boundary, ns.h, 12, normals=ns.normals,
+                            use_kdtree=True)
+    W = ow.all_weights(ns.coords, st, 2)
+    S = ostep.Stepper(ns.coords, ns.bc, ns.T_bc, ns.normals, ns.T_ref, st, W, 1e6, 0.71, ostep.dt_rule(ns.h))
+    v, T = ostep.initial_state(2, ns.N, ns.bc, ns.T_bc)
+    t1 = time.perf_counter()
+    v, T, p = S.run(v, T, n_steps)
+    t2 = time.perf_counter()
+    np.savez(out_npz, v=v, T=T, p=p, setup_s=t1 - t0, steps_s=t2 - t1)
+
+
+def run_field_linf(args):
+    """Field L-inf error of the GPU stepper after a fixed number of steps on
+    the full 2D irregular workload (222,555 nodes), against the oracle run for
+    the same steps in a separate single-threaded process: T and v, each
+    relative to the largest magnitude of the oracle's field."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2303_01760_gb300 import hsm, nodesets
+
+    S = args.field_linf
+    dev = torch.device("cuda:0")
+    ns = nodesets.cached(nodesets.square_holes)
+    d = {k: torch.from_numpy(np.ascontiguousarray(getattr(ns, k))).to(dev)
+         for k in ("coords", "is_regular", "is_boundary", "normals", "bc", "T_bc")}
+    plan = hsm.Plan(d["coords"], d["is_regular"], d["is_boundary"], ns.h, m=2, normals=d["normals"])
+    plan.build_stencils()
+    plan.compute_weights(hsm.HSM_PREC_FP64)
+    dt = 0.1 * ns.h * ns.h / 2.0
+    st = hsm.Stepper(plan, 1e6, 0.71, dt, ns.T_ref, d["bc"], d["T_bc"], d["normals"], krylov_tol=args.krylov_tol,
+                     krylov_max_it=4000)
+    v = torch.zeros((2, ns.N), dtype=torch.float64, device=dev)
+    T = torch.where(d["bc"] == 1, d["T_bc"], torch.zeros_like(d["T_bc"])).contiguous()
+    p = torch.zeros(ns.N, dtype=torch.float64, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    ev[0].record()
+    its, code = st.step(v, T, p, S, allow_notconv=True)
+    ev[1].record()
+    torch.cuda.synchronize()
+    gpu_ms = ev[0].elapsed_time(ev[1])
+    info = st.info()
+    g = dict(v=v.cpu().numpy(), T=T.cpu().numpy())
+    st.close()
+    plan.close()
+    out_npz = os.path.join(ROOT, "build", "oracle_field_linf.npz")
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code_s = ("import sys; sys.path.insert(0, %r); import bench; bench.oracle_steps(%d, %r)" % (ROOT, S, out_npz))
+    r = subprocess.run([sys.executable, "-c", code_s], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        print(json.dumps({"field_linf": {"error": r.stderr[-800:]}}))
+        return
+    o = np.load(out_npz)
+    rel = {k: float(np.abs(g[k] - o[k]).max() / max(np.abs(o[k]).max(), 1e-300)) for k in ("T", "v")}
+    print(json.dumps({"field_linf": {
+        "workload": "2D irregular domain, 222,555 nodes (h = 0.002, 8 holes), Ra = 1e6, Pr = 0.71, "
+                    "dt = 0.1 h^2/2, from rest; FP64 weights and state",
+        "steps": S, "krylov_tol": args.krylov_tol, "rel_linf": rel,
+        "gpu": {"ms_per_step": gpu_ms / S, "krylov_iters_mean": float(np.mean(its)),
+                "krylov_iters_last100": float(np.mean(its[-100:])), "status": int(code), **info},
+        "oracle": {"setup_s": float(o["setup_s"]), "steps_s": float(o["steps_s"]), "cores": 1,
+                   "pressure": "sparse LU of the bordered system, factored once"},
+        "max_abs": {"T": float(np.abs(o["T"]).max()), "v": float(np.abs(o["v"]).max())}}}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1253,7 +1335,15 @@ def main():
     ap.add_argument("--refined-steps", type=int, default=500, help="with --refined")
     ap.add_argument("--sweep", action="store_true", help="scattered-fraction sweep (5..100 %%), m = 2 and 4")
     ap.add_argument("--sweep-steps", type=int, default=100, help="with --sweep: explicit steps timed per set")
+    ap.add_argument("--guess-order", type=int, default=0, help="with --kernels --stepper: pressure initial "
+                    "guess (0 quadratic extrapolation, 1 linear, -1 last solution)")
+    ap.add_argument("--field-linf", type=int, default=0,
+                    help="GPU stepper vs the oracle after this many steps on the 2D irregular workload")
+    ap.add_argument("--krylov-tol", type=float, default=1e-12, help="with --field-linf")
     args = ap.parse_args()
+    if args.field_linf:
+        run_field_linf(args)
+        return
     if args.dvd:
         args.t_end = 0.15 if args.t_end is None else args.t_end
         run_dvd(args)

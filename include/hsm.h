@@ -245,6 +245,9 @@ typedef struct {
   double krylov_tol;     /* relative residual of the pressure solve (e.g. 1e-12)   */
   int krylov_max_it;     /* iteration cap of the pressure solve (e.g. 2000)        */
   int precond;           /* HSM_PRECOND_AMG (0, default) or HSM_PRECOND_JACOBI     */
+  int guess_order;       /* initial guess of each pressure solve from the call's
+                            previous solutions: 0 = quadratic extrapolation
+                            (default), 1 = linear, -1 = the last solution      */
 } hsm_phys;
 
 /* Right preconditioner of the pressure BiCGSTAB.  AMG: an aggregation
@@ -265,10 +268,13 @@ hsm_status hsm_stepper_create(hsm_stepper* out, hsm_plan plan, const hsm_phys* p
 /* Advances n_steps explicit steps in place (Section 3; Chorin projection):
  *   1. v* = v + dt[-(v.grad)v + Pr lap v + Ra Pr (T - T_ref) e_up], v* = 0 on
  *      walls (e_up = last axis);
- *   2. solve [Lp 1; 1^T 0][p; c] = [div(v*) / dt (0 on walls); 0] by BiCGSTAB,
- *      warm-started from the incoming p and, within one call, from the last
- *      step's c (each call starts c at 0: the caller owns p, so v, T and p
- *      are the whole state to save and restore between calls);
+ *   2. solve [Lp 1; 1^T 0][p; c] = [div(v*) / dt (0 on walls); 0] by BiCGSTAB.
+ *      The first two steps of a call start from the incoming p (c = 0) and
+ *      the last solution; later steps of the same call start from (p, c)
+ *      extrapolated in time from the call's last two (linear, third step) or
+ *      three (quadratic) solutions.  Each call starts afresh:
+ *      the caller owns p, so v, T and p are the whole state to save and
+ *      restore between calls;
  *   3. v = v* - dt grad p inside, 0 on walls;
  *   4. T = T + dt[-v.grad T + lap T] inside (new v advects T);
  *   5. Dirichlet T = T_bc; insulated nodes T_b = -sum_{i!=b} wn_i T_i / wn_b.
@@ -279,6 +285,19 @@ hsm_status hsm_stepper_create(hsm_stepper* out, hsm_plan plan, const hsm_phys* p
  * non-finite values (the steps still ran).                                  */
 hsm_status hsm_step(hsm_stepper st, int n_steps, double* v, double* T, double* p,
                     int* krylov_iters);
+
+/* Shape of the stepper's pressure solve (host outputs, any may be NULL):
+ *   mg_levels        multigrid levels (0 with the Jacobi preconditioner)
+ *   mg_tail_level    first level whose cycle work runs in the one
+ *                    thread-block-cluster kernel (0: none; picked by timing
+ *                    at hsm_stepper_create)
+ *   mg_tail_ctas     CTAs per cluster the device schedules (0: none)
+ *   kernels_per_iter kernels one Krylov iteration launches
+ *   tail_ms          host f32 [16] or NULL: device time of 10 cycles with
+ *                    the tail from level l (entry 0: no tail), -1 where the
+ *                    choice was not timed                                   */
+hsm_status hsm_stepper_info(hsm_stepper st, int* mg_levels, int* mg_tail_level, int* mg_tail_ctas,
+                            int* kernels_per_iter, float* tail_ms);
 
 hsm_status hsm_stepper_destroy(hsm_stepper st);
 
@@ -409,11 +428,12 @@ hsm_status hsm_rbf_weights_fp32r_noalloc(int dim, int aug_m, int stencil_n, unsi
 /* ------------------------------------------------------------------------ */
 
 /* FP64 fused multiply-add throughput of the current device, the bound of the
- * RBF-FD weight solves: 8 independent FMA chains per thread, 8 blocks of 256
- * threads per SM, 4096 iterations; the best of 5 timed launches (CUDA events
- * on cuda_stream) after one warm-up.
- *   gflops  host f64: 2 flop per FMA / best time, in GFLOP/s (required)
- *   ms      host f32 or NULL: that launch's time
+ * RBF-FD weight solves: 4, 8 or 16 independent FMA chains per thread, 4 or 8
+ * blocks of 256 threads per SM, 4096 iterations; the best rate over those
+ * shapes of 3 timed launches each (CUDA events on cuda_stream) after one
+ * warm-up.
+ *   gflops  host f64: 2 flop per FMA / time, in GFLOP/s (required)
+ *   ms      host f32 or NULL: the best launch's time
  * Synchronises the stream.                                                   */
 hsm_status hsm_probe_fp64_peak(double* gflops, float* ms, void* cuda_stream);
 

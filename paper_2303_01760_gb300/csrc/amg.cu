@@ -64,7 +64,7 @@ __device__ __forceinline__ double row_dot(const MgLevel& L, int g, int64_t p, co
 // ---- cycle -------------------------------------------------------------------
 // x = w f + w (f - A w f), w = omega D^-1: two Jacobi sweeps from zero.
 __global__ void __launch_bounds__(kMgThreads) k_mg_pre(MgLevel L, const double* __restrict__ f, const double* done) {
-  if (*done != 0.0) return;
+  if (done && *done != 0.0) return;
   int g;
   int64_t p, stride;
   mg_rows(L, g, p, stride);
@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_pre(MgLevel L, const double* 
 __global__ void __launch_bounds__(kMgThreads) k_mg_restrict(MgLevel L, const double* __restrict__ f,
                                                             double* __restrict__ fc, int64_t nc, const double* done) {
   constexpr int kBatch = 8;
-  if (*done != 0.0) return;
+  if (done && *done != 0.0) return;
   for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < nc; I += (int64_t)gridDim.x * blockDim.x) {
     double s = 0.0;
     const int32_t m1 = L.mstart[I + 1];
@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_restrict(MgLevel L, const dou
 __global__ void __launch_bounds__(kMgThreads) k_mg_post1(MgLevel L, const double* __restrict__ f,
                                                          const double* __restrict__ xc, double alpha,
                                                          const double* done) {
-  if (*done != 0.0) return;
+  if (done && *done != 0.0) return;
   int g;
   int64_t p, stride;
   mg_rows(L, g, p, stride);
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_post1(MgLevel L, const double
 __global__ void __launch_bounds__(kMgThreads) k_mg_post2(MgLevel L, const double* __restrict__ f,
                                                          double* __restrict__ out, int border,
                                                          const double* done) {
-  if (*done != 0.0) return;
+  if (done && *done != 0.0) return;
   int g;
   int64_t p, stride;
   mg_rows(L, g, p, stride);
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_post2(MgLevel L, const double
 __global__ void __launch_bounds__(kMgThreads) k_mg_coarse(const double* __restrict__ binv, int m,
                                                           const double* __restrict__ f, double* __restrict__ x,
                                                           int64_t border, const double* done) {
-  if (*done != 0.0) return;
+  if (done && *done != 0.0) return;
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); r < m; r += warps) {
@@ -160,6 +160,109 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_coarse(const double* __restri
     if (lane == 0) x[r] = s;
   }
   if (border >= 0 && blockIdx.x == 0 && threadIdx.x == 0) x[border] = f[border];
+}
+
+// ---- the coarse levels in one thread-block cluster -------------------------
+// Levels lt..L-1 of a cycle (their smoothing, restriction, the dense coarsest
+// solve and the way back up) run in one launch of one cluster of CTAs, the
+// phases separated by the cluster's hardware barrier instead of kernel
+// boundaries: on these levels every phase is a chain of a few dependent L2
+// loads over a few thousand rows, so a launch per phase costs more than its
+// work.  Vectors written inside the kernel (x, y, f of the levels) are read
+// through L2 (ld.global.cg): the barrier orders the writes of one CTA before
+// the reads of another at cluster scope, and no stale L1 line of another SM
+// can be hit.  Level descriptors are read from device memory.
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned cluster_size() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ double row_dot_cg(const MgLevel& L, int64_t p, const double* x) {
+  const int W = L.width[0];
+  const int64_t G = L.count[0];
+  double s = 0.0;
+  for (int e = 0; e < W; ++e) s = fma(L.val[0][(int64_t)e * G + p], __ldcg(x + L.idx[0][(int64_t)e * G + p]), s);
+  return s;
+}
+
+__global__ void __launch_bounds__(1024, 1) k_mg_tail(const MgLevel* __restrict__ lev, int lt, int L,
+                                                    const double* __restrict__ binv, int m, double alpha,
+                                                    const double* done) {
+  if (done && *done != 0.0) return;  // the same value for every thread of the cluster
+  const int64_t t0 = (int64_t)cluster_rank() * blockDim.x + threadIdx.x;
+  const int64_t T = (int64_t)cluster_size() * blockDim.x;
+  for (int l = lt; l + 1 < L; ++l) {
+    const MgLevel F = lev[l];
+    // x = w f + w (f - A w f)
+    for (int64_t i = t0; i < F.n; i += T) {
+      const int W = F.width[0];
+      const int64_t G = F.count[0];
+      double acc = 0.0;
+      for (int e = 0; e < W; ++e) {
+        const int32_t j = F.idx[0][(int64_t)e * G + i];
+        acc = fma(F.val[0][(int64_t)e * G + i], F.odinv[j] * __ldcg(F.f + j), acc);
+      }
+      const double fi = __ldcg(F.f + i), di = F.odinv[i];
+      __stcg(F.x + i, di * fi + di * (fi - acc));
+    }
+    cluster_sync_all();
+    // fc[I] = sum over the rows of aggregate I of (f - A x)
+    const int64_t nc = lev[l + 1].n;
+    double* fc = lev[l + 1].f;
+    for (int64_t I = t0; I < nc; I += T) {
+      double sum = 0.0;
+      const int32_t m1 = F.mstart[I + 1];
+      for (int32_t k = F.mstart[I]; k < m1; ++k) {
+        const int32_t r = F.mlist[k];
+        sum += __ldcg(F.f + r) - row_dot_cg(F, r, F.x);
+      }
+      __stcg(fc + I, sum);
+    }
+    cluster_sync_all();
+  }
+  // coarsest level: x = Binv f, one warp per row
+  {
+    const MgLevel C = lev[L - 1];
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = t0 >> 5, nw = T >> 5;
+    for (int64_t r = w0; r < m; r += nw) {
+      double acc = 0.0;
+      for (int c = lane; c < m; c += 32) acc = fma(binv[r * m + c], __ldcg(C.f + c), acc);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) __stcg(C.x + r, acc);
+    }
+  }
+  cluster_sync_all();
+  for (int l = L - 2; l >= lt; --l) {
+    const MgLevel F = lev[l];
+    const double* xc = lev[l + 1].x;
+    const int W = F.width[0];
+    const int64_t G = F.count[0];
+    // y = x' + w (f - A x'), x' = x + alpha P xc
+    for (int64_t i = t0; i < F.n; i += T) {
+      double acc = 0.0;
+      for (int e = 0; e < W; ++e) {
+        const int32_t j = F.idx[0][(int64_t)e * G + i];
+        acc = fma(F.val[0][(int64_t)e * G + i], fma(alpha, __ldcg(xc + F.agg[j]), __ldcg(F.x + j)), acc);
+      }
+      const double xi = fma(alpha, __ldcg(xc + F.agg[i]), __ldcg(F.x + i));
+      __stcg(F.y + i, fma(F.odinv[i], __ldcg(F.f + i) - acc, xi));
+    }
+    cluster_sync_all();
+    // x = y + w (f - A y)
+    for (int64_t i = t0; i < F.n; i += T)
+      __stcg(F.x + i, fma(F.odinv[i], __ldcg(F.f + i) - row_dot_cg(F, i, F.y), __ldcg(F.y + i)));
+    cluster_sync_all();
+  }
 }
 
 // ---- set-up ------------------------------------------------------------------
@@ -581,22 +684,46 @@ hsm_status amg_setup(hsm_plan pl, const double* wp_mon, const double* wp_rbf, do
   return HSM_OK;
 }
 
-cudaError_t amg_vcycle(const Amg& A, const double* in, double* out, const double* done, cudaStream_t s) {
+static cudaError_t launch_tail(const Amg& A, int lt, const double* done, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)A.tail_ctas;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3((unsigned)A.tail_ctas);
+  cfg.blockDim = dim3(1024);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_mg_tail, (const MgLevel*)A.dlev, lt, A.L, (const double*)A.binv, A.m, A.alpha,
+                            done);
+}
+
+static cudaError_t vcycle_lt(const Amg& A, int lt, const double* in, double* out, const double* done,
+                             cudaStream_t s) {
   const int cg = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div((int64_t)A.m, kMgThreads / 32), 1024));
   if (A.L == 1) {
     k_mg_coarse<<<cg, kMgThreads, 0, s>>>(A.binv, A.m, in, out, A.lev[0].n, done);
     return cudaGetLastError();
   }
+  const int stop = lt > 0 ? lt : A.L - 1;  // first level not handled by per-level kernels
   const double* f = in;
-  for (int l = 0; l + 1 < A.L; ++l) {
+  for (int l = 0; l < stop; ++l) {
     const MgLevel& F = A.lev[l];
     k_mg_pre<<<F.blocks, kMgThreads, 0, s>>>(F, f, done);
     k_mg_restrict<<<F.cblocks, kMgThreads, 0, s>>>(F, f, A.lev[l + 1].f, A.lev[l + 1].n, done);
     f = A.lev[l + 1].f;
   }
-  const MgLevel& Cs = A.lev[A.L - 1];
-  k_mg_coarse<<<cg, kMgThreads, 0, s>>>(A.binv, A.m, Cs.f, Cs.x, -1, done);
-  for (int l = A.L - 2; l >= 0; --l) {
+  if (lt > 0) {
+    cudaError_t e = launch_tail(A, lt, done, s);
+    if (e != cudaSuccess) return e;
+  } else {
+    const MgLevel& Cs = A.lev[A.L - 1];
+    k_mg_coarse<<<cg, kMgThreads, 0, s>>>(A.binv, A.m, Cs.f, Cs.x, -1, done);
+  }
+  for (int l = stop - 1; l >= 0; --l) {
     const MgLevel& F = A.lev[l];
     const double* fl = l == 0 ? in : F.f;
     k_mg_post1<<<F.blocks, kMgThreads, 0, s>>>(F, fl, A.lev[l + 1].x, A.alpha, done);
@@ -605,7 +732,91 @@ cudaError_t amg_vcycle(const Amg& A, const double* in, double* out, const double
   return cudaGetLastError();
 }
 
-int amg_kernels_per_cycle(const Amg& A) { return A.L == 1 ? 1 : 4 * (A.L - 1) + 1; }
+cudaError_t amg_vcycle(const Amg& A, const double* in, double* out, const double* done, cudaStream_t s) {
+  return vcycle_lt(A, A.lt, in, out, done, s);
+}
+
+int amg_kernels_per_cycle(const Amg& A) {
+  if (A.L == 1) return 1;
+  return 4 * (A.lt > 0 ? A.lt : A.L - 1) + 1;
+}
+
+hsm_status amg_tune_tail(hsm_plan pl, Amg* A) {
+  cudaStream_t s = pl->stream;
+  A->lt = 0;
+  for (int l = 0; l < kMgMaxLevels; ++l) A->tail_ms[l] = -1.f;
+  if (A->L < 2) return HSM_OK;
+  // the largest cluster the device schedules with 1024-thread CTAs
+  int ctas = 0;
+  for (int cl : {16, 8}) {
+    if (cl > 8 && cudaFuncSetAttribute(k_mg_tail, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)cl;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)cl);
+    cfg.blockDim = dim3(1024);
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k_mg_tail, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (nclusters >= 1) {
+      ctas = cl;
+      break;
+    }
+  }
+  if (!ctas) return HSM_OK;
+  A->tail_ctas = ctas;
+  HSM_CUDA(pl, dev_alloc(&A->dlev, A->L, s));
+  HSM_CUDA(pl, cudaMemcpyAsync(A->dlev, A->lev, A->L * sizeof(MgLevel), cudaMemcpyHostToDevice, s));
+  // time each choice of the first tail level on zero vectors
+  const int64_t N1 = A->lev[0].n + 1;
+  double *in = nullptr, *out = nullptr, *done = nullptr;
+  HSM_CUDA(pl, dev_alloc(&in, N1, s));
+  HSM_CUDA(pl, dev_alloc(&out, N1, s));
+  HSM_CUDA(pl, dev_alloc(&done, 1, s));
+  HSM_CUDA(pl, cudaMemsetAsync(in, 0, N1 * sizeof(double), s));
+  HSM_CUDA(pl, cudaMemsetAsync(done, 0, sizeof(double), s));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  HSM_CUDA(pl, cudaEventCreate(&e0));
+  HSM_CUDA(pl, cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_lt = 0;
+  cudaError_t ce = cudaSuccess;
+  for (int lt = 0; lt < A->L && ce == cudaSuccess; ++lt) {
+    if (lt > 0 && A->lev[lt].n > kMgTailMaxRows) continue;
+    if (lt == 0 && A->L == 1) continue;
+    float ms = 0.f;
+    for (int rep = 0; rep < 2 && ce == cudaSuccess; ++rep) {  // the first pass warms up
+      ce = cudaEventRecord(e0, s);
+      for (int k = 0; k < 10 && ce == cudaSuccess; ++k) ce = vcycle_lt(*A, lt, in, out, done, s);
+      if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
+      if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+      if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+    }
+    if (ce == cudaSuccess) A->tail_ms[lt] = ms;
+    if (ce == cudaSuccess && ms < best) {
+      best = ms;
+      best_lt = lt;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  dev_free(&in, s);
+  dev_free(&out, s);
+  dev_free(&done, s);
+  if (ce != cudaSuccess) return cuda_fail(pl, ce, "multigrid tail timing");
+  A->lt = best_lt;
+  return HSM_OK;
+}
 
 void amg_free(Amg* A, cudaStream_t s) {
   for (int l = 0; l < kMgMaxLevels; ++l) {
@@ -621,7 +832,9 @@ void amg_free(Amg* A, cudaStream_t s) {
     dev_free(&L.own_val, s);
   }
   dev_free(&A->binv, s);
+  dev_free(&A->dlev, s);
   A->L = 0;
+  A->lt = 0;
 }
 
 }  // namespace hsm

@@ -10,6 +10,7 @@ constexpr int kMgMaxLevels = 16;
 constexpr int kMgThreads = 256;
 constexpr int kMgMaxRow = 64;   // distinct columns of one coarse row
 constexpr int kMgCoarsest = 256;  // rows at which coarsening stops
+constexpr int64_t kMgTailMaxRows = 1 << 17;  // largest level the cluster tail may start at
 
 // One level.  Level 0 holds the nodes in the plan's two stencil groups (row =
 // node id, reached through kind/pos); coarse levels hold one group whose row r
@@ -43,6 +44,12 @@ struct Amg {
   int m = 0;
   double omega = 2.0 / 3.0;  // Jacobi damping
   double alpha = 1.8;        // scaling of the coarse-grid correction
+  // levels lt..L-1 of a cycle run in one cluster kernel (k_mg_tail); lt = 0:
+  // every level has its own kernels.  lt is picked at set-up by timing.
+  int lt = 0;
+  int tail_ctas = 0;             // CTAs of the tail's cluster (0: no cluster could be scheduled)
+  float tail_ms[kMgMaxLevels] = {};  // 10 cycles with the tail from level l (l = 0: no tail); -1 not tried
+  MgLevel* dlev = nullptr;       // device copy of lev[0..L)
 };
 
 // Builds the hierarchy of the pressure operator whose rows are the plan's
@@ -51,9 +58,13 @@ struct Amg {
 hsm_status amg_setup(hsm_plan pl, const double* wp_mon, const double* wp_rbf, double alpha, Amg* amg);
 // Enqueues one V(2,2)-cycle on s: out[0..N) = M^-1 in[0..N), out[N] = in[N]
 // (the border unknown of the bordered system is left as it is).  Every kernel
-// returns at once when *done != 0.
+// returns at once when *done != 0; done = nullptr runs the cycle unconditionally
+// (inside a device-side loop that ends on convergence by itself).
 cudaError_t amg_vcycle(const Amg& amg, const double* in, double* out, const double* done, cudaStream_t s);
 int amg_kernels_per_cycle(const Amg& amg);
+// Picks the first level of the cluster tail (or none) by timing a few cycles
+// of each choice on scratch vectors of N + 1 entries.  Synchronises.
+hsm_status amg_tune_tail(hsm_plan pl, Amg* amg);
 void amg_free(Amg* amg, cudaStream_t s);
 
 }  // namespace hsm

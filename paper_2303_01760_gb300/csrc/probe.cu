@@ -13,21 +13,21 @@ namespace {
 
 __device__ double g_fma_sink;
 
-// kChains independent FMA chains per thread, so that the FP64 pipe, not the
+// CH independent FMA chains per thread, so that the FP64 pipe, not the
 // dependency latency, bounds the issue rate.  The values stay bounded
 // (|a| < 1) and are kept alive by a store that never happens at run time.
-constexpr int kChains = 8;
+template <int CH>
 __global__ void __launch_bounds__(256) k_fp64_fma(int iters, double a, double b) {
-  double x[kChains];
+  double x[CH];
 #pragma unroll
-  for (int c = 0; c < kChains; ++c) x[c] = 1e-3 * (threadIdx.x + c);
+  for (int c = 0; c < CH; ++c) x[c] = 1e-3 * (threadIdx.x + c);
   for (int i = 0; i < iters; ++i) {
 #pragma unroll
-    for (int c = 0; c < kChains; ++c) x[c] = fma(x[c], a, b);
+    for (int c = 0; c < CH; ++c) x[c] = fma(x[c], a, b);
   }
   double s = 0.0;
 #pragma unroll
-  for (int c = 0; c < kChains; ++c) s += x[c];
+  for (int c = 0; c < CH; ++c) s += x[c];
   if (s == -1.0) g_fma_sink = s;
 }
 
@@ -59,28 +59,42 @@ extern "C" hsm_status hsm_probe_fp64_peak(double* gflops, float* ms, void* cuda_
     return HSM_EINVAL;
   }
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-  const int threads = 256, blocks = hsm::num_sms() * 8, iters = 4096;
-  const double flops = 2.0 * kChains * (double)iters * threads * blocks;
+  // shapes: (chains per thread, blocks of 256 threads per SM)
+  struct Shape {
+    void (*fn)(int, double, double);
+    int chains, bps;
+  };
+  const Shape shapes[] = {{k_fp64_fma<8>, 8, 8}, {k_fp64_fma<16>, 16, 4}, {k_fp64_fma<4>, 4, 8},
+                          {k_fp64_fma<16>, 16, 8}};
+  const int threads = 256, iters = 4096;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
-  float best = 1e30f;
-  for (int rep = 0; rep < 6 && e == cudaSuccess; ++rep) {
-    e = cudaEventRecord(e0, s);
-    if (e != cudaSuccess) break;
-    k_fp64_fma<<<blocks, threads, 0, s>>>(iters, 0.9999999, 1e-9);
-    if ((e = cudaGetLastError()) != cudaSuccess) break;
-    if ((e = cudaEventRecord(e1, s)) != cudaSuccess) break;
-    if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
-    float t = 0.f;
-    if ((e = cudaEventElapsedTime(&t, e0, e1)) != cudaSuccess) break;
-    if (rep > 0) best = std::min(best, t);  // the first run warms up
+  double best_rate = 0.0;
+  float best_ms = 0.f;
+  for (const Shape& sh : shapes) {
+    const int blocks = hsm::num_sms() * sh.bps;
+    const double flops = 2.0 * sh.chains * (double)iters * threads * blocks;
+    for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+      if ((e = cudaEventRecord(e0, s)) != cudaSuccess) break;
+      sh.fn<<<blocks, threads, 0, s>>>(iters, 0.9999999, 1e-9);
+      if ((e = cudaGetLastError()) != cudaSuccess) break;
+      if ((e = cudaEventRecord(e1, s)) != cudaSuccess) break;
+      if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+      float t = 0.f;
+      if ((e = cudaEventElapsedTime(&t, e0, e1)) != cudaSuccess) break;
+      const double rate = flops / (t * 1e-3) / 1e9;
+      if (rep > 0 && rate > best_rate) {  // the first run of a shape warms up
+        best_rate = rate;
+        best_ms = t;
+      }
+    }
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   if (e != cudaSuccess) return fail_cuda(e, "FP64 FMA probe");
-  *gflops = flops / (best * 1e-3) / 1e9;
-  if (ms) *ms = best;
+  *gflops = best_rate;
+  if (ms) *ms = best_ms;
   return HSM_OK;
 }
 

@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 KRYLOV_TOL = 1e-12
 
 
-def _run_both(ns, Ra, Pr, steps, T0=None, m=2, precond=0, dt=None):
+def _run_both(ns, Ra, Pr, steps, T0=None, m=2, precond=0, dt=None, max_it=20000):
     import torch
     from paper_2303_01760_gb300 import hsm
 
@@ -32,7 +32,7 @@ def _run_both(ns, Ra, Pr, steps, T0=None, m=2, precond=0, dt=None):
     assert code == 0
     dv = plan._dev
     stp = hsm.Stepper(plan, Ra, Pr, dt, ns.T_ref, dv["bc"], dv["T_bc"], dv["normals"],
-                      krylov_tol=KRYLOV_TOL, krylov_max_it=20000, precond=precond)
+                      krylov_tol=KRYLOV_TOL, krylov_max_it=max_it, precond=precond)
     v = torch.from_numpy(v0.copy()).cuda()
     T = torch.from_numpy(Ti.copy()).cuda()
     p = torch.zeros(ns.N, dtype=torch.float64, device="cuda:0")
@@ -56,6 +56,21 @@ def test_hybrid_square_100_steps_matches_oracle():
     g, o = _run_both(ns, 1e4, 0.71, 100)
     eT, ev = _rel(g["T"], o["T"]), _rel(g["v"], o["v"])
     print(f"T rel err {eT:.3e}  v rel err {ev:.3e}  iters/step {np.mean(g['iters']):.1f}")
+    assert eT <= 1e-9
+    assert ev <= 1e-7
+
+
+def test_irregular_222k_ra1e6_100_steps_matches_oracle():
+    """The 2D irregular workload at full size (unit square minus 8 seeded
+    holes, lattice h = 0.002, 222,555 nodes, 12.7 % scattered), Ra = 1e6,
+    Pr = 0.71, dt = 0.1 h^2/2: 100 steps from rest (a stated reduced count of
+    the configuration's 2,000) against the oracle's exact pressure solve.  The
+    GPU solves each pressure system to 1e-12 relative residual, from the
+    extrapolated initial guess and through the cluster-tail multigrid cycle."""
+    ns = nodesets.cached(nodesets.square_holes)
+    g, o = _run_both(ns, 1e6, 0.71, 100, max_it=4000)
+    eT, ev = _rel(g["T"], o["T"]), _rel(g["v"], o["v"])
+    print(f"222k, 100 steps: T rel err {eT:.3e}  v rel err {ev:.3e}  iters/step {np.mean(g['iters']):.1f}")
     assert eT <= 1e-9
     assert ev <= 1e-7
 
