@@ -588,20 +588,25 @@ def run_big_apply(hsm, nodesets, dev, stream, flush, args):
 
 
 def run_3d(hsm, nodesets, dev, stream, flush, args):
-    """The 3D configuration's shape at 213k nodes: unit cube minus 20 seeded
-    spheres, lattice h = 1/60, scattered within 0.05 of a sphere.  For m = 2
-    (n = 20) and m = 3 (n = 40): FP64 and FP32 + FP64-refinement weights
-    (times, fallbacks, the refinement's largest weight difference from the FP64
+    """The 3D configuration at full size: unit cube minus 20 seeded spheres,
+    lattice h = 1/125, scattered within 0.05 of a sphere (about 1.9M nodes;
+    the seeded set takes about 1.5 minutes to generate on the host and is
+    cached).  For m = 2 (n = 20) and m = 3 (n = 40): FP64 and FP32 +
+    FP64-refinement weights (times, fallbacks, nodes that took a lower
+    monomial degree, the refinement's largest weight difference from the FP64
     solve) and the fused application of grad and Laplacian with f64 and f32
-    storage."""
+    storage, against the measured HBM copy bandwidth."""
     import numpy as np
     import torch
 
-    ns = nodesets.cached(nodesets.cube_spheres, n=60)
+    t0 = time.time()
+    ns = nodesets.cached(nodesets.cube_spheres, n=125)
+    gen_s = time.time() - t0
     d = [torch.from_numpy(a).to(dev) for a in (ns.coords, ns.is_regular, ns.is_boundary, ns.normals)]
     u = torch.from_numpy(nodesets.field_random_smooth(ns.coords)[0]).to(dev)
     res = {"workload": f"3D, {ns.N} nodes ({ns.n_scattered / ns.N:.1%} scattered): unit cube minus 20 spheres, "
-                       "lattice h=1/60, band 0.05; ops dx,dy,dz,lap", "nodes": int(ns.N)}
+                       "lattice h=1/125, band 0.05; ops dx,dy,dz,lap", "nodes": int(ns.N),
+           "nodeset_seconds": round(gen_s, 1)}
     peak, _ = hbm_peak()
     for m in (2, 3):
         n = 2 * (10 if m == 2 else 20)
@@ -628,7 +633,8 @@ def run_3d(hsm, nodesets, dev, stream, flush, args):
             rows = np.flatnonzero((rp[1:] - rp[:-1] == n) & ~singular)
             ix = rp[rows][:, None] + np.arange(n)[None, :]
             entry = {"weights_ms": float(np.mean(ts)), "nodes_per_s": ns.N / (np.mean(ts) * 1e-3),
-                     "fallbacks": q["n_fallback"], "singular_nodes": int(singular.sum())}
+                     "fallbacks": q["n_fallback"], "singular_nodes": int(singular.sum()),
+                     "reduced_degree_nodes": int((stat == hsm.HSM_NODE_REDUCED_DEGREE).sum())}
             if ref is None:
                 ref = [v[ix] for v in vals]
             else:
@@ -999,10 +1005,11 @@ def _refined_dev(ns, dev, reg=None):
     return d
 
 
-def _time_steps(hsm, plan, ns, d, dev, n_steps, Ra, dt, cold=None):
+def _time_steps(hsm, plan, ns, d, dev, n_steps, Ra, dt, cold=None, chunks=1):
     """n_steps explicit Boussinesq steps from rest; returns ms/step (CUDA
     events), Krylov iterations per step and, with ``cold``, the final mean
-    |dT/dn| on those nodes."""
+    |dT/dn| on those nodes (and, with chunks > 1, its value after each of
+    ``chunks`` equal parts of the run)."""
     import numpy as np
     import torch
 
@@ -1013,17 +1020,28 @@ def _time_steps(hsm, plan, ns, d, dev, n_steps, Ra, dt, cold=None):
     p = torch.zeros(ns.N, dtype=torch.float64, device=dev)
     st.step(v, T, p, 3, allow_notconv=True)
     torch.cuda.synchronize()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    ev[0].record()
-    its, _ = st.step(v, T, p, n_steps, allow_notconv=True)
-    ev[1].record()
-    torch.cuda.synchronize()
-    out = {"ms_per_step": ev[0].elapsed_time(ev[1]) / n_steps, "krylov_iters_per_step": float(np.mean(its)),
+    cd = torch.from_numpy(cold).to(dev) if cold is not None else None
+    history = []
+    its, gpu_ms, done = [], 0.0, 0
+    for c in range(chunks):
+        k = (n_steps * (c + 1)) // chunks - done
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record()
+        it_c, _ = st.step(v, T, p, k, allow_notconv=True)
+        ev[1].record()
+        torch.cuda.synchronize()
+        gpu_ms += ev[0].elapsed_time(ev[1])
+        its += list(it_c)
+        done += k
+        if cd is not None and chunks > 1:
+            history.append([round((done + 3) * dt, 6), float(plan.wall_flux_mean(T, cd, d["normals"]).item())])
+    out = {"ms_per_step": gpu_ms / n_steps, "krylov_iters_per_step": float(np.mean(its)),
            "max_speed": float(v.abs().max().item()),
            "finite": bool(torch.isfinite(T).all() and torch.isfinite(v).all())}
     if cold is not None:
-        cd = torch.from_numpy(cold).to(dev)
         out["nu_cold"] = float(plan.wall_flux_mean(T, cd, d["normals"]).item())
+        if history:
+            out["nu_cold_history"] = history
     st.close()
     return out
 
@@ -1139,7 +1157,7 @@ def run_spheres3d(args):
         cold = np.flatnonzero((ns.is_boundary == 1) & (ns.bc == nodesets.BC_T_DIRICHLET)
                               & (ns.T_bc == 0.0)).astype(np.int32)
         setup = time.time() - t0
-        r = _time_steps(hsm, plan, ns, d, dev, n_steps, 1e4, dt, cold)
+        r = _time_steps(hsm, plan, ns, d, dev, n_steps, 1e4, dt, cold, chunks=10 if args.t_end else 1)
         plan.close()
         r.update({"N": int(ns.N), "n_mon": int(q["n_mon"]), "n_scattered": int(ns.n_scattered), "dt": dt,
                   "steps": n_steps, "t_reached": n_steps * dt, "setup_s": setup,
@@ -1310,6 +1328,83 @@ def run_field_linf(args):
         "max_abs": {"T": float(np.abs(o["T"]).max()), "v": float(np.abs(o["v"]).max())}}}))
 
 
+def run_precision_sweep(args):
+    """The 8M-node 2D precision sweep (7,339,248 nodes, 30 % scattered: 12 x 12
+    tiled copies of a unit square minus 8 holes, lattice h = 1/250): FP64 vs
+    FP32 + FP64-refinement weights for m = 2 and m = 4 (time, fallbacks and
+    the largest relative weight difference per stencil), and ``S`` explicit
+    Boussinesq steps at Ra = 1e6 from rest with FP64 and with FP32 operator
+    applications (FP64 state, time accumulation and pressure solve): field
+    L-inf of the FP32 run against the FP64 run, each relative to the largest
+    magnitude of the FP64 field.  The FP64 stepper matches the oracle to
+    ~1e-13 after 2,000 steps on the 222k-node set (``--field-linf``); at this
+    size the oracle's sparse LU is out of reach."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2303_01760_gb300 import hsm, nodesets
+
+    dev = torch.device("cuda:0")
+    S = args.precision_sweep
+    base = nodesets.cached(nodesets.square_holes, n=250, band=0.09)
+    ns = nodesets.tiled(base, 12, 12)
+    d = {k: torch.from_numpy(np.ascontiguousarray(getattr(ns, k))).to(dev)
+         for k in ("coords", "is_regular", "is_boundary", "normals", "bc", "T_bc")}
+    out = {"workload": f"2D, {ns.N} nodes ({ns.n_scattered / ns.N:.1%} scattered): 12x12 tiled unit squares minus "
+                       "8 holes, lattice h=1/250", "nodes": int(ns.N), "weights": {}}
+    for m in (2, 4):
+        plan = hsm.Plan(d["coords"], d["is_regular"], d["is_boundary"], ns.h, m=m, normals=d["normals"])
+        plan.set_timing(True)
+        plan.build_stencils()
+        res = {}
+        w = {}
+        for prec, name in ((hsm.HSM_PREC_FP64, "fp64"), (hsm.HSM_PREC_FP32_REFINE, "fp32_refine")):
+            plan.compute_weights(prec)
+            torch.cuda.synchronize()
+            plan.compute_weights(prec)
+            ph = plan.profile()[0]
+            w[name] = [plan.export_csr(b)[2] for b in (1, 2, 8)]
+            res[name] = {"weights_ms": ph[1] + ph[2], "fallbacks": plan.query()["n_fallback"]}
+        rp = plan.export_csr(1)[0]
+        rows = torch.repeat_interleave(torch.arange(ns.N, device=dev), (rp[1:] - rp[:-1]))
+        worst = 0.0
+        for a, b in zip(w["fp64"], w["fp32_refine"]):
+            num = torch.zeros(ns.N, dtype=torch.float64, device=dev).scatter_reduce(0, rows, (a - b).abs(), "amax")
+            den = torch.zeros(ns.N, dtype=torch.float64, device=dev).scatter_reduce(0, rows, a.abs(), "amax")
+            worst = max(worst, float((num / den.clamp_min(1e-300)).max()))
+        res["max_rel_weight_diff_fp32_refine_vs_fp64"] = worst
+        out["weights"][f"m{m}"] = res
+        if m == 2:
+            plan.compute_weights(hsm.HSM_PREC_FP64)
+            dt = 0.1 * ns.h * ns.h / 2.0
+            fields = {}
+            for name, f32 in (("fp64_apply", False), ("fp32_apply", True)):
+                st = hsm.Stepper(plan, 1e6, 0.71, dt, ns.T_ref, d["bc"], d["T_bc"], d["normals"], krylov_tol=1e-10,
+                                 krylov_max_it=4000, apply_f32=f32)
+                v = torch.zeros((2, ns.N), dtype=torch.float64, device=dev)
+                T = torch.where(d["bc"] == 1, d["T_bc"], torch.zeros_like(d["T_bc"])).contiguous()
+                p = torch.zeros(ns.N, dtype=torch.float64, device=dev)
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+                ev[0].record()
+                its, code = st.step(v, T, p, S, allow_notconv=True)
+                ev[1].record()
+                torch.cuda.synchronize()
+                fields[name] = (v, T)
+                out[name] = {"ms_per_step": ev[0].elapsed_time(ev[1]) / S, "krylov_iters_mean": float(np.mean(its)),
+                             "status": int(code)}
+                st.close()
+            (v64, T64), (v32, T32) = fields["fp64_apply"], fields["fp32_apply"]
+            out["steps"] = S
+            out["field_linf_fp32_apply_vs_fp64"] = {
+                "T": float((T32 - T64).abs().max() / T64.abs().max()),
+                "v": float((v32 - v64).abs().max() / v64.abs().max().clamp_min(1e-300))}
+        plan.close()
+    print(json.dumps({"precision_sweep": out}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1340,7 +1435,12 @@ def main():
     ap.add_argument("--field-linf", type=int, default=0,
                     help="GPU stepper vs the oracle after this many steps on the 2D irregular workload")
     ap.add_argument("--krylov-tol", type=float, default=1e-12, help="with --field-linf")
+    ap.add_argument("--precision-sweep", type=int, default=0,
+                    help="the 7.3M-node precision sweep with this many explicit steps")
     args = ap.parse_args()
+    if args.precision_sweep:
+        run_precision_sweep(args)
+        return
     if args.field_linf:
         run_field_linf(args)
         return

@@ -69,6 +69,9 @@ enum {
   HSM_NODE_DEMOTED = 1,      /* regular-flagged node that had to use RBF-FD        */
   HSM_NODE_REFINE_FP64 = 2,  /* FP32 refinement did not converge; FP64 solve used  */
   HSM_NODE_LEARNED_SOLVE = 3,/* learned weights rejected; FP64 solve used          */
+  HSM_NODE_REDUCED_DEGREE = 4,/* the degree-m monomials are not unisolvent on the
+                                stencil: FP64 solve with the largest lower degree
+                                m' >= 1 that is, on the same n nodes             */
   HSM_NODE_SINGULAR = 255    /* no valid weights                                    */
 };
 
@@ -146,7 +149,11 @@ hsm_status hsm_plan_build_stencils(hsm_plan plan);
  * (Section 2.1, Section 4), by the method selected with prec.
  *   node_status  device u8 [N] or NULL; receives one HSM_NODE_* per node
  * A system is singular when a pivot of the scaled FP64 system (entries of
- * order one) falls below 1e-12 in magnitude or is not finite.  Returns
+ * order one) falls below 1e-12 in magnitude or is not finite.  A singular
+ * system is solved again in FP64 with the monomials of degree m-1, m-2, ..., 1
+ * on the same stencil until one is not (status HSM_NODE_REDUCED_DEGREE): a
+ * stencil on which the degree-m monomials are not unisolvent still gets
+ * weights exact for the lower degree.  Returns
  * HSM_ESINGULAR when some node has no valid weights (its weights are then
  * zero and its status HSM_NODE_SINGULAR).  Synchronises the plan's stream (the failure count is read).  */
 hsm_status hsm_plan_compute_weights(hsm_plan plan, hsm_prec prec, uint8_t* node_status);
@@ -248,6 +255,12 @@ typedef struct {
   int guess_order;       /* initial guess of each pressure solve from the call's
                             previous solutions: 0 = quadratic extrapolation
                             (default), 1 = linear, -1 = the last solution      */
+  int apply_f32;         /* 1: the explicit operator applications (grad and lap
+                            of v in the predictor, div v*, grad p, grad T and
+                            lap T) use FP32 copies of the weights and FP32
+                            sums, each sum rounded to FP64 before it enters the
+                            FP64 state and time update; the pressure solve
+                            stays FP64.  0 (default): FP64 throughout          */
 } hsm_phys;
 
 /* Right preconditioner of the pressure BiCGSTAB.  AMG: an aggregation

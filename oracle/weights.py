@@ -139,18 +139,55 @@ def rbffd_system(xi, m, ops):
     return M, rhs
 
 
-def rbffd_weights(coords, stencil, m, ops=None):
-    """RBF-FD weights for stencils [B, n].  Returns {op: w [B, n]}."""
+# A stencil is unisolvent for the monomials of degree <= m when P has full
+# column rank; numerically, when its smallest singular value exceeds this
+# fraction of its largest (P of the scaled offsets has entries of order one).
+UNISOLVENT_RTOL = 1e-10
+
+
+def unisolvent(xi, m):
+    """[B] bool: the monomials of degree <= m are unisolvent on the scaled
+    stencil offsets xi [B, n, dim] (P [B, n, Mp] of full column rank)."""
+    P = eval_monomials(monomial_exponents(xi.shape[-1], m), xi)
+    sv = np.linalg.svd(P, compute_uv=False)
+    return sv[:, -1] > UNISOLVENT_RTOL * sv[:, 0]
+
+
+def rbffd_weights_degree(coords, stencil, m, ops=None):
+    """RBF-FD weights for stencils [B, n] and the monomial degree each used.
+
+    Reading (the paper requires a stencil whose system is solvable at every
+    node, Section 2): a stencil on which the monomials of degree <= m are not
+    unisolvent -- e.g. a 3D wall node next to a box edge whose stencil spans
+    three lattice layers across the edge, where a cubic vanishes on every
+    node -- takes the largest degree m' < m (m' >= 1) that is unisolvent on
+    the same n nodes.  Returns ({op: w [B, n]}, m_used [B])."""
     dim = coords.shape[0]
     ops = ops or ops_for(dim)
     stencil = np.asarray(stencil)
+    n = stencil.shape[1] if stencil.ndim == 2 else 0
     if len(stencil) == 0:
-        return {op: np.zeros((0, stencil.shape[1])) for op in ops}
+        return {op: np.zeros((0, n)) for op in ops}, np.zeros(0, dtype=np.int64)
     xi, s = _scaled_offsets(coords, stencil)
-    M, rhs = rbffd_system(xi, m, ops)
-    sol = np.linalg.solve(M, rhs)
-    n = stencil.shape[1]
-    return _unscale(sol[:, :n, :], s, ops)
+    m_used = np.full(len(stencil), m, dtype=np.int64)
+    todo = ~unisolvent(xi, m)
+    for mm in range(m - 1, 0, -1):
+        if not todo.any():
+            break
+        m_used[todo] = mm
+        sub = np.flatnonzero(todo)
+        todo[sub] = ~unisolvent(xi[sub], mm)
+    sol = np.zeros((len(stencil), n, len(ops)))
+    for mm in np.unique(m_used):
+        sel = np.flatnonzero(m_used == mm)
+        M, rhs = rbffd_system(xi[sel], int(mm), ops)
+        sol[sel] = np.linalg.solve(M, rhs)[:, :n, :]
+    return _unscale(sol, s, ops), m_used
+
+
+def rbffd_weights(coords, stencil, m, ops=None):
+    """RBF-FD weights for stencils [B, n].  Returns {op: w [B, n]}."""
+    return rbffd_weights_degree(coords, stencil, m, ops)[0]
 
 
 def mon_system(xi, ops):
@@ -180,8 +217,8 @@ def all_weights(coords, st, m, ops=None):
     """Weights for the stencils returned by ``stencils.build_stencils``."""
     dim = coords.shape[0]
     ops = ops or ops_for(dim)
-    return dict(mon=mon_weights(coords, st["mon_idx"], ops),
-                rbf=rbffd_weights(coords, st["rbf_idx"], m, ops))
+    w_rbf, m_used = rbffd_weights_degree(coords, st["rbf_idx"], m, ops)
+    return dict(mon=mon_weights(coords, st["mon_idx"], ops), rbf=w_rbf, rbf_m=m_used)
 
 
 def stencil_size(dim, m):

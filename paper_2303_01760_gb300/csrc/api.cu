@@ -149,6 +149,7 @@ static void free_plan_device(hsm_plan p) {
   dev_free(&p->pos, s);
   dev_free(&p->dev_flags, s);
   dev_free(&p->dev_count, s);
+  dev_free(&p->sing_list, s);
   free_build_ws(p);
 }
 
@@ -233,6 +234,14 @@ hsm_status hsm_plan_compute_weights(hsm_plan p, hsm_prec prec, uint8_t* node_sta
   dev_free(&p->mon.w32, s);
   dev_free(&p->rbf.w32, s);
   HSM_CUDA(p, cudaMemsetAsync(p->dev_flags, 0, sizeof(unsigned), s));
+  if (p->m >= 2 && p->sing_cap < p->rbf.count) {
+    dev_free(&p->sing_list, s);
+    p->sing_cap = 0;
+    HSM_CUDA(p, dev_alloc(&p->sing_list, 2 * (size_t)p->rbf.count, s));
+    p->sing_cap = p->rbf.count;
+  }
+  HSM_CUDA(p, cudaMemsetAsync(p->dev_count + 1, 0, sizeof(int), s));
+  p->n_reduced = 0;
   hsm_status st = HSM_OK;
   // the stencil build computed the MON weights; they are computed again here
   // only when the caller asks for per-node status
@@ -281,6 +290,31 @@ hsm_status hsm_plan_compute_weights(hsm_plan p, hsm_prec prec, uint8_t* node_sta
       }
     }
     dev_free(&fail_list, s);
+  }
+  // Systems singular for the degree-m monomials are solved again, on the same
+  // stencil, with the largest lower degree for which they are not (Section 2
+  // needs solvable weights at every node; 3D wall nodes next to a box edge
+  // with m = 3 span too few layers across the edge for the cubics).  Duplicate
+  // nodes stay singular at every degree.
+  if (p->m >= 2 && p->sing_cap >= p->rbf.count && p->rbf.count) {
+    int sc = 0;
+    HSM_CUDA(p, cudaMemcpyAsync(&sc, p->dev_count + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HSM_CUDA(p, cudaStreamSynchronize(s));
+    sc = (int)std::min<int64_t>(sc, p->sing_cap);  // a list holds each system at most once per pass
+    const int first = sc;
+    int32_t* in = p->sing_list;
+    int32_t* out = p->sing_list + p->sing_cap;
+    for (int deg = p->m - 1; deg >= 1 && sc > 0; --deg) {
+      HSM_CUDA(p, cudaMemsetAsync(p->dev_flags, 0, sizeof(unsigned), s));
+      HSM_CUDA(p, cudaMemsetAsync(p->dev_count + 1, 0, sizeof(int), s));
+      st = compute_rbf_weights_fp64_degree(p, in, sc, node_status, deg, out);
+      if (st != HSM_OK) return st;
+      HSM_CUDA(p, cudaMemcpyAsync(&sc, p->dev_count + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+      HSM_CUDA(p, cudaStreamSynchronize(s));
+      sc = (int)std::min<int64_t>(sc, p->sing_cap);
+      std::swap(in, out);
+    }
+    p->n_reduced = first - sc;
   }
   unsigned flags = 0;
   HSM_CUDA(p, cudaMemcpyAsync(&flags, p->dev_flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));

@@ -101,7 +101,10 @@ struct hsm_plan_s {
   uint8_t* kind = nullptr;      // [N] 0 = MON, 1 = RBF-FD
   int32_t* pos = nullptr;       // [N] position inside its group
   unsigned* dev_flags = nullptr;  // device status bits
-  int* dev_count = nullptr;       // device counter scratch
+  int* dev_count = nullptr;       // device counter scratch: [0] fallback list, [1] singular list
+  int32_t* sing_list = nullptr;   // [2][sing_cap]: systems the FP64 solve found singular (two lists)
+  int64_t sing_cap = 0;
+  int64_t n_reduced = 0;          // systems solved with a lower monomial degree in the last weights call
   uint16_t* pairs = nullptr;      // [n(n-1)/2] (i << 8 | j) upper-triangle pairs
   int8_t* mono_exp = nullptr;     // [n_mono][dim] monomial exponents
   std::vector<uint16_t> h_pairs;  // host sources of the two tables (kept for the async upload)
@@ -210,12 +213,19 @@ void free_build_ws(hsm_plan p);
 cudaError_t enqueue_mon_weights(hsm_plan p, const int* count_dev, double* w, cudaStream_t s);
 
 // ---- weights.cu ----------------------------------------------------------
+// Raises the maximum dynamic shared memory of kernel fn to at least smem
+// (never lowers it: shapes cached for larger systems stay launchable).
+cudaError_t raise_smem_limit(void* fn, size_t smem);
 hsm_status compute_mon_weights(hsm_plan p, uint8_t* status);
 hsm_status compute_rbf_weights_fp64_marked(hsm_plan p, const int32_t* list, int64_t count, uint8_t* status,
                                            uint8_t mark);
 hsm_status compute_rbf_weights_fp64(hsm_plan p, const int32_t* list, int64_t count, uint8_t* status);
 hsm_status compute_rbf_weights_fp32r(hsm_plan p, const int32_t* list, int64_t count, uint8_t* status,
                                      int32_t* fail_list, int* fail_count);
+// FP64 solve of the listed systems with the monomials of degree <= degree
+// only; solved systems get status HSM_NODE_REDUCED_DEGREE.
+hsm_status compute_rbf_weights_fp64_degree(hsm_plan p, const int32_t* list, int64_t count, uint8_t* status,
+                                           int degree, int32_t* sing_out);
 hsm_status weights_to_f32(hsm_plan p);
 
 // Weight systems for caller-supplied stencils, described without a plan

@@ -184,7 +184,7 @@ hsm_status launch_condition(hsm_plan p, double* kappa) {
     const size_t smem = per * threads;
     if (smem > 227 * 1024) return set_error(p, HSM_EINVAL, "RBF-FD system too large for the condition diagnostic");
     void* fn = p->dim == 2 ? (void*)k_cond_rbf<2> : (void*)k_cond_rbf<3>;
-    HSM_CUDA(p, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    HSM_CUDA(p, raise_smem_limit(fn, smem));
     const int grid = (int)std::min<int64_t>(ceil_div(p->rbf.count, threads), (int64_t)num_sms() * 4);
     const double* coords = p->coords;
     int64_t N = p->N, G = p->rbf.count;

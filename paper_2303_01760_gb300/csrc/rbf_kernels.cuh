@@ -44,6 +44,9 @@ struct RbfArgs {
   unsigned* flags;
   int32_t* fail_list;      // fp32r: positions that did not converge
   int* fail_count;
+  int32_t* sing_list;      // fp64: positions whose system was singular (nullptr: not recorded)
+  int* sing_count;
+  int64_t sing_cap;        // entries sing_list holds; later ones are counted, not stored
 };
 
 template <typename T>
@@ -785,6 +788,10 @@ __global__ void __launch_bounds__(256) k_rbf_fp64(RbfArgs a) {
     if (lane == 0) {
       const int32_t node = a.nodes[pos];
       if (!ok) atomicOr(a.flags, kDevSingular);
+      if (!ok && a.sing_list) {
+        const int slot = atomicAdd(a.sing_count, 1);
+        if (slot < a.sing_cap) a.sing_list[slot] = (int32_t)pos;
+      }
       if (a.status)
         a.status[node] = !ok ? HSM_NODE_SINGULAR
                              : (a.status_demoted_mark ? a.status_demoted_mark

@@ -836,7 +836,7 @@ hsm_status build_stencils(hsm_plan p) {
     void* fn = nullptr;
     if (p->dim == 2) fn = qt == 4 ? (void*)k_knn<2, 4> : (qt == 2 ? (void*)k_knn<2, 2> : (void*)k_knn<2, 1>);
     else fn = qt == 4 ? (void*)k_knn<3, 4> : (qt == 2 ? (void*)k_knn<3, 2> : (void*)k_knn<3, 1>);
-    if (smem > 48 * 1024) HSM_CUDA(p, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (smem > 48 * 1024) HSM_CUDA(p, raise_smem_limit(fn, smem));
     // the workspace allocations must be complete before the captured work runs
     HSM_CUDA(p, cudaStreamSynchronize(s));
     HSM_CUDA(p, cudaStreamBeginCapture(w.cap, cudaStreamCaptureModeThreadLocal));

@@ -91,6 +91,7 @@ struct StepArgs {
   const int32_t* nodes[2];
   const int32_t* idx[2];
   const double* w[2];      // plan weights [nops][width][count]
+  const float* w32[2];     // their FP32 copies (FP32 operator applications), or nullptr
   const double* wp[2];     // pressure weights of the group ([width][count])
   const double* wn[2];     // wall normal-derivative weights (rbf group only)
   int64_t count[2];
@@ -140,6 +141,19 @@ __device__ __forceinline__ bool node_of(const StepArgs& a, int& g, int64_t& pos,
 
 __device__ __forceinline__ const double* wslot(const StepArgs& a, int g, int slot) {
   return a.w[g] + (int64_t)slot * a.width[g] * a.count[g];
+}
+// Weights of an explicit operator application in the type TW it runs in:
+// FP64, or FP32 with FP32 sums (the fields and the state stay FP64; each sum
+// is rounded to FP64 before it enters the time update).
+template <typename TW>
+__device__ __forceinline__ const TW* wslot_t(const StepArgs& a, int g, int slot);
+template <>
+__device__ __forceinline__ const double* wslot_t<double>(const StepArgs& a, int g, int slot) {
+  return wslot(a, g, slot);
+}
+template <>
+__device__ __forceinline__ const float* wslot_t<float>(const StepArgs& a, int g, int slot) {
+  return a.w32[g] + (int64_t)slot * a.width[g] * a.count[g];
 }
 
 // Block-reduce up to 4 partial sums; the last block to finish sums all
@@ -199,7 +213,7 @@ __device__ bool block_done(const StepArgs& a, int which, double (&vals)[Q], doub
 }
 
 // ---- 1. predictor -----------------------------------------------------------
-template <int DIM>
+template <int DIM, typename TW>
 __global__ void k_predictor(StepArgs a) {
   int g;
   int64_t pos, stride;
@@ -213,24 +227,24 @@ __global__ void k_predictor(StepArgs a) {
       for (int k = 0; k < DIM; ++k) a.vstar[k * a.N + i] = 0.0;
       continue;
     }
-    double grad[DIM][DIM];  // grad[k][j] = d v_k / d x_j
-    double lap[DIM];
+    TW grad[DIM][DIM];  // grad[k][j] = d v_k / d x_j
+    TW lap[DIM];
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
-      lap[k] = 0.0;
+      lap[k] = TW(0);
 #pragma unroll
-      for (int j = 0; j < DIM; ++j) grad[k][j] = 0.0;
+      for (int j = 0; j < DIM; ++j) grad[k][j] = TW(0);
     }
-    const double* wl = wslot(a, g, a.slot_lap);
+    const TW* wl = wslot_t<TW>(a, g, a.slot_lap);
     for (int e = 0; e < W; ++e) {
       const int32_t id = a.idx[g][(int64_t)e * G + pos];
-      const double wle = wl[(int64_t)e * G + pos];
-      double wd[DIM];
+      const TW wle = wl[(int64_t)e * G + pos];
+      TW wd[DIM];
 #pragma unroll
-      for (int j = 0; j < DIM; ++j) wd[j] = wslot(a, g, a.slot_d[j])[(int64_t)e * G + pos];
+      for (int j = 0; j < DIM; ++j) wd[j] = wslot_t<TW>(a, g, a.slot_d[j])[(int64_t)e * G + pos];
 #pragma unroll
       for (int k = 0; k < DIM; ++k) {
-        const double vk = a.v[k * a.N + id];
+        const TW vk = (TW)a.v[k * a.N + id];
         lap[k] = fma(wle, vk, lap[k]);
 #pragma unroll
         for (int j = 0; j < DIM; ++j) grad[k][j] = fma(wd[j], vk, grad[k][j]);
@@ -241,8 +255,8 @@ __global__ void k_predictor(StepArgs a) {
     for (int k = 0; k < DIM; ++k) {
       double adv = 0.0;
 #pragma unroll
-      for (int j = 0; j < DIM; ++j) adv += a.v[j * a.N + i] * grad[k][j];
-      double f = -adv + a.Pr * lap[k];
+      for (int j = 0; j < DIM; ++j) adv += a.v[j * a.N + i] * (double)grad[k][j];
+      double f = -adv + a.Pr * (double)lap[k];
       if (k == DIM - 1) f += a.Ra * a.Pr * (Ti - a.T_ref);
       a.vstar[k * a.N + i] = a.v[k * a.N + i] + a.dt * f;
     }
@@ -279,7 +293,7 @@ __global__ void k_extrapolate(StepArgs a) {
 }
 
 // ---- 2a. rhs = div v*/dt, r = rhs - A x0, rhat = r, p = v = 0 ----------------
-template <int DIM>
+template <int DIM, typename TW>
 __global__ void k_krylov_init(StepArgs a) {
   int g;
   int64_t pos, stride;
@@ -295,17 +309,19 @@ __global__ void k_krylov_init(StepArgs a) {
   for (; pos < G; pos += stride) {
     const int32_t i = a.nodes[g][pos];
     const bool inner = a.bc[i] == 0;
-    double div = 0.0, ax = 0.0;
+    TW div = TW(0);
+    double ax = 0.0;
     const double* wpg = a.wp[g];
     for (int e = 0; e < W; ++e) {
       const int32_t id = a.idx[g][(int64_t)e * G + pos];
       if (inner) {
 #pragma unroll
-        for (int k = 0; k < DIM; ++k) div = fma(wslot(a, g, a.slot_d[k])[(int64_t)e * G + pos], a.vstar[k * a.N + id], div);
+        for (int k = 0; k < DIM; ++k)
+          div = fma(wslot_t<TW>(a, g, a.slot_d[k])[(int64_t)e * G + pos], (TW)a.vstar[k * a.N + id], div);
       }
       ax = fma(wpg[(int64_t)e * G + pos], a.p[id], ax);
     }
-    const double b = inner ? div / a.dt : 0.0;
+    const double b = inner ? (double)div / a.dt : 0.0;
     const double ri = b - (ax + xN);
     rhs[i] = b;
     r[i] = ri;
@@ -665,7 +681,7 @@ __global__ void k_pc_x(StepArgs a) {
 }
 
 // ---- 3. correction and 4. temperature ----------------------------------------
-template <int DIM>
+template <int DIM, typename TW>
 __global__ void k_correct_temperature(StepArgs a) {
   int g;
   int64_t pos, stride;
@@ -681,16 +697,16 @@ __global__ void k_correct_temperature(StepArgs a) {
       a.Tn[i] = b == HSM_BC_T_DIRICHLET ? a.T_bc[i] : a.T[i];
       continue;
     }
-    double gp[DIM], gT[DIM], lT = 0.0;
+    TW gp[DIM], gT[DIM], lT = TW(0);
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) gp[k] = gT[k] = 0.0;
-    const double* wl = wslot(a, g, a.slot_lap);
+    for (int k = 0; k < DIM; ++k) gp[k] = gT[k] = TW(0);
+    const TW* wl = wslot_t<TW>(a, g, a.slot_lap);
     for (int e = 0; e < W; ++e) {
       const int32_t id = a.idx[g][(int64_t)e * G + pos];
-      const double pj = a.p[id], Tj = a.T[id];
+      const TW pj = (TW)a.p[id], Tj = (TW)a.T[id];
 #pragma unroll
       for (int k = 0; k < DIM; ++k) {
-        const double wd = wslot(a, g, a.slot_d[k])[(int64_t)e * G + pos];
+        const TW wd = wslot_t<TW>(a, g, a.slot_d[k])[(int64_t)e * G + pos];
         gp[k] = fma(wd, pj, gp[k]);
         gT[k] = fma(wd, Tj, gT[k]);
       }
@@ -699,11 +715,11 @@ __global__ void k_correct_temperature(StepArgs a) {
     double adv = 0.0;
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
-      const double vk = a.vstar[k * a.N + i] - a.dt * gp[k];
+      const double vk = a.vstar[k * a.N + i] - a.dt * (double)gp[k];
       a.v[k * a.N + i] = vk;
-      adv += vk * gT[k];
+      adv += vk * (double)gT[k];
     }
-    a.Tn[i] = a.T[i] + a.dt * (-adv + lT);
+    a.Tn[i] = a.T[i] + a.dt * (-adv + (double)lT);
   }
 }
 
@@ -770,6 +786,8 @@ StepArgs make_args(hsm_stepper st, double* v, double* T, double* p) {
   a.idx[1] = pl->rbf.idx;
   a.w[0] = pl->mon.w64;
   a.w[1] = pl->rbf.w64;
+  a.w32[0] = pl->mon.w32;
+  a.w32[1] = pl->rbf.w32;
   a.wp[0] = pl->mon.w64 + (int64_t)st->slot_lap * pl->mon.width * pl->mon.count;
   a.wp[1] = st->wp_rbf;
   a.wn[0] = nullptr;
@@ -808,7 +826,13 @@ StepArgs make_args(hsm_stepper st, double* v, double* T, double* p) {
 // Device side of the conditional Krylov loop.  Every pass of the loop body
 // ends with k_loop_cond, which keeps the loop going while the solve has not
 // converged; a pass counter caps the loop at cap passes, so it always ends.
-__global__ void k_loop_begin(unsigned* ctl) { ctl[0] = 0u; }
+// Before the loop: reset the pass counter and open the loop only if the
+// set-up has not already met the tolerance (a good initial guess can), so
+// the body never runs on a converged solve.
+__global__ void k_loop_begin(const KS* ks, unsigned* ctl, cudaGraphConditionalHandle h) {
+  ctl[0] = 0u;
+  cudaGraphSetConditional(h, ks->done == 0.0 ? 1u : 0u);
+}
 
 __global__ void k_loop_cond(const KS* ks, unsigned* ctl, unsigned cap, cudaGraphConditionalHandle h) {
   const unsigned c = ++ctl[0];
@@ -824,6 +848,30 @@ __global__ void k_step_record(const KS* ks, unsigned* ctl, int* iters, int* bad,
     iters[k] = (int)ks->iter;
     bad[k] = (ks->breakdown != 0.0 || ks->rnorm2 > ks->tol2 * ks->bnorm2 * 1.0000001) ? 1 : 0;
   }
+}
+
+// The explicit operator applications in FP64 or, with hsm_phys.apply_f32,
+// FP32 weights and sums.
+template <int DIM>
+void launch_predictor(hsm_stepper st, const StepArgs& a, dim3 grid, dim3 blk, cudaStream_t s) {
+  if (st->phys.apply_f32)
+    k_predictor<DIM, float><<<grid, blk, 0, s>>>(a);
+  else
+    k_predictor<DIM, double><<<grid, blk, 0, s>>>(a);
+}
+template <int DIM>
+void launch_krylov_init(hsm_stepper st, const StepArgs& a, dim3 grid, dim3 blk, cudaStream_t s) {
+  if (st->phys.apply_f32)
+    k_krylov_init<DIM, float><<<grid, blk, 0, s>>>(a);
+  else
+    k_krylov_init<DIM, double><<<grid, blk, 0, s>>>(a);
+}
+template <int DIM>
+void launch_correct_temperature(hsm_stepper st, const StepArgs& a, dim3 grid, dim3 blk, cudaStream_t s) {
+  if (st->phys.apply_f32)
+    k_correct_temperature<DIM, float><<<grid, blk, 0, s>>>(a);
+  else
+    k_correct_temperature<DIM, double><<<grid, blk, 0, s>>>(a);
 }
 
 // Krylov iterations per captured chunk: Jacobi needs thousands of iterations
@@ -891,14 +939,13 @@ cudaError_t capture_step(hsm_stepper st, const StepArgs& a, dim3 grid, dim3 blk,
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return e;
-  k_predictor<DIM><<<grid, blk, 0, cs>>>(a);
+  launch_predictor<DIM>(st, a, grid, blk, cs);
   {
     StepArgs ax = a;
     ax.nsteps = st->ctl + 1;  // k_step_record counts the steps of the call
     k_extrapolate<<<grid, blk, 0, cs>>>(ax);
   }
-  k_krylov_init<DIM><<<grid, blk, 0, cs>>>(a);
-  k_loop_begin<<<1, 1, 0, cs>>>(st->ctl);
+  launch_krylov_init<DIM>(st, a, grid, blk, cs);
   cudaStreamCaptureStatus status;
   cudaGraph_t cg = nullptr;
   const cudaGraphNode_t* deps = nullptr;
@@ -907,7 +954,11 @@ cudaError_t capture_step(hsm_stepper st, const StepArgs& a, dim3 grid, dim3 blk,
   cudaGraphNode_t cnode = nullptr;
   cudaGraphNodeParams np = {};
   e = cudaStreamGetCaptureInfo(cs, &status, nullptr, &cg, &deps, nullptr, &ndeps);
-  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, cg, 1u, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, cg, 0u, 0u);
+  if (e == cudaSuccess) {
+    k_loop_begin<<<1, 1, 0, cs>>>(a.ks, st->ctl, h);
+    e = cudaStreamGetCaptureInfo(cs, &status, nullptr, &cg, &deps, nullptr, &ndeps);
+  }
   if (e == cudaSuccess) {
     np.type = cudaGraphNodeTypeConditional;
     np.conditional.handle = h;
@@ -929,7 +980,7 @@ cudaError_t capture_step(hsm_stepper st, const StepArgs& a, dim3 grid, dim3 blk,
     }
   }
   if (e == cudaSuccess) {
-    k_correct_temperature<DIM><<<grid, blk, 0, cs>>>(a);
+    launch_correct_temperature<DIM>(st, a, grid, blk, cs);
     k_temperature_bc<<<grid, blk, 0, cs>>>(a);
     k_step_record<<<1, 1, 0, cs>>>(a.ks, st->ctl, st->step_iters, st->step_bad, st->step_cap);
   }
@@ -971,7 +1022,7 @@ hsm_status run_steps(hsm_stepper st, int n_steps, double* v, double* T, double* 
   if (!st->g_chunk) HSM_CUDA(pl, capture(cs, &st->g_chunk, [&] { launch_chunk<DIM>(st, a, grid, blk, cs); }));
   if (!st->g_tail)
     HSM_CUDA(pl, capture(cs, &st->g_tail, [&] {
-      k_correct_temperature<DIM><<<grid, blk, 0, cs>>>(a);
+      launch_correct_temperature<DIM>(st, a, grid, blk, cs);
       k_temperature_bc<<<grid, blk, 0, cs>>>(a);
     }));
   // device-side loop: one graph launch per step, one synchronisation per call
@@ -1029,8 +1080,8 @@ hsm_status run_steps(hsm_stepper st, int n_steps, double* v, double* T, double* 
       if (st->g_head) cudaGraphExecDestroy(st->g_head);
       st->g_head = nullptr;
       HSM_CUDA(pl, capture(cs, &st->g_head, [&] {
-        k_predictor<DIM><<<grid, blk, 0, cs>>>(a);
-        k_krylov_init<DIM><<<grid, blk, 0, cs>>>(a);
+        launch_predictor<DIM>(st, a, grid, blk, cs);
+        launch_krylov_init<DIM>(st, a, grid, blk, cs);
         for (int c = 0; c < want; ++c) launch_chunk<DIM>(st, a, grid, blk, cs);
       }));
       st->head_chunks = want;
@@ -1074,8 +1125,16 @@ hsm_status hsm_stepper_create(hsm_stepper* out, hsm_plan pl, const hsm_phys* phy
     return set_error(pl, HSM_EINVAL, "dt, krylov_tol and krylov_max_it must be positive");
   if (phys->guess_order < -1 || phys->guess_order > 1)
     return set_error(pl, HSM_EINVAL, "guess_order must be -1, 0 or 1");
+  if (phys->apply_f32 != 0 && phys->apply_f32 != 1) return set_error(pl, HSM_EINVAL, "apply_f32 must be 0 or 1");
   if (phys->precond != HSM_PRECOND_AMG && phys->precond != HSM_PRECOND_JACOBI)
     return set_error(pl, HSM_EINVAL, "unknown preconditioner");
+  if (phys->apply_f32 && (!pl->mon.w32 || !pl->rbf.w32)) {
+    // FP32 copies of the plan's weights, as hsm_apply(HSM_F32) makes them
+    HSM_CUDA(pl, dev_alloc(&pl->mon.w32, (size_t)pl->nops * pl->mon.width * pl->mon.count, pl->stream));
+    HSM_CUDA(pl, dev_alloc(&pl->rbf.w32, (size_t)pl->nops * pl->rbf.width * pl->rbf.count, pl->stream));
+    const hsm_status ws = weights_to_f32(pl);
+    if (ws != HSM_OK) return ws;
+  }
   hsm_stepper st = new (std::nothrow) hsm_stepper_s();
   if (!st) return set_error(pl, HSM_ENOMEM, "host allocation failed");
   st->plan = pl;

@@ -25,10 +25,31 @@
 #include <cfloat>
 #include <vector>
 
+#include <map>
+#include <mutex>
+
 #include "common.cuh"
 #include "rbf_kernels.cuh"
 
 namespace hsm {
+
+// The maximum dynamic shared memory of a kernel is one attribute per
+// function, while shapes are cached per system size: the attribute is only
+// ever raised, so a cached shape of a larger system stays launchable after a
+// smaller one was computed.
+cudaError_t raise_smem_limit(void* fn, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::pair<int, void*>, size_t> limit;  // per device and kernel
+  int dev = 0;
+  cudaError_t de = cudaGetDevice(&dev);
+  if (de != cudaSuccess) return de;
+  std::lock_guard<std::mutex> g(mu);
+  size_t& cur = limit[{dev, fn}];
+  if (smem <= cur) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) cur = smem;
+  return e;
+}
 
 // Kernels with compile-time system sizes (rbf_fixed.cu); nullptr when the
 // size or lane count has none.
@@ -271,7 +292,7 @@ cudaError_t rbf_shape(bool r32, int dim, int nops, int K, int ld, int n, int lan
       if (threads < lanes) continue;
       const size_t smem = per * (size_t)(threads / lanes);
       if (smem > 220 * 1024) continue;
-      cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaError_t e = raise_smem_limit(fn, smem);
       if (e != cudaSuccess) return e;
       int bps = 0;
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, threads, smem);
@@ -287,8 +308,6 @@ cudaError_t rbf_shape(bool r32, int dim, int nops, int K, int ld, int n, int lan
       }
     }
     if (best_sys > 0) {
-      cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)best.smem);
-      if (e != cudaSuccess) return e;
       cache.push_back({fn, per, best});
       *out = best;
       return cudaSuccess;
@@ -299,9 +318,17 @@ cudaError_t rbf_shape(bool r32, int dim, int nops, int K, int ld, int n, int lan
 }
 
 hsm_status launch_rbf(hsm_plan p, bool r32, const int32_t* list, int64_t count, uint8_t* status,
-                      int32_t* fail_list, int* fail_count, uint8_t mark) {
+                      int32_t* fail_list, int* fail_count, uint8_t mark, int degree = 0,
+                      int32_t* sing_out = nullptr) {
   if (count == 0) return HSM_OK;
-  RbfArgs a;
+  // degree > 0: the monomials of total degree <= degree only (the first
+  // C(degree + d, d) of the graded table)
+  int n_mono = p->n_mono;
+  if (degree > 0) {
+    n_mono = 1;
+    for (int i = 1; i <= p->dim; ++i) n_mono = n_mono * (degree + i) / i;
+  }
+  RbfArgs a{};
   a.coords = p->coords;
   a.N = p->N;
   a.list = list;
@@ -310,13 +337,19 @@ hsm_status launch_rbf(hsm_plan p, bool r32, const int32_t* list, int64_t count, 
   a.G = p->rbf.count;
   a.nodes = p->rbf.nodes;
   a.n = p->n;
-  a.n_mono = p->n_mono;
-  a.K = p->n + p->n_mono;
+  a.n_mono = n_mono;
+  a.K = p->n + n_mono;
   a.ld = (a.K + p->nops) | 1;
   a.mono_exp = p->mono_exp;
   a.pairs = p->pairs;
   a.ops = make_ops(p, p->op_mask);
   a.w = p->rbf.w64;
+  // the FP64 solve records its singular systems (for the lower-degree retry)
+  // once the plan holds a list for every system of the group
+  const bool rec = !r32 && p->sing_list && p->sing_cap >= p->rbf.count;
+  a.sing_list = rec ? (sing_out ? sing_out : p->sing_list) : nullptr;
+  a.sing_count = rec ? p->dev_count + 1 : nullptr;
+  a.sing_cap = rec ? p->rbf.count : 0;
   a.status = status;
   a.status_demoted_mark = mark;
   a.is_regular = p->is_regular;
@@ -340,7 +373,7 @@ cudaError_t launch_rbf_external(const RbfExternal& x, bool r32, const int32_t* l
                                 uint8_t mark, bool* too_big) {
   *too_big = false;
   if (count == 0) return cudaSuccess;
-  RbfArgs a;
+  RbfArgs a{};
   a.coords = x.coords;
   a.N = x.N;
   a.list = list;
@@ -439,6 +472,11 @@ hsm_status compute_rbf_weights_fp64_marked(hsm_plan p, const int32_t* list, int6
 hsm_status compute_rbf_weights_fp32r(hsm_plan p, const int32_t* list, int64_t count, uint8_t* status,
                                      int32_t* fail_list, int* fail_count) {
   return launch_rbf(p, true, list, count, status, fail_list, fail_count, 0);
+}
+
+hsm_status compute_rbf_weights_fp64_degree(hsm_plan p, const int32_t* list, int64_t count, uint8_t* status,
+                                           int degree, int32_t* sing_out) {
+  return launch_rbf(p, false, list, count, status, nullptr, nullptr, HSM_NODE_REDUCED_DEGREE, degree, sing_out);
 }
 
 hsm_status weights_to_f32(hsm_plan p) {

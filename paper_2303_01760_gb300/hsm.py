@@ -18,6 +18,7 @@ HSM_DX, HSM_DY, HSM_DZ, HSM_LAP = 1, 2, 4, 8
 HSM_PREC_FP64, HSM_PREC_FP32_REFINE, HSM_PREC_LEARNED = 0, 1, 2
 HSM_F32, HSM_F64 = 0, 1
 HSM_NODE_OK, HSM_NODE_DEMOTED, HSM_NODE_REFINE_FP64, HSM_NODE_LEARNED_SOLVE, HSM_NODE_SINGULAR = 0, 1, 2, 3, 255
+HSM_NODE_REDUCED_DEGREE = 4
 HSM_BC_INTERIOR, HSM_BC_T_DIRICHLET, HSM_BC_T_NEUMANN = 0, 1, 2
 STATUS = {0: "HSM_OK", 1: "HSM_EINVAL", 2: "HSM_ENOMEM", 3: "HSM_ECUDA", 4: "HSM_ESINGULAR",
           5: "HSM_ENOTCONV", 6: "HSM_ETIMEOUT", 7: "HSM_EBOUNDS", 8: "HSM_ESTATE"}
@@ -35,7 +36,8 @@ _i64 = C.c_int64
 class hsm_phys(C.Structure):
     _fields_ = [("Ra", C.c_double), ("Pr", C.c_double), ("dt", C.c_double), ("T_ref", C.c_double),
                 ("bc", _p), ("T_bc", _p), ("normals", _p), ("krylov_tol", C.c_double),
-                ("krylov_max_it", C.c_int), ("precond", C.c_int), ("guess_order", C.c_int)]
+                ("krylov_max_it", C.c_int), ("precond", C.c_int), ("guess_order", C.c_int),
+                ("apply_f32", C.c_int)]
 
 
 (HSM_OK, HSM_EINVAL, HSM_ENOMEM, HSM_ECUDA, HSM_ESINGULAR, HSM_ENOTCONV, HSM_ETIMEOUT, HSM_EBOUNDS,
@@ -379,12 +381,12 @@ class Stepper:
     """Owns an hsm_stepper on a plan (Section 3 explicit Boussinesq step)."""
 
     def __init__(self, plan, Ra, Pr, dt, T_ref, bc, T_bc, normals, krylov_tol=1e-12, krylov_max_it=2000,
-                 precond=HSM_PRECOND_AMG, guess_order=0):
+                 precond=HSM_PRECOND_AMG, guess_order=0, apply_f32=False):
         self.plan = plan
         self._keep = (bc, T_bc, normals)
         self.phys = hsm_phys(float(Ra), float(Pr), float(dt), float(T_ref), ptr(bc).value, ptr(T_bc).value,
                              ptr(normals).value, float(krylov_tol), int(krylov_max_it), int(precond),
-                             int(guess_order))
+                             int(guess_order), int(bool(apply_f32)))
         h_ = C.c_void_p()
         check(lib.hsm_stepper_create(C.byref(h_), plan.h, C.byref(self.phys)), plan.h)
         self.h = h_

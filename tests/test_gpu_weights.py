@@ -61,11 +61,16 @@ def _check_plan(ns, m, prec=0, centers=None, tol=TOL_FP64, apply_check=True, sin
         assert q["n_mon"] == len(st["mon_nodes"])
         assert q["n_demoted"] == len(st["demoted"])
     status = status.cpu().numpy()
+    # stencils on which the degree-m monomials are not unisolvent take a lower
+    # degree on the same nodes (oracle and GPU alike), status 4
+    reduced = st["rbf_nodes"][W["rbf_m"] < m] if "rbf_m" in W else np.zeros(0, dtype=np.int64)
+    assert np.all(status[reduced] == 4)
+    assert not np.any(status[np.setdiff1d(st["rbf_nodes"], reduced)] == 4)
     if prec == 0:
         assert np.all(status[st["mon_nodes"]] == 0)
-        assert np.all(status[st["demoted"]] == 1)
+        assert np.all(status[np.setdiff1d(st["demoted"], reduced)] == 1)
     else:
-        assert np.all(np.isin(status[st["rbf_nodes"]], (0, 1, 2)))
+        assert np.all(np.isin(status[st["rbf_nodes"]], (0, 1, 2, 4)))
     worst = {}
     for op in ops:
         rp, col, val = gpu_csr(plan, BIT[op])
@@ -119,10 +124,11 @@ def test_cube_spheres_small_m2_m3():
     """3D: unit cube minus 2 spheres, m=2 (n=20) and m=3 (n=40).  With m=3 the
     wall nodes next to a box edge have one-sided stencils that span only three
     lattice layers across the edge, so the cubic monomials are not unisolvent
-    there; those nodes are reported singular and excluded."""
+    there; those nodes take m = 2 on the same 40 nodes (status 4), and every
+    node, those included, matches the oracle's weights."""
     ns = nodesets.cube_spheres(n=14, n_holes=2, r_range=(0.1, 0.15), band=0.12, seed=nodesets.SEED_BASE + 21)
     _check_plan(ns, m=2)
-    _check_plan(ns, m=3, singular_ok=True)
+    _check_plan(ns, m=3)
 
 
 def test_fp32_refinement_within_tolerance():
@@ -134,7 +140,7 @@ def test_fp32_refinement_within_tolerance():
 def test_fp32_refinement_m4_and_3d():
     _check_plan(nodesets.square_wall_band(n=30, seed=nodesets.SEED_BASE + 11), m=4, prec=1, tol=TOL_FP32R)
     ns = nodesets.cube_spheres(n=14, n_holes=2, r_range=(0.1, 0.15), band=0.12, seed=nodesets.SEED_BASE + 21)
-    _check_plan(ns, m=3, prec=1, tol=TOL_FP32R, singular_ok=True)
+    _check_plan(ns, m=3, prec=1, tol=TOL_FP32R)
 
 
 def test_irregular_250k_sampled():
@@ -273,15 +279,14 @@ REFINED_3D = dict(dim=3, n=12, n_holes=1, r_range=(0.15, 0.2), delta_h=3.0, rati
 def test_refined_sets_2d_and_3d():
     """h-refined sets (Sections 4.2 and 4.3: spacing h_r/3 in 2D and h_r/2 in
     3D at the holes), boundary stencils searched one local spacing inside:
-    every stencil and weight against the oracle, in FP64 and FP32 + refinement.
-    On the coarse 3D set one wall node next to a box edge has a one-sided
-    stencil whose system is singular to working precision (kappa ~ 3e18, with
-    either search point); it must be flagged, the rest must match."""
+    every stencil and weight against the oracle, in FP64 and FP32 + refinement
+    (the coarse 3D set included: with the spacing-aware fill every one of its
+    m = 2 systems is regular, the largest condition number about 4.4e3)."""
     ns2 = nodesets.holes_refined(**REFINED_2D)
     _check_plan(ns2, m=2)
     _check_plan(ns2, m=2, prec=1, tol=TOL_FP32R)
     _check_plan(ns2.all_scattered(), m=2)
-    _check_plan(nodesets.holes_refined(**REFINED_3D), m=2, singular_ok=True)
+    _check_plan(nodesets.holes_refined(**REFINED_3D), m=2)
 
 
 def test_setting_the_spacing_rebuilds_the_boundary_stencils():

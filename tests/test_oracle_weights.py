@@ -254,3 +254,53 @@ def test_convergence_on_h_refined_sets():
     slope = {op: np.polyfit(np.log(hs), np.log(errs[op]), 1)[0] for op in errs}
     assert slope["dx"] >= 1.5 and slope["dy"] >= 1.5, slope
     assert slope["lap"] >= 0.8, slope
+
+
+def test_reduced_degree_on_a_stencil_where_quadratics_are_not_unisolvent():
+    """Twelve nodes on the two lines x = 0 and x = 1: the quadratic x (x - 1)
+    vanishes on every node, so the m = 2 monomials are not unisolvent and P is
+    rank-deficient.  The stencil takes m = 1 on the same nodes: its weights are
+    the plain m = 1 solve, they reproduce every linear field exactly, and a
+    generic stencil beside it keeps m = 2."""
+    rng = np.random.default_rng(5)
+    ys = np.sort(rng.uniform(-1.0, 1.0, 12))
+    line = np.stack([np.r_[0.0, np.tile([0.0, 1.0], 6)[1:12]], np.r_[0.0, ys[1:]]])   # centre at the origin
+    generic = rng.uniform(-1.0, 1.0, (2, 12)) + np.array([[3.0], [3.0]])
+    generic[:, 0] = [3.0, 3.0]
+    coords = np.concatenate([line, generic], 1)
+    sten = np.array([np.arange(12), 12 + np.arange(12)])
+    xi, _ = ow._scaled_offsets(coords, sten)
+    assert list(ow.unisolvent(xi, 2)) == [False, True]
+    W, m_used = ow.rbffd_weights_degree(coords, sten, 2)
+    assert list(m_used) == [2 - 1, 2]
+    W1 = ow.rbffd_weights(coords, sten[:1], 1)
+    W2 = ow.rbffd_weights(coords, sten[1:], 2)
+    for op in ("dx", "dy", "lap"):
+        assert np.allclose(W[op][0], W1[op][0], rtol=0, atol=1e-12 * np.abs(W1[op][0]).max())
+        assert np.allclose(W[op][1], W2[op][0], rtol=0, atol=1e-12 * np.abs(W2[op][0]).max())
+    x, y = coords[:, sten[0]]
+    for f, fx, fy in ((np.ones(12), 0.0, 0.0), (x, 1.0, 0.0), (y, 0.0, 1.0), (2 * x - 3 * y, 2.0, -3.0)):
+        assert abs(W["dx"][0] @ f - fx) <= 1e-11 and abs(W["dy"][0] @ f - fy) <= 1e-11
+        assert abs(W["lap"][0] @ f) <= 1e-10
+
+
+def test_reduced_degree_agrees_with_the_singular_m3_systems_in_3d():
+    """3D, m = 3 (n = 40): the stencils the oracle reduces to m = 2 are exactly
+    those whose full m = 3 augmented system is singular to working precision
+    (condition number above 1e14); every other stencil keeps m = 3 with a
+    condition number far below that."""
+    ns = nodesets.cube_spheres(n=14, n_holes=2, r_range=(0.1, 0.15), band=0.12, seed=nodesets.SEED_BASE + 21)
+    st = ost.build_stencils(ns.coords, ns.is_regular, ns.is_boundary, ns.h, 40, normals=ns.normals)
+    W = ow.all_weights(ns.coords, st, 3)
+    xi, _ = ow._scaled_offsets(ns.coords, st["rbf_idx"])
+    M, _ = ow.rbffd_system(xi, 3, ow.ops_for(3))
+    cond = np.linalg.cond(M)
+    reduced = W["rbf_m"] < 3
+    assert reduced.any() and (~reduced).any()
+    assert np.all(cond[reduced] > 1e14)
+    assert np.all(cond[~reduced] < 1e10)
+    assert np.all(W["rbf_m"][reduced] == 2)
+    # the reduced stencils reproduce quadratics exactly
+    x = ns.coords[:, st["rbf_idx"][reduced]]
+    q = x[0] ** 2 + x[1] * x[2] - 2 * x[2] ** 2
+    assert np.allclose((W["rbf"]["lap"][reduced] * q).sum(1), 2.0 - 4.0, atol=1e-7)
