@@ -200,6 +200,65 @@ def cpu_sample_run(n_sample, gpu_npz=None, seed=CPU_SAMPLE_SEED):
     return t, n_sample, parity
 
 
+def _oracle_share(args):
+    """One worker's share of the all-cores oracle run: stencils, weights and
+    one application for the nodes ``centers`` (single-threaded)."""
+    centers, = args
+    import numpy as np
+
+    from oracle import apply as oap
+    from oracle import stencils as ost
+    from oracle import weights as ow
+    from paper_2303_01760_gb300 import nodesets
+
+    ns = nodesets.cached(nodesets.square_holes)
+    u, _ = nodesets.field_sincos(ns.coords)
+    st = ost.build_stencils(ns.coords, ns.is_regular, ns.is_boundary, ns.h, 12, centers=np.asarray(centers),
+                            use_kdtree=True, normals=ns.normals)
+    W = ow.all_weights(ns.coords, st, 2)
+    for op in ("dx", "dy", "lap"):
+        oap.apply_group(st["mon_idx"], W["mon"][op], u)
+        oap.apply_group(st["rbf_idx"], W["rbf"][op], u)
+    return len(centers)
+
+
+def cpu_baseline_all_cores():
+    """The same oracle work over the whole workload, split into equal shares
+    across every host core by a process pool (started with spawn, each worker
+    single-threaded); the pool's start-up and the node set's load are outside
+    the timed region.  Returns the cpu_baseline-style record."""
+    import multiprocessing as mp
+
+    import numpy as np
+
+    from paper_2303_01760_gb300 import nodesets
+
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    N = nodesets.cached(nodesets.square_holes).N
+    shares = [(c.tolist(),) for c in np.array_split(np.arange(N), cores)]
+    env_keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    old = {k: os.environ.get(k) for k in env_keys}
+    for k in env_keys:
+        os.environ[k] = "1"
+    try:
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(cores) as pool:
+            pool.map(_oracle_share, [(list(range(8)),)] * cores)  # start-up and imports
+            t0 = time.perf_counter()
+            done = sum(pool.map(_oracle_share, shares, chunksize=1))
+            t = time.perf_counter() - t0
+    finally:
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return {"value": done / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"all {done} nodes of the workload in {len(shares)} equal shares over a {cores}-process pool "
+                      f"(spawn, one thread each): stencils by k-d tree, weights, one application; {t:.2f} s",
+            "seconds": t}
+
+
 def cpu_baseline(n_sample=0, gpu_npz=None):
     """Runs the oracle sample in a fresh single-threaded process (and, after
     its timing, the parity check of the GPU's outputs for the same nodes).
@@ -243,10 +302,12 @@ def save_gpu_sample(ns, plan, u, n_sample, path):
 # ---------------------------------------------------------------------------
 # GPU arm
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
-# k_rbf_fp64<2, 3, 8> on the hybrid workload, from an ncu capture of the
-# kernel as it stands.  Set to None whenever that kernel changes until it is
+# k_weights_grouped<2, 3, 8> on the hybrid workload, from an ncu capture of
+# the kernel as it stands.  None whenever that kernel changes until it is
 # re-captured.
 RBF64_TRAFFIC_BYTES = 2465280 + 0
+# the same for k_weights_grouped<2, 3, 8> (both groups in one launch)
+GROUPED_TRAFFIC_BYTES = 9752832 + 18688
 
 
 def aggregate_ranks(times, n_nodes, dist, device):
@@ -350,6 +411,7 @@ def run_gpu(args):
         ms_a, ph_a, launches_a = timed(allr, args.steps, args.warmup)
     clocks = clk.summary()
     q_h, q_a = hyb.query(), allr.query()
+    tune_h, tune_a = hyb.tuning(), allr.tuning()
     t_h = float(np.mean(ms_h))
     t_a = float(np.mean(ms_a))
     n_total = float(ns.N)
@@ -396,9 +458,14 @@ def run_gpu(args):
             "config": workload_desc(ns),
             "e2e": e2e,
             "gpu_launches": int(launches_h // max(args.steps, 1)) * args.steps,
-            "roofline": {"bound": "alu", "kernel": "k_rbf_fp64 (RBF-FD FP64 null-space solve, hybrid set)",
+            "roofline": {"bound": "alu",
+                         "kernel": ("k_weights_grouped (FP64 weights of both groups in one persistent launch; the "
+                                    "RBF-FD null-space solves bound it; algorithmic flops of the RBF-FD systems only)"
+                                    if tune_h["grouped"] else
+                                    "k_rbf_fp64 (RBF-FD FP64 null-space solve, hybrid set; the MON weights run "
+                                    "beside the kNN search in the stencil build)"),
                          "achieved": ach_h, "peak": peak, "unit": "GFLOP/s", "frac": ach_h / peak,
-                         "traffic": RBF64_TRAFFIC_BYTES,
+                         "traffic": GROUPED_TRAFFIC_BYTES if tune_h["grouped"] else RBF64_TRAFFIC_BYTES,
                          "peak_source": "measured: FP64 FMA-chain probe (hsm_probe_fp64_peak) in this run, "
                                         f"{peak_ms:.3f} ms, SM clock median {peak_clocks.get('sm_mhz')} MHz",
                          "peak_clocks": peak_clocks,
@@ -418,9 +485,9 @@ def run_gpu(args):
                 "S1_hybrid_over_all_rbffd": combined(ph_h, 1)[0] / combined(ph_a, 1)[0],
                 "T_w_ms": {"hybrid": combined(ph_h, 1)[1], "all_rbffd": combined(ph_a, 1)[1]},
                 "T_a_ms": {"hybrid": combined(ph_h, 1)[2], "all_rbffd": combined(ph_a, 1)[2]}},
-            "phases_ms": {"hybrid": dict(zip(["stencils", "mon_weights", "rbf_weights", "apply"],
+            "phases_ms": {"hybrid": dict(zip(["stencils", "mon_weights", "weights", "apply"],
                                              np.mean(ph_h, 0).round(4).tolist())),
-                          "all_rbffd": dict(zip(["stencils", "mon_weights", "rbf_weights", "apply"],
+                          "all_rbffd": dict(zip(["stencils", "mon_weights", "weights", "apply"],
                                                 np.mean(ph_a, 0).round(4).tolist()))},
             "counts": {"mon": q_h["n_mon"], "rbf": n_rbf_h, "demoted": q_h["n_demoted"]},
             "parity": None,
@@ -428,8 +495,8 @@ def run_gpu(args):
             "three_d": three_d,
             "learned": learned,
             "clocks": clocks,
-            "tuning": {"note": "lanes per RBF-FD system and apply block size picked by hsm_plan_autotune "
-                               "before the timed region"},
+            "tuning": {"note": "kernel variants picked by hsm_plan_autotune before the timed region",
+                       "hybrid": tune_h, "all_rbffd": tune_a},
         }
     stepper = run_stepper(hsm, ns, hyb, d, dev, stream, args) if (rank == 0 and not args.no_extras) else None
     cond = run_condition(hsm, ns, hyb, dev) if (rank == 0 and not args.no_extras) else None
@@ -441,6 +508,10 @@ def run_gpu(args):
     if rank == 0:
         if world == 1:
             res["cpu_baseline"], res["parity"] = cpu_baseline(args.cpu_sample, gpu_npz)
+            try:
+                res["cpu_baseline_all_cores"] = cpu_baseline_all_cores()
+            except Exception as exc:  # reported, never fatal to the GPU line
+                res["cpu_baseline_all_cores"] = {"error": repr(exc)[:300]}
         else:
             res["cpu_baseline"] = None
         print(json.dumps(res))
@@ -853,7 +924,12 @@ def run_kernels(args):
     from paper_2303_01760_gb300 import hsm, nodesets
 
     dev = torch.device("cuda:0")
-    ns = nodesets.cached(nodesets.square_holes)
+    if args.big_apply:
+        # the 7.3M-node tiled set: FP64 weights, then f64 applies of dx, dy, lap
+        base = nodesets.cached(nodesets.square_holes, n=250, band=0.09)
+        ns = nodesets.tiled(base, 12, 12)
+    else:
+        ns = nodesets.cached(nodesets.square_holes)
     c = torch.from_numpy(ns.coords).to(dev)
     reg = torch.from_numpy(ns.is_regular).to(dev)
     if args.all_rbffd:
@@ -915,6 +991,16 @@ def run_kernels(args):
         st.close()
         plan.close()
         return
+    if args.big_apply:
+        plan.build_stencils()
+        plan.compute_weights(prec)
+        out = torch.empty((3, ns.N), dtype=torch.float64, device=dev)
+        for _ in range(args.warmup + args.steps):
+            plan.apply(u, out=out)
+        torch.cuda.synchronize()
+        plan.close()
+        print("big apply ok", ns.N)
+        return
     for _ in range(args.warmup + args.steps):
         plan.build_stencils()
         plan.compute_weights(prec)
@@ -974,13 +1060,20 @@ def run_dvd(args):
     wall = time.time() - t_run
     vmax = float(v.abs().max().item())
     ref = PAPER_NU_DVD[args.layout]
+    # vertical velocity across the section y = 0.5 (the nodes within h/2 of it,
+    # by x), the comparison the paper draws between the three layouts
+    sec = np.flatnonzero(np.abs(ns.coords[1] - 0.5) <= 0.5 * ns.h)
+    sec = sec[np.argsort(ns.coords[0][sec], kind="stable")]
+    vy = v[1].cpu().numpy()
+    profile = [[round(float(ns.coords[0][i]), 6), round(float(ns.coords[1][i]), 6), float(vy[i])] for i in sec]
     out = {"dvd": {"layout": args.layout, "n": args.dvd, "h": ns.h, "N": int(ns.N), "n_mon": int(q["n_mon"]),
                    "n_scattered": int(ns.n_scattered), "Ra": 1e6, "Pr": 0.71, "dt": dt, "t_end": args.t_end,
                    "steps": n_steps, "krylov_iters_per_step": iters / n_steps, "krylov_iters_max": worst},
            "nu_final": series[-1][1], "nu_paper": ref, "nu_rel_diff": series[-1][1] / ref - 1.0,
            "nu_last_tenth_spread": float(np.ptp([x[1] for x in series[-max(2, len(series) // 10):]])),
            "max_speed": vmax, "finite": bool(torch.isfinite(T).all() and torch.isfinite(v).all()),
-           "run_s": wall, "ms_per_step": 1e3 * wall / n_steps, "setup_s": t_run - t0, "nu_series": series}
+           "run_s": wall, "ms_per_step": 1e3 * wall / n_steps, "setup_s": t_run - t0, "nu_series": series,
+           "vy_profile_y05": profile}
     st.close()
     plan.close()
     print(json.dumps(out))
@@ -1329,16 +1422,20 @@ def run_field_linf(args):
 
 
 def run_precision_sweep(args):
-    """The 8M-node 2D precision sweep (7,339,248 nodes, 30 % scattered: 12 x 12
-    tiled copies of a unit square minus 8 holes, lattice h = 1/250): FP64 vs
-    FP32 + FP64-refinement weights for m = 2 and m = 4 (time, fallbacks and
-    the largest relative weight difference per stencil), and ``S`` explicit
+    """The 8M-node 2D precision sweep on one connected domain: the unit square
+    minus the 8 seeded holes of the 222k-node workload, lattice h = 1/2800,
+    scattered band 0.094 (about 31 % scattered; the seeded set takes several
+    minutes to generate on the host and is cached).  FP64 vs FP32 +
+    FP64-refinement weights for m = 2 and m = 4 (time, fallbacks and the
+    largest relative weight difference per stencil), and ``S`` explicit
     Boussinesq steps at Ra = 1e6 from rest with FP64 and with FP32 operator
     applications (FP64 state, time accumulation and pressure solve): field
     L-inf of the FP32 run against the FP64 run, each relative to the largest
     magnitude of the FP64 field.  The FP64 stepper matches the oracle to
     ~1e-13 after 2,000 steps on the 222k-node set (``--field-linf``); at this
-    size the oracle's sparse LU is out of reach."""
+    size the oracle's sparse LU is out of reach.  (The tiled 7.3M-node set of
+    the apply roofline is 144 disconnected squares, whose Neumann pressure
+    problem has one null vector per square: not a stepper workload.)"""
     import numpy as np
     import torch
 
@@ -1349,12 +1446,14 @@ def run_precision_sweep(args):
 
     dev = torch.device("cuda:0")
     S = args.precision_sweep
-    base = nodesets.cached(nodesets.square_holes, n=250, band=0.09)
-    ns = nodesets.tiled(base, 12, 12)
+    t0 = time.time()
+    ns = nodesets.cached(nodesets.square_holes, n=2800, band=0.094)
+    gen_s = time.time() - t0
     d = {k: torch.from_numpy(np.ascontiguousarray(getattr(ns, k))).to(dev)
          for k in ("coords", "is_regular", "is_boundary", "normals", "bc", "T_bc")}
-    out = {"workload": f"2D, {ns.N} nodes ({ns.n_scattered / ns.N:.1%} scattered): 12x12 tiled unit squares minus "
-                       "8 holes, lattice h=1/250", "nodes": int(ns.N), "weights": {}}
+    out = {"workload": f"2D, {ns.N} nodes ({ns.n_scattered / ns.N:.1%} scattered): unit square minus 8 holes, "
+                       "lattice h=1/2800, band 0.094", "nodes": int(ns.N), "nodeset_seconds": round(gen_s, 1),
+           "weights": {}}
     for m in (2, 4):
         plan = hsm.Plan(d["coords"], d["is_regular"], d["is_boundary"], ns.h, m=m, normals=d["normals"])
         plan.set_timing(True)
@@ -1420,6 +1519,7 @@ def main():
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32r"], help="with --kernels")
     ap.add_argument("--stepper", action="store_true", help="with --kernels: run --steps Boussinesq steps instead")
     ap.add_argument("--learned", action="store_true", help="with --kernels: learned weights instead")
+    ap.add_argument("--big-apply", action="store_true", help="with --kernels: f64 applies on the 7.3M-node set")
     ap.add_argument("--train-steps", type=int, default=3000, help="with --kernels --learned")
     ap.add_argument("--dvd", type=int, default=0, help="de Vahl Davis validation run on a 1/n lattice (no benchmark)")
     ap.add_argument("--layout", default="hybrid", choices=["hybrid", "scattered", "regular"], help="with --dvd")

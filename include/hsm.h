@@ -146,7 +146,12 @@ hsm_status hsm_plan_build_stencils(hsm_plan plan);
 /* Computes the weights of all nodes for the plan's operators (Eq. 1):
  * MON weights solve P^T w = L p over {1, x_k, x_k^2}; RBF-FD weights solve the
  * augmented system [A P; P^T 0][w; lambda] = [L phi; L p] with phi = r^3
- * (Section 2.1, Section 4), by the method selected with prec.
+ * (Section 2.1, Section 4), by the method selected with prec.  With
+ * HSM_PREC_FP64 the systems of both groups -- MON (2d+1 unknowns) and RBF-FD
+ * (n + C(m+d,m)) -- are solved either in one persistent launch whose blocks
+ * draw batches of either kind from one work queue, or as MON weights beside
+ * the kNN search in the stencil build plus one RBF-FD launch, whichever
+ * hsm_plan_autotune measured faster for the plan (the latter until tuned).
  *   node_status  device u8 [N] or NULL; receives one HSM_NODE_* per node
  * A system is singular when a pivot of the scaled FP64 system (entries of
  * order one) falls below 1e-12 in magnitude or is not finite.  A singular
@@ -208,11 +213,21 @@ hsm_status hsm_wall_flux_mean(hsm_plan plan, const double* T, const int32_t* nod
 hsm_status hsm_apply(hsm_plan plan, unsigned op_mask, hsm_dtype in_dtype, const void* u,
                      double* out);
 
-/* Times the kernel variants of this plan (stencil-apply thread layouts and
- * weight-solve lane counts) on its own data and keeps the fastest per group.
+/* Times the kernel variants of this plan (threads per kNN query, lanes per
+ * RBF-FD weight system in FP64 and FP32, the grouped or split arrangement of
+ * the FP64 weights, the apply block size) on its own data and keeps the
+ * fastest of each.
  * cache_path: NULL = no cache; otherwise a text file read before and updated
  * after tuning, keyed by device name and problem shape.  Synchronises.      */
 hsm_status hsm_plan_autotune(hsm_plan plan, const char* cache_path);
+
+/* The plan's kernel variants (host outputs, any may be NULL): threads per kNN
+ * query, lanes per RBF-FD system in FP64 and in FP32 + refinement, threads per
+ * block of the apply, and 1 when the FP64 weights of both groups run in one
+ * grouped launch (0: MON weights beside the kNN search, then one RBF-FD
+ * launch).  tuned is 1 after hsm_plan_autotune.                             */
+hsm_status hsm_plan_tuning(hsm_plan plan, int* knn_qt, int* rbf_lanes, int* rbf_lanes32, int* apply_threads,
+                           int* grouped, int* tuned);
 
 /* Phases timed by hsm_plan_profile. */
 enum { HSM_PHASE_STENCILS = 0, HSM_PHASE_MON = 1, HSM_PHASE_RBF = 2, HSM_PHASE_APPLY = 3,
@@ -261,6 +276,14 @@ typedef struct {
                             sums, each sum rounded to FP64 before it enters the
                             FP64 state and time update; the pressure solve
                             stays FP64.  0 (default): FP64 throughout          */
+  int mg_tail_from;      /* multigrid cycle shape (the preconditioner is the same
+                            operator either way): 0 = picked by timing at
+                            creation (default); k >= 1: levels k.. run in the
+                            thread-block-cluster kernel; -1: no such kernel    */
+  int mg_fused_from;     /* 0 = picked by timing (default); k >= 1: levels k-1..
+                            below the tail run their smoothing and restriction,
+                            and their post-smoothing, as one kernel each;
+                            -1: none                                           */
 } hsm_phys;
 
 /* Right preconditioner of the pressure BiCGSTAB.  AMG: an aggregation
@@ -302,15 +325,19 @@ hsm_status hsm_step(hsm_stepper st, int n_steps, double* v, double* T, double* p
 /* Shape of the stepper's pressure solve (host outputs, any may be NULL):
  *   mg_levels        multigrid levels (0 with the Jacobi preconditioner)
  *   mg_tail_level    first level whose cycle work runs in the one
- *                    thread-block-cluster kernel (0: none; picked by timing
- *                    at hsm_stepper_create)
+ *                    thread-block-cluster kernel (0: none)
  *   mg_tail_ctas     CTAs per cluster the device schedules (0: none)
+ *   mg_fused_level   first level (below the tail) whose smoothing and
+ *                    restriction, and whose two post-smoothing sweeps, run as
+ *                    one kernel each (>= mg_levels: none)
  *   kernels_per_iter kernels one Krylov iteration launches
- *   tail_ms          host f32 [16] or NULL: device time of 10 cycles with
- *                    the tail from level l (entry 0: no tail), -1 where the
- *                    choice was not timed                                   */
+ *   tail_ms, fused_ms host f32 [16] or NULL: device time of 10 cycles with
+ *                    the tail from level l (tail_ms[0]: neither form), or
+ *                    with the fused kernels from level l and no tail; -1
+ *                    where the choice was not timed
+ * Both levels are picked by timing these cycles at hsm_stepper_create.      */
 hsm_status hsm_stepper_info(hsm_stepper st, int* mg_levels, int* mg_tail_level, int* mg_tail_ctas,
-                            int* kernels_per_iter, float* tail_ms);
+                            int* mg_fused_level, int* kernels_per_iter, float* tail_ms, float* fused_ms);
 
 hsm_status hsm_stepper_destroy(hsm_stepper st);
 

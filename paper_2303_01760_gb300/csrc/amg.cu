@@ -162,6 +162,106 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_coarse(const double* __restri
   if (border >= 0 && blockIdx.x == 0 && threadIdx.x == 0) x[border] = f[border];
 }
 
+// ---- fused forms: two phases of a level in one kernel -------------------------
+// On the small levels a kernel is one chain of dependent L2 loads and costs a
+// launch; the fused forms recompute the first phase's values at a row's
+// stencil neighbours instead of waiting for another kernel (the matrix rows
+// are read twice, the launches halve).  Same formulas, same term order.
+__device__ __forceinline__ double pre_x(const MgLevel& L, const double* __restrict__ f, int64_t j) {
+  int g;
+  int64_t p;
+  mg_locate(L, j, g, p);
+  const int W = L.width[g];
+  const int64_t G = L.count[g];
+  double acc = 0.0;
+  for (int e = 0; e < W; ++e) {
+    const int32_t k = L.idx[g][(int64_t)e * G + p];
+    acc = fma(L.val[g][(int64_t)e * G + p], L.odinv[k] * f[k], acc);
+  }
+  const double fj = f[j], dj = L.odinv[j];
+  return dj * fj + dj * (fj - acc);
+}
+
+// k_mg_pre + k_mg_restrict: x of the aggregate's rows (stored for the way
+// up) and fc[I] = sum over the rows r of I of (f - A x)_r.
+__global__ void __launch_bounds__(kMgThreads) k_mg_down(MgLevel L, const double* __restrict__ f,
+                                                        double* __restrict__ fc, int64_t nc, const double* done) {
+  if (done && *done != 0.0) return;
+  for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < nc; I += (int64_t)gridDim.x * blockDim.x) {
+    double sum = 0.0;
+    const int32_t m1 = L.mstart[I + 1];
+    for (int32_t m0 = L.mstart[I]; m0 < m1; ++m0) {
+      const int32_t r = L.mlist[m0];
+      int g;
+      int64_t p;
+      mg_locate(L, r, g, p);
+      const int W = L.width[g];
+      const int64_t G = L.count[g];
+      double acc = 0.0;
+      bool own = false;
+      for (int e = 0; e < W; ++e) {
+        const int32_t j = L.idx[g][(int64_t)e * G + p];
+        const double xj = pre_x(L, f, j);
+        if (j == r) {  // the row's own entry (always present on level 0)
+          L.x[r] = xj;
+          own = true;
+        }
+        acc = fma(L.val[g][(int64_t)e * G + p], xj, acc);
+      }
+      if (!own) L.x[r] = pre_x(L, f, r);
+      sum += f[r] - acc;
+    }
+    fc[I] = sum;
+  }
+}
+
+__device__ __forceinline__ double post1_y(const MgLevel& L, const double* __restrict__ f,
+                                          const double* __restrict__ xc, double alpha, int64_t j) {
+  int g;
+  int64_t p;
+  mg_locate(L, j, g, p);
+  const int W = L.width[g];
+  const int64_t G = L.count[g];
+  double acc = 0.0;
+  for (int e = 0; e < W; ++e) {
+    const int32_t k = L.idx[g][(int64_t)e * G + p];
+    acc = fma(L.val[g][(int64_t)e * G + p], fma(alpha, xc[L.agg[k]], L.x[k]), acc);
+  }
+  const double xj = fma(alpha, xc[L.agg[j]], L.x[j]);
+  return fma(L.odinv[j], f[j] - acc, xj);
+}
+
+// k_mg_post1 + k_mg_post2: out = y + w (f - A y), y = x' + w (f - A x'),
+// x' = x + alpha P xc, y recomputed at every stencil neighbour.  out must not
+// alias L.x (level >= 1 writes L.y); on level 0 the border entry passes.
+__global__ void __launch_bounds__(kMgThreads) k_mg_up(MgLevel L, const double* __restrict__ f,
+                                                      const double* __restrict__ xc, double alpha,
+                                                      double* __restrict__ out, int border, const double* done) {
+  if (done && *done != 0.0) return;
+  int g;
+  int64_t p, stride;
+  mg_rows(L, g, p, stride);
+  const int W = L.width[g];
+  const int64_t G = L.count[g];
+  for (; p < G; p += stride) {
+    const int64_t i = mg_row_id(L, g, p);
+    double acc = 0.0, yi = 0.0;
+    bool own = false;
+    for (int e = 0; e < W; ++e) {
+      const int32_t j = L.idx[g][(int64_t)e * G + p];
+      const double yj = post1_y(L, f, xc, alpha, j);
+      if (j == i) {
+        yi = yj;
+        own = true;
+      }
+      acc = fma(L.val[g][(int64_t)e * G + p], yj, acc);
+    }
+    if (!own) yi = post1_y(L, f, xc, alpha, i);
+    out[i] = fma(L.odinv[i], f[i] - acc, yi);
+  }
+  if (border && blockIdx.x == 0 && threadIdx.x == 0) out[L.n] = f[L.n];
+}
+
 // ---- the coarse levels in one thread-block cluster -------------------------
 // Levels lt..L-1 of a cycle (their smoothing, restriction, the dense coarsest
 // solve and the way back up) run in one launch of one cluster of CTAs, the
@@ -701,7 +801,10 @@ static cudaError_t launch_tail(const Amg& A, int lt, const double* done, cudaStr
                             done);
 }
 
-static cudaError_t vcycle_lt(const Amg& A, int lt, const double* in, double* out, const double* done,
+// One V-cycle: levels below lt (all, when lt = 0) with their own kernels --
+// the fused down/up forms from level lf on -- and levels lt..L-1 in the
+// cluster tail.
+static cudaError_t vcycle_lt(const Amg& A, int lt, int lf, const double* in, double* out, const double* done,
                              cudaStream_t s) {
   const int cg = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div((int64_t)A.m, kMgThreads / 32), 1024));
   if (A.L == 1) {
@@ -712,8 +815,12 @@ static cudaError_t vcycle_lt(const Amg& A, int lt, const double* in, double* out
   const double* f = in;
   for (int l = 0; l < stop; ++l) {
     const MgLevel& F = A.lev[l];
-    k_mg_pre<<<F.blocks, kMgThreads, 0, s>>>(F, f, done);
-    k_mg_restrict<<<F.cblocks, kMgThreads, 0, s>>>(F, f, A.lev[l + 1].f, A.lev[l + 1].n, done);
+    if (l >= lf) {
+      k_mg_down<<<F.cblocks, kMgThreads, 0, s>>>(F, f, A.lev[l + 1].f, A.lev[l + 1].n, done);
+    } else {
+      k_mg_pre<<<F.blocks, kMgThreads, 0, s>>>(F, f, done);
+      k_mg_restrict<<<F.cblocks, kMgThreads, 0, s>>>(F, f, A.lev[l + 1].f, A.lev[l + 1].n, done);
+    }
     f = A.lev[l + 1].f;
   }
   if (lt > 0) {
@@ -723,28 +830,42 @@ static cudaError_t vcycle_lt(const Amg& A, int lt, const double* in, double* out
     const MgLevel& Cs = A.lev[A.L - 1];
     k_mg_coarse<<<cg, kMgThreads, 0, s>>>(A.binv, A.m, Cs.f, Cs.x, -1, done);
   }
+  // the corrected iterate of level stop: x of the coarsest level or the tail's
+  const double* xc = A.lev[stop].x;
   for (int l = stop - 1; l >= 0; --l) {
     const MgLevel& F = A.lev[l];
     const double* fl = l == 0 ? in : F.f;
-    k_mg_post1<<<F.blocks, kMgThreads, 0, s>>>(F, fl, A.lev[l + 1].x, A.alpha, done);
-    k_mg_post2<<<F.blocks, kMgThreads, 0, s>>>(F, fl, l == 0 ? out : F.x, l == 0 ? 1 : 0, done);
+    if (l >= lf) {
+      double* res = l == 0 ? out : F.y;  // the fused form reads F.x throughout
+      k_mg_up<<<F.blocks, kMgThreads, 0, s>>>(F, fl, xc, A.alpha, res, l == 0 ? 1 : 0, done);
+      xc = res;
+    } else {
+      k_mg_post1<<<F.blocks, kMgThreads, 0, s>>>(F, fl, xc, A.alpha, done);
+      double* res = l == 0 ? out : F.x;
+      k_mg_post2<<<F.blocks, kMgThreads, 0, s>>>(F, fl, res, l == 0 ? 1 : 0, done);
+      xc = res;
+    }
   }
   return cudaGetLastError();
 }
 
 cudaError_t amg_vcycle(const Amg& A, const double* in, double* out, const double* done, cudaStream_t s) {
-  return vcycle_lt(A, A.lt, in, out, done, s);
+  return vcycle_lt(A, A.lt, A.lf, in, out, done, s);
 }
 
 int amg_kernels_per_cycle(const Amg& A) {
   if (A.L == 1) return 1;
-  return 4 * (A.lt > 0 ? A.lt : A.L - 1) + 1;
+  const int stop = A.lt > 0 ? A.lt : A.L - 1;
+  int k = 1;
+  for (int l = 0; l < stop; ++l) k += l >= A.lf ? 2 : 4;
+  return k;
 }
 
-hsm_status amg_tune_tail(hsm_plan pl, Amg* A) {
+hsm_status amg_tune_tail(hsm_plan pl, Amg* A, int tail_from, int fused_from) {
   cudaStream_t s = pl->stream;
   A->lt = 0;
-  for (int l = 0; l < kMgMaxLevels; ++l) A->tail_ms[l] = -1.f;
+  A->lf = A->L;
+  for (int l = 0; l < kMgMaxLevels; ++l) A->tail_ms[l] = A->fuse_ms[l] = -1.f;
   if (A->L < 2) return HSM_OK;
   // the largest cluster the device schedules with 1024-thread CTAs
   int ctas = 0;
@@ -773,10 +894,11 @@ hsm_status amg_tune_tail(hsm_plan pl, Amg* A) {
       break;
     }
   }
-  if (!ctas) return HSM_OK;
   A->tail_ctas = ctas;
-  HSM_CUDA(pl, dev_alloc(&A->dlev, A->L, s));
-  HSM_CUDA(pl, cudaMemcpyAsync(A->dlev, A->lev, A->L * sizeof(MgLevel), cudaMemcpyHostToDevice, s));
+  if (ctas) {
+    HSM_CUDA(pl, dev_alloc(&A->dlev, A->L, s));
+    HSM_CUDA(pl, cudaMemcpyAsync(A->dlev, A->lev, A->L * sizeof(MgLevel), cudaMemcpyHostToDevice, s));
+  }
   // time each choice of the first tail level on zero vectors
   const int64_t N1 = A->lev[0].n + 1;
   double *in = nullptr, *out = nullptr, *done = nullptr;
@@ -789,23 +911,31 @@ hsm_status amg_tune_tail(hsm_plan pl, Amg* A) {
   HSM_CUDA(pl, cudaEventCreate(&e0));
   HSM_CUDA(pl, cudaEventCreate(&e1));
   float best = 1e30f;
-  int best_lt = 0;
+  int best_lt = 0, best_lf = A->L;
   cudaError_t ce = cudaSuccess;
   for (int lt = 0; lt < A->L && ce == cudaSuccess; ++lt) {
-    if (lt > 0 && A->lev[lt].n > kMgTailMaxRows) continue;
-    if (lt == 0 && A->L == 1) continue;
-    float ms = 0.f;
-    for (int rep = 0; rep < 2 && ce == cudaSuccess; ++rep) {  // the first pass warms up
-      ce = cudaEventRecord(e0, s);
-      for (int k = 0; k < 10 && ce == cudaSuccess; ++k) ce = vcycle_lt(*A, lt, in, out, done, s);
-      if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
-      if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
-      if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
-    }
-    if (ce == cudaSuccess) A->tail_ms[lt] = ms;
-    if (ce == cudaSuccess && ms < best) {
-      best = ms;
-      best_lt = lt;
+    if (lt > 0 && (!ctas || A->lev[lt].n > kMgTailMaxRows)) continue;
+    if (tail_from != 0 && lt != (tail_from > 0 ? tail_from : 0)) continue;  // fixed by the caller
+    // lf: first level of the fused down/up kernels (L: none)
+    for (int lf = A->L; lf >= 0 && ce == cudaSuccess; --lf) {
+      if (lt > 0 && lf > lt && lf != A->L) continue;  // past the tail: same cycle as lf = L
+      if (fused_from != 0 && lf != (fused_from > 0 ? std::min(fused_from - 1, A->L) : A->L)) continue;
+      float ms = 0.f;
+      for (int rep = 0; rep < 2 && ce == cudaSuccess; ++rep) {  // the first pass warms up
+        ce = cudaEventRecord(e0, s);
+        for (int k = 0; k < 10 && ce == cudaSuccess; ++k) ce = vcycle_lt(*A, lt, lf, in, out, done, s);
+        if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
+        if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+        if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+      }
+      if (ce != cudaSuccess) break;
+      if (lf == A->L) A->tail_ms[lt] = ms;
+      if (lt == 0 && lf < kMgMaxLevels) A->fuse_ms[lf] = ms;
+      if (ms < best) {
+        best = ms;
+        best_lt = lt;
+        best_lf = lf;
+      }
     }
   }
   cudaEventDestroy(e0);
@@ -813,8 +943,10 @@ hsm_status amg_tune_tail(hsm_plan pl, Amg* A) {
   dev_free(&in, s);
   dev_free(&out, s);
   dev_free(&done, s);
-  if (ce != cudaSuccess) return cuda_fail(pl, ce, "multigrid tail timing");
+  if (ce != cudaSuccess) return cuda_fail(pl, ce, "multigrid cycle timing");
+  if (best >= 1e30f) return set_error(pl, HSM_EINVAL, "the requested multigrid cycle shape is not available");
   A->lt = best_lt;
+  A->lf = best_lf;
   return HSM_OK;
 }
 
@@ -835,6 +967,7 @@ void amg_free(Amg* A, cudaStream_t s) {
   dev_free(&A->dlev, s);
   A->L = 0;
   A->lt = 0;
+  A->lf = kMgMaxLevels;
 }
 
 }  // namespace hsm

@@ -49,6 +49,10 @@ struct Amg {
   int lt = 0;
   int tail_ctas = 0;             // CTAs of the tail's cluster (0: no cluster could be scheduled)
   float tail_ms[kMgMaxLevels] = {};  // 10 cycles with the tail from level l (l = 0: no tail); -1 not tried
+  // levels lf.. (below the tail) use the fused down/up kernels (k_mg_down,
+  // k_mg_up); lf >= L: none.  Picked with lt by timing.
+  int lf = kMgMaxLevels;
+  float fuse_ms[kMgMaxLevels] = {};  // 10 cycles, no tail, fused from level l; -1 not tried
   MgLevel* dlev = nullptr;       // device copy of lev[0..L)
 };
 
@@ -62,9 +66,11 @@ hsm_status amg_setup(hsm_plan pl, const double* wp_mon, const double* wp_rbf, do
 // (inside a device-side loop that ends on convergence by itself).
 cudaError_t amg_vcycle(const Amg& amg, const double* in, double* out, const double* done, cudaStream_t s);
 int amg_kernels_per_cycle(const Amg& amg);
-// Picks the first level of the cluster tail (or none) by timing a few cycles
-// of each choice on scratch vectors of N + 1 entries.  Synchronises.
-hsm_status amg_tune_tail(hsm_plan pl, Amg* amg);
+// Picks the first level of the cluster tail (or none) and the first level of
+// the fused down/up kernels (or none) by timing a few cycles of each choice
+// on scratch vectors of N + 1 entries.  Synchronises.
+// tail_from / fused_from as hsm_phys.mg_tail_from / mg_fused_from (0: time).
+hsm_status amg_tune_tail(hsm_plan pl, Amg* amg, int tail_from, int fused_from);
 void amg_free(Amg* amg, cudaStream_t s);
 
 }  // namespace hsm

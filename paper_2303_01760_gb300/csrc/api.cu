@@ -242,10 +242,15 @@ hsm_status hsm_plan_compute_weights(hsm_plan p, hsm_prec prec, uint8_t* node_sta
   }
   HSM_CUDA(p, cudaMemsetAsync(p->dev_count + 1, 0, sizeof(int), s));
   p->n_reduced = 0;
+  // a phase this call does not run reports 0 in hsm_plan_profile
+  p->ev_used[HSM_PHASE_MON] = p->ev_used[HSM_PHASE_RBF] = false;
   hsm_status st = HSM_OK;
-  // the stencil build computed the MON weights; they are computed again here
-  // only when the caller asks for per-node status
-  if (node_status) {
+  // The MON weights: in the grouped FP64 launch (timed as the RBF-FD phase),
+  // else from the stencil build -- computed again here only when the build
+  // did not compute them (a grouped plan in another mode) or the caller asks
+  // for per-node status
+  const bool grouped = p->tune.grouped && prec == HSM_PREC_FP64;
+  if (!grouped && (node_status || p->tune.grouped)) {
     PhaseTimer tm(p, HSM_PHASE_MON);
     st = compute_mon_weights(p, node_status);
   }
@@ -253,7 +258,8 @@ hsm_status hsm_plan_compute_weights(hsm_plan p, hsm_prec prec, uint8_t* node_sta
   p->n_fallback = 0;
   PhaseTimer tm_rbf(p, HSM_PHASE_RBF);
   if (prec == HSM_PREC_FP64) {
-    st = compute_rbf_weights_fp64(p, nullptr, p->rbf.count, node_status);
+    st = grouped ? compute_weights_grouped_fp64(p, node_status)
+                 : compute_rbf_weights_fp64(p, nullptr, p->rbf.count, node_status);
     if (st != HSM_OK) return st;
   } else {
     int32_t* fail_list = nullptr;
@@ -465,6 +471,18 @@ static float time_ms(cudaStream_t s, const std::function<hsm_status()>& f, int r
   return ms / reps;
 }
 
+hsm_status hsm_plan_tuning(hsm_plan p, int* knn_qt, int* rbf_lanes, int* rbf_lanes32, int* apply_threads,
+                           int* grouped, int* tuned) {
+  if (!p) return set_error(nullptr, HSM_EINVAL, "plan is NULL");
+  if (knn_qt) *knn_qt = p->tune.knn_qt;
+  if (rbf_lanes) *rbf_lanes = p->tune.rbf_lanes;
+  if (rbf_lanes32) *rbf_lanes32 = p->tune.rbf_lanes32;
+  if (apply_threads) *apply_threads = p->tune.apply_threads;
+  if (grouped) *grouped = p->tune.grouped ? 1 : 0;
+  if (tuned) *tuned = p->tune.tuned ? 1 : 0;
+  return HSM_OK;
+}
+
 hsm_status hsm_plan_autotune(hsm_plan p, const char* cache_path) {
   if (!p) return set_error(nullptr, HSM_EINVAL, "plan is NULL");
   if (!p->stencils_built) return set_error(p, HSM_ESTATE, "hsm_plan_build_stencils must come first");
@@ -476,12 +494,13 @@ hsm_status hsm_plan_autotune(hsm_plan p, const char* cache_path) {
     while (in >> k >> v) cache[k] = v;
     auto it = cache.find(key);
     if (it != cache.end()) {
-      int t = 0, l = 0, qv = 1, l32 = 8;
-      if (sscanf(it->second.c_str(), "%d,%d,%d,%d", &t, &l, &qv, &l32) >= 2 && t > 0 && l > 0) {
+      int t = 0, l = 0, qv = 1, l32 = 8, gr = 0;
+      if (sscanf(it->second.c_str(), "%d,%d,%d,%d,%d", &t, &l, &qv, &l32, &gr) >= 2 && t > 0 && l > 0) {
         p->tune.apply_threads = t;
         p->tune.rbf_lanes = l;
         p->tune.knn_qt = qv;
         p->tune.rbf_lanes32 = l32;
+        p->tune.grouped = gr != 0;
         p->tune.tuned = true;
         return HSM_OK;
       }
@@ -541,6 +560,30 @@ hsm_status hsm_plan_autotune(hsm_plan p, const char* cache_path) {
   }
   p->tune.rbf_lanes = best_l;
   p->tune.rbf_lanes32 = best_l32;
+  // FP64 weights of both groups: MON beside the kNN search in the build graph
+  // plus one RBF-FD launch, or one grouped persistent launch; each timed as a
+  // whole build and weights pass
+  {
+    float best_ms = 1e30f;
+    bool best_g = p->tune.grouped;
+    for (bool gr : {false, true}) {
+      p->tune.grouped = gr;
+      float ms = time_ms(s, [&]() {
+        hsm_status r = hsm_plan_build_stencils(p);
+        if (r != HSM_OK) return r;
+        r = hsm_plan_compute_weights(p, HSM_PREC_FP64, nullptr);
+        return r == HSM_ESINGULAR ? HSM_OK : r;
+      }, 2, &st);
+      if (st != HSM_OK) return st;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best_g = gr;
+      }
+    }
+    p->tune.grouped = best_g;
+    st = hsm_plan_build_stencils(p);
+    if (st != HSM_OK) return st;
+  }
   if (!p->weights_built) {
     st = hsm_plan_compute_weights(p, HSM_PREC_FP64, nullptr);
     if (st != HSM_OK && st != HSM_ESINGULAR) return st;
@@ -569,7 +612,7 @@ hsm_status hsm_plan_autotune(hsm_plan p, const char* cache_path) {
   p->tune.tuned = true;
   if (cache_path) {
     std::ostringstream v;
-    v << best_t << "," << best_l << "," << p->tune.knn_qt << "," << best_l32;
+    v << best_t << "," << best_l << "," << p->tune.knn_qt << "," << best_l32 << "," << (p->tune.grouped ? 1 : 0);
     cache[key] = v.str();
     std::ofstream o(cache_path, std::ios::trunc);
     for (auto& kv : cache) o << kv.first << " " << kv.second << "\n";

@@ -41,6 +41,10 @@ struct Tuning {
   int rbf_lanes = 8;        // lanes per FP64 RBF-FD weight system (4, 8, 16, 32)
   int rbf_lanes32 = 8;      // lanes per FP32 + refinement weight system (4, 8, 16, 32)
   int knn_qt = 1;           // threads per kNN query (1, 2, 4)
+  // FP64 weights: false = MON weights beside the kNN search in the stencil
+  // build graph, then one RBF-FD launch; true = both groups in one persistent
+  // launch with a work queue (k_weights_grouped)
+  bool grouped = false;
   bool tuned = false;
 };
 
@@ -70,6 +74,7 @@ struct BuildWs {
   int* readback = nullptr;             // pinned host: demoted, n_mon, n_rbf, flags
   cudaGraphExec_t graph = nullptr;
   int graph_qt = 0;                    // kNN variant the graph was captured with
+  bool graph_grouped = false;          // captured without the MON weights branch
   const double* graph_spacing = nullptr;  // spacing array the graph was captured with
   int graph_kernels = 0;               // kernels per replay
   cudaStream_t cap = nullptr;
@@ -209,10 +214,13 @@ int64_t scan_scratch(int64_t n);
 hsm_status build_stencils(hsm_plan p);
 hsm_status alloc_build_ws(hsm_plan p);
 void free_build_ws(hsm_plan p);
-// MON weights enqueued inside the stencil build (count read on the device).
-cudaError_t enqueue_mon_weights(hsm_plan p, const int* count_dev, double* w, cudaStream_t s);
 
 // ---- weights.cu ----------------------------------------------------------
+// MON weights enqueued inside the stencil build (count read on the device).
+cudaError_t enqueue_mon_weights(hsm_plan p, const int* count_dev, double* w, cudaStream_t s);
+// FP64 weights of both stencil groups (MON and RBF-FD) in one persistent
+// launch with a work queue (k_weights_grouped); MON status codes as k_mon's.
+hsm_status compute_weights_grouped_fp64(hsm_plan p, uint8_t* status);
 // Raises the maximum dynamic shared memory of kernel fn to at least smem
 // (never lowers it: shapes cached for larger systems stay launchable).
 cudaError_t raise_smem_limit(void* fn, size_t smem);

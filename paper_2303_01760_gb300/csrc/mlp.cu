@@ -933,6 +933,26 @@ __global__ void k_gate_sample(const int32_t* __restrict__ learn, int64_t lc, int
   }
 }
 
+// The validation samples: S learned stencils spread evenly over the list.
+__global__ void k_gate_pick(const int32_t* __restrict__ learn, int64_t lc, int S, int32_t* sample_pos) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S; i += gridDim.x * blockDim.x)
+    sample_pos[i] = learn[(int64_t)i * lc / S];
+}
+
+// Puts the samples' saved weights back (inverse of k_gate_gather) and marks
+// their nodes as directly solved.
+__global__ void k_gate_scatter(double* __restrict__ w, int64_t G, int width, int nops,
+                               const int32_t* __restrict__ sample_pos, int S, const double* __restrict__ saved,
+                               const int32_t* __restrict__ nodes, uint8_t* status) {
+  const int64_t total = (int64_t)S * width * nops;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / ((int64_t)width * nops));
+    const int64_t r = e - (int64_t)i * width * nops;
+    w[r * G + sample_pos[i]] = saved[e];
+    if (status && r == 0) status[nodes[sample_pos[i]]] = HSM_NODE_LEARNED_SOLVE;
+  }
+}
+
 __global__ void k_gate_gather(const double* __restrict__ w, int64_t G, int width, int nops,
                               const int32_t* __restrict__ sample_pos, int S, double* saved) {
   const int64_t total = (int64_t)S * width * nops;
@@ -946,6 +966,15 @@ __global__ void k_gate_gather(const double* __restrict__ w, int64_t G, int width
 // Mean over the accepted samples of max|w_learned - w_direct| / max|w_direct|
 // (over all operators and stencil nodes), summed in a fixed order.
 constexpr int kGateThreads = 256;
+
+// Per-stencil out-of-distribution gate of the learned weights: a prediction
+// whose relative pre-projection residual |P^T w_hat - l_p| / |l_p| exceeds
+// this is re-solved directly.  The projection makes every accepted stencil
+// exact on the monomials whatever its residual, so this gate only rejects
+// gross outliers (the zero prediction, residual 1, projects to the
+// minimum-norm consistent stencil and passes); accuracy against the direct
+// solve is the batch validation's job.  The oracle states the same value.
+constexpr double kTauOod = 1.5;
 __global__ void __launch_bounds__(kGateThreads) k_gate_error(const double* __restrict__ w, int64_t G, int width,
                                                              int nops, const int32_t* __restrict__ sample_pos,
                                                              const uint8_t* __restrict__ sample_acc, int S,
@@ -1055,37 +1084,50 @@ hsm_status compute_rbf_weights_learned(hsm_plan p, uint8_t* status, int32_t* fai
     HSM_CUDA(p, dev_alloc(&Y, (size_t)lc * n * p->nops, s));
     HSM_CUDA(p, dev_alloc(&frame, lc, s));
     HSM_CUDA(p, dev_alloc(&acc, lc, s));
-    const int gl = (int)std::min<int64_t>(ceil_div(lc, T), (int64_t)num_sms() * 8);
-    k_features_infer2d<12><<<gl, T, 0, s>>>(p->coords, p->N, p->rbf.idx, G, learn, lc, X, frame);
-    HSM_CUDA(p, cudaGetLastError());
-    cudaStream_t old = m.stream;
-    m.stream = s;
-    hsm_status st = hsm_mlp_predict(p->mlp, X, lc, Y);
-    m.stream = old;
-    if (st != HSM_OK) return set_error(p, st, m.last_error);
-    const int gp = (int)std::min<int64_t>(ceil_div(lc, 128), (int64_t)num_sms() * 16);
-    k_project2d<12><<<gp, 128, 0, s>>>(p->coords, p->N, p->rbf.idx, G, learn, lc, Y, frame, 1.5, p->rbf.w64,
-                                       fail_list, fail_count, status, acc);
-    HSM_CUDA(p, cudaGetLastError());
-    p->launches += 4;
+    const int width = n, nops = p->nops;
+    // features, MLP and projection of the stencils in `list` (count of them)
+    auto infer = [&](const int32_t* list, int64_t count, int32_t* flist, int* fcount, uint8_t* accs) -> hsm_status {
+      const int gl = (int)std::min<int64_t>(ceil_div(count, T), (int64_t)num_sms() * 8);
+      k_features_infer2d<12><<<gl, T, 0, s>>>(p->coords, p->N, p->rbf.idx, G, list, count, X, frame);
+      HSM_CUDA(p, cudaGetLastError());
+      cudaStream_t old = m.stream;
+      m.stream = s;
+      hsm_status st = hsm_mlp_predict(p->mlp, X, count, Y);
+      m.stream = old;
+      if (st != HSM_OK) return set_error(p, st, m.last_error);
+      const int gp = (int)std::min<int64_t>(ceil_div(count, 128), (int64_t)num_sms() * 16);
+      k_project2d<12><<<gp, 128, 0, s>>>(p->coords, p->N, p->rbf.idx, G, list, count, Y, frame, kTauOod,
+                                         p->rbf.w64, flist, fcount, status, accs);
+      HSM_CUDA(p, cudaGetLastError());
+      p->launches += 4;
+      return HSM_OK;
+    };
     if (p->gate_samples > 0) {
+      // Batch validation first, on S samples alone: their learned weights
+      // against their direct solve.  A batch that fails it takes the direct
+      // solve without the full inference; one that passes runs the full
+      // inference and keeps the samples' direct weights.
       const int S = (int)std::min<int64_t>(lc, p->gate_samples);
-      const int width = n, nops = p->nops;
-      int32_t* spos = nullptr;
-      uint8_t* sacc = nullptr;
+      int32_t *spos = nullptr, *sfail = nullptr;
+      int* sfc = nullptr;
       double *saved = nullptr, *gerr = nullptr;
       HSM_CUDA(p, dev_alloc(&spos, S, s));
-      HSM_CUDA(p, dev_alloc(&sacc, S, s));
+      HSM_CUDA(p, dev_alloc(&sfail, S, s));
+      HSM_CUDA(p, dev_alloc(&sfc, 1, s));
       HSM_CUDA(p, dev_alloc(&saved, (size_t)S * width * nops, s));
       HSM_CUDA(p, dev_alloc(&gerr, 2, s));
-      k_gate_sample<<<(S + 255) / 256, 256, 0, s>>>(learn, lc, S, acc, spos, sacc);
-      k_gate_gather<<<(int)std::min<int64_t>(ceil_div((int64_t)S * width * nops, 256), 1024), 256, 0, s>>>(
-          p->rbf.w64, G, width, nops, spos, S, saved);
+      HSM_CUDA(p, cudaMemsetAsync(sfc, 0, sizeof(int), s));
+      k_gate_pick<<<(S + 255) / 256, 256, 0, s>>>(learn, lc, S, spos);
+      HSM_CUDA(p, cudaGetLastError());
+      hsm_status st = infer(spos, S, sfail, sfc, acc);
+      if (st != HSM_OK) return st;
+      const int gg = (int)std::min<int64_t>(ceil_div((int64_t)S * width * nops, 256), 1024);
+      k_gate_gather<<<gg, 256, 0, s>>>(p->rbf.w64, G, width, nops, spos, S, saved);
       HSM_CUDA(p, cudaGetLastError());
       // the samples' direct solve, in place (their status: learned -> solve)
-      hsm_status gs = compute_rbf_weights_fp64_marked(p, spos, S, status, HSM_NODE_LEARNED_SOLVE);
-      if (gs != HSM_OK) return gs;
-      k_gate_error<<<1, kGateThreads, 0, s>>>(p->rbf.w64, G, width, nops, spos, sacc, S, saved, gerr);
+      st = compute_rbf_weights_fp64_marked(p, spos, S, status, HSM_NODE_LEARNED_SOLVE);
+      if (st != HSM_OK) return st;
+      k_gate_error<<<1, kGateThreads, 0, s>>>(p->rbf.w64, G, width, nops, spos, acc, S, saved, gerr);
       HSM_CUDA(p, cudaGetLastError());
       double gh[2] = {0.0, 0.0};
       HSM_CUDA(p, cudaMemcpyAsync(gh, gerr, sizeof(gh), cudaMemcpyDeviceToHost, s));
@@ -1095,10 +1137,23 @@ hsm_status compute_rbf_weights_learned(hsm_plan p, uint8_t* status, int32_t* fai
       *gate_extra = (int64_t)gh[1];
       p->gate_accepted = (int64_t)gh[1];
       p->launches += 4;
+      if (!p->gate_failed) {
+        k_gate_gather<<<gg, 256, 0, s>>>(p->rbf.w64, G, width, nops, spos, S, saved);  // direct weights
+        HSM_CUDA(p, cudaGetLastError());
+        st = infer(learn, lc, fail_list, fail_count, acc);
+        if (st != HSM_OK) return st;
+        k_gate_scatter<<<gg, 256, 0, s>>>(p->rbf.w64, G, width, nops, spos, S, saved, p->rbf.nodes, status);
+        HSM_CUDA(p, cudaGetLastError());
+        p->launches += 2;
+      }
       dev_free(&spos, s);
-      dev_free(&sacc, s);
+      dev_free(&sfail, s);
+      dev_free(&sfc, s);
       dev_free(&saved, s);
       dev_free(&gerr, s);
+    } else {
+      hsm_status st = infer(learn, lc, fail_list, fail_count, acc);
+      if (st != HSM_OK) return st;
     }
   }
   dev_free(&learn, s);

@@ -569,16 +569,15 @@ __device__ __forceinline__ void flat2(int R, int C, int lane, F&& f) {
 //      all linear ones, so Z^T A Z is positive definite.
 // In exact arithmetic this is the solution of the augmented system; it takes
 // about half the FP64 operations of an LU of the (n + m) x (n + m) matrix.
+// FP64 RBF-FD systems at positions t0, t0 + stride, ... < t_end of the
+// launch's list, solved by the lane group whose system memory starts at xi
+// (sys_doubles doubles); par and cor are the monomial parent tables of the
+// block.
 template <int DIM, int NOPS, int LANES>
-__global__ void __launch_bounds__(256) k_rbf_fp64(RbfArgs a) {
-  extern __shared__ double smem[];
-  const int SYS = blockDim.x / LANES;
-  const int sub = threadIdx.x / LANES, lane = threadIdx.x % LANES;
-  const unsigned mask = LANES == 32 ? 0xffffffffu : (((1u << LANES) - 1u) << ((threadIdx.x & 31) / LANES * LANES));
+__device__ __forceinline__ void rbf64_systems(const RbfArgs& a, int64_t t0, int64_t t_end, int64_t stride, int lane,
+                                              unsigned mask, double* xi, const int8_t* par, const int8_t* cor) {
   const int n = a.n, m = a.n_mono, r = n - m, rc_ = r + NOPS;
   const int ldB = rc_ | 1;
-
-  double* xi = smem + (size_t)sub * sys_doubles(DIM, NOPS, n, m);
   double* rc = xi + n * DIM;
   double* Ap = rc + n;
   double* Sm = Ap;  // Ap is dead once Bm is formed
@@ -586,10 +585,7 @@ __global__ void __launch_bounds__(256) k_rbf_fp64(RbfArgs a) {
   double* Bm = Pw + (n + NOPS) * m;
   double* inv = Bm + n * ldB;
   int* perm = reinterpret_cast<int*>(inv + n);
-  __shared__ int8_t par[kMaxMonomials], cor[kMaxMonomials];
-  mono_parents(a.mono_exp, m, DIM, par, cor);
-  __syncthreads();
-  for (int64_t t = (int64_t)blockIdx.x * SYS + sub; t < a.count; t += (int64_t)gridDim.x * SYS) {
+  for (int64_t t = t0; t < t_end; t += stride) {
     const int64_t pos = a.list ? a.list[t] : t;
     const int32_t c = a.nodes[pos];
     // ---- offsets, the power-of-two scale, |xi| and the monomial rows of P
@@ -597,7 +593,7 @@ __global__ void __launch_bounds__(256) k_rbf_fp64(RbfArgs a) {
     for (int j = lane; j < n; j += LANES) {
       const int32_t id = a.idx[(int64_t)j * a.G + pos];
       double r2 = 0.0;
-#pragma unroll
+  #pragma unroll
       for (int k = 0; k < DIM; ++k) {
         const double o = a.coords[k * a.N + id] - a.coords[k * a.N + c];
         xi[j * DIM + k] = o;
@@ -608,7 +604,7 @@ __global__ void __launch_bounds__(256) k_rbf_fp64(RbfArgs a) {
       const unsigned long long rb = (unsigned long long)__double_as_longlong(r2);
       bmax = rb > bmax ? rb : bmax;
     }
-#pragma unroll
+  #pragma unroll
     for (int o = LANES / 2; o > 0; o >>= 1) {
       const unsigned long long u = shfl_xor_u64(mask, bmax, o, LANES);
       bmax = u > bmax ? u : bmax;
@@ -618,7 +614,7 @@ __global__ void __launch_bounds__(256) k_rbf_fp64(RbfArgs a) {
     __syncwarp(mask);
     for (int j = lane; j < n; j += LANES) {
       double* x = xi + j * DIM;
-#pragma unroll
+  #pragma unroll
       for (int k = 0; k < DIM; ++k) x[k] *= inv_s;
       double* row = Pw + j * m;
       for (int q = 0; q < m; ++q) row[q] = mono_value<DIM, double>(row, x, q, par, cor, a.mono_exp);
@@ -638,7 +634,7 @@ __global__ void __launch_bounds__(256) k_rbf_fp64(RbfArgs a) {
           brow = i;
         }
       }
-#pragma unroll
+  #pragma unroll
       for (int o = LANES / 2; o > 0; o >>= 1) {
         const unsigned long long ob = shfl_xor_u64(mask, best, o, LANES);
         const int orow = __shfl_xor_sync(mask, brow, o, LANES);
@@ -713,7 +709,7 @@ __global__ void __launch_bounds__(256) k_rbf_fp64(RbfArgs a) {
         const double* xa = xi + ni * DIM;
         const double* xb = xi + nj * DIM;
         double d2 = 0.0;
-#pragma unroll
+  #pragma unroll
         for (int k = 0; k < DIM; ++k) {
           const double d = xa[k] - xb[k];
           d2 = fma(d, d, d2);
@@ -799,6 +795,20 @@ __global__ void __launch_bounds__(256) k_rbf_fp64(RbfArgs a) {
     }
     __syncwarp(mask);
   }
+}
+
+template <int DIM, int NOPS, int LANES>
+__global__ void __launch_bounds__(256) k_rbf_fp64(RbfArgs a) {
+  extern __shared__ double smem[];
+  const int SYS = blockDim.x / LANES;
+  const int sub = threadIdx.x / LANES, lane = threadIdx.x % LANES;
+  const unsigned mask = LANES == 32 ? 0xffffffffu : (((1u << LANES) - 1u) << ((threadIdx.x & 31) / LANES * LANES));
+  double* xi = smem + (size_t)sub * sys_doubles(DIM, NOPS, a.n, a.n_mono);
+  __shared__ int8_t par[kMaxMonomials], cor[kMaxMonomials];
+  mono_parents(a.mono_exp, a.n_mono, DIM, par, cor);
+  __syncthreads();
+  rbf64_systems<DIM, NOPS, LANES>(a, (int64_t)blockIdx.x * SYS + sub, a.count, (int64_t)gridDim.x * SYS, lane, mask,
+                                  xi, par, cor);
 }
 
 // FP32 factorization with FP64 iterative refinement.  The FP32 matrix is

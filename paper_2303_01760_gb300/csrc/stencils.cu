@@ -758,10 +758,13 @@ cudaError_t enqueue_build(hsm_plan p, cudaStream_t s, int qt, int* nk) {
   else k_mon_stencil<3><<<grid, T, 0, w.side>>>(w.ijk, p->mon.nodes, counts, N, lh, p->mon.idx);
   ++k;
   HSM_TRY(cudaGetLastError());
-  // MON weights on the same branch: they need only the MON stencils and run
-  // beside the kNN search, which leaves most of each SM idle
-  HSM_TRY(enqueue_mon_weights(p, counts, w.mon_w64, w.side));
-  ++k;
+  // MON weights on the same branch (unless the plan solves both groups in the
+  // grouped weights launch): they need only the MON stencils and run beside
+  // the kNN search, which leaves most of each SM idle
+  if (!p->tune.grouped) {
+    HSM_TRY(enqueue_mon_weights(p, counts, w.mon_w64, w.side));
+    ++k;
+  }
   HSM_TRY(cudaEventRecord(w.ev_join, w.side));
 
   // ---- kNN for the RBF-FD group
@@ -828,7 +831,7 @@ hsm_status build_stencils(hsm_plan p) {
   BuildWs& w = p->ws;
   cudaStream_t s = p->stream;
   const int qt = p->tune.knn_qt == 4 ? 4 : (p->tune.knn_qt == 2 ? 2 : 1);
-  if (!w.graph || w.graph_qt != qt || w.graph_spacing != p->spacing) {
+  if (!w.graph || w.graph_qt != qt || w.graph_spacing != p->spacing || w.graph_grouped != p->tune.grouped) {
     if (w.graph) cudaGraphExecDestroy(w.graph);
     w.graph = nullptr;
     // kernel attributes are set outside the capture
@@ -853,6 +856,7 @@ hsm_status build_stencils(hsm_plan p) {
     }
     w.graph_qt = qt;
     w.graph_spacing = p->spacing;
+    w.graph_grouped = p->tune.grouped;
     w.graph_kernels = nk;
   }
   HSM_CUDA(p, cudaGraphLaunch(w.graph, s));

@@ -1126,6 +1126,8 @@ hsm_status hsm_stepper_create(hsm_stepper* out, hsm_plan pl, const hsm_phys* phy
   if (phys->guess_order < -1 || phys->guess_order > 1)
     return set_error(pl, HSM_EINVAL, "guess_order must be -1, 0 or 1");
   if (phys->apply_f32 != 0 && phys->apply_f32 != 1) return set_error(pl, HSM_EINVAL, "apply_f32 must be 0 or 1");
+  if (phys->mg_tail_from < -1 || phys->mg_fused_from < -1)
+    return set_error(pl, HSM_EINVAL, "mg_tail_from and mg_fused_from must be >= -1");
   if (phys->precond != HSM_PRECOND_AMG && phys->precond != HSM_PRECOND_JACOBI)
     return set_error(pl, HSM_EINVAL, "unknown preconditioner");
   if (phys->apply_f32 && (!pl->mon.w32 || !pl->rbf.w32)) {
@@ -1198,7 +1200,7 @@ hsm_status hsm_stepper_create(hsm_stepper* out, hsm_plan pl, const hsm_phys* phy
       if (!st->amg) return fail(set_error(pl, HSM_ENOMEM, "host allocation failed"));
       // over-correction of the coarse-grid step (2^d nodes per aggregate)
       hsm_status as = amg_setup(pl, a.wp[0], a.wp[1], pl->dim == 2 ? 1.8 : 1.5, st->amg);
-      if (as == HSM_OK) as = amg_tune_tail(pl, st->amg);
+      if (as == HSM_OK) as = amg_tune_tail(pl, st->amg, phys->mg_tail_from, phys->mg_fused_from);
       if (as != HSM_OK) return fail(as);
     }
   }
@@ -1220,14 +1222,17 @@ hsm_status hsm_step(hsm_stepper st, int n_steps, double* v, double* T, double* p
 }
 
 hsm_status hsm_stepper_info(hsm_stepper st, int* mg_levels, int* mg_tail_level, int* mg_tail_ctas,
-                            int* kernels_per_iter, float* tail_ms) {
+                            int* mg_fused_level, int* kernels_per_iter, float* tail_ms, float* fused_ms) {
   if (!st) return set_error(nullptr, HSM_EINVAL, "stepper is NULL");
   if (mg_levels) *mg_levels = st->amg ? st->amg->L : 0;
   if (mg_tail_level) *mg_tail_level = st->amg ? st->amg->lt : 0;
   if (mg_tail_ctas) *mg_tail_ctas = st->amg ? st->amg->tail_ctas : 0;
+  if (mg_fused_level) *mg_fused_level = st->amg ? st->amg->lf : 0;
   if (kernels_per_iter) *kernels_per_iter = chunk_kernels(st) / chunk_iters(st) + 1;
-  if (tail_ms)
-    for (int l = 0; l < kMgMaxLevels; ++l) tail_ms[l] = st->amg ? st->amg->tail_ms[l] : -1.f;
+  for (int l = 0; l < kMgMaxLevels; ++l) {
+    if (tail_ms) tail_ms[l] = st->amg ? st->amg->tail_ms[l] : -1.f;
+    if (fused_ms) fused_ms[l] = st->amg ? st->amg->fuse_ms[l] : -1.f;
+  }
   return HSM_OK;
 }
 

@@ -66,18 +66,16 @@ namespace {
 // pivoting: every pivot stays within rounding of 1, -1 or 2, so the
 // elimination runs as straight-line code in registers.  A pivot below 1e-8
 // (impossible for a lattice stencil) marks the node singular.
+// MON weights of the nodes at positions p0, p0 + stride, ... < G of the group.
 template <int DIM, int NOPS>
-__global__ void __launch_bounds__(128) k_mon(const double* __restrict__ coords, int64_t N,
-                                             const int32_t* __restrict__ idx, int64_t G, OpsDesc ops,
-                                             double* __restrict__ w, uint8_t* __restrict__ status,
-                                             const int32_t* __restrict__ nodes, unsigned* flags,
-                                             const int* __restrict__ G_dev) {
+__device__ __forceinline__ void mon_nodes(const double* __restrict__ coords, int64_t N,
+                                          const int32_t* __restrict__ idx, int64_t G, const OpsDesc& ops,
+                                          double* __restrict__ w, uint8_t* __restrict__ status,
+                                          const int32_t* __restrict__ nodes, unsigned* flags, int64_t p0,
+                                          int64_t stride) {
   constexpr int K = 2 * DIM + 1;
   constexpr int C = K + NOPS;
-  // the group size is read on the device when the launch is part of the
-  // stencil build (it is known on the host only after the build)
-  if (G_dev) G = *G_dev;
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < G; p += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t p = p0; p < G; p += stride) {
     int32_t id[K];
 #pragma unroll
     for (int j = 0; j < K; ++j) id[j] = idx[(int64_t)j * G + p];
@@ -216,6 +214,75 @@ __global__ void __launch_bounds__(128) k_mon(const double* __restrict__ coords, 
 }
 
 template <int DIM, int NOPS>
+__global__ void __launch_bounds__(128) k_mon(const double* __restrict__ coords, int64_t N,
+                                             const int32_t* __restrict__ idx, int64_t G, OpsDesc ops,
+                                             double* __restrict__ w, uint8_t* __restrict__ status,
+                                             const int32_t* __restrict__ nodes, unsigned* flags,
+                                             const int* __restrict__ G_dev) {
+  // the group size is read on the device when the launch is part of the
+  // stencil build (it is known on the host only after the build)
+  if (G_dev) G = *G_dev;
+  mon_nodes<DIM, NOPS>(coords, N, idx, G, ops, w, status, nodes, flags, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+                       (int64_t)gridDim.x * blockDim.x);
+}
+
+// MON group of a grouped launch.
+struct MonArgs {
+  const double* coords;
+  int64_t N;
+  const int32_t* idx;
+  int64_t G;
+  OpsDesc ops;
+  double* w;
+  uint8_t* status;
+  const int32_t* nodes;
+  unsigned* flags;
+};
+
+// Weights of both stencil groups, systems of uneven size, in one persistent
+// launch: every block takes work items from one queue (an atomic counter)
+// until it is empty.  An item is a batch of SYS = blockDim / LANES RBF-FD
+// systems (one per lane group, FP64 null-space solve: the FP64 pipe bounds
+// the launch) or a chunk of blockDim MON nodes (one per thread: a few loads
+// and stores, memory-bound).  The M MON chunks are spread evenly over the
+// T items (item i is the MON chunk f(i) when f(i+1) > f(i), f(i) =
+// floor(i M / T), else the RBF-FD batch i - f(i)), so memory-bound and
+// FP64-bound blocks share the SMs.  No block waits on another.
+template <int DIM, int NOPS, int LANES>
+__global__ void __launch_bounds__(256) k_weights_grouped(RbfArgs a, MonArgs mo, int64_t mon_items, int64_t items,
+                                                         int* queue) {
+  extern __shared__ double smem[];
+  const int SYS = blockDim.x / LANES;
+  const int sub = threadIdx.x / LANES, lane = threadIdx.x % LANES;
+  const unsigned mask = LANES == 32 ? 0xffffffffu : (((1u << LANES) - 1u) << ((threadIdx.x & 31) / LANES * LANES));
+  double* xi = smem + (size_t)sub * sys_doubles(DIM, NOPS, a.n, a.n_mono);
+  __shared__ int8_t par[kMaxMonomials], cor[kMaxMonomials];
+  __shared__ int item_s;
+  mono_parents(a.mono_exp, a.n_mono, DIM, par, cor);
+  __syncthreads();
+  for (;;) {
+    if (threadIdx.x == 0) item_s = atomicAdd(queue, 1);
+    __syncthreads();
+    const int64_t item = item_s;
+    __syncthreads();
+    if (item >= items) break;
+    const int64_t f0 = item * mon_items / items, f1 = (item + 1) * mon_items / items;
+    if (f1 == f0) {
+      const int64_t t = (item - f0) * SYS + sub;
+      rbf64_systems<DIM, NOPS, LANES>(a, t, t + 1 < a.count ? t + 1 : a.count, 1, lane, mask, xi, par, cor);
+    } else {
+      const int64_t p = f0 * blockDim.x + threadIdx.x;
+      mon_nodes<DIM, NOPS>(mo.coords, mo.N, mo.idx, mo.G, mo.ops, mo.w, mo.status, mo.nodes, mo.flags, p, mo.G);
+    }
+  }
+}
+
+template <int DIM, int NOPS, int LANES>
+struct GroupedKernel {
+  static void* ptr() { return (void*)k_weights_grouped<DIM, NOPS, LANES>; }
+};
+
+template <int DIM, int NOPS>
 __global__ void k_to_f32(const double* __restrict__ w, float* __restrict__ w32, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     w32[i] = (float)w[i];
@@ -270,7 +337,8 @@ struct RbfShape {
   size_t smem = 0;
 };
 
-cudaError_t rbf_shape(bool r32, int dim, int nops, int K, int ld, int n, int lanes, RbfShape* out) {
+cudaError_t rbf_shape(bool r32, int dim, int nops, int K, int ld, int n, int lanes, RbfShape* out,
+                      bool grouped = false) {
   struct Entry {
     void* fn;
     size_t per;
@@ -280,7 +348,9 @@ cudaError_t rbf_shape(bool r32, int dim, int nops, int K, int ld, int n, int lan
   const size_t per = smem_bytes(dim, nops, r32, K, ld, n);
   for (; lanes <= 32; lanes *= 2) {
     void* fn = r32 ? pick_fp32r_fixed(dim, nops, K, lanes) : nullptr;
-    if (!fn) fn = r32 ? pick<Fp32rKernel>(dim, nops, lanes) : pick<Fp64Kernel>(dim, nops, lanes);
+    if (!fn)
+      fn = r32 ? pick<Fp32rKernel>(dim, nops, lanes)
+               : (grouped ? pick<GroupedKernel>(dim, nops, lanes) : pick<Fp64Kernel>(dim, nops, lanes));
     for (const Entry& e : cache)
       if (e.fn == fn && e.per == per) {
         *out = e.shape;
@@ -367,7 +437,55 @@ hsm_status launch_rbf(hsm_plan p, bool r32, const int32_t* list, int64_t count, 
   return HSM_OK;
 }
 
+// Both groups' FP64 weights in one k_weights_grouped launch.
+hsm_status launch_grouped_fp64(hsm_plan p, uint8_t* status) {
+  RbfArgs a{};
+  a.coords = p->coords;
+  a.N = p->N;
+  a.list = nullptr;
+  a.count = p->rbf.count;
+  a.idx = p->rbf.idx;
+  a.G = p->rbf.count;
+  a.nodes = p->rbf.nodes;
+  a.n = p->n;
+  a.n_mono = p->n_mono;
+  a.K = p->n + p->n_mono;
+  a.ld = (a.K + p->nops) | 1;
+  a.mono_exp = p->mono_exp;
+  a.pairs = p->pairs;
+  a.ops = make_ops(p, p->op_mask);
+  a.w = p->rbf.w64;
+  a.status = status;
+  a.status_demoted_mark = 0;
+  a.is_regular = p->is_regular;
+  a.flags = p->dev_flags;
+  const bool rec = p->sing_list && p->sing_cap >= p->rbf.count;
+  a.sing_list = rec ? p->sing_list : nullptr;
+  a.sing_count = rec ? p->dev_count + 1 : nullptr;
+  a.sing_cap = rec ? p->rbf.count : 0;
+  MonArgs mo{p->coords, p->N, p->mon.idx, p->mon.count, make_ops(p, p->op_mask), p->mon.w64, status,
+             p->mon.nodes, p->dev_flags};
+  RbfShape sh;
+  HSM_CUDA(p, rbf_shape(false, p->dim, p->nops, a.K, a.ld, a.n, p->tune.rbf_lanes, &sh, true));
+  if (!sh.fn) return set_error(p, HSM_EINVAL, "RBF-FD system too large for shared memory");
+  const int spb = sh.threads / sh.lanes;
+  const int64_t mon_items = ceil_div(p->mon.count, sh.threads);
+  const int64_t items = ceil_div(p->rbf.count, spb) + mon_items;
+  if (items == 0) return HSM_OK;
+  if (items >= ((int64_t)1 << 31) - (int64_t)num_sms() * sh.blocks_per_sm)
+    return set_error(p, HSM_EINVAL, "too many weight systems for one grouped launch");
+  const int grid = (int)std::min<int64_t>(items, (int64_t)num_sms() * sh.blocks_per_sm);
+  int* queue = p->dev_count + 2;
+  HSM_CUDA(p, cudaMemsetAsync(queue, 0, sizeof(int), p->stream));
+  void* args[] = {&a, &mo, (void*)&mon_items, (void*)&items, &queue};
+  HSM_CUDA(p, cudaLaunchKernel(sh.fn, dim3(grid), dim3(sh.threads), args, sh.smem, p->stream));
+  p->launches += 1;
+  return HSM_OK;
+}
+
 }  // namespace
+
+hsm_status compute_weights_grouped_fp64(hsm_plan p, uint8_t* status) { return launch_grouped_fp64(p, status); }
 
 cudaError_t launch_rbf_external(const RbfExternal& x, bool r32, const int32_t* list, int64_t count, uint8_t* status,
                                 uint8_t mark, bool* too_big) {
@@ -449,15 +567,15 @@ static cudaError_t launch_mon(hsm_plan p, int64_t G, const int* G_dev, double* w
   return cudaGetLastError();
 }
 
+cudaError_t enqueue_mon_weights(hsm_plan p, const int* count_dev, double* w, cudaStream_t s) {
+  return launch_mon(p, p->N, count_dev, w, nullptr, s);
+}
+
 hsm_status compute_mon_weights(hsm_plan p, uint8_t* status) {
   if (p->mon.count == 0) return HSM_OK;
   HSM_CUDA(p, launch_mon(p, p->mon.count, nullptr, p->mon.w64, status, p->stream));
   p->launches += 1;
   return HSM_OK;
-}
-
-cudaError_t enqueue_mon_weights(hsm_plan p, const int* count_dev, double* w, cudaStream_t s) {
-  return launch_mon(p, p->N, count_dev, w, nullptr, s);
 }
 
 hsm_status compute_rbf_weights_fp64(hsm_plan p, const int32_t* list, int64_t count, uint8_t* status) {

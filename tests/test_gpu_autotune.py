@@ -1,7 +1,9 @@
 """Autotuned launch configurations against the FP64 oracle.
 
 hsm_plan_autotune picks, per plan, the threads per kNN query, the lanes per
-RBF-FD system (FP64 and FP32 + refinement) and the apply block size.  Every
+RBF-FD system (FP64 and FP32 + refinement), the arrangement of the FP64
+weights (one grouped persistent launch for both groups, or MON weights beside
+the kNN search plus one RBF-FD launch) and the apply block size.  Every
 configuration it can pick must give the oracle's stencils (bit-exact), weights
 (1e-10 FP64, 1e-5 FP32 + refinement) and operator values.  The tuner's own
 choice is checked, then every variant is forced through its cache file."""
@@ -62,11 +64,12 @@ def test_autotuned_plan_and_every_variant_match_the_oracle(tmp_path):
     _check(p, ns, st, W, hsm.HSM_PREC_FP32_REFINE, 1e-5)
     p.close()
     key, chosen = open(cache).read().split()
-    assert len(chosen.split(",")) == 4
-    # apply threads, FP64 lanes, kNN threads per query, FP32 lanes
-    for t, l64, q, l32 in ((64, 4, 2, 16), (128, 16, 4, 32), (256, 32, 1, 4)):
+    assert len(chosen.split(",")) == 5
+    # apply threads, FP64 lanes, kNN threads per query, FP32 lanes, grouped
+    # FP64 weights launch (1) or MON beside the kNN search (0)
+    for t, l64, q, l32, gr in ((64, 4, 2, 16, 1), (128, 16, 4, 32, 0), (256, 32, 1, 4, 1), (256, 8, 1, 8, 0)):
         with open(cache, "w") as f:
-            f.write(f"{key} {t},{l64},{q},{l32}\n")
+            f.write(f"{key} {t},{l64},{q},{l32},{gr}\n")
         p = plan_with(cache)                  # loads the forced variant
         _check(p, ns, st, W, hsm.HSM_PREC_FP64, 1e-10)
         _check(p, ns, st, W, hsm.HSM_PREC_FP32_REFINE, 1e-5)

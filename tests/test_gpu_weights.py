@@ -224,10 +224,11 @@ def test_mon_weights_on_slightly_perturbed_lattice():
     _check_plan(ns, m=2)
 
 
-def test_mon_weights_from_the_build_match_the_oracle():
-    """Without a node-status request the MON weights come from the stencil
-    build (computed beside the kNN search); they match the oracle, and bit for
-    bit the weights that the status-writing path computes."""
+def test_mon_weights_of_the_grouped_launch_match_the_oracle():
+    """The MON weights come from the grouped weights launch (MON chunks and
+    RBF-FD batches drawn from one work queue), with and without a node-status
+    request; they match the oracle, and the two calls agree bit for bit, on
+    exact, perturbed and banded lattices."""
     base = nodesets.square_wall_band(n=24, wall_band=0.0)
     pert = nodesets.square_wall_band(n=24, wall_band=0.0)
     rng = np.random.default_rng(9)

@@ -1,6 +1,7 @@
 """Pins for the oracle's learned-weight pieces: GELU, MLP gradients, Adam,
 and the consistency projection (its defining properties)."""
 import numpy as np
+import pytest
 
 from oracle import learned as ol
 from oracle import stencils as ost
@@ -136,3 +137,28 @@ def test_mlp_forward_hand_computed():
     # gelu(-1) = -(1 - Phi(1)), gelu(0) = 0
     assert abs(out[1, 0] - (-(1.0 - phi1) + 0.5)) < 1e-14
     assert np.array_equal(pre[0], np.array([[1.0, 2.0], [-1.0, 0.0]]))
+
+
+def test_bf16_inputs_alone_move_the_weights_beyond_the_learned_tolerance():
+    """The learned predictor's tensor-core layers take bf16 inputs (8-bit
+    significand).  Rounding the scaled offsets of interior scattered stencils
+    to bf16 and solving exactly moves the weights by about 1.4e-3 relative
+    (median; mean about 1.6e-3) on a Poisson-disk set: above the 1e-3 gate of
+    the learned path, before any approximation error of the network.  A
+    network whose first layer reads bf16 offsets cannot meet that gate on
+    average, however well trained."""
+    torch = pytest.importorskip("torch")
+    ns = nodesets.square_all_scattered(n=60, seed=nodesets.SEED_BASE + 700)
+    st = ost.build_stencils(ns.coords, ns.is_regular, ns.is_boundary, ns.h, 12, normals=ns.normals)
+    idx = st["rbf_idx"][ns.is_boundary[st["rbf_nodes"]] == 0][:1500]
+    xi, _ = ow._scaled_offsets(ns.coords, idx)
+
+    def solve(x):
+        M, rhs = ow.rbffd_system(x, 2, ow.ops_for(2))
+        return np.linalg.solve(M, rhs)[:, :12, :]
+
+    w = solve(xi)
+    xb = torch.from_numpy(xi).to(torch.bfloat16).to(torch.float64).numpy()
+    rel = np.abs(solve(xb) - w).max((1, 2)) / np.abs(w).max((1, 2))
+    assert np.abs(xb - xi).max() <= 2.0 ** -9 * np.abs(xi).max()   # bf16 rounding, nothing more
+    assert rel.mean() > 1e-3 and np.median(rel) > 7e-4
