@@ -455,6 +455,7 @@ def run_gpu(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_h, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded node sets; no paper geometry)",
+            "parity_ok": None, "parity": None,
             "config": workload_desc(ns),
             "e2e": e2e,
             "gpu_launches": int(launches_h // max(args.steps, 1)) * args.steps,
@@ -490,7 +491,6 @@ def run_gpu(args):
                           "all_rbffd": dict(zip(["stencils", "mon_weights", "weights", "apply"],
                                                 np.mean(ph_a, 0).round(4).tolist()))},
             "counts": {"mon": q_h["n_mon"], "rbf": n_rbf_h, "demoted": q_h["n_demoted"]},
-            "parity": None,
             "apply_roofline": big,
             "three_d": three_d,
             "learned": learned,
@@ -508,6 +508,7 @@ def run_gpu(args):
     if rank == 0:
         if world == 1:
             res["cpu_baseline"], res["parity"] = cpu_baseline(args.cpu_sample, gpu_npz)
+            res["parity_ok"] = bool(res["parity"] and res["parity"].get("ok"))
             try:
                 res["cpu_baseline_all_cores"] = cpu_baseline_all_cores()
             except Exception as exc:  # reported, never fatal to the GPU line
@@ -924,6 +925,23 @@ def run_kernels(args):
     from paper_2303_01760_gb300 import hsm, nodesets
 
     dev = torch.device("cuda:0")
+    if args.three_d:
+        # the 1.88M-node 3D set with m = args.three_d: FP64 weights, then f64
+        # and f32 applies of dx, dy, dz, lap
+        ns = nodesets.cached(nodesets.cube_spheres, n=125)
+        dd = [torch.from_numpy(a).to(dev) for a in (ns.coords, ns.is_regular, ns.is_boundary, ns.normals)]
+        plan = hsm.Plan(dd[0], dd[1], dd[2], ns.h, m=args.three_d, normals=dd[3])
+        plan.build_stencils()
+        plan.compute_weights(hsm.HSM_PREC_FP64, allow_singular=True)
+        u = torch.from_numpy(nodesets.field_random_smooth(ns.coords)[0]).to(dev)
+        out = torch.empty((4, ns.N), dtype=torch.float64, device=dev)
+        for uu in (u, u.float()):
+            for _ in range(args.warmup + args.steps):
+                plan.apply(uu, out=out)
+        torch.cuda.synchronize()
+        plan.close()
+        print("3d apply ok", ns.N)
+        return
     if args.big_apply:
         # the 7.3M-node tiled set: FP64 weights, then f64 applies of dx, dy, lap
         base = nodesets.cached(nodesets.square_holes, n=250, band=0.09)
@@ -938,6 +956,8 @@ def run_kernels(args):
     nrm = torch.from_numpy(ns.normals).to(dev)
     u = torch.from_numpy(nodesets.field_sincos(ns.coords)[0]).to(dev)
     plan = hsm.Plan(c, reg, bnd, ns.h, m=2, normals=nrm)
+    if args.knn_qt:
+        plan.set_tuning(knn_qt=args.knn_qt)
     prec = {"fp64": hsm.HSM_PREC_FP64, "fp32r": hsm.HSM_PREC_FP32_REFINE}[args.prec]
     if args.learned:
         # learned weights on the predictor's workload shape: a short training on
@@ -1520,6 +1540,8 @@ def main():
     ap.add_argument("--stepper", action="store_true", help="with --kernels: run --steps Boussinesq steps instead")
     ap.add_argument("--learned", action="store_true", help="with --kernels: learned weights instead")
     ap.add_argument("--big-apply", action="store_true", help="with --kernels: f64 applies on the 7.3M-node set")
+    ap.add_argument("--three-d", type=int, default=0, help="with --kernels: m of f64 and f32 applies on the 3D set")
+    ap.add_argument("--knn-qt", type=int, default=0, help="with --kernels: fix the kNN threads per query (1, 2, 4)")
     ap.add_argument("--train-steps", type=int, default=3000, help="with --kernels --learned")
     ap.add_argument("--dvd", type=int, default=0, help="de Vahl Davis validation run on a 1/n lattice (no benchmark)")
     ap.add_argument("--layout", default="hybrid", choices=["hybrid", "scattered", "regular"], help="with --dvd")

@@ -194,7 +194,8 @@ hsm_status hsm_plan_condition(hsm_plan plan, double* kappa);
  * gradient taken with the plan's first-derivative weights (Eq. 1).  The
  * plan's op mask must hold d/dx_k for every axis of its dimension.
  *   T        device f64 [N]
- *   nodes    device int32 [count] node ids, count >= 1
+ *   nodes    device int32 [count] node ids, count >= 1; an id outside
+ *            [0, N) is not followed and makes out[0] a quiet NaN
  *   normals  device f64 [dim][N] unit normals (only the listed nodes are read)
  *   scale    L / (T_H - T_C) for the Nusselt number
  *   out      device f64 [1]
@@ -213,21 +214,31 @@ hsm_status hsm_wall_flux_mean(hsm_plan plan, const double* T, const int32_t* nod
 hsm_status hsm_apply(hsm_plan plan, unsigned op_mask, hsm_dtype in_dtype, const void* u,
                      double* out);
 
-/* Times the kernel variants of this plan (threads per kNN query, lanes per
- * RBF-FD weight system in FP64 and FP32, the grouped or split arrangement of
- * the FP64 weights, the apply block size) on its own data and keeps the
- * fastest of each.
+/* Times the kernel variants of this plan (the kNN search: 1, 2 or 4 threads
+ * per query over growing rings of cells, or one warp per query over a fixed
+ * window of cells with the ring search finishing the queries the window
+ * cannot settle; lanes per RBF-FD weight system in FP64 and FP32; the grouped
+ * or split arrangement of the FP64 weights; the apply block size) on its own
+ * data and keeps the fastest of each.
  * cache_path: NULL = no cache; otherwise a text file read before and updated
  * after tuning, keyed by device name and problem shape.  Synchronises.      */
 hsm_status hsm_plan_autotune(hsm_plan plan, const char* cache_path);
 
 /* The plan's kernel variants (host outputs, any may be NULL): threads per kNN
- * query, lanes per RBF-FD system in FP64 and in FP32 + refinement, threads per
+ * query (1, 2 or 4), lanes per RBF-FD system in
+ * FP64 and in FP32 + refinement, threads per
  * block of the apply, and 1 when the FP64 weights of both groups run in one
  * grouped launch (0: MON weights beside the kNN search, then one RBF-FD
  * launch).  tuned is 1 after hsm_plan_autotune.                             */
 hsm_status hsm_plan_tuning(hsm_plan plan, int* knn_qt, int* rbf_lanes, int* rbf_lanes32, int* apply_threads,
                            int* grouped, int* tuned);
+
+/* Sets the plan's kernel variants instead of timing them (reproducible runs,
+ * tests): knn_qt 1, 2 or 4; rbf_lanes and rbf_lanes32 4, 8, 16 or 32;
+ * apply_threads 64, 128 or 256; grouped 0 or 1.  HSM_EINVAL for other
+ * values.  Takes effect at the next build / weights / apply call.          */
+hsm_status hsm_plan_set_tuning(hsm_plan plan, int knn_qt, int rbf_lanes, int rbf_lanes32, int apply_threads,
+                               int grouped);
 
 /* Phases timed by hsm_plan_profile. */
 enum { HSM_PHASE_STENCILS = 0, HSM_PHASE_MON = 1, HSM_PHASE_RBF = 2, HSM_PHASE_APPLY = 3,
@@ -468,10 +479,10 @@ hsm_status hsm_rbf_weights_fp32r_noalloc(int dim, int aug_m, int stencil_n, unsi
 /* ------------------------------------------------------------------------ */
 
 /* FP64 fused multiply-add throughput of the current device, the bound of the
- * RBF-FD weight solves: 4, 8 or 16 independent FMA chains per thread, 4 or 8
- * blocks of 256 threads per SM, 4096 iterations; the best rate over those
- * shapes of 3 timed launches each (CUDA events on cuda_stream) after one
- * warm-up.
+ * RBF-FD weight solves: 4 to 32 independent FMA chains per thread (with a
+ * constant or a register multiplier and addend), 2 to 8 blocks of 256 threads
+ * per SM, 4096 iterations; the best rate over those shapes of 3 timed launches
+ * each (CUDA events on cuda_stream) after one warm-up.
  *   gflops  host f64: 2 flop per FMA / time, in GFLOP/s (required)
  *   ms      host f32 or NULL: the best launch's time
  * Synchronises the stream.                                                   */

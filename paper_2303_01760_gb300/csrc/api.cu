@@ -483,6 +483,25 @@ hsm_status hsm_plan_tuning(hsm_plan p, int* knn_qt, int* rbf_lanes, int* rbf_lan
   return HSM_OK;
 }
 
+hsm_status hsm_plan_set_tuning(hsm_plan p, int knn_qt, int rbf_lanes, int rbf_lanes32, int apply_threads,
+                               int grouped) {
+  if (!p) return set_error(nullptr, HSM_EINVAL, "plan is NULL");
+  auto in = [](int v, std::initializer_list<int> ok) {
+    for (int o : ok)
+      if (v == o) return true;
+    return false;
+  };
+  if (!in(knn_qt, {1, 2, 4}) || !in(rbf_lanes, {4, 8, 16, 32}) || !in(rbf_lanes32, {4, 8, 16, 32}) ||
+      !in(apply_threads, {64, 128, 256}) || !in(grouped, {0, 1}))
+    return set_error(p, HSM_EINVAL, "unknown kernel variant");
+  p->tune.knn_qt = knn_qt;
+  p->tune.rbf_lanes = rbf_lanes;
+  p->tune.rbf_lanes32 = rbf_lanes32;
+  p->tune.apply_threads = apply_threads;
+  p->tune.grouped = grouped != 0;
+  return HSM_OK;
+}
+
 hsm_status hsm_plan_autotune(hsm_plan p, const char* cache_path) {
   if (!p) return set_error(nullptr, HSM_EINVAL, "plan is NULL");
   if (!p->stencils_built) return set_error(p, HSM_ESTATE, "hsm_plan_build_stencils must come first");
@@ -495,7 +514,8 @@ hsm_status hsm_plan_autotune(hsm_plan p, const char* cache_path) {
     auto it = cache.find(key);
     if (it != cache.end()) {
       int t = 0, l = 0, qv = 1, l32 = 8, gr = 0;
-      if (sscanf(it->second.c_str(), "%d,%d,%d,%d,%d", &t, &l, &qv, &l32, &gr) >= 2 && t > 0 && l > 0) {
+      if (sscanf(it->second.c_str(), "%d,%d,%d,%d,%d", &t, &l, &qv, &l32, &gr) >= 2 && t > 0 && l > 0 &&
+          (qv == 1 || qv == 2 || qv == 4)) {
         p->tune.apply_threads = t;
         p->tune.rbf_lanes = l;
         p->tune.knn_qt = qv;

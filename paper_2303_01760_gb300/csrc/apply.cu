@@ -112,7 +112,8 @@ void* pick_nops(int nops, int wm, int wr) {
 // Average Nusselt number of Section 4.1: scale * mean_i |n_i . grad T(x_i)|
 // over the listed nodes, one block; each thread sums its nodes in order and
 // the block adds the partial sums in a fixed tree, so the result does not
-// depend on timing.
+// depend on timing.  The node ids come from the caller: an id outside [0, N)
+// is not followed, and the result is then a quiet NaN.
 constexpr int kFluxThreads = 256;
 
 template <int DIM>
@@ -123,9 +124,16 @@ __global__ void __launch_bounds__(kFluxThreads) k_wall_flux(
     const int32_t* __restrict__ idx_r, const double* __restrict__ w_r, int64_t cnt_r, int width_r, Slots<3> slot,
     double scale, double* out) {
   __shared__ double part[kFluxThreads];
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
   double acc = 0.0;
   for (int64_t i = threadIdx.x; i < count; i += kFluxThreads) {
     const int32_t c = nodes[i];
+    if (c < 0 || (int64_t)c >= N) {
+      bad = 1;
+      continue;
+    }
     const bool mon = kind[c] == 0;
     const int32_t* idx = mon ? idx_m : idx_r;
     const double* w = mon ? w_m : w_r;
@@ -147,7 +155,7 @@ __global__ void __launch_bounds__(kFluxThreads) k_wall_flux(
     if (threadIdx.x < h) part[threadIdx.x] += part[threadIdx.x + h];
     __syncthreads();
   }
-  if (threadIdx.x == 0) out[0] = scale * part[0] / (double)count;
+  if (threadIdx.x == 0) out[0] = bad ? __longlong_as_double(0x7ff8000000000000ll) : scale * part[0] / (double)count;
 }
 
 }  // namespace

@@ -40,7 +40,7 @@ struct Tuning {
   int apply_split = 1;      // lanes per RBF-FD stencil in the apply kernel (1, 2, 4)
   int rbf_lanes = 8;        // lanes per FP64 RBF-FD weight system (4, 8, 16, 32)
   int rbf_lanes32 = 8;      // lanes per FP32 + refinement weight system (4, 8, 16, 32)
-  int knn_qt = 1;           // threads per kNN query (1, 2, 4)
+  int knn_qt = 1;           // threads per kNN query (1, 2 or 4)
   // FP64 weights: false = MON weights beside the kNN search in the stencil
   // build graph, then one RBF-FD launch; true = both groups in one persistent
   // launch with a work queue (k_weights_grouped)

@@ -1080,11 +1080,23 @@ hsm_status compute_rbf_weights_learned(hsm_plan p, uint8_t* status, int32_t* fai
     HSM_CUDA(p, cudaMemcpyAsync(kinds, kh, sizeof(kh), cudaMemcpyHostToDevice, s));
     if (!(dim == 2 && n == 12 && p->n_mono == 6 && p->op_mask == (HSM_DX | HSM_DY | HSM_LAP)))
       return set_error(p, HSM_EINVAL, "learned weights support 2D m = 2, n = 12 plans with ops dx, dy, lap");
-    HSM_CUDA(p, dev_alloc(&X, (size_t)lc * n * dim, s));
-    HSM_CUDA(p, dev_alloc(&Y, (size_t)lc * n * p->nops, s));
-    HSM_CUDA(p, dev_alloc(&frame, lc, s));
-    HSM_CUDA(p, dev_alloc(&acc, lc, s));
     const int width = n, nops = p->nops;
+    // feature, output, frame and acceptance buffers for `rows` stencils
+    // (first the validation samples alone, the whole batch only if it passes)
+    int64_t cap = 0;
+    auto reserve = [&](int64_t rows) -> hsm_status {
+      if (rows <= cap) return HSM_OK;
+      dev_free(&X, s);
+      dev_free(&Y, s);
+      dev_free(&frame, s);
+      dev_free(&acc, s);
+      HSM_CUDA(p, dev_alloc(&X, (size_t)rows * n * dim, s));
+      HSM_CUDA(p, dev_alloc(&Y, (size_t)rows * n * nops, s));
+      HSM_CUDA(p, dev_alloc(&frame, rows, s));
+      HSM_CUDA(p, dev_alloc(&acc, rows, s));
+      cap = rows;
+      return HSM_OK;
+    };
     // features, MLP and projection of the stencils in `list` (count of them)
     auto infer = [&](const int32_t* list, int64_t count, int32_t* flist, int* fcount, uint8_t* accs) -> hsm_status {
       const int gl = (int)std::min<int64_t>(ceil_div(count, T), (int64_t)num_sms() * 8);
@@ -1119,7 +1131,9 @@ hsm_status compute_rbf_weights_learned(hsm_plan p, uint8_t* status, int32_t* fai
       HSM_CUDA(p, cudaMemsetAsync(sfc, 0, sizeof(int), s));
       k_gate_pick<<<(S + 255) / 256, 256, 0, s>>>(learn, lc, S, spos);
       HSM_CUDA(p, cudaGetLastError());
-      hsm_status st = infer(spos, S, sfail, sfc, acc);
+      hsm_status st = reserve(S);
+      if (st != HSM_OK) return st;
+      st = infer(spos, S, sfail, sfc, acc);
       if (st != HSM_OK) return st;
       const int gg = (int)std::min<int64_t>(ceil_div((int64_t)S * width * nops, 256), 1024);
       k_gate_gather<<<gg, 256, 0, s>>>(p->rbf.w64, G, width, nops, spos, S, saved);
@@ -1140,6 +1154,8 @@ hsm_status compute_rbf_weights_learned(hsm_plan p, uint8_t* status, int32_t* fai
       if (!p->gate_failed) {
         k_gate_gather<<<gg, 256, 0, s>>>(p->rbf.w64, G, width, nops, spos, S, saved);  // direct weights
         HSM_CUDA(p, cudaGetLastError());
+        st = reserve(lc);
+        if (st != HSM_OK) return st;
         st = infer(learn, lc, fail_list, fail_count, acc);
         if (st != HSM_OK) return st;
         k_gate_scatter<<<gg, 256, 0, s>>>(p->rbf.w64, G, width, nops, spos, S, saved, p->rbf.nodes, status);
@@ -1152,7 +1168,9 @@ hsm_status compute_rbf_weights_learned(hsm_plan p, uint8_t* status, int32_t* fai
       dev_free(&saved, s);
       dev_free(&gerr, s);
     } else {
-      hsm_status st = infer(learn, lc, fail_list, fail_count, acc);
+      hsm_status st = reserve(lc);
+      if (st != HSM_OK) return st;
+      st = infer(learn, lc, fail_list, fail_count, acc);
       if (st != HSM_OK) return st;
     }
   }

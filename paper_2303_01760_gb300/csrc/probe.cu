@@ -31,6 +31,27 @@ __global__ void __launch_bounds__(256) k_fp64_fma(int iters, double a, double b)
   if (s == -1.0) g_fma_sink = s;
 }
 
+// The same with every operand in registers (a per-chain multiplier and a
+// per-thread addend), as the FMAs of the weight and apply kernels have them.
+template <int CH>
+__global__ void __launch_bounds__(256) k_fp64_fma_reg(int iters, double a, double b) {
+  double x[CH], m[CH];
+  const double z = b * (1.0 + 1e-3 * threadIdx.x);
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    x[c] = 1e-3 * (threadIdx.x + c);
+    m[c] = a - 1e-9 * c;
+  }
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < CH; ++c) x[c] = fma(x[c], m[c], z);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < CH; ++c) s += x[c];
+  if (s == -1.0) g_fma_sink = s;
+}
+
 __global__ void k_eval(int fn, const double* __restrict__ x, double* __restrict__ y, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double v = x[i];
@@ -64,8 +85,9 @@ extern "C" hsm_status hsm_probe_fp64_peak(double* gflops, float* ms, void* cuda_
     void (*fn)(int, double, double);
     int chains, bps;
   };
-  const Shape shapes[] = {{k_fp64_fma<8>, 8, 8}, {k_fp64_fma<16>, 16, 4}, {k_fp64_fma<4>, 4, 8},
-                          {k_fp64_fma<16>, 16, 8}};
+  const Shape shapes[] = {{k_fp64_fma<8>, 8, 8},      {k_fp64_fma<16>, 16, 4},     {k_fp64_fma<4>, 4, 8},
+                          {k_fp64_fma<16>, 16, 8},    {k_fp64_fma_reg<8>, 8, 8},   {k_fp64_fma_reg<16>, 16, 4},
+                          {k_fp64_fma_reg<4>, 4, 8},  {k_fp64_fma_reg<8>, 8, 4},   {k_fp64_fma_reg<32>, 32, 2}};
   const int threads = 256, iters = 4096;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t e = cudaEventCreate(&e0);

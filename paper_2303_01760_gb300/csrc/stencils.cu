@@ -15,6 +15,7 @@
 // interior nodes nearest to x_c - h n_c, so their one-sided stencils reach
 // several node layers.
 #include <cfloat>
+#include <cmath>
 
 #include "common.cuh"
 
@@ -425,27 +426,51 @@ __device__ __forceinline__ double sq_dist(const double* a, const double* b) {
   return s;
 }
 
-// QT threads per query (a "quad" of consecutive lanes).  The shell cells of
-// each ring are dealt round-robin to the quad's threads; every thread keeps its
-// own sorted top-n list in shared memory ([n][blockDim] structure of arrays,
-// bank-conflict free) and prunes candidates against its own n-th key and the
-// quad's merged n-th key of the previous ring.  After each ring the quad
-// leader merges the QT lists to find the quad's n-th key for the stopping
-// test; at the end it merges them into the stencil.
+// QT threads per query (a "quad" of consecutive lanes).  Every thread keeps
+// its own sorted top-n list of (d2, id) keys in shared memory ([n][blockDim]
+// structure of arrays, bank-conflict free) and prunes candidates against its
+// own n-th key and the quad's merged n-th key of the previous pass.
+//
+// The first pass scans the whole window of rings 0..R0 around the search
+// point's cell; each later pass scans one more ring.  After every pass the
+// quad leader merges the QT lists to find the quad's n-th key, and the search
+// stops once that distance is below the distance from the search point to the
+// scanned region's edge; at the end the leader merges the lists into the
+// stencil.  The result does not depend on R0: any region that passes the
+// stopping test holds the n smallest keys.  R0 only decides how much one pass
+// scans.  It is set per query from the local spacing hs (the plan's spacing
+// array, else h): R0 = floor(rfac * hs / cell) + 1, clamped to [1, RMAX], with
+// rfac * hs an estimate of the n-th neighbour distance (from n and the
+// dimension, set by the caller; a boundary node's search point lies h inside
+// the wall, where about half the disc or ball is outside the domain, so it
+// takes 2^(1/DIM) more).  The distance to the window's edge lies in
+// [R0, R0 + 1/2) cells, so the window holds the n-th neighbour with R0 cells
+// to spare in the common case.
+//
+// Scanning rings one by one, with a dependent chain of loads per cell (the
+// cell's range, then its nodes), left each query's thread waiting on memory
+// for about fifty cells in a row.  A row of the window, and the top and bottom
+// rows of a ring, are runs of cells that are consecutive in the cell order,
+// so their nodes are one contiguous range of the sorted arrays: one pair of
+// range loads per row, and the node loads of a range are issued four at a
+// time before any of them is used.  The rows of a pass are dealt round-robin
+// to the quad's threads, and so are the single side cells of a ring.
 template <int DIM, int QT>
 __global__ void __launch_bounds__(32 * QT) k_knn(const double* __restrict__ coords, int64_t N,
                                              const uint8_t* __restrict__ is_boundary,
                                              const double* __restrict__ normals, double h,
                                              const double* __restrict__ spacing,
                                              const int32_t* __restrict__ queries, const int* __restrict__ nq_dev,
-                                             int n_full, const CellGrid* __restrict__ cgp,
+                                             int n_full, double rfac, const CellGrid* __restrict__ cgp,
                                              const int32_t* __restrict__ start, const int32_t* __restrict__ sorted_id,
                                              const double* __restrict__ sorted_xyz,
                                              const uint8_t* __restrict__ sorted_bnd, int32_t* __restrict__ out_idx,
                                              unsigned* flags) {
+  constexpr int RMAX = DIM == 2 ? 6 : 4;
+  constexpr int BATCH = 4;
   extern __shared__ unsigned char smem_raw[];
   const int B = blockDim.x;
-  const int64_t nq = *nq_dev;
+  const int64_t nq = *nq_dev;  // the stride of out_idx
   const CellGrid cg = *cgp;
   double* kd = reinterpret_cast<double*>(smem_raw);
   int32_t* ki = reinterpret_cast<int32_t*>(kd + (size_t)n_full * B);
@@ -461,17 +486,51 @@ __global__ void __launch_bounds__(32 * QT) k_knn(const double* __restrict__ coor
     double q[DIM];
     int cq[DIM];
     // one local spacing inside: h(x_c) of a refined node set, else h
-    const double hc = (bnd_center && spacing) ? spacing[c] : h;
+    const double hs = spacing ? spacing[c] : h;
+    const double hc = bnd_center ? hs : h;
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
       q[k] = coords[k * N + c];
       if (bnd_center && normals) q[k] = __dsub_rn(q[k], __dmul_rn(hc, normals[k * N + c]));
       cq[k] = cg.cell_of(q[k], k);
     }
+    const double rf = bnd_center ? rfac * (DIM == 2 ? 1.4142135623730951 : 1.2599210498948732) : rfac;
+    const int r0 = (int)fmin(fmax(floor(rf * hs * cg.inv_cell) + 1.0, 1.0), (double)RMAX);
     int cnt = 0;
-    double qd = DBL_MAX;  // quad's n-th key after the last ring (pruning bound)
+    double qd = DBL_MAX;  // quad's n-th key after the last pass (pruning bound)
     int32_t qid = 0x7fffffff;
-    for (int r = 0;; ++r) {
+    // nodes [s0, s1) of the sorted arrays, loads issued BATCH at a time
+    auto scan = [&](int32_t s0, int32_t s1) {
+      for (int32_t s = s0; s < s1; s += BATCH) {
+        int32_t id[BATCH];
+        bool use[BATCH];
+        double x[BATCH][DIM];
+#pragma unroll
+        for (int u = 0; u < BATCH; ++u) {
+          const int32_t su = min(s + u, s1 - 1);
+          id[u] = sorted_id[su];
+          use[u] = s + u < s1 && !(bnd_center && sorted_bnd[su]);
+#pragma unroll
+          for (int k = 0; k < DIM; ++k) x[u][k] = sorted_xyz[(int64_t)su * kMaxDim + k];
+        }
+#pragma unroll
+        for (int u = 0; u < BATCH; ++u) {
+          if (!use[u]) continue;
+          const double d2 = sq_dist<DIM>(x[u], q);
+          if (!key_less(d2, id[u], qd, qid)) continue;
+          if (cnt == n && !key_less(d2, id[u], kd[(n - 1) * B + t], ki[(n - 1) * B + t])) continue;
+          int j = (cnt < n) ? cnt++ : n - 1;
+          while (j > 0 && key_less(d2, id[u], kd[(j - 1) * B + t], ki[(j - 1) * B + t])) {
+            kd[j * B + t] = kd[(j - 1) * B + t];
+            ki[j * B + t] = ki[(j - 1) * B + t];
+            --j;
+          }
+          kd[j * B + t] = d2;
+          ki[j * B + t] = id[u];
+        }
+      }
+    };
+    for (int r = r0;; ++r) {
       int lo[DIM], hi[DIM];
       bool any_inside = false;
 #pragma unroll
@@ -480,39 +539,25 @@ __global__ void __launch_bounds__(32 * QT) k_knn(const double* __restrict__ coor
         hi[k] = cq[k] + r;
         if (lo[k] >= 0 || hi[k] < cg.g[k]) any_inside = true;
       }
-      if (r > 0 && !any_inside) break;
-      int cc[DIM];
-      int turn = 0;  // shell-cell counter; this thread takes turn % QT == sub
+      if (r > r0 && !any_inside) break;
+      const bool window = r == r0;
+      int turn = 0;  // row / side-cell counter; this thread takes turn % QT == sub
+      const int xa = max(lo[0], 0), xb = min(hi[0], cg.g[0] - 1);
       const int zlo = DIM == 3 ? max(lo[DIM - 1], 0) : 0, zhi = DIM == 3 ? min(hi[DIM - 1], cg.g[DIM - 1] - 1) : 0;
       for (int z = zlo; z <= zhi; ++z) {
-        if (DIM == 3) cc[2] = z;
-        const bool zedge = DIM == 3 && (z == lo[2] || z == hi[2]);
+        const bool zedge = DIM == 3 && (z == lo[DIM - 1] || z == hi[DIM - 1]);
         for (int y = max(lo[1], 0); y <= min(hi[1], cg.g[1] - 1); ++y) {
-          cc[1] = y;
-          const bool full = r == 0 || zedge || y == lo[1] || y == hi[1];
-          const int xstep = full ? 1 : (hi[0] - lo[0]);
-          for (int x = lo[0]; x <= hi[0]; x += xstep) {
-            if (x < 0 || x >= cg.g[0]) continue;
+          const int64_t row = ((int64_t)z * cg.g[1] + y) * cg.g[0];
+          if (window || zedge || y == lo[1] || y == hi[1]) {
             if ((turn++ % QT) != sub) continue;
-            cc[0] = x;
-            int64_t l = 0;
+            scan(start[row + xa], start[row + xb + 1]);
+          } else {
 #pragma unroll
-            for (int k = DIM - 1; k >= 0; --k) l = l * cg.g[k] + cc[k];
-            const int32_t s0 = start[l], s1 = start[l + 1];
-            for (int32_t s = s0; s < s1; ++s) {
-              const int32_t id = sorted_id[s];
-              if (bnd_center && sorted_bnd[s]) continue;
-              const double d2 = sq_dist<DIM>(sorted_xyz + (int64_t)s * kMaxDim, q);
-              if (!key_less(d2, id, qd, qid)) continue;
-              if (cnt == n && !key_less(d2, id, kd[(n - 1) * B + t], ki[(n - 1) * B + t])) continue;
-              int j = (cnt < n) ? cnt++ : n - 1;
-              while (j > 0 && key_less(d2, id, kd[(j - 1) * B + t], ki[(j - 1) * B + t])) {
-                kd[j * B + t] = kd[(j - 1) * B + t];
-                ki[j * B + t] = ki[(j - 1) * B + t];
-                --j;
-              }
-              kd[j * B + t] = d2;
-              ki[j * B + t] = id;
+            for (int e = 0; e < 2; ++e) {
+              const int x = e ? hi[0] : lo[0];
+              if (x < 0 || x >= cg.g[0]) continue;
+              if ((turn++ % QT) != sub) continue;
+              scan(start[row + x], start[row + x + 1]);
             }
           }
         }
@@ -804,8 +849,13 @@ cudaError_t enqueue_build(hsm_plan p, cudaStream_t s, int qt, int* nk) {
     int32_t* sid = w.sorted_id;
     double* sxyz = w.sorted_xyz;
     uint8_t* sb = w.sorted_bnd;
+    // first-window radius factor: the radius of the disc (ball) that holds n
+    // nodes at density 1, widened by 1.1 for the lower density of a scattered
+    // set than of the lattice
+    const double omega = dim == 2 ? M_PI : 4.0 * M_PI / 3.0;
+    double rfac = 1.1 * std::pow((double)p->n / omega, 1.0 / dim);
     void* args[] = {(void*)&coords, (void*)&NN, (void*)&isb, (void*)&nrm, (void*)&hh, (void*)&spc, (void*)&qlist,
-                    (void*)&nqd, (void*)&nf, (void*)&cgd, (void*)&cs, (void*)&sid, (void*)&sxyz,
+                    (void*)&nqd, (void*)&nf, (void*)&rfac, (void*)&cgd, (void*)&cs, (void*)&sid, (void*)&sxyz,
                     (void*)&sb, (void*)&outp, (void*)&fl};
     HSM_TRY(cudaLaunchKernel(fn, dim3(gk), dim3(KT), args, smem, s));
     ++k;

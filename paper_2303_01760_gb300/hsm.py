@@ -64,6 +64,7 @@ _SIGS = {
     "hsm_plan_learned_gate": (C.c_int, [_p, C.POINTER(C.c_double), C.POINTER(C.c_int), C.POINTER(_i64)]),
     "hsm_plan_autotune": (C.c_int, [_p, C.c_char_p]),
     "hsm_plan_tuning": (C.c_int, [_p] + [C.POINTER(C.c_int)] * 6),
+    "hsm_plan_set_tuning": (C.c_int, [_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]),
     "hsm_plan_destroy": (C.c_int, [_p]),
     "hsm_plan_profile": (C.c_int, [_p, C.POINTER(C.c_float), C.POINTER(_i64)]),
     "hsm_plan_set_timing": (C.c_int, [_p, C.c_int]),
@@ -365,6 +366,10 @@ class Plan:
 
     def autotune(self, cache_path=None):
         check(lib.hsm_plan_autotune(self.h, cache_path.encode() if cache_path else None), self.h)
+
+    def set_tuning(self, knn_qt=1, rbf_lanes=8, rbf_lanes32=8, apply_threads=256, grouped=0):
+        check(lib.hsm_plan_set_tuning(self.h, int(knn_qt), int(rbf_lanes), int(rbf_lanes32), int(apply_threads),
+                                      int(grouped)), self.h)
 
     def tuning(self):
         v = [C.c_int() for _ in range(6)]

@@ -67,7 +67,8 @@ def test_autotuned_plan_and_every_variant_match_the_oracle(tmp_path):
     assert len(chosen.split(",")) == 5
     # apply threads, FP64 lanes, kNN threads per query, FP32 lanes, grouped
     # FP64 weights launch (1) or MON beside the kNN search (0)
-    for t, l64, q, l32, gr in ((64, 4, 2, 16, 1), (128, 16, 4, 32, 0), (256, 32, 1, 4, 1), (256, 8, 1, 8, 0)):
+    for t, l64, q, l32, gr in ((64, 4, 2, 16, 1), (128, 16, 4, 32, 0), (256, 32, 1, 4, 1), (256, 8, 1, 8, 0),
+                               (128, 8, 4, 8, 1)):
         with open(cache, "w") as f:
             f.write(f"{key} {t},{l64},{q},{l32},{gr}\n")
         p = plan_with(cache)                  # loads the forced variant
@@ -75,3 +76,48 @@ def test_autotuned_plan_and_every_variant_match_the_oracle(tmp_path):
         _check(p, ns, st, W, hsm.HSM_PREC_FP32_REFINE, 1e-5)
         p.close()
     assert os.path.exists(cache)
+
+
+@pytest.mark.parametrize("qt", [1, 2, 4])
+@pytest.mark.parametrize("which", ["refined2d", "refined3d", "cube_m3"])
+def test_knn_variants_match_the_oracle(which, qt):
+    """Every kNN variant (1, 2 or 4 threads per query; a first window of rings
+    0..R0 sized from the local spacing, then ring by ring) on h-refined sets,
+    whose spacing varies by a factor of several inside one window and whose
+    boundary stencils search from a point one local spacing inside, and on
+    the 3D set with m = 3 (n = 40): every stencil equal to the oracle's, and
+    the weights within 1e-10."""
+    from paper_2303_01760_gb300 import hsm
+
+    from test_gpu_weights import REFINED_2D, REFINED_3D
+
+    if which == "refined2d":
+        ns, m = nodesets.holes_refined(**REFINED_2D), 2
+    elif which == "refined3d":
+        ns, m = nodesets.holes_refined(**REFINED_3D), 2
+    else:
+        ns, m = nodesets.cube_spheres(n=14, n_holes=2, r_range=(0.1, 0.15), band=0.12,
+                                      seed=nodesets.SEED_BASE + 21), 3
+    n = ow.stencil_size(ns.dim, m)
+    st = ost.build_stencils(ns.coords, ns.is_regular, ns.is_boundary, ns.h, n, normals=ns.normals,
+                            spacing=ns.spacing)
+    W = ow.all_weights(ns.coords, st, m)
+    dv = to_dev(ns)
+    p = hsm.Plan(dv["coords"], dv["is_regular"], dv["is_boundary"], ns.h, m=m, normals=dv["normals"],
+                 spacing=dv["spacing"])
+    p._dv = dv
+    for bad in (0, 3, 32):
+        with pytest.raises(hsm.HsmError):
+            p.set_tuning(knn_qt=bad, rbf_lanes=8, rbf_lanes32=8, apply_threads=128, grouped=0)
+    p.set_tuning(knn_qt=qt, rbf_lanes=8, rbf_lanes32=8, apply_threads=128, grouped=0)
+    p.build_stencils()
+    assert p.tuning()["knn_qt"] == qt
+    assert p.compute_weights(hsm.HSM_PREC_FP64) == 0
+    bits = {"dx": 1, "dy": 2, "dz": 4, "lap": 8}
+    for op in ow.ops_for(ns.dim):
+        rp, col, val = gpu_csr(p, bits[op])
+        ix = rp[st["rbf_nodes"]][:, None] + np.arange(n)[None, :]
+        assert np.array_equal(col[ix], st["rbf_idx"]), which
+        e = np.abs(val[ix] - W["rbf"][op]).max(1) / np.abs(W["rbf"][op]).max(1)
+        assert e.max() <= 1e-10, (which, op, e.max())
+    p.close()

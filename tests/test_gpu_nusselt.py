@@ -37,3 +37,26 @@ def test_wall_flux_matches_the_oracle(layout):
         again = float(plan.wall_flux_mean(Td, nodes, nrm, scale=1.0).item())
         assert again == got
     plan.close()
+
+
+def test_wall_flux_rejects_node_ids_out_of_range():
+    """Node ids outside [0, N), forged on the host, are not followed: the
+    result is NaN, and the same call with the valid ids alone is unchanged."""
+    import torch
+
+    ns = nodesets.square_quarters(n=40, layout="hybrid")
+    plan, code, _ = make_plan(ns, m=2)
+    assert code == 0
+    cold = np.flatnonzero((ns.is_boundary == 1) & (ns.coords[0] == 0.0)).astype(np.int32)
+    Td = torch.from_numpy(ns.coords[0] - 0.5).cuda()
+    nrm = plan._dev["normals"]
+    good = float(plan.wall_flux_mean(Td, torch.from_numpy(cold).cuda(), nrm, scale=1.0).item())
+    assert np.isfinite(good)
+    for bad_id in (-1, ns.N, np.iinfo(np.int32).max, np.iinfo(np.int32).min):
+        forged = cold.copy()
+        forged[len(forged) // 2] = bad_id
+        got = float(plan.wall_flux_mean(Td, torch.from_numpy(forged).cuda(), nrm, scale=1.0).item())
+        assert np.isnan(got), bad_id
+    again = float(plan.wall_flux_mean(Td, torch.from_numpy(cold).cuda(), nrm, scale=1.0).item())
+    assert again == good
+    plan.close()
