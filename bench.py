@@ -576,13 +576,63 @@ def run_stepper(hsm, ns, plan, d, dev, stream, args, steps=30):
     b.record(stream)
     torch.cuda.synchronize()
     ms = a.elapsed_time(b)
+    info = st.info()
     st.close()
+    iters = float(np.mean(its))
+    us_it = ms * 1e3 / steps / max(iters, 1e-9)
+    wk = krylov_iteration_work(info, ns.N)
+    peak_h, src_h = hbm_peak()
     return {"workload": "2D irregular domain (the timed node set), Ra=1e6, Pr=0.71, dt=0.1h^2/2, "
                         "bordered pressure by BiCGSTAB to 1e-10, right-preconditioned by an aggregation-multigrid "
                         "V(2,2)-cycle",
             "steps": steps, "ms_per_step": ms / steps, "node_steps_per_s": ns.N * steps / (ms * 1e-3),
-            "krylov_iters_per_step": float(np.mean(its)), "first_steps_iters": it0,
-            "converged": code == 0, "T_finite": bool(torch.isfinite(T).all())}
+            "krylov_iters_per_step": iters, "first_steps_iters": it0,
+            "converged": code == 0, "T_finite": bool(torch.isfinite(T).all()),
+            "us_per_iteration": us_it,
+            "cycle": {k: info[k] for k in ("mg_levels", "mg_persistent", "mg_tail_level", "mg_fused_level",
+                                           "kernels_per_iter", "tail_ms_10_cycles", "fused_ms_10_cycles",
+                                           "persistent_ms_10_cycles", "level_rows", "level_entries")},
+            "roofline": {"bound": "latency", "unit": "GB/s",
+                         "note": "per Krylov iteration (two V(2,2)-cycles, two operator applications, the "
+                                 "vector updates): algorithmic bytes and FP64 flops from the level sizes, over "
+                                 "ms_per_step / krylov_iters_per_step (the step's other kernels included); the "
+                                 "working set (%.0f MB) stays in L2, so neither HBM nor the FP64 pipe bounds it"
+                                 % (wk["working_set_bytes"] / 1e6),
+                         "bytes_per_iteration": wk["bytes"], "flops_per_iteration": wk["flops"],
+                         "achieved": wk["bytes"] / (us_it * 1e3), "peak": peak_h, "peak_source": src_h,
+                         "frac": wk["bytes"] / (us_it * 1e3) / peak_h,
+                         "fp64_gflops": wk["flops"] / (us_it * 1e3)}}
+
+
+def krylov_iteration_work(info, N):
+    """Algorithmic work of one BiCGSTAB iteration with the multigrid
+    preconditioner, from the rows R and stored matrix entries Z of each
+    level (12 bytes per entry: a 4-byte column and an 8-byte value; 8 bytes
+    per vector element read or written).  Per non-coarsest level and cycle:
+    pre-smoothing 12Z + 24R bytes, 3Z + 3R flops; restriction 12Z + 20R +
+    12Rc bytes, 2Z + 2R flops; the two post-smoothing sweeps 12Z + 36R + 8Rc
+    and 12Z + 32R bytes, 4Z + 4R and 2Z + 3R flops (Rc: rows of the next
+    level).  Coarsest level: the dense m x m solve, 8m^2 + 16m bytes, 2m^2
+    flops.  Two cycles, two applications of the fine bordered operator
+    (12Z0 + 16N bytes, 2Z0 + 2N flops each) and the vector updates and dot
+    products (20 vector passes, 160N bytes, 22N flops)."""
+    R = list(info["level_rows"])
+    Z = list(info["level_entries"])
+    L = len(R)
+    by = fl = 0.0
+    for l in range(L - 1):
+        Rc = R[l + 1]
+        by += 48 * Z[l] + 112 * R[l] + 20 * Rc
+        fl += 11 * Z[l] + 12 * R[l]
+    if L:
+        m = R[-1]
+        by += 8 * m * m + 16 * m
+        fl += 2 * m * m
+    by, fl = 2 * by, 2 * fl
+    by += 2 * (12 * Z[0] + 16 * N) + 160 * N if L else 0
+    fl += 2 * (2 * Z[0] + 2 * N) + 22 * N if L else 0
+    ws = sum(12 * z + 48 * r for z, r in zip(Z, R)) + 12 * 8 * N
+    return {"bytes": by, "flops": fl, "working_set_bytes": ws}
 
 
 def hbm_peak():
@@ -996,7 +1046,7 @@ def run_kernels(args):
         bc = torch.from_numpy(ns.bc).to(dev)
         Tbc = torch.from_numpy(ns.T_bc).to(dev)
         st = hsm.Stepper(plan, 1e6, 0.71, 0.1 * ns.h * ns.h / 2.0, ns.T_ref, bc, Tbc, nrm, krylov_tol=1e-10,
-                         krylov_max_it=4000, guess_order=args.guess_order)
+                         krylov_max_it=4000, guess_order=args.guess_order, mg_sweeps=args.mg_sweeps)
         v = torch.zeros((2, ns.N), dtype=torch.float64, device=dev)
         T = torch.where(bc == 1, Tbc, torch.zeros_like(Tbc)).contiguous()
         p = torch.zeros(ns.N, dtype=torch.float64, device=dev)
@@ -1552,6 +1602,8 @@ def main():
     ap.add_argument("--refined-steps", type=int, default=500, help="with --refined")
     ap.add_argument("--sweep", action="store_true", help="scattered-fraction sweep (5..100 %%), m = 2 and 4")
     ap.add_argument("--sweep-steps", type=int, default=100, help="with --sweep: explicit steps timed per set")
+    ap.add_argument("--mg-sweeps", type=int, default=0, help="with --kernels --stepper: 1 or 2 Jacobi sweeps "
+                    "each way in the multigrid cycle (0: the library default)")
     ap.add_argument("--guess-order", type=int, default=0, help="with --kernels --stepper: pressure initial "
                     "guess (0 quadratic extrapolation, 1 linear, -1 last solution)")
     ap.add_argument("--field-linf", type=int, default=0,

@@ -295,6 +295,15 @@ typedef struct {
                             below the tail run their smoothing and restriction,
                             and their post-smoothing, as one kernel each;
                             -1: none                                           */
+  int mg_persistent;     /* 0 = picked by timing (default); 1 = the whole cycle
+                            in one cooperative kernel, its phases separated by
+                            grid-wide barriers (mg_tail_from and mg_fused_from
+                            then do not apply); -1: never                      */
+  int mg_sweeps;         /* damped-Jacobi sweeps before and after each coarse
+                            correction: 2 (default, also 0) or 1.  With 1 the
+                            pre-sweep from zero is x = w f and each level runs
+                            two kernels per cycle (the other cycle shapes then
+                            do not apply)                                      */
 } hsm_phys;
 
 /* Right preconditioner of the pressure BiCGSTAB.  AMG: an aggregation
@@ -346,9 +355,17 @@ hsm_status hsm_step(hsm_stepper st, int n_steps, double* v, double* T, double* p
  *                    the tail from level l (tail_ms[0]: neither form), or
  *                    with the fused kernels from level l and no tail; -1
  *                    where the choice was not timed
- * Both levels are picked by timing these cycles at hsm_stepper_create.      */
+ *   mg_persistent    1 when the whole cycle runs as one cooperative kernel
+ *                    (the level choices above then do not apply)
+ *   persistent_ms    device time of 10 such cycles; -1 where not timed
+ *   level_rows, level_entries  host i64 [16] or NULL: rows of each level and
+ *                    the matrix entries its ELL storage holds (padding
+ *                    included); 0 past the last level
+ * The shape is picked by timing these cycles at hsm_stepper_create.        */
 hsm_status hsm_stepper_info(hsm_stepper st, int* mg_levels, int* mg_tail_level, int* mg_tail_ctas,
-                            int* mg_fused_level, int* kernels_per_iter, float* tail_ms, float* fused_ms);
+                            int* mg_fused_level, int* kernels_per_iter, float* tail_ms, float* fused_ms,
+                            int* mg_persistent, float* persistent_ms, int64_t* level_rows,
+                            int64_t* level_entries);
 
 hsm_status hsm_stepper_destroy(hsm_stepper st);
 

@@ -53,12 +53,21 @@ __device__ __forceinline__ void mg_locate(const MgLevel& L, int64_t r, int& g, i
     p = r;
   }
 }
-__device__ __forceinline__ double row_dot(const MgLevel& L, int g, int64_t p, const double* __restrict__ x) {
-  const int W = L.width[g];
-  const int64_t G = L.count[g];
+// sum over the W entries e of an ELL row ([W][G] column-major, position p) of
+// val[e] * t(idx[e]), accumulated with FMAs in the order e = 0, 1, ...
+// (Loading the entries eight at a time before the FMAs made the cycle slower:
+// the padding of short rows cost loads and FP64 work, and the compiler
+// already overlaps the loads of this loop.)
+template <class TF>
+__device__ __forceinline__ double ell_dot(const int32_t* __restrict__ idx, const double* __restrict__ val,
+                                          int64_t G, int64_t p, int W, TF term) {
   double s = 0.0;
-  for (int e = 0; e < W; ++e) s = fma(L.val[g][(int64_t)e * G + p], x[L.idx[g][(int64_t)e * G + p]], s);
+  for (int e = 0; e < W; ++e) s = fma(val[(int64_t)e * G + p], term(idx[(int64_t)e * G + p]), s);
   return s;
+}
+
+__device__ __forceinline__ double row_dot(const MgLevel& L, int g, int64_t p, const double* __restrict__ x) {
+  return ell_dot(L.idx[g], L.val[g], L.count[g], p, L.width[g], [&](int32_t j) { return x[j]; });
 }
 
 // ---- cycle -------------------------------------------------------------------
@@ -72,11 +81,7 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_pre(MgLevel L, const double* 
   const int64_t G = L.count[g];
   for (; p < G; p += stride) {
     const int64_t i = mg_row_id(L, g, p);
-    double acc = 0.0;
-    for (int e = 0; e < W; ++e) {
-      const int32_t j = L.idx[g][(int64_t)e * G + p];
-      acc = fma(L.val[g][(int64_t)e * G + p], L.odinv[j] * f[j], acc);
-    }
+    const double acc = ell_dot(L.idx[g], L.val[g], G, p, W, [&](int32_t j) { return L.odinv[j] * f[j]; });
     const double fi = f[i], di = L.odinv[i];
     L.x[i] = di * fi + di * (fi - acc);
   }
@@ -120,11 +125,8 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_post1(MgLevel L, const double
   const int64_t G = L.count[g];
   for (; p < G; p += stride) {
     const int64_t i = mg_row_id(L, g, p);
-    double acc = 0.0;
-    for (int e = 0; e < W; ++e) {
-      const int32_t j = L.idx[g][(int64_t)e * G + p];
-      acc = fma(L.val[g][(int64_t)e * G + p], fma(alpha, xc[L.agg[j]], L.x[j]), acc);
-    }
+    const double acc =
+        ell_dot(L.idx[g], L.val[g], G, p, W, [&](int32_t j) { return fma(alpha, xc[L.agg[j]], L.x[j]); });
     const double xi = fma(alpha, xc[L.agg[i]], L.x[i]);
     L.y[i] = fma(L.odinv[i], f[i] - acc, xi);
   }
@@ -162,6 +164,52 @@ __global__ void __launch_bounds__(kMgThreads) k_mg_coarse(const double* __restri
   if (border >= 0 && blockIdx.x == 0 && threadIdx.x == 0) x[border] = f[border];
 }
 
+// ---- V(1,1): one sweep each way ------------------------------------------------
+// Pre-smoothing from zero is x = w f, with no gather; the down phase stores
+// it and restricts the residual: fc[I] = sum over the rows r of I of
+// (f - A w f)_r (fixed order).
+__global__ void __launch_bounds__(kMgThreads) k_mg_restrict1(MgLevel L, const double* __restrict__ f,
+                                                             double* __restrict__ fc, int64_t nc,
+                                                             const double* done) {
+  if (done && *done != 0.0) return;
+  for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < nc; I += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    const int32_t m1 = L.mstart[I + 1];
+    for (int32_t m0 = L.mstart[I]; m0 < m1; ++m0) {
+      const int32_t r = L.mlist[m0];
+      int g;
+      int64_t p;
+      mg_locate(L, r, g, p);
+      const double fr = f[r];
+      L.x[r] = L.odinv[r] * fr;
+      s += fr - ell_dot(L.idx[g], L.val[g], L.count[g], p, L.width[g],
+                        [&](int32_t j) { return L.odinv[j] * f[j]; });
+    }
+    fc[I] = s;
+  }
+}
+
+// The one post-smoothing sweep: out = x' + w (f - A x'), x' = x + alpha P xc
+// (k_mg_post1's formula), written to out; on level 0 the border entry passes.
+__global__ void __launch_bounds__(kMgThreads) k_mg_post1o(MgLevel L, const double* __restrict__ f,
+                                                          const double* __restrict__ xc, double alpha,
+                                                          double* __restrict__ out, int border, const double* done) {
+  if (done && *done != 0.0) return;
+  int g;
+  int64_t p, stride;
+  mg_rows(L, g, p, stride);
+  const int W = L.width[g];
+  const int64_t G = L.count[g];
+  for (; p < G; p += stride) {
+    const int64_t i = mg_row_id(L, g, p);
+    const double acc =
+        ell_dot(L.idx[g], L.val[g], G, p, W, [&](int32_t j) { return fma(alpha, xc[L.agg[j]], L.x[j]); });
+    const double xi = fma(alpha, xc[L.agg[i]], L.x[i]);
+    out[i] = fma(L.odinv[i], f[i] - acc, xi);
+  }
+  if (border && blockIdx.x == 0 && threadIdx.x == 0) out[L.n] = f[L.n];
+}
+
 // ---- fused forms: two phases of a level in one kernel -------------------------
 // On the small levels a kernel is one chain of dependent L2 loads and costs a
 // launch; the fused forms recompute the first phase's values at a row's
@@ -171,13 +219,8 @@ __device__ __forceinline__ double pre_x(const MgLevel& L, const double* __restri
   int g;
   int64_t p;
   mg_locate(L, j, g, p);
-  const int W = L.width[g];
-  const int64_t G = L.count[g];
-  double acc = 0.0;
-  for (int e = 0; e < W; ++e) {
-    const int32_t k = L.idx[g][(int64_t)e * G + p];
-    acc = fma(L.val[g][(int64_t)e * G + p], L.odinv[k] * f[k], acc);
-  }
+  const double acc =
+      ell_dot(L.idx[g], L.val[g], L.count[g], p, L.width[g], [&](int32_t k) { return L.odinv[k] * f[k]; });
   const double fj = f[j], dj = L.odinv[j];
   return dj * fj + dj * (fj - acc);
 }
@@ -220,13 +263,8 @@ __device__ __forceinline__ double post1_y(const MgLevel& L, const double* __rest
   int g;
   int64_t p;
   mg_locate(L, j, g, p);
-  const int W = L.width[g];
-  const int64_t G = L.count[g];
-  double acc = 0.0;
-  for (int e = 0; e < W; ++e) {
-    const int32_t k = L.idx[g][(int64_t)e * G + p];
-    acc = fma(L.val[g][(int64_t)e * G + p], fma(alpha, xc[L.agg[k]], L.x[k]), acc);
-  }
+  const double acc = ell_dot(L.idx[g], L.val[g], L.count[g], p, L.width[g],
+                             [&](int32_t k) { return fma(alpha, xc[L.agg[k]], L.x[k]); });
   const double xj = fma(alpha, xc[L.agg[j]], L.x[j]);
   return fma(L.odinv[j], f[j] - acc, xj);
 }
@@ -286,11 +324,7 @@ __device__ __forceinline__ unsigned cluster_size() {
   return r;
 }
 __device__ __forceinline__ double row_dot_cg(const MgLevel& L, int64_t p, const double* x) {
-  const int W = L.width[0];
-  const int64_t G = L.count[0];
-  double s = 0.0;
-  for (int e = 0; e < W; ++e) s = fma(L.val[0][(int64_t)e * G + p], __ldcg(x + L.idx[0][(int64_t)e * G + p]), s);
-  return s;
+  return ell_dot(L.idx[0], L.val[0], L.count[0], p, L.width[0], [&](int32_t j) { return __ldcg(x + j); });
 }
 
 __global__ void __launch_bounds__(1024, 1) k_mg_tail(const MgLevel* __restrict__ lev, int lt, int L,
@@ -303,13 +337,8 @@ __global__ void __launch_bounds__(1024, 1) k_mg_tail(const MgLevel* __restrict__
     const MgLevel F = lev[l];
     // x = w f + w (f - A w f)
     for (int64_t i = t0; i < F.n; i += T) {
-      const int W = F.width[0];
-      const int64_t G = F.count[0];
-      double acc = 0.0;
-      for (int e = 0; e < W; ++e) {
-        const int32_t j = F.idx[0][(int64_t)e * G + i];
-        acc = fma(F.val[0][(int64_t)e * G + i], F.odinv[j] * __ldcg(F.f + j), acc);
-      }
+      const double acc = ell_dot(F.idx[0], F.val[0], F.count[0], i, F.width[0],
+                                 [&](int32_t j) { return F.odinv[j] * __ldcg(F.f + j); });
       const double fi = __ldcg(F.f + i), di = F.odinv[i];
       __stcg(F.x + i, di * fi + di * (fi - acc));
     }
@@ -345,15 +374,11 @@ __global__ void __launch_bounds__(1024, 1) k_mg_tail(const MgLevel* __restrict__
   for (int l = L - 2; l >= lt; --l) {
     const MgLevel F = lev[l];
     const double* xc = lev[l + 1].x;
-    const int W = F.width[0];
-    const int64_t G = F.count[0];
     // y = x' + w (f - A x'), x' = x + alpha P xc
     for (int64_t i = t0; i < F.n; i += T) {
-      double acc = 0.0;
-      for (int e = 0; e < W; ++e) {
-        const int32_t j = F.idx[0][(int64_t)e * G + i];
-        acc = fma(F.val[0][(int64_t)e * G + i], fma(alpha, __ldcg(xc + F.agg[j]), __ldcg(F.x + j)), acc);
-      }
+      const double acc = ell_dot(F.idx[0], F.val[0], F.count[0], i, F.width[0], [&](int32_t j) {
+        return fma(alpha, __ldcg(xc + F.agg[j]), __ldcg(F.x + j));
+      });
       const double xi = fma(alpha, __ldcg(xc + F.agg[i]), __ldcg(F.x + i));
       __stcg(F.y + i, fma(F.odinv[i], __ldcg(F.f + i) - acc, xi));
     }
@@ -363,6 +388,186 @@ __global__ void __launch_bounds__(1024, 1) k_mg_tail(const MgLevel* __restrict__
       __stcg(F.x + i, fma(F.odinv[i], __ldcg(F.f + i) - row_dot_cg(F, i, F.y), __ldcg(F.y + i)));
     cluster_sync_all();
   }
+}
+
+// ---- the whole cycle in one cooperative kernel -------------------------------
+// Every phase of the V-cycle -- pre-smoothing and restriction of each level
+// on the way down, the dense coarsest solve, the two post-smoothing sweeps of
+// each level on the way up -- runs in one launch whose blocks are all
+// resident at once (cooperative launch), separated by a grid-wide barrier
+// instead of a kernel boundary.  Each phase computes what the per-level
+// kernel of the same name computes, row by row and in the same term order.
+// Vectors written inside the kernel are read and written through L2
+// (ld/st.global.cg), so no stale L1 line of another SM is read after a
+// barrier; the cycle's input and the matrices go through L1.
+//
+// The barrier: each block's thread 0 reads the generation, publishes the
+// block's writes (they are ordered before it by __syncthreads, and the
+// device-scope fence is cumulative) and arrives on the counter; the last
+// arrival resets the counter and advances the generation, the others wait
+// for the generation to move.  The wait is bounded: after kMgBarrierSpins
+// polls it sets the timeout flag and goes on, so the kernel always ends (its
+// results are then void and the caller reports HSM_ETIMEOUT).
+constexpr long kMgBarrierSpins = 1L << 20;
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void grid_barrier(unsigned* bar) {
+  __syncthreads();
+  // once a barrier has timed out the cycle is void: the later ones do not wait
+  if (threadIdx.x == 0 && ld_acquire_u32(bar + 2) == 0u) {
+    const unsigned gen = ld_acquire_u32(bar + 1);
+    __threadfence();
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long spins = 0;
+      while (ld_acquire_u32(bar + 1) == gen) {
+        if (++spins > kMgBarrierSpins || ld_acquire_u32(bar + 2) != 0u) {
+          atomicOr(bar + 2, 1u);
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+struct CycleArgs {
+  const MgLevel* lev;  // device copy of the levels
+  int L;
+  const double* binv;
+  int m;
+  double alpha;
+  const double* in;
+  double* out;
+  const double* done;
+  unsigned* bar;
+};
+
+// a vector of the cycle: the input through L1, the kernel's own through L2
+__device__ __forceinline__ double vld(const double* p, bool own) { return own ? __ldcg(p) : *p; }
+
+__device__ __forceinline__ double row_dot_own(const MgLevel& L, int g, int64_t p, const double* x) {
+  return ell_dot(L.idx[g], L.val[g], L.count[g], p, L.width[g], [&](int32_t j) { return __ldcg(x + j); });
+}
+
+// rows of a level, both groups as one range
+__device__ __forceinline__ void cyc_row(const MgLevel& F, int64_t q, int& g, int64_t& p, int64_t& i) {
+  g = q < F.count[0] ? 0 : 1;
+  p = g ? q - F.count[0] : q;
+  i = F.nodes[g] ? (int64_t)F.nodes[g][p] : p;
+}
+
+// k_mg_pre
+__device__ void cyc_pre(const MgLevel& F, const double* f, bool own, int64_t t0, int64_t T) {
+  const int64_t R = F.count[0] + F.count[1];
+  for (int64_t q = t0; q < R; q += T) {
+    int g;
+    int64_t p, i;
+    cyc_row(F, q, g, p, i);
+    const double acc = ell_dot(F.idx[g], F.val[g], F.count[g], p, F.width[g],
+                               [&](int32_t j) { return F.odinv[j] * vld(f + j, own); });
+    const double fi = vld(f + i, own), di = F.odinv[i];
+    __stcg(F.x + i, di * fi + di * (fi - acc));
+  }
+}
+
+// k_mg_restrict
+__device__ void cyc_restrict(const MgLevel& F, const double* f, bool own, double* fc, int64_t nc, int64_t t0,
+                             int64_t T) {
+  constexpr int kBatch = 8;
+  for (int64_t I = t0; I < nc; I += T) {
+    double s = 0.0;
+    const int32_t m1 = F.mstart[I + 1];
+    for (int32_t m0 = F.mstart[I]; m0 < m1; m0 += kBatch) {
+      int32_t r[kBatch], g[kBatch];
+      int64_t pp[kBatch];
+#pragma unroll
+      for (int k = 0; k < kBatch; ++k) r[k] = m0 + k < m1 ? F.mlist[m0 + k] : -1;
+#pragma unroll
+      for (int k = 0; k < kBatch; ++k)
+        if (r[k] >= 0) mg_locate(F, r[k], g[k], pp[k]);
+#pragma unroll
+      for (int k = 0; k < kBatch; ++k)
+        if (r[k] >= 0) s += vld(f + r[k], own) - row_dot_own(F, g[k], pp[k], F.x);
+    }
+    __stcg(fc + I, s);
+  }
+}
+
+// k_mg_coarse (one warp per row)
+__device__ void cyc_coarse(const MgLevel& C, const double* binv, int m, int64_t t0, int64_t T) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t r = t0 >> 5; r < m; r += T >> 5) {
+    double s = 0.0;
+    for (int c = lane; c < m; c += 32) s = fma(binv[r * m + c], __ldcg(C.f + c), s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) __stcg(C.x + r, s);
+  }
+}
+
+// k_mg_post1
+__device__ void cyc_post1(const MgLevel& F, const double* f, bool own, const double* xc, double alpha, int64_t t0,
+                          int64_t T) {
+  const int64_t R = F.count[0] + F.count[1];
+  for (int64_t q = t0; q < R; q += T) {
+    int g;
+    int64_t p, i;
+    cyc_row(F, q, g, p, i);
+    const double acc = ell_dot(F.idx[g], F.val[g], F.count[g], p, F.width[g], [&](int32_t j) {
+      return fma(alpha, __ldcg(xc + F.agg[j]), __ldcg(F.x + j));
+    });
+    const double xi = fma(alpha, __ldcg(xc + F.agg[i]), __ldcg(F.x + i));
+    __stcg(F.y + i, fma(F.odinv[i], vld(f + i, own) - acc, xi));
+  }
+}
+
+// k_mg_post2
+__device__ void cyc_post2(const MgLevel& F, const double* f, bool own, double* out, int64_t t0, int64_t T) {
+  const int64_t R = F.count[0] + F.count[1];
+  for (int64_t q = t0; q < R; q += T) {
+    int g;
+    int64_t p, i;
+    cyc_row(F, q, g, p, i);
+    __stcg(out + i, fma(F.odinv[i], vld(f + i, own) - row_dot_own(F, g, p, F.y), __ldcg(F.y + i)));
+  }
+}
+
+__global__ void __launch_bounds__(kMgCycleThreads) k_mg_cycle(CycleArgs a) {
+  if (a.done && *a.done != 0.0) return;  // the same value for every block
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t T = (int64_t)gridDim.x * blockDim.x;
+  const int L = a.L;
+  for (int l = 0; l + 1 < L; ++l) {
+    const MgLevel& F = a.lev[l];
+    const double* f = l == 0 ? a.in : F.f;
+    cyc_pre(F, f, l > 0, t0, T);
+    grid_barrier(a.bar);
+    cyc_restrict(F, f, l > 0, a.lev[l + 1].f, a.lev[l + 1].n, t0, T);
+    grid_barrier(a.bar);
+  }
+  cyc_coarse(a.lev[L - 1], a.binv, a.m, t0, T);
+  grid_barrier(a.bar);
+  for (int l = L - 2; l >= 0; --l) {
+    const MgLevel& F = a.lev[l];
+    const double* f = l == 0 ? a.in : F.f;
+    cyc_post1(F, f, l > 0, a.lev[l + 1].x, a.alpha, t0, T);
+    grid_barrier(a.bar);
+    cyc_post2(F, f, l > 0, l == 0 ? a.out : F.x, t0, T);
+    if (l > 0) grid_barrier(a.bar);
+  }
+  // the border entry of the bordered system passes through
+  if (t0 == 0) a.out[a.lev[0].n] = a.in[a.lev[0].n];
 }
 
 // ---- set-up ------------------------------------------------------------------
@@ -811,6 +1016,25 @@ static cudaError_t vcycle_lt(const Amg& A, int lt, int lf, const double* in, dou
     k_mg_coarse<<<cg, kMgThreads, 0, s>>>(A.binv, A.m, in, out, A.lev[0].n, done);
     return cudaGetLastError();
   }
+  if (A.nu == 1) {
+    // V(1,1): two kernels per level
+    const double* f = in;
+    for (int l = 0; l + 1 < A.L; ++l) {
+      const MgLevel& F = A.lev[l];
+      k_mg_restrict1<<<F.cblocks, kMgThreads, 0, s>>>(F, f, A.lev[l + 1].f, A.lev[l + 1].n, done);
+      f = A.lev[l + 1].f;
+    }
+    const MgLevel& Cs = A.lev[A.L - 1];
+    k_mg_coarse<<<cg, kMgThreads, 0, s>>>(A.binv, A.m, Cs.f, Cs.x, -1, done);
+    const double* xc = Cs.x;
+    for (int l = A.L - 2; l >= 0; --l) {
+      const MgLevel& F = A.lev[l];
+      double* res = l == 0 ? out : F.y;
+      k_mg_post1o<<<F.blocks, kMgThreads, 0, s>>>(F, l == 0 ? in : F.f, xc, A.alpha, res, l == 0 ? 1 : 0, done);
+      xc = res;
+    }
+    return cudaGetLastError();
+  }
   const int stop = lt > 0 ? lt : A.L - 1;  // first level not handled by per-level kernels
   const double* f = in;
   for (int l = 0; l < stop; ++l) {
@@ -849,24 +1073,57 @@ static cudaError_t vcycle_lt(const Amg& A, int lt, int lf, const double* in, dou
   return cudaGetLastError();
 }
 
+static cudaError_t launch_cycle(const Amg& A, const double* in, double* out, const double* done, cudaStream_t s) {
+  CycleArgs a{A.dlev, A.L, A.binv, A.m, A.alpha, in, out, done, A.gbar};
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.gridDim = dim3((unsigned)A.pblocks);
+  cfg.blockDim = dim3(kMgCycleThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_mg_cycle, a);
+}
+
 cudaError_t amg_vcycle(const Amg& A, const double* in, double* out, const double* done, cudaStream_t s) {
+  if (A.persist) return launch_cycle(A, in, out, done, s);
   return vcycle_lt(A, A.lt, A.lf, in, out, done, s);
 }
 
+cudaError_t amg_reset_barrier(const Amg& A, cudaStream_t s) {
+  if (!A.gbar) return cudaSuccess;
+  return cudaMemsetAsync(A.gbar, 0, 4 * sizeof(unsigned), s);
+}
+
+const unsigned* amg_timeout_flag(const Amg& A) { return A.persist && A.gbar ? A.gbar + 2 : nullptr; }
+
 int amg_kernels_per_cycle(const Amg& A) {
   if (A.L == 1) return 1;
+  if (A.persist) return 1;
+  if (A.nu == 1) return 2 * (A.L - 1) + 1;
   const int stop = A.lt > 0 ? A.lt : A.L - 1;
   int k = 1;
   for (int l = 0; l < stop; ++l) k += l >= A.lf ? 2 : 4;
   return k;
 }
 
-hsm_status amg_tune_tail(hsm_plan pl, Amg* A, int tail_from, int fused_from) {
+hsm_status amg_tune_tail(hsm_plan pl, Amg* A, int tail_from, int fused_from, int persistent) {
   cudaStream_t s = pl->stream;
   A->lt = 0;
   A->lf = A->L;
+  A->persist = 0;
+  A->persist_ms = -1.f;
   for (int l = 0; l < kMgMaxLevels; ++l) A->tail_ms[l] = A->fuse_ms[l] = -1.f;
   if (A->L < 2) return HSM_OK;
+  if (A->nu == 1) {
+    // V(1,1) has one shape (two kernels per level)
+    if (tail_from > 0 || fused_from > 0 || persistent > 0)
+      return set_error(pl, HSM_EINVAL, "the cycle shapes apply to V(2,2) only (mg_sweeps = 2)");
+    return HSM_OK;
+  }
   // the largest cluster the device schedules with 1024-thread CTAs
   int ctas = 0;
   for (int cl : {16, 8}) {
@@ -895,10 +1152,24 @@ hsm_status amg_tune_tail(hsm_plan pl, Amg* A, int tail_from, int fused_from) {
     }
   }
   A->tail_ctas = ctas;
-  if (ctas) {
+  // every block of the cooperative cycle resident at once
+  int dev = 0, coop = 0, per_sm = 0;
+  HSM_CUDA(pl, cudaGetDevice(&dev));
+  HSM_CUDA(pl, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  if (coop && persistent >= 0 &&
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mg_cycle, kMgCycleThreads, 0) == cudaSuccess &&
+      per_sm >= 1)
+    A->pblocks = num_sms() * std::min(per_sm, 2);
+  else
+    A->pblocks = 0;
+  cudaGetLastError();
+  if (persistent > 0 && A->pblocks == 0)
+    return set_error(pl, HSM_EINVAL, "the cooperative multigrid cycle cannot be launched on this device");
+  if (ctas || A->pblocks) {
     HSM_CUDA(pl, dev_alloc(&A->dlev, A->L, s));
     HSM_CUDA(pl, cudaMemcpyAsync(A->dlev, A->lev, A->L * sizeof(MgLevel), cudaMemcpyHostToDevice, s));
   }
+  if (A->pblocks) HSM_CUDA(pl, dev_alloc(&A->gbar, 4, s));
   // time each choice of the first tail level on zero vectors
   const int64_t N1 = A->lev[0].n + 1;
   double *in = nullptr, *out = nullptr, *done = nullptr;
@@ -938,15 +1209,48 @@ hsm_status amg_tune_tail(hsm_plan pl, Amg* A, int tail_from, int fused_from) {
       }
     }
   }
+  // the cooperative cycle, against the best of the shapes above
+  bool use_persist = false;
+  if (ce == cudaSuccess && A->pblocks) {
+    Amg P = *A;
+    P.persist = 1;
+    float ms = 0.f;
+    unsigned flag = 0;
+    ce = amg_reset_barrier(P, s);
+    for (int rep = 0; rep < 2 && ce == cudaSuccess; ++rep) {
+      ce = cudaEventRecord(e0, s);
+      for (int k = 0; k < 10 && ce == cudaSuccess; ++k) ce = launch_cycle(P, in, out, done, s);
+      if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
+      if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+      if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+    }
+    if (ce == cudaSuccess) ce = cudaMemcpy(&flag, A->gbar + 2, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    if (ce == cudaSuccess) ce = amg_reset_barrier(P, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (ce == cudaSuccess && flag == 0) {
+      A->persist_ms = ms;
+      use_persist = persistent > 0 || (persistent == 0 && tail_from == 0 && fused_from == 0 && ms < best);
+    }
+    if (ce == cudaSuccess && flag != 0 && persistent > 0) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      dev_free(&in, s);
+      dev_free(&out, s);
+      dev_free(&done, s);
+      return set_error(pl, HSM_ETIMEOUT, "a grid barrier of the cooperative multigrid cycle timed out");
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   dev_free(&in, s);
   dev_free(&out, s);
   dev_free(&done, s);
   if (ce != cudaSuccess) return cuda_fail(pl, ce, "multigrid cycle timing");
-  if (best >= 1e30f) return set_error(pl, HSM_EINVAL, "the requested multigrid cycle shape is not available");
+  if (best >= 1e30f && !use_persist)
+    return set_error(pl, HSM_EINVAL, "the requested multigrid cycle shape is not available");
   A->lt = best_lt;
   A->lf = best_lf;
+  A->persist = use_persist ? 1 : 0;
   return HSM_OK;
 }
 
@@ -965,6 +1269,7 @@ void amg_free(Amg* A, cudaStream_t s) {
   }
   dev_free(&A->binv, s);
   dev_free(&A->dlev, s);
+  dev_free(&A->gbar, s);
   A->L = 0;
   A->lt = 0;
   A->lf = kMgMaxLevels;

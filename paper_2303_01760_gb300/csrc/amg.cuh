@@ -44,6 +44,7 @@ struct Amg {
   int m = 0;
   double omega = 2.0 / 3.0;  // Jacobi damping
   double alpha = 1.8;        // scaling of the coarse-grid correction
+  int nu = 2;                // Jacobi sweeps before and after the coarse correction (2 or 1)
   // levels lt..L-1 of a cycle run in one cluster kernel (k_mg_tail); lt = 0:
   // every level has its own kernels.  lt is picked at set-up by timing.
   int lt = 0;
@@ -54,7 +55,17 @@ struct Amg {
   int lf = kMgMaxLevels;
   float fuse_ms[kMgMaxLevels] = {};  // 10 cycles, no tail, fused from level l; -1 not tried
   MgLevel* dlev = nullptr;       // device copy of lev[0..L)
+  // persist = 1: the whole cycle runs as one cooperative kernel (k_mg_cycle)
+  // of pblocks x kMgCycleThreads threads, its phases separated by a
+  // grid-wide barrier on gbar ([0] arrivals, [1] generation, [2] timeout
+  // flag).  Picked by timing against the best of the shapes above.
+  int persist = 0;
+  int pblocks = 0;
+  unsigned* gbar = nullptr;
+  float persist_ms = -1.f;        // 10 cycles of k_mg_cycle; -1 not tried
 };
+
+constexpr int kMgCycleThreads = 512;
 
 // Builds the hierarchy of the pressure operator whose rows are the plan's
 // stencils with weights wp_mon ([mon.width][mon.count]) and wp_rbf
@@ -69,8 +80,14 @@ int amg_kernels_per_cycle(const Amg& amg);
 // Picks the first level of the cluster tail (or none) and the first level of
 // the fused down/up kernels (or none) by timing a few cycles of each choice
 // on scratch vectors of N + 1 entries.  Synchronises.
-// tail_from / fused_from as hsm_phys.mg_tail_from / mg_fused_from (0: time).
-hsm_status amg_tune_tail(hsm_plan pl, Amg* amg, int tail_from, int fused_from);
+// tail_from / fused_from / persistent as hsm_phys.mg_tail_from /
+// mg_fused_from / mg_persistent (0: time).
+hsm_status amg_tune_tail(hsm_plan pl, Amg* amg, int tail_from, int fused_from, int persistent);
+// Clears the grid barrier of the cooperative cycle (arrivals, generation,
+// timeout flag); enqueued on s.  No-op for the other shapes.
+cudaError_t amg_reset_barrier(const Amg& amg, cudaStream_t s);
+// Device address of the barrier's timeout flag (nullptr for the other shapes).
+const unsigned* amg_timeout_flag(const Amg& amg);
 void amg_free(Amg* amg, cudaStream_t s);
 
 }  // namespace hsm

@@ -1019,6 +1019,10 @@ hsm_status run_steps(hsm_stepper st, int n_steps, double* v, double* T, double* 
   // solve could not then reach its relative tolerance.  Each call starts c
   // at zero; within a call every solve is warm-started from the last.
   HSM_CUDA(pl, cudaMemsetAsync(reinterpret_cast<char*>(st->scal) + offsetof(KS, xN), 0, sizeof(double), s));
+  // the grid barrier of the cooperative multigrid cycle starts each call clear
+  const unsigned* tflag = st->amg ? amg_timeout_flag(*st->amg) : nullptr;
+  unsigned timed_out = 0;
+  if (st->amg) HSM_CUDA(pl, amg_reset_barrier(*st->amg, s));
   if (!st->g_chunk) HSM_CUDA(pl, capture(cs, &st->g_chunk, [&] { launch_chunk<DIM>(st, a, grid, blk, cs); }));
   if (!st->g_tail)
     HSM_CUDA(pl, capture(cs, &st->g_tail, [&] {
@@ -1061,7 +1065,9 @@ hsm_status run_steps(hsm_stepper st, int n_steps, double* v, double* T, double* 
       HSM_CUDA(pl, cudaMemcpyAsync(bad_h.data(), st->step_bad, n_steps * sizeof(int), cudaMemcpyDeviceToHost, s));
     }
     HSM_CUDA(pl, cudaMemcpyAsync(ctl_h, st->ctl, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    if (tflag) HSM_CUDA(pl, cudaMemcpyAsync(&timed_out, tflag, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     HSM_CUDA(pl, cudaStreamSynchronize(s));
+    if (timed_out) return set_error(pl, HSM_ETIMEOUT, "a grid barrier of the multigrid cycle timed out");
     for (int it = 0; it < n_steps; ++it) {
       if (iters) iters[it] = it_h[it];
       if (bad_h[it]) *notconv = true;
@@ -1103,7 +1109,9 @@ hsm_status run_steps(hsm_stepper st, int n_steps, double* v, double* T, double* 
     HSM_CUDA(pl, cudaGraphLaunch(st->g_tail, s));
     pl->launches += 2;
   }
+  if (tflag) HSM_CUDA(pl, cudaMemcpyAsync(&timed_out, tflag, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   HSM_CUDA(pl, cudaStreamSynchronize(s));
+  if (timed_out) return set_error(pl, HSM_ETIMEOUT, "a grid barrier of the multigrid cycle timed out");
   return HSM_OK;
 }
 
@@ -1128,6 +1136,9 @@ hsm_status hsm_stepper_create(hsm_stepper* out, hsm_plan pl, const hsm_phys* phy
   if (phys->apply_f32 != 0 && phys->apply_f32 != 1) return set_error(pl, HSM_EINVAL, "apply_f32 must be 0 or 1");
   if (phys->mg_tail_from < -1 || phys->mg_fused_from < -1)
     return set_error(pl, HSM_EINVAL, "mg_tail_from and mg_fused_from must be >= -1");
+  if (phys->mg_persistent < -1 || phys->mg_persistent > 1)
+    return set_error(pl, HSM_EINVAL, "mg_persistent must be -1, 0 or 1");
+  if (phys->mg_sweeps < 0 || phys->mg_sweeps > 2) return set_error(pl, HSM_EINVAL, "mg_sweeps must be 0, 1 or 2");
   if (phys->precond != HSM_PRECOND_AMG && phys->precond != HSM_PRECOND_JACOBI)
     return set_error(pl, HSM_EINVAL, "unknown preconditioner");
   if (phys->apply_f32 && (!pl->mon.w32 || !pl->rbf.w32)) {
@@ -1200,7 +1211,10 @@ hsm_status hsm_stepper_create(hsm_stepper* out, hsm_plan pl, const hsm_phys* phy
       if (!st->amg) return fail(set_error(pl, HSM_ENOMEM, "host allocation failed"));
       // over-correction of the coarse-grid step (2^d nodes per aggregate)
       hsm_status as = amg_setup(pl, a.wp[0], a.wp[1], pl->dim == 2 ? 1.8 : 1.5, st->amg);
-      if (as == HSM_OK) as = amg_tune_tail(pl, st->amg, phys->mg_tail_from, phys->mg_fused_from);
+      if (as == HSM_OK) {
+        st->amg->nu = phys->mg_sweeps == 1 ? 1 : 2;
+        as = amg_tune_tail(pl, st->amg, phys->mg_tail_from, phys->mg_fused_from, phys->mg_persistent);
+      }
       if (as != HSM_OK) return fail(as);
     }
   }
@@ -1222,8 +1236,19 @@ hsm_status hsm_step(hsm_stepper st, int n_steps, double* v, double* T, double* p
 }
 
 hsm_status hsm_stepper_info(hsm_stepper st, int* mg_levels, int* mg_tail_level, int* mg_tail_ctas,
-                            int* mg_fused_level, int* kernels_per_iter, float* tail_ms, float* fused_ms) {
+                            int* mg_fused_level, int* kernels_per_iter, float* tail_ms, float* fused_ms,
+                            int* mg_persistent, float* persistent_ms, int64_t* level_rows,
+                            int64_t* level_entries) {
   if (!st) return set_error(nullptr, HSM_EINVAL, "stepper is NULL");
+  for (int l = 0; l < kMgMaxLevels; ++l) {
+    const bool in = st->amg && l < st->amg->L;
+    const MgLevel* F = in ? &st->amg->lev[l] : nullptr;
+    if (level_rows) level_rows[l] = in ? F->n : 0;
+    if (level_entries)
+      level_entries[l] = in ? F->count[0] * (int64_t)F->width[0] + F->count[1] * (int64_t)F->width[1] : 0;
+  }
+  if (mg_persistent) *mg_persistent = st->amg ? st->amg->persist : 0;
+  if (persistent_ms) *persistent_ms = st->amg ? st->amg->persist_ms : -1.f;
   if (mg_levels) *mg_levels = st->amg ? st->amg->L : 0;
   if (mg_tail_level) *mg_tail_level = st->amg ? st->amg->lt : 0;
   if (mg_tail_ctas) *mg_tail_ctas = st->amg ? st->amg->tail_ctas : 0;

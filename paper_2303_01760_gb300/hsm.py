@@ -37,7 +37,8 @@ class hsm_phys(C.Structure):
     _fields_ = [("Ra", C.c_double), ("Pr", C.c_double), ("dt", C.c_double), ("T_ref", C.c_double),
                 ("bc", _p), ("T_bc", _p), ("normals", _p), ("krylov_tol", C.c_double),
                 ("krylov_max_it", C.c_int), ("precond", C.c_int), ("guess_order", C.c_int),
-                ("apply_f32", C.c_int), ("mg_tail_from", C.c_int), ("mg_fused_from", C.c_int)]
+                ("apply_f32", C.c_int), ("mg_tail_from", C.c_int), ("mg_fused_from", C.c_int),
+                ("mg_persistent", C.c_int), ("mg_sweeps", C.c_int)]
 
 
 (HSM_OK, HSM_EINVAL, HSM_ENOMEM, HSM_ECUDA, HSM_ESINGULAR, HSM_ENOTCONV, HSM_ETIMEOUT, HSM_EBOUNDS,
@@ -73,7 +74,8 @@ _SIGS = {
     "hsm_step": (C.c_int, [_p, C.c_int, _p, _p, _p, C.POINTER(C.c_int)]),
     "hsm_stepper_destroy": (C.c_int, [_p]),
     "hsm_stepper_info": (C.c_int, [_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
-                                   C.POINTER(C.c_int), C.POINTER(C.c_int), _p, _p]),
+                                   C.POINTER(C.c_int), C.POINTER(C.c_int), _p, _p, C.POINTER(C.c_int),
+                                   C.POINTER(C.c_float), _p, _p]),
     "hsm_rbf_weights_fp32r_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_uint, _p, _i64, _p, _i64, _p, _p,
                                                 _p]),
     "hsm_mlp_create": (C.c_int, [C.POINTER(_p), C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint64, _p]),
@@ -393,24 +395,30 @@ class Stepper:
     """Owns an hsm_stepper on a plan (Section 3 explicit Boussinesq step)."""
 
     def __init__(self, plan, Ra, Pr, dt, T_ref, bc, T_bc, normals, krylov_tol=1e-12, krylov_max_it=2000,
-                 precond=HSM_PRECOND_AMG, guess_order=0, apply_f32=False, mg_tail_from=0, mg_fused_from=0):
+                 precond=HSM_PRECOND_AMG, guess_order=0, apply_f32=False, mg_tail_from=0, mg_fused_from=0,
+                 mg_persistent=0, mg_sweeps=0):
         self.plan = plan
         self._keep = (bc, T_bc, normals)
         self.phys = hsm_phys(float(Ra), float(Pr), float(dt), float(T_ref), ptr(bc).value, ptr(T_bc).value,
                              ptr(normals).value, float(krylov_tol), int(krylov_max_it), int(precond),
-                             int(guess_order), int(bool(apply_f32)), int(mg_tail_from), int(mg_fused_from))
+                             int(guess_order), int(bool(apply_f32)), int(mg_tail_from), int(mg_fused_from),
+                             int(mg_persistent), int(mg_sweeps))
         h_ = C.c_void_p()
         check(lib.hsm_stepper_create(C.byref(h_), plan.h, C.byref(self.phys)), plan.h)
         self.h = h_
 
     def info(self):
-        a, b, c, f, d = C.c_int(), C.c_int(), C.c_int(), C.c_int(), C.c_int()
-        ms, fms = (C.c_float * 16)(), (C.c_float * 16)()
-        check(lib.hsm_stepper_info(self.h, C.byref(a), C.byref(b), C.byref(c), C.byref(f), C.byref(d), ms, fms))
+        a, b, c, f, d, pe = C.c_int(), C.c_int(), C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        ms, fms, pms = (C.c_float * 16)(), (C.c_float * 16)(), C.c_float()
+        rows, ents = (C.c_int64 * 16)(), (C.c_int64 * 16)()
+        check(lib.hsm_stepper_info(self.h, C.byref(a), C.byref(b), C.byref(c), C.byref(f), C.byref(d), ms, fms,
+                                   C.byref(pe), C.byref(pms), rows, ents))
         n = max(a.value, 1)
         return dict(mg_levels=a.value, mg_tail_level=b.value, mg_tail_ctas=c.value, mg_fused_level=f.value,
                     kernels_per_iter=d.value, tail_ms_10_cycles=[round(x, 4) for x in ms[:n]],
-                    fused_ms_10_cycles=[round(x, 4) for x in fms[:n]])
+                    fused_ms_10_cycles=[round(x, 4) for x in fms[:n]], mg_persistent=pe.value,
+                    persistent_ms_10_cycles=round(pms.value, 4), level_rows=list(rows[:a.value]),
+                    level_entries=list(ents[:a.value]))
 
     def step(self, v, T, p, n_steps=1, allow_notconv=False):
         iters = (C.c_int * max(1, n_steps))()

@@ -19,3 +19,14 @@ def test_apply_bytes_per_node():
     assert per(12) == 368
     assert per(30) == 872
     assert per(12, True) == 48 + 144 + 4 + 24
+
+
+def test_krylov_iteration_work_counts():
+    """A two-level hierarchy counted by hand: level 0 with R = 10 rows and
+    Z = 50 stored entries, coarsest level m = 3 rows, N = 10 nodes."""
+    info = {"level_rows": [10, 3], "level_entries": [50, 9]}
+    w = bench.krylov_iteration_work(info, 10)
+    cycle_bytes = 48 * 50 + 112 * 10 + 20 * 3 + 8 * 9 + 16 * 3
+    cycle_flops = 11 * 50 + 12 * 10 + 2 * 9
+    assert w["bytes"] == 2 * cycle_bytes + 2 * (12 * 50 + 16 * 10) + 160 * 10
+    assert w["flops"] == 2 * cycle_flops + 2 * (2 * 50 + 2 * 10) + 22 * 10

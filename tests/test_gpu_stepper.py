@@ -96,8 +96,12 @@ def test_fp32_operator_applications_100_steps_against_the_fp64_oracle():
 def test_every_multigrid_cycle_shape_matches_oracle():
     """The multigrid cycle can run each level's phases as separate kernels,
     as fused kernels (smoothing with restriction, the two post-smoothing
-    sweeps together; neighbour values recomputed) or inside one
-    thread-block-cluster kernel for the coarse levels.  The preconditioner is
+    sweeps together; neighbour values recomputed), inside one
+    thread-block-cluster kernel for the coarse levels, or as one cooperative
+    kernel for the whole cycle (phases separated by grid barriers, the
+    per-level kernels' arithmetic in the same order: its 20 steps agree with
+    the per-level shape's to 1e-12); and V(1,1), one sweep each way, is a
+    second preconditioner for the same solve.  The preconditioner is
     the same operator either way: with each shape forced in turn, 20 steps on a
     9k-node irregular set match the oracle, and the stepper reports the shape
     it was given."""
@@ -114,22 +118,39 @@ def test_every_multigrid_cycle_shape_matches_oracle():
     plan, code, _ = make_plan(ns, m=2)
     assert code == 0
     dv = plan._dev
-    shapes = [(-1, -1), (-1, 1), (-1, 2), (2, -1), (1, 1)]
-    for tail_from, fused_from in shapes:
+    shapes = [(-1, -1, -1), (-1, 1, -1), (-1, 2, -1), (2, -1, -1), (1, 1, -1), (0, 0, 1), (0, 0, "V11")]
+    for tail_from, fused_from, persistent in shapes:
+        sweeps = 1 if persistent == "V11" else 2
+        persistent = 0 if persistent == "V11" else persistent
         stp = hsm.Stepper(plan, 1e6, 0.71, dt, ns.T_ref, dv["bc"], dv["T_bc"], dv["normals"],
                           krylov_tol=KRYLOV_TOL, krylov_max_it=4000, mg_tail_from=tail_from,
-                          mg_fused_from=fused_from)
+                          mg_fused_from=fused_from, mg_persistent=persistent, mg_sweeps=sweeps)
         info = stp.info()
         assert info["mg_levels"] >= 3
-        assert info["mg_tail_level"] == max(tail_from, 0)
-        assert info["mg_fused_level"] == (fused_from - 1 if fused_from > 0 else info["mg_levels"])
+        assert info["mg_persistent"] == max(persistent, 0)
+        if sweeps == 1:
+            # V(1,1): two kernels per level and the coarse solve, two cycles and
+            # five vector kernels per iteration
+            assert info["kernels_per_iter"] == 2 * (2 * (info["mg_levels"] - 1) + 1) + 5 + 1
+        elif persistent > 0:
+            # one cooperative kernel per cycle: 2 cycles and 5 vector kernels per iteration
+            assert info["kernels_per_iter"] == 8
+            assert info["persistent_ms_10_cycles"] > 0
+        else:
+            assert info["mg_tail_level"] == max(tail_from, 0)
+            assert info["mg_fused_level"] == (fused_from - 1 if fused_from > 0 else info["mg_levels"])
         v = torch.from_numpy(v0.copy()).cuda()
         T = torch.from_numpy(T0.copy()).cuda()
         p = torch.zeros(ns.N, dtype=torch.float64, device="cuda:0")
         stp.step(v, T, p, 20)
         eT = _rel(T.cpu().numpy(), To)
         ev = _rel(v.cpu().numpy(), vo)
-        assert eT <= 1e-9 and ev <= 1e-7, (tail_from, fused_from, eT, ev)
+        assert eT <= 1e-9 and ev <= 1e-7, (tail_from, fused_from, persistent, eT, ev)
+        if (tail_from, fused_from, persistent) == (-1, -1, -1):
+            per_level = (T.cpu().numpy(), v.cpu().numpy())
+        if persistent > 0:
+            assert _rel(T.cpu().numpy(), per_level[0]) <= 1e-12
+            assert _rel(v.cpu().numpy(), per_level[1]) <= 1e-12
         stp.close()
     plan.close()
 
