@@ -813,10 +813,17 @@ def run_learned(hsm, nodesets, dev, stream, flush, args):
     mlp = hsm.MLP(24, 256, 3, 36, seed=5, stream=stream)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    for lr, steps in ((1e-3, 6000), (3e-4, 3000), (1e-4, 3000)):
+    schedule = ((1e-3, 6000), (3e-4, 3000), (1e-4, 3000))
+    for lr, steps in schedule:
         log = mlp.train(X, Y, steps=steps, batch=4096, lr=lr, seed=int(lr * 1e7))
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t1
+    n_steps = sum(st for _, st in schedule)
+    # GEMM work of one training step with the padded layer widths (din 64,
+    # 256, 256, 256; dout 256, 256, 256, 128): forward and dW over every
+    # layer, dX over every layer but the first
+    wd = [(64, 256), (256, 256), (256, 256), (256, 128)]
+    train_flops = 2 * 4096 * (2 * sum(a * b for a, b in wd) + sum(a * b for a, b in wd[1:]))
     del X, Y
     pte = plan_of(te)
     pte.build_stencils()
@@ -865,6 +872,10 @@ def run_learned(hsm, nodesets, dev, stream, flush, args):
     mlp.close()
     return {"workload": f"train {tr.N} nodes, test {te.N} nodes (interior scattered stencils, n=12, m=2)",
             "train_s": round(t_train, 2), "final_train_loss": float(np.mean(log[-50:])),
+            "train_steps": n_steps, "train_step_ms": t_train * 1e3 / n_steps,
+            "train_gemm_tflops": train_flops * n_steps / t_train / 1e12,
+            "train_note": "batch 4096 rows; every GEMM of the step is a tcgen05 kernel (host wall clock over all "
+                          "steps, the Adam update and packing included)",
             "weights_ms": times, "rbf_weights_per_s": {k: n_rbf / (v * 1e-3) for k, v in times.items()},
             "learned_over_fp64": times["fp64"] / times["learned"],
             "learned_validated_over_fp64": times["fp64"] / times["learned_validated"],

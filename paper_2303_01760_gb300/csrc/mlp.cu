@@ -6,13 +6,15 @@
 // is the specification's predictor.
 //
 // Layers: Linear(2n -> H) GELU, (Linear(H -> H) GELU) x (L-1), Linear(H -> 3n),
-// GELU(x) = x Phi(x).  Every dense layer is a BF16 tensor-core GEMM with FP32
-// accumulation (mma.sync m16n8k16, operands staged in shared memory with
-// cp.async and read with ldmatrix), bias and activation fused into its
-// epilogue.  Master weights and Adam moments are FP32.  Dimensions are padded
-// so every GEMM is a whole number of 128 x 64 x 32 tiles: inputs to a multiple
-// of 64, hidden widths and outputs to multiples of 128, the batch to 128; the
-// padded inputs, outputs and weights stay zero.
+// GELU(x) = x Phi(x).  Every dense layer of training is a BF16 tcgen05 GEMM
+// with FP32 accumulation in tensor memory (mlp_tc.cu), bias and activation
+// fused into its epilogue; the GEMMs of the backward pass read transposed
+// copies that the forward pass and the loss write beside their outputs, so
+// both operands are always K-major.  Master weights and Adam moments are
+// FP32.  Dimensions are padded so every GEMM is a whole number of
+// 128 x 64 x 64 tiles: inputs to a multiple of 64, hidden widths and outputs
+// to multiples of 128, the batch to 128; the padded inputs, outputs and
+// weights stay zero.
 #include <cmath>
 #include <vector>
 
@@ -27,177 +29,7 @@ struct hsm_mlp_s {
 namespace hsm {
 namespace {
 
-constexpr int BM = 128, BN = 64, BK = 32, PAD = 8;
-enum { EPI_BIAS_GELU = 0, EPI_BIAS = 1, EPI_DGELU = 2, EPI_F32 = 3, EPI_BF16 = 4 };
-
-struct GemmArgs {
-  const __nv_bfloat16* A;
-  const __nv_bfloat16* B;
-  int lda, ldb;
-  int M, N, K;
-  const float* bias;       // [N]
-  const float* Zin;        // pre-activation for EPI_DGELU [M][N] (ldz = N)
-  float* Cf;               // fp32 output [M][N]
-  __nv_bfloat16* Ch;       // bf16 output [M][N]
-  float* Zout;             // pre-activation output (EPI_BIAS_GELU)
-};
-
-__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
-__device__ __forceinline__ float gelu_grad_f(float z) {
-  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
-}
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
-}
-__device__ __forceinline__ void ldsm_x4(unsigned (&r)[4], const void* p) {
-  unsigned s = (unsigned)__cvta_generic_to_shared(p);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(s));
-}
-__device__ __forceinline__ void ldsm_x4_t(unsigned (&r)[4], const void* p) {
-  unsigned s = (unsigned)__cvta_generic_to_shared(p);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(s));
-}
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// C[M x N] = A * B with A row-major [M][K] (AT: stored [K][M]) and B given as
-// [N][K] (BT: stored [K][N]).  M % 128 == N % 64 == K % 32 == 0.
-template <bool AT, bool BT, int EPI>
-__global__ void __launch_bounds__(128) k_gemm(GemmArgs g) {
-  constexpr int A_ROWS = AT ? BK : BM, A_COLS = AT ? BM : BK;
-  constexpr int B_ROWS = BT ? BK : BN, B_COLS = BT ? BN : BK;
-  __shared__ __align__(16) __nv_bfloat16 As[2][A_ROWS][A_COLS + PAD];
-  __shared__ __align__(16) __nv_bfloat16 Bs[2][B_ROWS][B_COLS + PAD];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wm = warp >> 1, wn = warp & 1;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  float acc[4][4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) acc[i][j][k] = 0.f;
-
-  auto load = [&](int kt, int buf) {
-    const int k0 = kt * BK;
-    constexpr int ACH = A_ROWS * A_COLS / 8;  // 16-byte chunks
-#pragma unroll
-    for (int c = tid; c < ACH; c += 128) {
-      const int row = c / (A_COLS / 8), col = (c % (A_COLS / 8)) * 8;
-      const __nv_bfloat16* src =
-          AT ? g.A + (size_t)(k0 + row) * g.lda + m0 + col : g.A + (size_t)(m0 + row) * g.lda + k0 + col;
-      cp_async16(&As[buf][row][col], src);
-    }
-    constexpr int BCH = B_ROWS * B_COLS / 8;
-#pragma unroll
-    for (int c = tid; c < BCH; c += 128) {
-      const int row = c / (B_COLS / 8), col = (c % (B_COLS / 8)) * 8;
-      const __nv_bfloat16* src =
-          BT ? g.B + (size_t)(k0 + row) * g.ldb + n0 + col : g.B + (size_t)(n0 + row) * g.ldb + k0 + col;
-      cp_async16(&Bs[buf][row][col], src);
-    }
-  };
-
-  const int KT = g.K / BK;
-  load(0, 0);
-  cp_commit();
-  for (int kt = 0; kt < KT; ++kt) {
-    const int buf = kt & 1;
-    if (kt + 1 < KT) {
-      load(kt + 1, buf ^ 1);
-      cp_commit();
-      cp_wait<1>();
-    } else {
-      cp_wait<0>();
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < BK / 16; ++kk) {
-      unsigned af[4][4];
-#pragma unroll
-      for (int mi = 0; mi < 4; ++mi) {
-        const int mb = wm * 64 + mi * 16;
-        if (AT)
-          ldsm_x4_t(af[mi], &As[buf][kk * 16 + (lane & 7) + (lane >> 4) * 8][mb + ((lane >> 3) & 1) * 8]);
-        else
-          ldsm_x4(af[mi], &As[buf][mb + (lane & 7) + ((lane >> 3) & 1) * 8][kk * 16 + (lane >> 4) * 8]);
-      }
-      unsigned bf[2][4];
-#pragma unroll
-      for (int np = 0; np < 2; ++np) {
-        const int nb = wn * 32 + np * 16;
-        if (BT)
-          ldsm_x4_t(bf[np], &Bs[buf][kk * 16 + (lane & 7) + ((lane >> 3) & 1) * 8][nb + (lane >> 4) * 8]);
-        else
-          ldsm_x4(bf[np], &Bs[buf][nb + (lane & 7) + (lane >> 4) * 8][kk * 16 + ((lane >> 3) & 1) * 8]);
-      }
-#pragma unroll
-      for (int mi = 0; mi < 4; ++mi)
-#pragma unroll
-        for (int ni = 0; ni < 4; ++ni) {
-          const unsigned* b = &bf[ni >> 1][(ni & 1) * 2];
-          mma_bf16(acc[mi][ni], af[mi], b[0], b[1]);
-        }
-    }
-    __syncthreads();
-  }
-  // epilogue
-  const int gid = lane >> 2, tig = lane & 3;
-#pragma unroll
-  for (int mi = 0; mi < 4; ++mi)
-#pragma unroll
-    for (int ni = 0; ni < 4; ++ni)
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int m = m0 + wm * 64 + mi * 16 + gid + h * 8;
-        const int n = n0 + wn * 32 + ni * 8 + tig * 2;
-        float v0 = acc[mi][ni][2 * h], v1 = acc[mi][ni][2 * h + 1];
-        const size_t o = (size_t)m * g.N + n;
-        if (EPI == EPI_BIAS_GELU) {
-          v0 += g.bias[n];
-          v1 += g.bias[n + 1];
-          g.Zout[o] = v0;
-          g.Zout[o + 1] = v1;
-          *reinterpret_cast<__nv_bfloat162*>(g.Ch + o) = __floats2bfloat162_rn(gelu_f(v0), gelu_f(v1));
-        } else if (EPI == EPI_BIAS) {
-          g.Cf[o] = v0 + g.bias[n];
-          g.Cf[o + 1] = v1 + g.bias[n + 1];
-        } else if (EPI == EPI_DGELU) {
-          v0 *= gelu_grad_f(g.Zin[o]);
-          v1 *= gelu_grad_f(g.Zin[o + 1]);
-          *reinterpret_cast<__nv_bfloat162*>(g.Ch + o) = __floats2bfloat162_rn(v0, v1);
-        } else if (EPI == EPI_F32) {
-          g.Cf[o] = v0;
-          g.Cf[o + 1] = v1;
-        } else {
-          *reinterpret_cast<__nv_bfloat162*>(g.Ch + o) = __floats2bfloat162_rn(v0, v1);
-        }
-      }
-}
-
-template <bool AT, bool BT, int EPI>
-cudaError_t gemm(const GemmArgs& g, cudaStream_t s) {
-  dim3 grid(g.N / BN, g.M / BM);
-  k_gemm<AT, BT, EPI><<<grid, 128, 0, s>>>(g);
-  return cudaGetLastError();
-}
+constexpr int BM = 128;  // rows of a GEMM tile: the batch is padded to a multiple
 
 // ---- small kernels ----------------------------------------------------------
 __device__ __forceinline__ uint64_t mix64(uint64_t x) {
@@ -211,15 +43,19 @@ __device__ __forceinline__ uint64_t mix64(uint64_t x) {
 // Gathers rows of the dataset into padded bf16 inputs and fp32 targets.
 // Row r of the batch takes sample idx = mix64(seed, step, r) % count, or r
 // itself when seed == 0 (in order; rows beyond count are zero).
+// Xt (optional): the transposed inputs [din][ldt].
 __global__ void k_pack(const float* __restrict__ X, const float* __restrict__ Y, int64_t count, int n_in, int n_out,
                        int din, int dout, int64_t rows, uint64_t seed, int64_t step, int64_t base,
-                       __nv_bfloat16* Xb, float* T) {
+                       __nv_bfloat16* Xb, float* T, __nv_bfloat16* Xt = nullptr, int64_t ldt = 0) {
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
     int64_t src = -1;
     if (seed) src = (int64_t)(mix64(seed ^ mix64((uint64_t)step * 0x100000001b3ull + (uint64_t)r)) % (uint64_t)count);
     else if (base + r < count) src = base + r;
-    for (int j = 0; j < din; ++j)
-      Xb[r * din + j] = __float2bfloat16(src >= 0 && j < n_in ? X[src * n_in + j] : 0.f);
+    for (int j = 0; j < din; ++j) {
+      const __nv_bfloat16 v = __float2bfloat16(src >= 0 && j < n_in ? X[src * n_in + j] : 0.f);
+      Xb[r * din + j] = v;
+      if (Xt) Xt[(int64_t)j * ldt + r] = v;
+    }
     if (T)
       for (int j = 0; j < dout; ++j) T[r * dout + j] = (src >= 0 && j < n_out && Y) ? Y[src * n_out + j] : 0.f;
   }
@@ -227,7 +63,7 @@ __global__ void k_pack(const float* __restrict__ X, const float* __restrict__ Y,
 
 // dY = 2 (Y - T) / (rows_valid * n_out) on valid entries, 0 elsewhere; loss sum.
 __global__ void k_mse(const float* __restrict__ Yo, const float* __restrict__ T, int64_t rows, int64_t valid,
-                      int n_out, int dout, __nv_bfloat16* dY, double* loss) {
+                      int n_out, int dout, __nv_bfloat16* dY, __nv_bfloat16* dYt, int64_t ldt, double* loss) {
   double part = 0.0;
   const float scale = 2.0f / (float)((double)valid * n_out);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows * dout; i += (int64_t)gridDim.x * blockDim.x) {
@@ -240,6 +76,7 @@ __global__ void k_mse(const float* __restrict__ Yo, const float* __restrict__ T,
       part += (double)d * d;
     }
     dY[i] = __float2bfloat16(g);
+    dYt[(int64_t)j * ldt + r] = __float2bfloat16(g);
   }
   for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
   if ((threadIdx.x & 31) == 0) atomicAdd(loss, part);
@@ -275,6 +112,15 @@ __global__ void k_adam(float* p, float* m, float* v, const float* g, size_t n, f
   }
 }
 
+// dst[c][r] = bf16(src[r][c]) for an R x C row-major matrix
+__global__ void k_to_bf16_t(const float* __restrict__ src, __nv_bfloat16* dst, int R, int C) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)R * C;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = i / R, r = i - c * R;
+    dst[i] = __float2bfloat16(src[r * C + c]);
+  }
+}
+
 __global__ void k_to_bf16(const float* __restrict__ src, __nv_bfloat16* dst, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     dst[i] = __float2bfloat16(src[i]);
@@ -306,6 +152,10 @@ hsm_status ensure_cap(Mlp& m, int64_t rows) {
   dev_free(&m.T, s);
   dev_free(&m.dA, s);
   dev_free(&m.dB, s);
+  dev_free(&m.Xt, s);
+  for (auto& h : m.Ht) dev_free(&h, s);
+  dev_free(&m.dAt, s);
+  dev_free(&m.dBt, s);
   int wmax = 0;
   for (int l = 0; l < m.nl; ++l) wmax = std::max(wmax, std::max(m.din[l], m.dout[l]));
   MLP_CUDA(dev_alloc(&m.X, (size_t)rows * m.din[0], s));
@@ -319,6 +169,11 @@ hsm_status ensure_cap(Mlp& m, int64_t rows) {
   MLP_CUDA(dev_alloc(&m.T, (size_t)rows * m.dout[m.nl - 1], s));
   MLP_CUDA(dev_alloc(&m.dA, (size_t)rows * wmax, s));
   MLP_CUDA(dev_alloc(&m.dB, (size_t)rows * wmax, s));
+  MLP_CUDA(dev_alloc(&m.Xt, (size_t)rows * m.din[0], s));
+  m.Ht.assign(m.nl - 1, nullptr);
+  for (int l = 0; l < m.nl - 1; ++l) MLP_CUDA(dev_alloc(&m.Ht[l], (size_t)rows * m.dout[l], s));
+  MLP_CUDA(dev_alloc(&m.dAt, (size_t)rows * wmax, s));
+  MLP_CUDA(dev_alloc(&m.dBt, (size_t)rows * wmax, s));
   m.cap = rows;
   return HSM_OK;
 }
@@ -328,16 +183,25 @@ hsm_status refresh_bf16(Mlp& m) {
     const size_t n = (size_t)m.dout[l] * m.din[l];
     k_to_bf16<<<(int)std::min<size_t>(ceil_div(n, 256), 4096), 256, 0, m.stream>>>(m.master + m.w_off[l],
                                                                                     m.wbf + m.wbf_off[l], n);
+    k_to_bf16_t<<<(int)std::min<size_t>(ceil_div(n, 256), 4096), 256, 0, m.stream>>>(
+        m.master + m.w_off[l], m.wbft + m.wbf_off[l], m.dout[l], m.din[l]);
   }
   MLP_CUDA(cudaGetLastError());
   return HSM_OK;
 }
 
-// Forward pass of ``rows`` packed rows (m.X filled); output in m.Yout.
+#define MLP_TRY(call)                                                      \
+  do {                                                                     \
+    const hsm_status s_ = (call);                                          \
+    if (s_ != HSM_OK) return mlp_fail(m, s_, "tensor-core GEMM launch failed"); \
+  } while (0)
+
+// Forward pass of ``rows`` packed rows (m.X and m.Xt filled); output in
+// m.Yout, hidden activations in m.H and (transposed) m.Ht.
 hsm_status forward(Mlp& m, int64_t rows) {
   const __nv_bfloat16* in = m.X;
   for (int l = 0; l < m.nl; ++l) {
-    GemmArgs g{};
+    MlpGemm g{};
     g.A = in;
     g.lda = m.din[l];
     g.B = m.wbf + m.wbf_off[l];
@@ -347,61 +211,71 @@ hsm_status forward(Mlp& m, int64_t rows) {
     g.K = m.din[l];
     g.bias = m.master + m.b_off[l];
     if (l < m.nl - 1) {
+      g.epi = MLP_EPI_BIAS_GELU;
       g.Ch = m.H[l];
       g.Zout = m.Z[l];
-      MLP_CUDA((gemm<false, false, EPI_BIAS_GELU>(g, m.stream)));
+      g.Cht = m.Ht[l];
+      g.ldt = m.cap;
+      MLP_TRY(mlp_gemm_tc(m, g));
       in = m.H[l];
     } else {
+      g.epi = MLP_EPI_BIAS;
       g.Cf = m.Yout;
-      MLP_CUDA((gemm<false, false, EPI_BIAS>(g, m.stream)));
+      MLP_TRY(mlp_gemm_tc(m, g));
     }
   }
   return HSM_OK;
 }
 
 // Backward pass after forward(); gradients (fp32, padded layout) into m.grad.
+// dW_l = dZ_l^T H_{l-1} reads the transposed gradient and activations (both
+// [width][rows], K = rows); dZ_{l-1} = (dZ_l W_l) GELU'(Z_{l-1}) reads the
+// transposed weights.
 hsm_status backward(Mlp& m, int64_t rows, int64_t valid) {
   cudaStream_t s = m.stream;
   const int L = m.nl;
   MLP_CUDA(cudaMemsetAsync(m.loss, 0, sizeof(double), s));
   k_mse<<<(int)std::min<int64_t>(ceil_div(rows * m.dout[L - 1], 256), 2048), 256, 0, s>>>(
-      m.Yout, m.T, rows, valid, m.n_out, m.dout[L - 1], m.dA, m.loss);
+      m.Yout, m.T, rows, valid, m.n_out, m.dout[L - 1], m.dA, m.dAt, m.cap, m.loss);
   MLP_CUDA(cudaGetLastError());
-  __nv_bfloat16* dZ = m.dA;
-  __nv_bfloat16* dnext = m.dB;
+  __nv_bfloat16 *dZ = m.dA, *dZt = m.dAt, *dnext = m.dB, *dnextt = m.dBt;
   for (int l = L - 1; l >= 0; --l) {
-    const __nv_bfloat16* Hprev = l == 0 ? m.X : m.H[l - 1];
-    // dW_l = dZ^T Hprev : M = dout, N = din, K = rows
-    GemmArgs gw{};
-    gw.A = dZ;
-    gw.lda = m.dout[l];
-    gw.B = Hprev;
-    gw.ldb = m.din[l];
+    MlpGemm gw{};
+    gw.A = dZt;
+    gw.lda = m.cap;
+    gw.B = l == 0 ? m.Xt : m.Ht[l - 1];
+    gw.ldb = m.cap;
     gw.M = m.dout[l];
     gw.N = m.din[l];
     gw.K = (int)rows;
+    gw.epi = MLP_EPI_F32;
     gw.Cf = m.grad + m.w_off[l];
-    MLP_CUDA((gemm<true, true, EPI_F32>(gw, s)));
+    MLP_TRY(mlp_gemm_tc(m, gw));
     k_colsum<<<m.dout[l], 256, 0, s>>>(dZ, rows, m.dout[l], m.grad + m.b_off[l]);
     MLP_CUDA(cudaGetLastError());
     if (l > 0) {
-      // dZ_{l-1} = (dZ_l W_l) * GELU'(Z_{l-1}) : M = rows, N = din, K = dout
-      GemmArgs gx{};
+      MlpGemm gx{};
       gx.A = dZ;
       gx.lda = m.dout[l];
-      gx.B = m.wbf + m.wbf_off[l];
-      gx.ldb = m.din[l];
+      gx.B = m.wbft + m.wbf_off[l];
+      gx.ldb = m.dout[l];
       gx.M = (int)rows;
       gx.N = m.din[l];
       gx.K = m.dout[l];
+      gx.epi = MLP_EPI_DGELU;
       gx.Zin = m.Z[l - 1];
       gx.Ch = dnext;
-      MLP_CUDA((gemm<false, true, EPI_DGELU>(gx, s)));
+      gx.Cht = dnextt;
+      gx.ldt = m.cap;
+      MLP_TRY(mlp_gemm_tc(m, gx));
       std::swap(dZ, dnext);
+      std::swap(dZt, dnextt);
     }
   }
   return HSM_OK;
 }
+
+#undef MLP_TRY
 
 }  // namespace
 }  // namespace hsm
@@ -449,7 +323,8 @@ hsm_status hsm_mlp_create(hsm_mlp* out, int n_in, int hidden, int layers, int n_
   };
   if (dev_alloc(&m.master, m.n_master, s) || dev_alloc(&m.adam_m, m.n_master, s) ||
       dev_alloc(&m.adam_v, m.n_master, s) || dev_alloc(&m.grad, m.n_master, s) || dev_alloc(&m.wbf, m.n_wbf, s) ||
-      dev_alloc(&m.loss, 1, s))
+      dev_alloc(&m.wbft, m.n_wbf, s) || dev_alloc(&m.loss, 1, s) || dev_alloc(&m.tc_err, 1, s) ||
+      cudaMemsetAsync(m.tc_err, 0, sizeof(unsigned), s))
     return fail("MLP allocation failed");
   // initialisation: uniform +-sqrt(6/fan_in)/2 on the real entries (seeded, on the host), zero bias
   std::vector<float> host(m.n_master, 0.f);
@@ -485,9 +360,14 @@ hsm_status hsm_mlp_destroy(hsm_mlp h) {
   dev_free(&m.adam_v, s);
   dev_free(&m.grad, s);
   dev_free(&m.wbf, s);
+  dev_free(&m.wbft, s);
   dev_free(&m.loss, s);
   dev_free(&m.X, s);
+  dev_free(&m.Xt, s);
   for (auto& x : m.H) dev_free(&x, s);
+  for (auto& x : m.Ht) dev_free(&x, s);
+  dev_free(&m.dAt, s);
+  dev_free(&m.dBt, s);
   for (auto& x : m.Z) dev_free(&x, s);
   dev_free(&m.Yout, s);
   dev_free(&m.T, s);
@@ -563,19 +443,23 @@ hsm_status hsm_mlp_grad(hsm_mlp h, const float* X, const float* Y, int64_t count
   const int64_t rows = ceil_div(count, BM) * BM;
   hsm_status st = ensure_cap(m, rows);
   if (st != HSM_OK) return st;
+  MLP_CUDA(cudaMemsetAsync(m.tc_err, 0, sizeof(unsigned), m.stream));
   k_pack<<<(int)std::min<int64_t>(ceil_div(rows, 256), 4096), 256, 0, m.stream>>>(
-      X, Y, count, m.n_in, m.n_out, m.din[0], m.dout[m.nl - 1], rows, 0, 0, 0, m.X, m.T);
+      X, Y, count, m.n_in, m.n_out, m.din[0], m.dout[m.nl - 1], rows, 0, 0, 0, m.X, m.T, m.Xt, m.cap);
   MLP_CUDA(cudaGetLastError());
   MLP_CUDA(cudaMemsetAsync(m.grad, 0, m.n_master * sizeof(float), m.stream));
   if ((st = forward(m, rows)) != HSM_OK) return st;
   if ((st = backward(m, rows, count)) != HSM_OK) return st;
   double l = 0.0;
+  unsigned err = 0;
   MLP_CUDA(cudaMemcpyAsync(&l, m.loss, sizeof(double), cudaMemcpyDeviceToHost, m.stream));
+  MLP_CUDA(cudaMemcpyAsync(&err, m.tc_err, sizeof(unsigned), cudaMemcpyDeviceToHost, m.stream));
   if (grads_host) {
     st = pack_io(h, grads_host, nullptr, m.grad, false);
     if (st != HSM_OK) return st;
   }
   MLP_CUDA(cudaStreamSynchronize(m.stream));
+  if (err) return mlp_fail(m, HSM_ETIMEOUT, "a tensor-core GEMM timed out");
   if (loss) *loss = (float)(l / ((double)count * m.n_out));
   return HSM_OK;
 }
@@ -591,9 +475,11 @@ hsm_status hsm_mlp_train(hsm_mlp h, const float* X, const float* Y, int64_t coun
   double* log_dev = nullptr;
   if (loss_log) MLP_CUDA(dev_alloc(&log_dev, std::max(steps, 1), m.stream));
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  MLP_CUDA(cudaMemsetAsync(m.tc_err, 0, sizeof(unsigned), m.stream));
   for (int it = 0; it < steps; ++it) {
     k_pack<<<(int)std::min<int64_t>(ceil_div(rows, 256), 4096), 256, 0, m.stream>>>(
-        X, Y, count, m.n_in, m.n_out, m.din[0], m.dout[m.nl - 1], rows, seed ? seed : 1, m.t, 0, m.X, m.T);
+        X, Y, count, m.n_in, m.n_out, m.din[0], m.dout[m.nl - 1], rows, seed ? seed : 1, m.t, 0, m.X, m.T, m.Xt,
+        m.cap);
     if ((st = forward(m, rows)) != HSM_OK) break;
     if ((st = backward(m, rows, rows)) != HSM_OK) break;
     if (log_dev) MLP_CUDA(cudaMemcpyAsync(log_dev + it, m.loss, sizeof(double), cudaMemcpyDeviceToDevice, m.stream));
@@ -611,7 +497,12 @@ hsm_status hsm_mlp_train(hsm_mlp h, const float* X, const float* Y, int64_t coun
     for (int i = 0; i < steps; ++i) loss_log[i] = (float)(l[i] / ((double)rows * m.n_out));
   }
   dev_free(&log_dev, m.stream);
-  if (st == HSM_OK) MLP_CUDA(cudaStreamSynchronize(m.stream));
+  if (st == HSM_OK) {
+    unsigned err = 0;
+    MLP_CUDA(cudaMemcpyAsync(&err, m.tc_err, sizeof(unsigned), cudaMemcpyDeviceToHost, m.stream));
+    MLP_CUDA(cudaStreamSynchronize(m.stream));
+    if (err) return mlp_fail(m, HSM_ETIMEOUT, "a tensor-core GEMM timed out");
+  }
   return st;
 }
 

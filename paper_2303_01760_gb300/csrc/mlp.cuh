@@ -1,5 +1,6 @@
-// Learned weight predictor: the MLP state shared by mlp.cu (training, the
-// mma.sync GEMMs, projection) and mlp_tc.cu (the fused tcgen05 forward pass).
+// Learned weight predictor: the MLP state shared by mlp.cu (training,
+// projection) and mlp_tc.cu (the tcgen05 training GEMMs and the fused
+// tcgen05 forward pass).
 #pragma once
 #include <string>
 #include <vector>
@@ -34,6 +35,14 @@ struct Mlp {
   float* T = nullptr;             // targets [cap][dout_last]
   __nv_bfloat16* dA = nullptr;    // [cap][max width]
   __nv_bfloat16* dB = nullptr;
+  // transposed copies, [width][cap], so every training GEMM reads both
+  // operands K-major: the inputs, the hidden activations, the gradients and
+  // the bf16 weights ([din][dout] per layer, at wbf_off)
+  __nv_bfloat16* Xt = nullptr;
+  std::vector<__nv_bfloat16*> Ht;
+  __nv_bfloat16* dAt = nullptr;
+  __nv_bfloat16* dBt = nullptr;
+  __nv_bfloat16* wbft = nullptr;
   double* loss = nullptr;         // device loss accumulator
   std::string last_error;
   // fused tcgen05 forward pass (mlp_tc.cu): packed inputs and error flag
@@ -47,6 +56,28 @@ struct Mlp {
 // for c < n_out.  Returns false (and enqueues nothing) when the network's
 // shape is not one the kernel handles.
 bool mlp_forward_tc_supported(const Mlp& m);
+
+// One training GEMM on the tensor cores (mlp_tc.cu): C[M x N] = A B^T with
+// A bf16 [M][K] (row stride lda) and B bf16 [N][K] (row stride ldb), both
+// K-major, M % 128 == K % 64 == N % 64 == 0; FP32 accumulation, then:
+enum { MLP_EPI_BIAS_GELU = 0,  // Zout = C + bias, Ch = GELU(Zout) (and Cht = its transpose)
+       MLP_EPI_BIAS = 1,       // Cf = C + bias
+       MLP_EPI_DGELU = 2,      // Ch = C * GELU'(Zin) (and Cht = its transpose)
+       MLP_EPI_F32 = 3 };      // Cf = C
+struct MlpGemm {
+  const __nv_bfloat16* A;
+  const __nv_bfloat16* B;
+  int64_t lda, ldb;
+  int M, N, K, epi;
+  const float* bias;
+  const float* Zin;
+  float* Cf;
+  float* Zout;
+  __nv_bfloat16* Ch;
+  __nv_bfloat16* Cht;  // [N][ldt] or nullptr
+  int64_t ldt;
+};
+hsm_status mlp_gemm_tc(Mlp& m, const MlpGemm& g);
 hsm_status mlp_forward_tc(Mlp& m, const __nv_bfloat16* X, int64_t rows, float* Y, int ldy);
 
 }  // namespace hsm

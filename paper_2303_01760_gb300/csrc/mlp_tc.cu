@@ -352,7 +352,252 @@ bool make_map(CUtensorMap* m, const void* ptr, uint64_t inner, uint64_t outer, u
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// 2D bf16 row-major tensor [outer][inner] with row stride ld elements, boxes
+// of [box_outer][64] with the 128-byte swizzle.
+bool make_map_ld(CUtensorMap* m, const void* ptr, uint64_t inner, uint64_t outer, uint64_t ld, uint32_t box_outer) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {inner, outer};
+  const cuuint64_t strides[1] = {ld * 2};
+  const cuuint32_t box[2] = {64, box_outer};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// ---- training GEMMs ------------------------------------------------------------
+// C[M x N] = A[M x K] B[N x K]^T with A and B bf16 K-major in global memory
+// (row-major [M][K] and [N][K]), FP32 accumulation in tensor memory.  One
+// 128 x BN output tile per CTA (BN = 64 or 128):
+//
+//   * warp 0 streams 64-column K slices of A and B into a four-stage ring with
+//     TMA (128-byte swizzle);
+//   * warp 1 allocates BN tensor-memory columns and issues tcgen05.mma
+//     (M = 128, N = BN, K = 16 per instruction), committing each stage back
+//     to the producer and, after the last slice, to the epilogue;
+//   * warps 4..7 drain the accumulator with tcgen05.ld (warp 4 + q reads lane
+//     quarter q: rows 32q .. 32q + 31) and apply the layer's epilogue.
+//
+// Every mbarrier wait is bounded.  On expiry the error flag is set and every
+// role leaves its loop; the producer then waits (bounded) for the copies it
+// issued, the MMA issuer for its issued MMAs, and only then is the tensor
+// memory released.
+constexpr int kGThreads = 256;
+constexpr int kGStages = 4;
+constexpr int kGStageBytes = 128 * 128;  // 128 rows x 64 bf16
+constexpr int kGSmemBytes = 2 * kGStages * kGStageBytes + 256 + 1024;
+
+struct GemmTcArgs {
+  int M, N, K, BN, epi;
+  const float* bias;   // [N] (MLP_EPI_BIAS_GELU, MLP_EPI_BIAS)
+  const float* Zin;    // [M][N] pre-activations (MLP_EPI_DGELU)
+  float* Cf;           // [M][N] FP32 output (MLP_EPI_BIAS, MLP_EPI_F32)
+  float* Zout;         // [M][N] pre-activations (MLP_EPI_BIAS_GELU)
+  __nv_bfloat16* Ch;   // [M][N] bf16 output (MLP_EPI_BIAS_GELU, MLP_EPI_DGELU)
+  __nv_bfloat16* Cht;  // [N][ldt] its transpose, or nullptr
+  int64_t ldt;
+  unsigned* err;
+};
+
+// d GELU / dz = Phi(z) + z phi(z), with the erf of gelu()
+__device__ __forceinline__ float gelu_grad(float z) {
+  const float e = erf_as(fabsf(z) * 0.70710678118654752f);
+  const float Phi = 0.5f * (1.0f + (z < 0.0f ? -e : e));
+  return fmaf(z * 0.39894228040143268f, __expf(-0.5f * z * z), Phi);
+}
+
+// a bounded wait that ignores the abort flag (draining after an abort)
+__device__ __forceinline__ void mbar_drain(uint64_t* b, uint32_t par) {
+  const uint32_t a = saddr(b);
+  for (uint32_t it = 0; it < kMaxSpins; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(par)
+        : "memory");
+    if (ok) return;
+  }
+}
+
+__global__ void __launch_bounds__(kGThreads, 1)
+    k_gemm_tc(GemmTcArgs a, const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint8_t* sa = base;                          // [stage][128 rows][128 B]
+  uint8_t* sb = sa + kGStages * kGStageBytes;  // [stage][BN rows][128 B]
+  uint64_t* full = reinterpret_cast<uint64_t*>(sb + kGStages * kGStageBytes);
+  uint64_t* empty = full + kGStages;
+  uint64_t* accfull = empty + kGStages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accfull + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  int* issued = const_cast<int*>(abort_flag) + 1;    // K slices the producer issued
+  int* consumed = issued + 1;                        // K slices the MMA issuer consumed
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * 128, n0 = blockIdx.x * a.BN;
+  const int KT = a.K / 64;
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < kGStages; ++st) {
+      mbar_init(&full[st], 1);
+      mbar_init(&empty[st], 1);
+    }
+    mbar_init(accfull, 1);
+    *abort_flag = 0;
+    *issued = 0;
+    *consumed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(tmem_slot)),
+                 "r"((uint32_t)a.BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  bool mma_done = false;
+  if (warp == 0 && lane == 0) {
+    // ---- producer
+    int c = 0;
+    for (; c < KT; ++c) {
+      const int st = c % kGStages;
+      const uint32_t u = (uint32_t)(c / kGStages);
+      if (!mbar_wait(&empty[st], (u & 1) ^ 1, abort_flag, a.err)) break;
+      mbar_expect_tx(&full[st], (uint32_t)(128 + a.BN) * 128u);
+      tma_load_2d(sa + st * kGStageBytes, &ta, c * 64, m0, &full[st]);
+      tma_load_2d(sb + st * kGStageBytes, &tb, c * 64, n0, &full[st]);
+    }
+    *issued = c;
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer
+    const uint32_t idesc = idesc_bf16(128, a.BN);
+    int c = 0;
+    for (; c < KT; ++c) {
+      const int st = c % kGStages;
+      const uint32_t u = (uint32_t)(c / kGStages);
+      if (!mbar_wait(&full[st], u & 1, abort_flag, a.err)) break;
+      tc_fence_after();
+      const uint64_t ad = sw128_desc(saddr(sa + st * kGStageBytes));
+      const uint64_t bd = sw128_desc(saddr(sb + st * kGStageBytes));
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) umma(tmem, ad + 2 * kk, bd + 2 * kk, idesc, (c | kk) != 0 ? 1u : 0u);
+      umma_commit(&empty[st]);
+    }
+    *consumed = c;
+    // the accumulator is complete (or, after an abort, every issued MMA has
+    // finished) when this commit arrives
+    umma_commit(accfull);
+    mma_done = c == KT;
+  } else if (warp >= 4) {
+    // ---- epilogue
+    const int q = warp & 3;
+    const int64_t row = m0 + 32 * q + lane;
+    bool ok = mbar_wait(accfull, 0, abort_flag, a.err);
+    ok = __all_sync(0xffffffffu, ok) && !*abort_flag;
+    if (ok) {
+      tc_fence_after();
+      const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16);
+      for (int cc = 0; cc < a.BN; cc += 32) {
+        float v[32];
+        tmem_ld32(trow + (uint32_t)cc, v);
+        const int n = n0 + cc;
+        const int64_t o = row * a.N + n;
+        if (a.epi == MLP_EPI_BIAS_GELU) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const float z = v[j] + a.bias[n + j];
+            a.Zout[o + j] = z;
+            v[j] = gelu(z);
+          }
+        } else if (a.epi == MLP_EPI_BIAS) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) a.Cf[o + j] = v[j] + a.bias[n + j];
+          continue;
+        } else if (a.epi == MLP_EPI_DGELU) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] *= gelu_grad(a.Zin[o + j]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) a.Cf[o + j] = v[j];
+          continue;
+        }
+        // bf16 outputs: the row, and its transpose (consecutive rows of a warp
+        // are consecutive entries of a transposed row)
+#pragma unroll
+        for (int j = 0; j < 32; j += 8) {
+          uint4 pk;
+          uint32_t* w = reinterpret_cast<uint32_t*>(&pk);
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[j + 2 * t], v[j + 2 * t + 1]);
+            w[t] = *reinterpret_cast<const uint32_t*>(&h2);
+          }
+          *reinterpret_cast<uint4*>(a.Ch + o + j) = pk;
+        }
+        if (a.Cht)
+#pragma unroll
+          for (int j = 0; j < 32; ++j) a.Cht[(int64_t)(n + j) * a.ldt + row] = __float2bfloat16(v[j]);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  // after an abort: the copies issued and not consumed, and the issued MMAs,
+  // finish before the shared and tensor memory are given up
+  if (warp == 0 && lane == 0) {
+    for (int c = *consumed; c < *issued; ++c) mbar_drain(&full[c % kGStages], (uint32_t)(c / kGStages) & 1);
+  }
+  if (warp == 1 && lane == 0 && !mma_done) mbar_drain(accfull, 0);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    __syncwarp();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)a.BN) : "memory");
+  }
+}
+
 }  // namespace
+
+hsm_status mlp_gemm_tc(Mlp& m, const MlpGemm& g) {
+  if (g.M % 128 || g.K % 64 || g.N % 64 || g.M <= 0 || g.N <= 0 || g.K <= 0) return HSM_EINVAL;
+  cudaStream_t s = m.stream;
+  if (!m.tc_err) {
+    if (dev_alloc(&m.tc_err, 1, s) != cudaSuccess) return HSM_ENOMEM;
+    if (cudaMemsetAsync(m.tc_err, 0, sizeof(unsigned), s) != cudaSuccess) return HSM_ECUDA;
+  }
+  GemmTcArgs a{};
+  a.M = g.M;
+  a.N = g.N;
+  a.K = g.K;
+  a.BN = g.N % 128 == 0 ? 128 : 64;
+  a.epi = g.epi;
+  a.bias = g.bias;
+  a.Zin = g.Zin;
+  a.Cf = g.Cf;
+  a.Zout = g.Zout;
+  a.Ch = g.Ch;
+  a.Cht = g.Cht;
+  a.ldt = g.ldt;
+  a.err = m.tc_err;
+  CUtensorMap ta, tb;
+  memset(&ta, 0, sizeof(ta));
+  memset(&tb, 0, sizeof(tb));
+  if (!make_map_ld(&ta, g.A, (uint64_t)g.K, (uint64_t)g.M, (uint64_t)g.lda, 128) ||
+      !make_map_ld(&tb, g.B, (uint64_t)g.K, (uint64_t)g.N, (uint64_t)g.ldb, (uint32_t)a.BN))
+    return HSM_ECUDA;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kGSmemBytes) != cudaSuccess)
+      return HSM_ECUDA;
+    attr = true;
+  }
+  k_gemm_tc<<<dim3((unsigned)(g.N / a.BN), (unsigned)(g.M / 128)), kGThreads, kGSmemBytes, s>>>(a, ta, tb);
+  return cudaGetLastError() == cudaSuccess ? HSM_OK : HSM_ECUDA;
+}
 
 bool mlp_forward_tc_supported(const Mlp& m) {
   if (m.nl < 2 || m.nl > kMaxLayers || m.din[0] != 64) return false;
