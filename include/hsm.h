@@ -214,6 +214,28 @@ hsm_status hsm_wall_flux_mean(hsm_plan plan, const double* T, const int32_t* nod
 hsm_status hsm_apply(hsm_plan plan, unsigned op_mask, hsm_dtype in_dtype, const void* u,
                      double* out);
 
+/* Stencil validation (no counterpart in the paper: a debugging aid).
+ * hsm_plan_validate scans the plan's stencil tables on the device -- the node
+ * list and the ELL index array of each group against [0, N), and the node map
+ * (group 0/1, position inside its group) -- and returns HSM_EBOUNDS, naming
+ * the table, when an entry is out of range.  Synchronises.
+ * hsm_plan_set_checks(plan, 1) turns on check mode: every call that gathers
+ * through the stencils (hsm_plan_compute_weights, hsm_apply,
+ * hsm_wall_flux_mean, hsm_plan_condition, hsm_stepper_create, hsm_step)
+ * validates them first and returns HSM_EBOUNDS before any gather runs.  The
+ * environment variable HSM_CHECK_BOUNDS=1 turns it on for every plan at
+ * creation.                                                                 */
+hsm_status hsm_plan_validate(hsm_plan plan);
+hsm_status hsm_plan_set_checks(hsm_plan plan, int enable);
+
+/* Failure-path test hook: HSM_FAULT_STENCIL_INDEX writes, from the host, the
+ * out-of-range index N into the last entry of the plan's first RBF-FD stencil
+ * (the first MON stencil when there is none) and turns check mode on, so
+ * that every gathering call returns HSM_EBOUNDS and no kernel reads through
+ * the bad index.  hsm_plan_build_stencils rebuilds valid tables.  Needs
+ * built stencils (HSM_ESTATE otherwise).                                    */
+hsm_status hsm_plan_inject_fault(hsm_plan plan, int fault);
+
 /* Times the kernel variants of this plan (the kNN search: 1, 2 or 4 threads
  * per query over growing rings of cells, or one warp per query over a fixed
  * window of cells with the ring search finishing the queries the window
@@ -419,7 +441,7 @@ hsm_status hsm_mlp_predict(hsm_mlp mlp, const float* X, int64_t count, float* Y)
  * out: that hsm_mlp_predict returns HSM_ETIMEOUT, and later calls work as
  * before.  The hook applies to one pass; HSM_FAULT_NONE clears it.
  * HSM_EINVAL for a NULL handle or an unknown fault.                          */
-enum { HSM_FAULT_NONE = 0, HSM_FAULT_HOLD_MLP_LOADS = 1 };
+enum { HSM_FAULT_NONE = 0, HSM_FAULT_HOLD_MLP_LOADS = 1, HSM_FAULT_STENCIL_INDEX = 2 };
 hsm_status hsm_mlp_inject_fault(hsm_mlp mlp, int fault);
 
 /* Attaches the predictor used by HSM_PREC_LEARNED (n_in = d n, n_out = nops n;

@@ -3,6 +3,7 @@
 // before anything is enqueued.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <fstream>
 #include <functional>
@@ -64,6 +65,72 @@ static std::vector<int8_t> monomial_exponents(int dim, int m) {
 }  // namespace hsm
 
 using namespace hsm;
+
+namespace hsm {
+namespace check_kernels {
+
+// bit b of *bad when an entry of a lies outside [0, hi)
+__global__ void k_check_range(const int32_t* __restrict__ a, int64_t n, int64_t hi, unsigned bit, unsigned* bad) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (a[i] < 0 || (int64_t)a[i] >= hi) {
+      atomicOr(bad, bit);
+      return;
+    }
+}
+
+// the node -> (group, position) map: kind in {0, 1}, position inside its group
+__global__ void k_check_map(const uint8_t* __restrict__ kind, const int32_t* __restrict__ pos, int64_t N,
+                            int64_t count0, int64_t count1, unsigned* bad) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const int k = kind[i];
+    const int64_t c = k == 0 ? count0 : count1;
+    if (k > 1 || pos[i] < 0 || pos[i] >= c) {
+      atomicOr(bad, 16u);
+      return;
+    }
+  }
+}
+
+}  // namespace check_kernels
+using namespace check_kernels;
+
+// Scans the stencil tables: node lists and index arrays of both groups
+// against [0, N), and the node map against the group sizes.
+hsm_status validate_stencils(hsm_plan p) {
+  cudaStream_t s = p->stream;
+  if (!p->check_flag) HSM_CUDA(p, dev_alloc(&p->check_flag, 1, s));
+  HSM_CUDA(p, cudaMemsetAsync(p->check_flag, 0, sizeof(unsigned), s));
+  const int T = 256;
+  auto grid = [&](int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, T), num_sms() * 8)); };
+  const Group* gs[2] = {&p->mon, &p->rbf};
+  for (int g = 0; g < 2; ++g) {
+    const Group& G = *gs[g];
+    if (G.count <= 0) continue;
+    k_check_range<<<grid(G.count), T, 0, s>>>(G.nodes, G.count, p->N, 1u << g, p->check_flag);
+    const int64_t ne = G.count * (int64_t)G.width;
+    k_check_range<<<grid(ne), T, 0, s>>>(G.idx, ne, p->N, 4u << g, p->check_flag);
+  }
+  k_check_map<<<grid(p->N), T, 0, s>>>(p->kind, p->pos, p->N, p->mon.count, p->rbf.count, p->check_flag);
+  HSM_CUDA(p, cudaGetLastError());
+  unsigned bad = 0;
+  HSM_CUDA(p, cudaMemcpyAsync(&bad, p->check_flag, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  HSM_CUDA(p, cudaStreamSynchronize(s));
+  if (!bad) return HSM_OK;
+  std::string what;
+  if (bad & 1u) what += " MON node list;";
+  if (bad & 2u) what += " RBF-FD node list;";
+  if (bad & 4u) what += " MON stencil indices;";
+  if (bad & 8u) what += " RBF-FD stencil indices;";
+  if (bad & 16u) what += " node-to-group map;";
+  return set_error(p, HSM_EBOUNDS, "entries out of range in the" + what.substr(0, what.size() - 1));
+}
+
+hsm_status check_gate(hsm_plan p) {
+  if (!p->checks || !p->stencils_built) return HSM_OK;
+  return validate_stencils(p);
+}
+
+}  // namespace hsm
 
 extern "C" {
 
@@ -128,6 +195,8 @@ hsm_status hsm_plan_create(hsm_plan* out, int dim, int64_t n_nodes, const double
   p->stream = (cudaStream_t)cuda_stream;
   for (int b = 0; b < 4; ++b)
     if (op_mask & (1u << b)) p->ops[p->nops++] = 1 << b;
+  const char* ck = std::getenv("HSM_CHECK_BOUNDS");
+  p->checks = ck && ck[0] && std::strcmp(ck, "0") != 0;
   *out = p;
   return HSM_OK;
 }
@@ -150,6 +219,7 @@ static void free_plan_device(hsm_plan p) {
   dev_free(&p->dev_flags, s);
   dev_free(&p->dev_count, s);
   dev_free(&p->sing_list, s);
+  dev_free(&p->check_flag, s);
   free_build_ws(p);
 }
 
@@ -228,6 +298,10 @@ hsm_status hsm_plan_compute_weights(hsm_plan p, hsm_prec prec, uint8_t* node_sta
     return set_error(p, HSM_EINVAL, "unknown precision mode");
   if (prec == HSM_PREC_LEARNED && !p->mlp)
     return set_error(p, HSM_ESTATE, "HSM_PREC_LEARNED needs a predictor attached with hsm_mlp_attach");
+  {
+    const hsm_status ck = check_gate(p);
+    if (ck != HSM_OK) return ck;
+  }
   cudaStream_t s = p->stream;
   if (!p->mon.w64) HSM_CUDA(p, dev_alloc(&p->mon.w64, (size_t)p->nops * p->mon.width * p->mon.count, s));
   if (!p->rbf.w64) HSM_CUDA(p, dev_alloc(&p->rbf.w64, (size_t)p->nops * p->rbf.width * p->rbf.count, s));
@@ -400,6 +474,8 @@ hsm_status hsm_apply(hsm_plan p, unsigned op_mask, hsm_dtype in_dtype, const voi
     hsm_status st = weights_to_f32(p);
     if (st != HSM_OK) return st;
   }
+  hsm_status ck = check_gate(p);
+  if (ck != HSM_OK) return ck;
   PhaseTimer tm(p, HSM_PHASE_APPLY);
   return launch_apply(p, op_mask, in_dtype, u, out, p->stream);
 }
@@ -424,6 +500,8 @@ hsm_status hsm_plan_condition(hsm_plan p, double* kappa) {
   if (!p) return set_error(nullptr, HSM_EINVAL, "plan is NULL");
   if (!p->stencils_built) return set_error(p, HSM_ESTATE, "hsm_plan_build_stencils must come first");
   if (!kappa) return set_error(p, HSM_EINVAL, "kappa is required");
+  hsm_status ck = check_gate(p);
+  if (ck != HSM_OK) return ck;
   return launch_condition(p, kappa);
 }
 
@@ -433,7 +511,38 @@ hsm_status hsm_wall_flux_mean(hsm_plan p, const double* T, const int32_t* nodes,
   if (!p->weights_built) return set_error(p, HSM_ESTATE, "weights are not computed");
   if (!T || !nodes || !normals || !out) return set_error(p, HSM_EINVAL, "T, nodes, normals and out are required");
   if (count < 1) return set_error(p, HSM_EINVAL, "count must be at least 1");
+  hsm_status ck = check_gate(p);
+  if (ck != HSM_OK) return ck;
   return launch_wall_flux(p, T, nodes, count, normals, scale, out);
+}
+
+hsm_status hsm_plan_validate(hsm_plan p) {
+  if (!p) return set_error(nullptr, HSM_EINVAL, "plan is NULL");
+  if (!p->stencils_built) return set_error(p, HSM_ESTATE, "hsm_plan_build_stencils must come first");
+  return validate_stencils(p);
+}
+
+hsm_status hsm_plan_set_checks(hsm_plan p, int enable) {
+  if (!p) return set_error(nullptr, HSM_EINVAL, "plan is NULL");
+  if (enable != 0 && enable != 1) return set_error(p, HSM_EINVAL, "enable must be 0 or 1");
+  p->checks = enable != 0;
+  return HSM_OK;
+}
+
+hsm_status hsm_plan_inject_fault(hsm_plan p, int fault) {
+  if (!p) return set_error(nullptr, HSM_EINVAL, "plan is NULL");
+  if (fault != HSM_FAULT_STENCIL_INDEX) return set_error(p, HSM_EINVAL, "unknown fault");
+  if (!p->stencils_built) return set_error(p, HSM_ESTATE, "hsm_plan_build_stencils must come first");
+  Group& G = p->rbf.count > 0 ? p->rbf : p->mon;
+  if (G.count <= 0) return set_error(p, HSM_ESTATE, "the plan has no stencils");
+  // the last entry of the group's first stencil ([width][count] layout) points
+  // one past the last node; check mode goes on first, so no gather follows it
+  p->checks = true;
+  const int32_t bad = (int32_t)p->N;
+  HSM_CUDA(p, cudaMemcpyAsync(G.idx + (int64_t)(G.width - 1) * G.count, &bad, sizeof(int32_t),
+                              cudaMemcpyHostToDevice, p->stream));
+  HSM_CUDA(p, cudaStreamSynchronize(p->stream));
+  return HSM_OK;
 }
 
 // ---------------------------------------------------------------------------

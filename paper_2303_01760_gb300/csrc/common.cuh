@@ -119,6 +119,10 @@ struct hsm_plan_s {
   unsigned build_flags = 0;  // device status bits of the last stencil build (MON weights included)
   bool stencils_built = false;
   bool weights_built = false;
+  // check mode: every call that gathers through the stencils validates them
+  // first (hsm_plan_set_checks, or HSM_CHECK_BOUNDS=1 at plan creation)
+  bool checks = false;
+  unsigned* check_flag = nullptr;  // device flag of the validation scan
   hsm::Tuning tune;
   hsm_mlp mlp = nullptr;         // attached learned predictor (not owned)
   // batch validation of the learned weights: `gate_samples` stencils of the
@@ -138,6 +142,11 @@ struct hsm_plan_s {
 };
 
 namespace hsm {
+
+// In check mode, validates the plan's stencils before a gathering call:
+// HSM_EBOUNDS when an index lies outside its range, HSM_OK otherwise (and
+// always HSM_OK outside check mode).
+hsm_status check_gate(hsm_plan p);
 
 // Event timing of one phase on the plan's stream (no-op unless enabled).
 struct PhaseTimer {

@@ -1126,6 +1126,10 @@ hsm_status hsm_stepper_create(hsm_stepper* out, hsm_plan pl, const hsm_phys* phy
   if (!out || !pl || !phys) return set_error(pl, HSM_EINVAL, "out, plan and phys are required");
   *out = nullptr;
   if (!pl->weights_built) return set_error(pl, HSM_ESTATE, "the plan's weights are not computed");
+  {
+    const hsm_status ck = check_gate(pl);
+    if (ck != HSM_OK) return ck;
+  }
   const unsigned need = HSM_DX | HSM_DY | HSM_LAP | (pl->dim == 3 ? HSM_DZ : 0);
   if ((pl->op_mask & need) != need) return set_error(pl, HSM_EINVAL, "the plan needs every first derivative and the Laplacian");
   if (!phys->bc || !phys->T_bc || !phys->normals) return set_error(pl, HSM_EINVAL, "bc, T_bc and normals are required");
@@ -1227,6 +1231,10 @@ hsm_status hsm_stepper_create(hsm_stepper* out, hsm_plan pl, const hsm_phys* phy
 hsm_status hsm_step(hsm_stepper st, int n_steps, double* v, double* T, double* p, int* krylov_iters) {
   if (!st) return set_error(nullptr, HSM_EINVAL, "stepper is NULL");
   if (n_steps < 0 || !v || !T || !p) return set_error(st->plan, HSM_EINVAL, "invalid step arguments");
+  {
+    const hsm_status ck = check_gate(st->plan);
+    if (ck != HSM_OK) return ck;
+  }
   bool notconv = false;
   hsm_status r = st->dim == 2 ? run_steps<2>(st, n_steps, v, T, p, krylov_iters, &notconv)
                               : run_steps<3>(st, n_steps, v, T, p, krylov_iters, &notconv);

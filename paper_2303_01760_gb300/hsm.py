@@ -43,7 +43,7 @@ class hsm_phys(C.Structure):
 
 (HSM_OK, HSM_EINVAL, HSM_ENOMEM, HSM_ECUDA, HSM_ESINGULAR, HSM_ENOTCONV, HSM_ETIMEOUT, HSM_EBOUNDS,
  HSM_ESTATE) = range(9)
-HSM_FAULT_NONE, HSM_FAULT_HOLD_MLP_LOADS = 0, 1
+HSM_FAULT_NONE, HSM_FAULT_HOLD_MLP_LOADS, HSM_FAULT_STENCIL_INDEX = 0, 1, 2
 
 HSM_PRECOND_AMG = 0
 HSM_PRECOND_JACOBI = 1
@@ -66,6 +66,9 @@ _SIGS = {
     "hsm_plan_autotune": (C.c_int, [_p, C.c_char_p]),
     "hsm_plan_tuning": (C.c_int, [_p] + [C.POINTER(C.c_int)] * 6),
     "hsm_plan_set_tuning": (C.c_int, [_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]),
+    "hsm_plan_validate": (C.c_int, [_p]),
+    "hsm_plan_set_checks": (C.c_int, [_p, C.c_int]),
+    "hsm_plan_inject_fault": (C.c_int, [_p, C.c_int]),
     "hsm_plan_destroy": (C.c_int, [_p]),
     "hsm_plan_profile": (C.c_int, [_p, C.POINTER(C.c_float), C.POINTER(_i64)]),
     "hsm_plan_set_timing": (C.c_int, [_p, C.c_int]),
@@ -368,6 +371,16 @@ class Plan:
 
     def autotune(self, cache_path=None):
         check(lib.hsm_plan_autotune(self.h, cache_path.encode() if cache_path else None), self.h)
+
+    def validate(self):
+        """Status of the stencil-table scan (HSM_OK or HSM_EBOUNDS); not raised."""
+        return lib.hsm_plan_validate(self.h)
+
+    def set_checks(self, enable=True):
+        check(lib.hsm_plan_set_checks(self.h, int(bool(enable))), self.h)
+
+    def inject_stencil_fault(self):
+        check(lib.hsm_plan_inject_fault(self.h, HSM_FAULT_STENCIL_INDEX), self.h)
 
     def set_tuning(self, knn_qt=1, rbf_lanes=8, rbf_lanes32=8, apply_threads=256, grouped=0):
         check(lib.hsm_plan_set_tuning(self.h, int(knn_qt), int(rbf_lanes), int(rbf_lanes32), int(apply_threads),
