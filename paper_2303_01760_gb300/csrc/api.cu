@@ -220,6 +220,8 @@ static void free_plan_device(hsm_plan p) {
   dev_free(&p->dev_count, s);
   dev_free(&p->sing_list, s);
   dev_free(&p->check_flag, s);
+  if (p->hrb) cudaFreeHost(p->hrb);
+  p->hrb = nullptr;
   free_build_ws(p);
 }
 
@@ -376,11 +378,17 @@ hsm_status hsm_plan_compute_weights(hsm_plan p, hsm_prec prec, uint8_t* node_sta
   // needs solvable weights at every node; 3D wall nodes next to a box edge
   // with m = 3 span too few layers across the edge for the cubics).  Duplicate
   // nodes stay singular at every degree.
-  if (p->m >= 2 && p->sing_cap >= p->rbf.count && p->rbf.count) {
-    int sc = 0;
-    HSM_CUDA(p, cudaMemcpyAsync(&sc, p->dev_count + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
-    HSM_CUDA(p, cudaStreamSynchronize(s));
-    sc = (int)std::min<int64_t>(sc, p->sing_cap);  // a list holds each system at most once per pass
+  // One read-back, into pinned words, of the singular-system count and the
+  // status flags; the degree retries below (rare) read back after each pass.
+  if (!p->hrb) HSM_CUDA(p, cudaMallocHost((void**)&p->hrb, 4 * sizeof(int)));
+  const bool retry = p->m >= 2 && p->sing_cap >= p->rbf.count && p->rbf.count;
+  p->hrb[0] = 0;
+  if (retry) HSM_CUDA(p, cudaMemcpyAsync(p->hrb, p->dev_count + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+  HSM_CUDA(p, cudaMemcpyAsync(p->hrb + 1, p->dev_flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  HSM_CUDA(p, cudaStreamSynchronize(s));
+  unsigned flags = (unsigned)p->hrb[1];
+  if (retry) {
+    int sc = (int)std::min<int64_t>(p->hrb[0], p->sing_cap);  // a list holds each system at most once per pass
     const int first = sc;
     int32_t* in = p->sing_list;
     int32_t* out = p->sing_list + p->sing_cap;
@@ -389,16 +397,15 @@ hsm_status hsm_plan_compute_weights(hsm_plan p, hsm_prec prec, uint8_t* node_sta
       HSM_CUDA(p, cudaMemsetAsync(p->dev_count + 1, 0, sizeof(int), s));
       st = compute_rbf_weights_fp64_degree(p, in, sc, node_status, deg, out);
       if (st != HSM_OK) return st;
-      HSM_CUDA(p, cudaMemcpyAsync(&sc, p->dev_count + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+      HSM_CUDA(p, cudaMemcpyAsync(p->hrb, p->dev_count + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+      HSM_CUDA(p, cudaMemcpyAsync(p->hrb + 1, p->dev_flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
       HSM_CUDA(p, cudaStreamSynchronize(s));
-      sc = (int)std::min<int64_t>(sc, p->sing_cap);
+      sc = (int)std::min<int64_t>(p->hrb[0], p->sing_cap);
+      flags = (unsigned)p->hrb[1];
       std::swap(in, out);
     }
     p->n_reduced = first - sc;
   }
-  unsigned flags = 0;
-  HSM_CUDA(p, cudaMemcpyAsync(&flags, p->dev_flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
-  HSM_CUDA(p, cudaStreamSynchronize(s));
   p->weights_built = true;
   if ((flags | p->build_flags) & kDevSingular) return set_error(p, HSM_ESINGULAR, "some nodes have singular weight systems");
   return HSM_OK;

@@ -123,6 +123,7 @@ struct hsm_plan_s {
   // first (hsm_plan_set_checks, or HSM_CHECK_BOUNDS=1 at plan creation)
   bool checks = false;
   unsigned* check_flag = nullptr;  // device flag of the validation scan
+  int* hrb = nullptr;              // pinned host words for the weights call's read-backs
   hsm::Tuning tune;
   hsm_mlp mlp = nullptr;         // attached learned predictor (not owned)
   // batch validation of the learned weights: `gate_samples` stencils of the

@@ -152,6 +152,20 @@ struct LatticeMap {
 // Bounding box (ordered-bit keys) and lattice extents of the node set: each
 // thread keeps running extrema, the block reduces them with warp shuffles,
 // and one thread per block issues the global atomics.
+// Reduction identities of the build: status flags zero; bbox minima all-ones
+// and maxima zero (ordered-bit keys, interleaved [min_k, max_k]); lattice
+// extents minima 0x7f7f7f7f and maxima 0x80808080 (negative), counters zero.
+__global__ void k_build_init(unsigned* flags, unsigned long long* bbox, int* lat) {
+  const int t = threadIdx.x;
+  if (t < 4) flags[t] = 0u;
+  if (t < 2 * kMaxDim) bbox[t] = (t & 1) ? 0ull : ~0ull;
+  if (t < kMaxDim) {
+    lat[t] = 0x7f7f7f7f;
+    lat[kMaxDim + t] = (int)0x80808080u;
+  }
+  if (t < 4) lat[2 * kMaxDim + t] = 0;
+}
+
 __global__ void __launch_bounds__(256) k_bounds(const double* __restrict__ coords, int64_t N, int dim, double inv_h,
                                                 unsigned long long* bbox, int* lat_lo, int* lat_hi, int32_t* ijk,
                                                 uint8_t* on_lat) {
@@ -756,16 +770,10 @@ cudaError_t enqueue_build(hsm_plan p, cudaStream_t s, int qt, int* nk) {
 
   // ---- bounds and lattice coordinates
   int* lat = w.lat;  // [0,6): lattice extents, [6]: demoted, [7]: n_mon, [8]: n_rbf, [9]: flags
-  HSM_TRY(cudaMemsetAsync(p->dev_flags, 0, 4 * sizeof(unsigned), s));
-  // bbox: minima start at all-ones, maxima at zero (ordered-bit keys), stored
-  // interleaved [min_k, max_k]
-  HSM_TRY(cudaMemsetAsync(w.bbox, 0, 2 * kMaxDim * sizeof(unsigned long long), s));
-  for (int d = 0; d < kMaxDim; ++d) HSM_TRY(cudaMemsetAsync(w.bbox + 2 * d, 0xff, sizeof(unsigned long long), s));
-  // lattice extents: minima 0x7f7f7f7f, maxima 0x80808080 (negative) -- only
-  // their initial values matter to k_bounds; counters zero
-  HSM_TRY(cudaMemsetAsync(lat, 0x7f, kMaxDim * sizeof(int), s));
-  HSM_TRY(cudaMemsetAsync(lat + kMaxDim, 0x80, kMaxDim * sizeof(int), s));
-  HSM_TRY(cudaMemsetAsync(lat + 2 * kMaxDim, 0, 4 * sizeof(int), s));
+  // status flags, the bounding box and the lattice extents start from their
+  // reduction identities (one small kernel instead of eight memset nodes)
+  k_build_init<<<1, 32, 0, s>>>(p->dev_flags, w.bbox, lat);
+  ++k;
   k_bounds<<<grid, T, 0, s>>>(p->coords, N, dim, 1.0 / p->h, w.bbox, lat, lat + kMaxDim, w.ijk, w.on_lat);
   ++k;
   HSM_TRY(cudaGetLastError());
