@@ -466,11 +466,12 @@ __device__ __forceinline__ double sq_dist(const double* a, const double* b) {
 // for about fifty cells in a row.  A row of the window, and the top and bottom
 // rows of a ring, are runs of cells that are consecutive in the cell order,
 // so their nodes are one contiguous range of the sorted arrays: one pair of
-// range loads per row, and the node loads of a range are issued four at a
+// range loads per row, the next row's pair loaded while the current row is
+// scanned (window pass), and the node loads of a range issued BATCH at a
 // time before any of them is used.  The rows of a pass are dealt round-robin
 // to the quad's threads, and so are the single side cells of a ring.
 template <int DIM, int QT>
-__global__ void __launch_bounds__(32 * QT) k_knn(const double* __restrict__ coords, int64_t N,
+__global__ void __launch_bounds__(32 * QT, 1) k_knn(const double* __restrict__ coords, int64_t N,
                                              const uint8_t* __restrict__ is_boundary,
                                              const double* __restrict__ normals, double h,
                                              const double* __restrict__ spacing,
@@ -481,7 +482,10 @@ __global__ void __launch_bounds__(32 * QT) k_knn(const double* __restrict__ coor
                                              const uint8_t* __restrict__ sorted_bnd, int32_t* __restrict__ out_idx,
                                              unsigned* flags) {
   constexpr int RMAX = DIM == 2 ? 6 : 4;
-  constexpr int BATCH = 4;
+  // node loads in flight per thread: 8 when a query has several threads (a
+  // 2D window row of ~7 nodes in one round trip), 4 with one thread per query
+  // (fewer registers, more resident queries for large query counts)
+  constexpr int BATCH = QT == 1 ? 4 : 8;
   extern __shared__ unsigned char smem_raw[];
   const int B = blockDim.x;
   const int64_t nq = *nq_dev;  // the stride of out_idx
@@ -558,7 +562,44 @@ __global__ void __launch_bounds__(32 * QT) k_knn(const double* __restrict__ coor
       int turn = 0;  // row / side-cell counter; this thread takes turn % QT == sub
       const int xa = max(lo[0], 0), xb = min(hi[0], cg.g[0] - 1);
       const int zlo = DIM == 3 ? max(lo[DIM - 1], 0) : 0, zhi = DIM == 3 ? min(hi[DIM - 1], cg.g[DIM - 1] - 1) : 0;
-      for (int z = zlo; z <= zhi; ++z) {
+      if (window) {
+        // every row of the window is one node range; this thread's rows (i =
+        // sub, sub + QT, ...) with the next row's range loaded while the
+        // current one is scanned
+        const int ylo = max(lo[1], 0), yhi = min(hi[1], cg.g[1] - 1);
+        // (y, z) of this thread's next row, advanced QT rows at a time
+        int y = ylo + sub, z = zlo;
+        auto advance = [&](int& yy, int& zz) {
+          yy += QT;
+#pragma unroll 1
+          while (yy > yhi) {
+            yy -= yhi - ylo + 1;
+            ++zz;
+          }
+        };
+#pragma unroll 1
+        while (y > yhi && z <= zhi) {
+          y -= yhi - ylo + 1;
+          ++z;
+        }
+        int32_t a0 = 0, a1 = 0;
+        if (z <= zhi) {
+          const int64_t rb = ((int64_t)z * cg.g[1] + y) * cg.g[0];
+          a0 = start[rb + xa];
+          a1 = start[rb + xb + 1];
+        }
+        while (z <= zhi) {
+          const int32_t s0 = a0, s1 = a1;
+          advance(y, z);
+          if (z <= zhi) {
+            const int64_t rb = ((int64_t)z * cg.g[1] + y) * cg.g[0];
+            a0 = start[rb + xa];
+            a1 = start[rb + xb + 1];
+          }
+          scan(s0, s1);
+        }
+      }
+      for (int z = zlo; z <= zhi && !window; ++z) {
         const bool zedge = DIM == 3 && (z == lo[DIM - 1] || z == hi[DIM - 1]);
         for (int y = max(lo[1], 0); y <= min(hi[1], cg.g[1] - 1); ++y) {
           const int64_t row = ((int64_t)z * cg.g[1] + y) * cg.g[0];
