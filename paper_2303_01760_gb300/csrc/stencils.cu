@@ -152,6 +152,14 @@ struct LatticeMap {
 // Bounding box (ordered-bit keys) and lattice extents of the node set: each
 // thread keeps running extrema, the block reduces them with warp shuffles,
 // and one thread per block issues the global atomics.
+struct CellGrid;
+struct LatticeDense;
+// Cell grid of the bounding box, and the dense lattice map's extents (defined
+// below); run by the last block of k_bounds once every block's minima and
+// maxima are in.
+__device__ void grid_setup(const unsigned long long* bbox, int dim, double h, int64_t N, CellGrid* out);
+__device__ void lattice_setup(const int* lat_lo, const int* lat_hi, int dim, long long dense_cap, LatticeDense* desc);
+
 // Reduction identities of the build: status flags zero; bbox minima all-ones
 // and maxima zero (ordered-bit keys, interleaved [min_k, max_k]); lattice
 // extents minima 0x7f7f7f7f and maxima 0x80808080 (negative), counters zero.
@@ -163,12 +171,13 @@ __global__ void k_build_init(unsigned* flags, unsigned long long* bbox, int* lat
     lat[t] = 0x7f7f7f7f;
     lat[kMaxDim + t] = (int)0x80808080u;
   }
-  if (t < 4) lat[2 * kMaxDim + t] = 0;
+  if (t < 5) lat[2 * kMaxDim + t] = 0;  // counters, and k_bounds' arrival count
 }
 
 __global__ void __launch_bounds__(256) k_bounds(const double* __restrict__ coords, int64_t N, int dim, double inv_h,
                                                 unsigned long long* bbox, int* lat_lo, int* lat_hi, int32_t* ijk,
-                                                uint8_t* on_lat) {
+                                                uint8_t* on_lat, unsigned* arrivals, double h, long long dense_cap,
+                                                CellGrid* cg_out, LatticeDense* ld_out) {
   unsigned long long bmin[kMaxDim], bmax[kMaxDim];
   int lmin[kMaxDim], lmax[kMaxDim];
   for (int k = 0; k < kMaxDim; ++k) {
@@ -240,21 +249,27 @@ __global__ void __launch_bounds__(256) k_bounds(const double* __restrict__ coord
         atomicMax(&lat_hi[k], d);
       }
     }
+    // the last block to arrive sets up the cell grid and the lattice map
+    __threadfence();
+    if (atomicAdd(arrivals, 1u) == gridDim.x - 1) {
+      __threadfence();
+      grid_setup(bbox, dim, h, N, cg_out);
+      lattice_setup(lat_lo, lat_hi, dim, dense_cap, ld_out);
+    }
   }
 }
 
 
 // Dense map extents from the lattice extents; the dense array is used when
 // the lattice has at most dense_cap points.
-__global__ void k_lattice_setup(const int* __restrict__ lat_lo, const int* __restrict__ lat_hi, int dim,
-                                long long dense_cap, LatticeDense* desc) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__device__ void lattice_setup(const int* lat_lo, const int* lat_hi, int dim, long long dense_cap, LatticeDense* desc) {
   LatticeDense d;
   long long size = 1;
   bool fits = true;
   for (int k = 0; k < kMaxDim; ++k) {
-    d.lo[k] = k < dim ? lat_lo[k] : 0;
-    const long long e = k < dim ? (long long)lat_hi[k] - lat_lo[k] + 1 : 1;
+    const int lo = k < dim ? __ldcg(lat_lo + k) : 0, hi = k < dim ? __ldcg(lat_hi + k) : 0;
+    d.lo[k] = lo;
+    const long long e = k < dim ? (long long)hi - lo + 1 : 1;
     d.ext[k] = e > 0 && e < (1ll << 30) ? (int)e : 0;
     if (e <= 0) size = 0;  // no node on the lattice
     if (e >= (1ll << 30)) fits = false;
@@ -368,15 +383,13 @@ struct CellGrid {
 
 // Cell grid of the bounding box: cell edge h, enlarged by 1.5x until the
 // grid has at most 4N + 1024 cells (the scan buffers are sized for that).
-__global__ void k_grid_setup(const unsigned long long* __restrict__ bbox, int dim, double h, int64_t N,
-                             CellGrid* out) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__device__ void grid_setup(const unsigned long long* bbox, int dim, double h, int64_t N, CellGrid* out) {
   CellGrid cg;
   cg.dim = dim;
   double lo[kMaxDim], hi[kMaxDim];
   for (int k = 0; k < kMaxDim; ++k) {
-    lo[k] = k < dim ? from_ordered(bbox[2 * k]) : 0.0;
-    hi[k] = k < dim ? from_ordered(bbox[2 * k + 1]) : 0.0;
+    lo[k] = k < dim ? from_ordered(__ldcg(bbox + 2 * k)) : 0.0;
+    hi[k] = k < dim ? from_ordered(__ldcg(bbox + 2 * k + 1)) : 0.0;
     cg.lo[k] = lo[k];
   }
   double cell = h;
@@ -727,7 +740,7 @@ hsm_status alloc_build_ws(hsm_plan p) {
   w.hcap = cap;
   CellGrid* cg = nullptr;
   HSM_CUDA(p, dev_alloc(&w.bbox, 2 * kMaxDim, s));
-  HSM_CUDA(p, dev_alloc(&w.lat, 2 * kMaxDim + 4, s));
+  HSM_CUDA(p, dev_alloc(&w.lat, 2 * kMaxDim + 5, s));
   HSM_CUDA(p, dev_alloc(&w.ijk, (size_t)p->dim * N, s));
   HSM_CUDA(p, dev_alloc(&w.on_lat, N, s));
   HSM_CUDA(p, dev_alloc(&w.hkeys, cap, s));
@@ -815,7 +828,9 @@ cudaError_t enqueue_build(hsm_plan p, cudaStream_t s, int qt, int* nk) {
   // reduction identities (one small kernel instead of eight memset nodes)
   k_build_init<<<1, 32, 0, s>>>(p->dev_flags, w.bbox, lat);
   ++k;
-  k_bounds<<<grid, T, 0, s>>>(p->coords, N, dim, 1.0 / p->h, w.bbox, lat, lat + kMaxDim, w.ijk, w.on_lat);
+  k_bounds<<<grid, T, 0, s>>>(p->coords, N, dim, 1.0 / p->h, w.bbox, lat, lat + kMaxDim, w.ijk, w.on_lat,
+                              reinterpret_cast<unsigned*>(lat + 2 * kMaxDim + 4), p->h, (long long)(4 * N + 1024),
+                              static_cast<CellGrid*>(w.cgd), static_cast<LatticeDense*>(w.ldesc));
   ++k;
   HSM_TRY(cudaGetLastError());
   // lattice map: dense over the lattice's extents when they hold at most
@@ -827,11 +842,10 @@ cudaError_t enqueue_build(hsm_plan p, cudaStream_t s, int qt, int* nk) {
   lh.hash.vals = w.hvals;
   lh.dmap = w.dmap;
   lh.desc = static_cast<const LatticeDense*>(w.ldesc);
-  k_lattice_setup<<<1, 32, 0, s>>>(lat, lat + kMaxDim, dim, (long long)(4 * N + 1024), static_cast<LatticeDense*>(w.ldesc));
   k_lattice_clear<<<grid, T, 0, s>>>(lh, w.hcap);
   if (dim == 2) k_lattice_insert<2><<<grid, T, 0, s>>>(w.ijk, w.on_lat, N, lh);
   else k_lattice_insert<3><<<grid, T, 0, s>>>(w.ijk, w.on_lat, N, lh);
-  k += 3;
+  k += 2;
   HSM_TRY(cudaGetLastError());
 
   // ---- classification
@@ -863,13 +877,12 @@ cudaError_t enqueue_build(hsm_plan p, cudaStream_t s, int qt, int* nk) {
 
   // ---- kNN for the RBF-FD group
   const int64_t ncell_max = 4 * N + 1024;
-  CellGrid* cgd = static_cast<CellGrid*>(w.cgd);
-  k_grid_setup<<<1, 32, 0, s>>>(w.bbox, dim, p->h, N, cgd);
+  CellGrid* cgd = static_cast<CellGrid*>(w.cgd);  // set up by k_bounds
   HSM_TRY(cudaMemsetAsync(w.ccount, 0, ncell_max * sizeof(int32_t), s));
   k_cell_count<<<grid, T, 0, s>>>(p->coords, N, cgd, w.cell_of, w.ccount);
   HSM_TRY(cudaGetLastError());
   HSM_TRY(exclusive_scan_i32(w.ccount, w.cstart, ncell_max, s, w.scan_ws));
-  k += 5;
+  k += 4;
   HSM_TRY(cudaMemsetAsync(w.ccount, 0, ncell_max * sizeof(int32_t), s));
   k_cell_scatter<<<grid, T, 0, s>>>(p->coords, p->is_boundary, N, dim, w.cell_of, w.cstart, w.ccount, w.sorted_id,
                                     w.sorted_xyz, w.sorted_bnd);
