@@ -209,7 +209,10 @@ inline int num_sms() {
 // ---- scan.cu -------------------------------------------------------------
 // Exclusive prefix sum of in[0..n) (int32 counts) into out[0..n], out[n] = total.
 // ws: scratch of scan_scratch(n) ints, or nullptr to allocate one.
-cudaError_t exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s, int32_t* ws = nullptr);
+// out[n] receives the total; zero_in (optional, may alias in): cleared as read.
+cudaError_t exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s, int32_t* ws = nullptr,
+                               int32_t* zero_in = nullptr);
+int scan_kernels(int64_t n);  // kernels one scan of n items launches
 // List of indices i (ascending) with key[i] == want; count written to *count_dev.
 cudaError_t select_indices(const uint8_t* key, uint8_t want, int64_t n, int32_t* out_list,
                            int32_t* out_pos, int* count_dev, cudaStream_t s, int32_t* ws = nullptr);

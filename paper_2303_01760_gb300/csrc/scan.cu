@@ -1,5 +1,7 @@
-// Device-wide exclusive scan and stream compaction (three passes: block sums,
-// scan of the block sums in one block, block-local scan plus offset).
+// Device-wide exclusive scan and stream compaction: block sums, then a
+// block-local scan plus the block's offset (the offsets come from a scan of
+// the block sums in one block, or, for at most 1,024 blocks, from each block
+// summing its predecessors' sums itself).
 #include "common.cuh"
 
 namespace hsm {
@@ -94,9 +96,45 @@ __global__ void k_block_write(F f, int64_t n, const int32_t* sums, W w) {
   }
 }
 
+// Second pass with the offsets of the earlier blocks summed in the block
+// itself (no separate scan of the block sums): nb reads per block, so it is
+// used when there are at most kFoldBlocks blocks.  The last block writes the
+// totals.
+constexpr int kFoldBlocks = 1024;
+template <typename F, typename W>
+__global__ void k_block_write_fold(F f, int64_t n, const int32_t* sums, W w, int32_t* grand, int32_t* rest) {
+  __shared__ int before, total;
+  int part = 0;
+  for (int i = threadIdx.x; i < (int)blockIdx.x; i += blockDim.x) part += sums[i];
+  block_excl_scan(part, &before);
+  int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  int vals[kScanItems];
+  int v = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    vals[k] = (base + k < n) ? f(base + k) : 0;
+    v += vals[k];
+  }
+  int e = block_excl_scan(v, &total) + before;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    if (base + k < n) w(base + k, e, vals[k]);
+    e += vals[k];
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+    if (grand) *grand = before + total;
+    if (rest) *rest = (int32_t)(n - (before + total));
+  }
+}
+
+// zero (optional): the counts, cleared as they are consumed
 struct WriteExcl {
   int32_t* out;
-  __device__ void operator()(int64_t i, int e, int) const { out[i] = e; }
+  int32_t* zero;
+  __device__ void operator()(int64_t i, int e, int) const {
+    out[i] = e;
+    if (zero) zero[i] = 0;
+  }
 };
 // Stable partition by a 0/1 key: e counts the selected items before i, so an
 // unselected item goes to place i - e of the second list.
@@ -131,8 +169,12 @@ cudaError_t run_scan(F f, W w, int64_t n, int32_t* grand, cudaStream_t s, int32_
     if (e != cudaSuccess) return e;
   }
   k_block_sums<<<nb, kScanThreads, 0, s>>>(f, n, sums);
-  k_scan_sums<<<1, kScanThreads, 0, s>>>(sums, nb, grand, n, rest);
-  k_block_write<<<nb, kScanThreads, 0, s>>>(f, n, sums, w);
+  if (nb <= kFoldBlocks) {
+    k_block_write_fold<<<nb, kScanThreads, 0, s>>>(f, n, sums, w, grand, rest);
+  } else {
+    k_scan_sums<<<1, kScanThreads, 0, s>>>(sums, nb, grand, n, rest);
+    k_block_write<<<nb, kScanThreads, 0, s>>>(f, n, sums, w);
+  }
   e = cudaGetLastError();
   if (!ws) dev_free(&sums, s);
   return e;
@@ -140,9 +182,12 @@ cudaError_t run_scan(F f, W w, int64_t n, int32_t* grand, cudaStream_t s, int32_
 
 }  // namespace
 
-cudaError_t exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s, int32_t* ws) {
-  return run_scan(CountsIn{in}, WriteExcl{out}, n, out + n, s, ws);
+cudaError_t exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s, int32_t* ws,
+                               int32_t* zero_in) {
+  return run_scan(CountsIn{in}, WriteExcl{out, zero_in}, n, out + n, s, ws);
 }
+
+int scan_kernels(int64_t n) { return ceil_div(n > 0 ? n : 1, kScanTile) <= kFoldBlocks ? 2 : 3; }
 
 cudaError_t select_indices(const uint8_t* key, uint8_t want, int64_t n, int32_t* out_list,
                            int32_t* out_pos, int* count_dev, cudaStream_t s, int32_t* ws) {

@@ -858,7 +858,7 @@ cudaError_t enqueue_build(hsm_plan p, cudaStream_t s, int qt, int* nk) {
 
   // ---- group lists (ascending node ids) and positions
   HSM_TRY(partition_indices(p->kind, 0, N, p->mon.nodes, p->rbf.nodes, p->pos, counts, counts + 1, s, w.scan_ws));
-  k += 3;
+  k += scan_kernels(N);
   // MON stencils on a side branch of the graph, joined before the read-back
   HSM_TRY(cudaEventRecord(w.ev_fork, s));
   HSM_TRY(cudaStreamWaitEvent(w.side, w.ev_fork, 0));
@@ -881,9 +881,9 @@ cudaError_t enqueue_build(hsm_plan p, cudaStream_t s, int qt, int* nk) {
   HSM_TRY(cudaMemsetAsync(w.ccount, 0, ncell_max * sizeof(int32_t), s));
   k_cell_count<<<grid, T, 0, s>>>(p->coords, N, cgd, w.cell_of, w.ccount);
   HSM_TRY(cudaGetLastError());
-  HSM_TRY(exclusive_scan_i32(w.ccount, w.cstart, ncell_max, s, w.scan_ws));
-  k += 4;
-  HSM_TRY(cudaMemsetAsync(w.ccount, 0, ncell_max * sizeof(int32_t), s));
+  // the counts are cleared as the scan consumes them: the scatter's cursors
+  HSM_TRY(exclusive_scan_i32(w.ccount, w.cstart, ncell_max, s, w.scan_ws, w.ccount));
+  k += 1 + scan_kernels(ncell_max);
   k_cell_scatter<<<grid, T, 0, s>>>(p->coords, p->is_boundary, N, dim, w.cell_of, w.cstart, w.ccount, w.sorted_id,
                                     w.sorted_xyz, w.sorted_bnd);
   ++k;
