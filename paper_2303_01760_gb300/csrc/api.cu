@@ -207,6 +207,7 @@ static void free_group(Group& g, cudaStream_t s) {
   dev_free(&g.w64, s);
   dev_free(&g.w32, s);
   g.count = 0;
+  g.w64_cap = 0;
 }
 
 static void free_plan_device(hsm_plan p) {
@@ -270,10 +271,10 @@ hsm_status hsm_plan_build_stencils(hsm_plan p) {
   // weights of an earlier build are stale; stencil arrays and the build
   // workspace persist across builds
   if (p->mon.w64 == p->ws.mon_w64) p->mon.w64 = nullptr;  // owned by the build workspace
-  for (Group* g : {&p->mon, &p->rbf}) {
-    dev_free(&g->w64, s);
-    dev_free(&g->w32, s);
-  }
+  dev_free(&p->mon.w64, s);
+  p->mon.w64_cap = 0;
+  // the RBF-FD weight array is kept and reused while it is large enough
+  for (Group* g : {&p->mon, &p->rbf}) dev_free(&g->w32, s);
   p->stencils_built = p->weights_built = false;
   // upper-triangle pair table and monomial exponents for the RBF-FD kernels,
   // uploaded once per plan from host copies the plan keeps
@@ -306,17 +307,29 @@ hsm_status hsm_plan_compute_weights(hsm_plan p, hsm_prec prec, uint8_t* node_sta
   }
   cudaStream_t s = p->stream;
   if (!p->mon.w64) HSM_CUDA(p, dev_alloc(&p->mon.w64, (size_t)p->nops * p->mon.width * p->mon.count, s));
-  if (!p->rbf.w64) HSM_CUDA(p, dev_alloc(&p->rbf.w64, (size_t)p->nops * p->rbf.width * p->rbf.count, s));
+  {
+    const int64_t need = (int64_t)p->nops * p->rbf.width * p->rbf.count;
+    if (!p->rbf.w64 || p->rbf.w64_cap < need) {
+      dev_free(&p->rbf.w64, s);
+      p->rbf.w64_cap = 0;
+      HSM_CUDA(p, dev_alloc(&p->rbf.w64, (size_t)need, s));
+      p->rbf.w64_cap = need;
+    }
+  }
   dev_free(&p->mon.w32, s);
   dev_free(&p->rbf.w32, s);
-  HSM_CUDA(p, cudaMemsetAsync(p->dev_flags, 0, sizeof(unsigned), s));
+  // the status words: cleared by the stencil build for the first weights call
+  // after it, here for later ones
+  const bool fresh = p->counters_fresh;
+  p->counters_fresh = false;
+  if (!fresh) HSM_CUDA(p, cudaMemsetAsync(p->dev_flags, 0, sizeof(unsigned), s));
   if (p->m >= 2 && p->sing_cap < p->rbf.count) {
     dev_free(&p->sing_list, s);
     p->sing_cap = 0;
     HSM_CUDA(p, dev_alloc(&p->sing_list, 2 * (size_t)p->rbf.count, s));
     p->sing_cap = p->rbf.count;
   }
-  HSM_CUDA(p, cudaMemsetAsync(p->dev_count + 1, 0, sizeof(int), s));
+  if (!fresh) HSM_CUDA(p, cudaMemsetAsync(p->dev_count + 1, 0, sizeof(int), s));
   p->n_reduced = 0;
   // a phase this call does not run reports 0 in hsm_plan_profile
   p->ev_used[HSM_PHASE_MON] = p->ev_used[HSM_PHASE_RBF] = false;

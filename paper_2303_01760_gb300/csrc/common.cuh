@@ -33,6 +33,7 @@ struct Group {
   int32_t* idx = nullptr;    // [width][count] stencil node ids (index-major)
   double* w64 = nullptr;     // [nops][width][count]
   float* w32 = nullptr;      // [nops][width][count]
+  int64_t w64_cap = 0;       // doubles allocated at w64 (kept across builds)
 };
 
 struct Tuning {
@@ -124,6 +125,7 @@ struct hsm_plan_s {
   bool checks = false;
   unsigned* check_flag = nullptr;  // device flag of the validation scan
   int* hrb = nullptr;              // pinned host words for the weights call's read-backs
+  bool counters_fresh = false;     // the build cleared the weights call's status words
   hsm::Tuning tune;
   hsm_mlp mlp = nullptr;         // attached learned predictor (not owned)
   // batch validation of the learned weights: `gate_samples` stencils of the

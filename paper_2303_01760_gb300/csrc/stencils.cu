@@ -160,12 +160,14 @@ struct LatticeDense;
 __device__ void grid_setup(const unsigned long long* bbox, int dim, double h, int64_t N, CellGrid* out);
 __device__ void lattice_setup(const int* lat_lo, const int* lat_hi, int dim, long long dense_cap, LatticeDense* desc);
 
-// Reduction identities of the build: status flags zero; bbox minima all-ones
+// Reduction identities of the build: status flags and the weights call's
+// counters zero; bbox minima all-ones
 // and maxima zero (ordered-bit keys, interleaved [min_k, max_k]); lattice
 // extents minima 0x7f7f7f7f and maxima 0x80808080 (negative), counters zero.
-__global__ void k_build_init(unsigned* flags, unsigned long long* bbox, int* lat) {
+__global__ void k_build_init(unsigned* flags, int* counts, unsigned long long* bbox, int* lat) {
   const int t = threadIdx.x;
   if (t < 4) flags[t] = 0u;
+  if (t < 4) counts[t] = 0;
   if (t < 2 * kMaxDim) bbox[t] = (t & 1) ? 0ull : ~0ull;
   if (t < kMaxDim) {
     lat[t] = 0x7f7f7f7f;
@@ -826,7 +828,7 @@ cudaError_t enqueue_build(hsm_plan p, cudaStream_t s, int qt, int* nk) {
   int* lat = w.lat;  // [0,6): lattice extents, [6]: demoted, [7]: n_mon, [8]: n_rbf, [9]: flags
   // status flags, the bounding box and the lattice extents start from their
   // reduction identities (one small kernel instead of eight memset nodes)
-  k_build_init<<<1, 32, 0, s>>>(p->dev_flags, w.bbox, lat);
+  k_build_init<<<1, 32, 0, s>>>(p->dev_flags, p->dev_count, w.bbox, lat);
   ++k;
   k_bounds<<<grid, T, 0, s>>>(p->coords, N, dim, 1.0 / p->h, w.bbox, lat, lat + kMaxDim, w.ijk, w.on_lat,
                               reinterpret_cast<unsigned*>(lat + 2 * kMaxDim + 4), p->h, (long long)(4 * N + 1024),
@@ -973,6 +975,7 @@ hsm_status build_stencils(hsm_plan p) {
   }
   HSM_CUDA(p, cudaGraphLaunch(w.graph, s));
   p->launches += w.graph_kernels;
+  p->counters_fresh = true;  // k_build_init cleared the weights call's status words
   HSM_CUDA(p, cudaStreamSynchronize(s));
   const int* rb = w.readback;
   p->n_demoted = rb[0];
