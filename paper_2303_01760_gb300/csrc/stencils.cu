@@ -748,6 +748,10 @@ hsm_status alloc_build_ws(hsm_plan p) {
   HSM_CUDA(p, dev_alloc(&w.hkeys, cap, s));
   HSM_CUDA(p, dev_alloc(&w.hvals, cap, s));
   HSM_CUDA(p, dev_alloc(&w.dmap, 4 * N + 1024, s));
+  // empty lattice map (kEmpty is the byte 0x7f repeated; empty hash keys are all ones)
+  HSM_CUDA(p, cudaMemsetAsync(w.dmap, 0x7f, (size_t)(4 * N + 1024) * sizeof(int32_t), s));
+  HSM_CUDA(p, cudaMemsetAsync(w.hkeys, 0xff, (size_t)cap * sizeof(unsigned long long), s));
+  HSM_CUDA(p, cudaMemsetAsync(w.hvals, 0x7f, (size_t)cap * sizeof(int32_t), s));
   {
     LatticeDense* ld = nullptr;
     HSM_CUDA(p, dev_alloc(&ld, 1, s));
@@ -844,10 +848,11 @@ cudaError_t enqueue_build(hsm_plan p, cudaStream_t s, int qt, int* nk) {
   lh.hash.vals = w.hvals;
   lh.dmap = w.dmap;
   lh.desc = static_cast<const LatticeDense*>(w.ldesc);
-  k_lattice_clear<<<grid, T, 0, s>>>(lh, w.hcap);
+  // the map starts empty: cleared once at allocation and by every build
+  // after its last reader (the MON stencils, on the side branch)
   if (dim == 2) k_lattice_insert<2><<<grid, T, 0, s>>>(w.ijk, w.on_lat, N, lh);
   else k_lattice_insert<3><<<grid, T, 0, s>>>(w.ijk, w.on_lat, N, lh);
-  k += 2;
+  ++k;
   HSM_TRY(cudaGetLastError());
 
   // ---- classification
@@ -866,7 +871,9 @@ cudaError_t enqueue_build(hsm_plan p, cudaStream_t s, int qt, int* nk) {
   HSM_TRY(cudaStreamWaitEvent(w.side, w.ev_fork, 0));
   if (dim == 2) k_mon_stencil<2><<<grid, T, 0, w.side>>>(w.ijk, p->mon.nodes, counts, N, lh, p->mon.idx);
   else k_mon_stencil<3><<<grid, T, 0, w.side>>>(w.ijk, p->mon.nodes, counts, N, lh, p->mon.idx);
-  ++k;
+  // the map's last reader: empty it for the next build, off the critical path
+  k_lattice_clear<<<grid, T, 0, w.side>>>(lh, w.hcap);
+  k += 2;
   HSM_TRY(cudaGetLastError());
   // MON weights on the same branch (unless the plan solves both groups in the
   // grouped weights launch): they need only the MON stencils and run beside
