@@ -316,32 +316,29 @@ __global__ void k_lattice_insert(const int32_t* __restrict__ ijk, const uint8_t*
 // kind = 0 (MON) when the node is regular, interior, owns its lattice point and
 // has all 2d lattice neighbours; 1 (RBF-FD) otherwise.
 template <int DIM>
-__global__ void k_classify(const int32_t* __restrict__ ijk, const uint8_t* __restrict__ on_lat,
-                           const uint8_t* __restrict__ is_regular, const uint8_t* __restrict__ is_boundary,
-                           int64_t N, LatticeMap g, uint8_t* kind, int* n_demoted) {
-  g.load();
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    bool reg = is_regular[i] != 0;
-    bool mon = reg && on_lat[i] && !(is_boundary && is_boundary[i]);
-    if (mon) {
-      int q[DIM];
+__device__ __forceinline__ void classify_node(const int32_t* __restrict__ ijk, const uint8_t* __restrict__ on_lat,
+                                              const uint8_t* __restrict__ is_regular,
+                                              const uint8_t* __restrict__ is_boundary, int64_t N,
+                                              const LatticeMap& g, int64_t i, uint8_t* kind, int* n_demoted) {
+  bool reg = is_regular[i] != 0;
+  bool mon = reg && on_lat[i] && !(is_boundary && is_boundary[i]);
+  if (mon) {
+    int q[DIM];
 #pragma unroll
-      for (int k = 0; k < DIM; ++k) q[k] = ijk[k * N + i];
-      mon = g.find<DIM>(q) == (int32_t)i;
+    for (int k = 0; k < DIM; ++k) q[k] = ijk[k * N + i];
+    mon = g.find<DIM>(q) == (int32_t)i;
 #pragma unroll
-      for (int k = 0; k < DIM; ++k) {
+    for (int k = 0; k < DIM; ++k) {
 #pragma unroll
-        for (int s = -1; s <= 1; s += 2) {
-          q[k] += s;
-          mon = mon && g.find<DIM>(q) != kEmpty;
-          q[k] -= s;
-        }
+      for (int s = -1; s <= 1; s += 2) {
+        q[k] += s;
+        mon = mon && g.find<DIM>(q) != kEmpty;
+        q[k] -= s;
       }
     }
-    kind[i] = mon ? 0 : 1;
-    if (reg && !mon) atomicAdd(n_demoted, 1);
   }
+  kind[i] = mon ? 0 : 1;
+  if (reg && !mon) atomicAdd(n_demoted, 1);
 }
 
 // MON stencils; the group size is read on the device.
@@ -409,13 +406,23 @@ __device__ void grid_setup(const unsigned long long* bbox, int dim, double h, in
   *out = cg;
 }
 
-__global__ void k_cell_count(const double* __restrict__ coords, int64_t N, const CellGrid* __restrict__ cgp,
-                             int32_t* cell_of, int32_t* counts) {
+// One pass over the nodes: the MON / RBF-FD classification (the lattice map
+// is complete) and each node's cell with the per-cell counts (the cell grid
+// is set up by k_bounds).
+template <int DIM>
+__global__ void k_classify_count(const int32_t* __restrict__ ijk, const uint8_t* __restrict__ on_lat,
+                                 const uint8_t* __restrict__ is_regular, const uint8_t* __restrict__ is_boundary,
+                                 int64_t N, LatticeMap g, uint8_t* kind, int* n_demoted,
+                                 const double* __restrict__ coords, const CellGrid* __restrict__ cgp,
+                                 int32_t* cell_of, int32_t* counts) {
+  g.load();
   const CellGrid cg = *cgp;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
+    classify_node<DIM>(ijk, on_lat, is_regular, is_boundary, N, g, i, kind, n_demoted);
     int64_t l = 0;
-    for (int k = cg.dim - 1; k >= 0; --k) l = l * cg.g[k] + cg.cell_of(coords[k * N + i], k);
+#pragma unroll
+    for (int k = DIM - 1; k >= 0; --k) l = l * cg.g[k] + cg.cell_of(coords[k * N + i], k);
     cell_of[i] = (int32_t)l;
     atomicAdd(&counts[l], 1);
   }
@@ -848,6 +855,10 @@ cudaError_t enqueue_build(hsm_plan p, cudaStream_t s, int qt, int* nk) {
   lh.hash.vals = w.hvals;
   lh.dmap = w.dmap;
   lh.desc = static_cast<const LatticeDense*>(w.ldesc);
+  // the cell counts start at zero (the previous build's scatter left its
+  // cursors there)
+  const int64_t ncell_max = 4 * N + 1024;
+  HSM_TRY(cudaMemsetAsync(w.ccount, 0, ncell_max * sizeof(int32_t), s));
   // the map starts empty: cleared once at allocation and by every build
   // after its last reader (the MON stencils, on the side branch)
   if (dim == 2) k_lattice_insert<2><<<grid, T, 0, s>>>(w.ijk, w.on_lat, N, lh);
@@ -858,8 +869,13 @@ cudaError_t enqueue_build(hsm_plan p, cudaStream_t s, int qt, int* nk) {
   // ---- classification
   int* d_demoted = lat + 2 * kMaxDim;
   int* counts = lat + 2 * kMaxDim + 1;
-  if (dim == 2) k_classify<2><<<grid, T, 0, s>>>(w.ijk, w.on_lat, p->is_regular, p->is_boundary, N, lh, p->kind, d_demoted);
-  else k_classify<3><<<grid, T, 0, s>>>(w.ijk, w.on_lat, p->is_regular, p->is_boundary, N, lh, p->kind, d_demoted);
+  CellGrid* cgd = static_cast<CellGrid*>(w.cgd);  // set up by k_bounds
+  if (dim == 2)
+    k_classify_count<2><<<grid, T, 0, s>>>(w.ijk, w.on_lat, p->is_regular, p->is_boundary, N, lh, p->kind, d_demoted,
+                                           p->coords, cgd, w.cell_of, w.ccount);
+  else
+    k_classify_count<3><<<grid, T, 0, s>>>(w.ijk, w.on_lat, p->is_regular, p->is_boundary, N, lh, p->kind, d_demoted,
+                                           p->coords, cgd, w.cell_of, w.ccount);
   ++k;
   HSM_TRY(cudaGetLastError());
 
@@ -885,14 +901,9 @@ cudaError_t enqueue_build(hsm_plan p, cudaStream_t s, int qt, int* nk) {
   HSM_TRY(cudaEventRecord(w.ev_join, w.side));
 
   // ---- kNN for the RBF-FD group
-  const int64_t ncell_max = 4 * N + 1024;
-  CellGrid* cgd = static_cast<CellGrid*>(w.cgd);  // set up by k_bounds
-  HSM_TRY(cudaMemsetAsync(w.ccount, 0, ncell_max * sizeof(int32_t), s));
-  k_cell_count<<<grid, T, 0, s>>>(p->coords, N, cgd, w.cell_of, w.ccount);
-  HSM_TRY(cudaGetLastError());
   // the counts are cleared as the scan consumes them: the scatter's cursors
   HSM_TRY(exclusive_scan_i32(w.ccount, w.cstart, ncell_max, s, w.scan_ws, w.ccount));
-  k += 1 + scan_kernels(ncell_max);
+  k += scan_kernels(ncell_max);
   k_cell_scatter<<<grid, T, 0, s>>>(p->coords, p->is_boundary, N, dim, w.cell_of, w.cstart, w.ccount, w.sorted_id,
                                     w.sorted_xyz, w.sorted_bnd);
   ++k;
