@@ -580,11 +580,11 @@ def run_stepper(hsm, ns, plan, d, dev, stream, args, steps=30):
     st.close()
     iters = float(np.mean(its))
     us_it = ms * 1e3 / steps / max(iters, 1e-9)
-    wk = krylov_iteration_work(info, ns.N)
+    wk = krylov_iteration_work(info, ns.N, gmres=True, j_avg=min(iters, 30.0) / 2.0)
     peak_h, src_h = hbm_peak()
     return {"workload": "2D irregular domain (the timed node set), Ra=1e6, Pr=0.71, dt=0.1h^2/2, "
-                        "bordered pressure by BiCGSTAB to 1e-10, right-preconditioned by an aggregation-multigrid "
-                        "V(2,2)-cycle",
+                        "bordered pressure by GMRES(30) to 1e-10, right-preconditioned by an aggregation-multigrid "
+                        "V(2,2)-cycle (one cycle per iteration)",
             "steps": steps, "ms_per_step": ms / steps, "node_steps_per_s": ns.N * steps / (ms * 1e-3),
             "krylov_iters_per_step": iters, "first_steps_iters": it0,
             "converged": code == 0, "T_finite": bool(torch.isfinite(T).all()),
@@ -593,8 +593,9 @@ def run_stepper(hsm, ns, plan, d, dev, stream, args, steps=30):
                                            "kernels_per_iter", "tail_ms_10_cycles", "fused_ms_10_cycles",
                                            "persistent_ms_10_cycles", "level_rows", "level_entries")},
             "roofline": {"bound": "latency", "unit": "GB/s",
-                         "note": "per Krylov iteration (two V(2,2)-cycles, two operator applications, the "
-                                 "vector updates): algorithmic bytes and FP64 flops from the level sizes, over "
+                         "note": "per GMRES iteration (one V(2,2)-cycle, one operator application, the "
+                                 "orthogonalisation against the basis so far): algorithmic bytes and FP64 flops "
+                                 "from the level sizes, over "
                                  "ms_per_step / krylov_iters_per_step (the step's other kernels included); the "
                                  "working set (%.0f MB) stays in L2, so neither HBM nor the FP64 pipe bounds it"
                                  % (wk["working_set_bytes"] / 1e6),
@@ -604,8 +605,8 @@ def run_stepper(hsm, ns, plan, d, dev, stream, args, steps=30):
                          "fp64_gflops": wk["flops"] / (us_it * 1e3)}}
 
 
-def krylov_iteration_work(info, N):
-    """Algorithmic work of one BiCGSTAB iteration with the multigrid
+def krylov_iteration_work(info, N, gmres=False, j_avg=0.0):
+    """Algorithmic work of one Krylov iteration with the multigrid
     preconditioner, from the rows R and stored matrix entries Z of each
     level (12 bytes per entry: a 4-byte column and an 8-byte value; 8 bytes
     per vector element read or written).  Per non-coarsest level and cycle:
@@ -613,9 +614,13 @@ def krylov_iteration_work(info, N):
     12Rc bytes, 2Z + 2R flops; the two post-smoothing sweeps 12Z + 36R + 8Rc
     and 12Z + 32R bytes, 4Z + 4R and 2Z + 3R flops (Rc: rows of the next
     level).  Coarsest level: the dense m x m solve, 8m^2 + 16m bytes, 2m^2
-    flops.  Two cycles, two applications of the fine bordered operator
-    (12Z0 + 16N bytes, 2Z0 + 2N flops each) and the vector updates and dot
-    products (20 vector passes, 160N bytes, 22N flops)."""
+    flops.  BiCGSTAB: two cycles, two applications of the fine bordered
+    operator (12Z0 + 16N bytes, 2Z0 + 2N flops each) and the vector updates
+    and dot products (20 vector passes, 160N bytes, 22N flops).  GMRES: one
+    cycle, one application, and against a basis of j + 1 vectors (j_avg on
+    average) the dot products and the update (each (j + 1) 8N + 16N bytes,
+    2 (j + 1) N flops), the scaling (24N bytes, N flops) and the copy of the
+    cycle's output into the basis (16N bytes)."""
     R = list(info["level_rows"])
     Z = list(info["level_entries"])
     L = len(R)
@@ -628,9 +633,14 @@ def krylov_iteration_work(info, N):
         m = R[-1]
         by += 8 * m * m + 16 * m
         fl += 2 * m * m
-    by, fl = 2 * by, 2 * fl
-    by += 2 * (12 * Z[0] + 16 * N) + 160 * N if L else 0
-    fl += 2 * (2 * Z[0] + 2 * N) + 22 * N if L else 0
+    if gmres:
+        jb = j_avg + 1.0
+        by += (12 * Z[0] + 16 * N) + 2 * (jb * 8 * N + 16 * N) + 24 * N + 16 * N if L else 0
+        fl += (2 * Z[0] + 2 * N) + 2 * (2 * jb * N) + N if L else 0
+    else:
+        by, fl = 2 * by, 2 * fl
+        by += 2 * (12 * Z[0] + 16 * N) + 160 * N if L else 0
+        fl += 2 * (2 * Z[0] + 2 * N) + 22 * N if L else 0
     ws = sum(12 * z + 48 * r for z, r in zip(Z, R)) + 12 * 8 * N
     return {"bytes": by, "flops": fl, "working_set_bytes": ws}
 
@@ -1057,7 +1067,8 @@ def run_kernels(args):
         bc = torch.from_numpy(ns.bc).to(dev)
         Tbc = torch.from_numpy(ns.T_bc).to(dev)
         st = hsm.Stepper(plan, 1e6, 0.71, 0.1 * ns.h * ns.h / 2.0, ns.T_ref, bc, Tbc, nrm, krylov_tol=1e-10,
-                         krylov_max_it=4000, guess_order=args.guess_order, mg_sweeps=args.mg_sweeps)
+                         krylov_max_it=4000, guess_order=args.guess_order, mg_sweeps=args.mg_sweeps,
+                         krylov=args.krylov)
         v = torch.zeros((2, ns.N), dtype=torch.float64, device=dev)
         T = torch.where(bc == 1, Tbc, torch.zeros_like(Tbc)).contiguous()
         p = torch.zeros(ns.N, dtype=torch.float64, device=dev)
@@ -1613,6 +1624,7 @@ def main():
     ap.add_argument("--refined-steps", type=int, default=500, help="with --refined")
     ap.add_argument("--sweep", action="store_true", help="scattered-fraction sweep (5..100 %%), m = 2 and 4")
     ap.add_argument("--sweep-steps", type=int, default=100, help="with --sweep: explicit steps timed per set")
+    ap.add_argument("--krylov", type=int, default=0, help="with --kernels --stepper: 0 BiCGSTAB, 1 GMRES(30)")
     ap.add_argument("--mg-sweeps", type=int, default=0, help="with --kernels --stepper: 1 or 2 Jacobi sweeps "
                     "each way in the multigrid cycle (0: the library default)")
     ap.add_argument("--guess-order", type=int, default=0, help="with --kernels --stepper: pressure initial "

@@ -326,6 +326,13 @@ typedef struct {
                             pre-sweep from zero is x = w f and each level runs
                             two kernels per cycle (the other cycle shapes then
                             do not apply)                                      */
+  int krylov;            /* with HSM_PRECOND_AMG: HSM_KRYLOV_GMRES (0, default),
+                            GMRES restarted every 30 iterations, right-
+                            preconditioned by one multigrid cycle per
+                            iteration; HSM_KRYLOV_BICGSTAB: BiCGSTAB, two
+                            cycles per iteration.  Both stop at the same
+                            relative residual.  The Jacobi preconditioner
+                            always runs BiCGSTAB.                              */
 } hsm_phys;
 
 /* Right preconditioner of the pressure BiCGSTAB.  AMG: an aggregation
@@ -334,6 +341,7 @@ typedef struct {
  * dense solve of the coarsest bordered system), built once by
  * hsm_stepper_create.  JACOBI: the inverse diagonal.                       */
 enum { HSM_PRECOND_AMG = 0, HSM_PRECOND_JACOBI = 1 };
+enum { HSM_KRYLOV_GMRES = 0, HSM_KRYLOV_BICGSTAB = 1 };
 
 /* Creates a stepper on a plan whose weights exist and whose op mask holds
  * every first derivative and the Laplacian.  Copies *phys (the device arrays

@@ -38,7 +38,7 @@ class hsm_phys(C.Structure):
                 ("bc", _p), ("T_bc", _p), ("normals", _p), ("krylov_tol", C.c_double),
                 ("krylov_max_it", C.c_int), ("precond", C.c_int), ("guess_order", C.c_int),
                 ("apply_f32", C.c_int), ("mg_tail_from", C.c_int), ("mg_fused_from", C.c_int),
-                ("mg_persistent", C.c_int), ("mg_sweeps", C.c_int)]
+                ("mg_persistent", C.c_int), ("mg_sweeps", C.c_int), ("krylov", C.c_int)]
 
 
 (HSM_OK, HSM_EINVAL, HSM_ENOMEM, HSM_ECUDA, HSM_ESINGULAR, HSM_ENOTCONV, HSM_ETIMEOUT, HSM_EBOUNDS,
@@ -47,6 +47,8 @@ HSM_FAULT_NONE, HSM_FAULT_HOLD_MLP_LOADS, HSM_FAULT_STENCIL_INDEX = 0, 1, 2
 
 HSM_PRECOND_AMG = 0
 HSM_PRECOND_JACOBI = 1
+HSM_KRYLOV_GMRES = 0
+HSM_KRYLOV_BICGSTAB = 1
 
 
 _SIGS = {
@@ -409,13 +411,13 @@ class Stepper:
 
     def __init__(self, plan, Ra, Pr, dt, T_ref, bc, T_bc, normals, krylov_tol=1e-12, krylov_max_it=2000,
                  precond=HSM_PRECOND_AMG, guess_order=0, apply_f32=False, mg_tail_from=0, mg_fused_from=0,
-                 mg_persistent=0, mg_sweeps=0):
+                 mg_persistent=0, mg_sweeps=0, krylov=0):
         self.plan = plan
         self._keep = (bc, T_bc, normals)
         self.phys = hsm_phys(float(Ra), float(Pr), float(dt), float(T_ref), ptr(bc).value, ptr(T_bc).value,
                              ptr(normals).value, float(krylov_tol), int(krylov_max_it), int(precond),
                              int(guess_order), int(bool(apply_f32)), int(mg_tail_from), int(mg_fused_from),
-                             int(mg_persistent), int(mg_sweeps))
+                             int(mg_persistent), int(mg_sweeps), int(krylov))
         h_ = C.c_void_p()
         check(lib.hsm_stepper_create(C.byref(h_), plan.h, C.byref(self.phys)), plan.h)
         self.h = h_

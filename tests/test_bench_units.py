@@ -30,3 +30,14 @@ def test_krylov_iteration_work_counts():
     cycle_flops = 11 * 50 + 12 * 10 + 2 * 9
     assert w["bytes"] == 2 * cycle_bytes + 2 * (12 * 50 + 16 * 10) + 160 * 10
     assert w["flops"] == 2 * cycle_flops + 2 * (2 * 50 + 2 * 10) + 22 * 10
+
+
+def test_krylov_iteration_work_gmres_counts():
+    """GMRES: one cycle, one application, orthogonalisation against j + 1 = 3
+    basis vectors (j_avg = 2), N = 10."""
+    info = {"level_rows": [10, 3], "level_entries": [50, 9]}
+    w = bench.krylov_iteration_work(info, 10, gmres=True, j_avg=2.0)
+    cycle_bytes = 48 * 50 + 112 * 10 + 20 * 3 + 8 * 9 + 16 * 3
+    cycle_flops = 11 * 50 + 12 * 10 + 2 * 9
+    assert w["bytes"] == cycle_bytes + (12 * 50 + 16 * 10) + 2 * (3 * 80 + 160) + 240 + 160
+    assert w["flops"] == cycle_flops + (2 * 50 + 2 * 10) + 2 * (2 * 3 * 10) + 10
