@@ -55,7 +55,9 @@ struct Mlp;  // learned predictor (mlp.cu)
 // whole build can be replayed as one CUDA graph.
 struct BuildWs {
   unsigned long long* bbox = nullptr;  // [2 * kMaxDim] ordered-bit extrema
-  int* lat = nullptr;                  // [2 * kMaxDim + 4]: lattice extents, demoted, n_mon, n_rbf
+  int* lat = nullptr;                  // [2 * kMaxDim + 5]: lattice extents, demoted, n_mon, n_rbf, flags, arrivals
+  unsigned long long* bpart = nullptr; // k_bounds' per-block extrema partials
+  int* lpart = nullptr;
   int32_t* ijk = nullptr;              // [dim][N]
   uint8_t* on_lat = nullptr;           // [N]
   unsigned long long* hkeys = nullptr; // lattice hash
@@ -71,7 +73,8 @@ struct BuildWs {
   double* sorted_xyz = nullptr;        // [N][kMaxDim]
   double* mon_w64 = nullptr;           // MON weights, [nops][2 dim + 1][count], room for count = N
   uint8_t* sorted_bnd = nullptr;       // [N]
-  int32_t* scan_ws = nullptr;          // scan block sums
+  int32_t* scan_ws = nullptr;          // block sums of the cell scan
+  int32_t* scan_ws2 = nullptr;         // block sums of the group partition (a parallel branch)
   int* readback = nullptr;             // pinned host: demoted, n_mon, n_rbf, flags
   cudaGraphExec_t graph = nullptr;
   int graph_qt = 0;                    // kNN variant the graph was captured with
@@ -80,7 +83,8 @@ struct BuildWs {
   int graph_kernels = 0;               // kernels per replay
   cudaStream_t cap = nullptr;
   cudaStream_t side = nullptr;         // capture branch of the MON stencils
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaStream_t side2 = nullptr;        // capture branch of the cell scan and scatter
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fork2 = nullptr, ev_join2 = nullptr;
   bool ready = false;
 };
 
@@ -211,9 +215,8 @@ inline int num_sms() {
 // ---- scan.cu -------------------------------------------------------------
 // Exclusive prefix sum of in[0..n) (int32 counts) into out[0..n], out[n] = total.
 // ws: scratch of scan_scratch(n) ints, or nullptr to allocate one.
-// out[n] receives the total; zero_in (optional, may alias in): cleared as read.
-cudaError_t exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s, int32_t* ws = nullptr,
-                               int32_t* zero_in = nullptr);
+// out[n] receives the total.
+cudaError_t exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s, int32_t* ws = nullptr);
 int scan_kernels(int64_t n);  // kernels one scan of n items launches
 // List of indices i (ascending) with key[i] == want; count written to *count_dev.
 cudaError_t select_indices(const uint8_t* key, uint8_t want, int64_t n, int32_t* out_list,

@@ -127,14 +127,9 @@ __global__ void k_block_write_fold(F f, int64_t n, const int32_t* sums, W w, int
   }
 }
 
-// zero (optional): the counts, cleared as they are consumed
 struct WriteExcl {
   int32_t* out;
-  int32_t* zero;
-  __device__ void operator()(int64_t i, int e, int) const {
-    out[i] = e;
-    if (zero) zero[i] = 0;
-  }
+  __device__ void operator()(int64_t i, int e, int) const { out[i] = e; }
 };
 // Stable partition by a 0/1 key: e counts the selected items before i, so an
 // unselected item goes to place i - e of the second list.
@@ -182,9 +177,8 @@ cudaError_t run_scan(F f, W w, int64_t n, int32_t* grand, cudaStream_t s, int32_
 
 }  // namespace
 
-cudaError_t exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s, int32_t* ws,
-                               int32_t* zero_in) {
-  return run_scan(CountsIn{in}, WriteExcl{out, zero_in}, n, out + n, s, ws);
+cudaError_t exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, cudaStream_t s, int32_t* ws) {
+  return run_scan(CountsIn{in}, WriteExcl{out}, n, out + n, s, ws);
 }
 
 int scan_kernels(int64_t n) { return ceil_div(n > 0 ? n : 1, kScanTile) <= kFoldBlocks ? 2 : 3; }

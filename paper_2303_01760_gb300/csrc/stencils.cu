@@ -23,7 +23,6 @@ namespace hsm {
 namespace {
 
 constexpr double kLatticeTol = 1e-6;
-constexpr double kLatticeRange = 1048576.0;  // |lattice coordinate| < 2^20 (21-bit key fields)
 
 __device__ __forceinline__ unsigned long long ordered_bits(double x) {
   unsigned long long b = (unsigned long long)__double_as_longlong(x);
@@ -149,9 +148,6 @@ struct LatticeMap {
   }
 };
 
-// Bounding box (ordered-bit keys) and lattice extents of the node set: each
-// thread keeps running extrema, the block reduces them with warp shuffles,
-// and one thread per block issues the global atomics.
 struct CellGrid;
 struct LatticeDense;
 // Cell grid of the bounding box, and the dense lattice map's extents (defined
@@ -160,61 +156,23 @@ struct LatticeDense;
 __device__ void grid_setup(const unsigned long long* bbox, int dim, double h, int64_t N, CellGrid* out);
 __device__ void lattice_setup(const int* lat_lo, const int* lat_hi, int dim, long long dense_cap, LatticeDense* desc);
 
-// Reduction identities of the build: status flags and the weights call's
-// counters zero; bbox minima all-ones
-// and maxima zero (ordered-bit keys, interleaved [min_k, max_k]); lattice
-// extents minima 0x7f7f7f7f and maxima 0x80808080 (negative), counters zero.
-__global__ void k_build_init(unsigned* flags, int* counts, unsigned long long* bbox, int* lat) {
-  const int t = threadIdx.x;
-  if (t < 4) flags[t] = 0u;
-  if (t < 4) counts[t] = 0;
-  if (t < 2 * kMaxDim) bbox[t] = (t & 1) ? 0ull : ~0ull;
-  if (t < kMaxDim) {
-    lat[t] = 0x7f7f7f7f;
-    lat[kMaxDim + t] = (int)0x80808080u;
-  }
-  if (t < 5) lat[2 * kMaxDim + t] = 0;  // counters, and k_bounds' arrival count
-}
+// Adding 1.5 * 2^52 to a double of magnitude below 2^51 rounds it to an
+// integer: the sum lies in [2^52, 2^53), where one unit in the last place is
+// 1, and the integer is the sum's bit pattern minus that of 1.5 * 2^52.
+constexpr double kRoundMagic = 6755399441055744.0;
+constexpr long long kRoundMagicBits = 0x4338000000000000ll;
+constexpr long long kLatticeRangeI = 1ll << 20;  // |lattice coordinate| < 2^20 (21-bit key fields)
+constexpr int kBoundsThreads = 256;
+constexpr int kBoundsItems = 2;  // nodes per thread per pass, their loads issued together
 
-__global__ void __launch_bounds__(256) k_bounds(const double* __restrict__ coords, int64_t N, int dim, double inv_h,
-                                                unsigned long long* bbox, int* lat_lo, int* lat_hi, int32_t* ijk,
-                                                uint8_t* on_lat, unsigned* arrivals, double h, long long dense_cap,
-                                                CellGrid* cg_out, LatticeDense* ld_out) {
-  unsigned long long bmin[kMaxDim], bmax[kMaxDim];
-  int lmin[kMaxDim], lmax[kMaxDim];
-  for (int k = 0; k < kMaxDim; ++k) {
-    bmin[k] = ~0ull;
-    bmax[k] = 0ull;
-    lmin[k] = 0x7fffffff;
-    lmax[k] = -0x7fffffff;
-  }
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    bool on = true;
-    int q[kMaxDim];
-    for (int k = 0; k < dim; ++k) {
-      double x = coords[k * N + i];
-      unsigned long long ob = ordered_bits(x);
-      bmin[k] = ob < bmin[k] ? ob : bmin[k];
-      bmax[k] = ob > bmax[k] ? ob : bmax[k];
-      double t = x * inv_h;
-      double r = rint(t);
-      if (!(fabs(t - r) <= kLatticeTol) || fabs(r) >= kLatticeRange) on = false;
-      q[k] = on ? (int)r : 0;
-    }
-    on_lat[i] = on ? 1 : 0;
-    for (int k = 0; k < dim; ++k) {
-      ijk[k * N + i] = q[k];
-      if (on) {
-        lmin[k] = min(lmin[k], q[k]);
-        lmax[k] = max(lmax[k], q[k]);
-      }
-    }
-  }
-  __shared__ unsigned long long sb[2][kMaxDim][8];
-  __shared__ int sl[2][kMaxDim][8];
+// Block-wide extrema of each thread's running ones; valid in thread 0.
+__device__ __forceinline__ void block_extrema(unsigned long long* bmin, unsigned long long* bmax, int* lmin, int* lmax, int dim) {
+  __shared__ unsigned long long sb[2][kMaxDim][kBoundsThreads / 32];
+  __shared__ int sl[2][kMaxDim][kBoundsThreads / 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int k = 0; k < dim; ++k) {
+#pragma unroll
+  for (int k = 0; k < kMaxDim; ++k) {
+    if (k >= dim) break;
     for (int o = 16; o > 0; o >>= 1) {
       unsigned long long a = __shfl_xor_sync(0xffffffffu, bmin[k], o);
       unsigned long long b = __shfl_xor_sync(0xffffffffu, bmax[k], o);
@@ -234,30 +192,143 @@ __global__ void __launch_bounds__(256) k_bounds(const double* __restrict__ coord
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    const int nw = (blockDim.x + 31) / 32;
-    for (int k = 0; k < dim; ++k) {
-      unsigned long long a = ~0ull, b = 0ull;
-      int c = 0x7fffffff, d = -0x7fffffff;
-      for (int w = 0; w < nw; ++w) {
-        a = sb[0][k][w] < a ? sb[0][k][w] : a;
-        b = sb[1][k][w] > b ? sb[1][k][w] : b;
-        c = min(c, sl[0][k][w]);
-        d = max(d, sl[1][k][w]);
+#pragma unroll
+    for (int k = 0; k < kMaxDim; ++k)
+      for (int w = 1; w < kBoundsThreads / 32 && k < dim; ++w) {
+        bmin[k] = sb[0][k][w] < bmin[k] ? sb[0][k][w] : bmin[k];
+        bmax[k] = sb[1][k][w] > bmax[k] ? sb[1][k][w] : bmax[k];
+        lmin[k] = min(lmin[k], sl[0][k][w]);
+        lmax[k] = max(lmax[k], sl[1][k][w]);
       }
-      atomicMin(&bbox[2 * k], a);
-      atomicMax(&bbox[2 * k + 1], b);
-      if (c <= d) {
-        atomicMin(&lat_lo[k], c);
-        atomicMax(&lat_hi[k], d);
+  }
+}
+
+// Bounding box (ordered-bit keys), each node's nearest lattice point and
+// whether it lies on it, and the lattice extents.  Each block writes its own
+// slot of extrema partials (bpart, lpart: [gridDim.x][2 kMaxDim], interleaved
+// [min_k, max_k]); the last block to arrive reduces them into bbox and
+// lat[0, 2 kMaxDim) (lattice extents; an empty lattice keeps 0x7f7f7f7f /
+// 0x80808080), sets up the cell grid and the lattice map, and zeroes the
+// build's counters for the kernels after it: the status flags, the weights
+// call's counts, lat[2 kMaxDim, +4) (demoted, n_mon, n_rbf, flags copy) and
+// the arrival count lat[2 kMaxDim + 4], which starts at zero on allocation.
+__global__ void __launch_bounds__(kBoundsThreads) k_bounds(const double* __restrict__ coords, int64_t N, int dim,
+                                                           double inv_h, unsigned long long* bpart, int* lpart,
+                                                           int32_t* ijk, uint8_t* on_lat, unsigned long long* bbox,
+                                                           int* lat, unsigned* flags, int* counts, double h,
+                                                           long long dense_cap, CellGrid* cg_out,
+                                                           LatticeDense* ld_out) {
+  unsigned long long bmin[kMaxDim], bmax[kMaxDim];
+  int lmin[kMaxDim], lmax[kMaxDim];
+#pragma unroll
+  for (int k = 0; k < kMaxDim; ++k) {
+    bmin[k] = ~0ull;
+    bmax[k] = 0ull;
+    lmin[k] = 0x7fffffff;
+    lmax[k] = -0x7fffffff;
+  }
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x * kBoundsItems;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x * kBoundsItems + threadIdx.x; i0 < N; i0 += stride) {
+    double x[kBoundsItems][kMaxDim];
+#pragma unroll
+    for (int u = 0; u < kBoundsItems; ++u) {
+      const int64_t i = i0 + (int64_t)u * blockDim.x;
+#pragma unroll
+      for (int k = 0; k < kMaxDim; ++k) x[u][k] = (i < N && k < dim) ? coords[k * N + i] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < kBoundsItems; ++u) {
+      const int64_t i = i0 + (int64_t)u * blockDim.x;
+      if (i >= N) break;
+      bool on = true;
+      int q[kMaxDim];
+#pragma unroll
+      for (int k = 0; k < kMaxDim; ++k) {
+        if (k >= dim) break;
+        const double xk = x[u][k];
+        const unsigned long long ob = ordered_bits(xk);
+        bmin[k] = ob < bmin[k] ? ob : bmin[k];
+        bmax[k] = ob > bmax[k] ? ob : bmax[k];
+        // nearest lattice coordinate r of x / h (the product rounded once,
+        // with the magic constant); NaN, infinities and |x / h| >= 2^20 give
+        // a sum outside (magic - 2^20, magic + 2^20)
+        const double s = __fma_rn(xk, inv_h, kRoundMagic);
+        const long long r = (long long)__double_as_longlong(s) - kRoundMagicBits;
+        const double d = __fma_rn(xk, inv_h, -__dsub_rn(s, kRoundMagic));  // x / h - r
+        if (!(r > -kLatticeRangeI && r < kLatticeRangeI && fabs(d) <= kLatticeTol)) on = false;
+        q[k] = on ? (int)r : 0;
+      }
+      on_lat[i] = on ? 1 : 0;
+#pragma unroll
+      for (int k = 0; k < kMaxDim; ++k) {
+        if (k >= dim) break;
+        ijk[k * N + i] = q[k];
+        if (on) {
+          lmin[k] = min(lmin[k], q[k]);
+          lmax[k] = max(lmax[k], q[k]);
+        }
       }
     }
-    // the last block to arrive sets up the cell grid and the lattice map
+  }
+  block_extrema(bmin, bmax, lmin, lmax, dim);
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    unsigned long long* bp = bpart + (size_t)blockIdx.x * 2 * kMaxDim;
+    int* lp = lpart + (size_t)blockIdx.x * 2 * kMaxDim;
+#pragma unroll
+    for (int k = 0; k < kMaxDim; ++k) {
+      if (k >= dim) break;
+      bp[2 * k] = bmin[k];
+      bp[2 * k + 1] = bmax[k];
+      lp[2 * k] = lmin[k];
+      lp[2 * k + 1] = lmax[k];
+    }
     __threadfence();
-    if (atomicAdd(arrivals, 1u) == gridDim.x - 1) {
-      __threadfence();
-      grid_setup(bbox, dim, h, N, cg_out);
-      lattice_setup(lat_lo, lat_hi, dim, dense_cap, ld_out);
+    unsigned* arrivals = reinterpret_cast<unsigned*>(lat + 2 * kMaxDim + 4);
+    last = atomicAdd(arrivals, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  // the last block: every other block's partials are visible
+  __threadfence();
+#pragma unroll
+  for (int k = 0; k < kMaxDim; ++k) {
+    bmin[k] = ~0ull;
+    bmax[k] = 0ull;
+    lmin[k] = 0x7fffffff;
+    lmax[k] = -0x7fffffff;
+  }
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    const unsigned long long* bp = bpart + (size_t)b * 2 * kMaxDim;
+    const int* lp = lpart + (size_t)b * 2 * kMaxDim;
+#pragma unroll
+    for (int k = 0; k < kMaxDim; ++k) {
+      if (k >= dim) break;
+      const unsigned long long a = __ldcg(bp + 2 * k), c = __ldcg(bp + 2 * k + 1);
+      bmin[k] = a < bmin[k] ? a : bmin[k];
+      bmax[k] = c > bmax[k] ? c : bmax[k];
+      lmin[k] = min(lmin[k], __ldcg(lp + 2 * k));
+      lmax[k] = max(lmax[k], __ldcg(lp + 2 * k + 1));
     }
+  }
+  block_extrema(bmin, bmax, lmin, lmax, dim);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < kMaxDim; ++k) {
+      const bool any = k < dim && lmin[k] <= lmax[k];
+      bbox[2 * k] = k < dim ? bmin[k] : ~0ull;
+      bbox[2 * k + 1] = k < dim ? bmax[k] : 0ull;
+      lat[k] = any ? lmin[k] : 0x7f7f7f7f;
+      lat[kMaxDim + k] = any ? lmax[k] : (int)0x80808080u;
+    }
+    grid_setup(bbox, dim, h, N, cg_out);
+    lattice_setup(lat, lat + kMaxDim, dim, dense_cap, ld_out);
+    for (int t = 0; t < 4; ++t) {
+      flags[t] = 0u;
+      counts[t] = 0;
+      lat[2 * kMaxDim + t] = 0;
+    }
+    lat[2 * kMaxDim + 4] = 0;  // arrivals, for the next launch
   }
 }
 
@@ -435,7 +506,9 @@ __global__ void k_cell_scatter(const double* __restrict__ coords, const uint8_t*
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
     int32_t l = cell_of[i];
-    int32_t s = start[l] + atomicAdd(&cursor[l], 1);
+    // the cursors are the cell counts, counted down to zero: the next build's
+    // counting starts from zero without a memset
+    int32_t s = start[l] + atomicSub(&cursor[l], 1) - 1;
     sorted_id[s] = (int32_t)i;
     for (int k = 0; k < dim; ++k) sorted_xyz[(int64_t)s * kMaxDim + k] = coords[k * N + i];
     sorted_bnd[s] = is_boundary ? is_boundary[i] : 0;
@@ -750,6 +823,10 @@ hsm_status alloc_build_ws(hsm_plan p) {
   CellGrid* cg = nullptr;
   HSM_CUDA(p, dev_alloc(&w.bbox, 2 * kMaxDim, s));
   HSM_CUDA(p, dev_alloc(&w.lat, 2 * kMaxDim + 5, s));
+  HSM_CUDA(p, cudaMemsetAsync(w.lat, 0, (2 * kMaxDim + 5) * sizeof(int), s));  // k_bounds' arrival count
+  const int64_t bgrid = (int64_t)num_sms() * 8;  // k_bounds' largest grid
+  HSM_CUDA(p, dev_alloc(&w.bpart, bgrid * 2 * kMaxDim, s));
+  HSM_CUDA(p, dev_alloc(&w.lpart, bgrid * 2 * kMaxDim, s));
   HSM_CUDA(p, dev_alloc(&w.ijk, (size_t)p->dim * N, s));
   HSM_CUDA(p, dev_alloc(&w.on_lat, N, s));
   HSM_CUDA(p, dev_alloc(&w.hkeys, cap, s));
@@ -769,11 +846,13 @@ hsm_status alloc_build_ws(hsm_plan p) {
   HSM_CUDA(p, dev_alloc(&w.cell_of, N, s));
   HSM_CUDA(p, dev_alloc(&w.cstart, ncell_max + 1, s));
   HSM_CUDA(p, dev_alloc(&w.ccount, ncell_max, s));
+  HSM_CUDA(p, cudaMemsetAsync(w.ccount, 0, ncell_max * sizeof(int32_t), s));  // then every scatter leaves zeros
   HSM_CUDA(p, dev_alloc(&w.sorted_id, N, s));
   HSM_CUDA(p, dev_alloc(&w.sorted_xyz, (size_t)N * kMaxDim, s));
   HSM_CUDA(p, dev_alloc(&w.mon_w64, (size_t)p->nops * (2 * p->dim + 1) * N, s));
   HSM_CUDA(p, dev_alloc(&w.sorted_bnd, N, s));
   HSM_CUDA(p, dev_alloc(&w.scan_ws, scan_scratch(ncell_max), s));
+  HSM_CUDA(p, dev_alloc(&w.scan_ws2, scan_scratch(N), s));
   HSM_CUDA(p, dev_alloc(&p->kind, N, s));
   HSM_CUDA(p, dev_alloc(&p->pos, N, s));
   HSM_CUDA(p, dev_alloc(&p->dev_flags, 4, s));
@@ -787,7 +866,9 @@ hsm_status alloc_build_ws(hsm_plan p) {
   HSM_CUDA(p, cudaMallocHost((void**)&w.readback, 4 * sizeof(int)));
   HSM_CUDA(p, cudaStreamCreateWithFlags(&w.cap, cudaStreamNonBlocking));
   HSM_CUDA(p, cudaStreamCreateWithFlags(&w.side, cudaStreamNonBlocking));
-  for (cudaEvent_t* e : {&w.ev_fork, &w.ev_join}) HSM_CUDA(p, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  HSM_CUDA(p, cudaStreamCreateWithFlags(&w.side2, cudaStreamNonBlocking));
+  for (cudaEvent_t* e : {&w.ev_fork, &w.ev_join, &w.ev_fork2, &w.ev_join2})
+    HSM_CUDA(p, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
   w.ready = true;
   return HSM_OK;
 }
@@ -799,17 +880,19 @@ void free_build_ws(hsm_plan p) {
   w.graph = nullptr;
   for (void** ptr : {(void**)&w.bbox, (void**)&w.lat, (void**)&w.ijk, (void**)&w.on_lat, (void**)&w.hkeys,
                      (void**)&w.hvals, (void**)&w.dmap, (void**)&w.ldesc, (void**)&w.cgd, (void**)&w.cell_of, (void**)&w.cstart, (void**)&w.ccount,
-                     (void**)&w.sorted_id, (void**)&w.sorted_xyz, (void**)&w.mon_w64, (void**)&w.sorted_bnd, (void**)&w.scan_ws})
+                     (void**)&w.sorted_id, (void**)&w.sorted_xyz, (void**)&w.mon_w64, (void**)&w.sorted_bnd, (void**)&w.scan_ws,
+                     (void**)&w.scan_ws2, (void**)&w.bpart, (void**)&w.lpart})
     dev_free(ptr, s);
   if (w.readback) cudaFreeHost(w.readback);
   w.readback = nullptr;
   if (w.cap) cudaStreamDestroy(w.cap);
   if (w.side) cudaStreamDestroy(w.side);
-  for (cudaEvent_t* e : {&w.ev_fork, &w.ev_join}) {
+  if (w.side2) cudaStreamDestroy(w.side2);
+  for (cudaEvent_t* e : {&w.ev_fork, &w.ev_join, &w.ev_fork2, &w.ev_join2}) {
     if (*e) cudaEventDestroy(*e);
     *e = nullptr;
   }
-  w.cap = w.side = nullptr;
+  w.cap = w.side = w.side2 = nullptr;
   w.ready = false;
 }
 
@@ -836,14 +919,14 @@ cudaError_t enqueue_build(hsm_plan p, cudaStream_t s, int qt, int* nk) {
   int k = 0;
 
   // ---- bounds and lattice coordinates
-  int* lat = w.lat;  // [0,6): lattice extents, [6]: demoted, [7]: n_mon, [8]: n_rbf, [9]: flags
-  // status flags, the bounding box and the lattice extents start from their
-  // reduction identities (one small kernel instead of eight memset nodes)
-  k_build_init<<<1, 32, 0, s>>>(p->dev_flags, p->dev_count, w.bbox, lat);
-  ++k;
-  k_bounds<<<grid, T, 0, s>>>(p->coords, N, dim, 1.0 / p->h, w.bbox, lat, lat + kMaxDim, w.ijk, w.on_lat,
-                              reinterpret_cast<unsigned*>(lat + 2 * kMaxDim + 4), p->h, (long long)(4 * N + 1024),
-                              static_cast<CellGrid*>(w.cgd), static_cast<LatticeDense*>(w.ldesc));
+  // [0,6): lattice extents, [6]: demoted, [7]: n_mon, [8]: n_rbf, [9]: flags, [10]: k_bounds' arrivals
+  int* lat = w.lat;
+  // k_bounds also zeroes the status flags and counters for the kernels after it
+  const int bgrid = (int)std::min<int64_t>(ceil_div(N, kBoundsThreads * kBoundsItems), (int64_t)num_sms() * 8);
+  k_bounds<<<bgrid, kBoundsThreads, 0, s>>>(p->coords, N, dim, 1.0 / p->h, w.bpart, w.lpart, w.ijk, w.on_lat,
+                                            w.bbox, lat, p->dev_flags, p->dev_count, p->h,
+                                            (long long)(4 * N + 1024), static_cast<CellGrid*>(w.cgd),
+                                            static_cast<LatticeDense*>(w.ldesc));
   ++k;
   HSM_TRY(cudaGetLastError());
   // lattice map: dense over the lattice's extents when they hold at most
@@ -855,10 +938,9 @@ cudaError_t enqueue_build(hsm_plan p, cudaStream_t s, int qt, int* nk) {
   lh.hash.vals = w.hvals;
   lh.dmap = w.dmap;
   lh.desc = static_cast<const LatticeDense*>(w.ldesc);
-  // the cell counts start at zero (the previous build's scatter left its
-  // cursors there)
+  // the cell counts start at zero: zeroed at allocation, and every scatter
+  // counts its cursors back down to zero
   const int64_t ncell_max = 4 * N + 1024;
-  HSM_TRY(cudaMemsetAsync(w.ccount, 0, ncell_max * sizeof(int32_t), s));
   // the map starts empty: cleared once at allocation and by every build
   // after its last reader (the MON stencils, on the side branch)
   if (dim == 2) k_lattice_insert<2><<<grid, T, 0, s>>>(w.ijk, w.on_lat, N, lh);
@@ -879,8 +961,20 @@ cudaError_t enqueue_build(hsm_plan p, cudaStream_t s, int qt, int* nk) {
   ++k;
   HSM_TRY(cudaGetLastError());
 
+  // ---- cell scan and scatter on a branch of their own, beside the group
+  // partition (each scan with its own block sums); the kNN search joins both
+  HSM_TRY(cudaEventRecord(w.ev_fork2, s));
+  HSM_TRY(cudaStreamWaitEvent(w.side2, w.ev_fork2, 0));
+  HSM_TRY(exclusive_scan_i32(w.ccount, w.cstart, ncell_max, w.side2, w.scan_ws));
+  k += scan_kernels(ncell_max);
+  k_cell_scatter<<<grid, T, 0, w.side2>>>(p->coords, p->is_boundary, N, dim, w.cell_of, w.cstart, w.ccount,
+                                          w.sorted_id, w.sorted_xyz, w.sorted_bnd);
+  ++k;
+  HSM_TRY(cudaGetLastError());
+  HSM_TRY(cudaEventRecord(w.ev_join2, w.side2));
+
   // ---- group lists (ascending node ids) and positions
-  HSM_TRY(partition_indices(p->kind, 0, N, p->mon.nodes, p->rbf.nodes, p->pos, counts, counts + 1, s, w.scan_ws));
+  HSM_TRY(partition_indices(p->kind, 0, N, p->mon.nodes, p->rbf.nodes, p->pos, counts, counts + 1, s, w.scan_ws2));
   k += scan_kernels(N);
   // MON stencils on a side branch of the graph, joined before the read-back
   HSM_TRY(cudaEventRecord(w.ev_fork, s));
@@ -900,14 +994,8 @@ cudaError_t enqueue_build(hsm_plan p, cudaStream_t s, int qt, int* nk) {
   }
   HSM_TRY(cudaEventRecord(w.ev_join, w.side));
 
-  // ---- kNN for the RBF-FD group
-  // the counts are cleared as the scan consumes them: the scatter's cursors
-  HSM_TRY(exclusive_scan_i32(w.ccount, w.cstart, ncell_max, s, w.scan_ws, w.ccount));
-  k += scan_kernels(ncell_max);
-  k_cell_scatter<<<grid, T, 0, s>>>(p->coords, p->is_boundary, N, dim, w.cell_of, w.cstart, w.ccount, w.sorted_id,
-                                    w.sorted_xyz, w.sorted_bnd);
-  ++k;
-  HSM_TRY(cudaGetLastError());
+  // ---- kNN for the RBF-FD group, once the cells are sorted
+  HSM_TRY(cudaStreamWaitEvent(s, w.ev_join2, 0));
   {
     // qt threads per query (1, 2 or 4), blocks of 32 * qt
     const int KT = 32 * qt;
@@ -993,7 +1081,7 @@ hsm_status build_stencils(hsm_plan p) {
   }
   HSM_CUDA(p, cudaGraphLaunch(w.graph, s));
   p->launches += w.graph_kernels;
-  p->counters_fresh = true;  // k_build_init cleared the weights call's status words
+  p->counters_fresh = true;  // k_bounds cleared the weights call's status words
   HSM_CUDA(p, cudaStreamSynchronize(s));
   const int* rb = w.readback;
   p->n_demoted = rb[0];
