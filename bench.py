@@ -302,12 +302,27 @@ def save_gpu_sample(ns, plan, u, n_sample, path):
 # ---------------------------------------------------------------------------
 # GPU arm
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
-# k_weights_grouped<2, 3, 8> on the hybrid workload, from an ncu capture of
+# k_rbf_fp64<2, 3, 8> on the hybrid workload, from an ncu capture of
 # the kernel as it stands.  None whenever that kernel changes until it is
 # re-captured.
 RBF64_TRAFFIC_BYTES = 2465280 + 0
 # the same for k_weights_grouped<2, 3, 8> (both groups in one launch)
 GROUPED_TRAFFIC_BYTES = 9752832 + 18688
+# the same summed over the chunk launches of k_rbf_fp64_chunk<2, 3, 8> (the
+# solve inside the stencil build), per chunk count; absent: not captured
+CHUNK_TRAFFIC_BYTES = {}
+
+
+def roofline_kernel(tune):
+    if tune["arrange"] == 1:
+        return ("k_weights_grouped (FP64 weights of both groups in one persistent launch; the RBF-FD null-space "
+                "solves bound it; algorithmic flops of the RBF-FD systems only)")
+    if tune["arrange"] == 2:
+        return (f"k_rbf_fp64_chunk (RBF-FD FP64 null-space solve inside the stencil build, {tune['chunks']} "
+                "chunk(s), chunk c beside the kNN search of chunk c + 1; timed over the span of its launches, "
+                "which overlaps the kNN search)")
+    return ("k_rbf_fp64 (RBF-FD FP64 null-space solve, hybrid set; the MON weights run beside the kNN search "
+            "in the stencil build)")
 
 
 def aggregate_ranks(times, n_nodes, dist, device):
@@ -436,9 +451,12 @@ def run_gpu(args):
     # configuration); at S = 1 it is the timed step's rate
     S_STEPS = 2000
 
-    def combined(ph, S):
-        tw = float(np.mean([p[0] + p[1] + p[2] for p in ph]))
+    def combined(ms, ph, S):
+        # T_w: the step's time (CUDA events around the whole step) less its
+        # apply phase, whatever the arrangement of the weights (with the
+        # weights in the build, the RBF-FD phase lies inside the stencil phase)
         ta = float(np.mean([p[3] for p in ph]))
+        tw = float(np.mean(ms)) - ta
         return n_total * S / ((tw + S * ta) * 1e-3), tw, ta
 
     # end to end through the C ABI from pinned host buffers
@@ -460,13 +478,10 @@ def run_gpu(args):
             "e2e": e2e,
             "gpu_launches": int(launches_h // max(args.steps, 1)) * args.steps,
             "roofline": {"bound": "alu",
-                         "kernel": ("k_weights_grouped (FP64 weights of both groups in one persistent launch; the "
-                                    "RBF-FD null-space solves bound it; algorithmic flops of the RBF-FD systems only)"
-                                    if tune_h["grouped"] else
-                                    "k_rbf_fp64 (RBF-FD FP64 null-space solve, hybrid set; the MON weights run "
-                                    "beside the kNN search in the stencil build)"),
+                         "kernel": roofline_kernel(tune_h),
                          "achieved": ach_h, "peak": peak, "unit": "GFLOP/s", "frac": ach_h / peak,
-                         "traffic": GROUPED_TRAFFIC_BYTES if tune_h["grouped"] else RBF64_TRAFFIC_BYTES,
+                         "traffic": ({0: RBF64_TRAFFIC_BYTES, 1: GROUPED_TRAFFIC_BYTES}.get(tune_h["arrange"])
+                                     if tune_h["arrange"] != 2 else CHUNK_TRAFFIC_BYTES.get(tune_h["chunks"])),
                          "peak_source": "measured: FP64 FMA-chain probe (hsm_probe_fp64_peak) in this run, "
                                         f"{peak_ms:.3f} ms, SM clock median {peak_clocks.get('sm_mhz')} MHz",
                          "peak_clocks": peak_clocks,
@@ -477,16 +492,18 @@ def run_gpu(args):
                           "roofline_frac_rbf_kernel": ach_a / peak,
                           "rbf_kernel_gflops": ach_a},
             "combined": {
-                "definition": "N*S/(T_w + S*T_a): T_w = stencils + weights, T_a = one fused apply of dx,dy,lap "
-                              "(phase events, L2 flushed before each step); S = 2000 is the step count of the "
-                              "configuration and the defining figure, S = 1 is the timed step (the headline value)",
+                "definition": "N*S/(T_w + S*T_a): T_a = one fused apply of dx,dy,lap (phase events), T_w = the "
+                              "timed step (stencils + weights + apply, L2 flushed before each step) less T_a; "
+                              "S = 2000 is the step count of the configuration and the defining figure, S = 1 is "
+                              "the timed step (the headline value)",
                 "S": S_STEPS,
-                "hybrid": combined(ph_h, S_STEPS)[0], "all_rbffd": combined(ph_a, S_STEPS)[0],
-                "hybrid_over_all_rbffd": combined(ph_h, S_STEPS)[0] / combined(ph_a, S_STEPS)[0],
-                "S1_hybrid_over_all_rbffd": combined(ph_h, 1)[0] / combined(ph_a, 1)[0],
-                "T_w_ms": {"hybrid": combined(ph_h, 1)[1], "all_rbffd": combined(ph_a, 1)[1]},
-                "T_a_ms": {"hybrid": combined(ph_h, 1)[2], "all_rbffd": combined(ph_a, 1)[2]}},
-            "phases_ms": {"hybrid": dict(zip(["stencils", "mon_weights", "weights", "apply"],
+                "hybrid": combined(ms_h, ph_h, S_STEPS)[0], "all_rbffd": combined(ms_a, ph_a, S_STEPS)[0],
+                "hybrid_over_all_rbffd": combined(ms_h, ph_h, S_STEPS)[0] / combined(ms_a, ph_a, S_STEPS)[0],
+                "S1_hybrid_over_all_rbffd": combined(ms_h, ph_h, 1)[0] / combined(ms_a, ph_a, 1)[0],
+                "T_w_ms": {"hybrid": combined(ms_h, ph_h, 1)[1], "all_rbffd": combined(ms_a, ph_a, 1)[1]},
+                "T_a_ms": {"hybrid": combined(ms_h, ph_h, 1)[2], "all_rbffd": combined(ms_a, ph_a, 1)[2]}},
+            "phases_ms": {"weights_in_build": {"hybrid": tune_h["arrange"] == 2, "all_rbffd": tune_a["arrange"] == 2},
+                          "hybrid": dict(zip(["stencils", "mon_weights", "weights", "apply"],
                                              np.mean(ph_h, 0).round(4).tolist())),
                           "all_rbffd": dict(zip(["stencils", "mon_weights", "weights", "apply"],
                                                 np.mean(ph_a, 0).round(4).tolist()))},
@@ -1061,8 +1078,8 @@ def run_kernels(args):
     nrm = torch.from_numpy(ns.normals).to(dev)
     u = torch.from_numpy(nodesets.field_sincos(ns.coords)[0]).to(dev)
     plan = hsm.Plan(c, reg, bnd, ns.h, m=2, normals=nrm)
-    if args.knn_qt:
-        plan.set_tuning(knn_qt=args.knn_qt)
+    if args.knn_qt or args.arrange:
+        plan.set_tuning(knn_qt=args.knn_qt or 1, arrange=args.arrange, chunks=args.chunks)
     prec = {"fp64": hsm.HSM_PREC_FP64, "fp32r": hsm.HSM_PREC_FP32_REFINE}[args.prec]
     if args.learned:
         # learned weights on the predictor's workload shape: a short training on
@@ -1648,6 +1665,9 @@ def main():
     ap.add_argument("--big-apply", action="store_true", help="with --kernels: f64 applies on the 7.3M-node set")
     ap.add_argument("--three-d", type=int, default=0, help="with --kernels: m of f64 and f32 applies on the 3D set")
     ap.add_argument("--knn-qt", type=int, default=0, help="with --kernels: fix the kNN threads per query (1, 2, 4)")
+    ap.add_argument("--arrange", type=int, default=0, help="with --kernels: FP64 weights arrangement (0 split, "
+                    "1 grouped launch, 2 in the stencil build)")
+    ap.add_argument("--chunks", type=int, default=1, help="with --kernels --arrange 2: kNN / solve chunks (1, 2, 4)")
     ap.add_argument("--train-steps", type=int, default=3000, help="with --kernels --learned")
     ap.add_argument("--dvd", type=int, default=0, help="de Vahl Davis validation run on a 1/n lattice (no benchmark)")
     ap.add_argument("--layout", default="hybrid", choices=["hybrid", "scattered", "regular"], help="with --dvd")
@@ -1658,7 +1678,7 @@ def main():
     ap.add_argument("--refined-steps", type=int, default=500, help="with --refined")
     ap.add_argument("--sweep", action="store_true", help="scattered-fraction sweep (5..100 %%), m = 2 and 4")
     ap.add_argument("--sweep-steps", type=int, default=100, help="with --sweep: explicit steps timed per set")
-    ap.add_argument("--krylov", type=int, default=0, help="with --kernels --stepper: 0 BiCGSTAB, 1 GMRES(30)")
+    ap.add_argument("--krylov", type=int, default=0, help="with --kernels --stepper: 0 GMRES(30), 1 BiCGSTAB")
     ap.add_argument("--mg-sweeps", type=int, default=0, help="with --kernels --stepper: 1 or 2 Jacobi sweeps "
                     "each way in the multigrid cycle (0: the library default)")
     ap.add_argument("--guess-order", type=int, default=0, help="with --kernels --stepper: pressure initial "

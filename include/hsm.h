@@ -237,30 +237,43 @@ hsm_status hsm_plan_set_checks(hsm_plan plan, int enable);
 hsm_status hsm_plan_inject_fault(hsm_plan plan, int fault);
 
 /* Times the kernel variants of this plan (the kNN search: 1, 2 or 4 threads
- * per query over growing rings of cells, or one warp per query over a fixed
- * window of cells with the ring search finishing the queries the window
- * cannot settle; lanes per RBF-FD weight system in FP64 and FP32; the grouped
- * or split arrangement of the FP64 weights; the apply block size) on its own
- * data and keeps the fastest of each.
+ * per query, a first window of cells sized from n and the node spacing, then
+ * ring by ring; lanes per RBF-FD weight system in FP64 and FP32; the
+ * arrangement of the FP64 weights and its chunk count; the apply block size)
+ * on its own data and keeps the fastest of each.
  * cache_path: NULL = no cache; otherwise a text file read before and updated
  * after tuning, keyed by device name and problem shape.  Synchronises.      */
 hsm_status hsm_plan_autotune(hsm_plan plan, const char* cache_path);
 
 /* The plan's kernel variants (host outputs, any may be NULL): threads per kNN
- * query (1, 2 or 4), lanes per RBF-FD system in
- * FP64 and in FP32 + refinement, threads per
- * block of the apply, and 1 when the FP64 weights of both groups run in one
- * grouped launch (0: MON weights beside the kNN search, then one RBF-FD
- * launch).  tuned is 1 after hsm_plan_autotune.                             */
+ * query (1, 2 or 4), lanes per RBF-FD system in FP64 and in FP32 +
+ * refinement, threads per block of the apply, the arrangement of the FP64
+ * weights and its chunk count, and tuned = 1 after hsm_plan_autotune.
+ * Arrangements:
+ *   0  the stencil build computes the MON weights beside the kNN search; the
+ *      weights call solves the RBF-FD group in one launch;
+ *   1  the weights call computes both groups in one persistent launch with a
+ *      work queue (the build computes no weights);
+ *   2  the stencil build computes both groups in FP64: the MON weights beside
+ *      the kNN search, and the RBF-FD group in `chunks` (1, 2 or 4) equal
+ *      chunks, chunk c solved on a branch of the build graph while the kNN
+ *      search runs on chunk c + 1.  The first FP64 weights call after the
+ *      build without node_status then only reads the status words (the
+ *      singular systems' lower-degree retry included); another precision,
+ *      node_status or a second call solves again.  The plan's RBF-FD weight
+ *      array then has room for N stencils.                                  */
 hsm_status hsm_plan_tuning(hsm_plan plan, int* knn_qt, int* rbf_lanes, int* rbf_lanes32, int* apply_threads,
-                           int* grouped, int* tuned);
+                           int* arrange, int* chunks, int* tuned);
 
 /* Sets the plan's kernel variants instead of timing them (reproducible runs,
  * tests): knn_qt 1, 2 or 4; rbf_lanes and rbf_lanes32 4, 8, 16 or 32;
- * apply_threads 64, 128 or 256; grouped 0 or 1.  HSM_EINVAL for other
- * values.  Takes effect at the next build / weights / apply call.          */
+ * apply_threads 64, 128 or 256; arrange 0, 1 or 2; chunks 1, 2 or 4 (used by
+ * arrangement 2).  HSM_EINVAL for other values.  Takes effect at the next
+ * build / weights / apply call; arrangement 2 with systems too large for the
+ * FP64 kernel's shared memory makes hsm_plan_build_stencils fail with
+ * HSM_EINVAL.                                                               */
 hsm_status hsm_plan_set_tuning(hsm_plan plan, int knn_qt, int rbf_lanes, int rbf_lanes32, int apply_threads,
-                               int grouped);
+                               int arrange, int chunks);
 
 /* Phases timed by hsm_plan_profile. */
 enum { HSM_PHASE_STENCILS = 0, HSM_PHASE_MON = 1, HSM_PHASE_RBF = 2, HSM_PHASE_APPLY = 3,
@@ -269,7 +282,10 @@ enum { HSM_PHASE_STENCILS = 0, HSM_PHASE_MON = 1, HSM_PHASE_RBF = 2, HSM_PHASE_A
 /* Device time of the last run of each phase, measured with CUDA events that
  * the library records on the plan's stream around the phase's kernels (only
  * while timing is enabled with hsm_plan_set_timing), and the number of kernels
- * the plan has launched since it was created.
+ * the plan has launched since it was created.  With weights arrangement 2 the
+ * RBF-FD phase is the span of the solve's launches inside the stencil build
+ * (from the first chunk's start to the last chunk's end, overlapping the kNN
+ * search): it lies inside HSM_PHASE_STENCILS.
  *   phase_ms  host float [HSM_PHASE_COUNT] or NULL (milliseconds)
  *   launches  host int64 or NULL
  * Synchronises the plan's stream.                                           */

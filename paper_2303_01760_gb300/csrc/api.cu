@@ -9,6 +9,7 @@
 #include <functional>
 #include <map>
 #include <mutex>
+#include <optional>
 #include <sstream>
 
 #include "common.cuh"
@@ -322,6 +323,10 @@ hsm_status hsm_plan_compute_weights(hsm_plan p, hsm_prec prec, uint8_t* node_sta
   // after it, here for later ones
   const bool fresh = p->counters_fresh;
   p->counters_fresh = false;
+  // the build solved both groups in FP64 (weights arrangement 2): the first
+  // FP64 call after it without per-node status only reads the status words
+  const bool from_build = p->rbf_from_build && fresh && prec == HSM_PREC_FP64 && !node_status;
+  p->rbf_from_build = false;
   if (!fresh) HSM_CUDA(p, cudaMemsetAsync(p->dev_flags, 0, sizeof(unsigned), s));
   if (p->m >= 2 && p->sing_cap < p->rbf.count) {
     dev_free(&p->sing_list, s);
@@ -332,21 +337,28 @@ hsm_status hsm_plan_compute_weights(hsm_plan p, hsm_prec prec, uint8_t* node_sta
   if (!fresh) HSM_CUDA(p, cudaMemsetAsync(p->dev_count + 1, 0, sizeof(int), s));
   p->n_reduced = 0;
   // a phase this call does not run reports 0 in hsm_plan_profile
-  p->ev_used[HSM_PHASE_MON] = p->ev_used[HSM_PHASE_RBF] = false;
+  // (the RBF-FD phase of an in-build solve is the span of its launches, kept)
+  p->ev_used[HSM_PHASE_MON] = false;
+  if (!from_build) p->ev_used[HSM_PHASE_RBF] = false;
   hsm_status st = HSM_OK;
   // The MON weights: in the grouped FP64 launch (timed as the RBF-FD phase),
   // else from the stencil build -- computed again here only when the build
   // did not compute them (a grouped plan in another mode) or the caller asks
   // for per-node status
-  const bool grouped = p->tune.grouped && prec == HSM_PREC_FP64;
-  if (!grouped && (node_status || p->tune.grouped)) {
+  const bool grouped = p->tune.arrange == 1 && prec == HSM_PREC_FP64;
+  if (!grouped && (node_status || p->tune.arrange == 1)) {
     PhaseTimer tm(p, HSM_PHASE_MON);
     st = compute_mon_weights(p, node_status);
   }
   if (st != HSM_OK) return st;
   p->n_fallback = 0;
-  PhaseTimer tm_rbf(p, HSM_PHASE_RBF);
-  if (prec == HSM_PREC_FP64) {
+  // the RBF-FD phase runs to the end of the call (the status read-back and
+  // the degree retries included), unless the build solved the group
+  std::optional<PhaseTimer> tm_rbf;
+  if (!from_build) tm_rbf.emplace(p, HSM_PHASE_RBF);
+  if (from_build) {
+    // computed by the build
+  } else if (prec == HSM_PREC_FP64) {
     st = grouped ? compute_weights_grouped_fp64(p, node_status)
                  : compute_rbf_weights_fp64(p, nullptr, p->rbf.count, node_status);
     if (st != HSM_OK) return st;
@@ -397,7 +409,9 @@ hsm_status hsm_plan_compute_weights(hsm_plan p, hsm_prec prec, uint8_t* node_sta
   const bool retry = p->m >= 2 && p->sing_cap >= p->rbf.count && p->rbf.count;
   p->hrb[0] = 0;
   if (retry) HSM_CUDA(p, cudaMemcpyAsync(p->hrb, p->dev_count + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
-  HSM_CUDA(p, cudaMemcpyAsync(p->hrb + 1, p->dev_flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  // (the in-build solve keeps its status in the second word)
+  HSM_CUDA(p, cudaMemcpyAsync(p->hrb + 1, p->dev_flags + (from_build ? 1 : 0), sizeof(unsigned),
+                              cudaMemcpyDeviceToHost, s));
   HSM_CUDA(p, cudaStreamSynchronize(s));
   unsigned flags = (unsigned)p->hrb[1];
   if (retry) {
@@ -601,19 +615,20 @@ static float time_ms(cudaStream_t s, const std::function<hsm_status()>& f, int r
 }
 
 hsm_status hsm_plan_tuning(hsm_plan p, int* knn_qt, int* rbf_lanes, int* rbf_lanes32, int* apply_threads,
-                           int* grouped, int* tuned) {
+                           int* arrange, int* chunks, int* tuned) {
   if (!p) return set_error(nullptr, HSM_EINVAL, "plan is NULL");
   if (knn_qt) *knn_qt = p->tune.knn_qt;
   if (rbf_lanes) *rbf_lanes = p->tune.rbf_lanes;
   if (rbf_lanes32) *rbf_lanes32 = p->tune.rbf_lanes32;
   if (apply_threads) *apply_threads = p->tune.apply_threads;
-  if (grouped) *grouped = p->tune.grouped ? 1 : 0;
+  if (arrange) *arrange = p->tune.arrange;
+  if (chunks) *chunks = p->tune.chunks;
   if (tuned) *tuned = p->tune.tuned ? 1 : 0;
   return HSM_OK;
 }
 
 hsm_status hsm_plan_set_tuning(hsm_plan p, int knn_qt, int rbf_lanes, int rbf_lanes32, int apply_threads,
-                               int grouped) {
+                               int arrange, int chunks) {
   if (!p) return set_error(nullptr, HSM_EINVAL, "plan is NULL");
   auto in = [](int v, std::initializer_list<int> ok) {
     for (int o : ok)
@@ -621,13 +636,14 @@ hsm_status hsm_plan_set_tuning(hsm_plan p, int knn_qt, int rbf_lanes, int rbf_la
     return false;
   };
   if (!in(knn_qt, {1, 2, 4}) || !in(rbf_lanes, {4, 8, 16, 32}) || !in(rbf_lanes32, {4, 8, 16, 32}) ||
-      !in(apply_threads, {64, 128, 256}) || !in(grouped, {0, 1}))
+      !in(apply_threads, {64, 128, 256}) || !in(arrange, {0, 1, 2}) || !in(chunks, {1, 2, 4}))
     return set_error(p, HSM_EINVAL, "unknown kernel variant");
   p->tune.knn_qt = knn_qt;
   p->tune.rbf_lanes = rbf_lanes;
   p->tune.rbf_lanes32 = rbf_lanes32;
   p->tune.apply_threads = apply_threads;
-  p->tune.grouped = grouped != 0;
+  p->tune.arrange = arrange;
+  p->tune.chunks = chunks;
   return HSM_OK;
 }
 
@@ -642,14 +658,15 @@ hsm_status hsm_plan_autotune(hsm_plan p, const char* cache_path) {
     while (in >> k >> v) cache[k] = v;
     auto it = cache.find(key);
     if (it != cache.end()) {
-      int t = 0, l = 0, qv = 1, l32 = 8, gr = 0;
-      if (sscanf(it->second.c_str(), "%d,%d,%d,%d,%d", &t, &l, &qv, &l32, &gr) >= 2 && t > 0 && l > 0 &&
-          (qv == 1 || qv == 2 || qv == 4)) {
+      int t = 0, l = 0, qv = 1, l32 = 8, ar = 0, ch = 1;
+      if (sscanf(it->second.c_str(), "%d,%d,%d,%d,%d,%d", &t, &l, &qv, &l32, &ar, &ch) >= 2 && t > 0 && l > 0 &&
+          (qv == 1 || qv == 2 || qv == 4) && ar >= 0 && ar <= 2 && (ch == 1 || ch == 2 || ch == 4)) {
         p->tune.apply_threads = t;
         p->tune.rbf_lanes = l;
         p->tune.knn_qt = qv;
         p->tune.rbf_lanes32 = l32;
-        p->tune.grouped = gr != 0;
+        p->tune.arrange = ar;
+        p->tune.chunks = ch;
         p->tune.tuned = true;
         return HSM_OK;
       }
@@ -710,26 +727,35 @@ hsm_status hsm_plan_autotune(hsm_plan p, const char* cache_path) {
   p->tune.rbf_lanes = best_l;
   p->tune.rbf_lanes32 = best_l32;
   // FP64 weights of both groups: MON beside the kNN search in the build graph
-  // plus one RBF-FD launch, or one grouped persistent launch; each timed as a
-  // whole build and weights pass
+  // plus one RBF-FD launch, one grouped persistent launch, or both groups in
+  // the build graph with the RBF-FD solve in 1, 2 or 4 chunks beside the kNN
+  // search; each timed as a whole build and weights pass
   {
     float best_ms = 1e30f;
-    bool best_g = p->tune.grouped;
-    for (bool gr : {false, true}) {
-      p->tune.grouped = gr;
+    int best_a = p->tune.arrange, best_c = p->tune.chunks;
+    const int cand[][2] = {{0, 1}, {1, 1}, {2, 1}, {2, 2}, {2, 4}};
+    for (const auto& ac : cand) {
+      p->tune.arrange = ac[0];
+      p->tune.chunks = ac[1];
       float ms = time_ms(s, [&]() {
         hsm_status r = hsm_plan_build_stencils(p);
         if (r != HSM_OK) return r;
         r = hsm_plan_compute_weights(p, HSM_PREC_FP64, nullptr);
         return r == HSM_ESINGULAR ? HSM_OK : r;
       }, 2, &st);
+      if (st == HSM_EINVAL && ac[0] == 2) {  // systems too large for the in-build arrangement
+        st = HSM_OK;
+        continue;
+      }
       if (st != HSM_OK) return st;
       if (ms < best_ms) {
         best_ms = ms;
-        best_g = gr;
+        best_a = ac[0];
+        best_c = ac[1];
       }
     }
-    p->tune.grouped = best_g;
+    p->tune.arrange = best_a;
+    p->tune.chunks = best_c;
     st = hsm_plan_build_stencils(p);
     if (st != HSM_OK) return st;
   }
@@ -761,7 +787,8 @@ hsm_status hsm_plan_autotune(hsm_plan p, const char* cache_path) {
   p->tune.tuned = true;
   if (cache_path) {
     std::ostringstream v;
-    v << best_t << "," << best_l << "," << p->tune.knn_qt << "," << best_l32 << "," << (p->tune.grouped ? 1 : 0);
+    v << best_t << "," << best_l << "," << p->tune.knn_qt << "," << best_l32 << "," << p->tune.arrange << ","
+      << p->tune.chunks;
     cache[key] = v.str();
     std::ofstream o(cache_path, std::ios::trunc);
     for (auto& kv : cache) o << kv.first << " " << kv.second << "\n";

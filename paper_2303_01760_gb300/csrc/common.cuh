@@ -13,6 +13,7 @@
 namespace hsm {
 
 constexpr int kMaxDim = 3;
+constexpr int kMaxBuildChunks = 4;  // kNN / RBF-FD solve chunks of the stencil build
 constexpr int kMaxOps = 4;
 constexpr int kMaxStencil = 128;
 constexpr int kMaxMonomials = 84;           // C(6+3, 3): m <= 6 in 3D
@@ -42,10 +43,14 @@ struct Tuning {
   int rbf_lanes = 8;        // lanes per FP64 RBF-FD weight system (4, 8, 16, 32)
   int rbf_lanes32 = 8;      // lanes per FP32 + refinement weight system (4, 8, 16, 32)
   int knn_qt = 1;           // threads per kNN query (1, 2 or 4)
-  // FP64 weights: false = MON weights beside the kNN search in the stencil
-  // build graph, then one RBF-FD launch; true = both groups in one persistent
-  // launch with a work queue (k_weights_grouped)
-  bool grouped = false;
+  // FP64 weights (arrange): 0 = MON weights beside the kNN search in the
+  // stencil build graph, then one RBF-FD launch in the weights call; 1 = both
+  // groups in one persistent launch with a work queue (k_weights_grouped);
+  // 2 = both groups in the stencil build graph: MON beside the kNN search,
+  // and the RBF-FD group in `chunks` chunks, chunk c solved on a second
+  // branch while the kNN search runs on chunk c + 1
+  int arrange = 0;
+  int chunks = 1;  // 1, 2 or 4 (arrange 2)
   bool tuned = false;
 };
 
@@ -78,13 +83,19 @@ struct BuildWs {
   int* readback = nullptr;             // pinned host: demoted, n_mon, n_rbf, flags
   cudaGraphExec_t graph = nullptr;
   int graph_qt = 0;                    // kNN variant the graph was captured with
-  bool graph_grouped = false;          // captured without the MON weights branch
+  int graph_arrange = 0;               // weights arrangement the graph was captured with
+  int graph_chunks = 0;
+  bool graph_timing = false;           // captured with the in-build solve's phase events
+  const double* graph_w64 = nullptr;   // RBF-FD weight array and singular list the graph writes
+  const int32_t* graph_sing = nullptr;
   const double* graph_spacing = nullptr;  // spacing array the graph was captured with
   int graph_kernels = 0;               // kernels per replay
   cudaStream_t cap = nullptr;
   cudaStream_t side = nullptr;         // capture branch of the MON stencils
   cudaStream_t side2 = nullptr;        // capture branch of the cell scan and scatter
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fork2 = nullptr, ev_join2 = nullptr;
+  cudaStream_t side3 = nullptr;        // capture branch of the in-build RBF-FD solve (arrange 2)
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fork2 = nullptr, ev_join2 = nullptr, ev_join3 = nullptr;
+  cudaEvent_t ev_chunk[kMaxBuildChunks] = {};  // kNN chunk c done
   bool ready = false;
 };
 
@@ -130,6 +141,7 @@ struct hsm_plan_s {
   unsigned* check_flag = nullptr;  // device flag of the validation scan
   int* hrb = nullptr;              // pinned host words for the weights call's read-backs
   bool counters_fresh = false;     // the build cleared the weights call's status words
+  bool rbf_from_build = false;     // the last build solved the RBF-FD weights in FP64 (arrange 2)
   hsm::Tuning tune;
   hsm_mlp mlp = nullptr;         // attached learned predictor (not owned)
   // batch validation of the learned weights: `gate_samples` stencils of the
@@ -236,6 +248,12 @@ void free_build_ws(hsm_plan p);
 // ---- weights.cu ----------------------------------------------------------
 // MON weights enqueued inside the stencil build (count read on the device).
 cudaError_t enqueue_mon_weights(hsm_plan p, const int* count_dev, double* w, cudaStream_t s);
+// FP64 RBF-FD weights of chunk `chunk` of `nchunks` equal chunks of the group
+// into w ([nops][n][G], G read from *G_dev on the device), on stream s; the
+// stencil build enqueues one per kNN chunk.  rbf_chunk_ready sets up the
+// kernel's launch shape (call it before a stream capture).
+cudaError_t rbf_chunk_ready(hsm_plan p);
+cudaError_t enqueue_rbf_chunk(hsm_plan p, const int* G_dev, double* w, int chunk, int nchunks, cudaStream_t s);
 // FP64 weights of both stencil groups (MON and RBF-FD) in one persistent
 // launch with a work queue (k_weights_grouped); MON status codes as k_mon's.
 hsm_status compute_weights_grouped_fp64(hsm_plan p, uint8_t* status);

@@ -572,10 +572,12 @@ __device__ __forceinline__ void flat2(int R, int C, int lane, F&& f) {
 // FP64 RBF-FD systems at positions t0, t0 + stride, ... < t_end of the
 // launch's list, solved by the lane group whose system memory starts at xi
 // (sys_doubles doubles); par and cor are the monomial parent tables of the
-// block.
-template <int DIM, int NOPS, int LANES>
+// block.  The group size (the stride of idx and w) is a.G, or G_arg when
+// DEV_G (a size read on the device).
+template <int DIM, int NOPS, int LANES, bool DEV_G = false>
 __device__ __forceinline__ void rbf64_systems(const RbfArgs& a, int64_t t0, int64_t t_end, int64_t stride, int lane,
-                                              unsigned mask, double* xi, const int8_t* par, const int8_t* cor) {
+                                              unsigned mask, double* xi, const int8_t* par, const int8_t* cor,
+                                              int64_t G_arg = 0) {
   const int n = a.n, m = a.n_mono, r = n - m, rc_ = r + NOPS;
   const int ldB = rc_ | 1;
   double* rc = xi + n * DIM;
@@ -591,7 +593,7 @@ __device__ __forceinline__ void rbf64_systems(const RbfArgs& a, int64_t t0, int6
     // ---- offsets, the power-of-two scale, |xi| and the monomial rows of P
     unsigned long long bmax = 0ull;
     for (int j = lane; j < n; j += LANES) {
-      const int32_t id = a.idx[(int64_t)j * a.G + pos];
+      const int32_t id = a.idx[(int64_t)j * (DEV_G ? G_arg : a.G) + pos];
       double r2 = 0.0;
   #pragma unroll
       for (int k = 0; k < DIM; ++k) {
@@ -770,7 +772,7 @@ __device__ __forceinline__ void rbf64_systems(const RbfArgs& a, int64_t t0, int6
       auto put = [&](int i, int o, double v) {
         v *= a.ops.kind[o] == 3 ? inv_s2 : inv_s;
         const bool fin = ((unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull) < 0x7ff0000000000000ull;
-        a.w[((int64_t)o * n + perm[i]) * a.G + pos] = fin ? v : 0.0;
+        a.w[((int64_t)o * n + perm[i]) * (DEV_G ? G_arg : a.G) + pos] = fin ? v : 0.0;
       };
       flat2<LANES>(m, NOPS, lane, [&](int i, int o) {
         double v = Pw[(n + o) * m + i];
@@ -779,7 +781,8 @@ __device__ __forceinline__ void rbf64_systems(const RbfArgs& a, int64_t t0, int6
       });
       flat2<LANES>(r, NOPS, lane, [&](int j, int o) { put(m + j, o, Sm[j * ldB + r + o]); });
     } else {
-      flat2<LANES>(n, NOPS, lane, [&](int i, int o) { a.w[((int64_t)o * n + i) * a.G + pos] = 0.0; });
+      flat2<LANES>(n, NOPS, lane,
+                   [&](int i, int o) { a.w[((int64_t)o * n + i) * (DEV_G ? G_arg : a.G) + pos] = 0.0; });
     }
     if (lane == 0) {
       const int32_t node = a.nodes[pos];
@@ -809,6 +812,29 @@ __global__ void __launch_bounds__(256) k_rbf_fp64(RbfArgs a) {
   __syncthreads();
   rbf64_systems<DIM, NOPS, LANES>(a, (int64_t)blockIdx.x * SYS + sub, a.count, (int64_t)gridDim.x * SYS, lane, mask,
                                   xi, par, cor);
+}
+
+// The same solve for chunk `chunk` of `nchunks` equal chunks of the whole
+// group, whose size G is read on the device (the stencil build enqueues it
+// before the group sizes reach the host): positions [chunk C, chunk C + C)
+// clipped to G, C = ceil(G / nchunks).  Blocks past the chunk return at once.
+template <int DIM, int NOPS, int LANES>
+__global__ void __launch_bounds__(256) k_rbf_fp64_chunk(RbfArgs a, const int* __restrict__ G_dev, int chunk,
+                                                         int nchunks) {
+  extern __shared__ double smem[];
+  const int64_t G = *G_dev;
+  const int64_t C = (G + nchunks - 1) / nchunks;
+  const int64_t lo = min(G, (int64_t)chunk * C), hi = min(G, lo + C);
+  const int SYS = blockDim.x / LANES;
+  if ((int64_t)blockIdx.x * SYS >= hi - lo) return;
+  const int sub = threadIdx.x / LANES, lane = threadIdx.x % LANES;
+  const unsigned mask = LANES == 32 ? 0xffffffffu : (((1u << LANES) - 1u) << ((threadIdx.x & 31) / LANES * LANES));
+  double* xi = smem + (size_t)sub * sys_doubles(DIM, NOPS, a.n, a.n_mono);
+  __shared__ int8_t par[kMaxMonomials], cor[kMaxMonomials];
+  mono_parents(a.mono_exp, a.n_mono, DIM, par, cor);
+  __syncthreads();
+  rbf64_systems<DIM, NOPS, LANES, true>(a, lo + (int64_t)blockIdx.x * SYS + sub, hi, (int64_t)gridDim.x * SYS, lane,
+                                        mask, xi, par, cor, G);
 }
 
 // FP32 factorization with FP64 iterative refinement.  The FP32 matrix is

@@ -397,16 +397,18 @@ __device__ __forceinline__ void classify_node(const int32_t* __restrict__ ijk, c
     int q[DIM];
 #pragma unroll
     for (int k = 0; k < DIM; ++k) q[k] = ijk[k * N + i];
-    mon = g.find<DIM>(q) == (int32_t)i;
+    // every lookup is made (no short circuit), so their loads are in flight together
+    bool all = g.find<DIM>(q) == (int32_t)i;
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
 #pragma unroll
       for (int s = -1; s <= 1; s += 2) {
         q[k] += s;
-        mon = mon && g.find<DIM>(q) != kEmpty;
+        all = all & (g.find<DIM>(q) != kEmpty);
         q[k] -= s;
       }
     }
+    mon = all;
   }
   kind[i] = mon ? 0 : 1;
   if (reg && !mon) atomicAdd(n_demoted, 1);
@@ -444,10 +446,11 @@ struct CellGrid {
   double cell;
   int g[kMaxDim];
   int dim;
+  // floor((x - lo) / cell) clamped to the grid: the conversion rounds down
+  // and saturates, the clamp is integer arithmetic (a NaN lands in cell 0)
   __device__ __forceinline__ int cell_of(double x, int k) const {
-    double t = floor((x - lo[k]) * inv_cell);
-    int c = (int)fmin(fmax(t, 0.0), (double)(g[k] - 1));
-    return c;
+    const int c = __double2int_rd(__dmul_rn(__dsub_rn(x, lo[k]), inv_cell));
+    return min(max(c, 0), g[k] - 1);
   }
 };
 
@@ -575,7 +578,7 @@ __global__ void __launch_bounds__(32 * QT, 1) k_knn(const double* __restrict__ c
                                              const int32_t* __restrict__ start, const int32_t* __restrict__ sorted_id,
                                              const double* __restrict__ sorted_xyz,
                                              const uint8_t* __restrict__ sorted_bnd, int32_t* __restrict__ out_idx,
-                                             unsigned* flags) {
+                                             unsigned* flags, int chunk, int nchunks) {
   constexpr int RMAX = DIM == 2 ? 6 : 4;
   // node loads in flight per thread: 8 when a query has several threads (a
   // 2D window row of ~7 nodes in one round trip), 4 with one thread per query
@@ -584,6 +587,9 @@ __global__ void __launch_bounds__(32 * QT, 1) k_knn(const double* __restrict__ c
   extern __shared__ unsigned char smem_raw[];
   const int B = blockDim.x;
   const int64_t nq = *nq_dev;  // the stride of out_idx
+  // this launch's queries: chunk `chunk` of `nchunks` equal chunks
+  const int64_t qc = (nq + nchunks - 1) / nchunks;
+  const int64_t q_lo = min(nq, (int64_t)chunk * qc), q_hi = min(nq, q_lo + qc);
   const CellGrid cg = *cgp;
   double* kd = reinterpret_cast<double*>(smem_raw);
   int32_t* ki = reinterpret_cast<int32_t*>(kd + (size_t)n_full * B);
@@ -591,7 +597,7 @@ __global__ void __launch_bounds__(32 * QT, 1) k_knn(const double* __restrict__ c
   const int lane = t & 31;
   const unsigned qmask = ((1u << QT) - 1u) << (lane - sub);
   const int64_t qpb = B / QT;
-  for (int64_t qi = blockIdx.x * qpb + t / QT; qi < nq; qi += (int64_t)gridDim.x * qpb) {
+  for (int64_t qi = q_lo + blockIdx.x * qpb + t / QT; qi < q_hi; qi += (int64_t)gridDim.x * qpb) {
     const int32_t c = queries[qi];
     const bool bnd_center = is_boundary && is_boundary[c];
     // boundary nodes: search the n-1 interior nodes nearest to x_c - h n_c
@@ -867,8 +873,10 @@ hsm_status alloc_build_ws(hsm_plan p) {
   HSM_CUDA(p, cudaStreamCreateWithFlags(&w.cap, cudaStreamNonBlocking));
   HSM_CUDA(p, cudaStreamCreateWithFlags(&w.side, cudaStreamNonBlocking));
   HSM_CUDA(p, cudaStreamCreateWithFlags(&w.side2, cudaStreamNonBlocking));
-  for (cudaEvent_t* e : {&w.ev_fork, &w.ev_join, &w.ev_fork2, &w.ev_join2})
+  HSM_CUDA(p, cudaStreamCreateWithFlags(&w.side3, cudaStreamNonBlocking));
+  for (cudaEvent_t* e : {&w.ev_fork, &w.ev_join, &w.ev_fork2, &w.ev_join2, &w.ev_join3})
     HSM_CUDA(p, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  for (cudaEvent_t& e : w.ev_chunk) HSM_CUDA(p, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   w.ready = true;
   return HSM_OK;
 }
@@ -888,11 +896,16 @@ void free_build_ws(hsm_plan p) {
   if (w.cap) cudaStreamDestroy(w.cap);
   if (w.side) cudaStreamDestroy(w.side);
   if (w.side2) cudaStreamDestroy(w.side2);
-  for (cudaEvent_t* e : {&w.ev_fork, &w.ev_join, &w.ev_fork2, &w.ev_join2}) {
+  if (w.side3) cudaStreamDestroy(w.side3);
+  for (cudaEvent_t& e : w.ev_chunk) {
+    if (e) cudaEventDestroy(e);
+    e = nullptr;
+  }
+  for (cudaEvent_t* e : {&w.ev_fork, &w.ev_join, &w.ev_fork2, &w.ev_join2, &w.ev_join3}) {
     if (*e) cudaEventDestroy(*e);
     *e = nullptr;
   }
-  w.cap = w.side = w.side2 = nullptr;
+  w.cap = w.side = w.side2 = w.side3 = nullptr;
   w.ready = false;
 }
 
@@ -988,7 +1001,7 @@ cudaError_t enqueue_build(hsm_plan p, cudaStream_t s, int qt, int* nk) {
   // MON weights on the same branch (unless the plan solves both groups in the
   // grouped weights launch): they need only the MON stencils and run beside
   // the kNN search, which leaves most of each SM idle
-  if (!p->tune.grouped) {
+  if (p->tune.arrange != 1) {
     HSM_TRY(enqueue_mon_weights(p, counts, w.mon_w64, w.side));
     ++k;
   }
@@ -997,10 +1010,13 @@ cudaError_t enqueue_build(hsm_plan p, cudaStream_t s, int qt, int* nk) {
   // ---- kNN for the RBF-FD group, once the cells are sorted
   HSM_TRY(cudaStreamWaitEvent(s, w.ev_join2, 0));
   {
-    // qt threads per query (1, 2 or 4), blocks of 32 * qt
+    // qt threads per query (1, 2 or 4), blocks of 32 * qt; with the weights
+    // in the build, the queries in nch chunks, the RBF-FD weights of chunk c
+    // solved on a branch of their own while the search runs on chunk c + 1
+    const int nch = p->tune.arrange == 2 ? p->tune.chunks : 1;
     const int KT = 32 * qt;
     size_t smem = (size_t)p->n * KT * (sizeof(double) + sizeof(int32_t));
-    int gk = (int)std::min<int64_t>(ceil_div(N, 32), (int64_t)num_sms() * 16);
+    int gk = (int)std::min<int64_t>(ceil_div(ceil_div(N, nch), 32), (int64_t)num_sms() * 16);
     void* fn = nullptr;
     if (dim == 2) fn = qt == 4 ? (void*)k_knn<2, 4> : (qt == 2 ? (void*)k_knn<2, 2> : (void*)k_knn<2, 1>);
     else fn = qt == 4 ? (void*)k_knn<3, 4> : (qt == 2 ? (void*)k_knn<3, 2> : (void*)k_knn<3, 1>);
@@ -1024,11 +1040,27 @@ cudaError_t enqueue_build(hsm_plan p, cudaStream_t s, int qt, int* nk) {
     // set than of the lattice
     const double omega = dim == 2 ? M_PI : 4.0 * M_PI / 3.0;
     double rfac = 1.1 * std::pow((double)p->n / omega, 1.0 / dim);
+    int c = 0, nc = nch;
     void* args[] = {(void*)&coords, (void*)&NN, (void*)&isb, (void*)&nrm, (void*)&hh, (void*)&spc, (void*)&qlist,
                     (void*)&nqd, (void*)&nf, (void*)&rfac, (void*)&cgd, (void*)&cs, (void*)&sid, (void*)&sxyz,
-                    (void*)&sb, (void*)&outp, (void*)&fl};
-    HSM_TRY(cudaLaunchKernel(fn, dim3(gk), dim3(KT), args, smem, s));
-    ++k;
+                    (void*)&sb, (void*)&outp, (void*)&fl, (void*)&c, (void*)&nc};
+    for (c = 0; c < nch; ++c) {
+      HSM_TRY(cudaLaunchKernel(fn, dim3(gk), dim3(KT), args, smem, s));
+      ++k;
+      if (p->tune.arrange != 2) continue;
+      HSM_TRY(cudaEventRecord(w.ev_chunk[c], s));
+      HSM_TRY(cudaStreamWaitEvent(w.side3, w.ev_chunk[c], 0));
+      if (c == 0 && p->timing)
+        HSM_TRY(cudaEventRecordWithFlags(p->ev[2 * HSM_PHASE_RBF], w.side3, cudaEventRecordExternal));
+      HSM_TRY(enqueue_rbf_chunk(p, nqd, p->rbf.w64, c, nch, w.side3));
+      ++k;
+    }
+    if (p->tune.arrange == 2) {
+      if (p->timing)
+        HSM_TRY(cudaEventRecordWithFlags(p->ev[2 * HSM_PHASE_RBF + 1], w.side3, cudaEventRecordExternal));
+      HSM_TRY(cudaEventRecord(w.ev_join3, w.side3));
+      HSM_TRY(cudaStreamWaitEvent(s, w.ev_join3, 0));
+    }
   }
   // ---- status bits next to the counters, then the one read-back
   HSM_TRY(cudaStreamWaitEvent(s, w.ev_join, 0));
@@ -1051,7 +1083,34 @@ hsm_status build_stencils(hsm_plan p) {
   BuildWs& w = p->ws;
   cudaStream_t s = p->stream;
   const int qt = p->tune.knn_qt == 4 ? 4 : (p->tune.knn_qt == 2 ? 2 : 1);
-  if (!w.graph || w.graph_qt != qt || w.graph_spacing != p->spacing || w.graph_grouped != p->tune.grouped) {
+  const bool in_build = p->tune.arrange == 2;
+  if (in_build) {
+    // the in-build solve writes the plan's RBF-FD weight array and singular
+    // list, sized here for a group of every node (the graph keeps the pointers)
+    const int64_t need = (int64_t)p->nops * p->n * p->N;
+    if (!p->rbf.w64 || p->rbf.w64_cap < need) {
+      dev_free(&p->rbf.w64, s);
+      p->rbf.w64_cap = 0;
+      HSM_CUDA(p, dev_alloc(&p->rbf.w64, (size_t)need, s));
+      p->rbf.w64_cap = need;
+    }
+    if (p->m >= 2 && p->sing_cap < p->N) {
+      dev_free(&p->sing_list, s);
+      p->sing_cap = 0;
+      HSM_CUDA(p, dev_alloc(&p->sing_list, 2 * (size_t)p->N, s));
+      p->sing_cap = p->N;
+    }
+    if (rbf_chunk_ready(p) != cudaSuccess)
+      return set_error(p, HSM_EINVAL, "RBF-FD system too large for the in-build weights arrangement");
+    if (p->timing && !p->ev[2 * HSM_PHASE_RBF]) {
+      HSM_CUDA(p, cudaEventCreate(&p->ev[2 * HSM_PHASE_RBF]));
+      HSM_CUDA(p, cudaEventCreate(&p->ev[2 * HSM_PHASE_RBF + 1]));
+    }
+  }
+  const bool timing = in_build && p->timing;
+  if (!w.graph || w.graph_qt != qt || w.graph_spacing != p->spacing || w.graph_arrange != p->tune.arrange ||
+      w.graph_chunks != p->tune.chunks || w.graph_timing != timing ||
+      (in_build && (w.graph_w64 != p->rbf.w64 || w.graph_sing != p->sing_list))) {
     if (w.graph) cudaGraphExecDestroy(w.graph);
     w.graph = nullptr;
     // kernel attributes are set outside the capture
@@ -1076,12 +1135,18 @@ hsm_status build_stencils(hsm_plan p) {
     }
     w.graph_qt = qt;
     w.graph_spacing = p->spacing;
-    w.graph_grouped = p->tune.grouped;
+    w.graph_arrange = p->tune.arrange;
+    w.graph_chunks = p->tune.chunks;
+    w.graph_timing = timing;
+    w.graph_w64 = p->rbf.w64;
+    w.graph_sing = p->sing_list;
     w.graph_kernels = nk;
   }
   HSM_CUDA(p, cudaGraphLaunch(w.graph, s));
   p->launches += w.graph_kernels;
   p->counters_fresh = true;  // k_bounds cleared the weights call's status words
+  p->rbf_from_build = in_build;
+  if (timing) p->ev_used[HSM_PHASE_RBF] = true;
   HSM_CUDA(p, cudaStreamSynchronize(s));
   const int* rb = w.readback;
   p->n_demoted = rb[0];

@@ -296,6 +296,10 @@ struct Fp64Kernel {
   static void* ptr() { return (void*)k_rbf_fp64<DIM, NOPS, LANES>; }
 };
 template <int DIM, int NOPS, int LANES>
+struct Fp64ChunkKernel {
+  static void* ptr() { return (void*)k_rbf_fp64_chunk<DIM, NOPS, LANES>; }
+};
+template <int DIM, int NOPS, int LANES>
 struct Fp32rKernel {
   static void* ptr() { return (void*)k_rbf_fp32r<DIM, NOPS, LANES, 0>; }
 };
@@ -337,8 +341,8 @@ struct RbfShape {
   size_t smem = 0;
 };
 
-cudaError_t rbf_shape(bool r32, int dim, int nops, int K, int ld, int n, int lanes, RbfShape* out,
-                      bool grouped = false) {
+// kind (FP64): 0 k_rbf_fp64, 1 k_weights_grouped, 2 k_rbf_fp64_chunk
+cudaError_t rbf_shape(bool r32, int dim, int nops, int K, int ld, int n, int lanes, RbfShape* out, int kind = 0) {
   struct Entry {
     void* fn;
     size_t per;
@@ -350,7 +354,8 @@ cudaError_t rbf_shape(bool r32, int dim, int nops, int K, int ld, int n, int lan
     void* fn = r32 ? pick_fp32r_fixed(dim, nops, K, lanes) : nullptr;
     if (!fn)
       fn = r32 ? pick<Fp32rKernel>(dim, nops, lanes)
-               : (grouped ? pick<GroupedKernel>(dim, nops, lanes) : pick<Fp64Kernel>(dim, nops, lanes));
+               : kind == 1 ? pick<GroupedKernel>(dim, nops, lanes)
+                           : (kind == 2 ? pick<Fp64ChunkKernel>(dim, nops, lanes) : pick<Fp64Kernel>(dim, nops, lanes));
     for (const Entry& e : cache)
       if (e.fn == fn && e.per == per) {
         *out = e.shape;
@@ -466,7 +471,7 @@ hsm_status launch_grouped_fp64(hsm_plan p, uint8_t* status) {
   MonArgs mo{p->coords, p->N, p->mon.idx, p->mon.count, make_ops(p, p->op_mask), p->mon.w64, status,
              p->mon.nodes, p->dev_flags};
   RbfShape sh;
-  HSM_CUDA(p, rbf_shape(false, p->dim, p->nops, a.K, a.ld, a.n, p->tune.rbf_lanes, &sh, true));
+  HSM_CUDA(p, rbf_shape(false, p->dim, p->nops, a.K, a.ld, a.n, p->tune.rbf_lanes, &sh, 1));
   if (!sh.fn) return set_error(p, HSM_EINVAL, "RBF-FD system too large for shared memory");
   const int spb = sh.threads / sh.lanes;
   const int64_t mon_items = ceil_div(p->mon.count, sh.threads);
@@ -486,6 +491,62 @@ hsm_status launch_grouped_fp64(hsm_plan p, uint8_t* status) {
 }  // namespace
 
 hsm_status compute_weights_grouped_fp64(hsm_plan p, uint8_t* status) { return launch_grouped_fp64(p, status); }
+
+// Arguments of the FP64 solve of the whole RBF-FD group into w, the group
+// size left to the device (chunk launches of the stencil build).
+static RbfArgs chunk_args(hsm_plan p, double* w) {
+  RbfArgs a{};
+  a.coords = p->coords;
+  a.N = p->N;
+  a.list = nullptr;
+  a.idx = p->rbf.idx;
+  a.nodes = p->rbf.nodes;
+  a.n = p->n;
+  a.n_mono = p->n_mono;
+  a.K = p->n + p->n_mono;
+  a.ld = (a.K + p->nops) | 1;
+  a.mono_exp = p->mono_exp;
+  a.pairs = p->pairs;
+  a.ops = make_ops(p, p->op_mask);
+  a.w = w;
+  a.status = nullptr;
+  a.is_regular = p->is_regular;
+  // its own status word (the second of the plan's four): the build reads the
+  // first back as its own status, and the weights call reads this one
+  a.flags = p->dev_flags + 1;
+  // singular systems are recorded for the lower-degree retry of the weights
+  // call; the list has room for every node
+  const bool rec = p->sing_list && p->sing_cap >= p->N;
+  a.sing_list = rec ? p->sing_list : nullptr;
+  a.sing_count = rec ? p->dev_count + 1 : nullptr;
+  a.sing_cap = rec ? p->sing_cap : 0;
+  return a;
+}
+
+static cudaError_t rbf_chunk_shape(hsm_plan p, RbfShape* sh) {
+  const int K = p->n + p->n_mono;
+  return rbf_shape(false, p->dim, p->nops, K, (K + p->nops) | 1, p->n, p->tune.rbf_lanes, sh, 2);
+}
+
+cudaError_t rbf_chunk_ready(hsm_plan p) {
+  RbfShape sh;
+  cudaError_t e = rbf_chunk_shape(p, &sh);
+  if (e != cudaSuccess) return e;
+  return sh.fn ? cudaSuccess : cudaErrorInvalidConfiguration;
+}
+
+cudaError_t enqueue_rbf_chunk(hsm_plan p, const int* G_dev, double* w, int chunk, int nchunks, cudaStream_t s) {
+  RbfShape sh;
+  cudaError_t e = rbf_chunk_shape(p, &sh);
+  if (e != cudaSuccess) return e;
+  if (!sh.fn) return cudaErrorInvalidConfiguration;
+  RbfArgs a = chunk_args(p, w);
+  const int spb = sh.threads / sh.lanes;
+  // sized for the largest possible chunk; blocks past the real one return
+  const int grid = (int)std::min<int64_t>(ceil_div(ceil_div(p->N, nchunks), spb), (int64_t)num_sms() * sh.blocks_per_sm);
+  void* args[] = {&a, (void*)&G_dev, &chunk, &nchunks};
+  return cudaLaunchKernel(sh.fn, dim3(grid), dim3(sh.threads), args, sh.smem, s);
+}
 
 cudaError_t launch_rbf_external(const RbfExternal& x, bool r32, const int32_t* list, int64_t count, uint8_t* status,
                                 uint8_t mark, bool* too_big) {

@@ -66,8 +66,8 @@ _SIGS = {
     "hsm_plan_set_learned_gate": (C.c_int, [_p, C.c_double, _i64]),
     "hsm_plan_learned_gate": (C.c_int, [_p, C.POINTER(C.c_double), C.POINTER(C.c_int), C.POINTER(_i64)]),
     "hsm_plan_autotune": (C.c_int, [_p, C.c_char_p]),
-    "hsm_plan_tuning": (C.c_int, [_p] + [C.POINTER(C.c_int)] * 6),
-    "hsm_plan_set_tuning": (C.c_int, [_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]),
+    "hsm_plan_tuning": (C.c_int, [_p] + [C.POINTER(C.c_int)] * 7),
+    "hsm_plan_set_tuning": (C.c_int, [_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]),
     "hsm_plan_validate": (C.c_int, [_p]),
     "hsm_plan_set_checks": (C.c_int, [_p, C.c_int]),
     "hsm_plan_inject_fault": (C.c_int, [_p, C.c_int]),
@@ -384,14 +384,17 @@ class Plan:
     def inject_stencil_fault(self):
         check(lib.hsm_plan_inject_fault(self.h, HSM_FAULT_STENCIL_INDEX), self.h)
 
-    def set_tuning(self, knn_qt=1, rbf_lanes=8, rbf_lanes32=8, apply_threads=256, grouped=0):
+    def set_tuning(self, knn_qt=1, rbf_lanes=8, rbf_lanes32=8, apply_threads=256, arrange=0, chunks=1):
+        """arrange: 0 MON weights in the build and one RBF-FD launch, 1 one
+        grouped launch, 2 both groups in the build (RBF-FD in `chunks` chunks
+        beside the kNN search)."""
         check(lib.hsm_plan_set_tuning(self.h, int(knn_qt), int(rbf_lanes), int(rbf_lanes32), int(apply_threads),
-                                      int(grouped)), self.h)
+                                      int(arrange), int(chunks)), self.h)
 
     def tuning(self):
-        v = [C.c_int() for _ in range(6)]
+        v = [C.c_int() for _ in range(7)]
         check(lib.hsm_plan_tuning(self.h, *[C.byref(x) for x in v]), self.h)
-        return dict(zip(("knn_qt", "rbf_lanes", "rbf_lanes32", "apply_threads", "grouped", "tuned"),
+        return dict(zip(("knn_qt", "rbf_lanes", "rbf_lanes32", "apply_threads", "arrange", "chunks", "tuned"),
                         [x.value for x in v]))
 
     def close(self):
