@@ -310,7 +310,7 @@ RBF64_TRAFFIC_BYTES = 2465280 + 0
 GROUPED_TRAFFIC_BYTES = 9752832 + 18688
 # the same summed over the chunk launches of k_rbf_fp64_chunk<2, 3, 8> (the
 # solve inside the stencil build), per chunk count; absent: not captured
-CHUNK_TRAFFIC_BYTES = {}
+CHUNK_TRAFFIC_BYTES = {1: 2464256 + 0}
 
 
 def roofline_kernel(tune):
