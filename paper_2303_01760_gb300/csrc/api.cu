@@ -408,11 +408,15 @@ hsm_status hsm_plan_compute_weights(hsm_plan p, hsm_prec prec, uint8_t* node_sta
   if (!p->hrb) HSM_CUDA(p, cudaMallocHost((void**)&p->hrb, 4 * sizeof(int)));
   const bool retry = p->m >= 2 && p->sing_cap >= p->rbf.count && p->rbf.count;
   p->hrb[0] = 0;
-  if (retry) HSM_CUDA(p, cudaMemcpyAsync(p->hrb, p->dev_count + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
-  // (the in-build solve keeps its status in the second word)
-  HSM_CUDA(p, cudaMemcpyAsync(p->hrb + 1, p->dev_flags + (from_build ? 1 : 0), sizeof(unsigned),
-                              cudaMemcpyDeviceToHost, s));
-  HSM_CUDA(p, cudaStreamSynchronize(s));
+  if (from_build) {
+    // the build's read-back already holds the in-build solve's count and bits
+    p->hrb[0] = retry ? p->build_sing : 0;
+    p->hrb[1] = (int)p->build_solve_flags;
+  } else {
+    if (retry) HSM_CUDA(p, cudaMemcpyAsync(p->hrb, p->dev_count + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HSM_CUDA(p, cudaMemcpyAsync(p->hrb + 1, p->dev_flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    HSM_CUDA(p, cudaStreamSynchronize(s));
+  }
   unsigned flags = (unsigned)p->hrb[1];
   if (retry) {
     int sc = (int)std::min<int64_t>(p->hrb[0], p->sing_cap);  // a list holds each system at most once per pass

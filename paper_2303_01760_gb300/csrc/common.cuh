@@ -80,7 +80,7 @@ struct BuildWs {
   uint8_t* sorted_bnd = nullptr;       // [N]
   int32_t* scan_ws = nullptr;          // block sums of the cell scan
   int32_t* scan_ws2 = nullptr;         // block sums of the group partition (a parallel branch)
-  int* readback = nullptr;             // pinned host: demoted, n_mon, n_rbf, flags
+  int* readback = nullptr;             // pinned host: demoted, n_mon, n_rbf, flags, -, singular count, solve flags
   cudaGraphExec_t graph = nullptr;
   int graph_qt = 0;                    // kNN variant the graph was captured with
   int graph_arrange = 0;               // weights arrangement the graph was captured with
@@ -133,6 +133,8 @@ struct hsm_plan_s {
   int64_t n_demoted = 0;
   int64_t n_fallback = 0;
   unsigned build_flags = 0;  // device status bits of the last stencil build (MON weights included)
+  int build_sing = 0;              // its in-build RBF-FD solve (arrange 2): singular systems recorded
+  unsigned build_solve_flags = 0;  // and that solve's status bits
   bool stencils_built = false;
   bool weights_built = false;
   // check mode: every call that gathers through the stencils validates them

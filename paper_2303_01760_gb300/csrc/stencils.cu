@@ -502,6 +502,16 @@ __global__ void k_classify_count(const int32_t* __restrict__ ijk, const uint8_t*
   }
 }
 
+// The build's status words beside its counters for the one read-back: st[3]
+// the status bits, st[5] the in-build solve's singular-system count, st[6]
+// its status bits (st[0..2]: demoted, n_mon, n_rbf; st[4]: k_bounds' arrivals).
+constexpr int kReadbackWords = 7;
+__global__ void k_build_status(const unsigned* __restrict__ flags, const int* __restrict__ counts, int* st) {
+  st[3] = (int)flags[0];
+  st[5] = counts[1];
+  st[6] = (int)flags[1];
+}
+
 __global__ void k_cell_scatter(const double* __restrict__ coords, const uint8_t* __restrict__ is_boundary,
                                int64_t N, int dim, const int32_t* __restrict__ cell_of,
                                const int32_t* __restrict__ start, int32_t* cursor, int32_t* sorted_id,
@@ -828,8 +838,8 @@ hsm_status alloc_build_ws(hsm_plan p) {
   w.hcap = cap;
   CellGrid* cg = nullptr;
   HSM_CUDA(p, dev_alloc(&w.bbox, 2 * kMaxDim, s));
-  HSM_CUDA(p, dev_alloc(&w.lat, 2 * kMaxDim + 5, s));
-  HSM_CUDA(p, cudaMemsetAsync(w.lat, 0, (2 * kMaxDim + 5) * sizeof(int), s));  // k_bounds' arrival count
+  HSM_CUDA(p, dev_alloc(&w.lat, 2 * kMaxDim + kReadbackWords, s));
+  HSM_CUDA(p, cudaMemsetAsync(w.lat, 0, (2 * kMaxDim + kReadbackWords) * sizeof(int), s));  // k_bounds' arrival count
   const int64_t bgrid = (int64_t)num_sms() * 8;  // k_bounds' largest grid
   HSM_CUDA(p, dev_alloc(&w.bpart, bgrid * 2 * kMaxDim, s));
   HSM_CUDA(p, dev_alloc(&w.lpart, bgrid * 2 * kMaxDim, s));
@@ -869,7 +879,7 @@ hsm_status alloc_build_ws(hsm_plan p) {
   HSM_CUDA(p, dev_alloc(&p->rbf.nodes, N, s));
   HSM_CUDA(p, dev_alloc(&p->mon.idx, (size_t)p->mon.width * N, s));
   HSM_CUDA(p, dev_alloc(&p->rbf.idx, (size_t)p->rbf.width * N, s));
-  HSM_CUDA(p, cudaMallocHost((void**)&w.readback, 4 * sizeof(int)));
+  HSM_CUDA(p, cudaMallocHost((void**)&w.readback, kReadbackWords * sizeof(int)));
   HSM_CUDA(p, cudaStreamCreateWithFlags(&w.cap, cudaStreamNonBlocking));
   HSM_CUDA(p, cudaStreamCreateWithFlags(&w.side, cudaStreamNonBlocking));
   HSM_CUDA(p, cudaStreamCreateWithFlags(&w.side2, cudaStreamNonBlocking));
@@ -1062,10 +1072,12 @@ cudaError_t enqueue_build(hsm_plan p, cudaStream_t s, int qt, int* nk) {
       HSM_TRY(cudaStreamWaitEvent(s, w.ev_join3, 0));
     }
   }
-  // ---- status bits next to the counters, then the one read-back
+  // ---- status words next to the counters, then the one read-back
   HSM_TRY(cudaStreamWaitEvent(s, w.ev_join, 0));
-  HSM_TRY(cudaMemcpyAsync(lat + 2 * kMaxDim + 3, p->dev_flags, sizeof(unsigned), cudaMemcpyDeviceToDevice, s));
-  HSM_TRY(cudaMemcpyAsync(w.readback, lat + 2 * kMaxDim, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  k_build_status<<<1, 1, 0, s>>>(p->dev_flags, p->dev_count, lat + 2 * kMaxDim);
+  ++k;
+  HSM_TRY(cudaGetLastError());
+  HSM_TRY(cudaMemcpyAsync(w.readback, lat + 2 * kMaxDim, kReadbackWords * sizeof(int), cudaMemcpyDeviceToHost, s));
   *nk = k;
   return cudaSuccess;
 }
@@ -1153,6 +1165,8 @@ hsm_status build_stencils(hsm_plan p) {
   p->mon.count = rb[1];
   p->rbf.count = rb[2];
   p->build_flags = (unsigned)rb[3];
+  p->build_sing = rb[5];
+  p->build_solve_flags = (unsigned)rb[6];
   p->mon.w64 = w.mon_w64;
   if ((unsigned)rb[3] & kDevKnnShort)
     return set_error(p, HSM_EINVAL, "not enough candidate nodes for an RBF-FD stencil");
