@@ -574,8 +574,10 @@ hsm_status hsm_plan_inject_fault(hsm_plan p, int fault) {
   Group& G = p->rbf.count > 0 ? p->rbf : p->mon;
   if (G.count <= 0) return set_error(p, HSM_ESTATE, "the plan has no stencils");
   // the last entry of the group's first stencil ([width][count] layout) points
-  // one past the last node; check mode goes on first, so no gather follows it
+  // one past the last node; check mode goes on first, so no gather follows it,
+  // and weights a build solved before the forgery are not handed out as new
   p->checks = true;
+  p->rbf_from_build = false;
   const int32_t bad = (int32_t)p->N;
   HSM_CUDA(p, cudaMemcpyAsync(G.idx + (int64_t)(G.width - 1) * G.count, &bad, sizeof(int32_t),
                               cudaMemcpyHostToDevice, p->stream));

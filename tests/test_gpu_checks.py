@@ -13,13 +13,20 @@ from gpu_helpers import make_plan
 pytestmark = pytest.mark.gpu
 
 
-def test_validation_and_check_mode_on_a_forged_index():
+@pytest.mark.parametrize("arrange", [0, 2])
+def test_validation_and_check_mode_on_a_forged_index(arrange):
+    """arrange 2: the weights are solved inside the build; a forgery after the
+    build must still be caught by the weights call's gate."""
     import torch
     from paper_2303_01760_gb300 import hsm
 
     ns = nodesets.square_holes(n=100)
     plan, code, _ = make_plan(ns, m=2)
     assert code == 0
+    if arrange:
+        plan.set_tuning(knn_qt=1, rbf_lanes=8, rbf_lanes32=8, apply_threads=256, arrange=arrange, chunks=1)
+        plan.build_stencils()
+        assert plan.compute_weights(hsm.HSM_PREC_FP64) == 0
     assert plan.validate() == hsm.HSM_OK
     u = torch.from_numpy(nodesets.field_sincos(ns.coords)[0]).cuda()
     ref = plan.apply(u).clone()
