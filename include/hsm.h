@@ -140,6 +140,8 @@ hsm_status hsm_plan_set_spacing(hsm_plan plan, const double* spacing);
  *   node's entry of hsm_plan_set_spacing.  A regular-flagged
  *   node that is a boundary node, is not on the lattice, or misses a lattice
  *   neighbour is demoted to RBF-FD.
+ * In weights arrangement 2 (hsm_plan_set_tuning) the build also solves the
+ * FP64 weights of both groups (see hsm_plan_compute_weights).
  * Synchronises the plan's stream (the group sizes are read back).           */
 hsm_status hsm_plan_build_stencils(hsm_plan plan);
 
@@ -148,10 +150,12 @@ hsm_status hsm_plan_build_stencils(hsm_plan plan);
  * augmented system [A P; P^T 0][w; lambda] = [L phi; L p] with phi = r^3
  * (Section 2.1, Section 4), by the method selected with prec.  With
  * HSM_PREC_FP64 the systems of both groups -- MON (2d+1 unknowns) and RBF-FD
- * (n + C(m+d,m)) -- are solved either in one persistent launch whose blocks
- * draw batches of either kind from one work queue, or as MON weights beside
- * the kNN search in the stencil build plus one RBF-FD launch, whichever
- * hsm_plan_autotune measured faster for the plan (the latter until tuned).
+ * (n + C(m+d,m)) -- are solved in one persistent launch whose blocks draw
+ * batches of either kind from one work queue, or as MON weights beside the
+ * kNN search in the stencil build plus one RBF-FD launch here, or both inside
+ * the stencil build (this call then only takes over their status), whichever
+ * hsm_plan_autotune measured fastest for the plan (the split one until tuned;
+ * see hsm_plan_tuning).
  *   node_status  device u8 [N] or NULL; receives one HSM_NODE_* per node
  * A system is singular when a pivot of the scaled FP64 system (entries of
  * order one) falls below 1e-12 in magnitude or is not finite.  A singular
@@ -160,7 +164,9 @@ hsm_status hsm_plan_build_stencils(hsm_plan plan);
  * stencil on which the degree-m monomials are not unisolvent still gets
  * weights exact for the lower degree.  Returns
  * HSM_ESINGULAR when some node has no valid weights (its weights are then
- * zero and its status HSM_NODE_SINGULAR).  Synchronises the plan's stream (the failure count is read).  */
+ * zero and its status HSM_NODE_SINGULAR).  Synchronises the plan's stream
+ * (the failure count is read), except after a build that solved the weights,
+ * whose read-back already holds it; the retries above always synchronise.   */
 hsm_status hsm_plan_compute_weights(hsm_plan plan, hsm_prec prec, uint8_t* node_status);
 
 /* Sizes after hsm_plan_build_stencils (host outputs; any may be NULL).
