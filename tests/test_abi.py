@@ -78,3 +78,75 @@ def test_spacing_and_fault_hooks_validate_on_the_host():
     assert lib.hsm_plan_set_spacing(h, None) == 0
     lib.hsm_plan_destroy.argtypes = [ctypes.c_void_p]
     assert lib.hsm_plan_destroy(h) == 0
+
+
+def _declarations():
+    """{name: [parameter type strings]} of every function in include/*.h."""
+    out = {}
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if not f.endswith(".h"):
+            continue
+        txt = open(os.path.join(ROOT, "include", f)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        txt = re.sub(r"//[^\n]*", "", txt)
+        for m in re.finditer(r"\b(hsm_[a-z0-9_]+)\s*\(([^;{}]*?)\)\s*;", txt):
+            params = [p.strip() for p in m.group(2).split(",")]
+            out[m.group(1)] = [] if params in ([""], ["void"]) else params
+    return out
+
+
+def _kind_of_c(param, handles, enums):
+    """Broad kind of a C parameter: the type without its name."""
+    t = re.sub(r"\b(const|struct|unsigned\s+char)\b", lambda m: "uchar" if "char" in m.group(0) else "", param)
+    if "*" in t or "[" in t:
+        return "ptr"
+    words = t.split()
+    base = " ".join(words[:-1]) if len(words) > 1 else words[0]
+    if base in handles:
+        return "ptr"
+    if base in enums or base in ("int", "int32_t"):
+        return "i32"
+    if base in ("unsigned", "unsigned int", "uint32_t"):
+        return "u32"
+    if base in ("int64_t", "long long"):
+        return "i64"
+    if base in ("uint64_t", "size_t"):
+        return "u64"
+    return {"double": "f64", "float": "f32"}.get(base, "?" + base)
+
+
+def _kind_of_ctypes(t):
+    if t in (ctypes.c_void_p, ctypes.c_char_p) or hasattr(t, "_type_") and isinstance(t._type_, type):
+        return "ptr"
+    size = ctypes.sizeof(t)
+    if t in (ctypes.c_double,):
+        return "f64"
+    if t in (ctypes.c_float,):
+        return "f32"
+    signed = t(-1).value < 0
+    return {(4, True): "i32", (4, False): "u32", (8, True): "i64", (8, False): "u64"}[(size, signed)]
+
+
+def test_binding_prototypes_match_the_header():
+    """Every ctypes prototype of the Python binding has the parameter count
+    and the broad parameter types (pointer, 32/64-bit signed/unsigned
+    integer, float, double) that include/hsm.h declares, so a signature
+    change on one side cannot go unnoticed until a GPU run."""
+    import sys
+
+    sys.path.insert(0, ROOT)
+    from paper_2303_01760_gb300 import hsm
+
+    header = open(os.path.join(ROOT, "include", "hsm.h")).read()
+    handles = set(re.findall(r"typedef\s+struct\s+\w+\s*\*\s*(\w+)\s*;", header))
+    enums = set(re.findall(r"}\s*(hsm_\w+)\s*;", header)) - handles
+    decl = _declarations()
+    assert len(decl) >= 30
+    checked = 0
+    for name, (_, args) in hsm._SIGS.items():
+        assert name in decl, name
+        c_kinds = [_kind_of_c(p, handles, enums) for p in decl[name]]
+        py_kinds = [_kind_of_ctypes(a) for a in args]
+        assert c_kinds == py_kinds, (name, c_kinds, py_kinds)
+        checked += 1
+    assert checked == len(hsm._SIGS) >= 30
